@@ -1,0 +1,443 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these tests uses a GPU.  Each pin targets a part of the oracle where a
+plausible mistake (dropped term, wrong sign, transposed block, wrong index) would
+show: closed forms, exact identities between the paper's own alternative
+formulas, brute force on tiny inputs, the paper's printed DOF tables, and
+convergence rates.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import workloads as W
+from oracle import assemble as asm
+from oracle import fields, physics as ph, solve, space
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- spaces (Sec. 2.2)
+
+def test_gll_points_closed_form():
+    assert np.allclose(space.gll_points(1), [-1, 1])
+    assert np.allclose(space.gll_points(2), [-1, 0, 1])
+    assert np.allclose(space.gll_points(3), [-1, -1 / np.sqrt(5), 1 / np.sqrt(5), 1])
+    assert np.allclose(space.gll_points(4), [-1, -np.sqrt(3 / 7), 0, np.sqrt(3 / 7), 1])
+
+
+def test_lagrange_reproduces_polynomials():
+    nodes = space.gll_points(3)
+    x = np.linspace(-1, 1, 7)
+    L, dL = space.lagrange(nodes, x)
+    assert np.allclose(space.lagrange(nodes, nodes)[0], np.eye(4))
+    f = lambda t: 2 * t ** 3 - t ** 2 + 0.5
+    df = lambda t: 6 * t ** 2 - 2 * t
+    assert np.allclose(L @ f(nodes), f(x), atol=1e-14)
+    assert np.allclose(dL @ f(nodes), df(x), atol=1e-13)
+
+
+def test_macro_geometry_exact_integrals():
+    # box [0.2, 0.7] x [0.1, 0.4], m = 2, p = 2: integrals of polynomials of degree <= 2p+3
+    g = space.MacroGeometry([0.2, 0.1], [0.7, 0.4], 2, 2)
+    x, y = g.xq
+    assert np.isclose(g.w.sum(), 0.5 * 0.3)
+    exact = (0.7 ** 4 - 0.2 ** 4) / 4 * (0.4 ** 3 - 0.1 ** 3) / 3
+    assert np.isclose(g.w @ (x ** 3 * y ** 2), exact, rtol=1e-14)
+    # C0 nodal interpolation of a Q2 function is exact and its gradient too
+    f = lambda X, Y: X ** 2 * Y - 3 * X * Y ** 2 + Y
+    fn = f(*g.xn)
+    assert np.allclose(g.T[0] @ fn, f(x, y), atol=1e-14)
+    assert np.allclose(g.T[1] @ fn, 2 * x * y - 3 * y ** 2, atol=1e-13)
+    assert np.allclose(g.T[2] @ fn, x ** 2 - 6 * x * y + 1, atol=1e-13)
+
+
+def _simplex_nodes(n, d=3):
+    from math import comb
+    return comb(n + d, d)
+
+
+def _tri_nodes(n):
+    return (n + 1) * (n + 2) // 2
+
+
+def test_dof_tables_of_the_paper():
+    """The paper's DOF tables follow from: u and q C0 on each macro-element with
+    (d+1)(d+2) unknowns per node, trace C0 per macro-face, independent across faces,
+    n_s = 5 unknowns per trace node (Tables 1, 3, 6-8, 10)."""
+    gold = json.load(open(os.path.join(GOLD, "dof_tables.json")))
+    per_node = 4 * 5      # (d+1)(d+2), d = 3
+    t1 = gold["table1_couette_768_elements_p3"]
+    for r in t1["rows"]:
+        mp = r["m"] * t1["p"]
+        assert per_node * _simplex_nodes(mp) == r["local"]
+        assert r["local"] * r["n_macro"] == r["total_local"]
+        faces = (4 * r["n_macro"] + r["boundary_triangles"]) // 2
+        assert 5 * faces * _tri_nodes(mp) == r["global"]
+        assert r["n_macro"] * r["m"] ** 3 == 768
+    t3 = gold["table3_couette_fixed_local"]
+    for r in t3["rows"]:
+        assert per_node * _simplex_nodes(t3["mp"]) == r["local"]
+        assert r["local"] * r["n_macro"] == r["total_local"]
+        faces = (4 * r["n_macro"] + r["boundary_triangles"]) // 2
+        assert 5 * faces * _tri_nodes(t3["mp"]) == r["global"]
+    t6 = gold["table6_sphere_p3"]
+    bnd = []
+    for r in t6["rows"]:
+        mp = r["m"] * t6["p"]
+        assert per_node * _simplex_nodes(mp) * r["n_macro"] == r["total_local"]
+        nf, rem = divmod(r["global"], 5 * _tri_nodes(mp))
+        assert rem == 0
+        bnd.append(2 * nf - 4 * r["n_macro"])
+    assert bnd[0] == 4 * bnd[1]          # each macro boundary triangle holds 4 element triangles
+    t8 = gold["table8_tgv_mp8_periodic"]
+    for r in t8["rows"]:
+        assert per_node * _simplex_nodes(t8["mp"]) * r["n_macro"] == r["total_local"]
+        assert 5 * (2 * r["n_macro"]) * _tri_nodes(t8["mp"]) == r["global"]
+
+
+@pytest.mark.parametrize("d,m,p", [(2, 2, 2), (3, 2, 1), (2, 3, 3)])
+def test_box_node_and_face_counts_brute_force(d, m, p):
+    pr = W.mms(dim=d, nmac=3, m=m, p=p)
+    P = solve.Problem(pr)
+    g = P.geometry(4)
+    pts = {tuple(np.round(x, 12)) for x in g.xn.T}
+    assert len(pts) == P.Np == (m * p + 1) ** d
+    # faces: enumerate unique (axis, position, tangential box) from every macro's boundary
+    faces = set()
+    for e in range(P.E):
+        lo, hi = P.mesh.macro_box(e)
+        for k in range(d):
+            for side in range(2):
+                key = [k, round((lo, hi)[side][k], 12)]
+                key += [round(lo[j], 12) for j in range(d) if j != k]
+                faces.add(tuple(key))
+    assert len(faces) == P.F
+    own = P.mesh.face_owners()
+    assert sum(len(o) for o in own) == 2 * d * P.E
+
+
+# ---------------------------------------------------------------- pointwise physics (Sec. 2.1)
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_inviscid_flux_eigenvalues(d):
+    rng = np.random.default_rng(3)
+    g = 1.4
+    for _ in range(5):
+        rho, T = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+        v = rng.uniform(-0.5, 0.5, d)
+        u = fields.uniform_u(d, rho, v, T, g)
+        n = rng.normal(size=d)
+        n /= np.linalg.norm(n)
+        An = np.zeros((d + 2, d + 2))
+        for s in range(d + 2):
+            up = u.astype(complex)
+            up[s] += 1j * ph.CS_H
+            F = ph.inviscid_flux(list(up), g)
+            An[:, s] = [np.imag(sum(F[t][k] * n[k] for k in range(d))) / ph.CS_H for t in range(d + 2)]
+        ev = np.sort(np.linalg.eigvals(An).real)
+        vn, c = v @ n, np.sqrt(T)
+        assert np.allclose(ev, np.sort([vn - c] + [vn] * d + [vn + c]), atol=1e-12)
+
+
+def test_viscous_flux_closed_forms():
+    """Shear flow v = (a y, 0, 0) with constant rho, and a linear temperature."""
+    g, Re, Pr = 1.4, 50.0, 0.72
+    phys = dict(gamma=g, Re=Re, Pr=Pr)
+    a, rho, T0, bT = 0.3, 1.3, 1.1, 0.2
+    x = np.array([0.4, 0.25, 0.7])
+    # primitives and gradients
+    v = [a * x[1], 0.0, 0.0]
+    gv = [[0.0, a, 0.0], [0.0] * 3, [0.0] * 3]
+    T = T0 + bT * x[0]
+    P = rho * T / g
+    gP = [rho * bT / g, 0.0, 0.0]
+    u = fields.conserved(rho, v, P, g)
+    q = fields.conserved_grad(rho, [0.0] * 3, v, gv, P, gP, g)
+    G = np.array(ph.viscous_flux(list(u), ph.to_list(np.array(q), 2), phys))
+    tau_xy = a / Re
+    assert np.isclose(G[1, 1], -tau_xy) and np.isclose(G[2, 0], -tau_xy)
+    assert np.isclose(G[1, 0], 0.0, atol=1e-15) and np.isclose(G[3, 2], 0.0, atol=1e-15)
+    kcoef = 1.0 / (Re * Pr * (g - 1.0))
+    assert np.isclose(G[4, 0], -(0.0 - (-kcoef * bT)))             # -(tau v - phi)_x
+    assert np.isclose(G[4, 1], -(tau_xy * v[0]))
+
+
+# ---------------------------------------------------------------- residual and Jacobian
+
+def _uniform_state(P, u0):
+    u = np.repeat(u0[None, :, None], P.E, 0).repeat(P.Np, 2)
+    q = np.zeros((P.E, P.d, P.ns, P.Np))
+    uh = np.tile(np.repeat(u0[:, None], P.Nfn, 1).reshape(-1), P.F)
+    return u, q, uh
+
+
+@pytest.mark.parametrize("d,p", [(2, 2), (3, 1)])
+def test_free_stream_preservation(d, p):
+    pr = W.periodic_uniform(dim=d, nmac=2, m=2, p=p)
+    P = solve.Problem(pr)
+    u, q, uh = _uniform_state(P, solve.uniform_from_par(pr))
+    _, _, nrm, _ = solve.global_assemble(P, u, q, uh, want_jac=False)
+    assert nrm["RF"] < 1e-13
+    # the same state with Dirichlet data equal to it on every boundary
+    pr2 = dict(pr, periodic=[0, 0, 0], bc=[W.BC_DIRICHLET] * 6)
+    P2 = solve.Problem(pr2)
+    u, q, uh = _uniform_state(P2, solve.uniform_from_par(pr2))
+    _, _, nrm, _ = solve.global_assemble(P2, u, q, uh, want_jac=False)
+    assert nrm["RF"] < 1e-13
+
+
+def _whole_residual_jacobian(P, geo, e, ue, qe, uhl, tt, src, bf, cols=None):
+    def res(uu, qq, hh):
+        b = asm.assemble_macro(geo, P.phys, uu, qq, hh, tt, src, bf, want_jac=False)
+        return np.concatenate([b["RU"].ravel(), b["RUh"].ravel()])
+    parts = [ue, qe, uhl]
+    sizes = [x.size for x in parts]
+    ncol = sum(sizes)
+    cols = range(ncol) if cols is None else cols
+    out = {}
+    for c in cols:
+        which = 0 if c < sizes[0] else (1 if c < sizes[0] + sizes[1] else 2)
+        off = c - sum(sizes[:which])
+        args = [x.astype(complex) for x in parts]
+        flat = args[which].reshape(-1)
+        flat[off] += 1j * ph.CS_H
+        out[c] = np.imag(res(*args)) / ph.CS_H
+    return out
+
+
+@pytest.mark.parametrize("case", ["mms2d", "couette2d", "mms3d"])
+def test_jacobian_equals_complex_step_of_residual(case):
+    """Every Newton block of eq. C312 equals the derivative of the residual (SUPG on,
+    DIRK time term on), random state: catches any dropped or mis-signed term."""
+    if case == "mms2d":
+        pr, e, cols = W.mms(dim=2, nmac=2, m=2, p=2), 3, None
+    elif case == "couette2d":
+        pr, e, cols = W.couette2d(nmac=2, m=2, p=2), 1, None
+    else:
+        pr, e = W.mms(dim=3, nmac=2, m=2, p=1), 5
+        cols = list(np.random.default_rng(0).choice(135 + 405 + 270, 36, replace=False))
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 7)
+    geo = P.geometry(e)
+    bf, src = P.bfaces(e, geo), P.source(geo)
+    ue, qe, uhl = u[e], q[e], P.local_trace(e, uh)
+    tt = dict(coef=0.7, hist=0.05 * np.ones_like(ue), supg_time=True)
+    blk = asm.assemble_macro(geo, P.phys, ue, qe, uhl, tt, src, bf)
+    Ja = np.block([[blk["Auu"], np.hstack(blk["Auq"]), blk["Auh"]],
+                   [blk["Ahu"], np.hstack(blk["Ahq"]), blk["Ahh"]]])
+    Jc = _whole_residual_jacobian(P, geo, e, ue, qe, uhl, tt, src, bf, cols)
+    scale = np.abs(Ja).max()
+    for c, col in Jc.items():
+        assert np.abs(col - Ja[:, c]).max() <= 1e-12 * scale, c
+    # R_Q is linear: its blocks are the mass, lifting and face matrices
+    Aqq, Aqu, Aqh, _, _ = asm.full_local_blocks(geo, blk)
+    RQ = Aqq @ qe.reshape(-1) + Aqu @ ue.reshape(-1) + Aqh @ uhl.reshape(-1)
+    assert np.allclose(RQ, blk["RQ"].reshape(-1), atol=1e-14)
+
+
+# ---------------------------------------------------------------- condensation (Sec. 3.2-3.3)
+
+@pytest.fixture(scope="module")
+def small2d():
+    pr = W.mms(dim=2, nmac=2, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 11)
+    blks, geos, nrm, _ = solve.global_assemble(P, u, q, uh)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    return P, blks, geos, cond
+
+
+def test_one_layer_equals_second_layer(small2d):
+    P, blks, geos, cond = small2d
+    for e in range(P.E):
+        A1, b1 = solve.condense_one_layer(geos[e], blks[e], shift=0.3)
+        c = cond[e]
+        SinvC = np.linalg.solve(c["S"], c["C"])
+        A2 = c["B"] @ SinvC + c["D"]
+        assert np.abs(A1 - A2).max() <= 1e-11 * np.abs(A1).max()
+        assert np.abs(b1 - c["bhat"]).max() <= 1e-11 * max(np.abs(b1).max(), 1e-300)
+
+
+def test_algorithm2_equals_explicit_matrix(small2d):
+    P, blks, geos, cond = small2d
+    A = solve.explicit_trace_matrix(P, cond)
+    x = W.random_vector(A.shape[0], 5)
+    assert np.allclose(solve.apply_trace(P, cond, x), A @ x, rtol=1e-12, atol=1e-13 * np.abs(A).max())
+
+
+def _monolithic(P, blks, geos, shift):
+    """The global block system of eq. C312 assembled densely (all macros)."""
+    ns, Np, d = P.ns, P.Np, P.d
+    nQ, nU = d * ns * Np, ns * Np
+    nloc = nQ + nU
+    nT = P.F * ns * P.Nfn
+    N = P.E * nloc + nT
+    A = np.zeros((N, N))
+    r = np.zeros(N)
+    for e in range(P.E):
+        Aqq, Aqu, Aqh, Auq, Ahq = asm.full_local_blocks(geos[e], blks[e])
+        Auu = blks[e]["Auu"] + shift * np.kron(np.eye(ns), blks[e]["M"])
+        o = e * nloc
+        eps = P.E * nloc + P.maps[e].reshape(-1)
+        A[o:o + nQ, o:o + nQ] = Aqq
+        A[o:o + nQ, o + nQ:o + nloc] = Aqu
+        A[o + nQ:o + nloc, o:o + nQ] = Auq
+        A[o + nQ:o + nloc, o + nQ:o + nloc] = Auu
+        A[np.ix_(np.arange(o, o + nQ), eps)] += Aqh
+        A[np.ix_(np.arange(o + nQ, o + nloc), eps)] += blks[e]["Auh"]
+        A[np.ix_(eps, np.arange(o, o + nQ))] += Ahq
+        A[np.ix_(eps, np.arange(o + nQ, o + nloc))] += blks[e]["Ahu"]
+        A[np.ix_(eps, eps)] += blks[e]["Ahh"]
+        r[o:o + nQ] = blks[e]["RQ"].reshape(-1)
+        r[o + nQ:o + nloc] = blks[e]["RU"].reshape(-1)
+        np.add.at(r, eps, blks[e]["RUh"].reshape(-1))
+    return A, r
+
+
+def test_condense_solve_recover_equals_monolithic(small2d):
+    P, blks, geos, cond = small2d
+    A, r = _monolithic(P, blks, geos, 0.3)
+    x = np.linalg.solve(A, -r)
+    dU, dQ, dUh, its, _ = solve.linear_step(P, blks, geos, shift=0.3, precond="direct")
+    nloc = P.d * P.ns * P.Np + P.ns * P.Np
+    assert np.allclose(dUh, x[P.E * nloc:], rtol=1e-9, atol=1e-11)
+    for e in range(P.E):
+        o = e * nloc
+        assert np.allclose(dQ[e].reshape(-1), x[o:o + P.d * P.ns * P.Np], atol=1e-9)
+        assert np.allclose(dU[e].reshape(-1), x[o + P.d * P.ns * P.Np:o + nloc], atol=1e-10)
+
+
+def test_fgmres_equals_dense_solve(small2d):
+    P, blks, geos, cond = small2d
+    A = solve.explicit_trace_matrix(P, cond)
+    b = solve.assemble_bhat(P, cond)
+    fb = solve.face_blocks(P, blks)
+    flu = [solve.lu_factor(fb[f]) for f in range(P.F)]
+    M0 = lambda r: solve.block_jacobi(P, flu, r)
+    for M in (M0, lambda r: solve.gmres_fixed(lambda x: A @ x, M0, r, 5)):
+        x, its, res = solve.fgmres(lambda x: solve.apply_trace(P, cond, x), M, b, rtol=1e-13, restart=20)
+        assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+
+
+def test_lu_factor_against_definition_and_scipy():
+    rng = np.random.default_rng(2)
+    for n in (1, 7, 64, 130):
+        A = rng.normal(size=(n, n))
+        LU, piv = solve.lu_factor(A)
+        L = np.tril(LU, -1) + np.eye(n)
+        U = np.triu(LU)
+        assert np.abs(A[piv] - L @ U).max() <= 20 * n * 2.2e-16 * np.abs(A).max()
+        assert np.all(np.abs(L) <= 1.0 + 1e-15)                       # partial pivoting bound
+        b = rng.normal(size=n)
+        assert np.allclose(solve.lu_solve(LU, piv, b), scipy.linalg.solve(A, b), rtol=1e-9)
+    # tie rule: first maximal row wins
+    A = np.array([[1.0, 2.0], [-1.0, 3.0]])
+    LU, piv = solve.lu_factor(A)
+    assert list(piv) == [0, 1]
+
+
+# ---------------------------------------------------------------- time integration (Sec. 2.4)
+
+def test_dirk3_order_conditions_and_stiff_accuracy():
+    A, b, c = solve.alexander_dirk3()
+    al = A[0, 0]
+    assert abs(al ** 3 - 3 * al ** 2 + 1.5 * al - 1 / 6) < 1e-14
+    assert np.isclose(b.sum(), 1) and np.isclose(b @ c, 0.5)
+    assert np.isclose(b @ c ** 2, 1 / 3) and np.isclose(b @ (A @ c), 1 / 6)
+    assert np.allclose(A.sum(1), c)
+    assert np.allclose(A[-1], b) and c[-1] == 1.0                    # stiffly accurate: u^{n+1} = u^{n,s}
+    # L-stability: R(z) = 1 + z b^T (I - z A)^{-1} 1 -> 0 as z -> -inf
+    z = -1e8
+    R = 1 + z * b @ np.linalg.solve(np.eye(3) - z * A, np.ones(3))
+    assert abs(R) < 1e-6
+
+
+def test_dirk_step_conserves_mass_momentum_energy():
+    """Periodic box: the trace equations make the fluxes conservative, so the totals
+    (integrals of u) are constant through each DIRK stage (eq. C242)."""
+    pr = W.periodic_uniform(dim=2, nmac=2, m=2, p=2, v=(0.1, 0.05, 0))
+    P = solve.Problem(pr)
+    u, q, uh = _uniform_state(P, solve.uniform_from_par(pr))
+    du, duh = W.perturbation(pr, 3, amp=2e-3)
+    u = u + du
+    uh = uh + duh
+    def totals(u):
+        return sum(P.geometry(e).w @ (u[e] @ P.geometry(e).T[0].T).T for e in range(P.E))
+    t0 = totals(u)
+    u1, q1, uh1, stats = solve.dirk_step(P, u, q, uh, dt=0.05, rtol=1e-13, precond="direct")
+    assert np.allclose(totals(u1), t0, rtol=0, atol=1e-12)
+    assert all(s["RF"] <= 1e-11 for s in stats)
+
+
+# ---------------------------------------------------------------- convergence rates
+
+def _init_from_field(P, ufun, qfun):
+    u = np.zeros((P.E, P.ns, P.Np))
+    q = np.zeros((P.E, P.d, P.ns, P.Np))
+    uh = np.zeros(P.F * P.ns * P.Nfn)
+    for e in range(P.E):
+        g = P.geometry(e)
+        u[e] = ufun(g.xn)
+        if qfun is not None:
+            q[e] = qfun(g.xn).transpose(1, 0, 2)
+        for fl, (f, _) in enumerate(P.mesh.macro_faces(e)):
+            fc = g.faces[fl]
+            idx = P.maps[e][:, fl * P.Nfn:(fl + 1) * P.Nfn]
+            uh[idx] = np.linalg.lstsq(fc["psi"], (u[e] @ fc["phi"].T).T, rcond=None)[0].T
+    return u, q, uh
+
+
+def _couette_error(n, p):
+    pr = W.couette2d(nmac=n, p=p)
+    P = solve.Problem(pr)
+    u0 = solve.uniform_from_par(pr)
+    u, q, uh = _uniform_state(P, u0)
+    du, duh = W.perturbation(pr, 0)
+    u, q, uh, hist = solve.newton_ser(P, u + du, q, uh + duh, rtol=1e-11, precond="direct")
+    mass = sum(P.geometry(e).w @ (u[e, 0] @ P.geometry(e).T[0].T) for e in range(P.E))
+    yq, wq = np.polynomial.legendre.leggauss(40)
+    yq, wq = (yq + 1) / 2, wq / 2
+    rho1 = fields.couette_exact(yq, pr["Mw"], 1.0, 1.0, P.phys)[0]
+    P0 = mass / (wq @ rho1)
+    err = 0.0
+    for e in range(P.E):
+        g = P.geometry(e)
+        rho, v, E, Pr_, T = ph.primitives(list(u[e] @ g.T[0].T), 1.4)
+        T_ex = fields.couette_exact(g.xq[1], pr["Mw"], 1.0, P0, P.phys)[2]
+        err += g.w @ (T - T_ex) ** 2
+    return np.sqrt(err), hist
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p", [1, 2])
+def test_couette_temperature_converges_at_rate_p_plus_1(p):
+    e1, h1 = _couette_error(2, p)
+    e2, h2 = _couette_error(4, p)
+    assert h1[-1]["RF"] <= 1e-11 * h1[0]["RF"] and h2[-1]["RF"] <= 1e-11 * h2[0]["RF"]
+    assert np.log2(e1 / e2) >= p + 1 - 0.3
+
+
+def _mms_error(n, p):
+    pr = W.mms(dim=2, nmac=n, m=2, p=p, vel=0.1)
+    P = solve.Problem(pr)
+    par = pr["field_par"]
+    u, q, uh = _init_from_field(P, lambda x: fields.mms_u(x, par, 1.4), lambda x: fields.mms_q(x, par, 1.4))
+    u, q, uh, hist = solve.newton_ser(P, u, q, uh, rtol=1e-10, precond="direct")
+    err = 0.0
+    for e in range(P.E):
+        g = P.geometry(e)
+        err += g.w @ np.sum((u[e] @ g.T[0].T - fields.mms_u(g.xq, par, 1.4)) ** 2, 0)
+    return np.sqrt(err), hist
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p", [1, 2])
+def test_manufactured_solution_converges_at_rate_p_plus_1(p):
+    e1, h1 = _mms_error(2, p)
+    e2, h2 = _mms_error(4, p)
+    assert h2[-1]["RF"] <= 1e-10 * h2[0]["RF"]
+    assert np.log2(e1 / e2) >= p + 1 - 0.3
