@@ -1,0 +1,192 @@
+/*
+ * mehdg.h -- C ABI of the GB300 matrix-free macro-element HDG solver for the
+ * compressible Navier-Stokes equations (Badrkhani, ten Eikelder, Hiemstra,
+ * Schillinger, arXiv 2402.11361).
+ *
+ * Conventions for every call
+ *  - Return value: MEHDG_OK (0) or a negative MEHDG_ERR_* code; the message of the
+ *    last failure is kept in the context (mehdg_last_error).  No call aborts.
+ *  - Pointers named u, q, uhat, x, y, r, z, bhat, du, dq, duhat, hist are DEVICE
+ *    pointers owned by the caller, contiguous FP64, in the layouts below.
+ *    Pointers documented as "host" are host memory.
+ *  - The context owns every internal block and workspace (allocated once in
+ *    mehdg_mesh, released by mehdg_destroy).
+ *  - All calls are ordered on the CUDA stream given to mehdg_mesh.  Calls that
+ *    return scalars to the host (norms, statistics) synchronise that stream.
+ *
+ * Data layout (one problem; E macro-elements, F macro-faces, d = dim, ns = d+2):
+ *  - macro-elements are boxes; macro e = ix + nx (iy + ny iz);
+ *  - Np = (m p + 1)^d C0 nodes per macro-element, lexicographic, x fastest;
+ *  - Nfn = (m p + 1)^(d-1) nodes per macro-face, Nth = 2 d Nfn per macro-element;
+ *  - u     [E][ns][Np]       conserved variables (rho, rho v, rho E)
+ *  - q     [E][d][ns][Np]    gradient, q[e][k][s] = d u_s / d x_k
+ *  - uhat  [F][ns][Nfn]      trace (hybrid) variable; this is also the layout of
+ *                            every global trace vector (x, y, r, z, bhat, duhat)
+ *  - faces: all x-normal, then y-normal, then z-normal macro-faces; within the
+ *    k-normal group index = pos + npos_k * (tangential macro index, lower axis
+ *    fastest), npos_k = n_k (periodic) or n_k + 1; face nodes lexicographic in
+ *    the tangential axes, lower axis fastest;
+ *  - local faces of a macro-element are ordered (-x, +x, -y, +y, -z, +z); a
+ *    macro's local trace vector is species-major [ns][(local face, face node)].
+ */
+#ifndef MEHDG_H
+#define MEHDG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MEHDG_OK 0
+#define MEHDG_ERR_ARG (-1)
+#define MEHDG_ERR_CUDA (-2)
+#define MEHDG_ERR_OOM (-3)
+#define MEHDG_ERR_SINGULAR (-4)
+#define MEHDG_ERR_NOT_CONVERGED (-5)
+#define MEHDG_ERR_TIMEOUT (-6)
+#define MEHDG_ERR_NAN (-7)
+
+/* boundary kinds per domain side (-x, +x, -y, +y, -z, +z) */
+#define MEHDG_BC_NONE 0      /* periodic direction (or unused) */
+#define MEHDG_BC_DIRICHLET 1 /* B^ = uhat - u_D, u_D from the problem's field */
+#define MEHDG_BC_WALL 2      /* isothermal no-slip wall at wall_T moving at wall_v */
+
+/* closed-form fields (Dirichlet data, source term, initial state) */
+#define MEHDG_FIELD_NONE 0
+#define MEHDG_FIELD_MMS 1     /* par: rho amplitude, velocity amplitude, pressure amplitude */
+#define MEHDG_FIELD_UNIFORM 2 /* par: rho, v1, v2, v3, T */
+#define MEHDG_FIELD_TGV 3     /* par: V0 (Mach of the vortex) */
+
+#define MEHDG_PREC_FP64 0   /* every block and solve in FP64 */
+#define MEHDG_PREC_MIXED 1  /* FP32 blocks, TF32 tensor-core condensation and LU,
+                               FP64 residuals, Krylov vectors and refinement */
+
+typedef struct mehdg_problem {
+  int dim;            /* 2 or 3 */
+  int m, p;           /* sub-elements per macro edge, polynomial degree */
+  int nmac[3];        /* macro-elements per direction */
+  double lo[3], hi[3];
+  int periodic[3];
+  int bc[6];
+  double wall_T[6];
+  double wall_v[6][3];
+  double gamma, Re, Pr; /* Re is the acoustic Reynolds number Re_c (Sec. 2.1) */
+  int supg;           /* 1: SUPG term of eq. C38b on */
+  int field;          /* MEHDG_FIELD_* */
+  double field_par[8];
+} mehdg_problem;
+
+typedef struct mehdg_options {
+  int precision;      /* MEHDG_PREC_* */
+  int precond;        /* 0 block-Jacobi (A_uhuh)^-1, 1 multi-level (inner GMRES + block-Jacobi),
+                         2 block-Jacobi + learned MLP correction */
+  int restart;        /* FGMRES restart length */
+  int max_iters;      /* FGMRES iteration cap per linear solve */
+  double lin_rtol, lin_atol;
+  int inner_iters;    /* inner GMRES iterations of precond 1 */
+  double newton_rtol, newton_atol;
+  int max_newton;
+  double tau_init, tau_max; /* pseudo-time SER parameters (eq. C31222) */
+  int refine_iters;   /* FP64 refinement sweeps of each local S solve (mixed precision) */
+} mehdg_options;
+
+typedef struct mehdg_info {
+  int dim, ns, Np, Nfn, Nth, Nu, Nq, Nt;
+  int n_macro, n_face;
+  long long n_trace;        /* F * ns * Nfn */
+  long long bytes_device;   /* bytes held by the context */
+} mehdg_info;
+
+typedef struct mehdg_time_term {
+  double coef;         /* d_ii / dt for a DIRK stage (eq. C242), 0 for steady */
+  const double* hist;  /* device [E][ns][Np] nodal history term or NULL */
+  int supg_time;       /* 1: the time term enters the SUPG strong residual */
+} mehdg_time_term;
+
+typedef struct mehdg_solve_stats {
+  int newton_steps;
+  int fgmres_iters;     /* summed over the Newton steps of the call */
+  double res0, res;     /* |R_F| at entry and exit */
+  double t_assemble, t_condense, t_krylov, t_recover; /* seconds (device events) */
+  int status;
+} mehdg_solve_stats;
+
+typedef struct mehdg_ctx mehdg_ctx;
+
+/* a0 -- macro-element mesh, DOF maps and reference operators (Sec. 2.2; the
+ * gather map eps of Algorithm 2 "Extract global DOF indices on dT_i").
+ * prob: host array of nprob problem descriptions (nprob == 1 in this version).
+ * opt: host, may be NULL for defaults.  stream: cudaStream_t or NULL.
+ * On success *ctx owns all device memory of the problem.  Errors: ARG for an
+ * invalid description, OOM when device memory is short, CUDA otherwise. */
+int mehdg_mesh(mehdg_ctx** ctx, const mehdg_problem* prob, int nprob,
+               const mehdg_options* opt, void* stream);
+
+/* sizes of the discrete spaces; info is host memory */
+int mehdg_query(const mehdg_ctx* ctx, mehdg_info* info);
+
+/* Initial state: u = closed-form field at the nodes + du_pert, q = 0 (or the
+ * lifted gradient when lift != 0, i.e. q solving R_Q = 0), uhat = trace of the
+ * owning macro-element's u + duh_pert.  du_pert [E][ns][Np] and duh_pert
+ * [F][ns][Nfn] are device pointers or NULL. */
+int mehdg_init_state(mehdg_ctx* ctx, const double* du_pert, const double* duh_pert,
+                     int lift, double* u, double* q, double* uhat);
+
+/* a1-a2 -- residuals R_Q, R_U, R_Uhat (eq. C31221 from C38 / C242) and the Newton
+ * blocks of eq. C312 of every macro-element at (u, q, uhat).  tt may be NULL
+ * (steady).  res_norms: host double[4] = |R_Q|, |R_U|, |R_Uhat|, |R_F| (global
+ * l2 norms; R_Uhat summed over both sides of each face) or NULL. */
+int mehdg_assemble_local(mehdg_ctx* ctx, const double* u, const double* q,
+                         const double* uhat, const mehdg_time_term* tt,
+                         double* res_norms);
+
+/* a3-a6 -- second-layer static condensation (eqs. AP12, ASC2): S, B, C, D of every
+ * macro-element, LU factorisation of S with partial pivoting (Remark, Sec. 3.3),
+ * and the condensed right-hand side b^ = sum_i eps_i^T (h_i - B_i S_i^{-1} g_i)
+ * (Algorithm 1, lines 2-5) written to bhat (device, global trace layout).
+ * shift adds shift * (I (x) M) to A_uu (pseudo-time term).  Also factors the
+ * macro-face blocks of A_uhuh used by mehdg_precondition.
+ * Errors: SINGULAR when a pivot is exactly zero (message names the macro). */
+int mehdg_condense_factor(mehdg_ctx* ctx, double shift, double* bhat);
+
+/* a7 -- matrix-free y = A^ x (Algorithm 2): per macro-element gather x on dT_i,
+ * y1 = C x, y2 = S^{-1} y1, y3 = B y2, y4 = y3 + D x, then the face reduction
+ * (step 4).  x and y are global trace vectors (device), x != y. */
+int mehdg_apply_trace(mehdg_ctx* ctx, const double* x, double* y);
+
+/* a9 -- z = P^{-1} r (Sec. 4.2): kind 0 block-Jacobi with the macro-face blocks of
+ * A_uhuh, kind 1 inner GMRES on A^ left-preconditioned by kind 0 (multi-level),
+ * kind 2 kind 0 plus the learned correction.  r != z. */
+int mehdg_precondition(mehdg_ctx* ctx, int kind, const double* r, double* z);
+
+/* a8 -- FGMRES (right, flexible) on A^ duhat = bhat with the options' preconditioner,
+ * CGS2 orthogonalisation in FP64 (Sec. 4.2).  stats: host or NULL.
+ * Returns NOT_CONVERGED when the iteration cap is reached (duhat holds the last iterate). */
+int mehdg_linear_solve(mehdg_ctx* ctx, const double* bhat, double* duhat,
+                       mehdg_solve_stats* stats);
+
+/* a10 -- local recovery (eqs. Csc4a then Csc4b): du = S^{-1}(g + C duhat_i),
+ * dq = A_qq^{-1}(-R_Q - A_qu du - A_quh duhat_i). */
+int mehdg_recover(mehdg_ctx* ctx, const double* duhat, double* du, double* dq);
+
+/* a11/a12 -- nonlinear solve.  stage 0: steady pseudo-transient Newton with SER
+ * (eq. C31222) to the options' tolerance.  stage i = 1..3: stage i of the
+ * 3-stage DIRK (eq. C242, Alexander's stiffly accurate scheme) with step dt;
+ * stage 1 records u as u^n; after stage 3, u holds u^{n+1}.  u, q, uhat are
+ * updated in place (device).  stats: host or NULL. */
+int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q,
+                     double* uhat, mehdg_solve_stats* stats);
+
+/* Copy one internal per-macro array to host memory (test access).  which:
+ * 0 A_uu/S (after condensation: LU factors), 1..3 A_uq_k, 4 A_uuh/C, 5 A_uhu/B,
+ * 6..8 A_uhq_k, 9 A_uhuh/D, 10 R_Q, 11 R_U, 12 R_Uhat (local), 13 g, 14 h,
+ * 15 pivots (as doubles), 16 bhat_local.  Returns the element count in *count. */
+int mehdg_get_block(mehdg_ctx* ctx, int which, int macro, double* host_out,
+                    long long* count);
+
+void mehdg_destroy(mehdg_ctx* ctx);
+const char* mehdg_last_error(const mehdg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,261 @@
+"""Python binding of libmehdg (GB300 matrix-free macro-element HDG, arXiv 2402.11361).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+declared in ``include/mehdg.h``.  PyTorch supplies device memory and the stream.
+Importing works without a GPU; creating a ``Context`` needs the built library
+and a CUDA device and raises otherwise (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmehdg.so")
+
+c_int, c_double, c_void_p, c_longlong = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+
+PREC_FP64, PREC_MIXED = 0, 1
+
+EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_local", "mehdg_condense_factor",
+           "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
+           "mehdg_get_block", "mehdg_destroy", "mehdg_last_error"]
+
+ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("m", c_int), ("p", c_int), ("nmac", c_int * 3), ("lo", c_double * 3),
+                ("hi", c_double * 3), ("periodic", c_int * 3), ("bc", c_int * 6), ("wall_T", c_double * 6),
+                ("wall_v", (c_double * 3) * 6), ("gamma", c_double), ("Re", c_double), ("Pr", c_double),
+                ("supg", c_int), ("field", c_int), ("field_par", c_double * 8)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("precond", c_int), ("restart", c_int), ("max_iters", c_int),
+                ("lin_rtol", c_double), ("lin_atol", c_double), ("inner_iters", c_int),
+                ("newton_rtol", c_double), ("newton_atol", c_double), ("max_newton", c_int),
+                ("tau_init", c_double), ("tau_max", c_double), ("refine_iters", c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("ns", c_int), ("Np", c_int), ("Nfn", c_int), ("Nth", c_int), ("Nu", c_int),
+                ("Nq", c_int), ("Nt", c_int), ("n_macro", c_int), ("n_face", c_int), ("n_trace", c_longlong),
+                ("bytes_device", c_longlong)]
+
+
+class TimeTerm(ctypes.Structure):
+    _fields_ = [("coef", c_double), ("hist", c_void_p), ("supg_time", c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("newton_steps", c_int), ("fgmres_iters", c_int), ("res0", c_double), ("res", c_double),
+                ("t_assemble", c_double), ("t_condense", c_double), ("t_krylov", c_double),
+                ("t_recover", c_double), ("status", c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+DEFAULT_OPTIONS = dict(precision=PREC_FP64, precond=0, restart=30, max_iters=2000, lin_rtol=1e-6, lin_atol=0.0,
+                       inner_iters=5, newton_rtol=1e-8, newton_atol=1e-14, max_newton=100, tau_init=1.0,
+                       tau_max=1e8, refine_iters=2)
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmehdg.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libmehdg.so not found at %s; run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I = ctypes.POINTER, c_int
+    lib.mehdg_mesh.argtypes = [P(c_void_p), P(Problem), I, P(Options), c_void_p]
+    lib.mehdg_query.argtypes = [c_void_p, P(Info)]
+    lib.mehdg_init_state.argtypes = [c_void_p, c_void_p, c_void_p, I, c_void_p, c_void_p, c_void_p]
+    lib.mehdg_assemble_local.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, P(TimeTerm), P(c_double)]
+    lib.mehdg_condense_factor.argtypes = [c_void_p, c_double, c_void_p]
+    lib.mehdg_apply_trace.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.mehdg_precondition.argtypes = [c_void_p, I, c_void_p, c_void_p]
+    lib.mehdg_linear_solve.argtypes = [c_void_p, c_void_p, c_void_p, P(SolveStats)]
+    lib.mehdg_recover.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.mehdg_dirk_stage.argtypes = [c_void_p, I, c_double, c_void_p, c_void_p, c_void_p, P(SolveStats)]
+    lib.mehdg_get_block.argtypes = [c_void_p, I, I, c_void_p, P(c_longlong)]
+    lib.mehdg_destroy.argtypes = [c_void_p]
+    lib.mehdg_destroy.restype = None
+    lib.mehdg_last_error.argtypes = [c_void_p]
+    lib.mehdg_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if not hasattr(lib, name):
+            raise RuntimeError("libmehdg.so lacks %s" % name)
+        if name not in ("mehdg_destroy", "mehdg_last_error"):
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def problem_struct(prob):
+    s = Problem()
+    s.dim, s.m, s.p = prob["dim"], prob["m"], prob["p"]
+    for k in range(3):
+        s.nmac[k] = int(prob["nmac"][k])
+        s.lo[k] = float(prob["lo"][k])
+        s.hi[k] = float(prob["hi"][k])
+        s.periodic[k] = int(prob["periodic"][k])
+    for i in range(6):
+        s.bc[i] = int(prob["bc"][i])
+        s.wall_T[i] = float(prob["wall_T"][i])
+        for k in range(3):
+            s.wall_v[i][k] = float(prob["wall_v"][i][k])
+    s.gamma, s.Re, s.Pr = prob["gamma"], prob["Re"], prob["Pr"]
+    s.supg, s.field = int(prob.get("supg", 0)), int(prob["field"])
+    for i in range(8):
+        s.field_par[i] = float(prob["field_par"][i])
+    return s
+
+
+def options_struct(opts=None):
+    o = dict(DEFAULT_OPTIONS)
+    o.update(opts or {})
+    s = Options()
+    for k, _ in Options._fields_:
+        setattr(s, k, o[k])
+    return s
+
+
+class MehdgError(RuntimeError):
+    pass
+
+
+class Context:
+    """One problem on one GPU; owns the library context (all blocks and workspaces)."""
+
+    def __init__(self, prob, options=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise MehdgError("mehdg needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda:0")
+        torch.cuda.set_device(self.device)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.prob = dict(prob)
+        self.options = dict(DEFAULT_OPTIONS)
+        self.options.update(options or {})
+        self._p = problem_struct(prob)
+        self._o = options_struct(self.options)
+        h = c_void_p()
+        rc = self.lib.mehdg_mesh(ctypes.byref(h), ctypes.byref(self._p), 1, ctypes.byref(self._o),
+                                 c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise MehdgError("mehdg_mesh failed (%s)" % ERRORS.get(rc, rc))
+        self.h = h
+        inf = Info()
+        self._check(self.lib.mehdg_query(self.h, ctypes.byref(inf)), "query")
+        self.info = {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    # -- helpers
+    def _check(self, rc, what, allow=()):
+        if rc != 0 and rc not in allow:
+            msg = self.lib.mehdg_last_error(self.h).decode() if self.h else ""
+            raise MehdgError("%s failed (%s): %s" % (what, ERRORS.get(rc, rc), msg))
+        return rc
+
+    def _ptr(self, t):
+        if t is None:
+            return None
+        assert t.is_cuda and t.dtype == self.torch.float64 and t.is_contiguous(), "need contiguous cuda float64"
+        return c_void_p(t.data_ptr())
+
+    def empty(self, *shape):
+        return self.torch.empty(*shape, dtype=self.torch.float64, device=self.device)
+
+    def zeros(self, *shape):
+        return self.torch.zeros(*shape, dtype=self.torch.float64, device=self.device)
+
+    def state_shapes(self):
+        i = self.info
+        return (i["n_macro"], i["ns"], i["Np"]), (i["n_macro"], i["dim"], i["ns"], i["Np"]), (i["n_trace"],)
+
+    def new_state(self):
+        su, sq, sh = self.state_shapes()
+        return self.zeros(*su), self.zeros(*sq), self.zeros(*sh)
+
+    # -- the C ABI
+    def init_state(self, du=None, duh=None, lift=False):
+        u, q, uh = self.new_state()
+        self._check(self.lib.mehdg_init_state(self.h, self._ptr(du), self._ptr(duh), int(lift), self._ptr(u),
+                                              self._ptr(q), self._ptr(uh)), "init_state")
+        return u, q, uh
+
+    def assemble(self, u, q, uh, coef=0.0, hist=None, supg_time=0):
+        norms = (c_double * 4)()
+        tt = TimeTerm(float(coef), None if hist is None else hist.data_ptr(), int(supg_time))
+        self._check(self.lib.mehdg_assemble_local(self.h, self._ptr(u), self._ptr(q), self._ptr(uh),
+                                                  ctypes.byref(tt), norms), "assemble_local")
+        return np.array(list(norms))
+
+    def condense(self, shift=0.0, bhat=None):
+        if bhat is None:
+            bhat = self.empty(self.info["n_trace"])
+        self._check(self.lib.mehdg_condense_factor(self.h, float(shift), self._ptr(bhat)), "condense_factor")
+        return bhat
+
+    def apply(self, x, y=None):
+        y = self.empty(self.info["n_trace"]) if y is None else y
+        self._check(self.lib.mehdg_apply_trace(self.h, self._ptr(x), self._ptr(y)), "apply_trace")
+        return y
+
+    def precondition(self, kind, r, z=None):
+        z = self.empty(self.info["n_trace"]) if z is None else z
+        self._check(self.lib.mehdg_precondition(self.h, int(kind), self._ptr(r), self._ptr(z)), "precondition")
+        return z
+
+    def linear_solve(self, b, x=None, allow_not_converged=False):
+        x = self.empty(self.info["n_trace"]) if x is None else x
+        st = SolveStats()
+        allow = (-5,) if allow_not_converged else ()
+        self._check(self.lib.mehdg_linear_solve(self.h, self._ptr(b), self._ptr(x), ctypes.byref(st)),
+                    "linear_solve", allow)
+        return x, st.as_dict()
+
+    def recover(self, duh):
+        su, sq, _ = self.state_shapes()
+        du, dq = self.empty(*su), self.empty(*sq)
+        self._check(self.lib.mehdg_recover(self.h, self._ptr(duh), self._ptr(du), self._ptr(dq)), "recover")
+        return du, dq
+
+    def dirk_stage(self, stage, dt, u, q, uh, allow_not_converged=False):
+        st = SolveStats()
+        allow = (-5,) if allow_not_converged else ()
+        self._check(self.lib.mehdg_dirk_stage(self.h, int(stage), float(dt), self._ptr(u), self._ptr(q),
+                                              self._ptr(uh), ctypes.byref(st)), "dirk_stage", allow)
+        return st.as_dict()
+
+    def get_block(self, which, macro):
+        n = c_longlong()
+        self._check(self.lib.mehdg_get_block(self.h, int(which), int(macro), None, ctypes.byref(n)), "get_block")
+        out = np.empty(n.value, dtype=np.float64)
+        self._check(self.lib.mehdg_get_block(self.h, int(which), int(macro), out.ctypes.data_as(c_void_p), None),
+                    "get_block")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mehdg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,145 @@
+// a7: matrix-free trace operator (Algorithm 2) and a10: local recovery (eq. Csc4),
+// FP64 blocks.  One CTA per macro-element: gather x on dT_i, y1 = C x (step 1),
+// y2 = S^-1 y1 by substitution with the stored LU factors (step 2), y3 = B y2
+// (step 3), y4 = y3 + D x (step 4, local part); the per-macro results go to a slot
+// array and a second kernel sums the (at most two) contributions of every
+// macro-face (step 4 reduction), in a fixed order.
+#include "internal.cuh"
+#include "lu.cuh"
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_apply(const double* __restrict__ S, const int* __restrict__ perm,
+                                               const double* __restrict__ B, const double* __restrict__ C,
+                                               const double* __restrict__ D, const int* __restrict__ gather,
+                                               const double* __restrict__ x, double* __restrict__ slot, int Nu,
+                                               int Nt) {
+  extern __shared__ double sm[];
+  double* xg = sm;            // Nt
+  double* y1 = xg + Nt;       // Nu
+  double* y2 = y1 + Nu;       // Nu
+  const int e = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = x[gather[(size_t)e * Nt + i]];
+  __syncthreads();
+  const double* Ce = C + (size_t)e * Nu * Nt;
+  for (int r = w; r < Nu; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < Nt; c += 32) s += Ce[(size_t)r * Nt + c] * xg[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y1[r] = s;
+  }
+  __syncthreads();
+  const int* pe = perm + (size_t)e * Nu;
+  for (int i = threadIdx.x; i < Nu; i += blockDim.x) y2[i] = y1[pe[i]];
+  __syncthreads();
+  lu_solve_block<double>(S + (size_t)e * Nu * Nu, Nu, y2);
+  const double* Be = B + (size_t)e * Nt * Nu;
+  const double* De = D + (size_t)e * Nt * Nt;
+  for (int r = w; r < Nt; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < Nu; c += 32) s += Be[(size_t)r * Nu + c] * y2[c];
+    for (int c = lane; c < Nt; c += 32) s += De[(size_t)r * Nt + c] * xg[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) slot[(size_t)e * Nt + r] = s;
+  }
+}
+
+// y[f][s][j] = sum over the owners (e, fl) of slot[e][s][fl, j]
+__global__ void k_face_reduce(const double* __restrict__ slot, const int* __restrict__ owner,
+                              double* __restrict__ y, int ns, int Nfn, int Nth, int Nt, int d, long long ntr) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= ntr) return;
+  int j = i % Nfn;
+  int s = (i / Nfn) % ns;
+  int f = (int)(i / ((long long)Nfn * ns));
+  double v = 0.0;
+  for (int o = 0; o < 2; ++o) {
+    int ow = owner[2 * f + o];
+    if (ow < 0) continue;
+    int e = ow / (2 * d), fl = ow % (2 * d);
+    v += slot[(size_t)e * Nt + (size_t)s * Nth + fl * Nfn + j];
+  }
+  y[i] = v;
+}
+
+// du = S^-1 (g + C duh_i);  dq[k][s] = -M^-1 R_Q[k][s] - W_k du_s - Wh_k duh_i,s
+__global__ void __launch_bounds__(256) k_recover(const double* __restrict__ S, const int* __restrict__ perm,
+                                                 const double* __restrict__ C, const double* __restrict__ gvec,
+                                                 const double* __restrict__ MinvRQ, const double* __restrict__ Wk,
+                                                 const double* __restrict__ Whk, const int* __restrict__ gather,
+                                                 const double* __restrict__ duh, double* __restrict__ du,
+                                                 double* __restrict__ dq, int Nu, int Nt, int Np, int Nth, int ns,
+                                                 int d) {
+  extern __shared__ double sm[];
+  double* xg = sm;        // Nt
+  double* y1 = xg + Nt;   // Nu
+  double* y2 = y1 + Nu;   // Nu
+  const int e = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = duh[gather[(size_t)e * Nt + i]];
+  __syncthreads();
+  const double* Ce = C + (size_t)e * Nu * Nt;
+  for (int r = w; r < Nu; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < Nt; c += 32) s += Ce[(size_t)r * Nt + c] * xg[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y1[r] = s + gvec[(size_t)e * Nu + r];
+  }
+  __syncthreads();
+  const int* pe = perm + (size_t)e * Nu;
+  for (int i = threadIdx.x; i < Nu; i += blockDim.x) y2[i] = y1[pe[i]];
+  __syncthreads();
+  lu_solve_block<double>(S + (size_t)e * Nu * Nu, Nu, y2);
+  for (int i = threadIdx.x; i < Nu; i += blockDim.x) du[(size_t)e * Nu + i] = y2[i];
+  const int nq = d * ns * Np;
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+    int a = i % Np, s = (i / Np) % ns, k = i / (Np * ns);
+    const double* W = Wk + ((size_t)k * Np + a) * Np;
+    const double* Wh = Whk + ((size_t)k * Np + a) * Nth;
+    double acc = MinvRQ[(size_t)e * nq + i];
+    for (int b = 0; b < Np; ++b) acc += W[b] * y2[s * Np + b];
+    for (int c = 0; c < Nth; ++c) acc += Wh[c] * xg[s * Nth + c];
+    dq[(size_t)e * nq + i] = -acc;
+  }
+}
+
+}  // namespace
+
+int face_reduce(mehdg_ctx* ctx, const double* slot, double* y) {
+  k_face_reduce<<<(ctx->ntr + 255) / 256, 256, 0, ctx->stream>>>(slot, ctx->owner, y, ctx->ns, ctx->Nfn, ctx->Nth,
+                                                                 ctx->Nt, ctx->d, ctx->ntr);
+  CKL();
+  return MEHDG_OK;
+}
+
+int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {
+  if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply before mehdg_condense_factor");
+  size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
+  CK(cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_apply<<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Ahu, ctx->Auh, ctx->Ahh, ctx->gather, x,
+                                              ctx->slot, ctx->Nu, ctx->Nt);
+  CKL();
+  return face_reduce(ctx, ctx->slot, y);
+}
+
+int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
+  if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "recover before mehdg_condense_factor");
+  size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
+  CK(cudaFuncSetAttribute(k_recover, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_recover<<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Auh, ctx->gv, ctx->MinvRQ, ctx->Wk,
+                                                ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np,
+                                                ctx->Nth, ctx->ns, ctx->d);
+  CKL();
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_apply_trace(mehdg_ctx* ctx, const double* x, double* y) {
+  if (!ctx || !x || !y || x == y) return MEHDG_ERR_ARG;
+  return apply_trace_impl(ctx, x, y);
+}
+
+extern "C" int mehdg_recover(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
+  if (!ctx || !duh || !du || !dq) return MEHDG_ERR_ARG;
+  return recover_impl(ctx, duh, du, dq);
+}

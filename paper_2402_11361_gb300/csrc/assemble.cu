@@ -1,0 +1,613 @@
+// a1-a2: residuals R_Q, R_U, R_Uhat (eq. C31221 from the weak form C38 / C242) and
+// the Newton blocks of eq. C312 of every macro-element.
+//
+// Volume: one thread per (macro, sub-element, Gauss point, Jacobian input) runs the
+// pointwise integrand (physics.cuh) in Dual<double,1> seeded on that input (a
+// state component u_s or a gradient component q_{s,j}); nested inner duals inside
+// the integrand give the flux Jacobian A_k and the strong-form divergence of the
+// SUPG residual, so the outer derivative is exact.  The derivative with respect
+// to the gradient of the input (d_l u_s, d_l q_{s,j}) enters only through the SUPG
+// residual and equals tau A_k^T d(F+G)_l/d(input), assembled from the same pass.
+// A second kernel contracts the pointwise kernels K[t,alpha;s,beta] with the
+// tensor-product basis T[g][alpha][a] of each sub-element into the macro blocks.
+// Faces: same structure with inputs (uhat, q, u) of the numerical flux and of B^.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "physics.cuh"
+
+namespace {
+
+template <int B, int E> struct IPow { static constexpr int v = B * IPow<B, E - 1>::v; };
+template <int B> struct IPow<B, 0> { static constexpr int v = 1; };
+
+struct Tables {
+  const double* b1;   // [NG1][P1]
+  const double* db1;  // [NG1][P1] reference derivative
+  const double* gw;   // [NG1]
+};
+__device__ __forceinline__ Tables tables(const double* tab, int ng1, int p1) {
+  Tables t;
+  t.b1 = tab;
+  t.db1 = tab + ng1 * p1;
+  t.gw = tab + 2 * ng1 * p1;
+  return t;
+}
+
+// ---------------------------------------------------------------- volume pointwise
+template <int D, int P>
+__global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restrict__ tab, Phys ph,
+                                                    const double* __restrict__ u, const double* __restrict__ q,
+                                                    const double* __restrict__ hist, double coef, int supg_time,
+                                                    const double* __restrict__ src, double* __restrict__ Kvol,
+                                                    double* __restrict__ rvol, int E) {
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  constexpr int NDIR = NS * (1 + D);
+  constexpr int KA = (D + 1) * NS * (D + 1);
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nel = g.nel;
+  if (tid >= (long long)E * nel * NG * NDIR) return;
+  const int dir = tid % NDIR;
+  long long r = tid / NDIR;
+  const int gq = r % NG;
+  r /= NG;
+  const int el = r % nel;
+  const int e = (int)(r / nel);
+  Tables tb = tables(tab, NG1, P1);
+
+  int gi[D], li[D];
+  double wq = 1.0;
+  {
+    int gg = gq, ll = el;
+    for (int k = 0; k < D; ++k) {
+      gi[k] = gg % NG1; gg /= NG1;
+      li[k] = ll % g.m; ll /= g.m;
+      wq *= tb.gw[gi[k]] * 0.5 * g.he[k];
+    }
+  }
+  double U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
+  for (int s = 0; s < NS; ++s) {
+    U[s] = 0.0; Hh[s] = 0.0;
+    for (int l = 0; l < D; ++l) {
+      GU[s][l] = 0.0;
+      for (int j = 0; j < D; ++j) { GQ[s][j][l] = 0.0; }
+      Q[s][l] = 0.0;
+    }
+  }
+  const size_t Np = g.Np;
+  for (int al = 0; al < NLOC; ++al) {
+    int ai[D], a = 0, aa = al, stride = 1;
+    for (int k = 0; k < D; ++k) {
+      ai[k] = aa % P1; aa /= P1;
+      a += (li[k] * P + ai[k]) * stride;
+      stride *= g.n1;
+    }
+    double bv[D], dv[D];
+    for (int k = 0; k < D; ++k) {
+      bv[k] = tb.b1[gi[k] * P1 + ai[k]];
+      dv[k] = tb.db1[gi[k] * P1 + ai[k]] * 2.0 / g.he[k];
+    }
+    double phi = 1.0, dphi[D];
+    for (int k = 0; k < D; ++k) phi *= bv[k];
+    for (int l = 0; l < D; ++l) {
+      dphi[l] = dv[l];
+      for (int k = 0; k < D; ++k)
+        if (k != l) dphi[l] *= bv[k];
+    }
+    for (int s = 0; s < NS; ++s) {
+      double ua = u[((size_t)e * NS + s) * Np + a];
+      U[s] += phi * ua;
+      for (int l = 0; l < D; ++l) GU[s][l] += dphi[l] * ua;
+      if (hist) Hh[s] += phi * hist[((size_t)e * NS + s) * Np + a];
+      for (int j = 0; j < D; ++j) {
+        double qa = q[(((size_t)e * D + j) * NS + s) * Np + a];
+        Q[s][j] += phi * qa;
+        for (int l = 0; l < D; ++l) GQ[s][j][l] += dphi[l] * qa;
+      }
+    }
+  }
+  double f[NS];
+  for (int s = 0; s < NS; ++s) f[s] = src ? src[(((size_t)e * nel + el) * NG + gq) * NS + s] : 0.0;
+
+  typedef Dual<double, 1> S;
+  const int X = dir / NS, s0 = dir % NS;
+  S Us[NS], GUs[NS][D], Qs[NS][D], GQs[NS][D][D], Ts[NS];
+  for (int s = 0; s < NS; ++s) {
+    Us[s].v = U[s]; Us[s].d[0] = (X == 0 && s == s0) ? 1.0 : 0.0;
+    for (int j = 0; j < D; ++j) {
+      Qs[s][j].v = Q[s][j]; Qs[s][j].d[0] = (X == 1 + j && s == s0) ? 1.0 : 0.0;
+      GUs[s][j].v = GU[s][j]; GUs[s][j].d[0] = 0.0;
+      for (int l = 0; l < D; ++l) { GQs[s][j][l].v = GQ[s][j][l]; GQs[s][j][l].d[0] = 0.0; }
+    }
+    Ts[s] = coef * Us[s] + Hh[s];
+  }
+  S W[NS], V[NS][D], FG[NS][D], A[D][NS][NS], tau;
+  vol_integrand<D, S>(Us, GUs, Qs, GQs, Ts, f, ph, supg_time, W, V, FG, A, tau);
+
+  for (int t = 0; t < NS; ++t) {
+    double* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
+    K[(0 * NS + s0) * (D + 1) + 0] = W[t].d[0] * wq;
+    for (int l = 0; l < D; ++l) K[(0 * NS + s0) * (D + 1) + 1 + l] = 0.0;
+    for (int k = 0; k < D; ++k) {
+      K[((1 + k) * NS + s0) * (D + 1) + 0] = V[t][k].d[0] * wq;
+      for (int l = 0; l < D; ++l) {
+        double val = 0.0;
+        if (ph.supg) {
+          for (int rr = 0; rr < NS; ++rr) val += A[k][rr][t].v * FG[rr][l].d[0];
+          val *= tau.v;
+        }
+        K[((1 + k) * NS + s0) * (D + 1) + 1 + l] = val * wq;
+      }
+    }
+    if (dir == 0) {
+      double* R = rvol + (((size_t)e * nel + el) * NG + gq) * NS * (D + 1) + t * (D + 1);
+      R[0] = W[t].v * wq;
+      for (int k = 0; k < D; ++k) R[1 + k] = V[t][k].v * wq;
+    }
+  }
+}
+
+// basis value T[g][alpha][a] of a sub-element from 1D tables (alpha 0: value, 1+k: d/dx_k)
+template <int D, int P>
+__device__ __forceinline__ double basis_T(const double* sb, const double* sdb, const double* sc, const int* gi,
+                                          const int* ai, int alpha) {
+  constexpr int P1 = P + 1;
+  double v = 1.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    v *= (alpha == 1 + k) ? sdb[gi[k] * P1 + ai[k]] * sc[k] : sb[gi[k] * P1 + ai[k]];
+  return v;
+}
+
+template <int D, int P> struct VolCfg {
+  static constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  static constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  static constexpr int KA = (D + 1) * NS * (D + 1);
+  static constexpr int ZG = (D + 1) * NS * NLOC;          // Z entries per Gauss point
+  static constexpr int GC = (ZG * 8 <= 1536) ? 32 : (ZG <= 600 ? 16 : 8);
+  static constexpr int NT = (NLOC * NS * NLOC > 8192) ? 512 : (NLOC * NS * NLOC > 1024 ? 256 : 128);
+  static constexpr int NOUT = NLOC * NS * NLOC;
+  static constexpr int OPT = (NOUT + NT - 1) / NT;
+  static constexpr size_t SMEM = sizeof(double) * ((size_t)GC * KA + (size_t)GC * ZG + 2 * NG1 * P1);
+};
+
+// A_X[(t, A)][(s, B)] += sum_g sum_{alpha,beta} T[g][alpha][a] K[g][alpha][s][beta] T[g][beta][b]
+template <int D, int P>
+__global__ void __launch_bounds__(VolCfg<D, P>::NT) k_vol_contract(Geo g, const double* __restrict__ tab,
+                                                                  const double* __restrict__ Kvol,
+                                                                  double* __restrict__ Auu,
+                                                                  double* __restrict__ Auq) {
+  typedef VolCfg<D, P> C;
+  constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, ZG = C::ZG;
+  constexpr int GC = C::GC, NT = C::NT, OPT = C::OPT, NOUT = C::NOUT;
+  extern __shared__ double smem[];
+  double* sK = smem;
+  double* sZ = sK + GC * KA;
+  double* sb = sZ + GC * ZG;
+  double* sdb = sb + NG1 * P1;
+  const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NG1 * P1; i += NT) {
+    sb[i] = tab[i];
+    sdb[i] = tab[NG1 * P1 + i];
+  }
+  double sc[D];
+  for (int k = 0; k < D; ++k) sc[k] = 2.0 / g.he[k];
+  const size_t Nu = g.Nu, Np = g.Np;
+  double* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
+  // per-thread output coordinates
+  int oa[OPT], os[OPT], ob[OPT];
+  for (int o = 0; o < OPT; ++o) {
+    int oi = tid + o * NT;
+    if (oi >= NOUT) oi = NOUT - 1;
+    oa[o] = oi / (NS * NLOC);
+    os[o] = (oi / NLOC) % NS;
+    ob[o] = oi % NLOC;
+  }
+  __syncthreads();
+  for (int el = 0; el < g.nel; ++el) {
+    int li[D];
+    {
+      int ll = el;
+      for (int k = 0; k < D; ++k) { li[k] = ll % g.m; ll /= g.m; }
+    }
+    double acc[OPT];
+    for (int o = 0; o < OPT; ++o) acc[o] = 0.0;
+    const double* Kel = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * g.nel + el) * (size_t)NG * KA;
+    for (int g0 = 0; g0 < NG; g0 += GC) {
+      const int gc = min(GC, NG - g0);
+      for (int i = tid; i < gc * KA; i += NT) sK[i] = Kel[(size_t)g0 * KA + i];
+      __syncthreads();
+      for (int idx = tid; idx < gc * ZG; idx += NT) {
+        int b = idx % NLOC;
+        int s = (idx / NLOC) % NS;
+        int al = (idx / (NLOC * NS)) % (D + 1);
+        int gg = idx / ZG;
+        int gi[D], bi[D];
+        int t1 = g0 + gg, t2 = b;
+        for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; bi[k] = t2 % P1; t2 /= P1; }
+        const double* Kp = sK + gg * KA + (al * NS + s) * (D + 1);
+        double z = 0.0;
+#pragma unroll
+        for (int be = 0; be <= D; ++be) z += Kp[be] * basis_T<D, P>(sb, sdb, sc, gi, bi, be);
+        sZ[idx] = z;
+      }
+      __syncthreads();
+      for (int o = 0; o < OPT; ++o) {
+        int ai[D];
+        int t2 = oa[o];
+        for (int k = 0; k < D; ++k) { ai[k] = t2 % P1; t2 /= P1; }
+        double sum = 0.0;
+        for (int gg = 0; gg < gc; ++gg) {
+          int gi[D];
+          int t1 = g0 + gg;
+          for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; }
+#pragma unroll
+          for (int al = 0; al <= D; ++al)
+            sum += basis_T<D, P>(sb, sdb, sc, gi, ai, al) * sZ[gg * ZG + (al * NS + os[o]) * NLOC + ob[o]];
+        }
+        acc[o] += sum;
+      }
+      __syncthreads();
+    }
+    for (int o = 0; o < OPT; ++o) {
+      int oi = tid + o * NT;
+      if (oi >= NOUT) break;
+      int A = 0, B = 0, sa = 1, t1 = oa[o], t2 = ob[o];
+      for (int k = 0; k < D; ++k) {
+        A += (li[k] * P + t1 % P1) * sa;
+        B += (li[k] * P + t2 % P1) * sa;
+        t1 /= P1; t2 /= P1; sa *= g.n1;
+      }
+      out[((size_t)t * Np + A) * Nu + (size_t)os[o] * Np + B] += acc[o];
+    }
+    __syncthreads();
+  }
+}
+
+// R_U[t][A] += sum_g sum_alpha T[g][alpha][a] r[g][t][alpha]
+template <int D, int P>
+__global__ void k_vol_res(Geo g, const double* __restrict__ tab, const double* __restrict__ rvol,
+                          double* __restrict__ RU) {
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  __shared__ double sb[NG1 * P1], sdb[NG1 * P1];
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < NG1 * P1; i += blockDim.x) {
+    sb[i] = tab[i];
+    sdb[i] = tab[NG1 * P1 + i];
+  }
+  double sc[D];
+  for (int k = 0; k < D; ++k) sc[k] = 2.0 / g.he[k];
+  __syncthreads();
+  for (int el = 0; el < g.nel; ++el) {
+    int li[D];
+    int ll = el;
+    for (int k = 0; k < D; ++k) { li[k] = ll % g.m; ll /= g.m; }
+    for (int oi = threadIdx.x; oi < NS * NLOC; oi += blockDim.x) {
+      int t = oi / NLOC, al = oi % NLOC;
+      int ai[D], A = 0, sa = 1, t2 = al;
+      for (int k = 0; k < D; ++k) {
+        ai[k] = t2 % P1; t2 /= P1;
+        A += (li[k] * P + ai[k]) * sa;
+        sa *= g.n1;
+      }
+      const double* R = rvol + ((size_t)e * g.nel + el) * NG * NS * (D + 1);
+      double sum = 0.0;
+      for (int gq = 0; gq < NG; ++gq) {
+        int gi[D], t1 = gq;
+        for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; }
+        for (int alpha = 0; alpha <= D; ++alpha)
+          sum += basis_T<D, P>(sb, sdb, sc, gi, ai, alpha) * R[((size_t)gq * NS + t) * (D + 1) + alpha];
+      }
+      RU[((size_t)e * NS + t) * g.Np + A] += sum;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- faces
+// tangential decomposition of a sub-face, sub-face node and face point
+template <int D>
+__device__ __forceinline__ void face_axes(int fl, int* tang) {
+  int k = fl / 2, c = 0;
+  for (int kk = 0; kk < D; ++kk)
+    if (kk != k) tang[c++] = kk;
+}
+
+template <int D, int P>
+__global__ void __launch_bounds__(128) k_face_point(Geo g, const double* __restrict__ tab, Phys ph,
+                                                     mehdg_problem pr, const int* __restrict__ bkind,
+                                                     const int* __restrict__ bside, const int* __restrict__ fnode,
+                                                     const int* __restrict__ gather, const double* __restrict__ uD,
+                                                     const double* __restrict__ u, const double* __restrict__ q,
+                                                     const double* __restrict__ uh, double* __restrict__ Kface,
+                                                     double* __restrict__ rface, int E) {
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NFS = IPow<P1, D - 1>::v, NFP = IPow<NG1, D - 1>::v;
+  constexpr int NDIR = NS * (D + 2);
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nsf = g.nsf;
+  if (tid >= (long long)E * 2 * D * nsf * NFP * NDIR) return;
+  const int dir = tid % NDIR;
+  long long r = tid / NDIR;
+  const int fp = r % NFP; r /= NFP;
+  const int sf = r % nsf; r /= nsf;
+  const int fl = r % (2 * D);
+  const int e = (int)(r / (2 * D));
+  Tables tb = tables(tab, NG1, P1);
+  int tang[D];
+  face_axes<D>(fl, tang);
+  int gi[D], si[D];
+  double wf = 1.0;
+  {
+    int pp = fp, ss = sf;
+    for (int c = 0; c < D - 1; ++c) {
+      gi[c] = pp % NG1; pp /= NG1;
+      si[c] = ss % g.m; ss /= g.m;
+      wf *= tb.gw[gi[c]] * 0.5 * g.he[tang[c]];
+    }
+  }
+  double Uf[NS], Qf[NS][D], UHf[NS];
+  for (int s = 0; s < NS; ++s) {
+    Uf[s] = 0.0; UHf[s] = 0.0;
+    for (int j = 0; j < D; ++j) Qf[s][j] = 0.0;
+  }
+  const size_t Np = g.Np;
+  for (int il = 0; il < NFS; ++il) {
+    int jf = 0, stride = 1, t2 = il;
+    double psi = 1.0;
+    for (int c = 0; c < D - 1; ++c) {
+      int ic = t2 % P1; t2 /= P1;
+      psi *= tb.b1[gi[c] * P1 + ic];
+      jf += (si[c] * P + ic) * stride;
+      stride *= g.n1;
+    }
+    int a = fnode[fl * g.Nfn + jf];
+    for (int s = 0; s < NS; ++s) {
+      Uf[s] += psi * u[((size_t)e * NS + s) * Np + a];
+      UHf[s] += psi * uh[gather[(size_t)e * g.Nt + s * g.Nth + fl * g.Nfn + jf]];
+      for (int j = 0; j < D; ++j) Qf[s][j] += psi * q[(((size_t)e * D + j) * NS + s) * Np + a];
+    }
+  }
+  double n[D];
+  for (int k = 0; k < D; ++k) n[k] = 0.0;
+  n[fl / 2] = (fl % 2) ? 1.0 : -1.0;
+  const int bk = bkind[e * 2 * D + fl];
+  typedef Dual<double, 1> S;
+  S Us[NS], Qs[NS][D], UHs[NS], fh[NS], eq[NS];
+  for (int s = 0; s < NS; ++s) {
+    UHs[s].v = UHf[s]; UHs[s].d[0] = (dir == s) ? 1.0 : 0.0;
+    for (int j = 0; j < D; ++j) {
+      Qs[s][j].v = Qf[s][j];
+      Qs[s][j].d[0] = (dir == NS + j * NS + s) ? 1.0 : 0.0;
+    }
+    Us[s].v = Uf[s]; Us[s].d[0] = (dir == NS + NS * D + s) ? 1.0 : 0.0;
+  }
+  trace_flux<D, S>(UHs, Qs, Us, n, ph, fh);
+  if (bk == MEHDG_BC_DIRICHLET) {
+    const double* ud = uD + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NS;
+    for (int s = 0; s < NS; ++s) eq[s] = UHs[s] - ud[s];
+  } else if (bk == MEHDG_BC_WALL) {
+    int bs = bside[e * 2 * D + fl];
+    wall_operator<D, S>(UHs, Us, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+  } else {
+    for (int s = 0; s < NS; ++s) eq[s] = fh[s];
+  }
+  double* K = Kface + (((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NDIR + dir) * 2 * NS;
+  for (int t = 0; t < NS; ++t) {
+    K[t] = fh[t].d[0] * wf;
+    K[NS + t] = eq[t].d[0] * wf;
+  }
+  if (dir == 0) {
+    double* R = rface + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * 2 * NS;
+    for (int t = 0; t < NS; ++t) {
+      R[t] = fh[t].v * wf;
+      R[NS + t] = eq[t].v * wf;
+    }
+  }
+}
+
+template <int D, int P>
+__global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __restrict__ tab,
+                                                        const int* __restrict__ fnode,
+                                                        const double* __restrict__ Kface,
+                                                        const double* __restrict__ rface, double* Auu, double* Auq,
+                                                        double* Auh, double* Ahu, double* Ahq, double* Ahh,
+                                                        double* RU, double* RUh) {
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NFS = IPow<P1, D - 1>::v, NFP = IPow<NG1, D - 1>::v;
+  constexpr int NDIR = NS * (D + 2);
+  __shared__ double spsi[NFS * NFP];
+  const int e = blockIdx.x;
+  const size_t Nu = g.Nu, Nt = g.Nt, Np = g.Np;
+  const int Nth = g.Nth, Nfn = g.Nfn;
+  const int tid = threadIdx.x;
+  for (int fl = 0; fl < 2 * D; ++fl) {
+    for (int sf = 0; sf < g.nsf; ++sf) {
+      int si[D];
+      {
+        int ss = sf;
+        for (int c = 0; c < D - 1; ++c) { si[c] = ss % g.m; ss /= g.m; }
+      }
+      __syncthreads();
+      for (int i = tid; i < NFS * NFP; i += blockDim.x) {
+        int il = i / NFP, fp = i % NFP;
+        double v = 1.0;
+        int t1 = il, t2 = fp;
+        for (int c = 0; c < D - 1; ++c) {
+          v *= tab[(t2 % NG1) * P1 + (t1 % P1)];
+          t1 /= P1; t2 /= NG1;
+        }
+        spsi[i] = v;
+      }
+      __syncthreads();
+      const double* K = Kface + (((size_t)e * 2 * D + fl) * g.nsf + sf) * NFP * NDIR * 2 * NS;
+      const double* R = rface + (((size_t)e * 2 * D + fl) * g.nsf + sf) * NFP * 2 * NS;
+      // local node -> face node index and macro node
+      auto jface = [&](int il) {
+        int jf = 0, stride = 1, t2 = il;
+        for (int c = 0; c < D - 1; ++c) {
+          jf += (si[c] * P + t2 % P1) * stride;
+          t2 /= P1;
+          stride *= g.n1;
+        }
+        return jf;
+      };
+      const int NOUT = NDIR * 2 * NS * NFS * NFS;
+      for (int oi = tid; oi < NOUT; oi += blockDim.x) {
+        int jn = oi % NFS;
+        int in = (oi / NFS) % NFS;
+        int t = (oi / (NFS * NFS)) % NS;
+        int et = (oi / (NFS * NFS * NS)) % 2;
+        int dir = oi / (NFS * NFS * NS * 2);
+        double sum = 0.0;
+        for (int fp = 0; fp < NFP; ++fp)
+          sum += spsi[in * NFP + fp] * K[((size_t)fp * NDIR + dir) * 2 * NS + et * NS + t] * spsi[jn * NFP + fp];
+        int ji = jface(in), jj = jface(jn);
+        int ai = fnode[fl * Nfn + ji], aj = fnode[fl * Nfn + jj];
+        int s, kind, jd = 0;
+        if (dir < NS) { kind = 0; s = dir; }
+        else if (dir < NS + NS * D) { kind = 1; jd = (dir - NS) / NS; s = (dir - NS) % NS; }
+        else { kind = 2; s = dir - NS - NS * D; }
+        if (et == 0) {   // numerical flux tested with phi (u rows)
+          size_t row = (size_t)t * Np + ai;
+          if (kind == 0) Auh[(size_t)e * Nu * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += sum;
+          else if (kind == 1) Auq[((size_t)e * D + jd) * Nu * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+          else Auu[(size_t)e * Nu * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+        } else {         // trace equation tested with psi (uhat rows)
+          size_t row = (size_t)t * Nth + fl * Nfn + ji;
+          if (kind == 0) Ahh[(size_t)e * Nt * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += sum;
+          else if (kind == 1) Ahq[((size_t)e * D + jd) * Nt * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+          else Ahu[(size_t)e * Nt * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+        }
+      }
+      for (int oi = tid; oi < 2 * NS * NFS; oi += blockDim.x) {
+        int in = oi % NFS;
+        int t = (oi / NFS) % NS;
+        int et = oi / (NFS * NS);
+        double sum = 0.0;
+        for (int fp = 0; fp < NFP; ++fp) sum += spsi[in * NFP + fp] * R[(size_t)fp * 2 * NS + et * NS + t];
+        int ji = jface(in);
+        if (et == 0) RU[((size_t)e * NS + t) * Np + fnode[fl * Nfn + ji]] += sum;
+        else RUh[(size_t)e * Nt + (size_t)t * Nth + fl * Nfn + ji] += sum;
+      }
+    }
+  }
+}
+
+// R_Q[k][s][a] = M q_k,s + G_k u_s + Gh_k uh_loc,s   (linear part of eq. C38a)
+__global__ void k_rq(Geo g, const double* __restrict__ M, const double* __restrict__ Gk,
+                     const double* __restrict__ Ghk, const int* __restrict__ gather, const double* __restrict__ u,
+                     const double* __restrict__ q, const double* __restrict__ uh, double* __restrict__ RQ, int E) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long tot = (long long)E * g.d * g.ns * g.Np;
+  if (tid >= tot) return;
+  int a = tid % g.Np;
+  int s = (tid / g.Np) % g.ns;
+  int k = (tid / ((long long)g.Np * g.ns)) % g.d;
+  int e = (int)(tid / ((long long)g.Np * g.ns * g.d));
+  const size_t Np = g.Np;
+  const double* Mr = M + (size_t)a * Np;
+  const double* Gr = Gk + ((size_t)k * Np + a) * Np;
+  const double* Hr = Ghk + ((size_t)k * Np + a) * g.Nth;
+  const double* qe = q + (((size_t)e * g.d + k) * g.ns + s) * Np;
+  const double* ue = u + ((size_t)e * g.ns + s) * Np;
+  const int* ge = gather + (size_t)e * g.Nt + (size_t)s * g.Nth;
+  double acc = 0.0;
+  for (int b = 0; b < g.Np; ++b) acc += Mr[b] * qe[b] + Gr[b] * ue[b];
+  for (int i = 0; i < g.Nth; ++i) acc += Hr[i] * uh[ge[i]];
+  RQ[tid] = acc;
+}
+
+template <int D, int P>
+int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt) {
+  Geo g = make_geo(ctx);
+  cudaStream_t st = ctx->stream;
+  const int E = ctx->E;
+  const size_t Nu = ctx->Nu, Nt = ctx->Nt;
+  Phys ph{ctx->prob.gamma, ctx->prob.Re, ctx->prob.Pr, ctx->prob.supg, ctx->h_supg, ctx->p};
+  CK(cudaMemsetAsync(ctx->Auu, 0, sizeof(double) * E * Nu * Nu, st));
+  CK(cudaMemsetAsync(ctx->Auq, 0, sizeof(double) * E * D * Nu * Nu, st));
+  CK(cudaMemsetAsync(ctx->Auh, 0, sizeof(double) * E * Nu * Nt, st));
+  CK(cudaMemsetAsync(ctx->Ahu, 0, sizeof(double) * E * Nt * Nu, st));
+  CK(cudaMemsetAsync(ctx->Ahq, 0, sizeof(double) * E * D * Nt * Nu, st));
+  CK(cudaMemsetAsync(ctx->Ahh, 0, sizeof(double) * E * Nt * Nt, st));
+  CK(cudaMemsetAsync(ctx->RU, 0, sizeof(double) * E * Nu, st));
+  CK(cudaMemsetAsync(ctx->RUh, 0, sizeof(double) * E * Nt, st));
+  constexpr int NS = D + 2;
+  constexpr int NG = IPow<P + 2, D>::v;
+  {
+    long long tot = (long long)E * ctx->nel * NG * NS * (1 + D);
+    k_vol_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, tt ? tt->hist : nullptr,
+                                                          tt ? tt->coef : 0.0, tt ? tt->supg_time : 0, ctx->src,
+                                                          ctx->Kvol, ctx->rvol, E);
+    CKL();
+  }
+  {
+    typedef VolCfg<D, P> C;
+    CK(cudaFuncSetAttribute(k_vol_contract<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    dim3 grid(E, D + 1, NS);
+    k_vol_contract<D, P><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, ctx->Kvol, ctx->Auu, ctx->Auq);
+    CKL();
+    k_vol_res<D, P><<<E, 128, 0, st>>>(g, ctx->tab, ctx->rvol, ctx->RU);
+    CKL();
+  }
+  {
+    constexpr int NFP = IPow<P + 2, D - 1>::v;
+    long long tot = (long long)E * 2 * D * ctx->nsf * NFP * NS * (D + 2);
+    k_face_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, ctx->prob, ctx->bkind, ctx->bside,
+                                                           ctx->fnode, ctx->gather, ctx->uD, u, q, uh,
+                                                           ctx->Kface, ctx->rface, E);
+    CKL();
+    k_face_contract<D, P><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, ctx->Kface, ctx->rface, ctx->Auu, ctx->Auq,
+                                              ctx->Auh, ctx->Ahu, ctx->Ahq, ctx->Ahh, ctx->RU, ctx->RUh);
+    CKL();
+  }
+  {
+    long long tot = (long long)E * ctx->Nq;
+    k_rq<<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->Mref, ctx->Gk, ctx->Ghk, ctx->gather, u, q, uh, ctx->RQ, E);
+    CKL();
+  }
+  return MEHDG_OK;
+}
+
+}  // namespace
+
+int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt,
+                 double* norms) {
+  int rc;
+  const int d = ctx->d, p = ctx->p;
+  if (d == 2 && p == 1) rc = assemble_dp<2, 1>(ctx, u, q, uh, tt);
+  else if (d == 2 && p == 2) rc = assemble_dp<2, 2>(ctx, u, q, uh, tt);
+  else if (d == 2 && p == 3) rc = assemble_dp<2, 3>(ctx, u, q, uh, tt);
+  else if (d == 3 && p == 1) rc = assemble_dp<3, 1>(ctx, u, q, uh, tt);
+  else if (d == 3 && p == 2) rc = assemble_dp<3, 2>(ctx, u, q, uh, tt);
+  else if (d == 3 && p == 3) rc = assemble_dp<3, 3>(ctx, u, q, uh, tt);
+  else return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
+  if (rc) return rc;
+  ctx->condensed = false;
+  if (norms) {
+    double a, b, c;
+    rc = vec_dot(ctx, ctx->RQ, ctx->RQ, (long long)ctx->E * ctx->Nq, &a);
+    if (rc) return rc;
+    rc = vec_dot(ctx, ctx->RU, ctx->RU, (long long)ctx->E * ctx->Nu, &b);
+    if (rc) return rc;
+    rc = face_reduce(ctx, ctx->RUh, ctx->tv2);
+    if (rc) return rc;
+    rc = vec_dot(ctx, ctx->tv2, ctx->tv2, ctx->ntr, &c);
+    if (rc) return rc;
+    norms[0] = sqrt(a);
+    norms[1] = sqrt(b);
+    norms[2] = sqrt(c);
+    norms[3] = sqrt(a + b + c);
+  }
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_assemble_local(mehdg_ctx* ctx, const double* u, const double* q, const double* uhat,
+                                    const mehdg_time_term* tt, double* res_norms) {
+  if (!ctx || !u || !q || !uhat) return MEHDG_ERR_ARG;
+  return assemble_all(ctx, u, q, uhat, tt, res_norms);
+}

@@ -1,0 +1,167 @@
+// Forward-mode dual numbers for exact pointwise Jacobians on the device.
+//
+// Dual<T, N> = v + sum_i d[i] eps_i with eps_i eps_j = 0.  T may itself be a Dual,
+// which gives second derivatives (the SUPG strong residual contains first
+// derivatives of the fluxes, and the Newton blocks of eq. C312 differentiate it
+// once more).  Everything is header-only and usable on host and device.
+#pragma once
+#include <cmath>
+
+#ifdef __CUDACC__
+#define HD __host__ __device__ __forceinline__
+#else
+#define HD inline
+#endif
+
+template <class T, int N>
+struct Dual {
+  T v;
+  T d[N];
+};
+
+// innermost double of a (possibly nested) scalar
+HD double val0(double x) { return x; }
+template <class T, int N>
+HD double val0(const Dual<T, N>& x) { return val0(x.v); }
+
+template <class T> struct Zero { HD static T get() { return T(0.0); } };
+template <class T, int N> struct Zero<Dual<T, N>> {
+  HD static Dual<T, N> get() {
+    Dual<T, N> r;
+    r.v = Zero<T>::get();
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = Zero<T>::get();
+    return r;
+  }
+};
+template <class T> HD T zero() { return Zero<T>::get(); }
+
+// constant of type T
+template <class T> struct Cst { HD static T get(double c) { return T(c); } };
+template <class T, int N> struct Cst<Dual<T, N>> {
+  HD static Dual<T, N> get(double c) {
+    Dual<T, N> r = Zero<Dual<T, N>>::get();
+    r.v = Cst<T>::get(c);
+    return r;
+  }
+};
+template <class T> HD T cst(double c) { return Cst<T>::get(c); }
+
+// ---------------------------------------------------------------- arithmetic
+template <class T, int N>
+HD Dual<T, N> operator+(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> operator-(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> operator-(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> operator*(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> operator/(const Dual<T, N>& a, const Dual<T, N>& b) {
+  Dual<T, N> r;
+  T inv = cst<T>(1.0) / b.v;
+  r.v = a.v * inv;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * inv;
+  return r;
+}
+// mixed with plain doubles
+template <class T, int N>
+HD Dual<T, N> operator+(const Dual<T, N>& a, double b) { Dual<T, N> r = a; r.v = a.v + b; return r; }
+template <class T, int N>
+HD Dual<T, N> operator+(double b, const Dual<T, N>& a) { return a + b; }
+template <class T, int N>
+HD Dual<T, N> operator-(const Dual<T, N>& a, double b) { Dual<T, N> r = a; r.v = a.v - b; return r; }
+template <class T, int N>
+HD Dual<T, N> operator-(double b, const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = b - a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> operator*(const Dual<T, N>& a, double b) {
+  Dual<T, N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> operator*(double b, const Dual<T, N>& a) { return a * b; }
+template <class T, int N>
+HD Dual<T, N> operator/(const Dual<T, N>& a, double b) { return a * (1.0 / b); }
+template <class T, int N>
+HD Dual<T, N> operator/(double b, const Dual<T, N>& a) {
+  Dual<T, N> r;
+  T inv = cst<T>(1.0) / a.v;
+  r.v = b * inv;
+  T f = -(r.v * inv);
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+  return r;
+}
+// ---------------------------------------------------------------- functions
+HD double dsqrt(double x) { return sqrt(x); }
+template <class T, int N>
+HD Dual<T, N> dsqrt(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = dsqrt(a.v);
+  T f = cst<T>(0.5) / r.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+  return r;
+}
+HD double dsin(double x) { return sin(x); }
+HD double dcos(double x) { return cos(x); }
+template <class T, int N>
+HD Dual<T, N> dsin(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = dsin(a.v);
+  T c = dcos(a.v);
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * c;
+  return r;
+}
+template <class T, int N>
+HD Dual<T, N> dcos(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = dcos(a.v);
+  T s = -dsin(a.v);
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * s;
+  return r;
+}
+// |x| with derivative sign(x), sign(0) = 0
+HD double dabs(double x) { return x > 0 ? x : (x < 0 ? -x : 0.0); }
+template <class T, int N>
+HD Dual<T, N> dabs(const Dual<T, N>& a) {
+  double s = val0(a);
+  double sg = s > 0 ? 1.0 : (s < 0 ? -1.0 : 0.0);
+  return a * sg;
+}

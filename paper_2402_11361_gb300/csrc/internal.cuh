@@ -1,0 +1,127 @@
+// Internal state of a mehdg context and helpers shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/mehdg.h"
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return ctx_fail(ctx, e_ == cudaErrorMemoryAllocation ? MEHDG_ERR_OOM : MEHDG_ERR_CUDA, \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    }                                                                                   \
+  } while (0)
+
+#define CKL()                                                                           \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess)                                                              \
+      return ctx_fail(ctx, MEHDG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct mehdg_ctx {
+  mehdg_problem prob;
+  mehdg_options opt;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // sizes
+  int d, ns, m, p, n1, Np, Nfn, Nth, Nu, Nq, Nt, E, F;
+  long long ntr;          // global trace length F * ns * Nfn
+  int nel, nloc, ng1, Ng; // sub-elements per macro, nodes per sub-element, Gauss points
+  int nsf, nfs, nfp;      // sub-faces per macro face, nodes per sub-face, points per sub-face
+  int ndir_v, ndir_f;     // Jacobian input directions (volume, face)
+  double hm[3], he[3];    // macro and sub-element sizes
+  double h_supg;
+  long long bytes = 0;
+
+  // host tables
+  std::vector<double> b1, db1, gw;   // [ng1][p+1] reference basis at Gauss points, weights
+  std::vector<int> facenode;         // [2d][Nfn] macro node of each face node
+  std::vector<int> h_gather;         // [E][Nt]
+  std::vector<int> h_owner;          // [F][2] (e * 2d + fl) or -1
+  std::vector<int> h_bkind;          // [E][2d]
+  std::vector<int> h_bside;          // [E][2d] domain side or -1
+
+  // device: maps and reference data
+  int* gather = nullptr;     // [E][Nt]
+  int* owner = nullptr;      // [F][2]
+  int* bkind = nullptr;      // [E][2d]
+  int* bside = nullptr;      // [E][2d]
+  int* fnode = nullptr;      // [2d][Nfn]
+  double* tab = nullptr;     // b1, db1, gw packed
+  double* Mref = nullptr;    // [Np][Np]
+  double* Minv = nullptr;    // [Np][Np]
+  double* Gk = nullptr;      // [d][Np][Np]
+  double* Ghk = nullptr;     // [d][Np][Nth]
+  double* Wk = nullptr;      // [d][Np][Np]   M^-1 G_k
+  double* Whk = nullptr;     // [d][Np][Nth]  M^-1 Gh_k
+  double* src = nullptr;     // [E][nel][Ng][ns] or null
+  double* uD = nullptr;      // [E][2d][nsf][nfp][ns] or null
+
+  // device: blocks (FP64)
+  double *Auu = nullptr, *Auq = nullptr, *Auh = nullptr, *Ahu = nullptr, *Ahq = nullptr, *Ahh = nullptr;
+  int* perm = nullptr;       // [E][Nu]
+  double *RQ = nullptr, *RU = nullptr, *RUh = nullptr, *gv = nullptr, *hv = nullptr, *MinvRQ = nullptr,
+         *bloc = nullptr, *slot = nullptr;
+  double *Kvol = nullptr, *rvol = nullptr, *Kface = nullptr, *rface = nullptr;
+  double* fblk = nullptr;    // [F][nfb][nfb]
+  int* fperm = nullptr;      // [F][nfb]
+  int nfb = 0;
+  int* dflag = nullptr;      // device status words
+  double* dred = nullptr;    // reduction scratch
+  double* hred = nullptr;    // pinned host mirror
+
+  // mixed precision copies
+  float *S32 = nullptr, *B32 = nullptr, *C32 = nullptr, *D32 = nullptr;
+  int* perm32 = nullptr;
+
+  // Krylov workspace
+  int restart = 30;
+  double *V = nullptr, *Zk = nullptr, *wv = nullptr, *tv = nullptr, *tv2 = nullptr, *rv = nullptr;
+  double *iV = nullptr, *iw = nullptr;    // inner GMRES
+  // Newton / DIRK
+  double *un = nullptr, *ustage = nullptr, *hist = nullptr, *du = nullptr, *dq = nullptr, *duh = nullptr,
+         *bhat = nullptr;
+  int lu_status = 0;
+  bool condensed = false;
+  // MLP preconditioner correction (kind 2)
+  void* mlp = nullptr;
+};
+
+int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg);
+
+// geometry helpers usable on the device
+struct Geo {
+  int d, ns, m, p, n1, Np, Nfn, Nth, Nu, Nt, nel, nloc, ng1, Ng, nsf, nfs, nfp;
+  double he[3];
+};
+Geo make_geo(const mehdg_ctx* c);
+
+// launch helpers implemented in the .cu files
+int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double* uh,
+                 const mehdg_time_term* tt, double* norms);
+int condense_all(mehdg_ctx* ctx, double shift, double* bhat);
+int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y);
+int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq);
+int precond_impl(mehdg_ctx* ctx, int kind, const double* r, double* z);
+int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_stats* st);
+int face_reduce(mehdg_ctx* ctx, const double* slot, double* y);
+int vec_dot(mehdg_ctx* ctx, const double* a, const double* b, long long n, double* out_host);
+int vec_axpy(mehdg_ctx* ctx, long long n, double a, const double* x, double* y);
+int vec_scal(mehdg_ctx* ctx, long long n, double a, double* x);
+int vec_copy(mehdg_ctx* ctx, long long n, const double* x, double* y);
+int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b, const double* y, double* z);
+int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag);
+int mlp_apply(mehdg_ctx* ctx, const double* r, double* z);

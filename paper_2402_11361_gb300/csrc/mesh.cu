@@ -1,0 +1,735 @@
+// a0: macro-element mesh, DOF maps, reference operators, closed-form data, state
+// initialisation and the context lifecycle (mehdg_mesh / query / init_state /
+// get_block / destroy).
+//
+// Spaces (Sec. 2.2): u and q are C0 tensor-product Lagrange polynomials of degree
+// p on the m^d sub-boxes of each macro-element (GLL nodes), the trace lives on
+// each macro-face in the C0 degree-p space of its m^(d-1) sub-faces.  Quadrature:
+// p+2 Gauss-Legendre points per direction on every sub-box / sub-face.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+#include "physics.cuh"
+
+int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+Geo make_geo(const mehdg_ctx* c) {
+  Geo g;
+  g.d = c->d; g.ns = c->ns; g.m = c->m; g.p = c->p; g.n1 = c->n1; g.Np = c->Np; g.Nfn = c->Nfn;
+  g.Nth = c->Nth; g.Nu = c->Nu; g.Nt = c->Nt; g.nel = c->nel; g.nloc = c->nloc; g.ng1 = c->ng1;
+  g.Ng = c->Ng; g.nsf = c->nsf; g.nfs = c->nfs; g.nfp = c->nfp;
+  for (int k = 0; k < 3; ++k) g.he[k] = c->he[k];
+  return g;
+}
+
+// ---------------------------------------------------------------- 1D rules
+static void legendre(int n, double x, double& P, double& dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { P = 1.0; dP = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  dP = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+static void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = -cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(n, z, P, dP);
+      double dz = P / dP;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double P, dP;
+    legendre(n, z, P, dP);
+    x[i] = z;
+    w[i] = 2.0 / ((1 - z * z) * dP * dP);
+  }
+}
+
+static std::vector<double> gll_nodes(int p) {
+  std::vector<double> x(p + 1);
+  x[0] = -1.0;
+  x[p] = 1.0;
+  for (int i = 1; i < p; ++i) {
+    double z = -cos(M_PI * i / p);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(p, z, P, dP);
+      double d2P = (2 * z * dP - p * (p + 1) * P) / (1 - z * z);
+      double dz = dP / d2P;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+  return x;
+}
+
+static void lagrange_at(const std::vector<double>& xn, double x, double* L, double* dL) {
+  int n = (int)xn.size();
+  for (int j = 0; j < n; ++j) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) v *= (x - xn[k]) / (xn[j] - xn[k]);
+    L[j] = v;
+    double dv = 0.0;
+    for (int l = 0; l < n; ++l) {
+      if (l == j) continue;
+      double t = 1.0 / (xn[j] - xn[l]);
+      for (int k = 0; k < n; ++k)
+        if (k != j && k != l) t *= (x - xn[k]) / (xn[j] - xn[k]);
+      dv += t;
+    }
+    dL[j] = dv;
+  }
+}
+
+// small dense inverse (Gauss-Jordan with partial pivoting)
+static void invert(std::vector<double>& A, int n) {
+  std::vector<double> I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int r = c;
+    for (int i = c + 1; i < n; ++i)
+      if (fabs(A[i * n + c]) > fabs(A[r * n + c])) r = i;
+    for (int j = 0; j < n; ++j) {
+      std::swap(A[c * n + j], A[r * n + j]);
+      std::swap(I[c * n + j], I[r * n + j]);
+    }
+    double piv = A[c * n + c];
+    for (int j = 0; j < n; ++j) { A[c * n + j] /= piv; I[c * n + j] /= piv; }
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      double f = A[i * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) { A[i * n + j] -= f * A[c * n + j]; I[i * n + j] -= f * I[c * n + j]; }
+    }
+  }
+  A = I;
+}
+
+// Kronecker product over axes (axis 0 fastest) of n1 x n1 (or n1 x 1) factors
+static void kron_dense(int d, int n1, const std::vector<const double*>& f, std::vector<int> cols,
+                       std::vector<double>& out, int& R, int& C) {
+  R = 1; C = 1;
+  for (int k = 0; k < d; ++k) { R *= n1; C *= cols[k]; }
+  out.assign((size_t)R * C, 0.0);
+  for (int a = 0; a < R; ++a)
+    for (int b = 0; b < C; ++b) {
+      int aa = a, bb = b;
+      double v = 1.0;
+      for (int k = 0; k < d; ++k) {
+        int ak = aa % n1, bk = bb % cols[k];
+        aa /= n1; bb /= cols[k];
+        v *= f[k][ak * cols[k] + bk];
+      }
+      out[(size_t)a * C + b] = v;
+    }
+}
+
+// ---------------------------------------------------------------- device kernels for data
+template <int D>
+__global__ void k_source(Geo g, const double* tab, mehdg_problem pr, double* src) {
+  constexpr int NS = D + 2;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long tot = (long long)pr.nmac[0] * (D > 1 ? pr.nmac[1] : 1) * (D > 2 ? pr.nmac[2] : 1) * g.nel * g.Ng;
+  if (tid >= tot) return;
+  int gq = tid % g.Ng;
+  int el = (tid / g.Ng) % g.nel;
+  int e = (int)(tid / ((long long)g.Ng * g.nel));
+  // table layout: b1, db1, Gauss weights, Gauss points, macro node coordinates
+  const double* gx = tab + 2 * g.ng1 * (g.p + 1) + g.ng1;
+  double x[D];
+  int ee = e, ll = el, gg = gq;
+  for (int k = 0; k < D; ++k) {
+    int ek = ee % pr.nmac[k]; ee /= pr.nmac[k];
+    int lk = ll % g.m; ll /= g.m;
+    int gk = gg % g.ng1; gg /= g.ng1;
+    double hm = (pr.hi[k] - pr.lo[k]) / pr.nmac[k];
+    x[k] = pr.lo[k] + ek * hm + (lk + 0.5 * (gx[gk] + 1.0)) * g.he[k];
+  }
+  typedef Dual<Dual<double, D>, D> X2;
+  typedef Dual<double, D> T1;
+  X2 xs[D];
+  for (int k = 0; k < D; ++k) {
+    xs[k] = zero<X2>();
+    xs[k].v.v = x[k];
+    xs[k].v.d[k] = 1.0;
+    xs[k].d[k].v = 1.0;
+  }
+  X2 u2[NS];
+  field_mms<D, X2>(xs, pr.field_par, pr.gamma, u2);
+  T1 uu[NS], qq[NS][D], F[NS][D], G[NS][D];
+  for (int s = 0; s < NS; ++s) {
+    uu[s].v = u2[s].v.v;
+    for (int l = 0; l < D; ++l) uu[s].d[l] = u2[s].v.d[l];
+    for (int j = 0; j < D; ++j) {
+      qq[s][j].v = u2[s].d[j].v;
+      for (int l = 0; l < D; ++l) qq[s][j].d[l] = u2[s].d[j].d[l];
+    }
+  }
+  Phys ph{pr.gamma, pr.Re, pr.Pr, 0, 1.0, 1};
+  inviscid_flux<D, T1>(uu, pr.gamma, F);
+  viscous_flux<D, T1>(uu, qq, ph, G);
+  for (int s = 0; s < NS; ++s) {
+    double f = 0.0;
+    for (int l = 0; l < D; ++l) f += F[s][l].d[l] + G[s][l].d[l];
+    src[tid * NS + s] = f;
+  }
+}
+
+// closed-form state at a physical point
+template <int D>
+__device__ void field_at(const mehdg_problem& pr, const double* x, double* u) {
+  if (pr.field == MEHDG_FIELD_MMS) field_mms<D, double>(x, pr.field_par, pr.gamma, u);
+  else if (pr.field == MEHDG_FIELD_TGV) field_tgv<D, double>(x, pr.field_par, pr.gamma, u);
+  else field_uniform<D>(pr.field_par, pr.gamma, u);
+}
+
+template <int D>
+__global__ void k_dirichlet(Geo g, const double* tab, mehdg_problem pr, const int* bkind, double* uD) {
+  constexpr int NS = D + 2;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int E = pr.nmac[0] * (D > 1 ? pr.nmac[1] : 1) * (D > 2 ? pr.nmac[2] : 1);
+  long long tot = (long long)E * 2 * D * g.nsf * g.nfp;
+  if (tid >= tot) return;
+  int fp = tid % g.nfp;
+  int sf = (tid / g.nfp) % g.nsf;
+  int fl = (tid / ((long long)g.nfp * g.nsf)) % (2 * D);
+  int e = (int)(tid / ((long long)g.nfp * g.nsf * 2 * D));
+  double* out = uD + tid * NS;
+  if (bkind[e * 2 * D + fl] != MEHDG_BC_DIRICHLET) {
+    for (int s = 0; s < NS; ++s) out[s] = 0.0;
+    return;
+  }
+  const double* gx = tab + 2 * g.ng1 * (g.p + 1) + g.ng1;
+  int k = fl / 2, side = fl % 2;
+  int eidx[3], ee = e;
+  for (int kk = 0; kk < D; ++kk) { eidx[kk] = ee % pr.nmac[kk]; ee /= pr.nmac[kk]; }
+  double x[D];
+  int ss = sf, pp = fp;
+  for (int kk = 0; kk < D; ++kk) {
+    double hm = (pr.hi[kk] - pr.lo[kk]) / pr.nmac[kk];
+    double x0 = pr.lo[kk] + eidx[kk] * hm;
+    if (kk == k) {
+      x[kk] = side ? x0 + hm : x0;
+    } else {
+      int sk = ss % g.m; ss /= g.m;
+      int gk = pp % g.ng1; pp /= g.ng1;
+      x[kk] = x0 + (sk + 0.5 * (gx[gk] + 1.0)) * g.he[kk];
+    }
+  }
+  double u[NS];
+  field_at<D>(pr, x, u);
+  for (int s = 0; s < NS; ++s) out[s] = u[s];
+}
+
+template <int D>
+__global__ void k_init_state(Geo g, mehdg_problem pr, const double* xnode1, const double* du,
+                             double* u) {
+  constexpr int NS = D + 2;
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int E = pr.nmac[0] * (D > 1 ? pr.nmac[1] : 1) * (D > 2 ? pr.nmac[2] : 1);
+  if (tid >= (long long)E * g.Np) return;
+  int a = tid % g.Np;
+  int e = (int)(tid / g.Np);
+  double x[D];
+  int ee = e, aa = a;
+  for (int k = 0; k < D; ++k) {
+    int ek = ee % pr.nmac[k]; ee /= pr.nmac[k];
+    int ak = aa % g.n1; aa /= g.n1;
+    double hm = (pr.hi[k] - pr.lo[k]) / pr.nmac[k];
+    x[k] = pr.lo[k] + ek * hm + xnode1[k * g.n1 + ak];
+  }
+  double uu[NS];
+  field_at<D>(pr, x, uu);
+  for (int s = 0; s < NS; ++s) {
+    long long o = ((long long)e * NS + s) * g.Np + a;
+    u[o] = uu[s] + (du ? du[o] : 0.0);
+  }
+}
+
+__global__ void k_init_trace(Geo g, const int* owner, const int* fnode, const double* u,
+                             const double* duh, double* uh, int F) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)F * g.ns * g.Nfn) return;
+  int j = tid % g.Nfn;
+  int f = (int)(tid / ((long long)g.ns * g.Nfn));
+  int s = (tid / g.Nfn) % g.ns;
+  int o = owner[2 * f];
+  if (o < 0) o = owner[2 * f + 1];
+  int e = o / (2 * g.d), fl = o % (2 * g.d);
+  int a = fnode[fl * g.Nfn + j];
+  uh[tid] = u[((long long)e * g.ns + s) * g.Np + a] + (duh ? duh[tid] : 0.0);
+}
+
+// q = -M^-1 (G_k u + Gh_k uh_loc): the gradient that makes R_Q vanish
+__global__ void k_lift(Geo g, const double* Wk, const double* Whk, const int* gather,
+                       const double* u, const double* uh, double* q, int E) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long tot = (long long)E * g.d * g.ns * g.Np;
+  if (tid >= tot) return;
+  int a = tid % g.Np;
+  int s = (tid / g.Np) % g.ns;
+  int k = (tid / ((long long)g.Np * g.ns)) % g.d;
+  int e = (int)(tid / ((long long)g.Np * g.ns * g.d));
+  const double* W = Wk + (size_t)k * g.Np * g.Np + (size_t)a * g.Np;
+  const double* Wh = Whk + (size_t)k * g.Np * g.Nth + (size_t)a * g.Nth;
+  const double* ue = u + ((size_t)e * g.ns + s) * g.Np;
+  const int* ge = gather + (size_t)e * g.Nt + (size_t)s * g.Nth;
+  double acc = 0.0;
+  for (int b = 0; b < g.Np; ++b) acc += W[b] * ue[b];
+  for (int i = 0; i < g.Nth; ++i) acc += Wh[i] * uh[ge[i]];
+  q[tid] = -acc;
+}
+
+// ---------------------------------------------------------------- context
+static int alloc(mehdg_ctx* ctx, void** p, size_t bytes) {
+  if (bytes == 0) { *p = nullptr; return 0; }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess)
+    return ctx_fail(ctx, MEHDG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  ctx->bytes += bytes;
+  return 0;
+}
+#define ALLOC(ptr, count)                                                        \
+  do {                                                                           \
+    int r_ = alloc(ctx, (void**)&(ptr), sizeof(*(ptr)) * (size_t)(count));       \
+    if (r_) return r_;                                                           \
+  } while (0)
+
+static void default_options(mehdg_options* o) {
+  memset(o, 0, sizeof(*o));
+  o->precision = MEHDG_PREC_FP64;
+  o->precond = 0;
+  o->restart = 30;
+  o->max_iters = 2000;
+  o->lin_rtol = 1e-6;
+  o->lin_atol = 0.0;
+  o->inner_iters = 5;
+  o->newton_rtol = 1e-8;
+  o->newton_atol = 1e-14;
+  o->max_newton = 100;
+  o->tau_init = 1.0;
+  o->tau_max = 1e8;
+  o->refine_iters = 2;
+}
+
+static int setup(mehdg_ctx* ctx) {
+  const mehdg_problem& pr = ctx->prob;
+  const int d = pr.dim;
+  ctx->d = d;
+  ctx->ns = d + 2;
+  ctx->m = pr.m;
+  ctx->p = pr.p;
+  ctx->n1 = pr.m * pr.p + 1;
+  ctx->Np = 1; ctx->Nfn = 1; ctx->nel = 1; ctx->nloc = 1; ctx->Ng = 1; ctx->nsf = 1; ctx->nfs = 1; ctx->nfp = 1;
+  ctx->ng1 = pr.p + 2;
+  for (int k = 0; k < d; ++k) {
+    ctx->Np *= ctx->n1;
+    ctx->nel *= pr.m;
+    ctx->nloc *= pr.p + 1;
+    ctx->Ng *= ctx->ng1;
+    if (k < d - 1) {
+      ctx->Nfn *= ctx->n1;
+      ctx->nsf *= pr.m;
+      ctx->nfs *= pr.p + 1;
+      ctx->nfp *= ctx->ng1;
+    }
+  }
+  ctx->Nth = 2 * d * ctx->Nfn;
+  ctx->Nu = ctx->ns * ctx->Np;
+  ctx->Nq = d * ctx->Nu;
+  ctx->Nt = ctx->ns * ctx->Nth;
+  ctx->E = 1;
+  ctx->F = 0;
+  int npos[3];
+  for (int k = 0; k < d; ++k) {
+    ctx->E *= pr.nmac[k];
+    npos[k] = pr.periodic[k] ? pr.nmac[k] : pr.nmac[k] + 1;
+  }
+  int goff[3];
+  for (int k = 0; k < d; ++k) {
+    goff[k] = ctx->F;
+    int nt = 1;
+    for (int j = 0; j < d; ++j)
+      if (j != k) nt *= pr.nmac[j];
+    ctx->F += npos[k] * nt;
+  }
+  ctx->ntr = (long long)ctx->F * ctx->ns * ctx->Nfn;
+  ctx->ndir_v = ctx->ns * (1 + d);
+  ctx->ndir_f = ctx->ns * (d + 2);
+  double hmin = 1e300;
+  for (int k = 0; k < 3; ++k) { ctx->hm[k] = 1.0; ctx->he[k] = 1.0; }
+  for (int k = 0; k < d; ++k) {
+    ctx->hm[k] = (pr.hi[k] - pr.lo[k]) / pr.nmac[k];
+    ctx->he[k] = ctx->hm[k] / pr.m;
+    hmin = std::min(hmin, ctx->he[k]);
+  }
+  ctx->h_supg = hmin;
+
+  // -- reference 1D data
+  const int p = pr.p, n1 = ctx->n1, ng1 = ctx->ng1, m = pr.m;
+  std::vector<double> xg, wg;
+  gauss_rule(ng1, xg, wg);
+  std::vector<double> xl = gll_nodes(p);
+  ctx->b1.assign(ng1 * (p + 1), 0.0);
+  ctx->db1.assign(ng1 * (p + 1), 0.0);
+  for (int gq = 0; gq < ng1; ++gq) lagrange_at(xl, xg[gq], &ctx->b1[gq * (p + 1)], &ctx->db1[gq * (p + 1)]);
+  ctx->gw = wg;
+
+  // -- 1D macro matrices per axis: mass M1, C1[i][j] = int dphi_i phi_j, node coordinates
+  std::vector<std::vector<double>> M1(d), C1(d), iM1(d), xn1(d);
+  for (int k = 0; k < d; ++k) {
+    M1[k].assign(n1 * n1, 0.0);
+    C1[k].assign(n1 * n1, 0.0);
+    xn1[k].assign(n1, 0.0);
+    double he = ctx->he[k];
+    for (int e = 0; e < m; ++e) {
+      for (int i = 0; i <= p; ++i) xn1[k][e * p + i] = e * he + 0.5 * (xl[i] + 1.0) * he;
+      for (int gq = 0; gq < ng1; ++gq) {
+        double w = wg[gq] * he / 2;
+        for (int i = 0; i <= p; ++i)
+          for (int j = 0; j <= p; ++j) {
+            double bi = ctx->b1[gq * (p + 1) + i], bj = ctx->b1[gq * (p + 1) + j];
+            double dbi = ctx->db1[gq * (p + 1) + i] * 2.0 / he;
+            M1[k][(e * p + i) * n1 + e * p + j] += w * bi * bj;
+            C1[k][(e * p + i) * n1 + e * p + j] += w * dbi * bj;
+          }
+      }
+    }
+    xn1[k][0] = 0.0;
+    xn1[k][n1 - 1] = ctx->hm[k];
+    iM1[k] = M1[k];
+    invert(iM1[k], n1);
+  }
+  const int Np = ctx->Np, Nth = ctx->Nth, Nfn = ctx->Nfn;
+  std::vector<int> sq(3, n1);
+  int R, C;
+  std::vector<double> Mref, Minv, Gk(d * (size_t)Np * Np), Ghk(d * (size_t)Np * Nth, 0.0), tmp;
+  {
+    std::vector<const double*> f(d);
+    for (int k = 0; k < d; ++k) f[k] = M1[k].data();
+    kron_dense(d, n1, f, std::vector<int>(d, n1), Mref, R, C);
+    for (int k = 0; k < d; ++k) f[k] = iM1[k].data();
+    kron_dense(d, n1, f, std::vector<int>(d, n1), Minv, R, C);
+    for (int kk = 0; kk < d; ++kk) {
+      for (int k = 0; k < d; ++k) f[k] = (k == kk) ? C1[k].data() : M1[k].data();
+      kron_dense(d, n1, f, std::vector<int>(d, n1), tmp, R, C);
+      std::copy(tmp.begin(), tmp.end(), Gk.begin() + (size_t)kk * Np * Np);
+    }
+  }
+  // face node tables and face mass matrices
+  ctx->facenode.assign(2 * d * Nfn, 0);
+  for (int fl = 0; fl < 2 * d; ++fl) {
+    int k = fl / 2, side = fl % 2;
+    for (int j = 0; j < Nfn; ++j) {
+      int jj = j, idx[3] = {0, 0, 0};
+      for (int kk = 0; kk < d; ++kk) {
+        if (kk == k) idx[kk] = side ? n1 - 1 : 0;
+        else { idx[kk] = jj % n1; jj /= n1; }
+      }
+      int a = 0;
+      for (int kk = d - 1; kk >= 0; --kk) a = a * n1 + idx[kk];
+      ctx->facenode[fl * Nfn + j] = a;
+    }
+    // face mass over tangential axes
+    std::vector<const double*> f;
+    std::vector<int> cols;
+    for (int kk = 0; kk < d; ++kk)
+      if (kk != k) { f.push_back(M1[kk].data()); cols.push_back(n1); }
+    std::vector<double> Mf;
+    if (d == 1) Mf.assign(1, 1.0);
+    else kron_dense(d - 1, n1, f, cols, Mf, R, C);
+    double nk = side ? 1.0 : -1.0;
+    for (int j = 0; j < Nfn; ++j)
+      for (int i = 0; i < Nfn; ++i)
+        Ghk[(size_t)k * Np * Nth + (size_t)ctx->facenode[fl * Nfn + j] * Nth + fl * Nfn + i] -= nk * Mf[j * Nfn + i];
+  }
+  std::vector<double> Wk(d * (size_t)Np * Np, 0.0), Whk(d * (size_t)Np * Nth, 0.0);
+  for (int k = 0; k < d; ++k)
+    for (int a = 0; a < Np; ++a) {
+      const double* mi = &Minv[(size_t)a * Np];
+      for (int c = 0; c < Np; ++c) {
+        double f = mi[c];
+        if (f == 0.0) continue;
+        const double* g = &Gk[(size_t)k * Np * Np + (size_t)c * Np];
+        double* w = &Wk[(size_t)k * Np * Np + (size_t)a * Np];
+        for (int b = 0; b < Np; ++b) w[b] += f * g[b];
+        const double* gh = &Ghk[(size_t)k * Np * Nth + (size_t)c * Nth];
+        double* wh = &Whk[(size_t)k * Np * Nth + (size_t)a * Nth];
+        for (int i = 0; i < Nth; ++i) wh[i] += f * gh[i];
+      }
+    }
+
+  // -- maps
+  const int E = ctx->E, F = ctx->F, ns = ctx->ns, Nt = ctx->Nt;
+  ctx->h_gather.assign((size_t)E * Nt, 0);
+  ctx->h_owner.assign(2 * F, -1);
+  ctx->h_bkind.assign(E * 2 * d, 0);
+  ctx->h_bside.assign(E * 2 * d, -1);
+  for (int e = 0; e < E; ++e) {
+    int idx[3] = {0, 0, 0}, ee = e;
+    for (int k = 0; k < d; ++k) { idx[k] = ee % pr.nmac[k]; ee /= pr.nmac[k]; }
+    for (int k = 0; k < d; ++k)
+      for (int side = 0; side < 2; ++side) {
+        int fl = 2 * k + side;
+        int pos = idx[k] + side;
+        int bs = -1;
+        if (pos == pr.nmac[k]) {
+          if (pr.periodic[k]) pos = 0;
+          else bs = 2 * k + 1;
+        }
+        if (pos == 0 && side == 0 && !pr.periodic[k]) bs = 2 * k;
+        int loc = 0;
+        for (int j = d - 1; j >= 0; --j)
+          if (j != k) loc = loc * pr.nmac[j] + idx[j];
+        int f = goff[k] + pos + npos[k] * loc;
+        for (int s = 0; s < ns; ++s)
+          for (int j = 0; j < Nfn; ++j)
+            ctx->h_gather[(size_t)e * Nt + s * Nth + fl * Nfn + j] = (f * ns + s) * Nfn + j;
+        int slotidx = (ctx->h_owner[2 * f] < 0) ? 0 : 1;
+        if (ctx->h_owner[2 * f + slotidx] >= 0) return ctx_fail(ctx, MEHDG_ERR_ARG, "face with more than two owners");
+        ctx->h_owner[2 * f + slotidx] = e * 2 * d + fl;
+        ctx->h_bside[e * 2 * d + fl] = bs;
+        ctx->h_bkind[e * 2 * d + fl] = bs >= 0 ? pr.bc[bs] : 0;
+        if (bs >= 0 && pr.bc[bs] == MEHDG_BC_NONE)
+          return ctx_fail(ctx, MEHDG_ERR_ARG, "boundary side without boundary condition");
+      }
+  }
+
+  // -- device allocations
+  const size_t Nu = ctx->Nu;
+  ALLOC(ctx->gather, (size_t)E * Nt);
+  ALLOC(ctx->owner, 2 * F);
+  ALLOC(ctx->bkind, E * 2 * d);
+  ALLOC(ctx->bside, E * 2 * d);
+  ALLOC(ctx->fnode, 2 * d * Nfn);
+  ALLOC(ctx->tab, 2 * ng1 * (p + 1) + 2 * ng1 + d * n1);
+  ALLOC(ctx->Mref, (size_t)Np * Np);
+  ALLOC(ctx->Minv, (size_t)Np * Np);
+  ALLOC(ctx->Gk, (size_t)d * Np * Np);
+  ALLOC(ctx->Ghk, (size_t)d * Np * Nth);
+  ALLOC(ctx->Wk, (size_t)d * Np * Np);
+  ALLOC(ctx->Whk, (size_t)d * Np * Nth);
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->gather, ctx->h_gather.data(), sizeof(int) * E * Nt, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->owner, ctx->h_owner.data(), sizeof(int) * 2 * F, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->bkind, ctx->h_bkind.data(), sizeof(int) * E * 2 * d, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->bside, ctx->h_bside.data(), sizeof(int) * E * 2 * d, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->fnode, ctx->facenode.data(), sizeof(int) * 2 * d * Nfn, cudaMemcpyHostToDevice, st));
+  std::vector<double> tab;
+  tab.insert(tab.end(), ctx->b1.begin(), ctx->b1.end());
+  tab.insert(tab.end(), ctx->db1.begin(), ctx->db1.end());
+  tab.insert(tab.end(), wg.begin(), wg.end());
+  tab.insert(tab.end(), xg.begin(), xg.end());
+  for (int k = 0; k < d; ++k) tab.insert(tab.end(), xn1[k].begin(), xn1[k].end());
+  CK(cudaMemcpyAsync(ctx->tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->Mref, Mref.data(), sizeof(double) * Np * Np, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->Minv, Minv.data(), sizeof(double) * Np * Np, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->Gk, Gk.data(), sizeof(double) * d * Np * Np, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->Ghk, Ghk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->Wk, Wk.data(), sizeof(double) * d * Np * Np, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->Whk, Whk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
+
+  ALLOC(ctx->Auu, (size_t)E * Nu * Nu);
+  ALLOC(ctx->Auq, (size_t)E * d * Nu * Nu);
+  ALLOC(ctx->Auh, (size_t)E * Nu * Nt);
+  ALLOC(ctx->Ahu, (size_t)E * Nt * Nu);
+  ALLOC(ctx->Ahq, (size_t)E * d * Nt * Nu);
+  ALLOC(ctx->Ahh, (size_t)E * Nt * Nt);
+  ALLOC(ctx->perm, (size_t)E * Nu);
+  ALLOC(ctx->RQ, (size_t)E * d * Nu);
+  ALLOC(ctx->RU, (size_t)E * Nu);
+  ALLOC(ctx->RUh, (size_t)E * Nt);
+  ALLOC(ctx->gv, (size_t)E * Nu);
+  ALLOC(ctx->hv, (size_t)E * Nt);
+  ALLOC(ctx->MinvRQ, (size_t)E * d * Nu);
+  ALLOC(ctx->bloc, (size_t)E * Nt);
+  ALLOC(ctx->slot, (size_t)E * Nt);
+  ALLOC(ctx->Kvol, (size_t)E * (d + 1) * ns * ctx->nel * ctx->Ng * (d + 1) * ns * (d + 1));
+  ALLOC(ctx->rvol, (size_t)E * ctx->nel * ctx->Ng * ns * (d + 1));
+  ALLOC(ctx->Kface, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * ctx->ndir_f * 2 * ns);
+  ALLOC(ctx->rface, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * 2 * ns);
+  ctx->nfb = ns * Nfn;
+  ALLOC(ctx->fblk, (size_t)F * ctx->nfb * ctx->nfb);
+  ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
+  ALLOC(ctx->dflag, 16);
+  ALLOC(ctx->dred, 1 << 16);
+  CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * (1 << 16)));
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) {
+    ALLOC(ctx->S32, (size_t)E * Nu * Nu);
+    ALLOC(ctx->B32, (size_t)E * Nt * Nu);
+    ALLOC(ctx->C32, (size_t)E * Nu * Nt);
+    ALLOC(ctx->D32, (size_t)E * Nt * Nt);
+    ALLOC(ctx->perm32, (size_t)E * Nu);
+  }
+  ctx->restart = std::max(2, ctx->opt.restart);
+  const long long n = ctx->ntr;
+  ALLOC(ctx->V, (size_t)(ctx->restart + 1) * n);
+  ALLOC(ctx->Zk, (size_t)ctx->restart * n);
+  ALLOC(ctx->wv, n);
+  ALLOC(ctx->tv, n);
+  ALLOC(ctx->tv2, n);
+  ALLOC(ctx->rv, n);
+  int nin = std::max(1, ctx->opt.inner_iters);
+  ALLOC(ctx->iV, (size_t)(nin + 1) * n);
+  ALLOC(ctx->iw, n);
+  ALLOC(ctx->un, (size_t)E * Nu);
+  ALLOC(ctx->ustage, (size_t)3 * E * Nu);
+  ALLOC(ctx->hist, (size_t)E * Nu);
+  ALLOC(ctx->du, (size_t)E * Nu);
+  ALLOC(ctx->dq, (size_t)E * d * Nu);
+  ALLOC(ctx->duh, n);
+  ALLOC(ctx->bhat, n);
+
+  // closed-form data
+  Geo g = make_geo(ctx);
+  if (pr.field == MEHDG_FIELD_MMS) {
+    long long tot = (long long)E * ctx->nel * ctx->Ng;
+    ALLOC(ctx->src, tot * ns);
+    int bs = 128;
+    if (d == 2) k_source<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->src);
+    else k_source<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->src);
+    CKL();
+  }
+  {
+    long long tot = (long long)E * 2 * d * ctx->nsf * ctx->nfp;
+    ALLOC(ctx->uD, tot * ns);
+    int bs = 128;
+    if (d == 2) k_dirichlet<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
+    else k_dirichlet<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
+    CKL();
+  }
+  CK(cudaStreamSynchronize(st));
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob, const mehdg_options* opt,
+                          void* stream) {
+  if (!out || !prob) return MEHDG_ERR_ARG;
+  *out = nullptr;
+  if (nprob != 1) return MEHDG_ERR_ARG;
+  const mehdg_problem& pr = prob[0];
+  if (pr.dim < 2 || pr.dim > 3 || pr.m < 1 || pr.p < 1 || pr.p > 3 || pr.m * pr.p > 12) return MEHDG_ERR_ARG;
+  for (int k = 0; k < pr.dim; ++k)
+    if (pr.nmac[k] < 1 || !(pr.hi[k] > pr.lo[k])) return MEHDG_ERR_ARG;
+  if (!(pr.gamma > 1.0) || !(pr.Re > 0.0) || !(pr.Pr > 0.0)) return MEHDG_ERR_ARG;
+  mehdg_ctx* ctx = new mehdg_ctx();
+  ctx->prob = pr;
+  default_options(&ctx->opt);
+  if (opt) ctx->opt = *opt;
+  ctx->stream = (cudaStream_t)stream;
+  int rc = setup(ctx);
+  if (rc != MEHDG_OK) {
+    std::string msg = ctx->err;
+    mehdg_destroy(ctx);
+    fprintf(stderr, "mehdg_mesh: %s\n", msg.c_str());
+    return rc;
+  }
+  *out = ctx;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_query(const mehdg_ctx* c, mehdg_info* info) {
+  if (!c || !info) return MEHDG_ERR_ARG;
+  info->dim = c->d; info->ns = c->ns; info->Np = c->Np; info->Nfn = c->Nfn; info->Nth = c->Nth;
+  info->Nu = c->Nu; info->Nq = c->Nq; info->Nt = c->Nt; info->n_macro = c->E; info->n_face = c->F;
+  info->n_trace = c->ntr; info->bytes_device = c->bytes;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_init_state(mehdg_ctx* ctx, const double* du, const double* duh, int lift, double* u,
+                                double* q, double* uh) {
+  if (!ctx || !u || !q || !uh) return MEHDG_ERR_ARG;
+  Geo g = make_geo(ctx);
+  cudaStream_t st = ctx->stream;
+  const double* xnode1 = ctx->tab + 2 * ctx->ng1 * (ctx->p + 1) + 2 * ctx->ng1;
+  long long tot = (long long)ctx->E * ctx->Np;
+  int bs = 128;
+  if (ctx->d == 2) k_init_state<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
+  else k_init_state<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
+  CKL();
+  k_init_trace<<<(ctx->ntr + bs - 1) / bs, bs, 0, st>>>(g, ctx->owner, ctx->fnode, u, duh, uh, ctx->F);
+  CKL();
+  long long nq = (long long)ctx->E * ctx->Nq;
+  if (lift) {
+    k_lift<<<(nq + bs - 1) / bs, bs, 0, st>>>(g, ctx->Wk, ctx->Whk, ctx->gather, u, uh, q, ctx->E);
+    CKL();
+  } else {
+    CK(cudaMemsetAsync(q, 0, sizeof(double) * nq, st));
+  }
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_get_block(mehdg_ctx* ctx, int which, int e, double* out, long long* count) {
+  if (!ctx || e < 0 || e >= ctx->E) return MEHDG_ERR_ARG;
+  const size_t Nu = ctx->Nu, Nt = ctx->Nt, d = ctx->d;
+  const double* src = nullptr;
+  size_t n = 0;
+  bool ints = false;
+  const int* isrc = nullptr;
+  switch (which) {
+    case 0: src = ctx->Auu + e * Nu * Nu; n = Nu * Nu; break;
+    case 1: case 2: case 3:
+      if (which > (int)d) return MEHDG_ERR_ARG;
+      src = ctx->Auq + (e * d + (which - 1)) * Nu * Nu; n = Nu * Nu; break;
+    case 4: src = ctx->Auh + e * Nu * Nt; n = Nu * Nt; break;
+    case 5: src = ctx->Ahu + e * Nt * Nu; n = Nt * Nu; break;
+    case 6: case 7: case 8:
+      if (which - 5 > (int)d) return MEHDG_ERR_ARG;
+      src = ctx->Ahq + (e * d + (which - 6)) * Nt * Nu; n = Nt * Nu; break;
+    case 9: src = ctx->Ahh + e * Nt * Nt; n = Nt * Nt; break;
+    case 10: src = ctx->RQ + e * d * Nu; n = d * Nu; break;
+    case 11: src = ctx->RU + e * Nu; n = Nu; break;
+    case 12: src = ctx->RUh + e * Nt; n = Nt; break;
+    case 13: src = ctx->gv + e * Nu; n = Nu; break;
+    case 14: src = ctx->hv + e * Nt; n = Nt; break;
+    case 15: isrc = ctx->perm + e * Nu; n = Nu; ints = true; break;
+    case 16: src = ctx->bloc + e * Nt; n = Nt; break;
+    default: return MEHDG_ERR_ARG;
+  }
+  if (count) *count = (long long)n;
+  if (!out) return MEHDG_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ints) {
+    std::vector<int> tmp(n);
+    CK(cudaMemcpy(tmp.data(), isrc, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
+  } else {
+    CK(cudaMemcpy(out, src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  }
+  return MEHDG_OK;
+}
+
+extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  void* ptrs[] = {ctx->gather, ctx->owner, ctx->bkind, ctx->bside, ctx->fnode, ctx->tab, ctx->Mref, ctx->Minv,
+                  ctx->Gk, ctx->Ghk, ctx->Wk, ctx->Whk, ctx->src, ctx->uD, ctx->Auu, ctx->Auq, ctx->Auh,
+                  ctx->Ahu, ctx->Ahq, ctx->Ahh, ctx->perm, ctx->RQ, ctx->RU, ctx->RUh, ctx->gv, ctx->hv,
+                  ctx->MinvRQ, ctx->bloc, ctx->slot, ctx->Kvol, ctx->rvol, ctx->Kface, ctx->rface, ctx->fblk,
+                  ctx->fperm, ctx->dflag, ctx->dred, ctx->S32, ctx->B32, ctx->C32, ctx->D32, ctx->perm32,
+                  ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
+                  ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->hred) cudaFreeHost(ctx->hred);
+  delete ctx;
+}
+
+extern "C" const char* mehdg_last_error(const mehdg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

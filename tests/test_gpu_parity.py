@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every test feeds the same seeded inputs to both sides and compares element by
+element.  Tolerances: blocks, residuals, condensed operators, the trace apply,
+local solves and recovery agree to 1e-11 relative to the largest entry (FP64 on
+both sides, different summation orders); Newton and DIRK end states agree to
+1e-9 relative in L2 (both solved to stagnation-level tolerances).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import assemble as asm
+from oracle import solve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as m
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for gpu tests")
+    return m
+
+
+def to_dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+CASES = {
+    "mms2d_p2": (lambda: W.mms(dim=2, nmac=3, m=2, p=2), [0, 4, 8]),
+    "couette2d_p2": (lambda: W.couette2d(nmac=3, m=2, p=2), [0, 1, 5, 8]),
+    "mms2d_p3_m1": (lambda: W.mms(dim=2, nmac=2, m=1, p=3), [0, 3]),
+    "mms3d_p1": (lambda: W.mms(dim=3, nmac=2, m=2, p=1), [0, 7]),
+    "tgv3d_p2": (lambda: W.tgv(nmac=2, m=2, p=2), [3]),
+}
+
+
+def _oracle_blocks(P, u, q, uh, e, tt=None):
+    geo = P.geometry(e)
+    tte = None
+    if tt is not None:
+        tte = dict(coef=tt["coef"], hist=None if tt.get("hist") is None else tt["hist"][e], supg_time=True)
+    return geo, asm.assemble_macro(geo, P.phys, u[e], q[e], P.local_trace(e, uh), tte, P.source(geo),
+                                   P.bfaces(e, geo))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_assembly_blocks_and_residuals(lib, case):
+    mk, macros = CASES[case]
+    pr = mk()
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 21)
+    hist = 0.05 * np.ones_like(u)
+    ctx = lib.Context(pr)
+    norms = ctx.assemble(to_dev(u), to_dev(q), to_dev(uh), coef=0.4, hist=to_dev(hist), supg_time=1)
+    tt = dict(coef=0.4, hist=hist)
+    _, _, onrm, _ = solve.global_assemble(P, u, q, uh, tt, want_jac=False)
+    assert np.allclose(norms, [onrm["RQ"], onrm["RU"], onrm["RUh"], onrm["RF"]], rtol=1e-11)
+    d = P.d
+    for e in macros:
+        geo, b = _oracle_blocks(P, u, q, uh, e, tt)
+        Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+        assert rel(ctx.get_block(0, e).reshape(Nu, Nu), b["Auu"]) < 1e-11
+        for k in range(d):
+            assert rel(ctx.get_block(1 + k, e).reshape(Nu, Nu), b["Auq"][k]) < 1e-11
+            assert rel(ctx.get_block(6 + k, e).reshape(Nt, Nu), b["Ahq"][k]) < 1e-11
+        assert rel(ctx.get_block(4, e).reshape(Nu, Nt), b["Auh"]) < 1e-11
+        assert rel(ctx.get_block(5, e).reshape(Nt, Nu), b["Ahu"]) < 1e-11
+        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), b["Ahh"]) < 1e-11
+        assert rel(ctx.get_block(10, e), b["RQ"].reshape(-1)) < 1e-11
+        assert rel(ctx.get_block(11, e), b["RU"].reshape(-1)) < 1e-11
+        assert rel(ctx.get_block(12, e), b["RUh"].reshape(-1)) < 1e-11
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def condensed2d(lib):
+    pr = W.mms(dim=2, nmac=3, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    ctx = lib.Context(pr)
+    ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+    bhat = ctx.condense(shift=0.3)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    yield P, ctx, blks, geos, cond, bhat
+    ctx.close()
+
+
+def test_condensed_operators_and_rhs(condensed2d):
+    P, ctx, blks, geos, cond, bhat = condensed2d
+    Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+    for e in range(P.E):
+        c = cond[e]
+        assert rel(ctx.get_block(4, e).reshape(Nu, Nt), c["C"]) < 1e-11
+        assert rel(ctx.get_block(5, e).reshape(Nt, Nu), c["B"]) < 1e-11
+        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), c["D"]) < 1e-11
+        assert rel(ctx.get_block(13, e), c["g"]) < 1e-11
+        assert rel(ctx.get_block(14, e), c["h"]) < 1e-11
+        perm = ctx.get_block(15, e).astype(int)
+        assert np.array_equal(perm, c["piv"])          # same pivot sequence (first max wins ties)
+        assert rel(ctx.get_block(0, e).reshape(Nu, Nu), c["LU"]) < 1e-10
+        assert rel(ctx.get_block(16, e), c["bhat"]) < 1e-10
+    assert rel(bhat.cpu().numpy(), solve.assemble_bhat(P, cond)) < 1e-10
+
+
+def test_trace_apply_matches_algorithm2(condensed2d):
+    P, ctx, blks, geos, cond, bhat = condensed2d
+    x = W.random_vector(P.F * P.ns * P.Nfn, 9)
+    y = ctx.apply(to_dev(x)).cpu().numpy()
+    assert rel(y, solve.apply_trace(P, cond, x)) < 1e-11
+    # linearity and the zero vector
+    assert np.abs(ctx.apply(to_dev(0 * x)).cpu().numpy()).max() == 0.0
+
+
+def test_recovery_matches_csc4(condensed2d):
+    P, ctx, blks, geos, cond, bhat = condensed2d
+    duh = W.random_vector(P.F * P.ns * P.Nfn, 10, 0.01)
+    du, dq = ctx.recover(to_dev(duh))
+    du, dq = du.cpu().numpy(), dq.cpu().numpy()
+    for e in range(P.E):
+        ou, oq = solve.recover(geos[e], blks[e], cond[e], duh[P.maps[e].reshape(-1)])
+        assert rel(du[e].reshape(-1), ou) < 1e-10
+        assert rel(dq[e].reshape(-1), oq) < 1e-10
+
+
+def test_preconditioners_match(condensed2d):
+    P, ctx, blks, geos, cond, bhat = condensed2d
+    fb = solve.face_blocks(P, blks)
+    flu = [solve.lu_factor(fb[f]) for f in range(P.F)]
+    r = W.random_vector(P.F * P.ns * P.Nfn, 12)
+    z0 = ctx.precondition(0, to_dev(r)).cpu().numpy()
+    M0 = lambda v: solve.block_jacobi(P, flu, v)
+    assert rel(z0, M0(r)) < 1e-11
+    z1 = ctx.precondition(1, to_dev(r)).cpu().numpy()
+    z1o = solve.gmres_fixed(lambda v: solve.apply_trace(P, cond, v), M0, r, ctx.options["inner_iters"])
+    assert rel(z1, z1o) < 1e-9
+
+
+def test_fgmres_matches_dense_solve(lib):
+    pr = W.mms(dim=2, nmac=3, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    for precond in (0, 1):
+        ctx = lib.Context(pr, dict(lin_rtol=1e-13, precond=precond, restart=25))
+        ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+        b = ctx.condense(shift=0.3)
+        x, st = ctx.linear_solve(b)
+        blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+        cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+        xo = np.linalg.solve(solve.explicit_trace_matrix(P, cond), solve.assemble_bhat(P, cond))
+        assert rel(x.cpu().numpy(), xo) < 1e-9
+        assert st["fgmres_iters"] > 0
+        ctx.close()
+
+
+def _oracle_init(P, pr, du, duh):
+    """The initial state rule of mehdg_init_state written with the oracle's spaces."""
+    from oracle import fields
+    u = np.zeros((P.E, P.ns, P.Np))
+    for e in range(P.E):
+        g = P.geometry(e)
+        if pr["field"] == W.FIELD_MMS:
+            u[e] = fields.mms_u(g.xn, pr["field_par"], pr["gamma"])
+        elif pr["field"] == W.FIELD_TGV:
+            u[e] = fields.tgv_u(g.xn, pr["field_par"][0], pr["gamma"])
+        else:
+            u[e] = solve.uniform_from_par(pr)[:, None]
+    u = u + du
+    uh = np.zeros(P.F * P.ns * P.Nfn)
+    fn = None
+    for f, own in enumerate(P.mesh.face_owners()):
+        e, fl = own[0]
+        g = P.geometry(e)
+        # macro nodes on local face fl in face-node order
+        k, side = fl // 2, fl % 2
+        idx = np.arange(P.Np).reshape([P.mesh.n1] * P.d)      # [.., i1, i0] (axis 0 fastest)
+        sl = [slice(None)] * P.d
+        sl[P.d - 1 - k] = -1 if side else 0
+        fn = idx[tuple(sl)].reshape(-1)
+        for s in range(P.ns):
+            uh[(f * P.ns + s) * P.Nfn:(f * P.ns + s + 1) * P.Nfn] = u[e, s, fn]
+    return u, np.zeros((P.E, P.d, P.ns, P.Np)), uh + duh
+
+
+def test_init_state_matches(lib):
+    pr = W.couette2d(nmac=3)
+    P = solve.Problem(pr)
+    du, duh = W.perturbation(pr, 0)
+    ctx = lib.Context(pr)
+    u, q, uh = ctx.init_state(to_dev(du), to_dev(duh))
+    ou, oq, ouh = _oracle_init(P, pr, du, duh)
+    assert rel(u.cpu().numpy(), ou) < 1e-14
+    assert rel(uh.cpu().numpy(), ouh) < 1e-14
+    ctx.close()
+
+
+def test_steady_newton_couette_matches_oracle(lib):
+    """Config 'Couette 2D' (4x4 macros of 2x2 quads, p = 2) solved to stagnation."""
+    pr = W.couette2d(nmac=4)
+    P = solve.Problem(pr)
+    du, duh = W.perturbation(pr, 0)
+    u0, q0, uh0 = _oracle_init(P, pr, du, duh)
+    ou, oq, ouh, hist = solve.newton_ser(P, u0, q0, uh0, rtol=1e-12, precond="direct")
+    ctx = lib.Context(pr, dict(newton_rtol=1e-12, lin_rtol=1e-12, max_iters=4000, max_newton=60, precond=1))
+    u, q, uh = ctx.init_state(to_dev(du), to_dev(duh))
+    st = ctx.dirk_stage(0, 0.0, u, q, uh)
+    assert st["res"] <= 1e-12 * st["res0"] * 1.0001 or st["res"] < 1e-13
+    assert rel(u.cpu().numpy(), ou) < 1e-9
+    assert rel(uh.cpu().numpy(), ouh) < 1e-9
+    ctx.close()
+
+
+def test_dirk_step_matches_oracle(lib):
+    """One 3-stage DIRK step (eq. C242) on a small periodic TGV-like 2D flow."""
+    pr = W.periodic_uniform(dim=2, nmac=2, m=2, p=2, v=(0.1, 0.05, 0))
+    P = solve.Problem(pr)
+    du, duh = W.perturbation(pr, 4, amp=2e-3)
+    u0, q0, uh0 = _oracle_init(P, pr, du, duh)
+    ou, oq, ouh, stats = solve.dirk_step(P, u0, q0, uh0, dt=0.05, rtol=1e-13, precond="direct")
+    ctx = lib.Context(pr, dict(newton_rtol=1e-13, newton_atol=1e-15, lin_rtol=1e-13, max_iters=4000, precond=1))
+    u, q, uh = ctx.init_state(to_dev(du), to_dev(duh))
+    for stage in (1, 2, 3):
+        ctx.dirk_stage(stage, 0.05, u, q, uh)
+    assert rel(u.cpu().numpy(), ou) < 1e-9
+    assert rel(uh.cpu().numpy(), ouh) < 1e-9
+    ctx.close()
