@@ -1,0 +1,405 @@
+"""Benchmark: time per Newton step of the steady manufactured-solution solve (3D cube,
+8^3 macro-elements of 2^3 hexes, p = 2) to a 1e-8 nonlinear residual, FGMRES
+iterations, batched local LU TFLOP/s, on one GB300.
+
+A "step" is one Newton step of that solve: assembly of residuals and Newton
+blocks, second-layer condensation and batched LU, FGMRES on the trace system,
+local recovery and the state update.  The warm-up runs the whole solve once and
+records the state and pseudo-time step entering every Newton step; the timed
+region replays K Newton steps of that sequence (step k uses recorded state
+k mod N), so the per-step mean over N steps is the mean over the real solve.
+Inputs (about 18 GB of blocks per step) exceed the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                  [--impl ours|reference]
+
+--impl reference times the FP64 numpy oracle on the host cores on a bounded
+sample of the same workload (a few macro-elements), scaled to the full problem.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "time per Newton/DIRK step & FGMRES iters at 1e-8 residual; batched local LU TFLOP/s"
+UNIT = "s/Newton step"
+
+
+def workload():
+    return W.mms(dim=3, nmac=8, m=2, p=2)
+
+
+def sizes(pr):
+    z = W.sizes(pr)
+    z["Nu"] = z["ns"] * z["Np"]
+    z["Nt"] = z["ns"] * z["Nth"]
+    return z
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lrk = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lrk
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        try:
+            sm = [float(r[1]) for r in self.rows if r[1] not in ("", "[N/A]")]
+            mx = [float(r[2]) for r in self.rows if r[2] not in ("", "[N/A]")]
+            if sm:
+                out["sm_mhz"] = float(np.median(sm))
+            if mx:
+                out["sm_max_mhz"] = max(mx)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for i, n in enumerate(names):
+                if any(r[5 + i].lower().startswith("active") for r in self.rows if len(r) > 5 + i):
+                    out["reasons"].append(n)
+        except (ValueError, IndexError):
+            pass
+        return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def fp64_peak_tflops(torch):
+    """Measured FP64 dense rate on this GPU: cuBLAS DGEMM 4096^3, best of 5 (CUDA events)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 1e9
+    for _ in range(5):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(a, b)
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def phase_work(z, E, precision):
+    """Algorithmic FLOPs (and bytes for the apply) per launch of the main phases."""
+    Nu, Nt, Np, Nth, d, ns = z["Nu"], z["Nt"], z["Np"], z["Nth"], z["d"], z["ns"]
+    w = 8 if precision == "fp64" else 4
+    cond = 2.0 * d * ns * (Nu * Np * Np + Nu * Np * Nth + Nt * Np * Np + Nt * Np * Nth) * E
+    lu = (2.0 / 3.0) * Nu ** 3 * E
+    apply_bytes = (w * (2 * Nu * Nt + Nt * Nt + Nu * Nu) + 8 * 2 * Nt + 4 * (Nu + Nt)) * E
+    apply_flops = 2.0 * (2 * Nu * Nt + Nt * Nt + Nu * Nu) * E
+    return dict(condense_flops=cond, lu_flops=lu, apply_bytes=apply_bytes, apply_flops=apply_flops)
+
+
+def run_ours(args, ws, rank, lrank):
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+
+    dev = torch.device("cuda:%d" % lrank)
+    torch.cuda.set_device(dev)
+    pr = workload()
+    z = sizes(pr)
+    prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
+    opts = dict(precision=prec, precond=args.precond, restart=30, max_iters=3000, lin_rtol=args.lin_rtol,
+                newton_rtol=1e-8, max_newton=60)
+    ctx = pkg.Context(pr, opts, device=dev)
+    du, duh = W.perturbation(pr, 0)
+    du_d = torch.as_tensor(du, device=dev)
+    duh_d = torch.as_tensor(duh, device=dev)
+    u, q, uh = ctx.init_state(du_d, duh_d, lift=True)
+    st = torch.cuda.current_stream(dev)
+
+    # ---- warm-up: the whole steady solve, recording every Newton step's input
+    records = []
+    tau_init, tau_max = 1.0, 1e8
+    norms = ctx.assemble(u, q, uh)
+    R0 = norms[3]
+    dtau = tau_init
+    t_solve0 = time.perf_counter()
+    its_total = 0
+    while norms[3] > 1e-8 * R0 and len(records) < 60:
+        records.append((u.clone(), q.clone(), uh.clone(), dtau, norms.copy()))
+        bhat = ctx.condense(shift=1.0 / dtau)
+        duh_s, stats = ctx.linear_solve(bhat, allow_not_converged=True)
+        its_total += stats["fgmres_iters"]
+        dU, dQ = ctx.recover(duh_s)
+        u += dU
+        q += dQ
+        uh += duh_s
+        RU_old = norms[1]
+        norms = ctx.assemble(u, q, uh)
+        dtau = min(max(dtau * RU_old / max(norms[1], 1e-300), tau_init), tau_max)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t_solve0
+    converged = bool(norms[3] <= 1e-8 * R0)
+    N = len(records)
+    assert N > 0
+    # extra warm-up replays if requested
+    def replay(k, host=None):
+        u0, q0, uh0, dt_, _ = records[k % N]
+        if host is not None:
+            hu, hq, huh = host[k % N]
+            u.copy_(hu, non_blocking=True)
+            q.copy_(hq, non_blocking=True)
+            uh.copy_(huh, non_blocking=True)
+        else:
+            u.copy_(u0)
+            q.copy_(q0)
+            uh.copy_(uh0)
+        ctx.assemble(u, q, uh)
+        bhat = ctx.condense(shift=1.0 / dt_)
+        duh_s, stats = ctx.linear_solve(bhat, allow_not_converged=True)
+        dU, dQ = ctx.recover(duh_s)
+        u.add_(dU)
+        q.add_(dQ)
+        uh.add_(duh_s)
+        return stats["fgmres_iters"]
+
+    for k in range(max(0, args.warmup - N)):
+        replay(k)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(lrank)
+    clk.start()
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phase_acc = {}
+    its_timed = 0
+    ev0.record(st)
+    for k in range(args.steps):
+        its_timed += replay(k)
+        ph = ctx.phase_times() if args.phases else {}
+        for key, v in ph.items():
+            phase_acc.setdefault(key, []).append(v)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    launches = ctx.launch_count() - l0
+    clocks = clk.stop()
+    if ws > 1:
+        t = torch.tensor([t_dev], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(t.item())
+        torch.distributed.barrier()
+
+    # ---- e2e: host (pinned) buffers in, state out, per step
+    host = [(r[0].cpu().pin_memory(), r[1].cpu().pin_memory(), r[2].cpu().pin_memory()) for r in records]
+    out_u = torch.empty(u.shape, dtype=torch.float64).pin_memory()
+    out_q = torch.empty(q.shape, dtype=torch.float64).pin_memory()
+    out_uh = torch.empty(uh.shape, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(args.steps):
+        replay(k, host)
+        out_u.copy_(u, non_blocking=True)
+        out_q.copy_(q, non_blocking=True)
+        out_uh.copy_(uh, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    bytes_io = 8 * (u.numel() + q.numel() + uh.numel())
+
+    # ---- roofline of the dominant kernel: phase with the largest time per step
+    work = phase_work(z, z["E"], args.precision)
+    ph_mean = {k: float(np.mean(v)) for k, v in phase_acc.items() if v and v[0] >= 0}
+    peaks = measured_peaks()
+    fp64_peak = None
+    roof = None
+    if ph_mean:
+        dom = max(("condense", "lu", "vol_contract", "vol_point", "apply"), key=lambda k: ph_mean.get(k, 0.0) *
+                  (its_timed / args.steps if k == "apply" else 1.0))
+        if args.precision == "fp64" or dom not in ("condense", "lu"):
+            fp64_peak = fp64_peak_tflops(torch)
+        if dom == "apply":
+            ach = work["apply_bytes"] / (ph_mean["apply"] / 1e3) / 1e9
+            pk = peaks.get("hbm_gbs", 6800.0)
+            roof = dict(kernel="k_apply (Algorithm 2, one launch = all macro-elements)", bound="hbm",
+                        achieved=ach, peak=pk, unit="GB/s", frac=ach / pk, traffic=None,
+                        peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback")
+        else:
+            fl = {"condense": work["condense_flops"], "lu": work["lu_flops"]}.get(dom)
+            if fl is None:
+                fl = 0.0
+            ach = fl / (ph_mean[dom] / 1e3) / 1e12
+            if args.precision == "fp64":
+                roof = dict(kernel=dom, bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s",
+                            frac=ach / fp64_peak if fp64_peak else None, traffic=None,
+                            peak_source="measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)")
+            else:
+                tf32 = peaks.get("bf16_tflops", 1918.0) / 2.0
+                roof = dict(kernel=dom, bound="tensor", achieved=ach, peak=tf32, unit="TFLOP/s", frac=ach / tf32,
+                            traffic=None, peak_source="measured bf16 burst x nominal tf32/bf16 ratio 1/2")
+    lu_tflops = None
+    if "lu" in ph_mean and ph_mean["lu"] > 0:
+        lu_tflops = work["lu_flops"] / (ph_mean["lu"] / 1e3) / 1e12
+
+    per_step = t_dev / args.steps
+    line = {
+        "metric": METRIC,
+        "value": per_step / ws,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": max(args.warmup, N),
+        "ms_per_step": per_step * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32/tf32 blocks, f64 residual+krylov",
+        "data": "synthetic (manufactured solution, seeded 1e-3 perturbation, seed 0)",
+        "config": {"workload": "3D steady MMS cube, 8^3 macro-elements x 2^3 hexes, p=2 (%d macros, Nu=%d, Nt=%d, "
+                               "%d trace DOFs)" % (z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
+                   "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "fgmres_iters_per_step": its_timed / args.steps,
+        "solve": {"newton_steps": N, "fgmres_iters": its_total, "converged_1e-8": converged,
+                  "wall_s": t_solve, "res0": float(R0), "res": float(norms[3])},
+        "batched_lu_tflops": lu_tflops,
+        "phases_ms": ph_mean,
+        "e2e": {"value": t_e2e / args.steps / ws, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                "d2h_bytes_per_step": bytes_io},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    ctx.close()
+    return line
+
+
+def oracle_sample_time(pr, n_macro=2, fgmres_iters=None):
+    """Oracle (numpy FP64) time of one Newton step on a bounded sample, scaled to the workload."""
+    from oracle import solve as osolve
+    from oracle import assemble as oasm
+    P = osolve.Problem(pr)
+    u, q, uh = W.random_state(pr, 0)
+    t0 = time.perf_counter()
+    for e in range(n_macro):
+        geo = P.geometry(e)
+        blk = oasm.assemble_macro(geo, P.phys, u[e], q[e], P.local_trace(e, uh), None, P.source(geo),
+                                  P.bfaces(e, geo))
+        c = osolve.condense_second_layer(geo, blk, 1.0)
+    t_local = (time.perf_counter() - t0) / n_macro
+    x = np.random.default_rng(1).normal(size=c["C"].shape[1])
+    t1 = time.perf_counter()
+    for _ in range(3):
+        osolve.apply_local(c, x)
+    t_apply = (time.perf_counter() - t1) / 3
+    its = fgmres_iters if fgmres_iters else 100
+    per_step = P.E * t_local + its * P.E * t_apply
+    return per_step, dict(sample="assembly + second-layer condensation + LU of %d macro-elements and 3 Algorithm-2 "
+                                 "applies of one macro-element, scaled by %d macros and %d FGMRES iterations per step"
+                                 % (n_macro, P.E, its), cores=os.cpu_count())
+
+
+def run_reference(args):
+    pr = workload()
+    times = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        t, info = oracle_sample_time(pr, n_macro=1)
+        if k >= args.warmup:
+            times.append(t)
+    val = float(np.mean(times))
+    import torch
+    threads = torch.get_num_threads() if hasattr(torch, "get_num_threads") else os.cpu_count()
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D steady MMS cube, 8^3 macro-elements x 2^3 hexes, p=2"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"], "threads_numpy": threads},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed Newton steps (default: one full solve)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", type=int, default=1)
+    ap.add_argument("--lin-rtol", type=float, default=1e-3)
+    ap.add_argument("--no-phases", dest="phases", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
+    args = ap.parse_args()
+    ws, rank, lrank = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            args.steps = args.steps or 1
+            print(json.dumps(run_reference(args)))
+        return
+    if ws > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    if args.steps == 0:
+        args.steps = 6
+    line = run_ours(args, ws, rank, lrank)
+    if rank == 0:
+        if args.cpu:
+            t, info = oracle_sample_time(workload(), n_macro=1,
+                                         fgmres_iters=max(1, int(round(line["fgmres_iters_per_step"]))))
+            line["cpu_baseline"] = {"value": t, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                                    "sample": info["sample"]}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

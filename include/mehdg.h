@@ -183,6 +183,18 @@ int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q,
 int mehdg_get_block(mehdg_ctx* ctx, int which, int macro, double* host_out,
                     long long* count);
 
+/* Device time in milliseconds of the most recent execution of each internal phase
+ * (CUDA events on the context stream; -1 for phases not run since mehdg_mesh):
+ * 0 volume pointwise Jacobians, 1 volume contraction, 2 faces + R_Q, 3 condensation
+ * products, 4 batched LU of S, 5 LU of the face blocks, 6 condensed rhs, 7 trace
+ * apply kernel, 8 recovery, 9 block-Jacobi.  ms: host double[n], n <= 16.
+ * Synchronises the stream. */
+int mehdg_phase_times(mehdg_ctx* ctx, double* ms, int n);
+
+/* Number of CUDA kernels this context has launched since mehdg_mesh (host counter;
+ * count is host memory). */
+int mehdg_launch_count(const mehdg_ctx* ctx, long long* count);
+
 void mehdg_destroy(mehdg_ctx* ctx);
 const char* mehdg_last_error(const mehdg_ctx* ctx);
 

@@ -19,7 +19,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_local", "mehdg_condense_factor",
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
-           "mehdg_get_block", "mehdg_destroy", "mehdg_last_error"]
+           "mehdg_get_block", "mehdg_phase_times", "mehdg_launch_count", "mehdg_destroy", "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
 
@@ -84,6 +84,8 @@ def load_library(path=LIB_PATH):
     lib.mehdg_recover.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     lib.mehdg_dirk_stage.argtypes = [c_void_p, I, c_double, c_void_p, c_void_p, c_void_p, P(SolveStats)]
     lib.mehdg_get_block.argtypes = [c_void_p, I, I, c_void_p, P(c_longlong)]
+    lib.mehdg_phase_times.argtypes = [c_void_p, P(c_double), I]
+    lib.mehdg_launch_count.argtypes = [c_void_p, P(c_longlong)]
     lib.mehdg_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.restype = None
     lib.mehdg_last_error.argtypes = [c_void_p]
@@ -242,6 +244,20 @@ class Context:
         self._check(self.lib.mehdg_get_block(self.h, int(which), int(macro), out.ctypes.data_as(c_void_p), None),
                     "get_block")
         return out
+
+    PHASES = ["vol_point", "vol_contract", "faces", "condense", "lu", "face_lu", "bhat", "apply", "recover",
+              "precond"]
+
+    def phase_times(self):
+        """Device milliseconds of the last run of each internal phase (dict)."""
+        out = (c_double * 16)()
+        self._check(self.lib.mehdg_phase_times(self.h, out, 16), "phase_times")
+        return {k: out[i] for i, k in enumerate(self.PHASES)}
+
+    def launch_count(self):
+        n = c_longlong()
+        self._check(self.lib.mehdg_launch_count(self.h, ctypes.byref(n)), "launch_count")
+        return n.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -117,9 +117,11 @@ int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {
   if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply before mehdg_condense_factor");
   size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
   CK(cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  phase_begin(ctx, PH_APPLY);
   k_apply<<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Ahu, ctx->Auh, ctx->Ahh, ctx->gather, x,
                                               ctx->slot, ctx->Nu, ctx->Nt);
   CKL();
+  phase_end(ctx, PH_APPLY);
   return face_reduce(ctx, ctx->slot, y);
 }
 
@@ -127,10 +129,12 @@ int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "recover before mehdg_condense_factor");
   size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
   CK(cudaFuncSetAttribute(k_recover, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  phase_begin(ctx, PH_RECOVER);
   k_recover<<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Auh, ctx->gv, ctx->MinvRQ, ctx->Wk,
                                                 ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np,
                                                 ctx->Nth, ctx->ns, ctx->d);
   CKL();
+  phase_end(ctx, PH_RECOVER);
   return MEHDG_OK;
 }
 

@@ -540,17 +540,22 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   constexpr int NG = IPow<P + 2, D>::v;
   {
     long long tot = (long long)E * ctx->nel * NG * NS * (1 + D);
+    phase_begin(ctx, PH_VOL_POINT);
     k_vol_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, tt ? tt->hist : nullptr,
                                                           tt ? tt->coef : 0.0, tt ? tt->supg_time : 0, ctx->src,
                                                           ctx->Kvol, ctx->rvol, E);
     CKL();
+    phase_end(ctx, PH_VOL_POINT);
   }
   {
     typedef VolCfg<D, P> C;
     CK(cudaFuncSetAttribute(k_vol_contract<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     dim3 grid(E, D + 1, NS);
+    phase_begin(ctx, PH_VOL_CONTRACT);
     k_vol_contract<D, P><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, ctx->Kvol, ctx->Auu, ctx->Auq);
     CKL();
+    phase_end(ctx, PH_VOL_CONTRACT);
+    phase_begin(ctx, PH_FACES);
     k_vol_res<D, P><<<E, 128, 0, st>>>(g, ctx->tab, ctx->rvol, ctx->RU);
     CKL();
   }
@@ -569,6 +574,7 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
     long long tot = (long long)E * ctx->Nq;
     k_rq<<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->Mref, ctx->Gk, ctx->Ghk, ctx->gather, u, q, uh, ctx->RQ, E);
     CKL();
+    phase_end(ctx, PH_FACES);
   }
   return MEHDG_OK;
 }

@@ -212,6 +212,7 @@ int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
                                                      ctx->F);
     CKL();
   }
+  phase_begin(ctx, PH_CONDENSE);
   // M^-1 R_Q
   {
     long long nvec = (long long)E * d * ns;
@@ -275,11 +276,17 @@ int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
     a.C = ctx->Ahh; a.ldc = (int)Nt; a.sC1 = Nt * Nt; a.sC2 = Nth;
     if ((rc = gemm(ctx, a, E))) return rc;
   }
+  phase_end(ctx, PH_CONDENSE);
   // LU of S and of the face blocks
   CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
+  phase_begin(ctx, PH_LU);
   if ((rc = batched_lu(ctx, ctx->Auu, ctx->perm, (int)Nu, E, ctx->dflag))) return rc;
+  phase_end(ctx, PH_LU);
+  phase_begin(ctx, PH_FACE_LU);
   if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;
+  phase_end(ctx, PH_FACE_LU);
   // b^
+  phase_begin(ctx, PH_BHAT);
   {
     size_t smem = sizeof(double) * 2 * Nu;
     CK(cudaFuncSetAttribute(k_bhat_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -289,6 +296,7 @@ int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
   if (bhat) {
     if ((rc = face_reduce(ctx, ctx->bloc, bhat))) return rc;
   }
+  phase_end(ctx, PH_BHAT);
   int flags[4];
   CK(cudaMemcpyAsync(flags, ctx->dflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

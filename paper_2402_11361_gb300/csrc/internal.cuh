@@ -19,6 +19,7 @@
 
 #define CKL()                                                                           \
   do {                                                                                  \
+    ++ctx->launches;                                                                    \
     cudaError_t e_ = cudaGetLastError();                                                \
     if (e_ != cudaSuccess)                                                              \
       return ctx_fail(ctx, MEHDG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
@@ -98,7 +99,18 @@ struct mehdg_ctx {
   bool condensed = false;
   // MLP preconditioner correction (kind 2)
   void* mlp = nullptr;
+  // phase timers (CUDA events on the context stream)
+  cudaEvent_t ev[2 * 16] = {};
+  long long launches = 0;   // kernels launched by this context
+  bool ev_rec[16] = {};
 };
+
+enum Phase {
+  PH_VOL_POINT = 0, PH_VOL_CONTRACT = 1, PH_FACES = 2, PH_CONDENSE = 3, PH_LU = 4, PH_FACE_LU = 5,
+  PH_BHAT = 6, PH_APPLY = 7, PH_RECOVER = 8, PH_PRECOND = 9, PH_COUNT = 16
+};
+void phase_begin(mehdg_ctx* ctx, int p);
+void phase_end(mehdg_ctx* ctx, int p);
 
 int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg);
 

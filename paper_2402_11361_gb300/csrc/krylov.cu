@@ -189,8 +189,10 @@ int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b
 
 static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
   size_t smem = sizeof(double) * ctx->nfb;
+  phase_begin(ctx, PH_PRECOND);
   k_block_jacobi<<<ctx->F, 128, smem, ctx->stream>>>(ctx->fblk, ctx->fperm, r, z, ctx->nfb);
   CKL();
+  phase_end(ctx, PH_PRECOND);
   return MEHDG_OK;
 }
 

@@ -18,6 +18,37 @@ int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg) {
   return code;
 }
 
+void phase_begin(mehdg_ctx* ctx, int p) {
+  if (!ctx->ev[2 * p]) {
+    cudaEventCreate(&ctx->ev[2 * p]);
+    cudaEventCreate(&ctx->ev[2 * p + 1]);
+  }
+  cudaEventRecord(ctx->ev[2 * p], ctx->stream);
+}
+void phase_end(mehdg_ctx* ctx, int p) {
+  cudaEventRecord(ctx->ev[2 * p + 1], ctx->stream);
+  ctx->ev_rec[p] = true;
+}
+
+extern "C" int mehdg_launch_count(const mehdg_ctx* ctx, long long* count) {
+  if (!ctx || !count) return MEHDG_ERR_ARG;
+  *count = ctx->launches;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_phase_times(mehdg_ctx* ctx, double* ms, int n) {
+  if (!ctx || !ms || n < 0 || n > PH_COUNT) return MEHDG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int p = 0; p < n; ++p) {
+    ms[p] = -1.0;
+    if (!ctx->ev_rec[p]) continue;
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[2 * p], ctx->ev[2 * p + 1]));
+    ms[p] = t;
+  }
+  return MEHDG_OK;
+}
+
 Geo make_geo(const mehdg_ctx* c) {
   Geo g;
   g.d = c->d; g.ns = c->ns; g.m = c->m; g.p = c->p; g.n1 = c->n1; g.Np = c->Np; g.Nfn = c->Nfn;
@@ -729,6 +760,8 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
+  for (int i = 0; i < 2 * PH_COUNT; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
 }
 
