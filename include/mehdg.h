@@ -44,6 +44,7 @@ extern "C" {
 #define MEHDG_ERR_NOT_CONVERGED (-5)
 #define MEHDG_ERR_TIMEOUT (-6)
 #define MEHDG_ERR_NAN (-7)
+#define MEHDG_ERR_TOO_LARGE (-8)
 
 /* boundary kinds per domain side (-x, +x, -y, +y, -z, +z) */
 #define MEHDG_BC_NONE 0      /* periodic direction (or unused) */
@@ -182,6 +183,42 @@ int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q,
  * 15 pivots (as doubles), 16 bhat_local.  Returns the element count in *count. */
 int mehdg_get_block(mehdg_ctx* ctx, int which, int macro, double* host_out,
                     long long* count);
+
+/* Trace apply for callers that cannot allocate device memory.  No counterpart in
+ * the paper: it is the a7 apply (same kernels, same result as mehdg_apply_trace)
+ * with every array supplied by the caller and the one scratch array it needs
+ * (one result slot of Nt doubles per macro-element, summed per face afterwards)
+ * taken from a fixed array compiled into this library.
+ *
+ * Who needs it: code that runs inside a host application that owns all device
+ * memory through its own pool or arena and gives a solver plugin a fixed budget,
+ * and loops that must not call cudaMalloc, which can stall or implicitly
+ * synchronise the device.  This call allocates nothing: no cudaMalloc, no cudaFree,
+ * no allocating library routine.
+ *
+ * Arguments (device pointers unless stated): dim 2 or 3 (ns = dim + 2,
+ * Nth = 2 dim Nfn, Nt = ns Nth); n_macro, n_face, Nu = ns Np, Nfn as in mehdg_info;
+ * S_lu [n_macro][Nu][Nu] LU factors of S with unit lower L (row-major) and perm
+ * [n_macro][Nu] the row permutation (row i of P S is row perm[i] of S); B
+ * [n_macro][Nt][Nu], C [n_macro][Nu][Nt], D [n_macro][Nt][Nt]; gather [n_macro][Nt]
+ * global trace index of each local trace entry; owner [n_face][2] the touching
+ * (macro * 2 dim + local face) or -1; x, y global trace vectors (n_face ns Nfn),
+ * x != y; stream a cudaStream_t or NULL.  All in the layouts of this header.
+ *
+ * Limits and sharing: n_macro * Nt must not exceed 4194304 (2^22) doubles, the size
+ * of the fixed scratch array (32 MiB, held on every GPU that loads the library
+ * until the process exits); larger sizes return MEHDG_ERR_TOO_LARGE with a message
+ * on stderr.  Every call on a device uses the same array and leaves its contents
+ * behind; each call overwrites every entry it reads, so nothing has to start at
+ * zero.  Calls that overlap on the GPU (other streams, other threads) race on the
+ * array: order them on one stream.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress with that device current); make that
+ * first call before any stream capture begins.  Errors: ARG for invalid sizes or
+ * pointers, TOO_LARGE as above, CUDA for a failed lookup or launch. */
+int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
+                              const double* S_lu, const int* perm, const double* B,
+                              const double* C, const double* D, const int* gather,
+                              const int* owner, const double* x, double* y, void* stream);
 
 /* Device time in milliseconds of the most recent execution of each internal phase
  * (CUDA events on the context stream; -1 for phases not run since mehdg_mesh):

@@ -147,3 +147,74 @@ extern "C" int mehdg_recover(mehdg_ctx* ctx, const double* duh, double* du, doub
   if (!ctx || !duh || !du || !dq) return MEHDG_ERR_ARG;
   return recover_impl(ctx, duh, du, dq);
 }
+
+// ---------------------------------------------------------------- allocation-free trace apply
+// Same kernels as mehdg_apply_trace, but every array is the caller's and the per-macro
+// slot scratch lives in a file-scope device array instead of context memory.
+#include <cstdio>
+#include <mutex>
+
+static constexpr long long kNoallocSlotMax = 1LL << 22;   // doubles (32 MiB)
+static __device__ __align__(256) double g_noalloc_slot[kNoallocSlotMax];
+
+namespace {
+std::mutex g_noalloc_mtx;
+double* g_noalloc_ptr[128] = {};
+
+int noalloc_slot(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 128) {
+    fprintf(stderr, "mehdg_apply_trace_noalloc: no usable current device (%s)\n", cudaGetErrorString(e));
+    return MEHDG_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mtx);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_slot);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "mehdg_apply_trace_noalloc: cudaGetSymbolAddress failed (%s)\n", cudaGetErrorString(e));
+      return MEHDG_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return MEHDG_OK;
+}
+}  // namespace
+
+extern "C" int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn, const double* S_lu,
+                                         const int* perm, const double* B, const double* C, const double* D,
+                                         const int* gather, const int* owner, const double* x, double* y,
+                                         void* stream) {
+  if (dim < 2 || dim > 3 || n_macro < 1 || n_face < 1 || Nu < 1 || Nfn < 1 || !S_lu || !perm || !B || !C || !D ||
+      !gather || !owner || !x || !y || x == y)
+    return MEHDG_ERR_ARG;
+  const int ns = dim + 2;
+  const int Nth = 2 * dim * Nfn;
+  const int Nt = ns * Nth;
+  const long long need = (long long)n_macro * Nt;
+  if (need > kNoallocSlotMax) {
+    fprintf(stderr,
+            "mehdg_apply_trace_noalloc: n_macro * Nt = %lld doubles exceeds the static scratch of %lld doubles\n",
+            need, kNoallocSlotMax);
+    return MEHDG_ERR_TOO_LARGE;
+  }
+  const size_t smem = sizeof(double) * (Nt + 2 * (size_t)Nu);
+  if (smem > 227 * 1024) return MEHDG_ERR_ARG;
+  double* slot = nullptr;
+  int rc = noalloc_slot(&slot);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return MEHDG_ERR_CUDA;
+  k_apply<<<n_macro, 256, smem, st>>>(S_lu, perm, B, C, D, gather, x, slot, Nu, Nt);
+  const long long ntr = (long long)n_face * ns * Nfn;
+  k_face_reduce<<<(ntr + 255) / 256, 256, 0, st>>>(slot, owner, y, ns, Nfn, Nth, Nt, dim, ntr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "mehdg_apply_trace_noalloc: launch failed (%s)\n", cudaGetErrorString(e));
+    return MEHDG_ERR_CUDA;
+  }
+  return MEHDG_OK;
+}
