@@ -35,8 +35,11 @@ METRIC = "time per Newton/DIRK step & FGMRES iters at 1e-8 residual; batched loc
 UNIT = "s/Newton step"
 
 
+NMAC = 8
+
+
 def workload():
-    return W.mms(dim=3, nmac=8, m=2, p=2)
+    return W.mms(dim=3, nmac=NMAC, m=2, p=2)
 
 
 def sizes(pr):
@@ -166,7 +169,7 @@ def run_ours(args, ws, rank, lrank):
     dtau = tau_init
     t_solve0 = time.perf_counter()
     its_total = 0
-    while norms[3] > 1e-8 * R0 and len(records) < 60:
+    while norms[3] > 1e-8 * R0 and len(records) < args.solve_steps:
         records.append((u.clone(), q.clone(), uh.clone(), dtau, norms.copy()))
         bhat = ctx.condense(shift=1.0 / dtau)
         duh_s, stats = ctx.linear_solve(bhat, allow_not_converged=True)
@@ -301,8 +304,8 @@ def run_ours(args, ws, rank, lrank):
         "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32/tf32 blocks, f64 residual+krylov",
         "data": "synthetic (manufactured solution, seeded 1e-3 perturbation, seed 0)",
-        "config": {"workload": "3D steady MMS cube, 8^3 macro-elements x 2^3 hexes, p=2 (%d macros, Nu=%d, Nt=%d, "
-                               "%d trace DOFs)" % (z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
+        "config": {"workload": "3D steady MMS cube, %d^3 macro-elements x 2^3 hexes, p=2 (%d macros, Nu=%d, Nt=%d, "
+                               "%d trace DOFs)" % (NMAC, z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
                    "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "fgmres_iters_per_step": its_timed / args.steps,
@@ -375,8 +378,12 @@ def main():
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--lin-rtol", type=float, default=1e-3)
     ap.add_argument("--no-phases", dest="phases", action="store_false")
+    ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
+    ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args()
+    global NMAC
+    NMAC = args.nmac
     ws, rank, lrank = dist_env()
     if args.impl == "reference":
         if rank == 0:
