@@ -130,14 +130,22 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def phase_work(z, E, precision):
-    """Algorithmic FLOPs (and bytes for the apply) per launch of the main phases."""
+def phase_work(z, E, precision, apply_mode=0):
+    """Algorithmic FLOPs (and bytes for the apply) per launch of the main phases.
+
+    Apply bytes per macro-element: the stored operators read once (Algorithm 2: C, S
+    factors, B, D; apply_mode 1: the local operator A^T_i), plus the gathered input
+    (8 B), the slot written (8 B) and the gather indices (4 B) per trace entry."""
     Nu, Nt, Np, Nth, d, ns = z["Nu"], z["Nt"], z["Np"], z["Nth"], z["d"], z["ns"]
     w = 8 if precision == "fp64" else 4
     cond = 2.0 * d * ns * (Nu * Np * Np + Nu * Np * Nth + Nt * Np * Np + Nt * Np * Nth) * E
     lu = (2.0 / 3.0) * Nu ** 3 * E
-    apply_bytes = (w * (2 * Nu * Nt + Nt * Nt + Nu * Nu) + 8 * 2 * Nt + 4 * (Nu + Nt)) * E
-    apply_flops = 2.0 * (2 * Nu * Nt + Nt * Nt + Nu * Nu) * E
+    if apply_mode == 1:
+        apply_bytes = (w * Nt * Nt + (8 + 8 + 4) * Nt) * E
+        apply_flops = 2.0 * Nt * Nt * E
+    else:
+        apply_bytes = (w * (2 * Nu * Nt + Nt * Nt + Nu * Nu) + (8 + 8 + 4) * Nt + 4 * Nu) * E
+        apply_flops = 2.0 * (2 * Nu * Nt + Nt * Nt + Nu * Nu) * E
     return dict(condense_flops=cond, lu_flops=lu, apply_bytes=apply_bytes, apply_flops=apply_flops)
 
 
@@ -152,8 +160,9 @@ def run_ours(args, ws, rank, lrank):
     pr = workload()
     z = sizes(pr)
     prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
-    opts = dict(precision=prec, precond=args.precond, restart=30, max_iters=3000, lin_rtol=args.lin_rtol,
-                newton_rtol=1e-8, max_newton=60)
+    opts = dict(precision=prec, precond=args.precond, restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol,
+                newton_rtol=1e-8, max_newton=60, inner_iters=args.inner, apply_mode=args.apply_mode,
+                tc_mode=args.tc_mode)
     ctx = pkg.Context(pr, opts, device=dev)
     du, duh = W.perturbation(pr, 0)
     du_d = torch.as_tensor(du, device=dev)
@@ -210,6 +219,8 @@ def run_ours(args, ws, rank, lrank):
     for k in range(max(0, args.warmup - N)):
         replay(k)
     torch.cuda.synchronize()
+    if args.steps < 0:
+        args.steps = N
 
     # ---- timed region (device-resident inputs)
     if ws > 1:
@@ -257,24 +268,27 @@ def run_ours(args, ws, rank, lrank):
     bytes_io = 8 * (u.numel() + q.numel() + uh.numel())
 
     # ---- roofline of the dominant kernel: phase with the largest time per step
-    work = phase_work(z, z["E"], args.precision)
+    work = phase_work(z, z["E"], args.precision, args.apply_mode)
     ph_mean = {k: float(np.mean(v)) for k, v in phase_acc.items() if v and v[0] >= 0}
     peaks = measured_peaks()
     fp64_peak = None
     roof = None
     if ph_mean:
-        dom = max(("condense", "lu", "vol_contract", "vol_point", "apply"), key=lambda k: ph_mean.get(k, 0.0) *
-                  (its_timed / args.steps if k == "apply" else 1.0))
+        applies = its_timed / args.steps * (1 + (args.inner if args.precond == 1 else 0))
+        dom = max(("condense", "lu", "vol_contract", "vol_point", "apply", "form_local"),
+                  key=lambda k: ph_mean.get(k, 0.0) * (applies if k == "apply" else 1.0))
         if args.precision == "fp64" or dom not in ("condense", "lu"):
             fp64_peak = fp64_peak_tflops(torch)
         if dom == "apply":
             ach = work["apply_bytes"] / (ph_mean["apply"] / 1e3) / 1e9
             pk = peaks.get("hbm_gbs", 6800.0)
-            roof = dict(kernel="k_apply (Algorithm 2, one launch = all macro-elements)", bound="hbm",
+            roof = dict(kernel=("k_apply_explicit (A^T_i x, " if args.apply_mode == 1 else "k_apply (Algorithm 2, ")
+                        + "one launch = all macro-elements)", bound="hbm",
                         achieved=ach, peak=pk, unit="GB/s", frac=ach / pk, traffic=None,
                         peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback")
         else:
-            fl = {"condense": work["condense_flops"], "lu": work["lu_flops"]}.get(dom)
+            fl = {"condense": work["condense_flops"], "lu": work["lu_flops"],
+                  "form_local": 2.0 * z["Nu"] ** 2 * z["Nt"] * z["E"] + 2.0 * z["Nt"] ** 2 * z["Nu"] * z["E"]}.get(dom)
             if fl is None:
                 fl = 0.0
             ach = fl / (ph_mean[dom] / 1e3) / 1e12
@@ -307,6 +321,8 @@ def run_ours(args, ws, rank, lrank):
         "config": {"workload": "3D steady MMS cube, %d^3 macro-elements x 2^3 hexes, p=2 (%d macros, Nu=%d, Nt=%d, "
                                "%d trace DOFs)" % (NMAC, z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
                    "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
+                   "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
+                   "tc_mode": args.tc_mode,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "fgmres_iters_per_step": its_timed / args.steps,
         "solve": {"newton_steps": N, "fgmres_iters": its_total, "converged_1e-8": converged,
@@ -377,6 +393,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--lin-rtol", type=float, default=1e-3)
+    ap.add_argument("--restart", type=int, default=60)
+    ap.add_argument("--inner", type=int, default=10, help="inner GMRES iterations of the multi-level preconditioner")
+    ap.add_argument("--apply-mode", type=int, default=1, help="0: Algorithm 2 four-step apply; 1: stored A^T_i")
+    ap.add_argument("--tc-mode", type=int, default=0, help="mixed local GEMMs: 0 FP32 SIMT, 1 split TF32, 2 TF32")
     ap.add_argument("--no-phases", dest="phases", action="store_false")
     ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
     ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
@@ -394,7 +414,7 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     if args.steps == 0:
-        args.steps = 6
+        args.steps = -1       # one replay of every recorded Newton step
     line = run_ours(args, ws, rank, lrank)
     if rank == 0:
         if args.cpu:

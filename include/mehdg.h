@@ -88,6 +88,12 @@ typedef struct mehdg_options {
   int max_newton;
   double tau_init, tau_max; /* pseudo-time SER parameters (eq. C31222) */
   int refine_iters;   /* FP64 refinement sweeps of each local S solve (mixed precision) */
+  int apply_mode;     /* 0: Algorithm 2 (C, S^-1, B, D per apply); 1: the local operator
+                         A^T_i = B S^-1 C + D is formed once after factorisation (it
+                         replaces D in place) and each apply is one product per macro */
+  int tc_mode;        /* mixed precision local GEMMs (condensation products, forming A^T_i):
+                         0 FP32 SIMT, 1 tcgen05 tensor cores with split TF32 (3 products,
+                         about FP32 accuracy), 2 tcgen05 with plain TF32 */
 } mehdg_options;
 
 typedef struct mehdg_info {
@@ -220,11 +226,26 @@ int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
                               const double* C, const double* D, const int* gather,
                               const int* owner, const double* x, double* y, void* stream);
 
+/* Batched dense product on the tcgen05 tensor cores (TF32 inputs, FP32 accumulation),
+ * the kernel used by the mixed-precision path for its local GEMMs (forming A^T_i,
+ * condensation products):  C_b = alpha A_b B_b + beta C_b for b < batch, with
+ * A_b = A + b sA [M x K], B_b = B + b sB [K x N], C_b = C + b sC [M x N], all
+ * row-major FP32 device arrays with the given leading dimensions (no alignment
+ * requirement).  split != 0: each operand is split into a TF32 part and a TF32
+ * remainder and three products are accumulated (close to FP32 accuracy, three
+ * times the tensor work).  err: device int set to 1 if an internal wait timed out
+ * (the result is then invalid).  Asynchronous on stream.  Errors: ARG, CUDA. */
+int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long lda, long long sA,
+                       const float* B, long long ldb, long long sB, float* C, long long ldc,
+                       long long sC, float alpha, float beta, int batch, int split, int* err,
+                       void* stream);
+
 /* Device time in milliseconds of the most recent execution of each internal phase
  * (CUDA events on the context stream; -1 for phases not run since mehdg_mesh):
  * 0 volume pointwise Jacobians, 1 volume contraction, 2 faces + R_Q, 3 condensation
  * products, 4 batched LU of S, 5 LU of the face blocks, 6 condensed rhs, 7 trace
- * apply kernel, 8 recovery, 9 block-Jacobi.  ms: host double[n], n <= 16.
+ * apply kernel, 8 recovery, 9 block-Jacobi, 10 forming A^T_i (apply_mode 1).
+ * ms: host double[n], n <= 16.
  * Synchronises the stream. */
 int mehdg_phase_times(mehdg_ctx* ctx, double* ms, int n);
 

@@ -9,39 +9,73 @@
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_apply(const double* __restrict__ S, const int* __restrict__ perm,
-                                               const double* __restrict__ B, const double* __restrict__ C,
-                                               const double* __restrict__ D, const int* __restrict__ gather,
+// Dot product of a global row with a shared-memory vector by one warp: four
+// independent partial sums keep four loads per lane in flight.
+template <class T, class A>
+__device__ __forceinline__ A warp_dot(const T* __restrict__ row, const A* x, int n, int lane) {
+  A s0 = A(0), s1 = A(0), s2 = A(0), s3 = A(0);
+  int c = lane;
+  for (; c + 96 < n; c += 128) {
+    s0 += (A)row[c] * x[c];
+    s1 += (A)row[c + 32] * x[c + 32];
+    s2 += (A)row[c + 64] * x[c + 64];
+    s3 += (A)row[c + 96] * x[c + 96];
+  }
+  for (; c < n; c += 32) s0 += (A)row[c] * x[c];
+  A s = (s0 + s1) + (s2 + s3);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// T: block storage type; A: arithmetic type of the local products and solves
+// (double for the FP64 path, float for the FP32-block path).
+template <class T, class A>
+__global__ void __launch_bounds__(512) k_apply(const T* __restrict__ S, const int* __restrict__ perm,
+                                               const T* __restrict__ B, const T* __restrict__ C,
+                                               const T* __restrict__ D, const int* __restrict__ gather,
                                                const double* __restrict__ x, double* __restrict__ slot, int Nu,
                                                int Nt) {
-  extern __shared__ double sm[];
-  double* xg = sm;            // Nt
-  double* y1 = xg + Nt;       // Nu
-  double* y2 = y1 + Nu;       // Nu
+  extern __shared__ unsigned char sm_raw[];
+  A* xg = reinterpret_cast<A*>(sm_raw);  // Nt
+  A* y1 = xg + Nt;                        // Nu
+  A* y2 = y1 + Nu;                        // Nu
   const int e = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = x[gather[(size_t)e * Nt + i]];
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (A)x[gather[(size_t)e * Nt + i]];
   __syncthreads();
-  const double* Ce = C + (size_t)e * Nu * Nt;
+  const T* Ce = C + (size_t)e * Nu * Nt;
   for (int r = w; r < Nu; r += nw) {
-    double s = 0.0;
-    for (int c = lane; c < Nt; c += 32) s += Ce[(size_t)r * Nt + c] * xg[c];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    A s = warp_dot<T, A>(Ce + (size_t)r * Nt, xg, Nt, lane);
     if (lane == 0) y1[r] = s;
   }
   __syncthreads();
   const int* pe = perm + (size_t)e * Nu;
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) y2[i] = y1[pe[i]];
   __syncthreads();
-  lu_solve_block<double>(S + (size_t)e * Nu * Nu, Nu, y2);
-  const double* Be = B + (size_t)e * Nt * Nu;
-  const double* De = D + (size_t)e * Nt * Nt;
+  lu_solve_block<T, A>(S + (size_t)e * Nu * Nu, Nu, y2);
+  const T* Be = B + (size_t)e * Nt * Nu;
+  const T* De = D + (size_t)e * Nt * Nt;
   for (int r = w; r < Nt; r += nw) {
-    double s = 0.0;
-    for (int c = lane; c < Nu; c += 32) s += Be[(size_t)r * Nu + c] * y2[c];
-    for (int c = lane; c < Nt; c += 32) s += De[(size_t)r * Nt + c] * xg[c];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) slot[(size_t)e * Nt + r] = s;
+    A s = warp_dot<T, A>(Be + (size_t)r * Nu, y2, Nu, lane) + warp_dot<T, A>(De + (size_t)r * Nt, xg, Nt, lane);
+    if (lane == 0) slot[(size_t)e * Nt + r] = (double)s;
+  }
+}
+
+// apply_mode 1: y4 = A^T_i x on dT_i with the stored local operator; grid (macro, row block)
+template <class T, class A>
+__global__ void __launch_bounds__(256) k_apply_explicit(const T* __restrict__ Ahat, const int* __restrict__ gather,
+                                                        const double* __restrict__ x, double* __restrict__ slot,
+                                                        int Nt, int rows) {
+  extern __shared__ unsigned char sm_raw[];
+  A* xg = reinterpret_cast<A*>(sm_raw);
+  const int e = blockIdx.x, r0 = blockIdx.y * rows;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (A)x[gather[(size_t)e * Nt + i]];
+  __syncthreads();
+  const int r1 = min(r0 + rows, Nt);
+  for (int r = r0 + w; r < r1; r += nw) {
+    A s = warp_dot<T, A>(Ahat + ((size_t)e * Nt + r) * Nt, xg, Nt, lane);
+    if (lane == 0) slot[(size_t)e * Nt + r] = (double)s;
   }
 }
 
@@ -64,8 +98,9 @@ __global__ void k_face_reduce(const double* __restrict__ slot, const int* __rest
 }
 
 // du = S^-1 (g + C duh_i);  dq[k][s] = -M^-1 R_Q[k][s] - W_k du_s - Wh_k duh_i,s
-__global__ void __launch_bounds__(256) k_recover(const double* __restrict__ S, const int* __restrict__ perm,
-                                                 const double* __restrict__ C, const double* __restrict__ gvec,
+template <class T>
+__global__ void __launch_bounds__(256) k_recover(const T* __restrict__ S, const int* __restrict__ perm,
+                                                 const T* __restrict__ C, const double* __restrict__ gvec,
                                                  const double* __restrict__ MinvRQ, const double* __restrict__ Wk,
                                                  const double* __restrict__ Whk, const int* __restrict__ gather,
                                                  const double* __restrict__ duh, double* __restrict__ du,
@@ -79,10 +114,10 @@ __global__ void __launch_bounds__(256) k_recover(const double* __restrict__ S, c
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = duh[gather[(size_t)e * Nt + i]];
   __syncthreads();
-  const double* Ce = C + (size_t)e * Nu * Nt;
+  const T* Ce = C + (size_t)e * Nu * Nt;
   for (int r = w; r < Nu; r += nw) {
     double s = 0.0;
-    for (int c = lane; c < Nt; c += 32) s += Ce[(size_t)r * Nt + c] * xg[c];
+    for (int c = lane; c < Nt; c += 32) s += (double)Ce[(size_t)r * Nt + c] * xg[c];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y1[r] = s + gvec[(size_t)e * Nu + r];
   }
@@ -90,7 +125,7 @@ __global__ void __launch_bounds__(256) k_recover(const double* __restrict__ S, c
   const int* pe = perm + (size_t)e * Nu;
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) y2[i] = y1[pe[i]];
   __syncthreads();
-  lu_solve_block<double>(S + (size_t)e * Nu * Nu, Nu, y2);
+  lu_solve_block<T, double>(S + (size_t)e * Nu * Nu, Nu, y2);
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) du[(size_t)e * Nu + i] = y2[i];
   const int nq = d * ns * Np;
   for (int i = threadIdx.x; i < nq; i += blockDim.x) {
@@ -113,24 +148,52 @@ int face_reduce(mehdg_ctx* ctx, const double* slot, double* y) {
   return MEHDG_OK;
 }
 
-int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {
-  if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply before mehdg_condense_factor");
-  size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
-  CK(cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <class T, class A>
+static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
+  if (ctx->opt.apply_mode == 1) {
+    const int rows = 64;
+    dim3 grid(ctx->E, (ctx->Nt + rows - 1) / rows);
+    phase_begin(ctx, PH_APPLY);
+    k_apply_explicit<T, A><<<grid, 256, sizeof(A) * ctx->Nt, ctx->stream>>>(
+        reinterpret_cast<const T*>(ctx->Ahh), ctx->gather, x, ctx->slot, ctx->Nt, rows);
+    CKL();
+    phase_end(ctx, PH_APPLY);
+    return face_reduce(ctx, ctx->slot, y);
+  }
+  size_t smem = sizeof(A) * (ctx->Nt + 2 * (size_t)ctx->Nu);
+  CK(cudaFuncSetAttribute(k_apply<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   phase_begin(ctx, PH_APPLY);
-  k_apply<<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Ahu, ctx->Auh, ctx->Ahh, ctx->gather, x,
-                                              ctx->slot, ctx->Nu, ctx->Nt);
+  k_apply<T, A><<<ctx->E, 512, smem, ctx->stream>>>(
+      reinterpret_cast<const T*>(ctx->Auu), ctx->perm, reinterpret_cast<const T*>(ctx->Ahu),
+      reinterpret_cast<const T*>(ctx->Auh), reinterpret_cast<const T*>(ctx->Ahh), ctx->gather, x, ctx->slot, ctx->Nu,
+      ctx->Nt);
   CKL();
   phase_end(ctx, PH_APPLY);
   return face_reduce(ctx, ctx->slot, y);
 }
 
+int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {
+  if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply before mehdg_condense_factor");
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) return apply_t<float, float>(ctx, x, y);
+  return apply_t<double, double>(ctx, x, y);
+}
+
 int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "recover before mehdg_condense_factor");
   size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
-  CK(cudaFuncSetAttribute(k_recover, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   phase_begin(ctx, PH_RECOVER);
-  k_recover<<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Auh, ctx->gv, ctx->MinvRQ, ctx->Wk,
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) {
+    CK(cudaFuncSetAttribute(k_recover<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_recover<float><<<ctx->E, 256, smem, ctx->stream>>>(
+        reinterpret_cast<const float*>(ctx->Auu), ctx->perm, reinterpret_cast<const float*>(ctx->Auh), ctx->gv,
+        ctx->MinvRQ, ctx->Wk, ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np, ctx->Nth, ctx->ns,
+        ctx->d);
+    CKL();
+    phase_end(ctx, PH_RECOVER);
+    return MEHDG_OK;
+  }
+  CK(cudaFuncSetAttribute(k_recover<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_recover<double><<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Auh, ctx->gv, ctx->MinvRQ, ctx->Wk,
                                                 ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np,
                                                 ctx->Nth, ctx->ns, ctx->d);
   CKL();
@@ -206,9 +269,10 @@ extern "C" int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int N
   int rc = noalloc_slot(&slot);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_apply<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
     return MEHDG_ERR_CUDA;
-  k_apply<<<n_macro, 256, smem, st>>>(S_lu, perm, B, C, D, gather, x, slot, Nu, Nt);
+  k_apply<double, double><<<n_macro, 512, smem, st>>>(S_lu, perm, B, C, D, gather, x, slot, Nu, Nt);
   const long long ntr = (long long)n_face * ns * Nfn;
   k_face_reduce<<<(ntr + 255) / 256, 256, 0, st>>>(slot, owner, y, ns, Nfn, Nth, Nt, dim, ntr);
   cudaError_t e = cudaGetLastError();

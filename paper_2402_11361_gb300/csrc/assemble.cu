@@ -35,11 +35,11 @@ __device__ __forceinline__ Tables tables(const double* tab, int ng1, int p1) {
 }
 
 // ---------------------------------------------------------------- volume pointwise
-template <int D, int P>
+template <int D, int P, class KT>
 __global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restrict__ tab, Phys ph,
                                                     const double* __restrict__ u, const double* __restrict__ q,
                                                     const double* __restrict__ hist, double coef, int supg_time,
-                                                    const double* __restrict__ src, double* __restrict__ Kvol,
+                                                    const double* __restrict__ src, KT* __restrict__ Kvol,
                                                     double* __restrict__ rvol, int E) {
   constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
@@ -126,18 +126,18 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restri
   vol_integrand<D, S>(Us, GUs, Qs, GQs, Ts, f, ph, supg_time, W, V, FG, A, tau);
 
   for (int t = 0; t < NS; ++t) {
-    double* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
-    K[(0 * NS + s0) * (D + 1) + 0] = W[t].d[0] * wq;
-    for (int l = 0; l < D; ++l) K[(0 * NS + s0) * (D + 1) + 1 + l] = 0.0;
+    KT* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
+    K[(0 * NS + s0) * (D + 1) + 0] = (KT)(W[t].d[0] * wq);
+    for (int l = 0; l < D; ++l) K[(0 * NS + s0) * (D + 1) + 1 + l] = (KT)0;
     for (int k = 0; k < D; ++k) {
-      K[((1 + k) * NS + s0) * (D + 1) + 0] = V[t][k].d[0] * wq;
+      K[((1 + k) * NS + s0) * (D + 1) + 0] = (KT)(V[t][k].d[0] * wq);
       for (int l = 0; l < D; ++l) {
         double val = 0.0;
         if (ph.supg) {
           for (int rr = 0; rr < NS; ++rr) val += A[k][rr][t].v * FG[rr][l].d[0];
           val *= tau.v;
         }
-        K[((1 + k) * NS + s0) * (D + 1) + 1 + l] = val * wq;
+        K[((1 + k) * NS + s0) * (D + 1) + 1 + l] = (KT)(val * wq);
       }
     }
     if (dir == 0) {
@@ -149,18 +149,18 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restri
 }
 
 // basis value T[g][alpha][a] of a sub-element from 1D tables (alpha 0: value, 1+k: d/dx_k)
-template <int D, int P>
-__device__ __forceinline__ double basis_T(const double* sb, const double* sdb, const double* sc, const int* gi,
-                                          const int* ai, int alpha) {
+template <int D, int P, class CT = double>
+__device__ __forceinline__ CT basis_T(const CT* sb, const CT* sdb, const CT* sc, const int* gi, const int* ai,
+                                      int alpha) {
   constexpr int P1 = P + 1;
-  double v = 1.0;
+  CT v = CT(1);
 #pragma unroll
   for (int k = 0; k < D; ++k)
     v *= (alpha == 1 + k) ? sdb[gi[k] * P1 + ai[k]] * sc[k] : sb[gi[k] * P1 + ai[k]];
   return v;
 }
 
-template <int D, int P> struct VolCfg {
+template <int D, int P, class CT = double> struct VolCfg {
   static constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   static constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
   static constexpr int KA = (D + 1) * NS * (D + 1);
@@ -169,33 +169,32 @@ template <int D, int P> struct VolCfg {
   static constexpr int NT = (NLOC * NS * NLOC > 8192) ? 512 : (NLOC * NS * NLOC > 1024 ? 256 : 128);
   static constexpr int NOUT = NLOC * NS * NLOC;
   static constexpr int OPT = (NOUT + NT - 1) / NT;
-  static constexpr size_t SMEM = sizeof(double) * ((size_t)GC * KA + (size_t)GC * ZG + 2 * NG1 * P1);
+  static constexpr size_t SMEM = sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + 2 * NG1 * P1);
 };
 
 // A_X[(t, A)][(s, B)] += sum_g sum_{alpha,beta} T[g][alpha][a] K[g][alpha][s][beta] T[g][beta][b]
-template <int D, int P>
-__global__ void __launch_bounds__(VolCfg<D, P>::NT) k_vol_contract(Geo g, const double* __restrict__ tab,
-                                                                  const double* __restrict__ Kvol,
-                                                                  double* __restrict__ Auu,
-                                                                  double* __restrict__ Auq) {
-  typedef VolCfg<D, P> C;
+template <int D, int P, class CT>
+__global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, const double* __restrict__ tab,
+                                                                      const CT* __restrict__ Kvol,
+                                                                      CT* __restrict__ Auu, CT* __restrict__ Auq) {
+  typedef VolCfg<D, P, CT> C;
   constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, ZG = C::ZG;
   constexpr int GC = C::GC, NT = C::NT, OPT = C::OPT, NOUT = C::NOUT;
-  extern __shared__ double smem[];
-  double* sK = smem;
-  double* sZ = sK + GC * KA;
-  double* sb = sZ + GC * ZG;
-  double* sdb = sb + NG1 * P1;
+  extern __shared__ unsigned char smem_raw[];
+  CT* sK = reinterpret_cast<CT*>(smem_raw);
+  CT* sZ = sK + GC * KA;
+  CT* sb = sZ + GC * ZG;
+  CT* sdb = sb + NG1 * P1;
   const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z;
   const int tid = threadIdx.x;
   for (int i = tid; i < NG1 * P1; i += NT) {
-    sb[i] = tab[i];
-    sdb[i] = tab[NG1 * P1 + i];
+    sb[i] = (CT)tab[i];
+    sdb[i] = (CT)tab[NG1 * P1 + i];
   }
-  double sc[D];
-  for (int k = 0; k < D; ++k) sc[k] = 2.0 / g.he[k];
+  CT sc[D];
+  for (int k = 0; k < D; ++k) sc[k] = (CT)(2.0 / g.he[k]);
   const size_t Nu = g.Nu, Np = g.Np;
-  double* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
+  CT* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
   // per-thread output coordinates
   int oa[OPT], os[OPT], ob[OPT];
   for (int o = 0; o < OPT; ++o) {
@@ -212,9 +211,9 @@ __global__ void __launch_bounds__(VolCfg<D, P>::NT) k_vol_contract(Geo g, const 
       int ll = el;
       for (int k = 0; k < D; ++k) { li[k] = ll % g.m; ll /= g.m; }
     }
-    double acc[OPT];
-    for (int o = 0; o < OPT; ++o) acc[o] = 0.0;
-    const double* Kel = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * g.nel + el) * (size_t)NG * KA;
+    CT acc[OPT];
+    for (int o = 0; o < OPT; ++o) acc[o] = CT(0);
+    const CT* Kel = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * g.nel + el) * (size_t)NG * KA;
     for (int g0 = 0; g0 < NG; g0 += GC) {
       const int gc = min(GC, NG - g0);
       for (int i = tid; i < gc * KA; i += NT) sK[i] = Kel[(size_t)g0 * KA + i];
@@ -227,10 +226,10 @@ __global__ void __launch_bounds__(VolCfg<D, P>::NT) k_vol_contract(Geo g, const 
         int gi[D], bi[D];
         int t1 = g0 + gg, t2 = b;
         for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; bi[k] = t2 % P1; t2 /= P1; }
-        const double* Kp = sK + gg * KA + (al * NS + s) * (D + 1);
-        double z = 0.0;
+        const CT* Kp = sK + gg * KA + (al * NS + s) * (D + 1);
+        CT z = CT(0);
 #pragma unroll
-        for (int be = 0; be <= D; ++be) z += Kp[be] * basis_T<D, P>(sb, sdb, sc, gi, bi, be);
+        for (int be = 0; be <= D; ++be) z += Kp[be] * basis_T<D, P, CT>(sb, sdb, sc, gi, bi, be);
         sZ[idx] = z;
       }
       __syncthreads();
@@ -238,14 +237,14 @@ __global__ void __launch_bounds__(VolCfg<D, P>::NT) k_vol_contract(Geo g, const 
         int ai[D];
         int t2 = oa[o];
         for (int k = 0; k < D; ++k) { ai[k] = t2 % P1; t2 /= P1; }
-        double sum = 0.0;
+        CT sum = CT(0);
         for (int gg = 0; gg < gc; ++gg) {
           int gi[D];
           int t1 = g0 + gg;
           for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; }
 #pragma unroll
           for (int al = 0; al <= D; ++al)
-            sum += basis_T<D, P>(sb, sdb, sc, gi, ai, al) * sZ[gg * ZG + (al * NS + os[o]) * NLOC + ob[o]];
+            sum += basis_T<D, P, CT>(sb, sdb, sc, gi, ai, al) * sZ[gg * ZG + (al * NS + os[o]) * NLOC + ob[o]];
         }
         acc[o] += sum;
       }
@@ -409,12 +408,12 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const double* __restr
   }
 }
 
-template <int D, int P>
+template <int D, int P, class BT>
 __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __restrict__ tab,
                                                         const int* __restrict__ fnode,
                                                         const double* __restrict__ Kface,
-                                                        const double* __restrict__ rface, double* Auu, double* Auq,
-                                                        double* Auh, double* Ahu, double* Ahq, double* Ahh,
+                                                        const double* __restrict__ rface, BT* Auu, BT* Auq,
+                                                        BT* Auh, BT* Ahu, BT* Ahq, BT* Ahh,
                                                         double* RU, double* RUh) {
   constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   constexpr int NFS = IPow<P1, D - 1>::v, NFP = IPow<NG1, D - 1>::v;
@@ -473,14 +472,14 @@ __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __re
         else { kind = 2; s = dir - NS - NS * D; }
         if (et == 0) {   // numerical flux tested with phi (u rows)
           size_t row = (size_t)t * Np + ai;
-          if (kind == 0) Auh[(size_t)e * Nu * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += sum;
-          else if (kind == 1) Auq[((size_t)e * D + jd) * Nu * Nu + row * Nu + (size_t)s * Np + aj] += sum;
-          else Auu[(size_t)e * Nu * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+          if (kind == 0) Auh[(size_t)e * Nu * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += (BT)sum;
+          else if (kind == 1) Auq[((size_t)e * D + jd) * Nu * Nu + row * Nu + (size_t)s * Np + aj] += (BT)sum;
+          else Auu[(size_t)e * Nu * Nu + row * Nu + (size_t)s * Np + aj] += (BT)sum;
         } else {         // trace equation tested with psi (uhat rows)
           size_t row = (size_t)t * Nth + fl * Nfn + ji;
-          if (kind == 0) Ahh[(size_t)e * Nt * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += sum;
-          else if (kind == 1) Ahq[((size_t)e * D + jd) * Nt * Nu + row * Nu + (size_t)s * Np + aj] += sum;
-          else Ahu[(size_t)e * Nt * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+          if (kind == 0) Ahh[(size_t)e * Nt * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += (BT)sum;
+          else if (kind == 1) Ahq[((size_t)e * D + jd) * Nt * Nu + row * Nu + (size_t)s * Np + aj] += (BT)sum;
+          else Ahu[(size_t)e * Nt * Nu + row * Nu + (size_t)s * Np + aj] += (BT)sum;
         }
       }
       for (int oi = tid; oi < 2 * NS * NFS; oi += blockDim.x) {
@@ -521,19 +520,26 @@ __global__ void k_rq(Geo g, const double* __restrict__ M, const double* __restri
   RQ[tid] = acc;
 }
 
-template <int D, int P>
+template <int D, int P, class BT>
 int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt) {
   Geo g = make_geo(ctx);
   cudaStream_t st = ctx->stream;
   const int E = ctx->E;
   const size_t Nu = ctx->Nu, Nt = ctx->Nt;
   Phys ph{ctx->prob.gamma, ctx->prob.Re, ctx->prob.Pr, ctx->prob.supg, ctx->h_supg, ctx->p};
-  CK(cudaMemsetAsync(ctx->Auu, 0, sizeof(double) * E * Nu * Nu, st));
-  CK(cudaMemsetAsync(ctx->Auq, 0, sizeof(double) * E * D * Nu * Nu, st));
-  CK(cudaMemsetAsync(ctx->Auh, 0, sizeof(double) * E * Nu * Nt, st));
-  CK(cudaMemsetAsync(ctx->Ahu, 0, sizeof(double) * E * Nt * Nu, st));
-  CK(cudaMemsetAsync(ctx->Ahq, 0, sizeof(double) * E * D * Nt * Nu, st));
-  CK(cudaMemsetAsync(ctx->Ahh, 0, sizeof(double) * E * Nt * Nt, st));
+  BT* Auu = reinterpret_cast<BT*>(ctx->Auu);
+  BT* Auq = reinterpret_cast<BT*>(ctx->Auq);
+  BT* Auh = reinterpret_cast<BT*>(ctx->Auh);
+  BT* Ahu = reinterpret_cast<BT*>(ctx->Ahu);
+  BT* Ahq = reinterpret_cast<BT*>(ctx->Ahq);
+  BT* Ahh = reinterpret_cast<BT*>(ctx->Ahh);
+  BT* Kvol = reinterpret_cast<BT*>(ctx->Kvol);
+  CK(cudaMemsetAsync(Auu, 0, sizeof(BT) * E * Nu * Nu, st));
+  CK(cudaMemsetAsync(Auq, 0, sizeof(BT) * E * D * Nu * Nu, st));
+  CK(cudaMemsetAsync(Auh, 0, sizeof(BT) * E * Nu * Nt, st));
+  CK(cudaMemsetAsync(Ahu, 0, sizeof(BT) * E * Nt * Nu, st));
+  CK(cudaMemsetAsync(Ahq, 0, sizeof(BT) * E * D * Nt * Nu, st));
+  CK(cudaMemsetAsync(Ahh, 0, sizeof(BT) * E * Nt * Nt, st));
   CK(cudaMemsetAsync(ctx->RU, 0, sizeof(double) * E * Nu, st));
   CK(cudaMemsetAsync(ctx->RUh, 0, sizeof(double) * E * Nt, st));
   constexpr int NS = D + 2;
@@ -541,18 +547,18 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   {
     long long tot = (long long)E * ctx->nel * NG * NS * (1 + D);
     phase_begin(ctx, PH_VOL_POINT);
-    k_vol_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, tt ? tt->hist : nullptr,
-                                                          tt ? tt->coef : 0.0, tt ? tt->supg_time : 0, ctx->src,
-                                                          ctx->Kvol, ctx->rvol, E);
+    k_vol_point<D, P, BT><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, tt ? tt->hist : nullptr,
+                                                              tt ? tt->coef : 0.0, tt ? tt->supg_time : 0, ctx->src,
+                                                              Kvol, ctx->rvol, E);
     CKL();
     phase_end(ctx, PH_VOL_POINT);
   }
   {
-    typedef VolCfg<D, P> C;
-    CK(cudaFuncSetAttribute(k_vol_contract<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    typedef VolCfg<D, P, BT> C;
+    CK(cudaFuncSetAttribute(k_vol_contract<D, P, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     dim3 grid(E, D + 1, NS);
     phase_begin(ctx, PH_VOL_CONTRACT);
-    k_vol_contract<D, P><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, ctx->Kvol, ctx->Auu, ctx->Auq);
+    k_vol_contract<D, P, BT><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, Kvol, Auu, Auq);
     CKL();
     phase_end(ctx, PH_VOL_CONTRACT);
     phase_begin(ctx, PH_FACES);
@@ -566,8 +572,8 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
                                                            ctx->fnode, ctx->gather, ctx->uD, u, q, uh,
                                                            ctx->Kface, ctx->rface, E);
     CKL();
-    k_face_contract<D, P><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, ctx->Kface, ctx->rface, ctx->Auu, ctx->Auq,
-                                              ctx->Auh, ctx->Ahu, ctx->Ahq, ctx->Ahh, ctx->RU, ctx->RUh);
+    k_face_contract<D, P, BT><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, ctx->Kface, ctx->rface, Auu, Auq,
+                                                  Auh, Ahu, Ahq, Ahh, ctx->RU, ctx->RUh);
     CKL();
   }
   {
@@ -579,19 +585,25 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   return MEHDG_OK;
 }
 
+template <class BT>
+int assemble_bt(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt) {
+  const int d = ctx->d, p = ctx->p;
+  if (d == 2 && p == 1) return assemble_dp<2, 1, BT>(ctx, u, q, uh, tt);
+  if (d == 2 && p == 2) return assemble_dp<2, 2, BT>(ctx, u, q, uh, tt);
+  if (d == 2 && p == 3) return assemble_dp<2, 3, BT>(ctx, u, q, uh, tt);
+  if (d == 3 && p == 1) return assemble_dp<3, 1, BT>(ctx, u, q, uh, tt);
+  if (d == 3 && p == 2) return assemble_dp<3, 2, BT>(ctx, u, q, uh, tt);
+  if (d == 3 && p == 3) return assemble_dp<3, 3, BT>(ctx, u, q, uh, tt);
+  return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
+}
+
 }  // namespace
 
 int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt,
                  double* norms) {
   int rc;
-  const int d = ctx->d, p = ctx->p;
-  if (d == 2 && p == 1) rc = assemble_dp<2, 1>(ctx, u, q, uh, tt);
-  else if (d == 2 && p == 2) rc = assemble_dp<2, 2>(ctx, u, q, uh, tt);
-  else if (d == 2 && p == 3) rc = assemble_dp<2, 3>(ctx, u, q, uh, tt);
-  else if (d == 3 && p == 1) rc = assemble_dp<3, 1>(ctx, u, q, uh, tt);
-  else if (d == 3 && p == 2) rc = assemble_dp<3, 2>(ctx, u, q, uh, tt);
-  else if (d == 3 && p == 3) rc = assemble_dp<3, 3>(ctx, u, q, uh, tt);
-  else return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) rc = assemble_bt<float>(ctx, u, q, uh, tt);
+  else rc = assemble_bt<double>(ctx, u, q, uh, tt);
   if (rc) return rc;
   ctx->condensed = false;
   if (norms) {

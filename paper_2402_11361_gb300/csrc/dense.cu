@@ -13,47 +13,50 @@
 
 #include "internal.cuh"
 #include "lu.cuh"
+#include "tc_gemm.cuh"
 
 namespace {
 
 // C[b] = alpha A[b] B[b] + beta C[b], row-major, batch b = (i, j), i < n1 (outer), j < n2:
 // X[b] = X + i * sX1 + j * sX2.
+template <class T, class TB = double>
 struct GemmArgs {
   int M, N, K;
-  const double* A; int lda; long long sA1, sA2;
-  const double* B; int ldb; long long sB1, sB2;
-  double* C; int ldc; long long sC1, sC2;
+  const T* A; int lda; long long sA1, sA2;
+  const TB* B; int ldb; long long sB1, sB2;
+  T* C; int ldc; long long sC1, sC2;
   double alpha, beta;
   int n2;
 };
 
 constexpr int TM = 64, TN = 64, TK = 16;
-__global__ void __launch_bounds__(256) k_gemm64(GemmArgs a) {
-  __shared__ double sA[TK][TM + 1];
-  __shared__ double sB[TK][TN + 1];
+template <class T, class TB>
+__global__ void __launch_bounds__(256) k_gemm64(GemmArgs<T, TB> a) {
+  __shared__ T sA[TK][TM + 1];
+  __shared__ T sB[TK][TN + 1];
   const int b = blockIdx.z;
   const int bi = b / a.n2, bj = b % a.n2;
-  const double* A = a.A + bi * a.sA1 + bj * a.sA2;
-  const double* B = a.B + bi * a.sB1 + bj * a.sB2;
-  double* C = a.C + bi * a.sC1 + bj * a.sC2;
+  const T* A = a.A + bi * a.sA1 + bj * a.sA2;
+  const TB* B = a.B + bi * a.sB1 + bj * a.sB2;
+  T* C = a.C + bi * a.sC1 + bj * a.sC2;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
+  T acc[4][4] = {};
   for (int k0 = 0; k0 < a.K; k0 += TK) {
     for (int i = threadIdx.x; i < TM * TK; i += 256) {
       int r = i / TK, c = i % TK;
       int gr = m0 + r, gc = k0 + c;
-      sA[c][r] = (gr < a.M && gc < a.K) ? A[(size_t)gr * a.lda + gc] : 0.0;
+      sA[c][r] = (gr < a.M && gc < a.K) ? A[(size_t)gr * a.lda + gc] : T(0);
     }
     for (int i = threadIdx.x; i < TK * TN; i += 256) {
       int r = i / TN, c = i % TN;
       int gr = k0 + r, gc = n0 + c;
-      sB[r][c] = (gr < a.K && gc < a.N) ? B[(size_t)gr * a.ldb + gc] : 0.0;
+      sB[r][c] = (gr < a.K && gc < a.N) ? (T)B[(size_t)gr * a.ldb + gc] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      double av[4], bv[4];
+      T av[4], bv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) av[i] = sA[kk][ty + 16 * i];
 #pragma unroll
@@ -71,56 +74,83 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs a) {
     for (int j = 0; j < 4; ++j) {
       int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
       if (r < a.M && c < a.N) {
-        double* p = C + (size_t)r * a.ldc + c;
-        *p = a.alpha * acc[i][j] + (a.beta == 0.0 ? 0.0 : a.beta * *p);
+        T* p = C + (size_t)r * a.ldc + c;
+        *p = (T)a.alpha * acc[i][j] + (a.beta == 0.0 ? T(0) : (T)a.beta * *p);
       }
     }
 }
 
-int gemm(mehdg_ctx* ctx, const GemmArgs& a, int n1) {
+template <class T, class TB>
+int gemm(mehdg_ctx* ctx, const GemmArgs<T, TB>& a, int n1) {
   dim3 grid((a.N + TN - 1) / TN, (a.M + TM - 1) / TM, n1 * a.n2);
-  k_gemm64<<<grid, 256, 0, ctx->stream>>>(a);
+  k_gemm64<T, TB><<<grid, 256, 0, ctx->stream>>>(a);
   CKL();
   return MEHDG_OK;
 }
 
+// The same product on the tcgen05 tensor cores (TF32 inputs, FP32 accumulation)
+int tc_gemm(mehdg_ctx* ctx, int M, int N, int K, const float* A, long long lda, long long sA1, long long sA2,
+            const float* B, long long ldb, long long sB1, long long sB2, float* C, long long ldc, long long sC1,
+            long long sC2, float alpha, float beta, int n1, int n2) {
+  TcArgs a{};
+  a.M = M; a.N = N; a.K = K;
+  a.A = A; a.lda = lda; a.sA1 = sA1; a.sA2 = sA2;
+  a.B = B; a.ldb = ldb; a.sB1 = sB1; a.sB2 = sB2;
+  a.C = C; a.ldc = ldc; a.sC1 = sC1; a.sC2 = sC2;
+  a.alpha = alpha; a.beta = beta; a.n2 = n2; a.err = ctx->dtcerr;
+  cudaError_t e = tc_gemm_launch(a, n1 * n2, ctx->stream, ctx->tc_split);
+  ++ctx->launches;
+  if (e != cudaSuccess) return ctx_fail(ctx, MEHDG_ERR_CUDA, std::string("tcgen05 GEMM launch: ") + cudaGetErrorString(e));
+  return MEHDG_OK;
+}
+
 // y[b] = alpha A[b] x[b] + beta y[b]; one warp per row
+template <class T>
 struct GemvArgs {
   int M, N;
-  const double* A; int lda; long long sA1, sA2;
+  const T* A; int lda; long long sA1, sA2;
   const double* x; long long sx1, sx2;
   double* y; long long sy1, sy2;
   double alpha, beta;
   int n2;
 };
-__global__ void k_gemv(GemvArgs a) {
+template <class T>
+__global__ void k_gemv(GemvArgs<T> a) {
   const int b = blockIdx.y;
   const int bi = b / a.n2, bj = b % a.n2;
-  const double* A = a.A + bi * a.sA1 + bj * a.sA2;
+  const T* A = a.A + bi * a.sA1 + bj * a.sA2;
   const double* x = a.x + bi * a.sx1 + bj * a.sx2;
   double* y = a.y + bi * a.sy1 + bj * a.sy2;
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (row >= a.M) return;
   double s = 0.0;
-  for (int c = lane; c < a.N; c += 32) s += A[(size_t)row * a.lda + c] * x[c];
+  for (int c = lane; c < a.N; c += 32) s += (double)A[(size_t)row * a.lda + c] * x[c];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) y[row] = a.alpha * s + (a.beta == 0.0 ? 0.0 : a.beta * y[row]);
 }
-int gemv(mehdg_ctx* ctx, const GemvArgs& a, int n1) {
+template <class T>
+int gemv(mehdg_ctx* ctx, const GemvArgs<T>& a, int n1) {
   dim3 grid((a.M + 7) / 8, n1 * a.n2);
-  k_gemv<<<grid, 256, 0, ctx->stream>>>(a);
+  k_gemv<T><<<grid, 256, 0, ctx->stream>>>(a);
   CKL();
   return MEHDG_OK;
 }
 
-__global__ void k_scale(double* x, long long n, double a) {
+__global__ void k_to_float(const double* x, float* y, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) x[i] *= a;
+  if (i < n) y[i] = (float)x[i];
+}
+
+template <class T>
+__global__ void k_scale(T* x, long long n, double a) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (T)(a * (double)x[i]);
 }
 
 // S[(s,a)][(s,b)] += shift M[a][b]
-__global__ void k_mass_shift(double* S, const double* M, int Np, int ns, double shift, int E) {
+template <class T>
+__global__ void k_mass_shift(T* S, const double* M, int Np, int ns, double shift, int E) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long tot = (long long)E * ns * Np * Np;
   if (i >= tot) return;
@@ -129,7 +159,7 @@ __global__ void k_mass_shift(double* S, const double* M, int Np, int ns, double 
   int s = (i / ((long long)Np * Np)) % ns;
   int e = (int)(i / ((long long)Np * Np * ns));
   size_t Nu = (size_t)ns * Np;
-  S[(size_t)e * Nu * Nu + ((size_t)s * Np + a) * Nu + (size_t)s * Np + b] += shift * M[(size_t)a * Np + b];
+  S[(size_t)e * Nu * Nu + ((size_t)s * Np + a) * Nu + (size_t)s * Np + b] += (T)(shift * M[(size_t)a * Np + b]);
 }
 
 // MinvRQ[e][k][s] = M^-1 R_Q[e][k][s]
@@ -146,7 +176,8 @@ __global__ void k_minv_rq(const double* Minv, const double* RQ, double* out, int
 }
 
 // face blocks of A_uhuh: sum of the owners' local blocks (before D overwrites A_uhuh)
-__global__ void k_face_blocks(const double* Ahh, const int* owner, double* fblk, int ns, int Nfn, int Nth,
+template <class T>
+__global__ void k_face_blocks(const T* Ahh, const int* owner, double* fblk, int ns, int Nfn, int Nth,
                               int Nt, int d, int F) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int nfb = ns * Nfn;
@@ -166,49 +197,90 @@ __global__ void k_face_blocks(const double* Ahh, const int* owner, double* fblk,
 }
 
 // b_loc = h - B S^-1 g, one CTA per macro-element
-__global__ void __launch_bounds__(256) k_bhat_local(const double* S, const int* perm, const double* B,
+template <class T>
+__global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm, const T* B,
                                                      const double* gvec, const double* hvec, double* bloc, int Nu,
                                                      int Nt) {
   extern __shared__ double sm[];
   double* y = sm;        // Nu
   double* tmp = sm + Nu; // Nu
   const int e = blockIdx.x;
-  const double* Se = S + (size_t)e * Nu * Nu;
+  const T* Se = S + (size_t)e * Nu * Nu;
   const int* pe = perm + (size_t)e * Nu;
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) tmp[i] = gvec[(size_t)e * Nu + i];
   __syncthreads();
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) y[i] = tmp[pe[i]];
   __syncthreads();
-  lu_solve_block<double>(Se, Nu, y);
-  const double* Be = B + (size_t)e * Nt * Nu;
+  lu_solve_block<T, double>(Se, Nu, y);
+  const T* Be = B + (size_t)e * Nt * Nu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int r = w; r < Nt; r += nw) {
     double s = 0.0;
-    for (int c = lane; c < Nu; c += 32) s += Be[(size_t)r * Nu + c] * y[c];
+    for (int c = lane; c < Nu; c += 32) s += (double)Be[(size_t)r * Nu + c] * y[c];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) bloc[(size_t)e * Nt + r] = hvec[(size_t)e * Nt + r] - s;
+  }
+}
+
+template <class T>
+int batched_lu_t(mehdg_ctx* ctx, T* A, int* perm, int n, int batch, int* flag) {
+  size_t smem = lu_smem_bytes<T>(n);
+  CK(cudaFuncSetAttribute(k_lu_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_lu_batched<T><<<batch, LU_NT, smem, ctx->stream>>>(A, perm, n, flag);
+  CKL();
+  return MEHDG_OK;
+}
+
+// A^T_i = D + B (S^-1 C) for every macro (apply_mode 1); D is overwritten
+template <class T>
+int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
+  const int E = ctx->E, Nu = ctx->Nu, Nt = ctx->Nt;
+  T* X = reinterpret_cast<T*>(ctx->Xbuf);
+  constexpr int RC = sizeof(T) == 4 ? 64 : 32;
+  size_t smem = sizeof(T) * (size_t)Nu * RC;
+  if (smem > 220 * 1024) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: local matrices too large");
+  CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(E, (Nt + RC - 1) / RC);
+  k_lu_solve_multi<T, RC><<<grid, 256, smem, ctx->stream>>>(S, ctx->perm, C, X, Nu, Nt);
+  CKL();
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->use_tc_form)
+      return tc_gemm(ctx, Nt, Nt, Nu, B, Nu, (long long)Nt * Nu, 0, X, Nt, (long long)Nu * Nt, 0, D, Nt,
+                   (long long)Nt * Nt, 0, 1.f, 1.f, E, 1);
+  }
+  {
+    GemmArgs<T, T> a{};
+    a.M = Nt; a.N = Nt; a.K = Nu;
+    a.A = B; a.lda = Nu; a.sA1 = (long long)Nt * Nu; a.sA2 = 0;
+    a.B = X; a.ldb = Nt; a.sB1 = (long long)Nu * Nt; a.sB2 = 0;
+    a.C = D; a.ldc = Nt; a.sC1 = (long long)Nt * Nt; a.sC2 = 0;
+    a.alpha = 1.0; a.beta = 1.0; a.n2 = 1;
+    return gemm(ctx, a, E);
   }
 }
 
 }  // namespace
 
 int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag) {
-  size_t smem = lu_smem_bytes<double>(n);
-  CK(cudaFuncSetAttribute(k_lu_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_lu_batched<double><<<batch, LU_NT, smem, ctx->stream>>>(A, perm, n, flag);
-  CKL();
-  return MEHDG_OK;
+  return batched_lu_t<double>(ctx, A, perm, n, batch, flag);
 }
 
-int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
+template <class T>
+int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   cudaStream_t st = ctx->stream;
   const int E = ctx->E, d = ctx->d, ns = ctx->ns, Np = ctx->Np, Nth = ctx->Nth;
   const long long Nu = ctx->Nu, Nt = ctx->Nt;
   int rc;
+  T* Auu = reinterpret_cast<T*>(ctx->Auu);
+  T* Auq = reinterpret_cast<T*>(ctx->Auq);
+  T* Auh = reinterpret_cast<T*>(ctx->Auh);
+  T* Ahu = reinterpret_cast<T*>(ctx->Ahu);
+  T* Ahq = reinterpret_cast<T*>(ctx->Ahq);
+  T* Ahh = reinterpret_cast<T*>(ctx->Ahh);
   // face blocks of A_uhuh for the preconditioner, then their LU
   {
     long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
-    k_face_blocks<<<(tot + 255) / 256, 256, 0, st>>>(ctx->Ahh, ctx->owner, ctx->fblk, ns, ctx->Nfn, Nth, (int)Nt, d,
+    k_face_blocks<T><<<(tot + 255) / 256, 256, 0, st>>>(Ahh, ctx->owner, ctx->fblk, ns, ctx->Nfn, Nth, (int)Nt, d,
                                                      ctx->F);
     CKL();
   }
@@ -221,89 +293,139 @@ int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
   }
   // g = -R_U + sum_k A_uq_k[:, s] MinvRQ[k][s];  h = -R_Uh + sum_k A_uhq_k[:, s] MinvRQ[k][s]
   CK(cudaMemcpyAsync(ctx->gv, ctx->RU, sizeof(double) * E * Nu, cudaMemcpyDeviceToDevice, st));
-  k_scale<<<(E * Nu + 255) / 256, 256, 0, st>>>(ctx->gv, E * Nu, -1.0);
+  k_scale<double><<<(E * Nu + 255) / 256, 256, 0, st>>>(ctx->gv, E * Nu, -1.0);
   CK(cudaMemcpyAsync(ctx->hv, ctx->RUh, sizeof(double) * E * Nt, cudaMemcpyDeviceToDevice, st));
-  k_scale<<<(E * Nt + 255) / 256, 256, 0, st>>>(ctx->hv, E * Nt, -1.0);
+  k_scale<double><<<(E * Nt + 255) / 256, 256, 0, st>>>(ctx->hv, E * Nt, -1.0);
   CKL();
   for (int k = 0; k < d; ++k)
     for (int s = 0; s < ns; ++s) {
-      GemvArgs a{};
+      GemvArgs<T> a{};
       a.M = (int)Nu; a.N = Np;
-      a.A = ctx->Auq + (size_t)k * Nu * Nu + (size_t)s * Np; a.lda = (int)Nu; a.sA1 = d * Nu * Nu; a.sA2 = 0;
+      a.A = Auq + (size_t)k * Nu * Nu + (size_t)s * Np; a.lda = (int)Nu; a.sA1 = d * Nu * Nu; a.sA2 = 0;
       a.x = ctx->MinvRQ + ((size_t)k * ns + s) * Np; a.sx1 = (long long)d * Nu; a.sx2 = 0;
       a.y = ctx->gv; a.sy1 = Nu; a.sy2 = 0;
       a.alpha = 1.0; a.beta = 1.0; a.n2 = 1;
       if ((rc = gemv(ctx, a, E))) return rc;
       a.M = (int)Nt;
-      a.A = ctx->Ahq + (size_t)k * Nt * Nu + (size_t)s * Np; a.sA1 = d * Nt * Nu;
+      a.A = Ahq + (size_t)k * Nt * Nu + (size_t)s * Np; a.sA1 = d * Nt * Nu;
       a.y = ctx->hv; a.sy1 = Nt;
       if ((rc = gemv(ctx, a, E))) return rc;
     }
   // S, C, B, D
   if (shift != 0.0) {
     long long tot = (long long)E * ns * Np * Np;
-    k_mass_shift<<<(tot + 255) / 256, 256, 0, st>>>(ctx->Auu, ctx->Mref, Np, ns, shift, E);
+    k_mass_shift<T><<<(tot + 255) / 256, 256, 0, st>>>(Auu, ctx->Mref, Np, ns, shift, E);
     CKL();
   }
-  k_scale<<<(E * Nu * Nt + 255) / 256, 256, 0, st>>>(ctx->Auh, E * Nu * Nt, -1.0);
+  k_scale<T><<<(E * Nu * Nt + 255) / 256, 256, 0, st>>>(Auh, E * Nu * Nt, -1.0);
   CKL();
   for (int k = 0; k < d; ++k) {
-    GemmArgs a{};
+    if (sizeof(T) == 4 && ctx->use_tc_condense) {
+      // S[:, s] -= A_uq_k[:, s] W_k ; C[:, s] += A_uq_k[:, s] Wh_k ; B[:, s] -= A_uhq_k[:, s] W_k ;
+      // D[:, s] -= A_uhq_k[:, s] Wh_k   (batch = (macro, species s))
+      const float* W32 = ctx->Wk32 + (size_t)k * Np * Np;
+      const float* Wh32 = ctx->Whk32 + (size_t)k * Np * Nth;
+      const float* Aq = reinterpret_cast<const float*>(Auq) + (size_t)k * Nu * Nu;
+      const float* Ahq_k = reinterpret_cast<const float*>(Ahq) + (size_t)k * Nt * Nu;
+      float* Auu_f = reinterpret_cast<float*>(Auu);
+      float* Auh_f = reinterpret_cast<float*>(Auh);
+      float* Ahu_f = reinterpret_cast<float*>(Ahu);
+      float* Ahh_f = reinterpret_cast<float*>(Ahh);
+      if ((rc = tc_gemm(ctx, (int)Nu, Np, Np, Aq, Nu, d * Nu * Nu, Np, W32, Np, 0, 0, Auu_f, Nu, Nu * Nu, Np, -1.f,
+                        1.f, E, ns)))
+        return rc;
+      if ((rc = tc_gemm(ctx, (int)Nu, Nth, Np, Aq, Nu, d * Nu * Nu, Np, Wh32, Nth, 0, 0, Auh_f, Nt, Nu * Nt, Nth, 1.f,
+                        1.f, E, ns)))
+        return rc;
+      if ((rc = tc_gemm(ctx, (int)Nt, Np, Np, Ahq_k, Nu, d * Nt * Nu, Np, W32, Np, 0, 0, Ahu_f, Nu, Nt * Nu, Np, -1.f,
+                        1.f, E, ns)))
+        return rc;
+      if ((rc = tc_gemm(ctx, (int)Nt, Nth, Np, Ahq_k, Nu, d * Nt * Nu, Np, Wh32, Nth, 0, 0, Ahh_f, Nt, Nt * Nt, Nth,
+                        -1.f, 1.f, E, ns)))
+        return rc;
+      continue;
+    }
+    GemmArgs<T> a{};
     a.n2 = ns;
     a.alpha = -1.0; a.beta = 1.0;
     // S[:, s blk] -= A_uq_k[:, s blk] W_k
     a.M = (int)Nu; a.N = Np; a.K = Np;
-    a.A = ctx->Auq + (size_t)k * Nu * Nu; a.lda = (int)Nu; a.sA1 = d * Nu * Nu; a.sA2 = Np;
+    a.A = Auq + (size_t)k * Nu * Nu; a.lda = (int)Nu; a.sA1 = d * Nu * Nu; a.sA2 = Np;
     a.B = ctx->Wk + (size_t)k * Np * Np; a.ldb = Np; a.sB1 = 0; a.sB2 = 0;
-    a.C = ctx->Auu; a.ldc = (int)Nu; a.sC1 = Nu * Nu; a.sC2 = Np;
+    a.C = Auu; a.ldc = (int)Nu; a.sC1 = Nu * Nu; a.sC2 = Np;
     if ((rc = gemm(ctx, a, E))) return rc;
     // C[:, s trace blk] += A_uq_k[:, s blk] Wh_k
     a.alpha = 1.0;
     a.N = Nth;
     a.B = ctx->Whk + (size_t)k * Np * Nth; a.ldb = Nth;
-    a.C = ctx->Auh; a.ldc = (int)Nt; a.sC1 = Nu * Nt; a.sC2 = Nth;
+    a.C = Auh; a.ldc = (int)Nt; a.sC1 = Nu * Nt; a.sC2 = Nth;
     if ((rc = gemm(ctx, a, E))) return rc;
     // B[:, s blk] -= A_uhq_k[:, s blk] W_k
     a.alpha = -1.0;
     a.M = (int)Nt; a.N = Np;
-    a.A = ctx->Ahq + (size_t)k * Nt * Nu; a.sA1 = d * Nt * Nu;
+    a.A = Ahq + (size_t)k * Nt * Nu; a.sA1 = d * Nt * Nu;
     a.B = ctx->Wk + (size_t)k * Np * Np; a.ldb = Np;
-    a.C = ctx->Ahu; a.ldc = (int)Nu; a.sC1 = Nt * Nu; a.sC2 = Np;
+    a.C = Ahu; a.ldc = (int)Nu; a.sC1 = Nt * Nu; a.sC2 = Np;
     if ((rc = gemm(ctx, a, E))) return rc;
     // D[:, s trace blk] -= A_uhq_k[:, s blk] Wh_k
     a.N = Nth;
     a.B = ctx->Whk + (size_t)k * Np * Nth; a.ldb = Nth;
-    a.C = ctx->Ahh; a.ldc = (int)Nt; a.sC1 = Nt * Nt; a.sC2 = Nth;
+    a.C = Ahh; a.ldc = (int)Nt; a.sC1 = Nt * Nt; a.sC2 = Nth;
     if ((rc = gemm(ctx, a, E))) return rc;
   }
   phase_end(ctx, PH_CONDENSE);
   // LU of S and of the face blocks
   CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
   phase_begin(ctx, PH_LU);
-  if ((rc = batched_lu(ctx, ctx->Auu, ctx->perm, (int)Nu, E, ctx->dflag))) return rc;
+  if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag))) return rc;
   phase_end(ctx, PH_LU);
   phase_begin(ctx, PH_FACE_LU);
   if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;
+  if (ctx->finv32) {
+    // explicit inverses (columns of A_uhuh,f^-1) in FP64, stored in FP32 for the block-Jacobi product
+    double* tmp = ctx->Kvol;   // assembly scratch, free until the next assembly
+    const int nfb = ctx->nfb;
+    size_t smem = sizeof(double) * (size_t)nfb * 32;
+    CK(cudaFuncSetAttribute(k_lu_solve_multi<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(ctx->F, (nfb + 31) / 32);
+    k_lu_solve_multi<double, 32><<<grid, 256, smem, st>>>(ctx->fblk, ctx->fperm, nullptr, tmp, nfb, nfb);
+    CKL();
+    long long tot = (long long)ctx->F * nfb * nfb;
+    k_to_float<<<(tot + 255) / 256, 256, 0, st>>>(tmp, ctx->finv32, tot);
+    CKL();
+  }
   phase_end(ctx, PH_FACE_LU);
   // b^
   phase_begin(ctx, PH_BHAT);
   {
     size_t smem = sizeof(double) * 2 * Nu;
-    CK(cudaFuncSetAttribute(k_bhat_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bhat_local<<<E, 256, smem, st>>>(ctx->Auu, ctx->perm, ctx->Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt);
+    CK(cudaFuncSetAttribute(k_bhat_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt);
     CKL();
   }
   if (bhat) {
     if ((rc = face_reduce(ctx, ctx->bloc, bhat))) return rc;
   }
   phase_end(ctx, PH_BHAT);
-  int flags[4];
+  if (ctx->opt.apply_mode == 1) {
+    phase_begin(ctx, PH_FORM);
+    if ((rc = form_local_operator<T>(ctx, Auu, Ahu, Auh, Ahh))) return rc;
+    phase_end(ctx, PH_FORM);
+  }
+  int flags[4], tcerr = 0;
   CK(cudaMemcpyAsync(flags, ctx->dflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&tcerr, ctx->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (tcerr) return ctx_fail(ctx, MEHDG_ERR_TIMEOUT, "a tensor-core GEMM wait timed out");
   ctx->condensed = true;
   if (flags[0]) return ctx_fail(ctx, MEHDG_ERR_SINGULAR, "zero pivot in S of macro-element " + std::to_string(flags[1] - 1));
   if (flags[2]) return ctx_fail(ctx, MEHDG_ERR_SINGULAR, "zero pivot in the A_uhuh block of face " + std::to_string(flags[3] - 1));
   return MEHDG_OK;
+}
+
+int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) return condense_t<float>(ctx, shift, bhat);
+  return condense_t<double>(ctx, shift, bhat);
 }
 
 extern "C" int mehdg_condense_factor(mehdg_ctx* ctx, double shift, double* bhat) {

@@ -84,6 +84,11 @@ struct mehdg_ctx {
   double* dred = nullptr;    // reduction scratch
   double* hred = nullptr;    // pinned host mirror
 
+  float *Wk32 = nullptr, *Whk32 = nullptr;   // FP32 copies of W_k, Wh_k (mixed precision)
+  int* dtcerr = nullptr;                       // tensor-core kernel error word
+  bool use_tc_condense = false, use_tc_form = false, tc_split = true;
+  float* finv32 = nullptr;   // explicit FP32 inverses of the face blocks (mixed precision block-Jacobi)
+  double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
   // mixed precision copies
   float *S32 = nullptr, *B32 = nullptr, *C32 = nullptr, *D32 = nullptr;
   int* perm32 = nullptr;
@@ -107,7 +112,7 @@ struct mehdg_ctx {
 
 enum Phase {
   PH_VOL_POINT = 0, PH_VOL_CONTRACT = 1, PH_FACES = 2, PH_CONDENSE = 3, PH_LU = 4, PH_FACE_LU = 5,
-  PH_BHAT = 6, PH_APPLY = 7, PH_RECOVER = 8, PH_PRECOND = 9, PH_COUNT = 16
+  PH_BHAT = 6, PH_APPLY = 7, PH_RECOVER = 8, PH_PRECOND = 9, PH_FORM = 10, PH_COUNT = 16
 };
 void phase_begin(mehdg_ctx* ctx, int p);
 void phase_end(mehdg_ctx* ctx, int p);
@@ -137,3 +142,5 @@ int vec_copy(mehdg_ctx* ctx, long long n, const double* x, double* y);
 int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b, const double* y, double* z);
 int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag);
 int mlp_apply(mehdg_ctx* ctx, const double* r, double* z);
+struct TcArgs;
+cudaError_t tc_gemm_launch(const TcArgs& a, int batch, cudaStream_t st, bool split);

@@ -20,6 +20,7 @@
 namespace {
 
 constexpr int RB = 512;   // reduction blocks
+constexpr size_t RED_OUT = (size_t)RB * 128;   // dred layout: partials [128][RB], results, coefficients
 
 __global__ void k_mdot_part(const double* __restrict__ V, long long ldv, int nv, const double* __restrict__ w,
                             long long n, double* __restrict__ part) {
@@ -84,12 +85,38 @@ __global__ void __launch_bounds__(128) k_block_jacobi(const double* __restrict__
   for (int i = threadIdx.x; i < nfb; i += blockDim.x) z[(size_t)f * nfb + i] = sy[i];
 }
 
+// z_f = Minv_f r_f with an explicit FP32 inverse per face block (mixed precision)
+__global__ void __launch_bounds__(256) k_block_gemv(const float* __restrict__ Minv, const double* __restrict__ r,
+                                                    double* __restrict__ z, int nfb) {
+  __shared__ float xs[512];
+  const int f = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < nfb; i += blockDim.x) xs[i] = (float)r[(size_t)f * nfb + i];
+  __syncthreads();
+  const float* Mf = Minv + (size_t)f * nfb * nfb;
+  for (int row = w; row < nfb; row += nw) {
+    const float* mr = Mf + (size_t)row * nfb;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int c = lane;
+    for (; c + 96 < nfb; c += 128) {
+      s0 += mr[c] * xs[c];
+      s1 += mr[c + 32] * xs[c + 32];
+      s2 += mr[c + 64] * xs[c + 64];
+      s3 += mr[c + 96] * xs[c + 96];
+    }
+    for (; c < nfb; c += 32) s0 += mr[c] * xs[c];
+    float s = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) z[(size_t)f * nfb + row] = (double)s;
+  }
+}
+
 int mdot(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* w, long long n, double* host) {
   dim3 grid(RB, nv);
   k_mdot_part<<<grid, 256, 0, ctx->stream>>>(V, ldv, nv, w, n, ctx->dred);
-  k_mdot_final<<<nv, RB, 0, ctx->stream>>>(ctx->dred, ctx->dred + (size_t)RB * 64);
+  k_mdot_final<<<nv, RB, 0, ctx->stream>>>(ctx->dred, ctx->dred + RED_OUT);
   CKL();
-  CK(cudaMemcpyAsync(ctx->hred, ctx->dred + (size_t)RB * 64, sizeof(double) * nv, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->hred, ctx->dred + RED_OUT, sizeof(double) * nv, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < nv; ++i) host[i] = ctx->hred[i];
   return MEHDG_OK;
@@ -97,7 +124,7 @@ int mdot(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* w
 
 int maxpy(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* chost, double* y, long long n,
           double sign) {
-  double* dc = ctx->dred + (size_t)RB * 64 + 64;
+  double* dc = ctx->dred + RED_OUT + 128;
   CK(cudaMemcpyAsync(dc, chost, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->stream));
   k_maxpy<<<(n + 255) / 256, 256, 0, ctx->stream>>>(V, ldv, nv, dc, y, n, sign);
   CKL();
@@ -189,6 +216,13 @@ int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b
 
 static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
   size_t smem = sizeof(double) * ctx->nfb;
+  if (ctx->finv32) {
+    phase_begin(ctx, PH_PRECOND);
+    k_block_gemv<<<ctx->F, 256, 0, ctx->stream>>>(ctx->finv32, r, z, ctx->nfb);
+    CKL();
+    phase_end(ctx, PH_PRECOND);
+    return MEHDG_OK;
+  }
   phase_begin(ctx, PH_PRECOND);
   k_block_jacobi<<<ctx->F, 128, smem, ctx->stream>>>(ctx->fblk, ctx->fperm, r, z, ctx->nfb);
   CKL();
@@ -199,7 +233,7 @@ static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
 // kind 1: nu steps of GMRES on A^ left-preconditioned by block-Jacobi, from z = 0
 static int inner_gmres(mehdg_ctx* ctx, const double* r, double* z) {
   const long long n = ctx->ntr;
-  const int nu = std::max(1, ctx->opt.inner_iters);
+  const int nu = std::min(120, std::max(1, ctx->opt.inner_iters));
   int rc;
   double* IV = ctx->iV;
   if ((rc = block_jacobi(ctx, r, ctx->iw))) return rc;

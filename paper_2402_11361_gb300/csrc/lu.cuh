@@ -143,23 +143,31 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
 }
 
 // y <- U^-1 L^-1 y for factors LU (row-major, unit L), y already permuted (P y).
-// Called by all threads of the CTA; y in shared memory; arithmetic in double.
-template <class T>
-__device__ void lu_solve_block(const T* __restrict__ LU, int n, double* y) {
+// Called by all threads of the CTA; y in shared memory; arithmetic in Acc.
+template <class T, class Acc = double>
+__device__ void lu_solve_block(const T* __restrict__ LU, int n, Acc* y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int ib = min(32, n - i0);
     for (int r = warp; r < ib; r += nw) {
       const T* row = LU + (size_t)(i0 + r) * n;
-      double s = 0.0;
-      for (int c = lane; c < i0; c += 32) s += (double)row[c] * y[c];
+      Acc s0 = Acc(0), s1 = Acc(0), s2 = Acc(0), s3 = Acc(0);
+      int c = lane;
+      for (; c + 96 < i0; c += 128) {
+        s0 += (Acc)row[c] * y[c];
+        s1 += (Acc)row[c + 32] * y[c + 32];
+        s2 += (Acc)row[c + 64] * y[c + 64];
+        s3 += (Acc)row[c + 96] * y[c + 96];
+      }
+      for (; c < i0; c += 32) s0 += (Acc)row[c] * y[c];
+      Acc s = (s0 + s1) + (s2 + s3);
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) y[i0 + r] -= s;
     }
     __syncthreads();
     if (warp == 0) {
       for (int r = 1; r < ib; ++r) {
-        double v = (lane < r) ? (double)LU[(size_t)(i0 + r) * n + i0 + lane] * y[i0 + lane] : 0.0;
+        Acc v = (lane < r) ? (Acc)LU[(size_t)(i0 + r) * n + i0 + lane] * y[i0 + lane] : Acc(0);
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) y[i0 + r] -= v;
         __syncwarp();
@@ -171,20 +179,117 @@ __device__ void lu_solve_block(const T* __restrict__ LU, int n, double* y) {
     const int ib = min(32, n - i0);
     for (int r = warp; r < ib; r += nw) {
       const T* row = LU + (size_t)(i0 + r) * n;
-      double s = 0.0;
-      for (int c = i0 + ib + lane; c < n; c += 32) s += (double)row[c] * y[c];
+      Acc s0 = Acc(0), s1 = Acc(0), s2 = Acc(0), s3 = Acc(0);
+      int c = i0 + ib + lane;
+      for (; c + 96 < n; c += 128) {
+        s0 += (Acc)row[c] * y[c];
+        s1 += (Acc)row[c + 32] * y[c + 32];
+        s2 += (Acc)row[c + 64] * y[c + 64];
+        s3 += (Acc)row[c + 96] * y[c + 96];
+      }
+      for (; c < n; c += 32) s0 += (Acc)row[c] * y[c];
+      Acc s = (s0 + s1) + (s2 + s3);
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) y[i0 + r] -= s;
     }
     __syncthreads();
     if (warp == 0) {
       for (int r = ib - 1; r >= 0; --r) {
-        double v = (lane > r && lane < ib) ? (double)LU[(size_t)(i0 + r) * n + i0 + lane] * y[i0 + lane] : 0.0;
+        Acc v = (lane > r && lane < ib) ? (Acc)LU[(size_t)(i0 + r) * n + i0 + lane] * y[i0 + lane] : Acc(0);
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[i0 + r] = (y[i0 + r] - v) / (double)LU[(size_t)(i0 + r) * n + i0 + r];
+        if (lane == 0) y[i0 + r] = (y[i0 + r] - v) / (Acc)LU[(size_t)(i0 + r) * n + i0 + r];
         __syncwarp();
       }
     }
     __syncthreads();
+  }
+}
+
+// X = S^-1 B for a block of RC right-hand-side columns of one macro-element
+// (grid: macro x column block), from the LU factors and row permutation of S.
+// B and X are row-major [n][nrhs]; the RC columns live in shared memory.  Blocked
+// substitution: for each 32-row block the update from the solved rows is a small
+// GEMM (32 x done) x (done x RC) with 32 x 32 tiles of L or U staged in shared
+// memory and 8 outputs per thread in registers; then the 32 x 32 diagonal block is
+// solved column by column (one thread per right-hand side).
+// B == nullptr solves for the identity (columns of S^-1).
+template <class T, int RC>
+__global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
+                                                       const T* __restrict__ Ball, T* __restrict__ Xall, int n,
+                                                       int nrhs) {
+  static_assert(RC % 8 == 0 && RC <= 256, "RC");
+  constexpr int OPT = 32 * RC / 256;   // outputs per thread in a 32-row block
+  extern __shared__ unsigned char lum_raw[];
+  T* x = reinterpret_cast<T*>(lum_raw);   // [n][RC]
+  __shared__ T lt[32][33];
+  const int e = blockIdx.x, c0 = blockIdx.y * RC;
+  const int rc = min(RC, nrhs - c0);
+  const T* LU = LUall + (size_t)e * n * n;
+  const int* perm = permall + (size_t)e * n;
+  const T* Bm = Ball ? Ball + (size_t)e * n * nrhs : nullptr;
+  T* X = Xall + (size_t)e * n * nrhs;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n * RC; i += blockDim.x) {
+    int r = i / RC, c = i % RC;
+    if (Bm) x[i] = (c < rc) ? Bm[(size_t)perm[r] * nrhs + c0 + c] : T(0);
+    else x[i] = (c < rc && perm[r] == c0 + c) ? T(1) : T(0);   // B = I: columns of S^-1
+  }
+  __syncthreads();
+  // thread layout of the block update: row rr = tid / (256/32) ... 32 rows x RC columns
+  constexpr int TPR = 256 / 32;          // threads per row
+  const int rr = tid / TPR, cq = tid % TPR;
+  auto block_update = [&](int i0, int ib, int j_begin, int j_end) {
+    T acc[OPT];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) acc[o] = T(0);
+    for (int jb = j_begin; jb < j_end; jb += 32) {
+      const int jl = min(32, j_end - jb);
+      for (int i = tid; i < 32 * 32; i += blockDim.x) {
+        int a = i / 32, b = i % 32;
+        lt[a][b] = (a < ib && b < jl) ? LU[(size_t)(i0 + a) * n + jb + b] : T(0);
+      }
+      __syncthreads();
+      for (int q = 0; q < jl; ++q) {
+        const T l = lt[rr][q];
+        const T* xr = x + (size_t)(jb + q) * RC;
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) acc[o] += l * xr[cq + TPR * o];
+      }
+      __syncthreads();
+    }
+    if (rr < ib) {
+      T* xo = x + (size_t)(i0 + rr) * RC;
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) xo[cq + TPR * o] -= acc[o];
+    }
+    __syncthreads();
+  };
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int ib = min(32, n - i0);
+    if (i0 > 0) block_update(i0, ib, 0, i0);
+    for (int cc = tid; cc < RC; cc += blockDim.x)
+      for (int r = 1; r < ib; ++r) {
+        const T* row = LU + (size_t)(i0 + r) * n + i0;
+        T s = T(0);
+        for (int q = 0; q < r; ++q) s += row[q] * x[(i0 + q) * RC + cc];
+        x[(i0 + r) * RC + cc] -= s;
+      }
+    __syncthreads();
+  }
+  for (int i0 = ((n - 1) / 32) * 32; i0 >= 0; i0 -= 32) {
+    const int ib = min(32, n - i0);
+    if (i0 + ib < n) block_update(i0, ib, i0 + ib, n);
+    for (int cc = tid; cc < RC; cc += blockDim.x)
+      for (int r = ib - 1; r >= 0; --r) {
+        const T* row = LU + (size_t)(i0 + r) * n;
+        T s = T(0);
+        for (int q = r + 1; q < ib; ++q) s += row[i0 + q] * x[(i0 + q) * RC + cc];
+        x[(i0 + r) * RC + cc] = (x[(i0 + r) * RC + cc] - s) / row[i0 + r];
+      }
+    __syncthreads();
+  }
+  for (int i = tid; i < n * RC; i += blockDim.x) {
+    int r = i / RC, c = i % RC;
+    if (c < rc) X[(size_t)r * nrhs + c0 + c] = x[i];
   }
 }

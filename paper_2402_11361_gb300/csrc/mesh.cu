@@ -357,6 +357,8 @@ static void default_options(mehdg_options* o) {
   o->tau_init = 1.0;
   o->tau_max = 1e8;
   o->refine_iters = 2;
+  o->apply_mode = 0;
+  o->tc_mode = 0;
 }
 
 static int setup(mehdg_ctx* ctx) {
@@ -600,16 +602,23 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->fblk, (size_t)F * ctx->nfb * ctx->nfb);
   ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
   ALLOC(ctx->dflag, 16);
-  ALLOC(ctx->dred, 1 << 16);
-  CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * (1 << 16)));
+  ALLOC(ctx->dred, 1 << 17);
+  CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * 256));
+  ALLOC(ctx->dtcerr, 4);
+  CK(cudaMemsetAsync(ctx->dtcerr, 0, sizeof(int) * 4, st));
   if (ctx->opt.precision == MEHDG_PREC_MIXED) {
-    ALLOC(ctx->S32, (size_t)E * Nu * Nu);
-    ALLOC(ctx->B32, (size_t)E * Nt * Nu);
-    ALLOC(ctx->C32, (size_t)E * Nu * Nt);
-    ALLOC(ctx->D32, (size_t)E * Nt * Nt);
-    ALLOC(ctx->perm32, (size_t)E * Nu);
+    ALLOC(ctx->finv32, (size_t)F * ctx->nfb * ctx->nfb);
+    std::vector<float> w32(Wk.begin(), Wk.end()), wh32(Whk.begin(), Whk.end());
+    ALLOC(ctx->Wk32, w32.size());
+    ALLOC(ctx->Whk32, wh32.size());
+    CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
   }
-  ctx->restart = std::max(2, ctx->opt.restart);
+  if (ctx->opt.apply_mode == 1) {
+    size_t esz = ctx->opt.precision == MEHDG_PREC_MIXED ? sizeof(float) : sizeof(double);
+    ALLOC(ctx->Xbuf, (size_t)E * Nu * Nt * esz / sizeof(double) + 1);
+  }
+  ctx->restart = std::min(120, std::max(2, ctx->opt.restart));
   const long long n = ctx->ntr;
   ALLOC(ctx->V, (size_t)(ctx->restart + 1) * n);
   ALLOC(ctx->Zk, (size_t)ctx->restart * n);
@@ -617,7 +626,7 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->tv, n);
   ALLOC(ctx->tv2, n);
   ALLOC(ctx->rv, n);
-  int nin = std::max(1, ctx->opt.inner_iters);
+  int nin = std::min(120, std::max(1, ctx->opt.inner_iters));
   ALLOC(ctx->iV, (size_t)(nin + 1) * n);
   ALLOC(ctx->iw, n);
   ALLOC(ctx->un, (size_t)E * Nu);
@@ -665,6 +674,8 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
   default_options(&ctx->opt);
   if (opt) ctx->opt = *opt;
   ctx->stream = (cudaStream_t)stream;
+  ctx->use_tc_condense = ctx->use_tc_form = (ctx->opt.tc_mode == 1 || ctx->opt.tc_mode == 2);
+  ctx->tc_split = ctx->opt.tc_mode == 1;
   int rc = setup(ctx);
   if (rc != MEHDG_OK) {
     std::string msg = ctx->err;
@@ -741,6 +752,23 @@ extern "C" int mehdg_get_block(mehdg_ctx* ctx, int which, int e, double* out, lo
     std::vector<int> tmp(n);
     CK(cudaMemcpy(tmp.data(), isrc, sizeof(int) * n, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
+  } else if (ctx->opt.precision == MEHDG_PREC_MIXED && which <= 9) {
+    // blocks are FP32 in the mixed-precision path (same element offsets)
+    const float* fsrc = nullptr;
+    std::vector<float> tmp(n);
+    const double* base = nullptr;
+    size_t idx = 0;
+    switch (which) {
+      case 0: base = ctx->Auu; idx = e * Nu * Nu; break;
+      case 1: case 2: case 3: base = ctx->Auq; idx = (e * d + (which - 1)) * Nu * Nu; break;
+      case 4: base = ctx->Auh; idx = e * Nu * Nt; break;
+      case 5: base = ctx->Ahu; idx = e * Nt * Nu; break;
+      case 6: case 7: case 8: base = ctx->Ahq; idx = (e * d + (which - 6)) * Nt * Nu; break;
+      default: base = ctx->Ahh; idx = e * Nt * Nt; break;
+    }
+    fsrc = reinterpret_cast<const float*>(base) + idx;
+    CK(cudaMemcpy(tmp.data(), fsrc, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
   } else {
     CK(cudaMemcpy(out, src, sizeof(double) * n, cudaMemcpyDeviceToHost));
   }
@@ -756,7 +784,8 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->MinvRQ, ctx->bloc, ctx->slot, ctx->Kvol, ctx->rvol, ctx->Kface, ctx->rface, ctx->fblk,
                   ctx->fperm, ctx->dflag, ctx->dred, ctx->S32, ctx->B32, ctx->C32, ctx->D32, ctx->perm32,
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
-                  ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat};
+                  ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
+                  ctx->Whk32, ctx->dtcerr, ctx->finv32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);

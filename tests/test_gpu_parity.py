@@ -249,3 +249,72 @@ def test_dirk_step_matches_oracle(lib):
     assert rel(u.cpu().numpy(), ou) < 1e-9
     assert rel(uh.cpu().numpy(), ouh) < 1e-9
     ctx.close()
+
+
+# ---------------------------------------------------------------- mixed precision (FP32 blocks)
+
+MIXED = dict(precision=1)
+
+
+def test_mixed_blocks_and_apply_close_to_oracle(lib):
+    """FP32 blocks: each block within FP32 rounding of the FP64 oracle; the trace apply
+    within the accuracy of TF32 condensation products (tensor cores)."""
+    pr = W.mms(dim=2, nmac=3, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    ctx = lib.Context(pr, MIXED)
+    norms = ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    blks, geos, onrm, _ = solve.global_assemble(P, u, q, uh)
+    assert np.allclose(norms, [onrm["RQ"], onrm["RU"], onrm["RUh"], onrm["RF"]], rtol=1e-11)   # FP64 residual
+    Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+    for e in (0, 4):
+        assert rel(ctx.get_block(0, e).reshape(Nu, Nu), blks[e]["Auu"]) < 1e-6
+        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), blks[e]["Ahh"]) < 1e-6
+    ctx.condense(shift=0.3)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    x = W.random_vector(P.F * P.ns * P.Nfn, 9)
+    y = ctx.apply(to_dev(x)).cpu().numpy()
+    # condensation products run as TF32 tensor-core tiles (10-bit mantissa)
+    assert rel(y, solve.apply_trace(P, cond, x)) < 5e-3
+    ctx.close()
+
+
+def test_mixed_newton_reaches_the_fp64_solution(lib):
+    """Inexact Newton with FP32 Jacobian blocks converges to the solution of the FP64
+    residual: same end state as the oracle's FP64 Newton (2D manufactured solution)."""
+    pr = W.mms(dim=2, nmac=4, m=2, p=2, vel=0.1)
+    P = solve.Problem(pr)
+    du, duh = W.perturbation(pr, 2)
+    u0, q0, uh0 = _oracle_init(P, pr, du, duh)
+    ou, oq, ouh, hist = solve.newton_ser(P, u0, q0, uh0, rtol=1e-12, precond="direct")
+    ctx = lib.Context(pr, dict(precision=1, newton_rtol=1e-11, lin_rtol=1e-6, max_iters=4000, precond=1))
+    u, q, uh = ctx.init_state(to_dev(du), to_dev(duh))
+    st = ctx.dirk_stage(0, 0.0, u, q, uh)
+    assert st["res"] <= 1e-11 * st["res0"]
+    assert rel(u.cpu().numpy(), ou) < 1e-8
+    assert rel(uh.cpu().numpy(), ouh) < 1e-8
+    ctx.close()
+
+
+# ---------------------------------------------------------------- explicit local operator (apply_mode 1)
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_explicit_local_operator_apply(lib, prec):
+    """apply_mode 1 forms A^T_i = B S^-1 C + D once (the one-layer form of eq. C47,
+    equal to eq. ASC2a) and applies it; same operator as Algorithm 2."""
+    pr = W.mms(dim=2, nmac=3, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    ctx = lib.Context(pr, dict(precision=prec, apply_mode=1))
+    ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    ctx.condense(shift=0.3)
+    blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+    Nt = P.ns * P.Nth
+    tol_blk, tol_apply = (1e-10, 1e-11) if prec == 0 else (5e-3, 5e-3)   # mixed: TF32 tensor-core products
+    for e in (0, 4, 8):
+        A1, _ = solve.condense_one_layer(geos[e], blks[e], shift=0.3)
+        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), A1) < tol_blk
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    x = W.random_vector(P.F * P.ns * P.Nfn, 9)
+    assert rel(ctx.apply(to_dev(x)).cpu().numpy(), solve.apply_trace(P, cond, x)) < tol_apply
+    ctx.close()
