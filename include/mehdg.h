@@ -226,6 +226,33 @@ int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
                               const double* C, const double* D, const int* gather,
                               const int* owner, const double* x, double* y, void* stream);
 
+/* Learned preconditioner correction (preconditioner kind 2).  No counterpart in the
+ * paper (spec addition): FGMRES tolerates a variable preconditioner (Sec. 4.2),
+ * so the block-Jacobi step is corrected face by face, z_f += |r_f| MLP(r_f/|r_f|),
+ * by a network n_in -> hidden (ReLU) -> hidden (ReLU) -> n_out (n_in = n_out = ns Nfn
+ * rounded up to 32) with BF16 weights, FP32 biases and FP32 accumulation.
+ * mehdg_mlp_setup: allocate with seeded weights and room for max_pairs pairs.
+ * mehdg_mlp_params: copy the FP32 master parameters to (set = 0) or from (set = 1)
+ *   host memory, packed [W1 (h x n_in), b1, W2 (h x h), b2, W3 (n_out x h), b3];
+ *   *count receives the length.
+ * mehdg_mlp_record: store one (residual r, error e) pair of global trace vectors as
+ *   one sample per face (input r_f/|r_f|, target (e_f - z0_f)/|r_f|, z0 the
+ *   block-Jacobi output).  mehdg_mlp_set_recording(on): FGMRES then records up to 8
+ *   pairs per converged solve (iterates of its last cycle against its solution).
+ * mehdg_mlp_gradient: mean-squared loss and gradient (host float[count]) for n rows
+ *   of device inputs X [n][n_in] and targets T [n][n_out].
+ * mehdg_mlp_train: epochs of Adam over the recorded samples in minibatches; losses
+ *   (host double[2]) receives the mean loss of the first and last epoch.
+ * In kind-2 solves FGMRES falls back to kind 1 when its residual falls by less than
+ * 10x over 20 iterations (stats->status bit 0). */
+int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long seed, int max_pairs);
+int mehdg_mlp_params(mehdg_ctx* ctx, int set, float* host, long long* count);
+int mehdg_mlp_record(mehdg_ctx* ctx, const double* r, const double* e);
+int mehdg_mlp_set_recording(mehdg_ctx* ctx, int on, int* n_samples);
+int mehdg_mlp_gradient(mehdg_ctx* ctx, const float* X, const float* T, int n, float* grad,
+                       double* loss);
+int mehdg_mlp_train(mehdg_ctx* ctx, int epochs, int batch, double lr, double* losses);
+
 /* Batched dense product on the tcgen05 tensor cores (TF32 inputs, FP32 accumulation),
  * the kernel used by the mixed-precision path for its local GEMMs (forming A^T_i,
  * condensation products):  C_b = alpha A_b B_b + beta C_b for b < batch, with

@@ -19,7 +19,9 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_local", "mehdg_condense_factor",
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
-           "mehdg_get_block", "mehdg_phase_times", "mehdg_launch_count", "mehdg_destroy", "mehdg_last_error"]
+           "mehdg_get_block", "mehdg_phase_times", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
+           "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
+           "mehdg_tc_gemm_tf32", "mehdg_apply_trace_noalloc", "mehdg_destroy", "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
 
@@ -87,6 +89,12 @@ def load_library(path=LIB_PATH):
     lib.mehdg_get_block.argtypes = [c_void_p, I, I, c_void_p, P(c_longlong)]
     lib.mehdg_phase_times.argtypes = [c_void_p, P(c_double), I]
     lib.mehdg_launch_count.argtypes = [c_void_p, P(c_longlong)]
+    lib.mehdg_mlp_setup.argtypes = [c_void_p, I, ctypes.c_ulonglong, I]
+    lib.mehdg_mlp_params.argtypes = [c_void_p, I, c_void_p, P(c_longlong)]
+    lib.mehdg_mlp_record.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.mehdg_mlp_set_recording.argtypes = [c_void_p, I, P(c_int)]
+    lib.mehdg_mlp_gradient.argtypes = [c_void_p, c_void_p, c_void_p, I, c_void_p, P(c_double)]
+    lib.mehdg_mlp_train.argtypes = [c_void_p, I, I, c_double, P(c_double)]
     lib.mehdg_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.restype = None
     lib.mehdg_last_error.argtypes = [c_void_p]
@@ -254,6 +262,47 @@ class Context:
         out = (c_double * 16)()
         self._check(self.lib.mehdg_phase_times(self.h, out, 16), "phase_times")
         return {k: out[i] for i, k in enumerate(self.PHASES)}
+
+    # -- learned preconditioner correction (kind 2)
+    def mlp_setup(self, hidden=256, seed=0, max_pairs=400):
+        self._check(self.lib.mehdg_mlp_setup(self.h, int(hidden), int(seed), int(max_pairs)), "mlp_setup")
+        n = c_longlong()
+        self._check(self.lib.mehdg_mlp_params(self.h, 0, None, ctypes.byref(n)), "mlp_params")
+        self.mlp_nparams = n.value
+        self.mlp_nin = ((self.info["ns"] * self.info["Nfn"] + 31) // 32) * 32
+        self.mlp_hidden = int(hidden)
+
+    def mlp_params(self, values=None):
+        """Get (values None) or set the packed FP32 master parameters (numpy float32)."""
+        if values is None:
+            out = np.empty(self.mlp_nparams, dtype=np.float32)
+            self._check(self.lib.mehdg_mlp_params(self.h, 0, out.ctypes.data_as(c_void_p), None), "mlp_params")
+            return out
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        self._check(self.lib.mehdg_mlp_params(self.h, 1, v.ctypes.data_as(c_void_p), None), "mlp_params")
+
+    def mlp_record(self, r, e):
+        self._check(self.lib.mehdg_mlp_record(self.h, self._ptr(r), self._ptr(e)), "mlp_record")
+
+    def mlp_set_recording(self, on):
+        n = c_int()
+        self._check(self.lib.mehdg_mlp_set_recording(self.h, int(bool(on)), ctypes.byref(n)), "mlp_set_recording")
+        return n.value
+
+    def mlp_gradient(self, X, T):
+        """Loss and gradient for device float32 tensors X [n][n_in], T [n][n_out]."""
+        assert X.dtype == self.torch.float32 and T.dtype == self.torch.float32 and X.is_contiguous()
+        g = np.empty(self.mlp_nparams, dtype=np.float32)
+        loss = c_double()
+        self._check(self.lib.mehdg_mlp_gradient(self.h, c_void_p(X.data_ptr()), c_void_p(T.data_ptr()),
+                                                int(X.shape[0]), g.ctypes.data_as(c_void_p), ctypes.byref(loss)),
+                    "mlp_gradient")
+        return loss.value, g
+
+    def mlp_train(self, epochs=200, batch=4096, lr=1e-3):
+        out = (c_double * 2)()
+        self._check(self.lib.mehdg_mlp_train(self.h, int(epochs), int(batch), float(lr), out), "mlp_train")
+        return out[0], out[1]
 
     def launch_count(self):
         n = c_longlong()

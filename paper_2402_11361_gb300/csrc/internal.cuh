@@ -97,6 +97,7 @@ struct mehdg_ctx {
   int restart = 30;
   double *V = nullptr, *Zk = nullptr, *wv = nullptr, *tv = nullptr, *tv2 = nullptr, *rv = nullptr;
   double *iV = nullptr, *iw = nullptr;    // inner GMRES
+  double* xstart = nullptr;               // FGMRES iterate at the start of the current cycle
   // Newton / DIRK
   double *un = nullptr, *ustage = nullptr, *hist = nullptr, *du = nullptr, *dq = nullptr, *duh = nullptr,
          *bhat = nullptr;
@@ -142,5 +143,8 @@ int vec_copy(mehdg_ctx* ctx, long long n, const double* x, double* y);
 int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b, const double* y, double* z);
 int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag);
 int mlp_apply(mehdg_ctx* ctx, const double* r, double* z);
+bool mlp_recording(const mehdg_ctx* ctx);
+int mlp_record_pair(mehdg_ctx* ctx, const double* r, const double* e);
+void mlp_destroy(mehdg_ctx* ctx);
 struct TcArgs;
 cudaError_t tc_gemm_launch(const TcArgs& a, int batch, cudaStream_t st, bool split);

@@ -284,14 +284,23 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
   double beta = bnorm;
   int its = 0;
   bool conv = beta <= tol;
+  int kind = ctx->opt.precond;
+  // learned preconditioner fallback: switch to the multi-level preconditioner when the
+  // residual falls by less than 10x over 20 iterations
+  double watch = beta;
+  int watch_it = 0;
+  Hess last(m);
+  int last_k = 0;
   while (!conv && its < ctx->opt.max_iters) {
+    if ((rc = vec_copy(ctx, n, x, ctx->xstart))) return rc;
     if ((rc = vec_lincomb(ctx, n, 1.0 / beta, ctx->rv, 0.0, ctx->rv, ctx->V))) return rc;
     Hess hs(m);
     hs.g[0] = beta;
     int k = 0;
+    bool fallback = false;
     for (int j = 0; j < m; ++j) {
       double* Zj = ctx->Zk + (size_t)j * n;
-      if ((rc = precond_impl(ctx, ctx->opt.precond, ctx->V + (size_t)j * n, Zj))) return rc;
+      if ((rc = precond_impl(ctx, kind, ctx->V + (size_t)j * n, Zj))) return rc;
       if ((rc = apply_trace_impl(ctx, Zj, ctx->wv))) return rc;
       double hn;
       if ((rc = arnoldi_cgs2(ctx, ctx->V, j, ctx->wv, n, hs, &hn))) return rc;
@@ -300,6 +309,14 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
       k = j + 1;
       if (!std::isfinite(res)) return ctx_fail(ctx, MEHDG_ERR_NAN, "non-finite FGMRES residual");
       if (res <= tol || its >= ctx->opt.max_iters || hn == 0.0) break;
+      if (kind == 2 && its - watch_it >= 20) {
+        if (res > 0.1 * watch) {
+          fallback = true;
+          break;
+        }
+        watch = res;
+        watch_it = its;
+      }
     }
     std::vector<double> y = hs.solve(k);
     if ((rc = maxpy(ctx, ctx->Zk, n, k, y.data(), x, n, 1.0))) return rc;
@@ -308,12 +325,38 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
     if ((rc = vec_dot(ctx, ctx->rv, ctx->rv, n, &beta))) return rc;
     beta = std::sqrt(beta);
     conv = beta <= tol;
+    last = hs;
+    last_k = k;
+    if (fallback) {
+      kind = 1;
+      if (st) st->status |= 1;   // bit 0: the learned preconditioner fell back
+    }
   }
   if (st) {
     st->fgmres_iters += its;
     st->res = beta;
   }
   if (!conv) return ctx_fail(ctx, MEHDG_ERR_NOT_CONVERGED, "FGMRES reached its iteration cap");
+  if (mlp_recording(ctx) && last_k > 0) {
+    // (residual, error) pairs of iterates of the last cycle: x_i = x_start + Z y_i,
+    // y_i from the rotated Hessenberg of that cycle (its first i columns are final)
+    const int npairs = std::min(8, last_k);
+    int prev = -1;
+    for (int q = 0; q < npairs; ++q) {
+      int i = (int)((long long)q * last_k / npairs);
+      if (i == prev) continue;
+      prev = i;
+      if ((rc = vec_copy(ctx, n, ctx->xstart, ctx->tv2))) return rc;
+      if (i > 0) {
+        std::vector<double> yi = last.solve(i);
+        if ((rc = maxpy(ctx, ctx->Zk, n, i, yi.data(), ctx->tv2, n, 1.0))) return rc;
+      }
+      if ((rc = apply_trace_impl(ctx, ctx->tv2, ctx->wv))) return rc;
+      if ((rc = vec_lincomb(ctx, n, 1.0, b, -1.0, ctx->wv, ctx->rv))) return rc;
+      if ((rc = vec_lincomb(ctx, n, 1.0, x, -1.0, ctx->tv2, ctx->tv))) return rc;
+      if ((rc = mlp_record_pair(ctx, ctx->rv, ctx->tv))) return rc;
+    }
+  }
   return MEHDG_OK;
 }
 

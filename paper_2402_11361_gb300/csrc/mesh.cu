@@ -629,6 +629,7 @@ static int setup(mehdg_ctx* ctx) {
   int nin = std::min(120, std::max(1, ctx->opt.inner_iters));
   ALLOC(ctx->iV, (size_t)(nin + 1) * n);
   ALLOC(ctx->iw, n);
+  ALLOC(ctx->xstart, n);
   ALLOC(ctx->un, (size_t)E * Nu);
   ALLOC(ctx->ustage, (size_t)3 * E * Nu);
   ALLOC(ctx->hist, (size_t)E * Nu);
@@ -789,6 +790,8 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
+  if (ctx->xstart) cudaFree(ctx->xstart);
+  mlp_destroy(ctx);
   for (int i = 0; i < 2 * PH_COUNT; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   delete ctx;

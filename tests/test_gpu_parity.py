@@ -318,3 +318,67 @@ def test_explicit_local_operator_apply(lib, prec):
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
     assert rel(ctx.apply(to_dev(x)).cpu().numpy(), solve.apply_trace(P, cond, x)) < tol_apply
     ctx.close()
+
+
+# ---------------------------------------------------------------- learned preconditioner correction
+
+def test_mlp_gradient_matches_oracle(lib):
+    """GPU forward/backward (BF16 weights, FP32 accumulation) against the FP64 oracle run
+    with the same BF16-rounded weights."""
+    from oracle import mlp as omlp
+    pr = W.mms(dim=2, nmac=2, m=2, p=2)
+    ctx = lib.Context(pr)
+    ctx.mlp_setup(hidden=64, seed=3)
+    nin, hid = ctx.mlp_nin, ctx.mlp_hidden
+    rng = np.random.default_rng(8)
+    p = (rng.normal(size=ctx.mlp_nparams) * 0.2).astype(np.float32)
+    ctx.mlp_params(p)
+    assert np.array_equal(ctx.mlp_params(), p)
+    X = rng.normal(size=(300, nin)).astype(np.float32)
+    T = rng.normal(size=(300, nin)).astype(np.float32)
+    loss, g = ctx.mlp_gradient(torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda"))
+    # oracle parameters: weights rounded to BF16 as stored for the products, biases FP32
+    po = p.astype(np.float64)
+    o = 0
+    for shape, is_w in [((hid, nin), True), ((hid,), False), ((hid, hid), True), ((hid,), False),
+                        ((nin, hid), True), ((nin,), False)]:
+        n = int(np.prod(shape))
+        if is_w:
+            po[o:o + n] = omlp.bf16_round(p[o:o + n])
+        o += n
+    lo, go = omlp.loss_and_grad(po, X.astype(np.float64), T.astype(np.float64), nin, hid, nin)
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max()
+    ctx.close()
+
+
+def test_mlp_training_and_kind2_solve(lib):
+    """Pairs recorded from plain FGMRES solves train the correction (loss falls); the
+    kind-2 solve reaches the dense solution of the same system."""
+    pr = W.mms(dim=2, nmac=3, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    ctx = lib.Context(pr, dict(lin_rtol=1e-10, precond=0, restart=60, max_iters=3000))
+    ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    b = ctx.condense(shift=0.3)
+    ctx.mlp_setup(hidden=64, seed=1, max_pairs=64)
+    ctx.mlp_set_recording(True)
+    x0, st0 = ctx.linear_solve(b)
+    nsamp = ctx.mlp_set_recording(False)
+    assert nsamp > 0
+    first, last = ctx.mlp_train(epochs=300, batch=1024, lr=2e-3)
+    assert last < first
+    ctx2 = lib.Context(pr, dict(lin_rtol=1e-10, precond=2, restart=60, max_iters=3000))
+    ctx2.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    b2 = ctx2.condense(shift=0.3)
+    ctx2.mlp_setup(hidden=64, seed=1, max_pairs=1)
+    ctx2.mlp_params(ctx.mlp_params())
+    x2, st2 = ctx2.linear_solve(b2)
+    blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    xo = np.linalg.solve(solve.explicit_trace_matrix(P, cond), solve.assemble_bhat(P, cond))
+    assert rel(x2.cpu().numpy(), xo) < 1e-8
+    print("block-Jacobi its %d, with learned correction its %d (fallback %d)" %
+          (st0["fgmres_iters"], st2["fgmres_iters"], st2["status"] & 1))
+    ctx.close()
+    ctx2.close()

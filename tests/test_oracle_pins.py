@@ -441,3 +441,25 @@ def test_manufactured_solution_converges_at_rate_p_plus_1(p):
     e2, h2 = _mms_error(4, p)
     assert h2[-1]["RF"] <= 1e-10 * h2[0]["RF"]
     assert np.log2(e1 / e2) >= p + 1 - 0.3
+
+
+# ---------------------------------------------------------------- MLP correction (oracle side)
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    nin, hid, nout = 8, 6, 8
+    rng = np.random.default_rng(4)
+    p = rng.normal(size=mlp.n_params(nin, hid, nout)) * 0.5
+    X = rng.normal(size=(5, nin))
+    T = rng.normal(size=(5, nout))
+    loss, g = mlp.loss_and_grad(p, X, T, nin, hid, nout)
+    h = 1e-6
+    for i in rng.choice(len(p), 25, replace=False):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (mlp.loss_and_grad(pp, X, T, nin, hid, nout)[0] - mlp.loss_and_grad(pm, X, T, nin, hid, nout)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i]))
+    # bf16 rounding: 8 significant bits, round to nearest even
+    assert mlp.bf16_round(np.float32(1.0 + 2 ** -9))[()] == 1.0
+    assert mlp.bf16_round(np.float32(1.0 + 3 * 2 ** -9))[()] == 1.0 + 2 ** -7
