@@ -149,6 +149,47 @@ def phase_work(z, E, precision, apply_mode=0):
     return dict(condense_flops=cond, lu_flops=lu, apply_bytes=apply_bytes, apply_flops=apply_flops)
 
 
+def newton_solve(ctx, state, tol=1e-8, max_steps=60, record=False):
+    """Steady pseudo-transient Newton/SER solve through the C ABI (one call per phase).
+
+    Returns statistics and, when record is set, the input state and pseudo-time step
+    of every Newton step (for replay)."""
+    import torch
+    u, q, uh = (t.clone() for t in state)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    records = []
+    tau_init, tau_max = 1.0, 1e8
+    its = 0
+    status = 0
+    e0.record(st)
+    norms = ctx.assemble(u, q, uh)
+    R0 = norms[3]
+    dtau = tau_init
+    steps = 0
+    while norms[3] > tol * R0 and steps < max_steps:
+        if record:
+            records.append((u.clone(), q.clone(), uh.clone(), dtau))
+        bhat = ctx.condense(shift=1.0 / dtau)
+        duh_s, stats = ctx.linear_solve(bhat, allow_not_converged=True)
+        its += stats["fgmres_iters"]
+        status |= stats["status"]
+        dU, dQ = ctx.recover(duh_s)
+        u += dU
+        q += dQ
+        uh += duh_s
+        RU_old = norms[1]
+        norms = ctx.assemble(u, q, uh)
+        dtau = min(max(dtau * RU_old / max(norms[1], 1e-300), tau_init), tau_max)
+        steps += 1
+    e1.record(st)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    return dict(newton_steps=steps, fgmres_iters=its, converged=bool(norms[3] <= tol * R0), time_s=t,
+                s_per_step=t / max(steps, 1), res0=float(R0), res=float(norms[3]), fallback=bool(status & 1),
+                records=records, state=(u, q, uh))
+
+
 def run_ours(args, ws, rank, lrank):
     import torch
     import __graft_entry__ as ge
@@ -160,44 +201,32 @@ def run_ours(args, ws, rank, lrank):
     pr = workload()
     z = sizes(pr)
     prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
-    opts = dict(precision=prec, precond=args.precond, restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol,
-                newton_rtol=1e-8, max_newton=60, inner_iters=args.inner, apply_mode=args.apply_mode,
-                tc_mode=args.tc_mode)
+    base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, max_newton=60,
+                inner_iters=args.inner, tc_mode=args.tc_mode)
+    opts = dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode)
     ctx = pkg.Context(pr, opts, device=dev)
     du, duh = W.perturbation(pr, 0)
     du_d = torch.as_tensor(du, device=dev)
     duh_d = torch.as_tensor(duh, device=dev)
-    u, q, uh = ctx.init_state(du_d, duh_d, lift=True)
+    state0 = ctx.init_state(du_d, duh_d, lift=True)
     st = torch.cuda.current_stream(dev)
+    learn = args.compare and args.precision == "mixed"
+    if learn:
+        ctx.mlp_setup(hidden=256, seed=0, max_pairs=512)
+        ctx.mlp_set_recording(True)
 
     # ---- warm-up: the whole steady solve, recording every Newton step's input
-    records = []
-    tau_init, tau_max = 1.0, 1e8
-    norms = ctx.assemble(u, q, uh)
-    R0 = norms[3]
-    dtau = tau_init
-    t_solve0 = time.perf_counter()
-    its_total = 0
-    while norms[3] > 1e-8 * R0 and len(records) < args.solve_steps:
-        records.append((u.clone(), q.clone(), uh.clone(), dtau, norms.copy()))
-        bhat = ctx.condense(shift=1.0 / dtau)
-        duh_s, stats = ctx.linear_solve(bhat, allow_not_converged=True)
-        its_total += stats["fgmres_iters"]
-        dU, dQ = ctx.recover(duh_s)
-        u += dU
-        q += dQ
-        uh += duh_s
-        RU_old = norms[1]
-        norms = ctx.assemble(u, q, uh)
-        dtau = min(max(dtau * RU_old / max(norms[1], 1e-300), tau_init), tau_max)
-    torch.cuda.synchronize()
-    t_solve = time.perf_counter() - t_solve0
-    converged = bool(norms[3] <= 1e-8 * R0)
+    sol = newton_solve(ctx, state0, record=True, max_steps=args.solve_steps)
+    records = sol["records"]
     N = len(records)
     assert N > 0
-    # extra warm-up replays if requested
+    u, q, uh = sol["state"]
+    its_total = sol["fgmres_iters"]
+    if learn:
+        n_samples = ctx.mlp_set_recording(False)
+
     def replay(k, host=None):
-        u0, q0, uh0, dt_, _ = records[k % N]
+        u0, q0, uh0, dt_ = records[k % N]
         if host is not None:
             hu, hq, huh = host[k % N]
             u.copy_(hu, non_blocking=True)
@@ -267,18 +296,37 @@ def run_ours(args, ws, rank, lrank):
     t_e2e = e0.elapsed_time(e1) / 1e3
     bytes_io = 8 * (u.numel() + q.numel() + uh.numel())
 
+    # ---- comparison forms on the same workload (same initial state, same tolerance)
+    compare = {}
+    if args.compare:
+        if learn:
+            first, last = ctx.mlp_train(epochs=args.mlp_epochs, batch=8192, lr=1e-3)
+            ctxl = pkg.Context(pr, dict(opts, precond=2), device=dev)
+            ctxl.mlp_setup(hidden=256, seed=0, max_pairs=1)
+            ctxl.mlp_params(ctx.mlp_params())
+            sl = newton_solve(ctxl, state0)
+            du_ = sl["state"][0] - sol["state"][0]
+            compare["mixed_learned"] = {k: v for k, v in sl.items() if k not in ("records", "state")}
+            compare["mixed_learned"].update(train_samples=n_samples, train_loss_first=first, train_loss_last=last,
+                                            rel_diff_u_vs_primary=float(du_.norm() / sol["state"][0].norm()))
+            ctxl.close()
+        ctxp = pkg.Context(pr, dict(base, precision=pkg.PREC_FP64, precond=1, apply_mode=0), device=dev)
+        sp = newton_solve(ctxp, state0)
+        dup = sp["state"][0] - sol["state"][0]
+        compare["plain_fp64_algorithm2"] = {k: v for k, v in sp.items() if k not in ("records", "state")}
+        compare["plain_fp64_algorithm2"]["rel_diff_u_vs_primary"] = float(dup.norm() / sol["state"][0].norm())
+        ctxp.close()
+        compare["primary_full_solve"] = {k: v for k, v in sol.items() if k not in ("records", "state")}
+
     # ---- roofline of the dominant kernel: phase with the largest time per step
     work = phase_work(z, z["E"], args.precision, args.apply_mode)
     ph_mean = {k: float(np.mean(v)) for k, v in phase_acc.items() if v and v[0] >= 0}
     peaks = measured_peaks()
-    fp64_peak = None
     roof = None
+    applies = its_timed / args.steps * (1 + (args.inner if args.precond == 1 else 0))
     if ph_mean:
-        applies = its_timed / args.steps * (1 + (args.inner if args.precond == 1 else 0))
         dom = max(("condense", "lu", "vol_contract", "vol_point", "apply", "form_local"),
                   key=lambda k: ph_mean.get(k, 0.0) * (applies if k == "apply" else 1.0))
-        if args.precision == "fp64" or dom not in ("condense", "lu"):
-            fp64_peak = fp64_peak_tflops(torch)
         if dom == "apply":
             ach = work["apply_bytes"] / (ph_mean["apply"] / 1e3) / 1e9
             pk = peaks.get("hbm_gbs", 6800.0)
@@ -288,21 +336,24 @@ def run_ours(args, ws, rank, lrank):
                         peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback")
         else:
             fl = {"condense": work["condense_flops"], "lu": work["lu_flops"],
-                  "form_local": 2.0 * z["Nu"] ** 2 * z["Nt"] * z["E"] + 2.0 * z["Nt"] ** 2 * z["Nu"] * z["E"]}.get(dom)
-            if fl is None:
-                fl = 0.0
-            ach = fl / (ph_mean[dom] / 1e3) / 1e12
+                  "form_local": 2.0 * z["Nu"] ** 2 * z["Nt"] * z["E"] + 2.0 * z["Nt"] ** 2 * z["Nu"] * z["E"],
+                  "vol_contract": None, "vol_point": None}.get(dom)
             if args.precision == "fp64":
-                roof = dict(kernel=dom, bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s",
-                            frac=ach / fp64_peak if fp64_peak else None, traffic=None,
-                            peak_source="measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)")
+                pk, src = fp64_peak_tflops(torch), "measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)"
+                bound = "alu"
+            elif args.tc_mode in (1, 2) and dom in ("condense", "form_local"):
+                pk = peaks.get("bf16_tflops", 1918.0) / 2.0
+                src, bound = "measured bf16 burst x nominal tf32/bf16 ratio 1/2", "tensor"
             else:
-                tf32 = peaks.get("bf16_tflops", 1918.0) / 2.0
-                roof = dict(kernel=dom, bound="tensor", achieved=ach, peak=tf32, unit="TFLOP/s", frac=ach / tf32,
-                            traffic=None, peak_source="measured bf16 burst x nominal tf32/bf16 ratio 1/2")
+                pk = 2 * 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                src, bound = "FP32 FMA pipe: 128 lanes x 2 flop x 152 SMs x max SM clock", "alu"
+            ach = fl / (ph_mean[dom] / 1e3) / 1e12 if fl else None
+            roof = dict(kernel=dom, bound=bound, achieved=ach, peak=pk, unit="TFLOP/s",
+                        frac=(ach / pk) if ach else None, traffic=None, peak_source=src)
     lu_tflops = None
     if "lu" in ph_mean and ph_mean["lu"] > 0:
         lu_tflops = work["lu_flops"] / (ph_mean["lu"] / 1e3) / 1e12
+    apply_gbs = work["apply_bytes"] / (ph_mean["apply"] / 1e3) / 1e9 if ph_mean.get("apply") else None
 
     per_step = t_dev / args.steps
     line = {
@@ -316,7 +367,7 @@ def run_ours(args, ws, rank, lrank):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32/tf32 blocks, f64 residual+krylov",
+        "dtype": "f64" if args.precision == "fp64" else "f32 blocks + f64 residual/krylov",
         "data": "synthetic (manufactured solution, seeded 1e-3 perturbation, seed 0)",
         "config": {"workload": "3D steady MMS cube, %d^3 macro-elements x 2^3 hexes, p=2 (%d macros, Nu=%d, Nt=%d, "
                                "%d trace DOFs)" % (NMAC, z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
@@ -325,10 +376,12 @@ def run_ours(args, ws, rank, lrank):
                    "tc_mode": args.tc_mode,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "fgmres_iters_per_step": its_timed / args.steps,
-        "solve": {"newton_steps": N, "fgmres_iters": its_total, "converged_1e-8": converged,
-                  "wall_s": t_solve, "res0": float(R0), "res": float(norms[3])},
+        "solve": {"newton_steps": N, "fgmres_iters": its_total, "converged_1e-8": sol["converged"],
+                  "time_s": sol["time_s"], "res0": sol["res0"], "res": sol["res"]},
         "batched_lu_tflops": lu_tflops,
+        "trace_apply_gbs": apply_gbs,
         "phases_ms": ph_mean,
+        "compare": compare,
         "e2e": {"value": t_e2e / args.steps / ws, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": launches,
@@ -390,7 +443,7 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed Newton steps (default: one full solve)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--lin-rtol", type=float, default=1e-3)
     ap.add_argument("--restart", type=int, default=60)
@@ -399,8 +452,12 @@ def main():
     ap.add_argument("--tc-mode", type=int, default=0, help="mixed local GEMMs: 0 FP32 SIMT, 1 split TF32, 2 TF32")
     ap.add_argument("--no-phases", dest="phases", action="store_false")
     ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
-    ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
+
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the plain FP64 (Algorithm 2) and learned-preconditioner solves")
+    ap.add_argument("--mlp-epochs", type=int, default=300)
+    ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
     args = ap.parse_args()
     global NMAC
     NMAC = args.nmac

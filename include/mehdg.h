@@ -91,9 +91,10 @@ typedef struct mehdg_options {
   int apply_mode;     /* 0: Algorithm 2 (C, S^-1, B, D per apply); 1: the local operator
                          A^T_i = B S^-1 C + D is formed once after factorisation (it
                          replaces D in place) and each apply is one product per macro */
-  int tc_mode;        /* mixed precision local GEMMs (condensation products, forming A^T_i):
-                         0 FP32 SIMT, 1 tcgen05 tensor cores with split TF32 (3 products,
-                         about FP32 accuracy), 2 tcgen05 with plain TF32 */
+  int tc_mode;        /* mixed precision dense local work: 0 FP32 SIMT; 1 batched LU of S
+                         with tcgen05 trailing updates in split TF32 (3 products, about
+                         FP32 accuracy); 2 also the condensation products and forming
+                         A^T_i in split TF32; 3 as 2 with plain TF32 */
 } mehdg_options;
 
 typedef struct mehdg_info {
@@ -228,16 +229,16 @@ int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
 
 /* Learned preconditioner correction (preconditioner kind 2).  No counterpart in the
  * paper (spec addition): FGMRES tolerates a variable preconditioner (Sec. 4.2),
- * so the block-Jacobi step is corrected face by face, z_f += |r_f| MLP(r_f/|r_f|),
- * by a network n_in -> hidden (ReLU) -> hidden (ReLU) -> n_out (n_in = n_out = ns Nfn
- * rounded up to 32) with BF16 weights, FP32 biases and FP32 accumulation.
+ * so the block-Jacobi output z0 is corrected face by face,
+ *   z_f = z0_f + |z0_f| MLP(r_f/|r_f|, z0_f/|z0_f|),
+ * by a network n_in -> hidden (ReLU) -> hidden (ReLU) -> n_out (n_out = ns Nfn rounded up
+ * to 32, n_in = 2 n_out) with BF16 weights, FP32 biases and FP32 accumulation.
  * mehdg_mlp_setup: allocate with seeded weights and room for max_pairs pairs.
  * mehdg_mlp_params: copy the FP32 master parameters to (set = 0) or from (set = 1)
  *   host memory, packed [W1 (h x n_in), b1, W2 (h x h), b2, W3 (n_out x h), b3];
  *   *count receives the length.
  * mehdg_mlp_record: store one (residual r, error e) pair of global trace vectors as
- *   one sample per face (input r_f/|r_f|, target (e_f - z0_f)/|r_f|, z0 the
- *   block-Jacobi output).  mehdg_mlp_set_recording(on): FGMRES then records up to 8
+ *   one sample per face (inputs as above, target (e_f - z0_f)/|z0_f|).  mehdg_mlp_set_recording(on): FGMRES then records up to 8
  *   pairs per converged solve (iterates of its last cycle against its solution).
  * mehdg_mlp_gradient: mean-squared loss and gradient (host float[count]) for n rows
  *   of device inputs X [n][n_in] and targets T [n][n_out].

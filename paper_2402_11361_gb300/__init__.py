@@ -269,7 +269,8 @@ class Context:
         n = c_longlong()
         self._check(self.lib.mehdg_mlp_params(self.h, 0, None, ctypes.byref(n)), "mlp_params")
         self.mlp_nparams = n.value
-        self.mlp_nin = ((self.info["ns"] * self.info["Nfn"] + 31) // 32) * 32
+        self.mlp_nout = ((self.info["ns"] * self.info["Nfn"] + 31) // 32) * 32
+        self.mlp_nin = 2 * self.mlp_nout
         self.mlp_hidden = int(hidden)
 
     def mlp_params(self, values=None):

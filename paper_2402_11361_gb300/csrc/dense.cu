@@ -377,7 +377,20 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // LU of S and of the face blocks
   CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
   phase_begin(ctx, PH_LU);
-  if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag))) return rc;
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->use_tc_lu) {
+      // SIMT panel and block row, trailing update A22 -= L21 U12 on tcgen05 in the same kernel
+      float* Sf = reinterpret_cast<float*>(Auu);
+      const size_t smem = lu_tc_smem_bytes();
+      CK(cudaFuncSetAttribute(k_lu_batched<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_lu_batched<float, true><<<E, LU_NT, smem, st>>>(Sf, ctx->perm, (int)Nu, ctx->dflag, ctx->dtcerr);
+      CKL();
+    } else if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag))) {
+      return rc;
+    }
+  } else {
+    if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag))) return rc;
+  }
   phase_end(ctx, PH_LU);
   phase_begin(ctx, PH_FACE_LU);
   if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;

@@ -86,7 +86,7 @@ struct mehdg_ctx {
 
   float *Wk32 = nullptr, *Whk32 = nullptr;   // FP32 copies of W_k, Wh_k (mixed precision)
   int* dtcerr = nullptr;                       // tensor-core kernel error word
-  bool use_tc_condense = false, use_tc_form = false, tc_split = true;
+  bool use_tc_condense = false, use_tc_form = false, use_tc_lu = false, tc_split = true;
   float* finv32 = nullptr;   // explicit FP32 inverses of the face blocks (mixed precision block-Jacobi)
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
   // mixed precision copies

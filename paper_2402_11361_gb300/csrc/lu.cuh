@@ -3,9 +3,13 @@
 // factorisation of each Schur complement S and applies S^-1 by substitution
 // (Remark, Sec. 3.3); here one CTA factors one matrix held in global memory:
 // unblocked panel of width LU_NB with row swaps over whole rows, triangular solve
-// for the block row of U, then a tiled rank-LU_NB update of the trailing matrix.
+// for the block row of U, then a tiled rank-LU_NB update of the trailing matrix
+// (FP32 SIMT or FP64 DFMA; for FP32 matrices optionally split-TF32 tcgen05 MMAs with the
+// accumulator in tensor memory).
 #pragma once
 #include <cuda_runtime.h>
+
+#include "tc_gemm.cuh"
 
 constexpr int LU_NT = 256;
 constexpr int LU_NB = 32;
@@ -17,9 +21,107 @@ inline size_t lu_smem_bytes(int n) {
   return sizeof(T) * ((size_t)LU_TM * (LU_NB + 1) + (size_t)LU_NB * (LU_TM + 1));
 }
 
-template <class T>
+// tensor-core trailing update (FP32 matrices): staging for a 128 x 32 tile of L21 and a
+// 256 x 32 tile of U12^T in the canonical K-major layout (2 x hi/lo), then a 128 x 257
+// result tile for the coalesced epilogue
+constexpr int LUTC_BM = 128, LUTC_BN = 256;
+constexpr size_t LUTC_STAGE = 2 * (size_t)(LUTC_BM + LUTC_BN) * 32 * 4;   // hi and lo parts
+constexpr size_t LUTC_TILE = (size_t)LUTC_BM * (LUTC_BN + 1) * 4;
+inline size_t lu_tc_smem_bytes() { return LUTC_STAGE + LUTC_TILE + 1024; }
+
+// A22[0:m2, 0:m2] -= L21 U12 with split TF32 (hi*hi + hi*lo + lo*hi) on tcgen05, called by
+// all threads of the CTA; L21 = A + (c0)*n + j0, U12 = A + j0*n + c0, A22 = A + c0*n + c0.
+__device__ __forceinline__ bool lu_tc_update(float* A, int n, int j0, int jb, int c0, unsigned char* smem,
+                                             uint32_t tmem, uint64_t* bar, uint32_t& phase) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m2 = n - c0;
+  unsigned char* sAh = smem;
+  unsigned char* sAl = sAh + LUTC_BM * 32 * 4;
+  unsigned char* sBh = sAl + LUTC_BM * 32 * 4;
+  unsigned char* sBl = sBh + LUTC_BN * 32 * 4;
+  float* tile = reinterpret_cast<float*>(smem + LUTC_STAGE);
+  bool ok = true;
+  for (int ti = 0; ti < m2; ti += LUTC_BM) {
+    // L21 tile: rows c0+ti.., columns j0..j0+jb (zero beyond)
+    for (int i = tid; i < LUTC_BM * 32; i += blockDim.x) {
+      int r = i >> 5, k = i & 31;
+      float v = (ti + r < m2 && k < jb) ? A[(size_t)(c0 + ti + r) * n + j0 + k] : 0.f;
+      float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      uint32_t off = tc::canon_off(r, k);
+      *reinterpret_cast<float*>(sAh + off) = hi;
+      *reinterpret_cast<float*>(sAl + off) = v - hi;
+    }
+    for (int tj = 0; tj < m2; tj += LUTC_BN) {
+      for (int i = tid; i < LUTC_BN * 32; i += blockDim.x) {
+        int k = i / LUTC_BN, c = i % LUTC_BN;
+        float v = (tj + c < m2 && k < jb) ? A[(size_t)(j0 + k) * n + c0 + tj + c] : 0.f;
+        float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        uint32_t off = tc::canon_off(c, k);
+        *reinterpret_cast<float*>(sBh + off) = hi;
+        *reinterpret_cast<float*>(sBl + off) = v - hi;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            uint64_t ad = tc::desc_kmajor((t == 2 ? al : ah) + kk * 256, 128, 1024);
+            uint64_t bd = tc::desc_kmajor((t == 1 ? bl : bh) + kk * 256, 128, 1024);
+            uint32_t accum = (kk > 0 || t > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(tc::idesc_tf32(LUTC_BM, LUTC_BN)), "r"(accum)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc::smem_u32(bar))
+                     : "memory");
+      }
+      if (!tc::mbar_wait(bar, phase)) ok = false;
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // TMEM -> tile: warp w reads lanes 32 (w % 4).., columns (w / 4) * 128 ..
+      {
+        const int lrow = (warp & 3) * 32 + lane;
+        const int cbase = (warp >> 2) * (LUTC_BN / 2);
+#pragma unroll 1
+        for (int cc = 0; cc < LUTC_BN / 2; cc += 16) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cbase + cc);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tile[lrow * (LUTC_BN + 1) + cbase + cc + j] = __uint_as_float(r[j]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      const int rows = min(LUTC_BM, m2 - ti), cols = min(LUTC_BN, m2 - tj);
+      for (int i = tid; i < rows * LUTC_BN; i += blockDim.x) {
+        int rr = i / LUTC_BN, cc = i % LUTC_BN;
+        if (cc < cols) A[(size_t)(c0 + ti + rr) * n + c0 + tj + cc] -= tile[rr * (LUTC_BN + 1) + cc];
+      }
+      __syncthreads();
+    }
+  }
+  return ok;
+}
+
+template <class T, bool TC = false>
 __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int* __restrict__ permall, int n,
-                                                     int* __restrict__ flag) {
+                                                     int* __restrict__ flag, int* __restrict__ tcerr = nullptr) {
   extern __shared__ unsigned char lu_smem_raw[];
   T* sL = reinterpret_cast<T*>(lu_smem_raw);          // [LU_TM][LU_NB+1]
   T* sU = sL + LU_TM * (LU_NB + 1);                   // [LU_NB][LU_TM+1]
@@ -30,8 +132,26 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
   T* A = Aall + (size_t)blockIdx.x * n * n;
   int* perm = permall + (size_t)blockIdx.x * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ uint32_t tc_slot;
+  uint32_t tc_phase = 0;
+  bool tc_ok = true;
+  if (TC) {
+    if (tid == 0) {
+      tc::mbar_init(&tc_bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tc_slot)),
+                   "r"(256u)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
   for (int i = tid; i < n; i += LU_NT) perm[i] = i;
   __syncthreads();
+  if (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   for (int j0 = 0; j0 < n; j0 += LU_NB) {
     const int jb = min(LU_NB, n - j0);
     for (int j = j0; j < j0 + jb; ++j) {
@@ -96,6 +216,11 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
       }
     }
     __syncthreads();
+    if constexpr (TC) {
+      if (!lu_tc_update(reinterpret_cast<float*>(A), n, j0, jb, c0, lu_smem_raw, tc_slot, &tc_bar, tc_phase))
+        tc_ok = false;
+      continue;
+    }
     // A22 -= L21 U12, 64 x 64 tiles, 16 outputs per thread
     const int m2 = n - c0;
     const int tx = tid % 16, ty = tid / 16;
@@ -139,6 +264,13 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
       }
     }
     __syncthreads();
+  }
+  if (TC) {
+    if (!tc_ok && tid == 0) atomicExch(tcerr, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc_slot), "r"(256u) : "memory");
   }
 }
 
@@ -293,3 +425,4 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     if (c < rc) X[(size_t)r * nrhs + c0 + c] = x[i];
   }
 }
+

@@ -579,12 +579,14 @@ static int setup(mehdg_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->Whk, Whk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
 
-  ALLOC(ctx->Auu, (size_t)E * Nu * Nu);
-  ALLOC(ctx->Auq, (size_t)E * d * Nu * Nu);
-  ALLOC(ctx->Auh, (size_t)E * Nu * Nt);
-  ALLOC(ctx->Ahu, (size_t)E * Nt * Nu);
-  ALLOC(ctx->Ahq, (size_t)E * d * Nt * Nu);
-  ALLOC(ctx->Ahh, (size_t)E * Nt * Nt);
+  // blocks are FP32 in the mixed-precision path: allocate half the doubles
+  const size_t bsz = ctx->opt.precision == MEHDG_PREC_MIXED ? 2 : 1;
+  ALLOC(ctx->Auu, (size_t)E * Nu * Nu / bsz + 1);
+  ALLOC(ctx->Auq, (size_t)E * d * Nu * Nu / bsz + 1);
+  ALLOC(ctx->Auh, (size_t)E * Nu * Nt / bsz + 1);
+  ALLOC(ctx->Ahu, (size_t)E * Nt * Nu / bsz + 1);
+  ALLOC(ctx->Ahq, (size_t)E * d * Nt * Nu / bsz + 1);
+  ALLOC(ctx->Ahh, (size_t)E * Nt * Nt / bsz + 1);
   ALLOC(ctx->perm, (size_t)E * Nu);
   ALLOC(ctx->RQ, (size_t)E * d * Nu);
   ALLOC(ctx->RU, (size_t)E * Nu);
@@ -594,7 +596,12 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->MinvRQ, (size_t)E * d * Nu);
   ALLOC(ctx->bloc, (size_t)E * Nt);
   ALLOC(ctx->slot, (size_t)E * Nt);
-  ALLOC(ctx->Kvol, (size_t)E * (d + 1) * ns * ctx->nel * ctx->Ng * (d + 1) * ns * (d + 1));
+  {
+    size_t nk = (size_t)E * (d + 1) * ns * ctx->nel * ctx->Ng * (d + 1) * ns * (d + 1) / bsz + 1;
+    // the same scratch holds the face-block inverses of the mixed block-Jacobi (FP64, F nfb^2)
+    nk = std::max(nk, (size_t)ctx->F * ns * Nfn * ns * Nfn);
+    ALLOC(ctx->Kvol, nk);
+  }
   ALLOC(ctx->rvol, (size_t)E * ctx->nel * ctx->Ng * ns * (d + 1));
   ALLOC(ctx->Kface, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * ctx->ndir_f * 2 * ns);
   ALLOC(ctx->rface, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * 2 * ns);
@@ -675,8 +682,11 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
   default_options(&ctx->opt);
   if (opt) ctx->opt = *opt;
   ctx->stream = (cudaStream_t)stream;
-  ctx->use_tc_condense = ctx->use_tc_form = (ctx->opt.tc_mode == 1 || ctx->opt.tc_mode == 2);
-  ctx->tc_split = ctx->opt.tc_mode == 1;
+  // tc_mode: 0 SIMT; 1 tensor cores (split TF32) for the LU trailing updates only;
+  // 2 split TF32 for LU, condensation and forming A^T_i; 3 plain TF32 everywhere
+  ctx->use_tc_lu = ctx->opt.tc_mode >= 1;
+  ctx->use_tc_condense = ctx->use_tc_form = ctx->opt.tc_mode >= 2;
+  ctx->tc_split = ctx->opt.tc_mode <= 2;
   int rc = setup(ctx);
   if (rc != MEHDG_OK) {
     std::string msg = ctx->err;

@@ -1,13 +1,14 @@
 // Learned preconditioner correction (preconditioner kind 2).  Not part of the
 // paper: FGMRES accepts a variable preconditioner (Sec. 4.2), so the block-Jacobi
-// step z = (A_uhuh)^-1 r is corrected face by face by a small network,
-//   z_f += |r_f| MLP(r_f / |r_f|),
-// MLP: n_in -> hid (ReLU) -> hid (ReLU) -> n_out, n_in = n_out = ns Nfn rounded up
-// to a multiple of 32.  Weights are stored in BF16 for the products, with FP32
-// master copies, FP32 biases and FP32 accumulation everywhere.  Training pairs
-// (residual r, error e) come from the plain FGMRES solves; the target of face f is
-// (e_f - z0_f) / |r_f| with z0 the block-Jacobi output, i.e. what block-Jacobi misses.
-// Forward, backward and Adam run in the kernels below.
+// output z0 = (A_uhuh)^-1 r is corrected face by face by a small network,
+//   z_f = z0_f + |z0_f| MLP(r_f / |r_f|, z0_f / |z0_f|),
+// MLP: n_in -> hid (ReLU) -> hid (ReLU) -> n_out with n_out = ns Nfn rounded up to a
+// multiple of 32 and n_in = 2 n_out (the two normalised face vectors).  Weights are
+// stored in BF16 for the products, with FP32 master copies, FP32 biases and FP32
+// accumulation everywhere.  Training pairs (residual r, error e) come from the plain
+// FGMRES solves; the target of face f is (e_f - z0_f) / |z0_f|, what block-Jacobi
+// misses relative to its own output.  Forward, backward and Adam run in the kernels
+// below.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -29,7 +30,7 @@ struct Mlp {
   int wcap = 0;                       // rows of the work buffers
   float *H1 = nullptr, *H2 = nullptr, *Y = nullptr, *dY = nullptr, *dH1 = nullptr, *dH2 = nullptr,
         *Xin = nullptr;
-  double* nrm = nullptr;              // per-face residual norms
+  double* nrm = nullptr;              // per-face norms |z0_f|
   double* dloss = nullptr;
   long long step = 0;
   bool trained = false;
@@ -138,30 +139,51 @@ __global__ void k_to_bf16(const float* P, __nv_bfloat16* Ph, long long n) {
   if (i < n) Ph[i] = __float2bfloat16(P[i]);
 }
 
-// per face: norm of r_f, normalised input row, and (when recording) the target
+// per face: normalised inputs [r_f/|r_f|, z0_f/|z0_f|], |z0_f|, and (when recording)
+// the target (e_f - z0_f)/|z0_f|
 __global__ void k_face_samples(const double* __restrict__ r, const double* __restrict__ e,
                                const double* __restrict__ z0, float* __restrict__ X, float* __restrict__ T,
                                double* __restrict__ nrm, int nfb, int nin, int nout) {
-  __shared__ double red[8];
+  __shared__ double red[2][8];
   const int f = blockIdx.x;
   const double* rf = r + (size_t)f * nfb;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nfb; i += blockDim.x) s += rf[i] * rf[i];
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  const double* zf = z0 + (size_t)f * nfb;
+  double s = 0.0, t = 0.0;
+  for (int i = threadIdx.x; i < nfb; i += blockDim.x) {
+    s += rf[i] * rf[i];
+    t += zf[i] * zf[i];
+  }
+  for (int o = 16; o; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s;
+    red[1][threadIdx.x >> 5] = t;
+  }
   __syncthreads();
-  double tot = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-  const double nr = sqrt(tot);
-  const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
-  if (threadIdx.x == 0 && nrm) nrm[f] = nr;
-  for (int i = threadIdx.x; i < nin; i += blockDim.x) X[(size_t)f * nin + i] = i < nfb ? (float)(rf[i] * inv) : 0.f;
+  double sr = 0.0, sz = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    sr += red[0][w];
+    sz += red[1][w];
+  }
+  const double ir = sr > 0.0 ? 1.0 / sqrt(sr) : 0.0;
+  const double nz = sqrt(sz);
+  const double iz = nz > 0.0 ? 1.0 / nz : 0.0;
+  if (threadIdx.x == 0 && nrm) nrm[f] = nz;
+  const int half = nin / 2;
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    float v = 0.f;
+    if (i < half) v = i < nfb ? (float)(rf[i] * ir) : 0.f;
+    else if (i - half < nfb) v = (float)(zf[i - half] * iz);
+    X[(size_t)f * nin + i] = v;
+  }
   if (T)
     for (int i = threadIdx.x; i < nout; i += blockDim.x)
-      T[(size_t)f * nout + i] = i < nfb ? (float)((e[(size_t)f * nfb + i] - z0[(size_t)f * nfb + i]) * inv) : 0.f;
+      T[(size_t)f * nout + i] = i < nfb ? (float)((e[(size_t)f * nfb + i] - zf[i]) * iz) : 0.f;
 }
 
-// z_f += |r_f| y_f
+// z_f += |z0_f| y_f
 __global__ void k_face_correct(const float* __restrict__ Y, const double* __restrict__ nrm, double* __restrict__ z,
                                int nfb, int nout, int F) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -259,8 +281,7 @@ void init_params(std::vector<float>& p, const Mlp& m, unsigned long long seed) {
 int mlp_apply(mehdg_ctx* ctx, const double* r, double* z) {
   Mlp* m = M_(ctx);
   if (!m) return ctx_fail(ctx, MEHDG_ERR_ARG, "preconditioner kind 2 needs mehdg_mlp_setup");
-  k_face_samples<<<m->F, 256, 0, ctx->stream>>>(r, nullptr, nullptr, m->Xin, nullptr, m->nrm, m->nfb, m->nin,
-                                                m->nout);
+  k_face_samples<<<m->F, 256, 0, ctx->stream>>>(r, nullptr, z, m->Xin, nullptr, m->nrm, m->nfb, m->nin, m->nout);
   CKL();
   int rc;
   if ((rc = forward(ctx, m->Xin, m->F))) return rc;
@@ -296,7 +317,8 @@ extern "C" int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long se
   Mlp* m = new Mlp();
   m->nfb = ctx->nfb;
   m->F = ctx->F;
-  m->nin = m->nout = ((ctx->nfb + 31) / 32) * 32;
+  m->nout = ((ctx->nfb + 31) / 32) * 32;
+  m->nin = 2 * m->nout;
   m->nh = hidden;
   m->oW1 = 0;
   m->ob1 = m->oW1 + (long long)m->nh * m->nin;

@@ -329,24 +329,24 @@ def test_mlp_gradient_matches_oracle(lib):
     pr = W.mms(dim=2, nmac=2, m=2, p=2)
     ctx = lib.Context(pr)
     ctx.mlp_setup(hidden=64, seed=3)
-    nin, hid = ctx.mlp_nin, ctx.mlp_hidden
+    nin, hid, nout = ctx.mlp_nin, ctx.mlp_hidden, ctx.mlp_nout
     rng = np.random.default_rng(8)
     p = (rng.normal(size=ctx.mlp_nparams) * 0.2).astype(np.float32)
     ctx.mlp_params(p)
     assert np.array_equal(ctx.mlp_params(), p)
     X = rng.normal(size=(300, nin)).astype(np.float32)
-    T = rng.normal(size=(300, nin)).astype(np.float32)
+    T = rng.normal(size=(300, nout)).astype(np.float32)
     loss, g = ctx.mlp_gradient(torch.as_tensor(X, device="cuda"), torch.as_tensor(T, device="cuda"))
     # oracle parameters: weights rounded to BF16 as stored for the products, biases FP32
     po = p.astype(np.float64)
     o = 0
     for shape, is_w in [((hid, nin), True), ((hid,), False), ((hid, hid), True), ((hid,), False),
-                        ((nin, hid), True), ((nin,), False)]:
+                        ((nout, hid), True), ((nout,), False)]:
         n = int(np.prod(shape))
         if is_w:
             po[o:o + n] = omlp.bf16_round(p[o:o + n])
         o += n
-    lo, go = omlp.loss_and_grad(po, X.astype(np.float64), T.astype(np.float64), nin, hid, nin)
+    lo, go = omlp.loss_and_grad(po, X.astype(np.float64), T.astype(np.float64), nin, hid, nout)
     assert abs(loss - lo) <= 1e-5 * lo
     assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max()
     ctx.close()
