@@ -449,7 +449,9 @@ def main():
     ap.add_argument("--restart", type=int, default=60)
     ap.add_argument("--inner", type=int, default=10, help="inner GMRES iterations of the multi-level preconditioner")
     ap.add_argument("--apply-mode", type=int, default=1, help="0: Algorithm 2 four-step apply; 1: stored A^T_i")
-    ap.add_argument("--tc-mode", type=int, default=0, help="mixed local GEMMs: 0 FP32 SIMT, 1 split TF32, 2 TF32")
+    ap.add_argument("--tc-mode", type=int, default=0,
+                    help="mixed path: 0 FP32 SIMT; 1 tcgen05 split-TF32 LU updates; 2 also condensation and A^T_i"
+                         " products; 3 plain TF32 products")
     ap.add_argument("--no-phases", dest="phases", action="store_false")
     ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
 

@@ -21,13 +21,15 @@ namespace {
 template <int B, int E> struct IPow { static constexpr int v = B * IPow<B, E - 1>::v; };
 template <int B> struct IPow<B, 0> { static constexpr int v = 1; };
 
+template <class CT = double>
 struct Tables {
-  const double* b1;   // [NG1][P1]
-  const double* db1;  // [NG1][P1] reference derivative
-  const double* gw;   // [NG1]
+  const CT* b1;   // [NG1][P1]
+  const CT* db1;  // [NG1][P1] reference derivative
+  const CT* gw;   // [NG1]
 };
-__device__ __forceinline__ Tables tables(const double* tab, int ng1, int p1) {
-  Tables t;
+template <class CT>
+__device__ __forceinline__ Tables<CT> tables(const CT* tab, int ng1, int p1) {
+  Tables<CT> t;
   t.b1 = tab;
   t.db1 = tab + ng1 * p1;
   t.gw = tab + 2 * ng1 * p1;
@@ -35,15 +37,23 @@ __device__ __forceinline__ Tables tables(const double* tab, int ng1, int p1) {
 }
 
 // ---------------------------------------------------------------- volume pointwise
-template <int D, int P, class KT>
-__global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restrict__ tab, Phys ph,
-                                                    const double* __restrict__ u, const double* __restrict__ q,
-                                                    const double* __restrict__ hist, double coef, int supg_time,
-                                                    const double* __restrict__ src, KT* __restrict__ Kvol,
+// One thread per (macro, sub-element, Gauss point, input direction): interpolates
+// u, grad u, q, grad q at the point, evaluates the volume integrand of eqs. C38a-b
+// (with the SUPG term) on Dual numbers seeded along one input (u_s or q_js), and
+// writes the Jacobian column K[X][t][s0][.] of the integrand, pre-weighted by the
+// quadrature weight.  CT is the arithmetic type.  MODE 0 also writes the residual
+// integrand (FP64 path); MODE 1 writes the Jacobian only (mixed path, CT = float:
+// the Jacobian only shapes an inexact Newton step); MODE 2 writes the residual
+// only, one thread per point, plain FP64 values (mixed path).
+template <int D, int P, class KT, class CT = double, int MODE = 0>
+__global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__ tab, Phys ph,
+                                                    const CT* __restrict__ u, const CT* __restrict__ q,
+                                                    const CT* __restrict__ hist, double coef, int supg_time,
+                                                    const CT* __restrict__ src, KT* __restrict__ Kvol,
                                                     double* __restrict__ rvol, int E) {
   constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
-  constexpr int NDIR = NS * (1 + D);
+  constexpr int NDIR = (MODE == 2) ? 1 : NS * (1 + D);
   constexpr int KA = (D + 1) * NS * (D + 1);
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int nel = g.nel;
@@ -54,25 +64,26 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restri
   r /= NG;
   const int el = r % nel;
   const int e = (int)(r / nel);
-  Tables tb = tables(tab, NG1, P1);
+  Tables<CT> tb = tables(tab, NG1, P1);
 
   int gi[D], li[D];
-  double wq = 1.0;
+  CT wq = CT(1), he[D];
   {
     int gg = gq, ll = el;
     for (int k = 0; k < D; ++k) {
       gi[k] = gg % NG1; gg /= NG1;
       li[k] = ll % g.m; ll /= g.m;
-      wq *= tb.gw[gi[k]] * 0.5 * g.he[k];
+      he[k] = (CT)g.he[k];
+      wq *= tb.gw[gi[k]] * CT(0.5) * he[k];
     }
   }
-  double U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
+  CT U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
   for (int s = 0; s < NS; ++s) {
-    U[s] = 0.0; Hh[s] = 0.0;
+    U[s] = CT(0); Hh[s] = CT(0);
     for (int l = 0; l < D; ++l) {
-      GU[s][l] = 0.0;
-      for (int j = 0; j < D; ++j) { GQ[s][j][l] = 0.0; }
-      Q[s][l] = 0.0;
+      GU[s][l] = CT(0);
+      for (int j = 0; j < D; ++j) { GQ[s][j][l] = CT(0); }
+      Q[s][l] = CT(0);
     }
   }
   const size_t Np = g.Np;
@@ -83,12 +94,12 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restri
       a += (li[k] * P + ai[k]) * stride;
       stride *= g.n1;
     }
-    double bv[D], dv[D];
+    CT bv[D], dv[D];
     for (int k = 0; k < D; ++k) {
       bv[k] = tb.b1[gi[k] * P1 + ai[k]];
-      dv[k] = tb.db1[gi[k] * P1 + ai[k]] * 2.0 / g.he[k];
+      dv[k] = tb.db1[gi[k] * P1 + ai[k]] * CT(2) / he[k];
     }
-    double phi = 1.0, dphi[D];
+    CT phi = CT(1), dphi[D];
     for (int k = 0; k < D; ++k) phi *= bv[k];
     for (int l = 0; l < D; ++l) {
       dphi[l] = dv[l];
@@ -96,54 +107,66 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const double* __restri
         if (k != l) dphi[l] *= bv[k];
     }
     for (int s = 0; s < NS; ++s) {
-      double ua = u[((size_t)e * NS + s) * Np + a];
+      CT ua = u[((size_t)e * NS + s) * Np + a];
       U[s] += phi * ua;
       for (int l = 0; l < D; ++l) GU[s][l] += dphi[l] * ua;
       if (hist) Hh[s] += phi * hist[((size_t)e * NS + s) * Np + a];
       for (int j = 0; j < D; ++j) {
-        double qa = q[(((size_t)e * D + j) * NS + s) * Np + a];
+        CT qa = q[(((size_t)e * D + j) * NS + s) * Np + a];
         Q[s][j] += phi * qa;
         for (int l = 0; l < D; ++l) GQ[s][j][l] += dphi[l] * qa;
       }
     }
   }
-  double f[NS];
-  for (int s = 0; s < NS; ++s) f[s] = src ? src[(((size_t)e * nel + el) * NG + gq) * NS + s] : 0.0;
+  CT f[NS];
+  for (int s = 0; s < NS; ++s) f[s] = src ? src[(((size_t)e * nel + el) * NG + gq) * NS + s] : CT(0);
 
-  typedef Dual<double, 1> S;
-  const int X = dir / NS, s0 = dir % NS;
-  S Us[NS], GUs[NS][D], Qs[NS][D], GQs[NS][D][D], Ts[NS];
-  for (int s = 0; s < NS; ++s) {
-    Us[s].v = U[s]; Us[s].d[0] = (X == 0 && s == s0) ? 1.0 : 0.0;
-    for (int j = 0; j < D; ++j) {
-      Qs[s][j].v = Q[s][j]; Qs[s][j].d[0] = (X == 1 + j && s == s0) ? 1.0 : 0.0;
-      GUs[s][j].v = GU[s][j]; GUs[s][j].d[0] = 0.0;
-      for (int l = 0; l < D; ++l) { GQs[s][j][l].v = GQ[s][j][l]; GQs[s][j][l].d[0] = 0.0; }
-    }
-    Ts[s] = coef * Us[s] + Hh[s];
-  }
-  S W[NS], V[NS][D], FG[NS][D], A[D][NS][NS], tau;
-  vol_integrand<D, S>(Us, GUs, Qs, GQs, Ts, f, ph, supg_time, W, V, FG, A, tau);
-
-  for (int t = 0; t < NS; ++t) {
-    KT* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
-    K[(0 * NS + s0) * (D + 1) + 0] = (KT)(W[t].d[0] * wq);
-    for (int l = 0; l < D; ++l) K[(0 * NS + s0) * (D + 1) + 1 + l] = (KT)0;
-    for (int k = 0; k < D; ++k) {
-      K[((1 + k) * NS + s0) * (D + 1) + 0] = (KT)(V[t][k].d[0] * wq);
-      for (int l = 0; l < D; ++l) {
-        double val = 0.0;
-        if (ph.supg) {
-          for (int rr = 0; rr < NS; ++rr) val += A[k][rr][t].v * FG[rr][l].d[0];
-          val *= tau.v;
-        }
-        K[((1 + k) * NS + s0) * (D + 1) + 1 + l] = (KT)(val * wq);
-      }
-    }
-    if (dir == 0) {
+  if constexpr (MODE == 2) {
+    // residual integrand only, plain values
+    CT Ts[NS], W[NS], V[NS][D], FG[NS][D], A[D][NS][NS], tau;
+    for (int s = 0; s < NS; ++s) Ts[s] = (CT)coef * U[s] + Hh[s];
+    vol_integrand<D, CT, CT>(U, GU, Q, GQ, Ts, f, ph, supg_time, W, V, FG, A, tau);
+    for (int t = 0; t < NS; ++t) {
       double* R = rvol + (((size_t)e * nel + el) * NG + gq) * NS * (D + 1) + t * (D + 1);
-      R[0] = W[t].v * wq;
-      for (int k = 0; k < D; ++k) R[1 + k] = V[t][k].v * wq;
+      R[0] = W[t] * wq;
+      for (int k = 0; k < D; ++k) R[1 + k] = V[t][k] * wq;
+    }
+  } else {
+    typedef Dual<CT, 1> S;
+    const int X = dir / NS, s0 = dir % NS;
+    S Us[NS], GUs[NS][D], Qs[NS][D], GQs[NS][D][D], Ts[NS];
+    for (int s = 0; s < NS; ++s) {
+      Us[s].v = U[s]; Us[s].d[0] = (X == 0 && s == s0) ? CT(1) : CT(0);
+      for (int j = 0; j < D; ++j) {
+        Qs[s][j].v = Q[s][j]; Qs[s][j].d[0] = (X == 1 + j && s == s0) ? CT(1) : CT(0);
+        GUs[s][j].v = GU[s][j]; GUs[s][j].d[0] = CT(0);
+        for (int l = 0; l < D; ++l) { GQs[s][j][l].v = GQ[s][j][l]; GQs[s][j][l].d[0] = CT(0); }
+      }
+      Ts[s] = coef * Us[s] + Hh[s];
+    }
+    S W[NS], V[NS][D], FG[NS][D], A[D][NS][NS], tau;
+    vol_integrand<D, S, CT>(Us, GUs, Qs, GQs, Ts, f, ph, supg_time, W, V, FG, A, tau);
+
+    for (int t = 0; t < NS; ++t) {
+      KT* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
+      K[(0 * NS + s0) * (D + 1) + 0] = (KT)(W[t].d[0] * wq);
+      for (int l = 0; l < D; ++l) K[(0 * NS + s0) * (D + 1) + 1 + l] = (KT)0;
+      for (int k = 0; k < D; ++k) {
+        K[((1 + k) * NS + s0) * (D + 1) + 0] = (KT)(V[t][k].d[0] * wq);
+        for (int l = 0; l < D; ++l) {
+          CT val = CT(0);
+          if (ph.supg) {
+            for (int rr = 0; rr < NS; ++rr) val += A[k][rr][t].v * FG[rr][l].d[0];
+            val *= tau.v;
+          }
+          K[((1 + k) * NS + s0) * (D + 1) + 1 + l] = (KT)(val * wq);
+        }
+      }
+      if (MODE == 0 && dir == 0) {
+        double* R = rvol + (((size_t)e * nel + el) * NG + gq) * NS * (D + 1) + t * (D + 1);
+        R[0] = W[t].v * wq;
+        for (int k = 0; k < D; ++k) R[1 + k] = V[t][k].v * wq;
+      }
     }
   }
 }
@@ -335,7 +358,7 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const double* __restr
   const int sf = r % nsf; r /= nsf;
   const int fl = r % (2 * D);
   const int e = (int)(r / (2 * D));
-  Tables tb = tables(tab, NG1, P1);
+  Tables<double> tb = tables(tab, NG1, P1);
   int tang[D];
   face_axes<D>(fl, tang);
   int gi[D], si[D];
@@ -546,11 +569,30 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   constexpr int NG = IPow<P + 2, D>::v;
   {
     long long tot = (long long)E * ctx->nel * NG * NS * (1 + D);
+    const double* hist = tt ? tt->hist : nullptr;
+    const double coef = tt ? tt->coef : 0.0;
+    const int supg_time = tt ? tt->supg_time : 0;
     phase_begin(ctx, PH_VOL_POINT);
-    k_vol_point<D, P, BT><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, tt ? tt->hist : nullptr,
-                                                              tt ? tt->coef : 0.0, tt ? tt->supg_time : 0, ctx->src,
-                                                              Kvol, ctx->rvol, E);
-    CKL();
+    if constexpr (sizeof(BT) == 4) {
+      // Jacobian columns in FP32 from FP32 copies of the state; residual integrand in FP64
+      const long long nu = (long long)E * NS * ctx->Np;
+      int rc;
+      if ((rc = to_float(ctx, u, ctx->u32, nu))) return rc;
+      if ((rc = to_float(ctx, q, ctx->q32, nu * D))) return rc;
+      if (hist && (rc = to_float(ctx, hist, ctx->h32, nu))) return rc;
+      k_vol_point<D, P, float, float, 1><<<(tot + 127) / 128, 128, 0, st>>>(
+          g, ctx->tab32, ph, ctx->u32, ctx->q32, hist ? ctx->h32 : nullptr, coef, supg_time, ctx->src32, Kvol,
+          nullptr, E);
+      CKL();
+      const long long tot2 = (long long)E * ctx->nel * NG;
+      k_vol_point<D, P, float, double, 2><<<(tot2 + 127) / 128, 128, 0, st>>>(
+          g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, nullptr, ctx->rvol, E);
+      CKL();
+    } else {
+      k_vol_point<D, P, BT><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, hist, coef, supg_time,
+                                                                ctx->src, Kvol, ctx->rvol, E);
+      CKL();
+    }
     phase_end(ctx, PH_VOL_POINT);
   }
   {

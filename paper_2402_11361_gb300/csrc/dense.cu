@@ -13,6 +13,7 @@
 
 #include "internal.cuh"
 #include "lu.cuh"
+#include "lu_panel.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
@@ -104,37 +105,29 @@ int tc_gemm(mehdg_ctx* ctx, int M, int N, int K, const float* A, long long lda, 
   return MEHDG_OK;
 }
 
-// y[b] = alpha A[b] x[b] + beta y[b]; one warp per row
+// y[e][r] = -R[e][r] + sum_k sum_c A_k[e][r][c] x[e][k][c] (one warp per row, FP64 sums):
+// the condensed right-hand-side pieces g and h, all directions k in one pass over A_.q
 template <class T>
-struct GemvArgs {
-  int M, N;
-  const T* A; int lda; long long sA1, sA2;
-  const double* x; long long sx1, sx2;
-  double* y; long long sy1, sy2;
-  double alpha, beta;
-  int n2;
-};
-template <class T>
-__global__ void k_gemv(GemvArgs<T> a) {
-  const int b = blockIdx.y;
-  const int bi = b / a.n2, bj = b % a.n2;
-  const T* A = a.A + bi * a.sA1 + bj * a.sA2;
-  const double* x = a.x + bi * a.sx1 + bj * a.sx2;
-  double* y = a.y + bi * a.sy1 + bj * a.sy2;
-  const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (row >= a.M) return;
-  double s = 0.0;
-  for (int c = lane; c < a.N; c += 32) s += (double)A[(size_t)row * a.lda + c] * x[c];
+__global__ void __launch_bounds__(256) k_cond_rhs(const T* __restrict__ A, int M, int N, int d, long long sAe,
+                                                  long long sAk, const double* __restrict__ x, long long sxe,
+                                                  long long sxk, const double* __restrict__ R, double* __restrict__ y) {
+  const int e = blockIdx.y, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= M) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const T* a = A + e * sAe + k * sAk + (size_t)r * N;
+    const double* xv = x + e * sxe + k * sxk;
+    int c = lane;
+    for (; c + 32 < N; c += 64) {
+      s0 += (double)a[c] * xv[c];
+      s1 += (double)a[c + 32] * xv[c + 32];
+    }
+    for (; c < N; c += 32) s0 += (double)a[c] * xv[c];
+  }
+  double s = s0 + s1;
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = a.alpha * s + (a.beta == 0.0 ? 0.0 : a.beta * y[row]);
-}
-template <class T>
-int gemv(mehdg_ctx* ctx, const GemvArgs<T>& a, int n1) {
-  dim3 grid((a.M + 7) / 8, n1 * a.n2);
-  k_gemv<T><<<grid, 256, 0, ctx->stream>>>(a);
-  CKL();
-  return MEHDG_OK;
+  if (lane == 0) y[(size_t)e * M + r] = s - R[(size_t)e * M + r];
 }
 
 __global__ void k_to_float(const double* x, float* y, long long n) {
@@ -222,8 +215,29 @@ __global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm,
   }
 }
 
+// blocked LU with the panel in shared memory where it fits (227 KB per CTA), else the
+// global-memory variant; tc selects the tcgen05 trailing update (FP32 only)
 template <class T>
-int batched_lu_t(mehdg_ctx* ctx, T* A, int* perm, int n, int batch, int* flag) {
+int batched_lu_t(mehdg_ctx* ctx, T* A, int* perm, int n, int batch, int* flag, bool tc = false) {
+  if (batch == 0 || n == 0) return MEHDG_OK;
+  constexpr size_t kMaxSmem = 227 * 1024 - 1024;
+  if constexpr (sizeof(T) == 4) {
+    if (tc && lu_panel_smem<T, true>(n) <= kMaxSmem) {
+      const size_t smem = lu_panel_smem<T, true>(n);
+      CK(cudaFuncSetAttribute(k_lu_panel_smem<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_lu_panel_smem<T, true><<<batch, LP_NT, smem, ctx->stream>>>(A, perm, n, flag, ctx->dtcerr);
+      CKL();
+      return MEHDG_OK;
+    }
+  }
+  // small matrices (the face blocks) keep the light kernel: more CTAs per SM
+  if (n >= 256 && lu_panel_smem<T, false>(n) <= kMaxSmem) {
+    const size_t smem = lu_panel_smem<T, false>(n);
+    CK(cudaFuncSetAttribute(k_lu_panel_smem<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lu_panel_smem<T, false><<<batch, LP_NT, smem, ctx->stream>>>(A, perm, n, flag, nullptr);
+    CKL();
+    return MEHDG_OK;
+  }
   size_t smem = lu_smem_bytes<T>(n);
   CK(cudaFuncSetAttribute(k_lu_batched<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_lu_batched<T><<<batch, LU_NT, smem, ctx->stream>>>(A, perm, n, flag);
@@ -261,6 +275,13 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
 
 }  // namespace
 
+int to_float(mehdg_ctx* ctx, const double* x, float* y, long long n) {
+  if (n <= 0) return MEHDG_OK;
+  k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(x, y, n);
+  CKL();
+  return MEHDG_OK;
+}
+
 int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag) {
   return batched_lu_t<double>(ctx, A, perm, n, batch, flag);
 }
@@ -291,26 +312,17 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     k_minv_rq<<<(nvec * Np + 255) / 256, 256, 0, st>>>(ctx->Minv, ctx->RQ, ctx->MinvRQ, Np, nvec);
     CKL();
   }
-  // g = -R_U + sum_k A_uq_k[:, s] MinvRQ[k][s];  h = -R_Uh + sum_k A_uhq_k[:, s] MinvRQ[k][s]
-  CK(cudaMemcpyAsync(ctx->gv, ctx->RU, sizeof(double) * E * Nu, cudaMemcpyDeviceToDevice, st));
-  k_scale<double><<<(E * Nu + 255) / 256, 256, 0, st>>>(ctx->gv, E * Nu, -1.0);
-  CK(cudaMemcpyAsync(ctx->hv, ctx->RUh, sizeof(double) * E * Nt, cudaMemcpyDeviceToDevice, st));
-  k_scale<double><<<(E * Nt + 255) / 256, 256, 0, st>>>(ctx->hv, E * Nt, -1.0);
-  CKL();
-  for (int k = 0; k < d; ++k)
-    for (int s = 0; s < ns; ++s) {
-      GemvArgs<T> a{};
-      a.M = (int)Nu; a.N = Np;
-      a.A = Auq + (size_t)k * Nu * Nu + (size_t)s * Np; a.lda = (int)Nu; a.sA1 = d * Nu * Nu; a.sA2 = 0;
-      a.x = ctx->MinvRQ + ((size_t)k * ns + s) * Np; a.sx1 = (long long)d * Nu; a.sx2 = 0;
-      a.y = ctx->gv; a.sy1 = Nu; a.sy2 = 0;
-      a.alpha = 1.0; a.beta = 1.0; a.n2 = 1;
-      if ((rc = gemv(ctx, a, E))) return rc;
-      a.M = (int)Nt;
-      a.A = Ahq + (size_t)k * Nt * Nu + (size_t)s * Np; a.sA1 = d * Nt * Nu;
-      a.y = ctx->hv; a.sy1 = Nt;
-      if ((rc = gemv(ctx, a, E))) return rc;
-    }
+  // g = -R_U + sum_k A_uq_k MinvRQ[k];  h = -R_Uh + sum_k A_uhq_k MinvRQ[k]  (eq. ASC2b pieces)
+  {
+    dim3 grid((unsigned)((Nu + 7) / 8), (unsigned)E);
+    k_cond_rhs<T><<<grid, 256, 0, st>>>(Auq, (int)Nu, (int)Nu, d, (long long)d * Nu * Nu, (long long)Nu * Nu,
+                                        ctx->MinvRQ, (long long)d * Nu, (long long)Nu, ctx->RU, ctx->gv);
+    CKL();
+    grid.x = (unsigned)((Nt + 7) / 8);
+    k_cond_rhs<T><<<grid, 256, 0, st>>>(Ahq, (int)Nt, (int)Nu, d, (long long)d * Nt * Nu, (long long)Nt * Nu,
+                                        ctx->MinvRQ, (long long)d * Nu, (long long)Nu, ctx->RUh, ctx->hv);
+    CKL();
+  }
   // S, C, B, D
   if (shift != 0.0) {
     long long tot = (long long)E * ns * Np * Np;
@@ -377,35 +389,27 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // LU of S and of the face blocks
   CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
   phase_begin(ctx, PH_LU);
-  if constexpr (sizeof(T) == 4) {
-    if (ctx->use_tc_lu) {
-      // SIMT panel and block row, trailing update A22 -= L21 U12 on tcgen05 in the same kernel
-      float* Sf = reinterpret_cast<float*>(Auu);
-      const size_t smem = lu_tc_smem_bytes();
-      CK(cudaFuncSetAttribute(k_lu_batched<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_lu_batched<float, true><<<E, LU_NT, smem, st>>>(Sf, ctx->perm, (int)Nu, ctx->dflag, ctx->dtcerr);
-      CKL();
-    } else if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag))) {
-      return rc;
-    }
-  } else {
-    if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag))) return rc;
-  }
+  if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag, sizeof(T) == 4 && ctx->use_tc_lu)))
+    return rc;
   phase_end(ctx, PH_LU);
   phase_begin(ctx, PH_FACE_LU);
-  if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;
   if (ctx->finv32) {
-    // explicit inverses (columns of A_uhuh,f^-1) in FP64, stored in FP32 for the block-Jacobi product
-    double* tmp = ctx->Kvol;   // assembly scratch, free until the next assembly
+    // mixed path: the block-Jacobi preconditioner only needs A_uhuh,f^-1 to FP32 accuracy, so
+    // the face blocks are factored and inverted in FP32 (scratch: the assembly buffer, free
+    // until the next assembly) and the inverses land in finv32
     const int nfb = ctx->nfb;
-    size_t smem = sizeof(double) * (size_t)nfb * 32;
-    CK(cudaFuncSetAttribute(k_lu_solve_multi<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(ctx->F, (nfb + 31) / 32);
-    k_lu_solve_multi<double, 32><<<grid, 256, smem, st>>>(ctx->fblk, ctx->fperm, nullptr, tmp, nfb, nfb);
+    const long long tot = (long long)ctx->F * nfb * nfb;
+    float* f32 = reinterpret_cast<float*>(ctx->Kvol);
+    k_to_float<<<(tot + 255) / 256, 256, 0, st>>>(ctx->fblk, f32, tot);
     CKL();
-    long long tot = (long long)ctx->F * nfb * nfb;
-    k_to_float<<<(tot + 255) / 256, 256, 0, st>>>(tmp, ctx->finv32, tot);
+    if ((rc = batched_lu_t<float>(ctx, f32, ctx->fperm, nfb, ctx->F, ctx->dflag + 2))) return rc;
+    const size_t smem = sizeof(float) * (size_t)nfb * 64;
+    CK(cudaFuncSetAttribute(k_lu_solve_multi<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid(ctx->F, (nfb + 63) / 64);
+    k_lu_solve_multi<float, 64><<<grid, 256, smem, st>>>(f32, ctx->fperm, nullptr, ctx->finv32, nfb, nfb);
     CKL();
+  } else {
+    if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;
   }
   phase_end(ctx, PH_FACE_LU);
   // b^

@@ -19,8 +19,15 @@ struct Dual {
   T d[N];
 };
 
-// innermost double of a (possibly nested) scalar
+// innermost scalar type of a (possibly nested) dual; constants mixed into dual
+// arithmetic are converted to it, so that FP32 duals never compute in FP64
+template <class T> struct Base { typedef T type; };
+template <class T, int N> struct Base<Dual<T, N>> { typedef typename Base<T>::type type; };
+template <class T> HD typename Base<T>::type bcast(double c) { return static_cast<typename Base<T>::type>(c); }
+
+// innermost value of a (possibly nested) scalar, as a double
 HD double val0(double x) { return x; }
+HD double val0(float x) { return x; }
 template <class T, int N>
 HD double val0(const Dual<T, N>& x) { return val0(x.v); }
 
@@ -91,15 +98,15 @@ HD Dual<T, N> operator/(const Dual<T, N>& a, const Dual<T, N>& b) {
 }
 // mixed with plain doubles
 template <class T, int N>
-HD Dual<T, N> operator+(const Dual<T, N>& a, double b) { Dual<T, N> r = a; r.v = a.v + b; return r; }
+HD Dual<T, N> operator+(const Dual<T, N>& a, double b) { Dual<T, N> r = a; r.v = a.v + bcast<T>(b); return r; }
 template <class T, int N>
 HD Dual<T, N> operator+(double b, const Dual<T, N>& a) { return a + b; }
 template <class T, int N>
-HD Dual<T, N> operator-(const Dual<T, N>& a, double b) { Dual<T, N> r = a; r.v = a.v - b; return r; }
+HD Dual<T, N> operator-(const Dual<T, N>& a, double b) { Dual<T, N> r = a; r.v = a.v - bcast<T>(b); return r; }
 template <class T, int N>
 HD Dual<T, N> operator-(double b, const Dual<T, N>& a) {
   Dual<T, N> r;
-  r.v = b - a.v;
+  r.v = bcast<T>(b) - a.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
   return r;
@@ -107,20 +114,28 @@ HD Dual<T, N> operator-(double b, const Dual<T, N>& a) {
 template <class T, int N>
 HD Dual<T, N> operator*(const Dual<T, N>& a, double b) {
   Dual<T, N> r;
-  r.v = a.v * b;
+  const auto c = bcast<T>(b);
+  r.v = a.v * c;
 #pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * c;
   return r;
 }
 template <class T, int N>
 HD Dual<T, N> operator*(double b, const Dual<T, N>& a) { return a * b; }
 template <class T, int N>
-HD Dual<T, N> operator/(const Dual<T, N>& a, double b) { return a * (1.0 / b); }
+HD Dual<T, N> operator/(const Dual<T, N>& a, double b) {
+  const auto c = bcast<T>(1.0) / bcast<T>(b);
+  Dual<T, N> r;
+  r.v = a.v * c;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * c;
+  return r;
+}
 template <class T, int N>
 HD Dual<T, N> operator/(double b, const Dual<T, N>& a) {
   Dual<T, N> r;
   T inv = cst<T>(1.0) / a.v;
-  r.v = b * inv;
+  r.v = bcast<T>(b) * inv;
   T f = -(r.v * inv);
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
@@ -128,6 +143,7 @@ HD Dual<T, N> operator/(double b, const Dual<T, N>& a) {
 }
 // ---------------------------------------------------------------- functions
 HD double dsqrt(double x) { return sqrt(x); }
+HD float dsqrt(float x) { return sqrtf(x); }
 template <class T, int N>
 HD Dual<T, N> dsqrt(const Dual<T, N>& a) {
   Dual<T, N> r;
@@ -139,6 +155,8 @@ HD Dual<T, N> dsqrt(const Dual<T, N>& a) {
 }
 HD double dsin(double x) { return sin(x); }
 HD double dcos(double x) { return cos(x); }
+HD float dsin(float x) { return sinf(x); }
+HD float dcos(float x) { return cosf(x); }
 template <class T, int N>
 HD Dual<T, N> dsin(const Dual<T, N>& a) {
   Dual<T, N> r;
@@ -159,6 +177,7 @@ HD Dual<T, N> dcos(const Dual<T, N>& a) {
 }
 // |x| with derivative sign(x), sign(0) = 0
 HD double dabs(double x) { return x > 0 ? x : (x < 0 ? -x : 0.0); }
+HD float dabs(float x) { return x > 0 ? x : (x < 0 ? -x : 0.f); }
 template <class T, int N>
 HD Dual<T, N> dabs(const Dual<T, N>& a) {
   double s = val0(a);

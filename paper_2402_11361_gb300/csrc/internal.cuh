@@ -88,6 +88,9 @@ struct mehdg_ctx {
   int* dtcerr = nullptr;                       // tensor-core kernel error word
   bool use_tc_condense = false, use_tc_form = false, use_tc_lu = false, tc_split = true;
   float* finv32 = nullptr;   // explicit FP32 inverses of the face blocks (mixed precision block-Jacobi)
+  // mixed precision: FP32 copies of the state, history, 1D tables and source for the FP32
+  // Jacobian pass of the assembly
+  float *u32 = nullptr, *q32 = nullptr, *h32 = nullptr, *tab32 = nullptr, *src32 = nullptr;
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
   // mixed precision copies
   float *S32 = nullptr, *B32 = nullptr, *C32 = nullptr, *D32 = nullptr;
@@ -142,6 +145,7 @@ int vec_scal(mehdg_ctx* ctx, long long n, double a, double* x);
 int vec_copy(mehdg_ctx* ctx, long long n, const double* x, double* y);
 int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b, const double* y, double* z);
 int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag);
+int to_float(mehdg_ctx* ctx, const double* x, float* y, long long n);
 int mlp_apply(mehdg_ctx* ctx, const double* r, double* z);
 bool mlp_recording(const mehdg_ctx* ctx);
 int mlp_record_pair(mehdg_ctx* ctx, const double* r, const double* e);

@@ -9,6 +9,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "tc_gemm.cuh"
 
 constexpr int LU_NT = 256;
@@ -21,107 +23,9 @@ inline size_t lu_smem_bytes(int n) {
   return sizeof(T) * ((size_t)LU_TM * (LU_NB + 1) + (size_t)LU_NB * (LU_TM + 1));
 }
 
-// tensor-core trailing update (FP32 matrices): staging for a 128 x 32 tile of L21 and a
-// 256 x 32 tile of U12^T in the canonical K-major layout (2 x hi/lo), then a 128 x 257
-// result tile for the coalesced epilogue
-constexpr int LUTC_BM = 128, LUTC_BN = 256;
-constexpr size_t LUTC_STAGE = 2 * (size_t)(LUTC_BM + LUTC_BN) * 32 * 4;   // hi and lo parts
-constexpr size_t LUTC_TILE = (size_t)LUTC_BM * (LUTC_BN + 1) * 4;
-inline size_t lu_tc_smem_bytes() { return LUTC_STAGE + LUTC_TILE + 1024; }
-
-// A22[0:m2, 0:m2] -= L21 U12 with split TF32 (hi*hi + hi*lo + lo*hi) on tcgen05, called by
-// all threads of the CTA; L21 = A + (c0)*n + j0, U12 = A + j0*n + c0, A22 = A + c0*n + c0.
-__device__ __forceinline__ bool lu_tc_update(float* A, int n, int j0, int jb, int c0, unsigned char* smem,
-                                             uint32_t tmem, uint64_t* bar, uint32_t& phase) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m2 = n - c0;
-  unsigned char* sAh = smem;
-  unsigned char* sAl = sAh + LUTC_BM * 32 * 4;
-  unsigned char* sBh = sAl + LUTC_BM * 32 * 4;
-  unsigned char* sBl = sBh + LUTC_BN * 32 * 4;
-  float* tile = reinterpret_cast<float*>(smem + LUTC_STAGE);
-  bool ok = true;
-  for (int ti = 0; ti < m2; ti += LUTC_BM) {
-    // L21 tile: rows c0+ti.., columns j0..j0+jb (zero beyond)
-    for (int i = tid; i < LUTC_BM * 32; i += blockDim.x) {
-      int r = i >> 5, k = i & 31;
-      float v = (ti + r < m2 && k < jb) ? A[(size_t)(c0 + ti + r) * n + j0 + k] : 0.f;
-      float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-      uint32_t off = tc::canon_off(r, k);
-      *reinterpret_cast<float*>(sAh + off) = hi;
-      *reinterpret_cast<float*>(sAl + off) = v - hi;
-    }
-    for (int tj = 0; tj < m2; tj += LUTC_BN) {
-      for (int i = tid; i < LUTC_BN * 32; i += blockDim.x) {
-        int k = i / LUTC_BN, c = i % LUTC_BN;
-        float v = (tj + c < m2 && k < jb) ? A[(size_t)(j0 + k) * n + c0 + tj + c] : 0.f;
-        float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-        uint32_t off = tc::canon_off(c, k);
-        *reinterpret_cast<float*>(sBh + off) = hi;
-        *reinterpret_cast<float*>(sBl + off) = v - hi;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-          for (int t = 0; t < 3; ++t) {
-            uint64_t ad = tc::desc_kmajor((t == 2 ? al : ah) + kk * 256, 128, 1024);
-            uint64_t bd = tc::desc_kmajor((t == 1 ? bl : bh) + kk * 256, 128, 1024);
-            uint32_t accum = (kk > 0 || t > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(tc::idesc_tf32(LUTC_BM, LUTC_BN)), "r"(accum)
-                : "memory");
-          }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         tc::smem_u32(bar))
-                     : "memory");
-      }
-      if (!tc::mbar_wait(bar, phase)) ok = false;
-      phase ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // TMEM -> tile: warp w reads lanes 32 (w % 4).., columns (w / 4) * 128 ..
-      {
-        const int lrow = (warp & 3) * 32 + lane;
-        const int cbase = (warp >> 2) * (LUTC_BN / 2);
-#pragma unroll 1
-        for (int cc = 0; cc < LUTC_BN / 2; cc += 16) {
-          uint32_t r[16];
-          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cbase + cc);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 16; ++j) tile[lrow * (LUTC_BN + 1) + cbase + cc + j] = __uint_as_float(r[j]);
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-      const int rows = min(LUTC_BM, m2 - ti), cols = min(LUTC_BN, m2 - tj);
-      for (int i = tid; i < rows * LUTC_BN; i += blockDim.x) {
-        int rr = i / LUTC_BN, cc = i % LUTC_BN;
-        if (cc < cols) A[(size_t)(c0 + ti + rr) * n + c0 + tj + cc] -= tile[rr * (LUTC_BN + 1) + cc];
-      }
-      __syncthreads();
-    }
-  }
-  return ok;
-}
-
-template <class T, bool TC = false>
+template <class T>
 __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int* __restrict__ permall, int n,
-                                                     int* __restrict__ flag, int* __restrict__ tcerr = nullptr) {
+                                                     int* __restrict__ flag) {
   extern __shared__ unsigned char lu_smem_raw[];
   T* sL = reinterpret_cast<T*>(lu_smem_raw);          // [LU_TM][LU_NB+1]
   T* sU = sL + LU_TM * (LU_NB + 1);                   // [LU_NB][LU_TM+1]
@@ -132,26 +36,8 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
   T* A = Aall + (size_t)blockIdx.x * n * n;
   int* perm = permall + (size_t)blockIdx.x * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ __align__(8) uint64_t tc_bar;
-  __shared__ uint32_t tc_slot;
-  uint32_t tc_phase = 0;
-  bool tc_ok = true;
-  if (TC) {
-    if (tid == 0) {
-      tc::mbar_init(&tc_bar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tc_slot)),
-                   "r"(256u)
-                   : "memory");
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  }
   for (int i = tid; i < n; i += LU_NT) perm[i] = i;
   __syncthreads();
-  if (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   for (int j0 = 0; j0 < n; j0 += LU_NB) {
     const int jb = min(LU_NB, n - j0);
     for (int j = j0; j < j0 + jb; ++j) {
@@ -216,11 +102,6 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
       }
     }
     __syncthreads();
-    if constexpr (TC) {
-      if (!lu_tc_update(reinterpret_cast<float*>(A), n, j0, jb, c0, lu_smem_raw, tc_slot, &tc_bar, tc_phase))
-        tc_ok = false;
-      continue;
-    }
     // A22 -= L21 U12, 64 x 64 tiles, 16 outputs per thread
     const int m2 = n - c0;
     const int tx = tid % 16, ty = tid / 16;
@@ -264,13 +145,6 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
       }
     }
     __syncthreads();
-  }
-  if (TC) {
-    if (!tc_ok && tid == 0) atomicExch(tcerr, 1);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc_slot), "r"(256u) : "memory");
   }
 }
 
@@ -349,9 +223,7 @@ template <class T, int RC>
 __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
                                                        const T* __restrict__ Ball, T* __restrict__ Xall, int n,
                                                        int nrhs) {
-  static_assert(RC % 8 == 0 && RC <= 256, "RC");
-  constexpr int OPT = 32 * RC / 256;   // outputs per thread in a 32-row block
-  extern __shared__ unsigned char lum_raw[];
+  extern __shared__ __align__(16) unsigned char lum_raw[];
   T* x = reinterpret_cast<T*>(lum_raw);   // [n][RC]
   __shared__ T lt[32][33];
   const int e = blockIdx.x, c0 = blockIdx.y * RC;
@@ -367,13 +239,16 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     else x[i] = (c < rc && perm[r] == c0 + c) ? T(1) : T(0);   // B = I: columns of S^-1
   }
   __syncthreads();
-  // thread layout of the block update: row rr = tid / (256/32) ... 32 rows x RC columns
-  constexpr int TPR = 256 / 32;          // threads per row
-  const int rr = tid / TPR, cq = tid % TPR;
+  // block update: thread (rp, cg) accumulates rows rp and rp + 16 of the 32-row block
+  // over CPT contiguous columns (one 16-byte shared-memory load per q)
+  constexpr int CPT = RC / 16;
+  static_assert(RC % 16 == 0 && CPT * sizeof(T) == 16, "RC");
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int rp = tid / 16, cg = tid % 16;
   auto block_update = [&](int i0, int ib, int j_begin, int j_end) {
-    T acc[OPT];
+    T acc[2][CPT];
 #pragma unroll
-    for (int o = 0; o < OPT; ++o) acc[o] = T(0);
+    for (int o = 0; o < CPT; ++o) acc[0][o] = acc[1][o] = T(0);
     for (int jb = j_begin; jb < j_end; jb += 32) {
       const int jl = min(32, j_end - jb);
       for (int i = tid; i < 32 * 32; i += blockDim.x) {
@@ -381,43 +256,80 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
         lt[a][b] = (a < ib && b < jl) ? LU[(size_t)(i0 + a) * n + jb + b] : T(0);
       }
       __syncthreads();
+#pragma unroll 4
       for (int q = 0; q < jl; ++q) {
-        const T l = lt[rr][q];
-        const T* xr = x + (size_t)(jb + q) * RC;
+        const T l0 = lt[rp][q], l1 = lt[rp + 16][q];
+        const V xv = *reinterpret_cast<const V*>(x + (size_t)(jb + q) * RC + cg * CPT);
+        const T* xs = reinterpret_cast<const T*>(&xv);
 #pragma unroll
-        for (int o = 0; o < OPT; ++o) acc[o] += l * xr[cq + TPR * o];
+        for (int o = 0; o < CPT; ++o) {
+          acc[0][o] += l0 * xs[o];
+          acc[1][o] += l1 * xs[o];
+        }
       }
       __syncthreads();
     }
-    if (rr < ib) {
-      T* xo = x + (size_t)(i0 + rr) * RC;
 #pragma unroll
-      for (int o = 0; o < OPT; ++o) xo[cq + TPR * o] -= acc[o];
+    for (int h = 0; h < 2; ++h)
+      if (rp + 16 * h < ib) {
+        T* xo = x + (size_t)(i0 + rp + 16 * h) * RC + cg * CPT;
+#pragma unroll
+        for (int o = 0; o < CPT; ++o) xo[o] -= acc[h][o];
+      }
+    __syncthreads();
+  };
+  // diagonal 32 x 32 block of the factors into shared memory (zero outside the matrix)
+  auto load_diag = [&](int i0, int ib) {
+    for (int i = tid; i < 32 * 32; i += blockDim.x) {
+      int a = i / 32, b = i % 32;
+      lt[a][b] = (a < ib && b < ib) ? LU[(size_t)(i0 + a) * n + i0 + b] : T(0);
     }
     __syncthreads();
   };
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int ib = min(32, n - i0);
     if (i0 > 0) block_update(i0, ib, 0, i0);
-    for (int cc = tid; cc < RC; cc += blockDim.x)
-      for (int r = 1; r < ib; ++r) {
-        const T* row = LU + (size_t)(i0 + r) * n + i0;
+    load_diag(i0, ib);
+    // unit lower triangular solve of the block, one thread per right-hand side, in registers
+    for (int cc = tid; cc < RC; cc += blockDim.x) {
+      T v[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = (r < ib) ? x[(i0 + r) * RC + cc] : T(0);
+#pragma unroll
+      for (int r = 1; r < 32; ++r) {
         T s = T(0);
-        for (int q = 0; q < r; ++q) s += row[q] * x[(i0 + q) * RC + cc];
-        x[(i0 + r) * RC + cc] -= s;
+#pragma unroll
+        for (int q = 0; q < r; ++q) s += lt[r][q] * v[q];
+        v[r] -= s;
       }
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r < ib) x[(i0 + r) * RC + cc] = v[r];
+    }
     __syncthreads();
   }
   for (int i0 = ((n - 1) / 32) * 32; i0 >= 0; i0 -= 32) {
     const int ib = min(32, n - i0);
     if (i0 + ib < n) block_update(i0, ib, i0 + ib, n);
-    for (int cc = tid; cc < RC; cc += blockDim.x)
-      for (int r = ib - 1; r >= 0; --r) {
-        const T* row = LU + (size_t)(i0 + r) * n;
-        T s = T(0);
-        for (int q = r + 1; q < ib; ++q) s += row[i0 + q] * x[(i0 + q) * RC + cc];
-        x[(i0 + r) * RC + cc] = (x[(i0 + r) * RC + cc] - s) / row[i0 + r];
+    load_diag(i0, ib);
+    // upper triangular solve of the block (rows beyond ib are zero and skipped)
+    for (int cc = tid; cc < RC; cc += blockDim.x) {
+      T v[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) v[r] = (r < ib) ? x[(i0 + r) * RC + cc] : T(0);
+#pragma unroll
+      for (int r = 31; r >= 0; --r) {
+        if (r < ib) {
+          T s = T(0);
+#pragma unroll
+          for (int q = r + 1; q < 32; ++q) s += lt[r][q] * v[q];
+          v[r] = (v[r] - s) / lt[r][r];
+        }
       }
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r < ib) x[(i0 + r) * RC + cc] = v[r];
+    }
     __syncthreads();
   }
   for (int i = tid; i < n * RC; i += blockDim.x) {

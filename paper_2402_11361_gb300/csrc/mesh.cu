@@ -620,6 +620,12 @@ static int setup(mehdg_ctx* ctx) {
     ALLOC(ctx->Whk32, wh32.size());
     CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
+    ALLOC(ctx->u32, (size_t)E * ns * Np);
+    ALLOC(ctx->h32, (size_t)E * ns * Np);
+    ALLOC(ctx->q32, (size_t)E * d * ns * Np);
+    std::vector<float> t32(tab.begin(), tab.end());
+    ALLOC(ctx->tab32, t32.size());
+    CK(cudaMemcpy(ctx->tab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
   }
   if (ctx->opt.apply_mode == 1) {
     size_t esz = ctx->opt.precision == MEHDG_PREC_MIXED ? sizeof(float) : sizeof(double);
@@ -654,6 +660,10 @@ static int setup(mehdg_ctx* ctx) {
     if (d == 2) k_source<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->src);
     else k_source<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->src);
     CKL();
+    if (ctx->opt.precision == MEHDG_PREC_MIXED) {
+      ALLOC(ctx->src32, tot * ns);
+      if (int r_ = to_float(ctx, ctx->src, ctx->src32, tot * ns)) return r_;
+    }
   }
   {
     long long tot = (long long)E * 2 * d * ctx->nsf * ctx->nfp;
@@ -796,7 +806,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->fperm, ctx->dflag, ctx->dred, ctx->S32, ctx->B32, ctx->C32, ctx->D32, ctx->perm32,
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
-                  ctx->Whk32, ctx->dtcerr, ctx->finv32};
+                  ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);

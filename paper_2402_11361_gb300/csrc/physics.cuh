@@ -136,10 +136,10 @@ HD T supg_tau(const T* u, const Phys& ph) {
 // Volume integrand of R_U at a point: R_U[t,a] += w (phi_a W_t + sum_k d_k phi_a V_tk).
 // Also returns FG = F + G (so that outer derivatives give the flux Jacobians),
 // A[k][t][s] = dF_tk/du_s and tau (used only when SUPG is on).
-// S is double (values) or Dual<double,1> (one Jacobian column).
-template <int D, class S>
+// S is a plain scalar (values) or Dual<., 1> (one Jacobian column), in FP64 or FP32.
+template <int D, class S, class FT = double>
 HD void vol_integrand(const S* U, const S (*GU)[D], const S (*Q)[D], const S (*GQ)[D][D],
-                      const S* time, const double* f, const Phys& ph, int supg_time,
+                      const S* time, const FT* f, const Phys& ph, int supg_time,
                       S* W, S (*V)[D], S (*FG)[D], S (*A)[D + 2][D + 2], S& tau) {
   constexpr int NS = D + 2;
 #pragma unroll

@@ -114,6 +114,29 @@ def test_condensed_operators_and_rhs(condensed2d):
     assert rel(bhat.cpu().numpy(), solve.assemble_bhat(P, cond)) < 1e-10
 
 
+def test_condensed_lu_3d_p2_matches_oracle(lib):
+    """3D p = 2 macros: S is 625 x 625, so the blocked LU runs 19 full panels of 32
+    and a ragged one of 17, with multi-tile trailing updates; factors, pivot sequence,
+    condensed right-hand side and the trace apply match the oracle."""
+    pr = W.mms(dim=3, nmac=2, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 6)
+    ctx = lib.Context(pr)
+    ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    bhat = ctx.condense(shift=0.3)
+    blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    Nu = P.ns * P.Np
+    assert Nu == 625
+    for e in (0, 5):
+        assert np.array_equal(ctx.get_block(15, e).astype(int), cond[e]["piv"])
+        assert rel(ctx.get_block(0, e).reshape(Nu, Nu), cond[e]["LU"]) < 1e-10
+    assert rel(bhat.cpu().numpy(), solve.assemble_bhat(P, cond)) < 1e-10
+    x = W.random_vector(P.F * P.ns * P.Nfn, 9)
+    assert rel(ctx.apply(to_dev(x)).cpu().numpy(), solve.apply_trace(P, cond, x)) < 1e-11
+    ctx.close()
+
+
 def test_trace_apply_matches_algorithm2(condensed2d):
     P, ctx, blks, geos, cond, bhat = condensed2d
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
@@ -268,8 +291,12 @@ def test_mixed_blocks_and_apply_close_to_oracle(lib):
     assert np.allclose(norms, [onrm["RQ"], onrm["RU"], onrm["RUh"], onrm["RF"]], rtol=1e-11)   # FP64 residual
     Nu, Nt = P.ns * P.Np, P.ns * P.Nth
     for e in (0, 4):
-        assert rel(ctx.get_block(0, e).reshape(Nu, Nu), blks[e]["Auu"]) < 1e-6
-        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), blks[e]["Ahh"]) < 1e-6
+        # FP32 pointwise Jacobians (unit roundoff 2^-24 ~ 6e-8, through the ~10^2 dependent
+        # operations of the dual-number flux evaluation) stored in FP32; observed 3e-7
+        eu = rel(ctx.get_block(0, e).reshape(Nu, Nu), blks[e]["Auu"])
+        eh = rel(ctx.get_block(9, e).reshape(Nt, Nt), blks[e]["Ahh"])
+        print("mixed block errors", e, eu, eh)
+        assert eu < 3e-6 and eh < 3e-6
     ctx.condense(shift=0.3)
     cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
