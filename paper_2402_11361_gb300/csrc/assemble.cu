@@ -338,17 +338,23 @@ __device__ __forceinline__ void face_axes(int fl, int* tang) {
     if (kk != k) tang[c++] = kk;
 }
 
-template <int D, int P>
-__global__ void __launch_bounds__(128) k_face_point(Geo g, const double* __restrict__ tab, Phys ph,
+// One thread per (macro, face, sub-face, face Gauss point, input direction): the
+// trace flux of eq. C38c (or the boundary operator B^) and the numerical flux tested
+// against the volume space, differentiated along one input (u^_s, q_js or u_s).
+// MODE 0: Jacobian and residual (FP64 path); MODE 1: Jacobian only, CT = float, from
+// FP32 copies of the state (mixed path); MODE 2: residual only, one thread per point.
+template <int D, int P, class CT = double, int MODE = 0>
+__global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict__ tab, Phys ph,
                                                      mehdg_problem pr, const int* __restrict__ bkind,
                                                      const int* __restrict__ bside, const int* __restrict__ fnode,
-                                                     const int* __restrict__ gather, const double* __restrict__ uD,
-                                                     const double* __restrict__ u, const double* __restrict__ q,
-                                                     const double* __restrict__ uh, double* __restrict__ Kface,
+                                                     const int* __restrict__ gather, const CT* __restrict__ uD,
+                                                     const CT* __restrict__ u, const CT* __restrict__ q,
+                                                     const CT* __restrict__ uh, CT* __restrict__ Kface,
                                                      double* __restrict__ rface, int E) {
   constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   constexpr int NFS = IPow<P1, D - 1>::v, NFP = IPow<NG1, D - 1>::v;
-  constexpr int NDIR = NS * (D + 2);
+  constexpr int NDIR_K = NS * (D + 2);
+  constexpr int NDIR = (MODE == 2) ? 1 : NDIR_K;
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int nsf = g.nsf;
   if (tid >= (long long)E * 2 * D * nsf * NFP * NDIR) return;
@@ -358,28 +364,28 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const double* __restr
   const int sf = r % nsf; r /= nsf;
   const int fl = r % (2 * D);
   const int e = (int)(r / (2 * D));
-  Tables<double> tb = tables(tab, NG1, P1);
+  Tables<CT> tb = tables(tab, NG1, P1);
   int tang[D];
   face_axes<D>(fl, tang);
   int gi[D], si[D];
-  double wf = 1.0;
+  CT wf = CT(1);
   {
     int pp = fp, ss = sf;
     for (int c = 0; c < D - 1; ++c) {
       gi[c] = pp % NG1; pp /= NG1;
       si[c] = ss % g.m; ss /= g.m;
-      wf *= tb.gw[gi[c]] * 0.5 * g.he[tang[c]];
+      wf *= tb.gw[gi[c]] * CT(0.5) * (CT)g.he[tang[c]];
     }
   }
-  double Uf[NS], Qf[NS][D], UHf[NS];
+  CT Uf[NS], Qf[NS][D], UHf[NS];
   for (int s = 0; s < NS; ++s) {
-    Uf[s] = 0.0; UHf[s] = 0.0;
-    for (int j = 0; j < D; ++j) Qf[s][j] = 0.0;
+    Uf[s] = CT(0); UHf[s] = CT(0);
+    for (int j = 0; j < D; ++j) Qf[s][j] = CT(0);
   }
   const size_t Np = g.Np;
   for (int il = 0; il < NFS; ++il) {
     int jf = 0, stride = 1, t2 = il;
-    double psi = 1.0;
+    CT psi = CT(1);
     for (int c = 0; c < D - 1; ++c) {
       int ic = t2 % P1; t2 /= P1;
       psi *= tb.b1[gi[c] * P1 + ic];
@@ -397,44 +403,62 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const double* __restr
   for (int k = 0; k < D; ++k) n[k] = 0.0;
   n[fl / 2] = (fl % 2) ? 1.0 : -1.0;
   const int bk = bkind[e * 2 * D + fl];
-  typedef Dual<double, 1> S;
-  S Us[NS], Qs[NS][D], UHs[NS], fh[NS], eq[NS];
-  for (int s = 0; s < NS; ++s) {
-    UHs[s].v = UHf[s]; UHs[s].d[0] = (dir == s) ? 1.0 : 0.0;
-    for (int j = 0; j < D; ++j) {
-      Qs[s][j].v = Qf[s][j];
-      Qs[s][j].d[0] = (dir == NS + j * NS + s) ? 1.0 : 0.0;
+  const CT* ud = uD ? uD + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NS : nullptr;
+  if constexpr (MODE == 2) {
+    CT fh[NS], eq[NS];
+    trace_flux<D, CT>(UHf, Qf, Uf, n, ph, fh);
+    if (bk == MEHDG_BC_DIRICHLET) {
+      for (int s = 0; s < NS; ++s) eq[s] = UHf[s] - ud[s];
+    } else if (bk == MEHDG_BC_WALL) {
+      int bs = bside[e * 2 * D + fl];
+      wall_operator<D, CT>(UHf, Uf, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+    } else {
+      for (int s = 0; s < NS; ++s) eq[s] = fh[s];
     }
-    Us[s].v = Uf[s]; Us[s].d[0] = (dir == NS + NS * D + s) ? 1.0 : 0.0;
-  }
-  trace_flux<D, S>(UHs, Qs, Us, n, ph, fh);
-  if (bk == MEHDG_BC_DIRICHLET) {
-    const double* ud = uD + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NS;
-    for (int s = 0; s < NS; ++s) eq[s] = UHs[s] - ud[s];
-  } else if (bk == MEHDG_BC_WALL) {
-    int bs = bside[e * 2 * D + fl];
-    wall_operator<D, S>(UHs, Us, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
-  } else {
-    for (int s = 0; s < NS; ++s) eq[s] = fh[s];
-  }
-  double* K = Kface + (((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NDIR + dir) * 2 * NS;
-  for (int t = 0; t < NS; ++t) {
-    K[t] = fh[t].d[0] * wf;
-    K[NS + t] = eq[t].d[0] * wf;
-  }
-  if (dir == 0) {
     double* R = rface + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * 2 * NS;
     for (int t = 0; t < NS; ++t) {
-      R[t] = fh[t].v * wf;
-      R[NS + t] = eq[t].v * wf;
+      R[t] = fh[t] * wf;
+      R[NS + t] = eq[t] * wf;
+    }
+  } else {
+    typedef Dual<CT, 1> S;
+    S Us[NS], Qs[NS][D], UHs[NS], fh[NS], eq[NS];
+    for (int s = 0; s < NS; ++s) {
+      UHs[s].v = UHf[s]; UHs[s].d[0] = (dir == s) ? CT(1) : CT(0);
+      for (int j = 0; j < D; ++j) {
+        Qs[s][j].v = Qf[s][j];
+        Qs[s][j].d[0] = (dir == NS + j * NS + s) ? CT(1) : CT(0);
+      }
+      Us[s].v = Uf[s]; Us[s].d[0] = (dir == NS + NS * D + s) ? CT(1) : CT(0);
+    }
+    trace_flux<D, S>(UHs, Qs, Us, n, ph, fh);
+    if (bk == MEHDG_BC_DIRICHLET) {
+      for (int s = 0; s < NS; ++s) eq[s] = UHs[s] - (double)ud[s];
+    } else if (bk == MEHDG_BC_WALL) {
+      int bs = bside[e * 2 * D + fl];
+      wall_operator<D, S>(UHs, Us, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+    } else {
+      for (int s = 0; s < NS; ++s) eq[s] = fh[s];
+    }
+    CT* K = Kface + (((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NDIR_K + dir) * 2 * NS;
+    for (int t = 0; t < NS; ++t) {
+      K[t] = fh[t].d[0] * wf;
+      K[NS + t] = eq[t].d[0] * wf;
+    }
+    if (MODE == 0 && dir == 0) {
+      double* R = rface + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * 2 * NS;
+      for (int t = 0; t < NS; ++t) {
+        R[t] = fh[t].v * wf;
+        R[NS + t] = eq[t].v * wf;
+      }
     }
   }
 }
 
-template <int D, int P, class BT>
+template <int D, int P, class BT, class KT = double>
 __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __restrict__ tab,
                                                         const int* __restrict__ fnode,
-                                                        const double* __restrict__ Kface,
+                                                        const KT* __restrict__ Kface,
                                                         const double* __restrict__ rface, BT* Auu, BT* Auq,
                                                         BT* Auh, BT* Ahu, BT* Ahq, BT* Ahh,
                                                         double* RU, double* RUh) {
@@ -442,6 +466,7 @@ __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __re
   constexpr int NFS = IPow<P1, D - 1>::v, NFP = IPow<NG1, D - 1>::v;
   constexpr int NDIR = NS * (D + 2);
   __shared__ double spsi[NFS * NFP];
+  __shared__ KT kpsi[NFS * NFP];
   const int e = blockIdx.x;
   const size_t Nu = g.Nu, Nt = g.Nt, Np = g.Np;
   const int Nth = g.Nth, Nfn = g.Nfn;
@@ -463,9 +488,10 @@ __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __re
           t1 /= P1; t2 /= NG1;
         }
         spsi[i] = v;
+        kpsi[i] = (KT)v;
       }
       __syncthreads();
-      const double* K = Kface + (((size_t)e * 2 * D + fl) * g.nsf + sf) * NFP * NDIR * 2 * NS;
+      const KT* K = Kface + (((size_t)e * 2 * D + fl) * g.nsf + sf) * NFP * NDIR * 2 * NS;
       const double* R = rface + (((size_t)e * 2 * D + fl) * g.nsf + sf) * NFP * 2 * NS;
       // local node -> face node index and macro node
       auto jface = [&](int il) {
@@ -484,9 +510,9 @@ __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __re
         int t = (oi / (NFS * NFS)) % NS;
         int et = (oi / (NFS * NFS * NS)) % 2;
         int dir = oi / (NFS * NFS * NS * 2);
-        double sum = 0.0;
+        KT sum = KT(0);
         for (int fp = 0; fp < NFP; ++fp)
-          sum += spsi[in * NFP + fp] * K[((size_t)fp * NDIR + dir) * 2 * NS + et * NS + t] * spsi[jn * NFP + fp];
+          sum += kpsi[in * NFP + fp] * K[((size_t)fp * NDIR + dir) * 2 * NS + et * NS + t] * kpsi[jn * NFP + fp];
         int ji = jface(in), jj = jface(jn);
         int ai = fnode[fl * Nfn + ji], aj = fnode[fl * Nfn + jj];
         int s, kind, jd = 0;
@@ -610,13 +636,32 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   {
     constexpr int NFP = IPow<P + 2, D - 1>::v;
     long long tot = (long long)E * 2 * D * ctx->nsf * NFP * NS * (D + 2);
-    k_face_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, ctx->prob, ctx->bkind, ctx->bside,
-                                                           ctx->fnode, ctx->gather, ctx->uD, u, q, uh,
-                                                           ctx->Kface, ctx->rface, E);
-    CKL();
-    k_face_contract<D, P, BT><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, ctx->Kface, ctx->rface, Auu, Auq,
-                                                  Auh, Ahu, Ahq, Ahh, ctx->RU, ctx->RUh);
-    CKL();
+    if constexpr (sizeof(BT) == 4) {
+      // Jacobian in FP32 (state copies made for the volume pass), residual in FP64
+      int rc;
+      if ((rc = to_float(ctx, uh, ctx->uh32, ctx->ntr))) return rc;
+      float* Kf = reinterpret_cast<float*>(ctx->Kface);
+      k_face_point<D, P, float, 1><<<(tot + 127) / 128, 128, 0, st>>>(
+          g, ctx->tab32, ph, ctx->prob, ctx->bkind, ctx->bside, ctx->fnode, ctx->gather, ctx->uD32, ctx->u32,
+          ctx->q32, ctx->uh32, Kf, nullptr, E);
+      CKL();
+      const long long tot2 = (long long)E * 2 * D * ctx->nsf * NFP;
+      k_face_point<D, P, double, 2><<<(tot2 + 127) / 128, 128, 0, st>>>(
+          g, ctx->tab, ph, ctx->prob, ctx->bkind, ctx->bside, ctx->fnode, ctx->gather, ctx->uD, u, q, uh, nullptr,
+          ctx->rface, E);
+      CKL();
+      k_face_contract<D, P, BT, float><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, Kf, ctx->rface, Auu, Auq, Auh,
+                                                          Ahu, Ahq, Ahh, ctx->RU, ctx->RUh);
+      CKL();
+    } else {
+      k_face_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, ctx->prob, ctx->bkind, ctx->bside,
+                                                             ctx->fnode, ctx->gather, ctx->uD, u, q, uh,
+                                                             ctx->Kface, ctx->rface, E);
+      CKL();
+      k_face_contract<D, P, BT><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, ctx->Kface, ctx->rface, Auu, Auq,
+                                                    Auh, Ahu, Ahq, Ahh, ctx->RU, ctx->RUh);
+      CKL();
+    }
   }
   {
     long long tot = (long long)E * ctx->Nq;

@@ -91,6 +91,7 @@ struct mehdg_ctx {
   // mixed precision: FP32 copies of the state, history, 1D tables and source for the FP32
   // Jacobian pass of the assembly
   float *u32 = nullptr, *q32 = nullptr, *h32 = nullptr, *tab32 = nullptr, *src32 = nullptr;
+  float *uD32 = nullptr, *uh32 = nullptr;
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
   // mixed precision copies
   float *S32 = nullptr, *B32 = nullptr, *C32 = nullptr, *D32 = nullptr;

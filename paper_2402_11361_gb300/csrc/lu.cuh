@@ -213,19 +213,27 @@ __device__ void lu_solve_block(const T* __restrict__ LU, int n, Acc* y) {
 
 // X = S^-1 B for a block of RC right-hand-side columns of one macro-element
 // (grid: macro x column block), from the LU factors and row permutation of S.
-// B and X are row-major [n][nrhs]; the RC columns live in shared memory.  Blocked
-// substitution: for each 32-row block the update from the solved rows is a small
-// GEMM (32 x done) x (done x RC) with 32 x 32 tiles of L or U staged in shared
-// memory and 8 outputs per thread in registers; then the 32 x 32 diagonal block is
-// solved column by column (one thread per right-hand side).
-// B == nullptr solves for the identity (columns of S^-1).
+// B and X are row-major [n][nrhs]; the RC columns of P B live in shared memory.
+// Right-looking blocked substitution: for each 32-row block, the diagonal block of
+// L (or U) is staged in shared memory and the block's rows are solved in registers
+// (one thread per right-hand side); then every row below (forward) or above
+// (backward) is updated, x_r -= L[r, blk] x_blk, in chunks of 128 rows: the chunk of
+// L is staged in shared memory (prefetched into registers while the previous chunk
+// computes) and each thread keeps an 8-row x CPT-column tile of the update in
+// registers.  B == nullptr solves for the identity (columns of S^-1).
 template <class T, int RC>
 __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
                                                        const T* __restrict__ Ball, T* __restrict__ Xall, int n,
                                                        int nrhs) {
+  constexpr int CH = 128;                 // rows per update chunk
+  constexpr int CPT = RC / 16;            // columns per thread in the update
+  constexpr int PF = CH * 32 / 256;       // chunk elements per thread
+  static_assert(RC % 16 == 0 && CPT * sizeof(T) == 16, "RC");
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   extern __shared__ __align__(16) unsigned char lum_raw[];
   T* x = reinterpret_cast<T*>(lum_raw);   // [n][RC]
-  __shared__ T lt[32][33];
+  __shared__ T lt[32][33];                // diagonal block
+  __shared__ T ls[CH][33];                // update chunk of L or U
   const int e = blockIdx.x, c0 = blockIdx.y * RC;
   const int rc = min(RC, nrhs - c0);
   const T* LU = LUall + (size_t)e * n * n;
@@ -238,59 +246,65 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     if (Bm) x[i] = (c < rc) ? Bm[(size_t)perm[r] * nrhs + c0 + c] : T(0);
     else x[i] = (c < rc && perm[r] == c0 + c) ? T(1) : T(0);   // B = I: columns of S^-1
   }
-  __syncthreads();
-  // block update: thread (rp, cg) accumulates rows rp and rp + 16 of the 32-row block
-  // over CPT contiguous columns (one 16-byte shared-memory load per q)
-  constexpr int CPT = RC / 16;
-  static_assert(RC % 16 == 0 && CPT * sizeof(T) == 16, "RC");
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int rp = tid / 16, cg = tid % 16;
-  auto block_update = [&](int i0, int ib, int j_begin, int j_end) {
-    T acc[2][CPT];
+  const int tr = tid / 16, tcol = (tid % 16) * CPT;   // update tile: rows tr*8.., columns tcol..
+  T pf[PF];
+  // chunk rows [r0, r1) x block columns [i0, i0 + ib) into registers (zero outside)
+  auto fetch = [&](int r0, int r1, int i0, int ib) {
 #pragma unroll
-    for (int o = 0; o < CPT; ++o) acc[0][o] = acc[1][o] = T(0);
-    for (int jb = j_begin; jb < j_end; jb += 32) {
-      const int jl = min(32, j_end - jb);
-      for (int i = tid; i < 32 * 32; i += blockDim.x) {
-        int a = i / 32, b = i % 32;
-        lt[a][b] = (a < ib && b < jl) ? LU[(size_t)(i0 + a) * n + jb + b] : T(0);
-      }
-      __syncthreads();
+    for (int j = 0; j < PF; ++j) {
+      const int i = tid + 256 * j, rr = i / 32, kk = i % 32;
+      pf[j] = (r0 + rr < r1 && kk < ib) ? LU[(size_t)(r0 + rr) * n + i0 + kk] : T(0);
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      const int i = tid + 256 * j;
+      ls[i / 32][i % 32] = pf[j];
+    }
+  };
+  // x[r0 + rr] -= ls[rr] . x[i0 .. i0 + ib) for the rows of the chunk
+  auto update = [&](int r0, int r1, int i0, int ib) {
+    T acc[8][CPT];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int o = 0; o < CPT; ++o) acc[a][o] = T(0);
 #pragma unroll 4
-      for (int q = 0; q < jl; ++q) {
-        const T l0 = lt[rp][q], l1 = lt[rp + 16][q];
-        const V xv = *reinterpret_cast<const V*>(x + (size_t)(jb + q) * RC + cg * CPT);
-        const T* xs = reinterpret_cast<const T*>(&xv);
+    for (int q = 0; q < ib; ++q) {
+      const V xv = *reinterpret_cast<const V*>(x + (size_t)(i0 + q) * RC + tcol);
+      const T* xs = reinterpret_cast<const T*>(&xv);
 #pragma unroll
-        for (int o = 0; o < CPT; ++o) {
-          acc[0][o] += l0 * xs[o];
-          acc[1][o] += l1 * xs[o];
-        }
+      for (int a = 0; a < 8; ++a) {
+        const T l = ls[tr * 8 + a][q];
+#pragma unroll
+        for (int o = 0; o < CPT; ++o) acc[a][o] += l * xs[o];
       }
-      __syncthreads();
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-      if (rp + 16 * h < ib) {
-        T* xo = x + (size_t)(i0 + rp + 16 * h) * RC + cg * CPT;
+    for (int a = 0; a < 8; ++a) {
+      const int r = r0 + tr * 8 + a;
+      if (r < r1) {
+        T* xo = x + (size_t)r * RC + tcol;
 #pragma unroll
-        for (int o = 0; o < CPT; ++o) xo[o] -= acc[h][o];
+        for (int o = 0; o < CPT; ++o) xo[o] -= acc[a][o];
       }
-    __syncthreads();
+    }
   };
-  // diagonal 32 x 32 block of the factors into shared memory (zero outside the matrix)
   auto load_diag = [&](int i0, int ib) {
     for (int i = tid; i < 32 * 32; i += blockDim.x) {
       int a = i / 32, b = i % 32;
       lt[a][b] = (a < ib && b < ib) ? LU[(size_t)(i0 + a) * n + i0 + b] : T(0);
     }
-    __syncthreads();
   };
+  __syncthreads();
+  // ---- forward: L y = P b (unit diagonal)
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int ib = min(32, n - i0);
-    if (i0 > 0) block_update(i0, ib, 0, i0);
     load_diag(i0, ib);
-    // unit lower triangular solve of the block, one thread per right-hand side, in registers
+    int r0 = i0 + ib;
+    if (r0 < n) fetch(r0, n, i0, ib);
+    __syncthreads();
     for (int cc = tid; cc < RC; cc += blockDim.x) {
       T v[32];
 #pragma unroll
@@ -306,13 +320,21 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
       for (int r = 0; r < 32; ++r)
         if (r < ib) x[(i0 + r) * RC + cc] = v[r];
     }
+    for (; r0 < n; r0 += CH) {
+      stash();
+      __syncthreads();
+      if (r0 + CH < n) fetch(r0 + CH, n, i0, ib);
+      update(r0, min(r0 + CH, n), i0, ib);
+      __syncthreads();
+    }
     __syncthreads();
   }
+  // ---- backward: U x = y
   for (int i0 = ((n - 1) / 32) * 32; i0 >= 0; i0 -= 32) {
     const int ib = min(32, n - i0);
-    if (i0 + ib < n) block_update(i0, ib, i0 + ib, n);
     load_diag(i0, ib);
-    // upper triangular solve of the block (rows beyond ib are zero and skipped)
+    if (i0 > 0) fetch(0, i0, i0, ib);
+    __syncthreads();
     for (int cc = tid; cc < RC; cc += blockDim.x) {
       T v[32];
 #pragma unroll
@@ -330,6 +352,13 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
       for (int r = 0; r < 32; ++r)
         if (r < ib) x[(i0 + r) * RC + cc] = v[r];
     }
+    for (int r0 = 0; r0 < i0; r0 += CH) {
+      stash();
+      __syncthreads();
+      if (r0 + CH < i0) fetch(r0 + CH, i0, i0, ib);
+      update(r0, min(r0 + CH, i0), i0, ib);
+      __syncthreads();
+    }
     __syncthreads();
   }
   for (int i = tid; i < n * RC; i += blockDim.x) {
@@ -337,4 +366,3 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     if (c < rc) X[(size_t)r * nrhs + c0 + c] = x[i];
   }
 }
-

@@ -672,6 +672,11 @@ static int setup(mehdg_ctx* ctx) {
     if (d == 2) k_dirichlet<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
     else k_dirichlet<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
     CKL();
+    if (ctx->opt.precision == MEHDG_PREC_MIXED) {
+      ALLOC(ctx->uD32, tot * ns);
+      if (int r_ = to_float(ctx, ctx->uD, ctx->uD32, tot * ns)) return r_;
+      ALLOC(ctx->uh32, ctx->ntr);
+    }
   }
   CK(cudaStreamSynchronize(st));
   return MEHDG_OK;
@@ -806,7 +811,8 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->fperm, ctx->dflag, ctx->dred, ctx->S32, ctx->B32, ctx->C32, ctx->D32, ctx->perm32,
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
-                  ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32};
+                  ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
+                  ctx->uD32, ctx->uh32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
