@@ -187,102 +187,120 @@ template <int D, int P, class CT = double> struct VolCfg {
   static constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   static constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
   static constexpr int KA = (D + 1) * NS * (D + 1);
-  static constexpr int ZG = (D + 1) * NS * NLOC;          // Z entries per Gauss point
+  static constexpr int NCOL = NS * NLOC;                  // output columns (s, b)
+  static constexpr int ZG = (D + 1) * NCOL;               // Z entries per Gauss point
+  static constexpr int TG = (D + 1) * NLOC;               // basis entries per Gauss point
   static constexpr int GC = (ZG * 8 <= 1536) ? 32 : (ZG <= 600 ? 16 : 8);
-  static constexpr int NT = (NLOC * NS * NLOC > 8192) ? 512 : (NLOC * NS * NLOC > 1024 ? 256 : 128);
-  static constexpr int NOUT = NLOC * NS * NLOC;
-  static constexpr int OPT = (NOUT + NT - 1) / NT;
-  static constexpr size_t SMEM = sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + 2 * NG1 * P1);
+  static constexpr int RG = (NLOC + 15) / 16;             // row groups
+  static constexpr int RPT = (NLOC + RG - 1) / RG;        // output rows per thread
+  static constexpr int ITEMS = NCOL * RG;                 // (column, row group) items
+  static constexpr int NT0 = (ITEMS + 31) / 32 * 32;
+  static constexpr int NT = NT0 > 512 ? 512 : NT0;
+  static constexpr int OPT = (ITEMS + NT - 1) / NT;
+  static constexpr size_t SMEM = sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + (size_t)GC * TG);
 };
 
 // A_X[(t, A)][(s, B)] += sum_g sum_{alpha,beta} T[g][alpha][a] K[g][alpha][s][beta] T[g][beta][b]
+// per sub-element: with Z[g][alpha][(s, b)] = sum_beta K[g][alpha][s][beta] T[g][beta][b],
+// the output block is the product T^T Z over the (g, alpha) index.  Per chunk of Gauss
+// points the basis values T and Z are tabulated in shared memory; each thread owns one
+// output column (s, b) and RPT rows a, so a step of the product costs one Z load, RPT
+// broadcast T loads and RPT FMAs.
 template <int D, int P, class CT>
 __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, const double* __restrict__ tab,
                                                                       const CT* __restrict__ Kvol,
                                                                       CT* __restrict__ Auu, CT* __restrict__ Auq) {
   typedef VolCfg<D, P, CT> C;
   constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, ZG = C::ZG;
-  constexpr int GC = C::GC, NT = C::NT, OPT = C::OPT, NOUT = C::NOUT;
+  constexpr int TG = C::TG, NCOL = C::NCOL, GC = C::GC, NT = C::NT, OPT = C::OPT, RPT = C::RPT;
+  constexpr int ITEMS = C::ITEMS;
   extern __shared__ unsigned char smem_raw[];
-  CT* sK = reinterpret_cast<CT*>(smem_raw);
-  CT* sZ = sK + GC * KA;
-  CT* sb = sZ + GC * ZG;
-  CT* sdb = sb + NG1 * P1;
+  CT* sK = reinterpret_cast<CT*>(smem_raw);   // [GC][KA]
+  CT* sZ = sK + GC * KA;                      // [GC][D+1][NCOL]
+  CT* sT = sZ + GC * ZG;                      // [GC][D+1][NLOC]
   const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z;
   const int tid = threadIdx.x;
-  for (int i = tid; i < NG1 * P1; i += NT) {
-    sb[i] = (CT)tab[i];
-    sdb[i] = (CT)tab[NG1 * P1 + i];
-  }
   CT sc[D];
   for (int k = 0; k < D; ++k) sc[k] = (CT)(2.0 / g.he[k]);
   const size_t Nu = g.Nu, Np = g.Np;
   CT* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
-  // per-thread output coordinates
-  int oa[OPT], os[OPT], ob[OPT];
+  int icol[OPT], irow[OPT];
   for (int o = 0; o < OPT; ++o) {
-    int oi = tid + o * NT;
-    if (oi >= NOUT) oi = NOUT - 1;
-    oa[o] = oi / (NS * NLOC);
-    os[o] = (oi / NLOC) % NS;
-    ob[o] = oi % NLOC;
+    int w = tid + o * NT;
+    if (w >= ITEMS) w = ITEMS - 1;
+    icol[o] = w % NCOL;
+    irow[o] = (w / NCOL) * RPT;
   }
-  __syncthreads();
   for (int el = 0; el < g.nel; ++el) {
     int li[D];
     {
       int ll = el;
       for (int k = 0; k < D; ++k) { li[k] = ll % g.m; ll /= g.m; }
     }
-    CT acc[OPT];
-    for (int o = 0; o < OPT; ++o) acc[o] = CT(0);
+    CT acc[OPT][RPT];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o)
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) acc[o][r] = CT(0);
     const CT* Kel = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * g.nel + el) * (size_t)NG * KA;
     for (int g0 = 0; g0 < NG; g0 += GC) {
       const int gc = min(GC, NG - g0);
       for (int i = tid; i < gc * KA; i += NT) sK[i] = Kel[(size_t)g0 * KA + i];
-      __syncthreads();
-      for (int idx = tid; idx < gc * ZG; idx += NT) {
-        int b = idx % NLOC;
-        int s = (idx / NLOC) % NS;
-        int al = (idx / (NLOC * NS)) % (D + 1);
-        int gg = idx / ZG;
-        int gi[D], bi[D];
-        int t1 = g0 + gg, t2 = b;
-        for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; bi[k] = t2 % P1; t2 /= P1; }
-        const CT* Kp = sK + gg * KA + (al * NS + s) * (D + 1);
-        CT z = CT(0);
-#pragma unroll
-        for (int be = 0; be <= D; ++be) z += Kp[be] * basis_T<D, P, CT>(sb, sdb, sc, gi, bi, be);
-        sZ[idx] = z;
+      // T[g][alpha][a]: value (alpha 0) or derivative along x_{alpha-1} of basis a at point g
+      for (int i = tid; i < gc * TG; i += NT) {
+        const int a = i % NLOC, al = (i / NLOC) % (D + 1), gg = i / TG;
+        int t1 = g0 + gg, t2 = a;
+        CT v = CT(1);
+        for (int k = 0; k < D; ++k) {
+          const int gk = t1 % NG1, ak = t2 % P1;
+          t1 /= NG1; t2 /= P1;
+          v *= (al == 1 + k) ? (CT)tab[NG1 * P1 + gk * P1 + ak] * sc[k] : (CT)tab[gk * P1 + ak];
+        }
+        sT[i] = v;
       }
       __syncthreads();
-      for (int o = 0; o < OPT; ++o) {
-        int ai[D];
-        int t2 = oa[o];
-        for (int k = 0; k < D; ++k) { ai[k] = t2 % P1; t2 /= P1; }
-        CT sum = CT(0);
-        for (int gg = 0; gg < gc; ++gg) {
-          int gi[D];
-          int t1 = g0 + gg;
-          for (int k = 0; k < D; ++k) { gi[k] = t1 % NG1; t1 /= NG1; }
+      for (int i = tid; i < gc * ZG; i += NT) {
+        const int col = i % NCOL, al = (i / NCOL) % (D + 1), gg = i / ZG;
+        const int s = col / NLOC, b = col % NLOC;
+        const CT* Kp = sK + gg * KA + (al * NS + s) * (D + 1);
+        const CT* Tp = sT + gg * TG + b;
+        CT z = CT(0);
 #pragma unroll
-          for (int al = 0; al <= D; ++al)
-            sum += basis_T<D, P, CT>(sb, sdb, sc, gi, ai, al) * sZ[gg * ZG + (al * NS + os[o]) * NLOC + ob[o]];
+        for (int be = 0; be <= D; ++be) z += Kp[be] * Tp[be * NLOC];
+        sZ[i] = z;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) {
+        for (int k = 0; k < gc * (D + 1); ++k) {
+          const CT z = sZ[k * NCOL + icol[o]];
+          const CT* Tk = sT + k * NLOC + irow[o];
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) acc[o][r] += Tk[min(r, NLOC - 1 - irow[o])] * z;
         }
-        acc[o] += sum;
       }
       __syncthreads();
     }
+#pragma unroll
     for (int o = 0; o < OPT; ++o) {
-      int oi = tid + o * NT;
-      if (oi >= NOUT) break;
-      int A = 0, B = 0, sa = 1, t1 = oa[o], t2 = ob[o];
+      if (tid + o * NT >= ITEMS) break;
+      const int s = icol[o] / NLOC, b = icol[o] % NLOC;
+      int B = 0, sa = 1, t2 = b;
       for (int k = 0; k < D; ++k) {
-        A += (li[k] * P + t1 % P1) * sa;
         B += (li[k] * P + t2 % P1) * sa;
-        t1 /= P1; t2 /= P1; sa *= g.n1;
+        t2 /= P1; sa *= g.n1;
       }
-      out[((size_t)t * Np + A) * Nu + (size_t)os[o] * Np + B] += acc[o];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int a = irow[o] + r;
+        if (a >= NLOC) break;
+        int A = 0, sb = 1, t1 = a;
+        for (int k = 0; k < D; ++k) {
+          A += (li[k] * P + t1 % P1) * sb;
+          t1 /= P1; sb *= g.n1;
+        }
+        out[((size_t)t * Np + A) * Nu + (size_t)s * Np + B] += acc[o][r];
+      }
     }
     __syncthreads();
   }

@@ -81,6 +81,114 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs<T, TB> a) {
     }
 }
 
+// Second-layer condensation products of one (macro e, species s) pair in one GEMM
+// (eq. ASC2a with the lifting factorisation of Sec. 3.2), P = [A_.q_1[:, s] | ... |
+// A_.q_d[:, s]] [W_1 | -Wh_1; ...; W_d | -Wh_d]:
+//   S_s -= P[:, W part],  C_s -= P[:, Wh part]   (C = -A_uuh + sum A_uq Wh)
+//   B_s -= P[:, W part],  D_s += P[:, Wh part]   (D = A_uhuh - sum A_uhq Wh).  K = d*Np concatenates the directions, so
+// each output is read and written once; the right factor [W | -Wh] is shared by all
+// macros.  Tile 128 x 96 x 16, 8 x 6 outputs per thread, next K tile prefetched into
+// registers while the current one is multiplied.
+template <class T>
+struct CondArgs {
+  const T* A; long long sAe, sAk; int lda, M;   // A_.q: [e][k][M][lda]
+  const T* Bc; int N, K, Np, Nth, ns;           // [K][N] = [d*Np][Np + Nth]
+  T* O1; long long sO1e; int ldo1;              // S or B: columns s*Np + j
+  T* O2; long long sO2e; int ldo2;              // C or D: columns s*Nth + j - Np
+  int o2_add;                                   // 1: O2 += P (D), 0: O2 -= P (C)
+};
+constexpr int CG_BM = 128, CG_BN = 96, CG_BK = 16;
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondArgs<T> a) {
+  __shared__ __align__(16) T sA[CG_BK][CG_BM + 4];
+  __shared__ __align__(16) T sB[CG_BK][CG_BN];
+  const int es = blockIdx.z, e = es / a.ns, s = es % a.ns;
+  const int m0 = blockIdx.y * CG_BM, n0 = blockIdx.x * CG_BN;
+  const int tid = threadIdx.x, tm = tid / 16, tn = tid % 16;
+  const T* Ae = a.A + e * a.sAe + (size_t)s * a.Np;
+  constexpr int LA = CG_BM * CG_BK / 256, LB = CG_BK * CG_BN / 256;
+  T ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < LA; ++j) {
+      const int i = tid + 256 * j, r = i / CG_BK, kq = i % CG_BK;
+      const int gr = m0 + r, kk = k0 + kq;
+      T v = T(0);
+      if (gr < a.M && kk < a.K) {
+        const int k = kk / a.Np, c = kk - k * a.Np;
+        v = Ae[k * a.sAk + (size_t)gr * a.lda + c];
+      }
+      ra[j] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+      const int i = tid + 256 * j, r = i / CG_BN, c = i % CG_BN;
+      const int kk = k0 + r, gc = n0 + c;
+      rb[j] = (kk < a.K && gc < a.N) ? a.Bc[(size_t)kk * a.N + gc] : T(0);
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int j = 0; j < LA; ++j) {
+      const int i = tid + 256 * j;
+      sA[i % CG_BK][i / CG_BK] = ra[j];
+    }
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+      const int i = tid + 256 * j;
+      sB[i / CG_BN][i % CG_BN] = rb[j];
+    }
+  };
+  T acc[8][6];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) acc[i][j] = T(0);
+  fetch(0);
+  for (int k0 = 0; k0 < a.K; k0 += CG_BK) {
+    stash();
+    __syncthreads();
+    if (k0 + CG_BK < a.K) fetch(k0 + CG_BK);
+#pragma unroll
+    for (int kk = 0; kk < CG_BK; ++kk) {
+      T av[8], bv[6];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) av[i] = sA[kk][tm * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) bv[j] = sB[kk][tn * 6 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = m0 + tm * 8 + i;
+    if (r >= a.M) continue;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int c = n0 + tn * 6 + j;
+      if (c >= a.N) continue;
+      if (c < a.Np) {
+        a.O1[e * a.sO1e + (size_t)r * a.ldo1 + (size_t)s * a.Np + c] -= acc[i][j];
+      } else {
+        T* p = a.O2 + e * a.sO2e + (size_t)r * a.ldo2 + (size_t)s * a.Nth + (c - a.Np);
+        *p = a.o2_add ? *p + acc[i][j] : *p - acc[i][j];
+      }
+    }
+  }
+}
+
+template <class T>
+int cond_gemm(mehdg_ctx* ctx, const CondArgs<T>& a, int E) {
+  dim3 grid((a.N + CG_BN - 1) / CG_BN, (a.M + CG_BM - 1) / CG_BM, (unsigned)(E * a.ns));
+  k_cond_gemm<T><<<grid, 256, 0, ctx->stream>>>(a);
+  CKL();
+  return MEHDG_OK;
+}
+
 template <class T, class TB>
 int gemm(mehdg_ctx* ctx, const GemmArgs<T, TB>& a, int n1) {
   dim3 grid((a.N + TN - 1) / TN, (a.M + TM - 1) / TM, n1 * a.n2);
@@ -331,8 +439,22 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   }
   k_scale<T><<<(E * Nu * Nt + 255) / 256, 256, 0, st>>>(Auh, E * Nu * Nt, -1.0);
   CKL();
-  for (int k = 0; k < d; ++k) {
-    if (sizeof(T) == 4 && ctx->use_tc_condense) {
+  if (!(sizeof(T) == 4 && ctx->use_tc_condense)) {
+    // [S | C] -= A_uq [W | -Wh],  [B | -D] -= A_uhq [W | -Wh]  (all directions in one K)
+    CondArgs<T> a{};
+    a.Bc = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)ctx->Bcat32 : (const void*)ctx->Bcat);
+    a.N = Np + Nth; a.K = d * Np; a.Np = Np; a.Nth = Nth; a.ns = ns;
+    a.A = Auq; a.sAe = (long long)d * Nu * Nu; a.sAk = (long long)Nu * Nu; a.lda = (int)Nu; a.M = (int)Nu;
+    a.O1 = Auu; a.sO1e = (long long)Nu * Nu; a.ldo1 = (int)Nu;
+    a.O2 = Auh; a.sO2e = (long long)Nu * Nt; a.ldo2 = (int)Nt; a.o2_add = 0;
+    if ((rc = cond_gemm(ctx, a, E))) return rc;
+    a.A = Ahq; a.sAe = (long long)d * Nt * Nu; a.sAk = (long long)Nt * Nu; a.lda = (int)Nu; a.M = (int)Nt;
+    a.O1 = Ahu; a.sO1e = (long long)Nt * Nu; a.ldo1 = (int)Nu;
+    a.O2 = Ahh; a.sO2e = (long long)Nt * Nt; a.ldo2 = (int)Nt; a.o2_add = 1;
+    if ((rc = cond_gemm(ctx, a, E))) return rc;
+  }
+  if (sizeof(T) == 4 && ctx->use_tc_condense) {
+    for (int k = 0; k < d; ++k) {
       // S[:, s] -= A_uq_k[:, s] W_k ; C[:, s] += A_uq_k[:, s] Wh_k ; B[:, s] -= A_uhq_k[:, s] W_k ;
       // D[:, s] -= A_uhq_k[:, s] Wh_k   (batch = (macro, species s))
       const float* W32 = ctx->Wk32 + (size_t)k * Np * Np;
@@ -355,35 +477,7 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
       if ((rc = tc_gemm(ctx, (int)Nt, Nth, Np, Ahq_k, Nu, d * Nt * Nu, Np, Wh32, Nth, 0, 0, Ahh_f, Nt, Nt * Nt, Nth,
                         -1.f, 1.f, E, ns)))
         return rc;
-      continue;
     }
-    GemmArgs<T> a{};
-    a.n2 = ns;
-    a.alpha = -1.0; a.beta = 1.0;
-    // S[:, s blk] -= A_uq_k[:, s blk] W_k
-    a.M = (int)Nu; a.N = Np; a.K = Np;
-    a.A = Auq + (size_t)k * Nu * Nu; a.lda = (int)Nu; a.sA1 = d * Nu * Nu; a.sA2 = Np;
-    a.B = ctx->Wk + (size_t)k * Np * Np; a.ldb = Np; a.sB1 = 0; a.sB2 = 0;
-    a.C = Auu; a.ldc = (int)Nu; a.sC1 = Nu * Nu; a.sC2 = Np;
-    if ((rc = gemm(ctx, a, E))) return rc;
-    // C[:, s trace blk] += A_uq_k[:, s blk] Wh_k
-    a.alpha = 1.0;
-    a.N = Nth;
-    a.B = ctx->Whk + (size_t)k * Np * Nth; a.ldb = Nth;
-    a.C = Auh; a.ldc = (int)Nt; a.sC1 = Nu * Nt; a.sC2 = Nth;
-    if ((rc = gemm(ctx, a, E))) return rc;
-    // B[:, s blk] -= A_uhq_k[:, s blk] W_k
-    a.alpha = -1.0;
-    a.M = (int)Nt; a.N = Np;
-    a.A = Ahq + (size_t)k * Nt * Nu; a.sA1 = d * Nt * Nu;
-    a.B = ctx->Wk + (size_t)k * Np * Np; a.ldb = Np;
-    a.C = Ahu; a.ldc = (int)Nu; a.sC1 = Nt * Nu; a.sC2 = Np;
-    if ((rc = gemm(ctx, a, E))) return rc;
-    // D[:, s trace blk] -= A_uhq_k[:, s blk] Wh_k
-    a.N = Nth;
-    a.B = ctx->Whk + (size_t)k * Np * Nth; a.ldb = Nth;
-    a.C = Ahh; a.ldc = (int)Nt; a.sC1 = Nt * Nt; a.sC2 = Nth;
-    if ((rc = gemm(ctx, a, E))) return rc;
   }
   phase_end(ctx, PH_CONDENSE);
   // LU of S and of the face blocks

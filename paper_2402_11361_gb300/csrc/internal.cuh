@@ -68,6 +68,8 @@ struct mehdg_ctx {
   double* Ghk = nullptr;     // [d][Np][Nth]
   double* Wk = nullptr;      // [d][Np][Np]   M^-1 G_k
   double* Whk = nullptr;     // [d][Np][Nth]  M^-1 Gh_k
+  double* Bcat = nullptr;    // [d*Np][Np+Nth] = [W_k | -Wh_k] stacked over k (fused condensation GEMM)
+  float* Bcat32 = nullptr;   // FP32 copy (mixed precision)
   double* src = nullptr;     // [E][nel][Ng][ns] or null
   double* uD = nullptr;      // [E][2d][nsf][nfp][ns] or null
 

@@ -39,10 +39,11 @@ inline size_t lu_panel_smem(int n) {
   return p + sizeof(T) * (size_t)LP_NB * (LP_TM + 1);
 }
 
-__device__ __forceinline__ void lp_warp_argmax(double& bv, int& bi) {
+template <class T>
+__device__ __forceinline__ void lp_warp_argmax(T& bv, int& bi) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
     if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
   }
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
   extern __shared__ __align__(128) unsigned char lp_raw[];
   T* sP = reinterpret_cast<T*>(lp_raw);   // [n][LP_LDP], rows j0.. of the current panel
   unsigned char* sX = lp_raw + (sizeof(T) * (size_t)n * LP_LDP + 127) / 128 * 128;
-  __shared__ double rv[LP_NT / 32];
+  __shared__ T rv[LP_NT / 32];   // pivot candidates, compared in the matrix's own precision
   __shared__ int ri[LP_NT / 32];
   __shared__ int spiv[LP_NB];
   __shared__ int topsrc[LP_NB], xsrc[LP_NB], xdst[LP_NB];
@@ -181,10 +182,10 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
     }
     __syncthreads();
     {
-      double bv = -1.0;
+      T bv = T(-1);
       int bi = m;
       for (int i = tid; i < m; i += LP_NT) {
-        const double v = fabs((double)sP[i * LP_LDP]);
+        const T v = fabs(sP[i * LP_LDP]);
         if (v > bv) { bv = v; bi = i; }
       }
       lp_warp_argmax(bv, bi);
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
     }
     __syncthreads();
     for (int j = 0; j < jb; ++j) {
-      double b = rv[0];
+      T b = rv[0];
       int r = ri[0];
 #pragma unroll
       for (int w = 1; w < LP_NT / 32; ++w)
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
       if (r >= m) r = j;   // no finite candidate (NaN column): keep the row
       if (tid == 0) {
         spiv[j] = r;
-        if (b == 0.0 && atomicCAS(flag, 0, 1) == 0) flag[1] = blockIdx.x + 1;
+        if (b == T(0) && atomicCAS(flag, 0, 1) == 0) flag[1] = blockIdx.x + 1;
       }
       if (r != j && tid < LP_NB) {
         const T t = sP[j * LP_LDP + tid];
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
       __syncthreads();
       const T piv = sP[j * LP_LDP + j];
       const T inv = (piv != T(0)) ? T(1) / piv : T(0);
-      double bv = -1.0;
+      T bv = T(-1);
       int bi = m;
       for (int i = j + 1 + tid; i < m; i += LP_NT) {
         T* row = sP + i * LP_LDP;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
         row[j] = l;
         for (int c = j + 1; c < jb; ++c) row[c] -= l * sP[j * LP_LDP + c];
         if (j + 1 < jb) {
-          const double v = fabs((double)row[j + 1]);
+          const T v = fabs(row[j + 1]);
           if (v > bv) { bv = v; bi = i; }
         }
       }
@@ -307,43 +308,65 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
       T* sU = reinterpret_cast<T*>(sX);   // [LP_NB][LP_TM + 1]
       const int m2 = n - c0;
       const int tx = tid % 16, ty = tid / 16;
-      for (int ti = 0; ti < m2; ti += LP_TM) {
-        for (int tj = 0; tj < m2; tj += LP_TM) {
-          for (int i = tid; i < LP_NB * LP_TM; i += LP_NT) {
-            const int rr = i / LP_TM, cc = i % LP_TM;
-            const int gc = c0 + tj + cc;
-            sU[rr * (LP_TM + 1) + cc] = (gc < n) ? A[(size_t)(j0 + rr) * n + gc] : T(0);
-          }
-          __syncthreads();
-          T acc[4][4];
+      const int nt = (m2 + LP_TM - 1) / LP_TM, ntiles = nt * nt;
+      constexpr int RU = LP_NB * LP_TM / LP_NT;
+      T ru[RU];
+      // U12 tile (32 x 64) of column block tj into registers
+      auto fetch_u = [&](int tj) {
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-          int prow[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) prow[a] = min(jb + ti + ty + 16 * a, m - 1) * LP_LDP;
-#pragma unroll 8
-          for (int kk = 0; kk < LP_NB; ++kk) {
-            T lv[4], uv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) lv[a] = sP[prow[a] + kk];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) uv[b] = sU[kk * (LP_TM + 1) + tx + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const int gr = c0 + ti + ty + 16 * a, gc = c0 + tj + tx + 16 * b;
-              if (gr < n && gc < n) A[(size_t)gr * n + gc] -= acc[a][b];
-            }
-          __syncthreads();
+        for (int j = 0; j < RU; ++j) {
+          const int i = tid + LP_NT * j, rr = i / LP_TM, cc = i % LP_TM;
+          const int gc = c0 + tj + cc;
+          ru[j] = (gc < n) ? A[(size_t)(j0 + rr) * n + gc] : T(0);
         }
+      };
+      fetch_u(0);
+      for (int t = 0; t < ntiles; ++t) {
+        const int ti = (t / nt) * LP_TM, tj = (t % nt) * LP_TM;
+        // the 4 x 4 entries of A22 this thread updates, loaded before the product
+        T a22[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int gr = c0 + ti + ty + 16 * a, gc = c0 + tj + tx + 16 * b;
+            a22[a][b] = (gr < n && gc < n) ? A[(size_t)gr * n + gc] : T(0);
+          }
+#pragma unroll
+        for (int j = 0; j < RU; ++j) {
+          const int i = tid + LP_NT * j;
+          sU[(i / LP_TM) * (LP_TM + 1) + i % LP_TM] = ru[j];
+        }
+        __syncthreads();
+        if (t + 1 < ntiles) fetch_u(((t + 1) % nt) * LP_TM);
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+        int prow[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) prow[a] = min(jb + ti + ty + 16 * a, m - 1) * LP_LDP;
+#pragma unroll 8
+        for (int kk = 0; kk < LP_NB; ++kk) {
+          T lv[4], uv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) lv[a] = sP[prow[a] + kk];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) uv[b] = sU[kk * (LP_TM + 1) + tx + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int gr = c0 + ti + ty + 16 * a, gc = c0 + tj + tx + 16 * b;
+            if (gr < n && gc < n) A[(size_t)gr * n + gc] = a22[a][b] - acc[a][b];
+          }
+        __syncthreads();
       }
     }
   }

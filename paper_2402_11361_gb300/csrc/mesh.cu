@@ -577,6 +577,24 @@ static int setup(mehdg_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->Ghk, Ghk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Wk, Wk.data(), sizeof(double) * d * Np * Np, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Whk, Whk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
+  {
+    // right factor of the fused condensation GEMM: [W_1 | -Wh_1; ...; W_d | -Wh_d], [d*Np][Np+Nth]
+    const int nc = Np + Nth;
+    std::vector<double> bc((size_t)d * Np * nc);
+    for (int k = 0; k < d; ++k)
+      for (int c = 0; c < Np; ++c) {
+        double* row = bc.data() + ((size_t)k * Np + c) * nc;
+        for (int j = 0; j < Np; ++j) row[j] = Wk[((size_t)k * Np + c) * Np + j];
+        for (int j = 0; j < Nth; ++j) row[Np + j] = -Whk[((size_t)k * Np + c) * Nth + j];
+      }
+    ALLOC(ctx->Bcat, bc.size());
+    CK(cudaMemcpy(ctx->Bcat, bc.data(), sizeof(double) * bc.size(), cudaMemcpyHostToDevice));
+    if (ctx->opt.precision == MEHDG_PREC_MIXED) {
+      std::vector<float> bc32(bc.begin(), bc.end());
+      ALLOC(ctx->Bcat32, bc32.size());
+      CK(cudaMemcpy(ctx->Bcat32, bc32.data(), sizeof(float) * bc32.size(), cudaMemcpyHostToDevice));
+    }
+  }
   CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
 
   // blocks are FP32 in the mixed-precision path: allocate half the doubles
@@ -812,7 +830,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
-                  ctx->uD32, ctx->uh32};
+                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
