@@ -104,6 +104,12 @@ struct mehdg_ctx {
   double *V = nullptr, *Zk = nullptr, *wv = nullptr, *tv = nullptr, *tv2 = nullptr, *rv = nullptr;
   double *iV = nullptr, *iw = nullptr;    // inner GMRES
   double* xstart = nullptr;               // FGMRES iterate at the start of the current cycle
+  double* dHo = nullptr;                  // device Hessenberg, rotations, rhs of the outer FGMRES
+  double* dHi = nullptr;                  // the same for the inner GMRES
+  double *gin = nullptr, *gout = nullptr; // fixed in/out vectors of the captured inner GMRES
+  cudaGraphExec_t ig_exec = nullptr;      // inner GMRES as one CUDA graph
+  long long ig_nodes = 0;                 // kernels per replay of that graph
+  bool ig_failed = false, capturing = false;
   // Newton / DIRK
   double *un = nullptr, *ustage = nullptr, *hist = nullptr, *du = nullptr, *dq = nullptr, *duh = nullptr,
          *bhat = nullptr;

@@ -72,6 +72,78 @@ __global__ void k_lincomb(long long n, double a, const double* x, double b, cons
   if (k < n) z[k] = a * x[k] + b * y[k];
 }
 
+// ---------------------------------------------------------------- device-side Arnoldi
+// The orthogonalisation coefficients, the Hessenberg matrix and the Givens rotations
+// stay on the device, so an Arnoldi step needs no host round trip: the outer FGMRES
+// reads back one residual estimate per iteration, and the inner GMRES of the
+// multi-level preconditioner (a fixed number of steps) runs as one CUDA graph.
+
+// sum of the partials of vector i -> out[i]; with H, also H[i][col] (= or +=)
+__global__ void k_mdot_final_h(const double* __restrict__ part, double* __restrict__ out, double* __restrict__ H,
+                               int ldh, int col, int accumulate) {
+  __shared__ double red[RB];
+  const int i = blockIdx.x;
+  red[threadIdx.x] = part[(size_t)i * RB + threadIdx.x];
+  __syncthreads();
+  for (int s = RB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[i] = red[0];
+    if (H) H[(size_t)i * ldh + col] = accumulate ? H[(size_t)i * ldh + col] + red[0] : red[0];
+  }
+}
+// v = w / sqrt(*dot) (v = 0 if the norm is 0); thread 0 stores the norm in *nrm
+__global__ void k_normalize(long long n, const double* __restrict__ dot, const double* __restrict__ w,
+                            double* __restrict__ v, double* __restrict__ nrm) {
+  const double s = sqrt(fmax(*dot, 0.0));
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k == 0 && nrm) *nrm = s;
+  if (k < n) v[k] = w[k] * inv;
+}
+__global__ void k_set(double* p, double v) { *p = v; }
+// Hessenberg block on the device: H [(m+1) x m] row-major, cs [m], sn [m], g [m+1]
+struct DevHess {
+  double *H, *cs, *sn, *g;
+  int m;
+};
+__device__ void givens_column(DevHess h, int j) {
+  const int m = h.m;
+  for (int i = 0; i < j; ++i) {
+    const double a = h.H[(size_t)i * m + j], b = h.H[(size_t)(i + 1) * m + j];
+    h.H[(size_t)i * m + j] = h.cs[i] * a + h.sn[i] * b;
+    h.H[(size_t)(i + 1) * m + j] = -h.sn[i] * a + h.cs[i] * b;
+  }
+  const double a = h.H[(size_t)j * m + j], b = h.H[(size_t)(j + 1) * m + j];
+  const double rr = hypot(a, b);
+  if (rr == 0.0) { h.cs[j] = 1.0; h.sn[j] = 0.0; }
+  else { h.cs[j] = a / rr; h.sn[j] = b / rr; }
+  h.H[(size_t)j * m + j] = rr;
+  h.H[(size_t)(j + 1) * m + j] = 0.0;
+  h.g[j + 1] = -h.sn[j] * h.g[j];
+  h.g[j] = h.cs[j] * h.g[j];
+}
+// rotate column j; out[0] = |residual estimate|, out[1] = H[j+1][j] before the rotation
+__global__ void k_givens_step(DevHess h, int j, double* out) {
+  out[1] = h.H[(size_t)(j + 1) * h.m + j];
+  givens_column(h, j);
+  out[0] = fabs(h.g[j + 1]);
+}
+// least squares of a fresh (unrotated) k-column Hessenberg: rotate, back-substitute -> y
+__global__ void k_lsq(DevHess h, int k, const double* __restrict__ beta, double* __restrict__ y) {
+  for (int i = 0; i <= k; ++i) h.g[i] = 0.0;
+  h.g[0] = *beta;
+  for (int j = 0; j < k; ++j) givens_column(h, j);
+  for (int i = k - 1; i >= 0; --i) {
+    double s = h.g[i];
+    for (int c = i + 1; c < k; ++c) s -= h.H[(size_t)i * h.m + c] * y[c];
+    const double d = h.H[(size_t)i * h.m + i];
+    y[i] = (d != 0.0) ? s / d : 0.0;
+  }
+}
+
 // block-Jacobi: z_f = (A_uhuh,f)^-1 r_f
 __global__ void __launch_bounds__(128) k_block_jacobi(const double* __restrict__ fblk, const int* __restrict__ fperm,
                                                       const double* __restrict__ r, double* __restrict__ z, int nfb) {
@@ -133,28 +205,55 @@ int maxpy(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* 
   return MEHDG_OK;
 }
 
-// Givens-based least squares for the small Hessenberg problem (host)
+// scratch in dred after the reduction results: [RED_OUT .. +128) results, +128 coefficients
+constexpr size_t RED_SCAL = RED_OUT + 256;   // device scalars (norms, residual estimates)
+
+// out[0..nv) = V_i . w, on the device (no host copy); with H, also H[i][col]
+int mdot_dev(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* w, long long n, double* out,
+             double* H = nullptr, int ldh = 0, int col = 0, int accumulate = 0) {
+  dim3 grid(RB, nv);
+  k_mdot_part<<<grid, 256, 0, ctx->stream>>>(V, ldv, nv, w, n, ctx->dred);
+  CKL();
+  k_mdot_final_h<<<nv, RB, 0, ctx->stream>>>(ctx->dred, out, H, ldh, col, accumulate);
+  CKL();
+  return MEHDG_OK;
+}
+
+// CGS2 step on the device: w -= V[0..j] (V^T w) twice (coefficients summed into H[.][j]),
+// H[j+1][j] = |w|, V[j+1] = w / |w|
+int arnoldi_dev(mehdg_ctx* ctx, double* V, int j, double* w, long long n, DevHess h) {
+  double* coef = ctx->dred + RED_OUT;
+  int rc;
+  for (int pass = 0; pass < 2; ++pass) {
+    if ((rc = mdot_dev(ctx, V, n, j + 1, w, n, coef, h.H, h.m, j, pass))) return rc;
+    k_maxpy<<<(n + 255) / 256, 256, 0, ctx->stream>>>(V, n, j + 1, coef, w, n, -1.0);
+    CKL();
+  }
+  double* dot = ctx->dred + RED_SCAL;
+  if ((rc = mdot_dev(ctx, w, n, 1, w, n, dot))) return rc;
+  k_normalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dot, w, V + (size_t)(j + 1) * n,
+                                                         h.H + (size_t)(j + 1) * h.m + j);
+  CKL();
+  return MEHDG_OK;
+}
+
+DevHess dev_hess(double* base, int m) {
+  DevHess h;
+  h.m = m;
+  h.H = base;
+  h.cs = base + (size_t)(m + 1) * m;
+  h.sn = h.cs + m;
+  h.g = h.sn + m;
+  return h;
+}
+
+// host copy of a rotated Hessenberg (upper triangular part) and its right-hand side,
+// for the back-substitution of a cycle's iterates
 struct Hess {
   int m;
-  std::vector<double> H, cs, sn, g;
-  explicit Hess(int m_) : m(m_), H((m_ + 1) * m_, 0.0), cs(m_, 0.0), sn(m_, 0.0), g(m_ + 1, 0.0) {}
+  std::vector<double> H, g;
+  explicit Hess(int m_) : m(m_), H((m_ + 1) * m_, 0.0), g(m_ + 1, 0.0) {}
   double& h(int i, int j) { return H[(size_t)i * m + j]; }
-  // rotate column j (already holding the new Arnoldi coefficients); returns |residual|
-  double rotate(int j) {
-    for (int i = 0; i < j; ++i) {
-      double t = cs[i] * h(i, j) + sn[i] * h(i + 1, j);
-      h(i + 1, j) = -sn[i] * h(i, j) + cs[i] * h(i + 1, j);
-      h(i, j) = t;
-    }
-    double rr = std::hypot(h(j, j), h(j + 1, j));
-    if (rr == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-    else { cs[j] = h(j, j) / rr; sn[j] = h(j + 1, j) / rr; }
-    h(j, j) = rr;
-    h(j + 1, j) = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    return std::fabs(g[j + 1]);
-  }
   std::vector<double> solve(int k) {
     std::vector<double> y(k, 0.0);
     for (int i = k - 1; i >= 0; --i) {
@@ -165,29 +264,6 @@ struct Hess {
     return y;
   }
 };
-
-// CGS2 step: orthogonalise w against V[0..j], H column j, then normalise into V[j+1]
-int arnoldi_cgs2(mehdg_ctx* ctx, double* V, int j, double* w, long long n, Hess& hs, double* hnorm) {
-  std::vector<double> h(j + 1);
-  for (int pass = 0; pass < 2; ++pass) {
-    int rc = mdot(ctx, V, n, j + 1, w, n, h.data());
-    if (rc) return rc;
-    rc = maxpy(ctx, V, n, j + 1, h.data(), w, n, -1.0);
-    if (rc) return rc;
-    for (int i = 0; i <= j; ++i) hs.h(i, j) += h[i];
-  }
-  double nn;
-  int rc = mdot(ctx, w, n, 1, w, n, &nn);
-  if (rc) return rc;
-  nn = std::sqrt(nn);
-  hs.h(j + 1, j) = nn;
-  *hnorm = nn;
-  if (nn > 0.0) {
-    k_lincomb<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, 1.0 / nn, w, 0.0, w, V + (size_t)(j + 1) * n);
-    CKL();
-  }
-  return MEHDG_OK;
-}
 
 }  // namespace
 
@@ -230,33 +306,69 @@ static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
   return MEHDG_OK;
 }
 
-// kind 1: nu steps of GMRES on A^ left-preconditioned by block-Jacobi, from z = 0
-static int inner_gmres(mehdg_ctx* ctx, const double* r, double* z) {
+// kind 1: nu steps of GMRES on A^ left-preconditioned by block-Jacobi, from z = 0,
+// entirely on the device (fixed step count: no convergence test, no host round trip)
+static int inner_gmres_dev(mehdg_ctx* ctx, const double* r, double* z) {
   const long long n = ctx->ntr;
   const int nu = std::min(120, std::max(1, ctx->opt.inner_iters));
   int rc;
   double* IV = ctx->iV;
+  DevHess h = dev_hess(ctx->dHi, nu);
+  double* beta = ctx->dred + RED_SCAL + 1;
+  double* dot = ctx->dred + RED_SCAL + 2;
+  double* y = ctx->dred + RED_SCAL + 8;
+  CK(cudaMemsetAsync(h.H, 0, sizeof(double) * (size_t)(nu + 1) * nu, ctx->stream));
   if ((rc = block_jacobi(ctx, r, ctx->iw))) return rc;
-  double beta;
-  if ((rc = vec_dot(ctx, ctx->iw, ctx->iw, n, &beta))) return rc;
-  beta = std::sqrt(beta);
-  CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
-  if (beta == 0.0) return MEHDG_OK;
-  if ((rc = vec_lincomb(ctx, n, 1.0 / beta, ctx->iw, 0.0, ctx->iw, IV))) return rc;
-  Hess hs(nu);
-  hs.g[0] = beta;
-  int k = 0;
+  if ((rc = mdot_dev(ctx, ctx->iw, n, 1, ctx->iw, n, dot))) return rc;
+  k_normalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dot, ctx->iw, IV, beta);
+  CKL();
   for (int j = 0; j < nu; ++j) {
     if ((rc = apply_trace_impl(ctx, IV + (size_t)j * n, ctx->tv))) return rc;
     if ((rc = block_jacobi(ctx, ctx->tv, ctx->iw))) return rc;
-    double hn;
-    if ((rc = arnoldi_cgs2(ctx, IV, j, ctx->iw, n, hs, &hn))) return rc;
-    hs.rotate(j);
-    k = j + 1;
-    if (hn == 0.0) break;
+    if ((rc = arnoldi_dev(ctx, IV, j, ctx->iw, n, h))) return rc;
   }
-  std::vector<double> y = hs.solve(k);
-  return maxpy(ctx, IV, n, k, y.data(), z, n, 1.0);
+  k_lsq<<<1, 1, 0, ctx->stream>>>(h, nu, beta, y);
+  CKL();
+  CK(cudaMemsetAsync(z, 0, sizeof(double) * n, ctx->stream));
+  k_maxpy<<<(n + 255) / 256, 256, 0, ctx->stream>>>(IV, n, nu, y, z, n, 1.0);
+  CKL();
+  return MEHDG_OK;
+}
+
+// The inner GMRES is captured once per context into a CUDA graph on fixed input and
+// output buffers (all other pointers are fixed for the context's lifetime); each call
+// copies r in, replays the graph and copies z out.
+static int inner_gmres(mehdg_ctx* ctx, const double* r, double* z) {
+  const long long n = ctx->ntr;
+  if (!ctx->ig_exec && !ctx->ig_failed) {
+    cudaGraph_t graph = nullptr;
+    const long long l0 = ctx->launches;
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      ctx->capturing = true;
+      int rc = inner_gmres_dev(ctx, ctx->gin, ctx->gout);
+      ctx->capturing = false;
+      cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+      if (rc == MEHDG_OK && ec == cudaSuccess && graph &&
+          cudaGraphInstantiate(&ctx->ig_exec, graph, 0) == cudaSuccess) {
+        ctx->ig_nodes = ctx->launches - l0;
+      } else {
+        ctx->ig_exec = nullptr;
+        ctx->ig_failed = true;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      ctx->launches = l0;
+      cudaGetLastError();
+    } else {
+      ctx->ig_failed = true;
+      cudaGetLastError();
+    }
+  }
+  if (!ctx->ig_exec) return inner_gmres_dev(ctx, r, z);
+  CK(cudaMemcpyAsync(ctx->gin, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaGraphLaunch(ctx->ig_exec, ctx->stream));
+  ctx->launches += ctx->ig_nodes;
+  CK(cudaMemcpyAsync(z, ctx->gout, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  return MEHDG_OK;
 }
 
 int precond_impl(mehdg_ctx* ctx, int kind, const double* r, double* z) {
@@ -296,15 +408,23 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
     if ((rc = vec_lincomb(ctx, n, 1.0 / beta, ctx->rv, 0.0, ctx->rv, ctx->V))) return rc;
     Hess hs(m);
     hs.g[0] = beta;
+    DevHess dh = dev_hess(ctx->dHo, m);
+    CK(cudaMemsetAsync(dh.H, 0, sizeof(double) * ((size_t)(m + 1) * m + 3 * (size_t)m + 1), ctx->stream));
+    k_set<<<1, 1, 0, ctx->stream>>>(dh.g, beta);
+    CKL();
+    double* est = ctx->dred + RED_SCAL + 4;
     int k = 0;
     bool fallback = false;
     for (int j = 0; j < m; ++j) {
       double* Zj = ctx->Zk + (size_t)j * n;
       if ((rc = precond_impl(ctx, kind, ctx->V + (size_t)j * n, Zj))) return rc;
       if ((rc = apply_trace_impl(ctx, Zj, ctx->wv))) return rc;
-      double hn;
-      if ((rc = arnoldi_cgs2(ctx, ctx->V, j, ctx->wv, n, hs, &hn))) return rc;
-      double res = hs.rotate(j);
+      if ((rc = arnoldi_dev(ctx, ctx->V, j, ctx->wv, n, dh))) return rc;
+      k_givens_step<<<1, 1, 0, ctx->stream>>>(dh, j, est);
+      CKL();
+      CK(cudaMemcpyAsync(ctx->hred + 200, est, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      const double res = ctx->hred[200], hn = ctx->hred[201];
       ++its;
       k = j + 1;
       if (!std::isfinite(res)) return ctx_fail(ctx, MEHDG_ERR_NAN, "non-finite FGMRES residual");
@@ -318,6 +438,10 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
         watch_it = its;
       }
     }
+    // rotated Hessenberg and right-hand side of this cycle to the host
+    CK(cudaMemcpyAsync(hs.H.data(), dh.H, sizeof(double) * hs.H.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hs.g.data(), dh.g, sizeof(double) * hs.g.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     std::vector<double> y = hs.solve(k);
     if ((rc = maxpy(ctx, ctx->Zk, n, k, y.data(), x, n, 1.0))) return rc;
     if ((rc = apply_trace_impl(ctx, x, ctx->wv))) return rc;

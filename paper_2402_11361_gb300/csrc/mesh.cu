@@ -19,6 +19,7 @@ int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg) {
 }
 
 void phase_begin(mehdg_ctx* ctx, int p) {
+  if (ctx->capturing) return;   // no timing events inside a captured graph
   if (!ctx->ev[2 * p]) {
     cudaEventCreate(&ctx->ev[2 * p]);
     cudaEventCreate(&ctx->ev[2 * p + 1]);
@@ -26,6 +27,7 @@ void phase_begin(mehdg_ctx* ctx, int p) {
   cudaEventRecord(ctx->ev[2 * p], ctx->stream);
 }
 void phase_end(mehdg_ctx* ctx, int p) {
+  if (ctx->capturing) return;
   cudaEventRecord(ctx->ev[2 * p + 1], ctx->stream);
   ctx->ev_rec[p] = true;
 }
@@ -661,6 +663,10 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->iV, (size_t)(nin + 1) * n);
   ALLOC(ctx->iw, n);
   ALLOC(ctx->xstart, n);
+  ALLOC(ctx->dHo, (size_t)(ctx->restart + 1) * ctx->restart + 3 * (size_t)ctx->restart + 1);
+  ALLOC(ctx->dHi, (size_t)(nin + 1) * nin + 3 * (size_t)nin + 1);
+  ALLOC(ctx->gin, n);
+  ALLOC(ctx->gout, n);
   ALLOC(ctx->un, (size_t)E * Nu);
   ALLOC(ctx->ustage, (size_t)3 * E * Nu);
   ALLOC(ctx->hist, (size_t)E * Nu);
@@ -830,10 +836,11 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
-                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32};
+                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
+  if (ctx->ig_exec) cudaGraphExecDestroy(ctx->ig_exec);
   if (ctx->xstart) cudaFree(ctx->xstart);
   mlp_destroy(ctx);
   for (int i = 0; i < 2 * PH_COUNT; ++i)
