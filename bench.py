@@ -202,7 +202,7 @@ def run_ours(args, ws, rank, lrank):
     z = sizes(pr)
     prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
     base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, max_newton=60,
-                inner_iters=args.inner, tc_mode=args.tc_mode)
+                inner_iters=args.inner, tc_mode=args.tc_mode, refine_iters=args.refine)
     opts = dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode)
     ctx = pkg.Context(pr, opts, device=dev)
     du, duh = W.perturbation(pr, 0)
@@ -373,7 +373,7 @@ def run_ours(args, ws, rank, lrank):
                                "%d trace DOFs)" % (NMAC, z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
                    "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
                    "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
-                   "tc_mode": args.tc_mode,
+                   "tc_mode": args.tc_mode, "refine_iters": args.refine,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "fgmres_iters_per_step": its_timed / args.steps,
         "solve": {"newton_steps": N, "fgmres_iters": its_total, "converged_1e-8": sol["converged"],
@@ -389,6 +389,147 @@ def run_ours(args, ws, rank, lrank):
         "clocks": clocks,
     }
     ctx.close()
+    return line
+
+
+def run_tgv(args, ws, rank, lrank):
+    """Unsteady Taylor-Green vortex (periodic [0, 2 pi]^3, Re 1600, M0 0.1, p = 2): time per
+    DIRK3 step (three stages, each a Newton solve to a 1e-8 relative residual).
+
+    Warm-up: W DIRK steps from the initial condition (FGMRES pairs recorded for the
+    learned correction).  Timed: K DIRK steps.  Compare: the learned correction
+    (trained on the recorded pairs) against the multi-level preconditioner over the
+    same K steps from the same state, and the plain FP64 method (Algorithm 2 apply,
+    FP64 LU) against the mixed path on one DIRK step of a reduced mesh."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+
+    dev = torch.device("cuda:%d" % lrank)
+    torch.cuda.set_device(dev)
+    nmac = args.nmac_tgv
+    pr = W.tgv(nmac=nmac)
+    z = sizes(pr)
+    dt = 0.05 / 0.1          # 0.05 t_c, t_c = L / V0 = 10 acoustic units (L = 1, V0 = M0 = 0.1)
+    base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, max_newton=60,
+                inner_iters=args.inner, tc_mode=args.tc_mode, refine_iters=args.refine)
+    prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
+    ctx = pkg.Context(pr, dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode),
+                      device=dev)
+    u, q, uh = ctx.init_state(None, None, lift=True)
+    st = torch.cuda.current_stream(dev)
+    learn = args.compare and args.precision == "mixed"
+    if learn:
+        ctx.mlp_setup(hidden=256, seed=0, max_pairs=64)
+        ctx.mlp_set_recording(True)
+
+    def dirk_step(c, u, q, uh):
+        tot = dict(newton_steps=0, fgmres_iters=0, status=0)
+        for stage in (1, 2, 3):
+            r = c.dirk_stage(stage, dt, u, q, uh)
+            tot["newton_steps"] += r["newton_steps"]
+            tot["fgmres_iters"] += r["fgmres_iters"]
+            tot["status"] |= r["status"]
+        return tot
+
+    for _ in range(args.warmup):
+        dirk_step(ctx, u, q, uh)
+    torch.cuda.synchronize()
+    K = max(1, args.steps)
+    clk = ClockSampler(lrank)
+    clk.start()
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    newton, its = 0, 0
+    ev0.record(st)
+    for _ in range(K):
+        r = dirk_step(ctx, u, q, uh)
+        newton += r["newton_steps"]
+        its += r["fgmres_iters"]
+    ev1.record(st)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    clocks = clk.stop()
+    launches = ctx.launch_count() - l0
+    # kinetic energy of the resolved field (nodal mean of rho |v|^2 / 2) as a sanity value
+    ke = float((0.5 * (u[:, 1:4] ** 2).sum(1) / u[:, 0]).mean())
+    compare = {}
+    if args.compare:
+        state = (u.clone(), q.clone(), uh.clone())
+        if learn:
+            n_samples = ctx.mlp_set_recording(False)
+            first, last = ctx.mlp_train(epochs=args.mlp_epochs, batch=8192, lr=1e-3)
+            res = {}
+            for kind, name in ((1, "multilevel"), (2, "learned")):
+                ctx.set_precond(kind)
+                uu, qq, hh = (x.clone() for x in state)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                tot = dict(newton_steps=0, fgmres_iters=0, status=0)
+                for _ in range(K):
+                    r = dirk_step(ctx, uu, qq, hh)
+                    for k2 in tot:
+                        tot[k2] = tot[k2] | r[k2] if k2 == "status" else tot[k2] + r[k2]
+                e1.record(st)
+                torch.cuda.synchronize()
+                res[name] = dict(s_per_dirk_step=e0.elapsed_time(e1) / 1e3 / K, newton_steps=tot["newton_steps"],
+                                 fgmres_iters=tot["fgmres_iters"], fallback=bool(tot["status"] & 1), state=uu)
+            du = res["learned"].pop("state") - res["multilevel"]["state"]
+            res["learned"]["rel_diff_u_vs_multilevel"] = float(du.norm() / res["multilevel"].pop("state").norm())
+            res["train"] = dict(samples=n_samples, loss_first=first, loss_last=last)
+            compare["learned_vs_multilevel"] = res
+        ctx.close()
+        # plain FP64 (Algorithm 2) vs mixed on one DIRK step of a reduced mesh
+        nsmall = args.nmac_tgv_fp64
+        prs = W.tgv(nmac=nsmall)
+        out = {}
+        for name, opt in (("mixed", dict(base, precision=pkg.PREC_MIXED, precond=1, apply_mode=1)),
+                          ("plain_fp64_algorithm2", dict(base, precision=pkg.PREC_FP64, precond=1, apply_mode=0))):
+            c = pkg.Context(prs, opt, device=dev)
+            uu, qq, hh = c.init_state(None, None, lift=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            r = dirk_step(c, uu, qq, hh)
+            e1.record(st)
+            torch.cuda.synchronize()
+            out[name] = dict(s_per_dirk_step=e0.elapsed_time(e1) / 1e3, newton_steps=r["newton_steps"],
+                             fgmres_iters=r["fgmres_iters"], state=uu)
+            c.close()
+        du = out["mixed"]["state"] - out["plain_fp64_algorithm2"]["state"]
+        out["mixed"]["rel_diff_u_vs_fp64"] = float(du.norm() / out["plain_fp64_algorithm2"]["state"].norm())
+        for v in out.values():
+            v.pop("state", None)
+        compare["reduced_mesh_%d^3" % nsmall] = out
+    else:
+        ctx.close()
+    per = t / K
+    line = {
+        "metric": METRIC,
+        "value": per / ws,
+        "unit": "s/DIRK step",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": per * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 blocks + f64 residual/krylov",
+        "data": "synthetic (Taylor-Green initial condition, closed form)",
+        "config": {"workload": "3D Taylor-Green vortex, periodic [0,2pi]^3, Re 1600, M0 0.1, %d^3 macro-elements "
+                               "x 2^3 hexes, p=2 (%d macros, %d trace DOFs), DIRK3 dt = 0.05 t_c"
+                               % (nmac, z["E"], z["F"] * z["ns"] * z["Nfn"]),
+                   "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
+                   "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
+                   "refine_iters": args.refine, "l2": "inputs larger than L2 (no flush)", "parallelism": "1 GPU"},
+        "newton_steps_per_dirk_step": newton / K,
+        "fgmres_iters_per_dirk_step": its / K,
+        "kinetic_energy_mean": ke,
+        "compare": compare,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
     return line
 
 
@@ -452,6 +593,8 @@ def main():
     ap.add_argument("--tc-mode", type=int, default=0,
                     help="mixed path: 0 FP32 SIMT; 1 tcgen05 split-TF32 LU updates; 2 also condensation and A^T_i"
                          " products; 3 plain TF32 products")
+    ap.add_argument("--refine", type=int, default=1,
+                    help="FP64 refinement sweeps of each local S solve (b^ and recovery) on the mixed path")
     ap.add_argument("--no-phases", dest="phases", action="store_false")
     ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
 
@@ -460,6 +603,10 @@ def main():
                     help="skip the plain FP64 (Algorithm 2) and learned-preconditioner solves")
     ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
+    ap.add_argument("--workload", default="mms", choices=["mms", "tgv"],
+                    help="mms: steady 3D manufactured solution (default); tgv: Taylor-Green DIRK steps")
+    ap.add_argument("--nmac-tgv", type=int, default=16, help="TGV macro-elements per edge (16 = the config)")
+    ap.add_argument("--nmac-tgv-fp64", type=int, default=8, help="reduced TGV mesh of the FP64 comparison")
     args = ap.parse_args()
     global NMAC
     NMAC = args.nmac
@@ -472,6 +619,12 @@ def main():
     if ws > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.workload == "tgv":
+        args.steps = args.steps or 2
+        line = run_tgv(args, ws, rank, lrank)
+        if rank == 0:
+            print(json.dumps(line))
+        return
     if args.steps == 0:
         args.steps = -1       # one replay of every recorded Newton step
     line = run_ours(args, ws, rank, lrank)

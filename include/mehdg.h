@@ -187,7 +187,9 @@ int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q,
 /* Copy one internal per-macro array to host memory (test access).  which:
  * 0 A_uu/S (after condensation: LU factors), 1..3 A_uq_k, 4 A_uuh/C, 5 A_uhu/B,
  * 6..8 A_uhq_k, 9 A_uhuh/D, 10 R_Q, 11 R_U, 12 R_Uhat (local), 13 g, 14 h,
- * 15 pivots (as doubles), 16 bhat_local.  Returns the element count in *count. */
+ * 15 pivots (as doubles), 16 bhat_local, 17 the unfactored S kept for the FP64
+ * refinement of the local solves (mixed precision with refine_iters > 0).  Returns
+ * the element count in *count. */
 int mehdg_get_block(mehdg_ctx* ctx, int which, int macro, double* host_out,
                     long long* count);
 
@@ -246,6 +248,11 @@ int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
  *   (host double[2]) receives the mean loss of the first and last epoch.
  * In kind-2 solves FGMRES falls back to kind 1 when its residual falls by less than
  * 10x over 20 iterations (stats->status bit 0). */
+/* Switch the preconditioner kind (0, 1, 2 as in mehdg_precondition) used by later
+ * mehdg_linear_solve / mehdg_dirk_stage calls of this context, e.g. to compare the
+ * learned correction with the multi-level preconditioner on one resident problem.
+ * Kind 2 needs mehdg_mlp_setup first.  Returns MEHDG_ERR_ARG otherwise. */
+int mehdg_set_precond(mehdg_ctx* ctx, int kind);
 int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long seed, int max_pairs);
 int mehdg_mlp_params(mehdg_ctx* ctx, int set, float* host, long long* count);
 int mehdg_mlp_record(mehdg_ctx* ctx, const double* r, const double* e);

@@ -21,7 +21,8 @@ EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_loca
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
            "mehdg_get_block", "mehdg_phase_times", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
-           "mehdg_tc_gemm_tf32", "mehdg_apply_trace_noalloc", "mehdg_destroy", "mehdg_last_error"]
+           "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_apply_trace_noalloc", "mehdg_destroy",
+           "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
 
@@ -95,6 +96,7 @@ def load_library(path=LIB_PATH):
     lib.mehdg_mlp_set_recording.argtypes = [c_void_p, I, P(c_int)]
     lib.mehdg_mlp_gradient.argtypes = [c_void_p, c_void_p, c_void_p, I, c_void_p, P(c_double)]
     lib.mehdg_mlp_train.argtypes = [c_void_p, I, I, c_double, P(c_double)]
+    lib.mehdg_set_precond.argtypes = [c_void_p, I]
     lib.mehdg_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.restype = None
     lib.mehdg_last_error.argtypes = [c_void_p]
@@ -264,6 +266,10 @@ class Context:
         return {k: out[i] for i, k in enumerate(self.PHASES)}
 
     # -- learned preconditioner correction (kind 2)
+    def set_precond(self, kind):
+        self._check(self.lib.mehdg_set_precond(self.h, int(kind)), "set_precond")
+        self.options["precond"] = int(kind)
+
     def mlp_setup(self, hidden=256, seed=0, max_pairs=400):
         self._check(self.lib.mehdg_mlp_setup(self.h, int(hidden), int(seed), int(max_pairs)), "mlp_setup")
         n = c_longlong()

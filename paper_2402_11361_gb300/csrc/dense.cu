@@ -297,14 +297,17 @@ __global__ void k_face_blocks(const T* Ahh, const int* owner, double* fblk, int 
   fblk[i] = v;
 }
 
-// b_loc = h - B S^-1 g, one CTA per macro-element
+// b_loc = h - B S^-1 g, one CTA per macro-element; with S0 (the FP32 copy of S before
+// its factorisation, mixed path) the local solve is refined `iters` times in FP64
 template <class T>
 __global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm, const T* B,
                                                      const double* gvec, const double* hvec, double* bloc, int Nu,
-                                                     int Nt) {
+                                                     int Nt, const T* S0, int iters) {
   extern __shared__ double sm[];
-  double* y = sm;        // Nu
-  double* tmp = sm + Nu; // Nu
+  double* y = sm;             // Nu: solution
+  double* tmp = sm + Nu;      // Nu: right-hand side g
+  double* r = tmp + Nu;       // Nu, Nu: refinement scratch
+  double* t = r + Nu;
   const int e = blockIdx.x;
   const T* Se = S + (size_t)e * Nu * Nu;
   const int* pe = perm + (size_t)e * Nu;
@@ -313,13 +316,14 @@ __global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm,
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) y[i] = tmp[pe[i]];
   __syncthreads();
   lu_solve_block<T, double>(Se, Nu, y);
+  if (S0) lu_refine<T>(Se, pe, S0 + (size_t)e * Nu * Nu, Nu, tmp, y, r, t, iters);
   const T* Be = B + (size_t)e * Nt * Nu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = w; r < Nt; r += nw) {
+  for (int row = w; row < Nt; row += nw) {
     double s = 0.0;
-    for (int c = lane; c < Nu; c += 32) s += (double)Be[(size_t)r * Nu + c] * y[c];
+    for (int c = lane; c < Nu; c += 32) s += (double)Be[(size_t)row * Nu + c] * y[c];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) bloc[(size_t)e * Nt + r] = hvec[(size_t)e * Nt + r] - s;
+    if (lane == 0) bloc[(size_t)e * Nt + row] = hvec[(size_t)e * Nt + row] - s;
   }
 }
 
@@ -483,6 +487,8 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // LU of S and of the face blocks
   CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
   phase_begin(ctx, PH_LU);
+  if (sizeof(T) == 4 && ctx->S32)   // unfactored S for the FP64 refinement of the local solves
+    CK(cudaMemcpyAsync(ctx->S32, Auu, sizeof(float) * E * Nu * Nu, cudaMemcpyDeviceToDevice, st));
   if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag, sizeof(T) == 4 && ctx->use_tc_lu)))
     return rc;
   phase_end(ctx, PH_LU);
@@ -509,9 +515,11 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // b^
   phase_begin(ctx, PH_BHAT);
   {
-    size_t smem = sizeof(double) * 2 * Nu;
+    size_t smem = sizeof(double) * 4 * Nu;
+    const T* S0 = (sizeof(T) == 4 && ctx->S32) ? reinterpret_cast<const T*>(ctx->S32) : nullptr;
     CK(cudaFuncSetAttribute(k_bhat_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt);
+    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt, S0,
+                                          ctx->opt.refine_iters);
     CKL();
   }
   if (bhat) {

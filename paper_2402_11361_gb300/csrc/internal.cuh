@@ -95,9 +95,8 @@ struct mehdg_ctx {
   float *u32 = nullptr, *q32 = nullptr, *h32 = nullptr, *tab32 = nullptr, *src32 = nullptr;
   float *uD32 = nullptr, *uh32 = nullptr;
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
-  // mixed precision copies
-  float *S32 = nullptr, *B32 = nullptr, *C32 = nullptr, *D32 = nullptr;
-  int* perm32 = nullptr;
+  // mixed precision: S before its factorisation, for the FP64 refinement of local solves
+  float* S32 = nullptr;
 
   // Krylov workspace
   int restart = 30;

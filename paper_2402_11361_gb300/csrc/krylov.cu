@@ -493,3 +493,10 @@ extern "C" int mehdg_linear_solve(mehdg_ctx* ctx, const double* b, double* x, me
   if (!ctx || !b || !x || b == x) return MEHDG_ERR_ARG;
   return linear_solve_impl(ctx, b, x, st);
 }
+
+extern "C" int mehdg_set_precond(mehdg_ctx* ctx, int kind) {
+  if (!ctx || kind < 0 || kind > 2) return MEHDG_ERR_ARG;
+  if (kind == 2 && !ctx->mlp) return ctx_fail(ctx, MEHDG_ERR_ARG, "kind 2 needs mehdg_mlp_setup");
+  ctx->opt.precond = kind;
+  return MEHDG_OK;
+}

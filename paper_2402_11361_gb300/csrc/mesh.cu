@@ -640,6 +640,7 @@ static int setup(mehdg_ctx* ctx) {
     ALLOC(ctx->Whk32, wh32.size());
     CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
+    if (ctx->opt.refine_iters > 0) ALLOC(ctx->S32, (size_t)E * Nu * Nu);
     ALLOC(ctx->u32, (size_t)E * ns * Np);
     ALLOC(ctx->h32, (size_t)E * ns * Np);
     ALLOC(ctx->q32, (size_t)E * d * ns * Np);
@@ -793,6 +794,9 @@ extern "C" int mehdg_get_block(mehdg_ctx* ctx, int which, int e, double* out, lo
     case 14: src = ctx->hv + e * Nt; n = Nt; break;
     case 15: isrc = ctx->perm + e * Nu; n = Nu; ints = true; break;
     case 16: src = ctx->bloc + e * Nt; n = Nt; break;
+    case 17:
+      if (!ctx->S32) return MEHDG_ERR_ARG;
+      n = Nu * Nu; break;
     default: return MEHDG_ERR_ARG;
   }
   if (count) *count = (long long)n;
@@ -801,6 +805,10 @@ extern "C" int mehdg_get_block(mehdg_ctx* ctx, int which, int e, double* out, lo
   if (ints) {
     std::vector<int> tmp(n);
     CK(cudaMemcpy(tmp.data(), isrc, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
+  } else if (which == 17) {
+    std::vector<float> tmp(n);
+    CK(cudaMemcpy(tmp.data(), ctx->S32 + e * Nu * Nu, sizeof(float) * n, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < n; ++i) out[i] = tmp[i];
   } else if (ctx->opt.precision == MEHDG_PREC_MIXED && which <= 9) {
     // blocks are FP32 in the mixed-precision path (same element offsets)
@@ -832,7 +840,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->Gk, ctx->Ghk, ctx->Wk, ctx->Whk, ctx->src, ctx->uD, ctx->Auu, ctx->Auq, ctx->Auh,
                   ctx->Ahu, ctx->Ahq, ctx->Ahh, ctx->perm, ctx->RQ, ctx->RU, ctx->RUh, ctx->gv, ctx->hv,
                   ctx->MinvRQ, ctx->bloc, ctx->slot, ctx->Kvol, ctx->rvol, ctx->Kface, ctx->rface, ctx->fblk,
-                  ctx->fperm, ctx->dflag, ctx->dred, ctx->S32, ctx->B32, ctx->C32, ctx->D32, ctx->perm32,
+                  ctx->fperm, ctx->dflag, ctx->dred, ctx->S32,
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,

@@ -323,6 +323,38 @@ def test_mixed_newton_reaches_the_fp64_solution(lib):
     ctx.close()
 
 
+@pytest.mark.parametrize("iters", [0, 2])
+def test_mixed_local_solves_refined_in_fp64(lib, iters):
+    """Mixed path: the recovery's local solve du = S^-1 (g + C duh) uses the FP32 LU of S;
+    with refinement sweeps (residual of the stored unfactored S accumulated in FP64) the
+    solve residual drops from the FP32 level to the FP64 level."""
+    pr = W.mms(dim=3, nmac=2, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    ctx = lib.Context(pr, dict(precision=1, refine_iters=iters))
+    ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    ctx.condense(shift=0.3)
+    duh = W.random_vector(P.F * P.ns * P.Nfn, 10, 0.01)
+    du, _ = ctx.recover(to_dev(duh))
+    du = du.cpu().numpy()
+    Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+    worst = 0.0
+    for e in (0, 3, 7):
+        if iters == 0:
+            with pytest.raises(RuntimeError):
+                ctx.get_block(17, e)
+            break
+        S0 = ctx.get_block(17, e).reshape(Nu, Nu)
+        C = ctx.get_block(4, e).reshape(Nu, Nt)
+        rhs = ctx.get_block(13, e) + C @ duh[P.maps[e].reshape(-1)]
+        res = np.linalg.norm(rhs - S0 @ du[e].reshape(-1)) / np.linalg.norm(rhs)
+        worst = max(worst, res)
+    print("refine_iters", iters, "worst relative local residual", worst)
+    if iters:
+        assert worst < 1e-12
+    ctx.close()
+
+
 # ---------------------------------------------------------------- explicit local operator (apply_mode 1)
 
 @pytest.mark.parametrize("prec", [0, 1])
