@@ -61,68 +61,54 @@ __global__ void __launch_bounds__(512) k_apply(const T* __restrict__ S, const in
   }
 }
 
-// FP32 row . x with 16-byte loads: the first (address mod 16) / 4 entries are peeled
-// off so that every lane then reads float4 chunks of the row, four per iteration in
-// flight; x is kept in shared memory as four copies shifted by 0..3 entries (stride
-// ldx), so that the chunk of x matching a row chunk is one aligned 16-byte load.
-__device__ __forceinline__ float warp_dot_f4(const float* __restrict__ row, const float* xs, int ldx, int n,
-                                             int lane) {
-  const int peel = min(n, (int)((16 - ((size_t)row & 15)) & 15) / 4);
+// FP32 row . x with 8-byte loads (rows of an even-length FP32 block start 8-byte
+// aligned): four float2 loads per lane in flight per iteration, x read as float2 pairs
+// from shared memory
+__device__ __forceinline__ float warp_dot_f2(const float* __restrict__ row, const float* x, int n, int lane) {
+  const float2* r2 = reinterpret_cast<const float2*>(row);
+  const float2* x2 = reinterpret_cast<const float2*>(x);
+  const int n2 = n / 2;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  if (lane < peel) s0 = row[lane] * xs[lane];
-  const float4* r4 = reinterpret_cast<const float4*>(row + peel);
-  const float4* x4 = reinterpret_cast<const float4*>(xs + (size_t)peel * ldx);   // x4[j] = x[peel + 4j ..]
-  const int n4 = (n - peel) / 4;
   int j = lane;
-  for (; j + 96 < n4; j += 128) {
-    const float4 a = __ldg(r4 + j), b = __ldg(r4 + j + 32), c = __ldg(r4 + j + 64), d = __ldg(r4 + j + 96);
-    const float4 xa = x4[j], xb = x4[j + 32], xc = x4[j + 64], xd = x4[j + 96];
-    s0 += a.x * xa.x + a.y * xa.y + a.z * xa.z + a.w * xa.w;
-    s1 += b.x * xb.x + b.y * xb.y + b.z * xb.z + b.w * xb.w;
-    s2 += c.x * xc.x + c.y * xc.y + c.z * xc.z + c.w * xc.w;
-    s3 += d.x * xd.x + d.y * xd.y + d.z * xd.z + d.w * xd.w;
+  for (; j + 96 < n2; j += 128) {
+    const float2 a = __ldg(r2 + j), b = __ldg(r2 + j + 32), c = __ldg(r2 + j + 64), d = __ldg(r2 + j + 96);
+    const float2 xa = x2[j], xb = x2[j + 32], xc = x2[j + 64], xd = x2[j + 96];
+    s0 += a.x * xa.x + a.y * xa.y;
+    s1 += b.x * xb.x + b.y * xb.y;
+    s2 += c.x * xc.x + c.y * xc.y;
+    s3 += d.x * xd.x + d.y * xd.y;
   }
-  for (; j < n4; j += 32) {
-    const float4 a = __ldg(r4 + j), xa = x4[j];
-    s0 += a.x * xa.x + a.y * xa.y + a.z * xa.z + a.w * xa.w;
+  for (; j < n2; j += 32) {
+    const float2 a = __ldg(r2 + j), xa = x2[j];
+    s0 += a.x * xa.x + a.y * xa.y;
   }
-  for (int c = peel + 4 * n4 + lane; c < n; c += 32) s1 += row[c] * xs[c];
+  if ((n & 1) && lane == 0) s1 += row[n - 1] * x[n - 1];
   float s = (s0 + s1) + (s2 + s3);
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
-// stride of one shifted copy of x (multiple of 4 entries, so each copy stays 16-byte aligned)
-__host__ __device__ inline int x4_stride(int n) { return (n + 4 + 3) / 4 * 4; }
 
 // apply_mode 1: y4 = A^T_i x on dT_i with the stored local operator; grid (macro, row block)
 template <class T, class A>
-__global__ void __launch_bounds__(256) k_apply_explicit(const T* __restrict__ Ahat, const int* __restrict__ gather,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_apply_explicit(const T* __restrict__ Ahat, const int* __restrict__ gather,
                                                         const double* __restrict__ x, double* __restrict__ slot,
                                                         int Nt, int rows) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   A* xg = reinterpret_cast<A*>(sm_raw);
   const int e = blockIdx.x, r0 = blockIdx.y * rows;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  constexpr bool F4 = sizeof(T) == 4 && sizeof(A) == 4;
-  const int ldx = x4_stride(Nt);
-  if constexpr (F4) {
-    // four copies shifted by k = 0..3: xg[k * ldx + i] = x_loc[i + k] (gathered once)
-    for (int i = threadIdx.x; i < ldx; i += blockDim.x) xg[i] = (i < Nt) ? (A)x[gather[(size_t)e * Nt + i]] : A(0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < 3 * ldx; i += blockDim.x) {
-      const int k = 1 + i / ldx, c = i % ldx + k;
-      xg[k * ldx + i % ldx] = (c < ldx) ? xg[c] : A(0);
-    }
-  } else {
-    for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (A)x[gather[(size_t)e * Nt + i]];
-  }
+  // FP32 blocks with an even row length: 8-byte row loads
+  const bool F2 = sizeof(T) == 4 && sizeof(A) == 4 && (Nt % 2) == 0;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (A)x[gather[(size_t)e * Nt + i]];
   __syncthreads();
   const int r1 = min(r0 + rows, Nt);
   for (int r = r0 + w; r < r1; r += nw) {
     A s;
-    if constexpr (F4) s = warp_dot_f4(reinterpret_cast<const float*>(Ahat) + ((size_t)e * Nt + r) * Nt,
-                                      reinterpret_cast<const float*>(xg), ldx, Nt, lane);
-    else s = warp_dot<T, A>(Ahat + ((size_t)e * Nt + r) * Nt, xg, Nt, lane);
+    if (F2)
+      s = (A)warp_dot_f2(reinterpret_cast<const float*>(Ahat) + ((size_t)e * Nt + r) * Nt,
+                         reinterpret_cast<const float*>(xg), Nt, lane);
+    else
+      s = warp_dot<T, A>(Ahat + ((size_t)e * Nt + r) * Nt, xg, Nt, lane);
     if (lane == 0) slot[(size_t)e * Nt + r] = (double)s;
   }
 }
@@ -205,8 +191,7 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
     const int rows = 64;
     dim3 grid(ctx->E, (ctx->Nt + rows - 1) / rows);
     phase_begin(ctx, PH_APPLY);
-    const size_t smem = sizeof(A) * (sizeof(T) == 4 && sizeof(A) == 4 ? 4 * (size_t)x4_stride(ctx->Nt) : ctx->Nt);
-    k_apply_explicit<T, A><<<grid, 256, smem, ctx->stream>>>(
+    k_apply_explicit<T, A><<<grid, 256, sizeof(A) * ctx->Nt, ctx->stream>>>(
         reinterpret_cast<const T*>(ctx->Ahh), ctx->gather, x, ctx->slot, ctx->Nt, rows);
     CKL();
     phase_end(ctx, PH_APPLY);
