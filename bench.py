@@ -203,7 +203,8 @@ def run_ours(args, ws, rank, lrank):
     prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
     base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, max_newton=60,
                 inner_iters=args.inner, tc_mode=args.tc_mode, refine_iters=args.refine)
-    opts = dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode)
+    opts = dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode,
+                precond_bf16=args.precond_bf16 if prec == pkg.PREC_MIXED else 0)
     ctx = pkg.Context(pr, opts, device=dev)
     du, duh = W.perturbation(pr, 0)
     du_d = torch.as_tensor(du, device=dev)
@@ -373,7 +374,7 @@ def run_ours(args, ws, rank, lrank):
                                "%d trace DOFs)" % (NMAC, z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
                    "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
                    "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
-                   "tc_mode": args.tc_mode, "refine_iters": args.refine,
+                   "tc_mode": args.tc_mode, "refine_iters": args.refine, "precond_bf16": args.precond_bf16,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "fgmres_iters_per_step": its_timed / args.steps,
         "solve": {"newton_steps": N, "fgmres_iters": its_total, "converged_1e-8": sol["converged"],
@@ -415,8 +416,8 @@ def run_tgv(args, ws, rank, lrank):
     base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, max_newton=60,
                 inner_iters=args.inner, tc_mode=args.tc_mode, refine_iters=args.refine)
     prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
-    ctx = pkg.Context(pr, dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode),
-                      device=dev)
+    ctx = pkg.Context(pr, dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode,
+                               precond_bf16=args.precond_bf16 if prec == pkg.PREC_MIXED else 0), device=dev)
     u, q, uh = ctx.init_state(None, None, lift=True)
     st = torch.cuda.current_stream(dev)
     learn = args.compare and args.precision == "mixed"
@@ -484,7 +485,8 @@ def run_tgv(args, ws, rank, lrank):
         nsmall = args.nmac_tgv_fp64
         prs = W.tgv(nmac=nsmall)
         out = {}
-        for name, opt in (("mixed", dict(base, precision=pkg.PREC_MIXED, precond=1, apply_mode=1)),
+        for name, opt in (("mixed", dict(base, precision=pkg.PREC_MIXED, precond=1, apply_mode=1,
+                                         precond_bf16=args.precond_bf16)),
                           ("plain_fp64_algorithm2", dict(base, precision=pkg.PREC_FP64, precond=1, apply_mode=0))):
             c = pkg.Context(prs, opt, device=dev)
             uu, qq, hh = c.init_state(None, None, lift=True)
@@ -522,7 +524,8 @@ def run_tgv(args, ws, rank, lrank):
                                % (nmac, z["E"], z["F"] * z["ns"] * z["Nfn"]),
                    "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
                    "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
-                   "refine_iters": args.refine, "l2": "inputs larger than L2 (no flush)", "parallelism": "1 GPU"},
+                   "refine_iters": args.refine, "precond_bf16": args.precond_bf16,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "1 GPU"},
         "newton_steps_per_dirk_step": newton / K,
         "fgmres_iters_per_dirk_step": its / K,
         "kinetic_energy_mean": ke,
@@ -595,6 +598,8 @@ def main():
                          " products; 3 plain TF32 products")
     ap.add_argument("--refine", type=int, default=1,
                     help="FP64 refinement sweeps of each local S solve (b^ and recovery) on the mixed path")
+    ap.add_argument("--precond-bf16", type=int, default=1,
+                    help="mixed path: BF16 copy of A^T_i for the inner GMRES of the multi-level preconditioner")
     ap.add_argument("--no-phases", dest="phases", action="store_false")
     ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
 

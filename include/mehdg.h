@@ -95,6 +95,10 @@ typedef struct mehdg_options {
                          with tcgen05 trailing updates in split TF32 (3 products, about
                          FP32 accuracy); 2 also the condensation products and forming
                          A^T_i in split TF32; 3 as 2 with plain TF32 */
+  int precond_bf16;   /* apply_mode 1 with precond 1: the inner GMRES of the multi-level
+                         preconditioner applies a BF16 copy of A^T_i (half the bytes of
+                         the FP32 operator; FGMRES allows the inexact preconditioner),
+                         the outer FGMRES keeps the FP32/FP64 operator */
 } mehdg_options;
 
 typedef struct mehdg_info {

@@ -88,6 +88,50 @@ __device__ __forceinline__ float warp_dot_f2(const float* __restrict__ row, cons
   return s;
 }
 
+// The same product on the BF16 copy of A^T_i (inner GMRES of the multi-level
+// preconditioner): each 4-byte load brings two BF16 entries, widened to FP32 by a
+// shift; eight loads per lane in flight per iteration; FP32 accumulation.
+__global__ void __launch_bounds__(256, 8) k_apply_explicit_bf16(const unsigned short* __restrict__ Ahat,
+                                                                const int* __restrict__ gather,
+                                                                const double* __restrict__ x,
+                                                                double* __restrict__ slot, int Nt, int rows) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* xg = reinterpret_cast<float*>(sm_raw);
+  const int e = blockIdx.x, r0 = blockIdx.y * rows;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (float)x[gather[(size_t)e * Nt + i]];
+  __syncthreads();
+  const int r1 = min(r0 + rows, Nt), n2 = Nt / 2;
+  const float2* x2 = reinterpret_cast<const float2*>(xg);
+  for (int r = r0 + w; r < r1; r += nw) {
+    const unsigned short* row = Ahat + ((size_t)e * Nt + r) * Nt;
+    const unsigned int* w2 = reinterpret_cast<const unsigned int*>(row);   // rows start 4-byte aligned (Nt even)
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int j = lane;
+    for (; j + 224 < n2; j += 256) {
+      unsigned int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(w2 + j + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float2 xv = x2[j + 32 * u];
+        const float a = __uint_as_float(v[u] << 16), b = __uint_as_float(v[u] & 0xFFFF0000u);
+        if (u & 1) s1 += a * xv.x + b * xv.y;
+        else s0 += a * xv.x + b * xv.y;
+      }
+    }
+    for (; j < n2; j += 32) {
+      const unsigned int v = __ldg(w2 + j);
+      const float2 xv = x2[j];
+      s2 += __uint_as_float(v << 16) * xv.x + __uint_as_float(v & 0xFFFF0000u) * xv.y;
+    }
+    if ((Nt & 1) && lane == 0) s3 += __uint_as_float((unsigned int)row[Nt - 1] << 16) * xg[Nt - 1];
+    float s = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) slot[(size_t)e * Nt + r] = (double)s;
+  }
+}
+
 // apply_mode 1: y4 = A^T_i x on dT_i with the stored local operator; grid (macro, row block)
 template <class T, class A>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_apply_explicit(const T* __restrict__ Ahat, const int* __restrict__ gather,
@@ -176,6 +220,63 @@ __global__ void __launch_bounds__(256) k_recover(const T* __restrict__ S, const 
   }
 }
 
+// Mixed-precision recovery: the same equations with FP32 products (per-lane FP32 partial
+// sums, FP64 across lanes), FP32 substitutions with FP64-refined local solve, and the
+// lifting products W_k, Wh_k in FP32.
+__global__ void __launch_bounds__(256) k_recover_f32(const float* __restrict__ S, const int* __restrict__ perm,
+                                                     const float* __restrict__ C, const double* __restrict__ gvec,
+                                                     const double* __restrict__ MinvRQ, const float* __restrict__ Wk,
+                                                     const float* __restrict__ Whk, const int* __restrict__ gather,
+                                                     const double* __restrict__ duh, double* __restrict__ du,
+                                                     double* __restrict__ dq, int Nu, int Nt, int Np, int Nth, int ns,
+                                                     int d, const float* __restrict__ S0, int iters) {
+  extern __shared__ double sm[];
+  double* y1 = sm;                                 // Nu: right-hand side
+  double* y2 = y1 + Nu;                            // Nu: solution
+  double* r = y2 + Nu;                             // Nu: refinement residual
+  double* td = r + Nu;                             // Nu: refinement correction
+  float* xf = reinterpret_cast<float*>(td + Nu);   // Nt: gathered duh
+  float* t = xf + ((Nt + 1) & ~1);                 // Nu: FP32 solve vector (first Nt doubles: gathered duh)
+  float* yf = t + (Nu > 2 * Nt ? Nu : 2 * Nt);     // Nu: FP32 copy of the solution
+  const int e = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* xg = reinterpret_cast<double*>(t);   // the FP32 scratch is not in use yet: gathered duh in FP64
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) {
+    const double v = duh[gather[(size_t)e * Nt + i]];
+    xf[i] = (float)v;
+    xg[i] = v;
+  }
+  __syncthreads();
+  // right-hand side of the local solve, g + C duh, accumulated in FP64 (the refined solve
+  // is then accurate to the FP64 level for this right-hand side)
+  const float* Ce = C + (size_t)e * Nu * Nt;
+  for (int row = w; row < Nu; row += nw) {
+    double s = 0.0;
+    for (int c = lane; c < Nt; c += 32) s += (double)Ce[(size_t)row * Nt + c] * xg[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y1[row] = s + gvec[(size_t)e * Nu + row];
+  }
+  __syncthreads();
+  const int* pe = perm + (size_t)e * Nu;
+  lu_solve_f32_refined(S + (size_t)e * Nu * Nu, pe, S0 ? S0 + (size_t)e * Nu * Nu : nullptr, Nu, y1, y2, r, td, t,
+                       iters);
+  for (int i = threadIdx.x; i < Nu; i += blockDim.x) {
+    du[(size_t)e * Nu + i] = y2[i];
+    yf[i] = (float)y2[i];
+  }
+  __syncthreads();
+  const int nq = d * ns * Np;
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+    int a = i % Np, s = (i / Np) % ns, k = i / (Np * ns);
+    const float* W = Wk + ((size_t)k * Np + a) * Np;
+    const float* Wh = Whk + ((size_t)k * Np + a) * Nth;
+    float acc = 0.f;
+    for (int b = 0; b < Np; ++b) acc += W[b] * yf[s * Np + b];
+    for (int c = 0; c < Nth; ++c) acc += Wh[c] * xf[s * Nth + c];
+    dq[(size_t)e * nq + i] = -(MinvRQ[(size_t)e * nq + i] + (double)acc);
+  }
+}
+
 }  // namespace
 
 int face_reduce(mehdg_ctx* ctx, const double* slot, double* y) {
@@ -190,6 +291,12 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
   if (ctx->opt.apply_mode == 1) {
     const int rows = 64;
     dim3 grid(ctx->E, (ctx->Nt + rows - 1) / rows);
+    if (ctx->lowp_apply && ctx->Ahat16 && (ctx->Nt % 2) == 0) {
+      k_apply_explicit_bf16<<<grid, 256, sizeof(float) * ctx->Nt, ctx->stream>>>(ctx->Ahat16, ctx->gather, x,
+                                                                               ctx->slot, ctx->Nt, rows);
+      CKL();
+      return face_reduce(ctx, ctx->slot, y);
+    }
     phase_begin(ctx, PH_APPLY);
     k_apply_explicit<T, A><<<grid, 256, sizeof(A) * ctx->Nt, ctx->stream>>>(
         reinterpret_cast<const T*>(ctx->Ahh), ctx->gather, x, ctx->slot, ctx->Nt, rows);
@@ -220,10 +327,12 @@ int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   size_t smem = sizeof(double) * (ctx->Nt + 4 * (size_t)ctx->Nu);
   phase_begin(ctx, PH_RECOVER);
   if (ctx->opt.precision == MEHDG_PREC_MIXED) {
-    CK(cudaFuncSetAttribute(k_recover<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_recover<float><<<ctx->E, 256, smem, ctx->stream>>>(
+    const size_t Nu = ctx->Nu, Nt = ctx->Nt;
+    const size_t smem32 = sizeof(double) * 4 * Nu + sizeof(float) * (((Nt + 1) & ~(size_t)1) + (Nu > 2 * Nt ? Nu : 2 * Nt) + Nu);
+    CK(cudaFuncSetAttribute(k_recover_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    k_recover_f32<<<ctx->E, 256, smem32, ctx->stream>>>(
         reinterpret_cast<const float*>(ctx->Auu), ctx->perm, reinterpret_cast<const float*>(ctx->Auh), ctx->gv,
-        ctx->MinvRQ, ctx->Wk, ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np, ctx->Nth, ctx->ns,
+        ctx->MinvRQ, ctx->Wk32, ctx->Whk32, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np, ctx->Nth, ctx->ns,
         ctx->d, ctx->S32, ctx->opt.refine_iters);
     CKL();
     phase_end(ctx, PH_RECOVER);

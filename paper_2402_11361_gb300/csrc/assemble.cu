@@ -189,23 +189,26 @@ template <int D, int P, class CT = double> struct VolCfg {
   static constexpr int KA = (D + 1) * NS * (D + 1);
   static constexpr int NCOL = NS * NLOC;                  // output columns (s, b)
   static constexpr int ZG = (D + 1) * NCOL;               // Z entries per Gauss point
-  static constexpr int TG = (D + 1) * NLOC;               // basis entries per Gauss point
   static constexpr int GC = (ZG * 8 <= 1536) ? 32 : (ZG <= 600 ? 16 : 8);
-  static constexpr int RG = (NLOC + 15) / 16;             // row groups
-  static constexpr int RPT = (NLOC + RG - 1) / RG;        // output rows per thread
+  static constexpr int RPT0 = (NLOC + 3) / 4 * 4;
+  static constexpr int RPT = RPT0 > 16 ? 16 : RPT0;       // output rows per thread (multiple of 4)
+  static constexpr int RG = (NLOC + RPT - 1) / RPT;       // row groups
+  static constexpr int NLOCP = RG * RPT;                  // padded basis count (row stride of T)
+  static constexpr int TG = (D + 1) * NLOCP;              // basis entries per Gauss point
   static constexpr int ITEMS = NCOL * RG;                 // (column, row group) items
   static constexpr int NT0 = (ITEMS + 31) / 32 * 32;
   static constexpr int NT = NT0 > 512 ? 512 : NT0;
   static constexpr int OPT = (ITEMS + NT - 1) / NT;
-  static constexpr size_t SMEM = sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + (size_t)GC * TG);
+  static constexpr size_t SMEM =
+      sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + (size_t)GC * TG + 2 * (size_t)NG1 * P1 + 4);
 };
 
 // A_X[(t, A)][(s, B)] += sum_g sum_{alpha,beta} T[g][alpha][a] K[g][alpha][s][beta] T[g][beta][b]
 // per sub-element: with Z[g][alpha][(s, b)] = sum_beta K[g][alpha][s][beta] T[g][beta][b],
 // the output block is the product T^T Z over the (g, alpha) index.  Per chunk of Gauss
-// points the basis values T and Z are tabulated in shared memory; each thread owns one
-// output column (s, b) and RPT rows a, so a step of the product costs one Z load, RPT
-// broadcast T loads and RPT FMAs.
+// points the basis values T (rows padded to a multiple of 4) and Z are tabulated in
+// shared memory; each thread owns one output column (s, b) and RPT rows a, so a step of
+// the product costs one Z load, RPT/4 broadcast 16-byte T loads (FP32) and RPT FMAs.
 template <int D, int P, class CT>
 __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, const double* __restrict__ tab,
                                                                       const CT* __restrict__ Kvol,
@@ -213,15 +216,23 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
   typedef VolCfg<D, P, CT> C;
   constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, ZG = C::ZG;
   constexpr int TG = C::TG, NCOL = C::NCOL, GC = C::GC, NT = C::NT, OPT = C::OPT, RPT = C::RPT;
+  constexpr int NLOCP = C::NLOCP;
   constexpr int ITEMS = C::ITEMS;
-  extern __shared__ unsigned char smem_raw[];
-  CT* sK = reinterpret_cast<CT*>(smem_raw);   // [GC][KA]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* sT = reinterpret_cast<CT*>(smem_raw);   // [GC][D+1][NLOCP]
+  CT* sK = sT + GC * TG;                      // [GC][KA]
   CT* sZ = sK + GC * KA;                      // [GC][D+1][NCOL]
-  CT* sT = sZ + GC * ZG;                      // [GC][D+1][NLOC]
+  CT* sb = sZ + GC * ZG;                      // 1D basis values [NG1][P1] in CT
+  CT* sdb = sb + NG1 * P1;                    // 1D reference derivatives
   const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z;
   const int tid = threadIdx.x;
   CT sc[D];
   for (int k = 0; k < D; ++k) sc[k] = (CT)(2.0 / g.he[k]);
+  for (int i = tid; i < NG1 * P1; i += NT) {
+    sb[i] = (CT)tab[i];
+    sdb[i] = (CT)tab[NG1 * P1 + i];
+  }
+  __syncthreads();
   const size_t Nu = g.Nu, Np = g.Np;
   CT* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
   int icol[OPT], irow[OPT];
@@ -248,13 +259,16 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
       for (int i = tid; i < gc * KA; i += NT) sK[i] = Kel[(size_t)g0 * KA + i];
       // T[g][alpha][a]: value (alpha 0) or derivative along x_{alpha-1} of basis a at point g
       for (int i = tid; i < gc * TG; i += NT) {
-        const int a = i % NLOC, al = (i / NLOC) % (D + 1), gg = i / TG;
-        int t1 = g0 + gg, t2 = a;
-        CT v = CT(1);
-        for (int k = 0; k < D; ++k) {
-          const int gk = t1 % NG1, ak = t2 % P1;
-          t1 /= NG1; t2 /= P1;
-          v *= (al == 1 + k) ? (CT)tab[NG1 * P1 + gk * P1 + ak] * sc[k] : (CT)tab[gk * P1 + ak];
+        const int a = i % NLOCP, al = (i / NLOCP) % (D + 1), gg = i / TG;
+        CT v = CT(0);
+        if (a < NLOC) {
+          int t1 = g0 + gg, t2 = a;
+          v = CT(1);
+          for (int k = 0; k < D; ++k) {
+            const int gk = t1 % NG1, ak = t2 % P1;
+            t1 /= NG1; t2 /= P1;
+            v *= (al == 1 + k) ? sdb[gk * P1 + ak] * sc[k] : sb[gk * P1 + ak];
+          }
         }
         sT[i] = v;
       }
@@ -266,7 +280,7 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
         const CT* Tp = sT + gg * TG + b;
         CT z = CT(0);
 #pragma unroll
-        for (int be = 0; be <= D; ++be) z += Kp[be] * Tp[be * NLOC];
+        for (int be = 0; be <= D; ++be) z += Kp[be] * Tp[be * NLOCP];
         sZ[i] = z;
       }
       __syncthreads();
@@ -274,9 +288,20 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
       for (int o = 0; o < OPT; ++o) {
         for (int k = 0; k < gc * (D + 1); ++k) {
           const CT z = sZ[k * NCOL + icol[o]];
-          const CT* Tk = sT + k * NLOC + irow[o];
+          const CT* Tk = sT + k * NLOCP + irow[o];
+          if constexpr (sizeof(CT) == 4) {
 #pragma unroll
-          for (int r = 0; r < RPT; ++r) acc[o][r] += Tk[min(r, NLOC - 1 - irow[o])] * z;
+            for (int r = 0; r < RPT; r += 4) {
+              const float4 tv = *reinterpret_cast<const float4*>(Tk + r);
+              acc[o][r] += tv.x * z;
+              acc[o][r + 1] += tv.y * z;
+              acc[o][r + 2] += tv.z * z;
+              acc[o][r + 3] += tv.w * z;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) acc[o][r] += Tk[r] * z;
+          }
         }
       }
       __syncthreads();

@@ -12,74 +12,13 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include <cuda_bf16.h>
+
 #include "lu.cuh"
 #include "lu_panel.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
-
-// C[b] = alpha A[b] B[b] + beta C[b], row-major, batch b = (i, j), i < n1 (outer), j < n2:
-// X[b] = X + i * sX1 + j * sX2.
-template <class T, class TB = double>
-struct GemmArgs {
-  int M, N, K;
-  const T* A; int lda; long long sA1, sA2;
-  const TB* B; int ldb; long long sB1, sB2;
-  T* C; int ldc; long long sC1, sC2;
-  double alpha, beta;
-  int n2;
-};
-
-constexpr int TM = 64, TN = 64, TK = 16;
-template <class T, class TB>
-__global__ void __launch_bounds__(256) k_gemm64(GemmArgs<T, TB> a) {
-  __shared__ T sA[TK][TM + 1];
-  __shared__ T sB[TK][TN + 1];
-  const int b = blockIdx.z;
-  const int bi = b / a.n2, bj = b % a.n2;
-  const T* A = a.A + bi * a.sA1 + bj * a.sA2;
-  const TB* B = a.B + bi * a.sB1 + bj * a.sB2;
-  T* C = a.C + bi * a.sC1 + bj * a.sC2;
-  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4] = {};
-  for (int k0 = 0; k0 < a.K; k0 += TK) {
-    for (int i = threadIdx.x; i < TM * TK; i += 256) {
-      int r = i / TK, c = i % TK;
-      int gr = m0 + r, gc = k0 + c;
-      sA[c][r] = (gr < a.M && gc < a.K) ? A[(size_t)gr * a.lda + gc] : T(0);
-    }
-    for (int i = threadIdx.x; i < TK * TN; i += 256) {
-      int r = i / TN, c = i % TN;
-      int gr = k0 + r, gc = n0 + c;
-      sB[r][c] = (gr < a.K && gc < a.N) ? (T)B[(size_t)gr * a.ldb + gc] : T(0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < TK; ++kk) {
-      T av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = sA[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = sB[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int r = m0 + ty + 16 * i, c = n0 + tx + 16 * j;
-      if (r < a.M && c < a.N) {
-        T* p = C + (size_t)r * a.ldc + c;
-        *p = (T)a.alpha * acc[i][j] + (a.beta == 0.0 ? T(0) : (T)a.beta * *p);
-      }
-    }
-}
 
 // Second-layer condensation products of one (macro e, species s) pair in one GEMM
 // (eq. ASC2a with the lifting factorisation of Sec. 3.2), P = [A_.q_1[:, s] | ... |
@@ -89,13 +28,16 @@ __global__ void __launch_bounds__(256) k_gemm64(GemmArgs<T, TB> a) {
 // each output is read and written once; the right factor [W | -Wh] is shared by all
 // macros.  Tile 128 x 96 x 16, 8 x 6 outputs per thread, next K tile prefetched into
 // registers while the current one is multiplied.
+// The same tiles serve the plain batched product D += B X of the explicit local
+// operator (one "species" block, no column split).
 template <class T>
 struct CondArgs {
-  const T* A; long long sAe, sAk; int lda, M;   // A_.q: [e][k][M][lda]
-  const T* Bc; int N, K, Np, Nth, ns;           // [K][N] = [d*Np][Np + Nth]
-  T* O1; long long sO1e; int ldo1;              // S or B: columns s*Np + j
-  T* O2; long long sO2e; int ldo2;              // C or D: columns s*Nth + j - Np
-  int o2_add;                                   // 1: O2 += P (D), 0: O2 -= P (C)
+  const T* A; long long sAe, sAk, sAs; int lda, M, kdiv;   // A(e,s)[r][kk] = A + e sAe + s sAs + (kk/kdiv) sAk + r lda + kk%kdiv
+  const T* Bc; long long sBe; int ldb;                      // B(e)[kk][c] = Bc + e sBe + kk ldb + c
+  int N, K, ns;
+  T* O1; long long sO1e, sO1s; int ldo1, o1_add;            // columns c < nsplit: O1 + e sO1e + s sO1s + r ldo1 + c
+  T* O2; long long sO2e, sO2s; int ldo2, o2_add;            // columns c >= nsplit: O2 + ... + (c - nsplit)
+  int nsplit;
 };
 constexpr int CG_BM = 128, CG_BN = 96, CG_BK = 16;
 template <class T>
@@ -105,7 +47,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
   const int es = blockIdx.z, e = es / a.ns, s = es % a.ns;
   const int m0 = blockIdx.y * CG_BM, n0 = blockIdx.x * CG_BN;
   const int tid = threadIdx.x, tm = tid / 16, tn = tid % 16;
-  const T* Ae = a.A + e * a.sAe + (size_t)s * a.Np;
+  const T* Ae = a.A + e * a.sAe + s * a.sAs;
+  const T* Be = a.Bc + e * a.sBe;
   constexpr int LA = CG_BM * CG_BK / 256, LB = CG_BK * CG_BN / 256;
   T ra[LA], rb[LB];
   auto fetch = [&](int k0) {
@@ -115,7 +58,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
       const int gr = m0 + r, kk = k0 + kq;
       T v = T(0);
       if (gr < a.M && kk < a.K) {
-        const int k = kk / a.Np, c = kk - k * a.Np;
+        const int k = kk / a.kdiv, c = kk - k * a.kdiv;
         v = Ae[k * a.sAk + (size_t)gr * a.lda + c];
       }
       ra[j] = v;
@@ -124,7 +67,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
     for (int j = 0; j < LB; ++j) {
       const int i = tid + 256 * j, r = i / CG_BN, c = i % CG_BN;
       const int kk = k0 + r, gc = n0 + c;
-      rb[j] = (kk < a.K && gc < a.N) ? a.Bc[(size_t)kk * a.N + gc] : T(0);
+      rb[j] = (kk < a.K && gc < a.N) ? Be[(size_t)kk * a.ldb + gc] : T(0);
     }
   };
   auto stash = [&]() {
@@ -171,10 +114,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
     for (int j = 0; j < 6; ++j) {
       const int c = n0 + tn * 6 + j;
       if (c >= a.N) continue;
-      if (c < a.Np) {
-        a.O1[e * a.sO1e + (size_t)r * a.ldo1 + (size_t)s * a.Np + c] -= acc[i][j];
+      if (c < a.nsplit) {
+        T* p = a.O1 + e * a.sO1e + s * a.sO1s + (size_t)r * a.ldo1 + c;
+        *p = a.o1_add ? *p + acc[i][j] : *p - acc[i][j];
       } else {
-        T* p = a.O2 + e * a.sO2e + (size_t)r * a.ldo2 + (size_t)s * a.Nth + (c - a.Np);
+        T* p = a.O2 + e * a.sO2e + s * a.sO2s + (size_t)r * a.ldo2 + (c - a.nsplit);
         *p = a.o2_add ? *p + acc[i][j] : *p - acc[i][j];
       }
     }
@@ -189,13 +133,6 @@ int cond_gemm(mehdg_ctx* ctx, const CondArgs<T>& a, int E) {
   return MEHDG_OK;
 }
 
-template <class T, class TB>
-int gemm(mehdg_ctx* ctx, const GemmArgs<T, TB>& a, int n1) {
-  dim3 grid((a.N + TN - 1) / TN, (a.M + TM - 1) / TM, n1 * a.n2);
-  k_gemm64<T, TB><<<grid, 256, 0, ctx->stream>>>(a);
-  CKL();
-  return MEHDG_OK;
-}
 
 // The same product on the tcgen05 tensor cores (TF32 inputs, FP32 accumulation)
 int tc_gemm(mehdg_ctx* ctx, int M, int N, int K, const float* A, long long lda, long long sA1, long long sA2,
@@ -217,25 +154,34 @@ int tc_gemm(mehdg_ctx* ctx, int M, int N, int K, const float* A, long long lda, 
 // the condensed right-hand-side pieces g and h, all directions k in one pass over A_.q
 template <class T>
 __global__ void __launch_bounds__(256) k_cond_rhs(const T* __restrict__ A, int M, int N, int d, long long sAe,
-                                                  long long sAk, const double* __restrict__ x, long long sxe,
+                                                  long long sAk, const T* __restrict__ x, long long sxe,
                                                   long long sxk, const double* __restrict__ R, double* __restrict__ y) {
   const int e = blockIdx.y, lane = threadIdx.x & 31;
   const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (r >= M) return;
-  double s0 = 0.0, s1 = 0.0;
+  // per-lane partial sums in the block precision (FP32 blocks: FP32, so the product
+  // stays off the FP64 pipe), summed across the warp in FP64
+  T s0 = T(0), s1 = T(0);
   for (int k = 0; k < d; ++k) {
     const T* a = A + e * sAe + k * sAk + (size_t)r * N;
-    const double* xv = x + e * sxe + k * sxk;
+    const T* xv = x + e * sxe + k * sxk;
     int c = lane;
     for (; c + 32 < N; c += 64) {
-      s0 += (double)a[c] * xv[c];
-      s1 += (double)a[c + 32] * xv[c + 32];
+      s0 += a[c] * xv[c];
+      s1 += a[c + 32] * xv[c + 32];
     }
-    for (; c < N; c += 32) s0 += (double)a[c] * xv[c];
+    for (; c < N; c += 32) s0 += a[c] * xv[c];
   }
-  double s = s0 + s1;
+  double s = (double)s0 + (double)s1;
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) y[(size_t)e * M + r] = s - R[(size_t)e * M + r];
+}
+
+// BF16 copy (round to nearest even) of the local operators for the inner GMRES
+template <class T>
+__global__ void k_to_bf16(const T* __restrict__ x, unsigned short* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)x[i]));
 }
 
 __global__ void k_to_float(const double* x, float* y, long long n) {
@@ -327,6 +273,36 @@ __global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm,
   }
 }
 
+// Mixed precision: the same with FP32 substitutions refined in FP64 and the B product
+// as FP32 per-lane partial sums added across lanes in FP64
+__global__ void __launch_bounds__(256) k_bhat_local_f32(const float* S, const int* perm, const float* B,
+                                                        const double* gvec, const double* hvec, double* bloc,
+                                                        int Nu, int Nt, const float* S0, int iters) {
+  extern __shared__ double sm[];
+  double* g = sm;                                // Nu
+  double* y = g + Nu;                            // Nu
+  double* r = y + Nu;                            // Nu
+  double* td = r + Nu;                           // Nu
+  float* t = reinterpret_cast<float*>(td + Nu);  // Nu
+  float* yf = t + Nu;                            // Nu
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < Nu; i += blockDim.x) g[i] = gvec[(size_t)e * Nu + i];
+  __syncthreads();
+  lu_solve_f32_refined(S + (size_t)e * Nu * Nu, perm + (size_t)e * Nu, S0 ? S0 + (size_t)e * Nu * Nu : nullptr, Nu,
+                       g, y, r, td, t, iters);
+  for (int i = threadIdx.x; i < Nu; i += blockDim.x) yf[i] = (float)y[i];
+  __syncthreads();
+  const float* Be = B + (size_t)e * Nt * Nu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = w; row < Nt; row += nw) {
+    float s = 0.f;
+    for (int c = lane; c < Nu; c += 32) s += Be[(size_t)row * Nu + c] * yf[c];
+    double sd = s;
+    for (int o = 16; o; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    if (lane == 0) bloc[(size_t)e * Nt + row] = hvec[(size_t)e * Nt + row] - sd;
+  }
+}
+
 // blocked LU with the panel in shared memory where it fits (227 KB per CTA), else the
 // global-memory variant; tc selects the tcgen05 trailing update (FP32 only)
 template <class T>
@@ -375,13 +351,13 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
                    (long long)Nt * Nt, 0, 1.f, 1.f, E, 1);
   }
   {
-    GemmArgs<T, T> a{};
-    a.M = Nt; a.N = Nt; a.K = Nu;
-    a.A = B; a.lda = Nu; a.sA1 = (long long)Nt * Nu; a.sA2 = 0;
-    a.B = X; a.ldb = Nt; a.sB1 = (long long)Nu * Nt; a.sB2 = 0;
-    a.C = D; a.ldc = Nt; a.sC1 = (long long)Nt * Nt; a.sC2 = 0;
-    a.alpha = 1.0; a.beta = 1.0; a.n2 = 1;
-    return gemm(ctx, a, E);
+    CondArgs<T> a{};
+    a.A = B; a.sAe = (long long)Nt * Nu; a.sAk = 0; a.sAs = 0; a.lda = Nu; a.M = Nt; a.kdiv = Nu;
+    a.Bc = X; a.sBe = (long long)Nu * Nt; a.ldb = Nt;
+    a.N = Nt; a.K = Nu; a.ns = 1;
+    a.O1 = D; a.sO1e = (long long)Nt * Nt; a.sO1s = 0; a.ldo1 = Nt; a.o1_add = 1; a.nsplit = Nt;
+    a.O2 = D; a.sO2e = 0; a.sO2s = 0; a.ldo2 = Nt; a.o2_add = 1;
+    return cond_gemm(ctx, a, E);
   }
 }
 
@@ -426,13 +402,19 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   }
   // g = -R_U + sum_k A_uq_k MinvRQ[k];  h = -R_Uh + sum_k A_uhq_k MinvRQ[k]  (eq. ASC2b pieces)
   {
+    // M^-1 R_Q in the block precision (FP32 path: into the FP32 q scratch of the assembly)
+    const T* xq = reinterpret_cast<const T*>(ctx->MinvRQ);
+    if constexpr (sizeof(T) == 4) {
+      if ((rc = to_float(ctx, ctx->MinvRQ, ctx->q32, (long long)E * d * Nu))) return rc;
+      xq = reinterpret_cast<const T*>(ctx->q32);
+    }
     dim3 grid((unsigned)((Nu + 7) / 8), (unsigned)E);
     k_cond_rhs<T><<<grid, 256, 0, st>>>(Auq, (int)Nu, (int)Nu, d, (long long)d * Nu * Nu, (long long)Nu * Nu,
-                                        ctx->MinvRQ, (long long)d * Nu, (long long)Nu, ctx->RU, ctx->gv);
+                                        xq, (long long)d * Nu, (long long)Nu, ctx->RU, ctx->gv);
     CKL();
     grid.x = (unsigned)((Nt + 7) / 8);
     k_cond_rhs<T><<<grid, 256, 0, st>>>(Ahq, (int)Nt, (int)Nu, d, (long long)d * Nt * Nu, (long long)Nt * Nu,
-                                        ctx->MinvRQ, (long long)d * Nu, (long long)Nu, ctx->RUh, ctx->hv);
+                                        xq, (long long)d * Nu, (long long)Nu, ctx->RUh, ctx->hv);
     CKL();
   }
   // S, C, B, D
@@ -447,10 +429,12 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     // [S | C] -= A_uq [W | -Wh],  [B | -D] -= A_uhq [W | -Wh]  (all directions in one K)
     CondArgs<T> a{};
     a.Bc = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)ctx->Bcat32 : (const void*)ctx->Bcat);
-    a.N = Np + Nth; a.K = d * Np; a.Np = Np; a.Nth = Nth; a.ns = ns;
-    a.A = Auq; a.sAe = (long long)d * Nu * Nu; a.sAk = (long long)Nu * Nu; a.lda = (int)Nu; a.M = (int)Nu;
-    a.O1 = Auu; a.sO1e = (long long)Nu * Nu; a.ldo1 = (int)Nu;
-    a.O2 = Auh; a.sO2e = (long long)Nu * Nt; a.ldo2 = (int)Nt; a.o2_add = 0;
+    a.sBe = 0; a.ldb = Np + Nth;
+    a.N = Np + Nth; a.K = d * Np; a.ns = ns; a.kdiv = Np; a.nsplit = Np;
+    a.A = Auq; a.sAe = (long long)d * Nu * Nu; a.sAk = (long long)Nu * Nu; a.sAs = Np; a.lda = (int)Nu;
+    a.M = (int)Nu;
+    a.O1 = Auu; a.sO1e = (long long)Nu * Nu; a.sO1s = Np; a.ldo1 = (int)Nu; a.o1_add = 0;
+    a.O2 = Auh; a.sO2e = (long long)Nu * Nt; a.sO2s = Nth; a.ldo2 = (int)Nt; a.o2_add = 0;
     if ((rc = cond_gemm(ctx, a, E))) return rc;
     a.A = Ahq; a.sAe = (long long)d * Nt * Nu; a.sAk = (long long)Nt * Nu; a.lda = (int)Nu; a.M = (int)Nt;
     a.O1 = Ahu; a.sO1e = (long long)Nt * Nu; a.ldo1 = (int)Nu;
@@ -514,12 +498,18 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   phase_end(ctx, PH_FACE_LU);
   // b^
   phase_begin(ctx, PH_BHAT);
-  {
+  if constexpr (sizeof(T) == 4) {
+    const size_t smem = sizeof(double) * 4 * Nu + sizeof(float) * 2 * Nu;
+    CK(cudaFuncSetAttribute(k_bhat_local_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bhat_local_f32<<<E, 256, smem, st>>>(reinterpret_cast<const float*>(Auu), ctx->perm,
+                                           reinterpret_cast<const float*>(Ahu), ctx->gv, ctx->hv, ctx->bloc, (int)Nu,
+                                           (int)Nt, ctx->S32, ctx->opt.refine_iters);
+    CKL();
+  } else {
     size_t smem = sizeof(double) * 4 * Nu;
-    const T* S0 = (sizeof(T) == 4 && ctx->S32) ? reinterpret_cast<const T*>(ctx->S32) : nullptr;
     CK(cudaFuncSetAttribute(k_bhat_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt, S0,
-                                          ctx->opt.refine_iters);
+    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt,
+                                          nullptr, 0);
     CKL();
   }
   if (bhat) {
@@ -529,6 +519,11 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   if (ctx->opt.apply_mode == 1) {
     phase_begin(ctx, PH_FORM);
     if ((rc = form_local_operator<T>(ctx, Auu, Ahu, Auh, Ahh))) return rc;
+    if (ctx->Ahat16) {
+      const long long tot = (long long)E * Nt * Nt;
+      k_to_bf16<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Ahh, ctx->Ahat16, tot);
+      CKL();
+    }
     phase_end(ctx, PH_FORM);
   }
   int flags[4], tcerr = 0;

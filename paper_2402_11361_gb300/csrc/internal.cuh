@@ -95,6 +95,8 @@ struct mehdg_ctx {
   float *u32 = nullptr, *q32 = nullptr, *h32 = nullptr, *tab32 = nullptr, *src32 = nullptr;
   float *uD32 = nullptr, *uh32 = nullptr;
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
+  unsigned short* Ahat16 = nullptr;   // BF16 copy of A^T_i for the inner GMRES (precond_bf16)
+  bool lowp_apply = false;            // set while the inner GMRES runs: apply the BF16 copy
   // mixed precision: S before its factorisation, for the FP64 refinement of local solves
   float* S32 = nullptr;
 

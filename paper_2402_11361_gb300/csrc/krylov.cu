@@ -323,7 +323,10 @@ static int inner_gmres_dev(mehdg_ctx* ctx, const double* r, double* z) {
   k_normalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dot, ctx->iw, IV, beta);
   CKL();
   for (int j = 0; j < nu; ++j) {
-    if ((rc = apply_trace_impl(ctx, IV + (size_t)j * n, ctx->tv))) return rc;
+    ctx->lowp_apply = true;   // the BF16 operator copy, when the context keeps one
+    rc = apply_trace_impl(ctx, IV + (size_t)j * n, ctx->tv);
+    ctx->lowp_apply = false;
+    if (rc) return rc;
     if ((rc = block_jacobi(ctx, ctx->tv, ctx->iw))) return rc;
     if ((rc = arnoldi_dev(ctx, IV, j, ctx->iw, n, h))) return rc;
   }

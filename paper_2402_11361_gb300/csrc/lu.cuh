@@ -236,6 +236,37 @@ __device__ void lu_refine(const T* __restrict__ LU, const int* __restrict__ perm
   }
 }
 
+// FP32-factor solve with FP64 refinement (mixed precision): x = S^-1 rhs by FP32
+// substitutions, then `iters` sweeps of r = rhs - S0 x accumulated in FP64 (S0 the FP32
+// matrix before factorisation, or none) and x += S^-1 r, the correction by substitutions
+// in FP64 arithmetic on the FP32 factors.  rhs, x, r, td: FP64 shared vectors of length
+// n; t: FP32 shared scratch of length n.
+__device__ inline void lu_solve_f32_refined(const float* __restrict__ LU, const int* __restrict__ perm,
+                                            const float* __restrict__ S0, int n, const double* rhs, double* x,
+                                            double* r, double* td, float* t, int iters) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = (float)rhs[perm[i]];
+  __syncthreads();
+  lu_solve_block<float, float>(LU, n, t);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = t[i];
+  __syncthreads();
+  for (int it = 0; S0 && it < iters; ++it) {
+    for (int row = w; row < n; row += nw) {
+      const float* sr = S0 + (size_t)row * n;
+      double s = 0.0;
+      for (int c = lane; c < n; c += 32) s += (double)sr[c] * x[c];
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) r[row] = rhs[row] - s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) td[i] = r[perm[i]];
+    __syncthreads();
+    lu_solve_block<float, double>(LU, n, td);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += td[i];
+    __syncthreads();
+  }
+}
+
 // X = S^-1 B for a block of RC right-hand-side columns of one macro-element
 // (grid: macro x column block), from the LU factors and row permutation of S.
 // B and X are row-major [n][nrhs]; the RC columns of P B live in shared memory.

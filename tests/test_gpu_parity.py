@@ -355,6 +355,35 @@ def test_mixed_local_solves_refined_in_fp64(lib, iters):
     ctx.close()
 
 
+def test_bf16_inner_operator_keeps_the_fgmres_solution(lib):
+    """precond_bf16: the inner GMRES of the multi-level preconditioner applies a BF16
+    copy of A^T_i.  The preconditioner changes (BF16 rounding, 2^-8 relative per entry)
+    but FGMRES, which tolerates a variable preconditioner, still reaches the requested
+    residual of the operator it solves (the FP32 A^T_i applied with FP32 products, whose
+    own rounding sets a floor near 1e-6, hence the 1e-5 tolerance)."""
+    pr = W.mms(dim=3, nmac=2, m=2, p=2)
+    u, q, uh = W.random_state(pr, 5)
+    z = W.sizes(pr)
+    b = W.random_vector(z["F"] * z["ns"] * z["Nfn"], 11)
+    out = {}
+    for bf in (0, 1):
+        ctx = lib.Context(pr, dict(precision=1, apply_mode=1, precond=1, inner_iters=5, lin_rtol=1e-5,
+                                   restart=60, max_iters=4000, precond_bf16=bf))
+        ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+        ctx.condense(shift=0.3)
+        z1 = ctx.precondition(1, to_dev(b)).cpu().numpy()
+        x, st = ctx.linear_solve(to_dev(b))
+        res = np.linalg.norm(b - ctx.apply(x).cpu().numpy()) / np.linalg.norm(b)
+        out[bf] = (z1, st["fgmres_iters"], res)
+        ctx.close()
+    dz = rel(out[1][0], out[0][0])
+    print("bf16 inner operator: preconditioner change", dz, "iterations", out[0][1], out[1][1],
+          "residuals", out[0][2], out[1][2])
+    assert 1e-6 < dz < 5e-2
+    assert out[1][2] <= 1.05e-5 and out[0][2] <= 1.05e-5
+    assert out[1][1] <= 2 * out[0][1] + 5
+
+
 # ---------------------------------------------------------------- explicit local operator (apply_mode 1)
 
 @pytest.mark.parametrize("prec", [0, 1])
