@@ -37,6 +37,11 @@ UNIT = "s/Newton step"
 
 NMAC = 8
 
+# DRAM bytes (read + write) per macro-element and launch of the apply kernels, from ncu
+# captures of the 6^3 case (216 macros; profiles/k_apply_explicit_mms3d_6cubed.md),
+# scaled by the macro count; keyed by (phase, precision, apply_mode)
+TRAFFIC_PER_MACRO = {("apply", "mixed", 1): (491.278848e6 + 8.894208e6) / 216}
+
 
 def workload():
     return W.mms(dim=3, nmac=NMAC, m=2, p=2)
@@ -319,38 +324,57 @@ def run_ours(args, ws, rank, lrank):
         ctxp.close()
         compare["primary_full_solve"] = {k: v for k, v in sol.items() if k not in ("records", "state")}
 
-    # ---- roofline of the dominant kernel: phase with the largest time per step
+    # ---- roofline of the dominant kernel: the kernel with the largest device time per step
+    # (phase events around single kernels; the BF16 apply is timed inside the inner-GMRES graph)
     work = phase_work(z, z["E"], args.precision, args.apply_mode)
     ph_mean = {k: float(np.mean(v)) for k, v in phase_acc.items() if v and v[0] >= 0}
     peaks = measured_peaks()
+    its_step = its_timed / args.steps
+    inner = args.inner if args.precond == 1 else 0
+    bf = bool(opts.get("precond_bf16")) and args.apply_mode == 1 and args.precond == 1
+    per_step = {}
+    if "apply" in ph_mean:
+        per_step["apply"] = ph_mean["apply"] * (its_step * (1 if bf else 1 + inner) + 1)
+    if bf and "apply_bf16" in ph_mean:
+        per_step["apply_bf16"] = ph_mean["apply_bf16"] * its_step * inner
+    for k in ("cond_gemm", "lu", "vol_contract", "trsm"):
+        if k in ph_mean:
+            per_step[k] = ph_mean[k]
     roof = None
-    applies = its_timed / args.steps * (1 + (args.inner if args.precond == 1 else 0))
-    if ph_mean:
-        dom = max(("condense", "lu", "vol_contract", "vol_point", "apply", "form_local"),
-                  key=lambda k: ph_mean.get(k, 0.0) * (applies if k == "apply" else 1.0))
-        if dom == "apply":
-            ach = work["apply_bytes"] / (ph_mean["apply"] / 1e3) / 1e9
+    if per_step:
+        dom = max(per_step, key=per_step.get)
+        E, Nu, Nt = z["E"], z["Nu"], z["Nt"]
+        if dom in ("apply", "apply_bf16"):
+            byts = work["apply_bytes"] if dom == "apply" else (2 * Nt * Nt + 20 * Nt) * E
+            ach = byts / (ph_mean[dom] / 1e3) / 1e9
             pk = peaks.get("hbm_gbs", 6800.0)
-            roof = dict(kernel=("k_apply_explicit (A^T_i x, " if args.apply_mode == 1 else "k_apply (Algorithm 2, ")
-                        + "one launch = all macro-elements)", bound="hbm",
-                        achieved=ach, peak=pk, unit="GB/s", frac=ach / pk, traffic=None,
-                        peak_source="MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback")
+            tr = TRAFFIC_PER_MACRO.get((dom, args.precision, args.apply_mode))
+            name = {"apply": "k_apply_explicit" if args.apply_mode == 1 else "k_apply (Algorithm 2)",
+                    "apply_bf16": "k_apply_explicit_bf16 (inner GMRES)"}[dom]
+            roof = dict(kernel=name + ", one launch = all %d macro-elements" % E, bound="hbm", achieved=ach, peak=pk,
+                        unit="GB/s", frac=ach / pk, traffic=(tr * E / 1e9 if tr else None), traffic_unit="GB/launch",
+                        algorithmic=byts / 1e9, peak_source="MEASURED_PEAKS.json hbm_gbs (measured copy)"
+                        if "hbm_gbs" in peaks else "fallback 6800 GB/s")
         else:
-            fl = {"condense": work["condense_flops"], "lu": work["lu_flops"],
-                  "form_local": 2.0 * z["Nu"] ** 2 * z["Nt"] * z["E"] + 2.0 * z["Nt"] ** 2 * z["Nu"] * z["E"],
-                  "vol_contract": None, "vol_point": None}.get(dom)
+            # volume contraction: per (macro, input X, test species t, sub-element) a product
+            # [NLOC x (d+1) NG] x [(d+1) NG x ns NLOC], NLOC = (p+1)^d, NG = (p+2)^d, m^d sub-elements
+            d, p_, m_ = z["d"], 2, 2
+            nloc, ngp = (p_ + 1) ** d, (p_ + 2) ** d
+            vc = 2.0 * nloc * (z["ns"] * nloc) * ngp * (d + 1) * E * (d + 1) * z["ns"] * m_ ** d
+            fl = {"cond_gemm": work["condense_flops"], "lu": work["lu_flops"],
+                  "trsm": 2.0 * Nu * Nu * Nt * E, "vol_contract": vc}[dom]
             if args.precision == "fp64":
                 pk, src = fp64_peak_tflops(torch), "measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)"
-                bound = "alu"
-            elif args.tc_mode in (1, 2) and dom in ("condense", "form_local"):
-                pk = peaks.get("bf16_tflops", 1918.0) / 2.0
-                src, bound = "measured bf16 burst x nominal tf32/bf16 ratio 1/2", "tensor"
             else:
                 pk = 2 * 128 * 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-                src, bound = "FP32 FMA pipe: 128 lanes x 2 flop x 152 SMs x max SM clock", "alu"
-            ach = fl / (ph_mean[dom] / 1e3) / 1e12 if fl else None
-            roof = dict(kernel=dom, bound=bound, achieved=ach, peak=pk, unit="TFLOP/s",
-                        frac=(ach / pk) if ach else None, traffic=None, peak_source=src)
+                src = "FP32 FMA pipe: 128 lanes x 2 flop x 152 SMs x max SM clock (derived)"
+            name = {"cond_gemm": "k_cond_gemm (2 launches)", "lu": "k_lu_panel_smem", "trsm": "k_lu_solve_multi",
+                    "vol_contract": "k_vol_contract"}[dom]
+            ach = fl / (ph_mean[dom] / 1e3) / 1e12
+            roof = dict(kernel=name, bound="alu", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk,
+                        traffic=None, peak_source=src)
+        roof["ms_per_launch"] = ph_mean[dom]
+        roof["ms_per_step_all_launches"] = per_step[dom]
     lu_tflops = None
     if "lu" in ph_mean and ph_mean["lu"] > 0:
         lu_tflops = work["lu_flops"] / (ph_mean["lu"] / 1e3) / 1e12

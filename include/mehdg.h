@@ -283,7 +283,10 @@ int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long lda, long 
  * (CUDA events on the context stream; -1 for phases not run since mehdg_mesh):
  * 0 volume pointwise Jacobians, 1 volume contraction, 2 faces + R_Q, 3 condensation
  * products, 4 batched LU of S, 5 LU of the face blocks, 6 condensed rhs, 7 trace
- * apply kernel, 8 recovery, 9 block-Jacobi, 10 forming A^T_i (apply_mode 1).
+ * apply kernel, 8 recovery, 9 block-Jacobi, 10 forming A^T_i (apply_mode 1),
+ * 11 BF16 trace apply of the inner GMRES (precond_bf16; timed inside its CUDA graph),
+ * 12 the two fused condensation GEMM launches, 13 the multi-right-hand-side S^-1 C
+ * substitutions of forming A^T_i.
  * ms: host double[n], n <= 16.
  * Synchronises the stream. */
 int mehdg_phase_times(mehdg_ctx* ctx, double* ms, int n);

@@ -258,7 +258,7 @@ class Context:
         return out
 
     PHASES = ["vol_point", "vol_contract", "faces", "condense", "lu", "face_lu", "bhat", "apply", "recover",
-              "precond", "form_local"]
+              "precond", "form_local", "apply_bf16", "cond_gemm", "trsm"]
 
     def phase_times(self):
         """Device milliseconds of the last run of each internal phase (dict)."""

@@ -4,6 +4,8 @@
 // (step 3), y4 = y3 + D x (step 4, local part); the per-macro results go to a slot
 // array and a second kernel sums the (at most two) contributions of every
 // macro-face (step 4 reduction), in a fixed order.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "lu.cuh"
 
@@ -62,98 +64,118 @@ __global__ void __launch_bounds__(512) k_apply(const T* __restrict__ S, const in
 }
 
 // FP32 row . x with 8-byte loads (rows of an even-length FP32 block start 8-byte
-// aligned): four float2 loads per lane in flight per iteration, x read as float2 pairs
-// from shared memory
+// aligned), x read as float2 pairs from shared memory
 __device__ __forceinline__ float warp_dot_f2(const float* __restrict__ row, const float* x, int n, int lane) {
+  // a whole row (up to 32 x RB float2) is requested at once: RB independent loads per lane
+  constexpr int RB = 12;
   const float2* r2 = reinterpret_cast<const float2*>(row);
   const float2* x2 = reinterpret_cast<const float2*>(x);
   const int n2 = n / 2;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  int j = lane;
-  for (; j + 96 < n2; j += 128) {
-    const float2 a = __ldg(r2 + j), b = __ldg(r2 + j + 32), c = __ldg(r2 + j + 64), d = __ldg(r2 + j + 96);
-    const float2 xa = x2[j], xb = x2[j + 32], xc = x2[j + 64], xd = x2[j + 96];
-    s0 += a.x * xa.x + a.y * xa.y;
-    s1 += b.x * xb.x + b.y * xb.y;
-    s2 += c.x * xc.x + c.y * xc.y;
-    s3 += d.x * xd.x + d.y * xd.y;
-  }
-  for (; j < n2; j += 32) {
-    const float2 a = __ldg(r2 + j), xa = x2[j];
-    s0 += a.x * xa.x + a.y * xa.y;
+  float s0 = 0.f, s1 = 0.f;
+  for (int base = 0; base < n2; base += 32 * RB) {
+    float2 a[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int j = base + lane + 32 * u;
+      a[u] = (j < n2) ? __ldg(r2 + j) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int j = base + lane + 32 * u;
+      const float2 xv = (j < n2) ? x2[j] : make_float2(0.f, 0.f);
+      if (u & 1) s1 += a[u].x * xv.x + a[u].y * xv.y;
+      else s0 += a[u].x * xv.x + a[u].y * xv.y;
+    }
   }
   if ((n & 1) && lane == 0) s1 += row[n - 1] * x[n - 1];
-  float s = (s0 + s1) + (s2 + s3);
+  float s = s0 + s1;
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
 // The same product on the BF16 copy of A^T_i (inner GMRES of the multi-level
-// preconditioner): each 4-byte load brings two BF16 entries, widened to FP32 by a
-// shift; eight loads per lane in flight per iteration; FP32 accumulation.
-__global__ void __launch_bounds__(256, 8) k_apply_explicit_bf16(const unsigned short* __restrict__ Ahat,
+// preconditioner): BF16 entries widened to FP32 by shifts, FP32 accumulation; the same
+// persistent row-range schedule as the FP32 kernel.
+__global__ void __launch_bounds__(256, 5) k_apply_explicit_bf16(const unsigned short* __restrict__ Ahat,
                                                                 const int* __restrict__ gather,
                                                                 const double* __restrict__ x,
-                                                                double* __restrict__ slot, int Nt, int rows) {
+                                                                double* __restrict__ slot, int Nt, int E,
+                                                                long long rows_per_cta) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   float* xg = reinterpret_cast<float*>(sm_raw);
-  const int e = blockIdx.x, r0 = blockIdx.y * rows;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (float)x[gather[(size_t)e * Nt + i]];
-  __syncthreads();
-  const int r1 = min(r0 + rows, Nt), n2 = Nt / 2;
   const float2* x2 = reinterpret_cast<const float2*>(xg);
-  for (int r = r0 + w; r < r1; r += nw) {
-    const unsigned short* row = Ahat + ((size_t)e * Nt + r) * Nt;
-    const unsigned int* w2 = reinterpret_cast<const unsigned int*>(row);   // rows start 4-byte aligned (Nt even)
+  const long long total = (long long)E * Nt, g0 = (long long)blockIdx.x * rows_per_cta;
+  const long long g1 = min(g0 + rows_per_cta, total);
+  for (long long gs = g0; gs < g1;) {
+   const int e = (int)(gs / Nt);
+   const long long ge = min(g1, (long long)(e + 1) * Nt);
+   __syncthreads();
+   for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (float)x[gather[(size_t)e * Nt + i]];
+   __syncthreads();
+   for (long long gr = gs + w; gr < ge; gr += nw) {
+    const unsigned short* row = Ahat + (size_t)gr * Nt;
+    // 4-byte loads of BF16 pairs (rows start 4-byte aligned: Nt even), consecutive
+    // across lanes so the matching x pairs come from shared memory without conflicts;
+    // the whole row is requested at once (up to 12 loads per lane)
+    const unsigned int* w2 = reinterpret_cast<const unsigned int*>(row);
+    const int n2 = Nt / 2;
+    constexpr int RB = 12;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int j = lane;
-    for (; j + 224 < n2; j += 256) {
-      unsigned int v[8];
+    for (int base = 0; base < n2; base += 32 * RB) {
+      unsigned int v[RB];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldg(w2 + j + 32 * u);
+      for (int u = 0; u < RB; ++u) {
+        const int j = base + lane + 32 * u;
+        v[u] = (j < n2) ? __ldg(w2 + j) : 0u;
+      }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float2 xv = x2[j + 32 * u];
+      for (int u = 0; u < RB; ++u) {
+        const int j = base + lane + 32 * u;
+        const float2 xv = (j < n2) ? x2[j] : make_float2(0.f, 0.f);
         const float a = __uint_as_float(v[u] << 16), b = __uint_as_float(v[u] & 0xFFFF0000u);
         if (u & 1) s1 += a * xv.x + b * xv.y;
         else s0 += a * xv.x + b * xv.y;
       }
     }
-    for (; j < n2; j += 32) {
-      const unsigned int v = __ldg(w2 + j);
-      const float2 xv = x2[j];
-      s2 += __uint_as_float(v << 16) * xv.x + __uint_as_float(v & 0xFFFF0000u) * xv.y;
-    }
     if ((Nt & 1) && lane == 0) s3 += __uint_as_float((unsigned int)row[Nt - 1] << 16) * xg[Nt - 1];
     float s = (s0 + s1) + (s2 + s3);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) slot[(size_t)e * Nt + r] = (double)s;
+    if (lane == 0) slot[gr] = (double)s;
+   }
+   gs = ge;
   }
 }
 
 // apply_mode 1: y4 = A^T_i x on dT_i with the stored local operator; grid (macro, row block)
 template <class T, class A>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 4) k_apply_explicit(const T* __restrict__ Ahat, const int* __restrict__ gather,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_apply_explicit(const T* __restrict__ Ahat, const int* __restrict__ gather,
                                                         const double* __restrict__ x, double* __restrict__ slot,
-                                                        int Nt, int rows) {
+                                                        int Nt, int E, long long rows_per_cta) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   A* xg = reinterpret_cast<A*>(sm_raw);
-  const int e = blockIdx.x, r0 = blockIdx.y * rows;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // FP32 blocks with an even row length: 8-byte row loads
   const bool F2 = sizeof(T) == 4 && sizeof(A) == 4 && (Nt % 2) == 0;
-  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (A)x[gather[(size_t)e * Nt + i]];
-  __syncthreads();
-  const int r1 = min(r0 + rows, Nt);
-  for (int r = r0 + w; r < r1; r += nw) {
-    A s;
-    if (F2)
-      s = (A)warp_dot_f2(reinterpret_cast<const float*>(Ahat) + ((size_t)e * Nt + r) * Nt,
-                         reinterpret_cast<const float*>(xg), Nt, lane);
-    else
-      s = warp_dot<T, A>(Ahat + ((size_t)e * Nt + r) * Nt, xg, Nt, lane);
-    if (lane == 0) slot[(size_t)e * Nt + r] = (double)s;
+  // persistent CTA: a contiguous range of the E * Nt rows, x regathered per macro-element
+  const long long total = (long long)E * Nt, g0 = (long long)blockIdx.x * rows_per_cta;
+  const long long g1 = min(g0 + rows_per_cta, total);
+  for (long long gs = g0; gs < g1;) {
+    const int e = (int)(gs / Nt);
+    const long long ge = min(g1, (long long)(e + 1) * Nt);
+    __syncthreads();
+    for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (A)x[gather[(size_t)e * Nt + i]];
+    __syncthreads();
+    for (long long gr = gs + w; gr < ge; gr += nw) {
+      A s;
+      if (F2)
+        s = (A)warp_dot_f2(reinterpret_cast<const float*>(Ahat) + (size_t)gr * Nt,
+                           reinterpret_cast<const float*>(xg), Nt, lane);
+      else
+        s = warp_dot<T, A>(Ahat + (size_t)gr * Nt, xg, Nt, lane);
+      if (lane == 0) slot[gr] = (double)s;
+    }
+    gs = ge;
   }
 }
 
@@ -289,17 +311,33 @@ int face_reduce(mehdg_ctx* ctx, const double* slot, double* y) {
 template <class T, class A>
 static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
   if (ctx->opt.apply_mode == 1) {
-    const int rows = 64;
-    dim3 grid(ctx->E, (ctx->Nt + rows - 1) / rows);
-    if (ctx->lowp_apply && ctx->Ahat16 && (ctx->Nt % 2) == 0) {
+    // persistent grid: (resident CTAs per SM) x (SM count), each CTA a contiguous
+    // share of the rows, so no partial last wave
+    const bool lowp = ctx->lowp_apply && ctx->Ahat16 && (ctx->Nt % 2) == 0;
+    int& grid = lowp ? ctx->apply_grid16 : ctx->apply_grid;
+    if (grid <= 0) {
+      int dev = 0, sms = 0, per = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      if (lowp)
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_explicit_bf16, 256, sizeof(float) * ctx->Nt));
+      else
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_explicit<T, A>, 256, sizeof(A) * ctx->Nt));
+      grid = std::max(1, sms * std::max(1, per));
+    }
+    const long long total = (long long)ctx->E * ctx->Nt;
+    const long long rows = (total + grid - 1) / grid;
+    if (lowp) {
+      phase_begin(ctx, PH_APPLY_BF16);
       k_apply_explicit_bf16<<<grid, 256, sizeof(float) * ctx->Nt, ctx->stream>>>(ctx->Ahat16, ctx->gather, x,
-                                                                               ctx->slot, ctx->Nt, rows);
+                                                                               ctx->slot, ctx->Nt, ctx->E, rows);
       CKL();
+      phase_end(ctx, PH_APPLY_BF16);
       return face_reduce(ctx, ctx->slot, y);
     }
     phase_begin(ctx, PH_APPLY);
     k_apply_explicit<T, A><<<grid, 256, sizeof(A) * ctx->Nt, ctx->stream>>>(
-        reinterpret_cast<const T*>(ctx->Ahh), ctx->gather, x, ctx->slot, ctx->Nt, rows);
+        reinterpret_cast<const T*>(ctx->Ahh), ctx->gather, x, ctx->slot, ctx->Nt, ctx->E, rows);
     CKL();
     phase_end(ctx, PH_APPLY);
     return face_reduce(ctx, ctx->slot, y);

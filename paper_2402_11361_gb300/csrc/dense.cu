@@ -343,8 +343,10 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
   if (smem > 220 * 1024) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: local matrices too large");
   CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(E, (Nt + RC - 1) / RC);
+  phase_begin(ctx, PH_TRSM);
   k_lu_solve_multi<T, RC><<<grid, 256, smem, ctx->stream>>>(S, ctx->perm, C, X, Nu, Nt);
   CKL();
+  phase_end(ctx, PH_TRSM);
   if constexpr (sizeof(T) == 4) {
     if (ctx->use_tc_form)
       return tc_gemm(ctx, Nt, Nt, Nu, B, Nu, (long long)Nt * Nu, 0, X, Nt, (long long)Nu * Nt, 0, D, Nt,
@@ -435,11 +437,13 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     a.M = (int)Nu;
     a.O1 = Auu; a.sO1e = (long long)Nu * Nu; a.sO1s = Np; a.ldo1 = (int)Nu; a.o1_add = 0;
     a.O2 = Auh; a.sO2e = (long long)Nu * Nt; a.sO2s = Nth; a.ldo2 = (int)Nt; a.o2_add = 0;
+    phase_begin(ctx, PH_COND_GEMM);
     if ((rc = cond_gemm(ctx, a, E))) return rc;
     a.A = Ahq; a.sAe = (long long)d * Nt * Nu; a.sAk = (long long)Nt * Nu; a.lda = (int)Nu; a.M = (int)Nt;
     a.O1 = Ahu; a.sO1e = (long long)Nt * Nu; a.ldo1 = (int)Nu;
     a.O2 = Ahh; a.sO2e = (long long)Nt * Nt; a.ldo2 = (int)Nt; a.o2_add = 1;
     if ((rc = cond_gemm(ctx, a, E))) return rc;
+    phase_end(ctx, PH_COND_GEMM);
   }
   if (sizeof(T) == 4 && ctx->use_tc_condense) {
     for (int k = 0; k < d; ++k) {

@@ -97,6 +97,7 @@ struct mehdg_ctx {
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
   unsigned short* Ahat16 = nullptr;   // BF16 copy of A^T_i for the inner GMRES (precond_bf16)
   bool lowp_apply = false;            // set while the inner GMRES runs: apply the BF16 copy
+  int apply_grid = 0, apply_grid16 = 0;   // persistent grids of the explicit apply kernels
   // mixed precision: S before its factorisation, for the FP64 refinement of local solves
   float* S32 = nullptr;
 
@@ -126,7 +127,8 @@ struct mehdg_ctx {
 
 enum Phase {
   PH_VOL_POINT = 0, PH_VOL_CONTRACT = 1, PH_FACES = 2, PH_CONDENSE = 3, PH_LU = 4, PH_FACE_LU = 5,
-  PH_BHAT = 6, PH_APPLY = 7, PH_RECOVER = 8, PH_PRECOND = 9, PH_FORM = 10, PH_COUNT = 16
+  PH_BHAT = 6, PH_APPLY = 7, PH_RECOVER = 8, PH_PRECOND = 9, PH_FORM = 10, PH_APPLY_BF16 = 11,
+  PH_COND_GEMM = 12, PH_TRSM = 13, PH_COUNT = 16
 };
 void phase_begin(mehdg_ctx* ctx, int p);
 void phase_end(mehdg_ctx* ctx, int p);

@@ -18,17 +18,20 @@ int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg) {
   return code;
 }
 
+// Inside a stream capture the events become event-record nodes of the graph
+// (cudaEventRecordExternal), so phases inside the captured inner GMRES are timed at
+// each replay too.
 void phase_begin(mehdg_ctx* ctx, int p) {
-  if (ctx->capturing) return;   // no timing events inside a captured graph
   if (!ctx->ev[2 * p]) {
     cudaEventCreate(&ctx->ev[2 * p]);
     cudaEventCreate(&ctx->ev[2 * p + 1]);
   }
-  cudaEventRecord(ctx->ev[2 * p], ctx->stream);
+  if (ctx->capturing) cudaEventRecordWithFlags(ctx->ev[2 * p], ctx->stream, cudaEventRecordExternal);
+  else cudaEventRecord(ctx->ev[2 * p], ctx->stream);
 }
 void phase_end(mehdg_ctx* ctx, int p) {
-  if (ctx->capturing) return;
-  cudaEventRecord(ctx->ev[2 * p + 1], ctx->stream);
+  if (ctx->capturing) cudaEventRecordWithFlags(ctx->ev[2 * p + 1], ctx->stream, cudaEventRecordExternal);
+  else cudaEventRecord(ctx->ev[2 * p + 1], ctx->stream);
   ctx->ev_rec[p] = true;
 }
 
