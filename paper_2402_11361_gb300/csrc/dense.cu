@@ -52,16 +52,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
   constexpr int LA = CG_BM * CG_BK / 256, LB = CG_BK * CG_BN / 256;
   T ra[LA], rb[LB];
   auto fetch = [&](int k0) {
+    // this thread's A column kk = k0 + tid % CG_BK is the same for all its rows
+    const int kk = k0 + tid % CG_BK;
+    const int kdir = kk / a.kdiv;
+    const T* Ak = Ae + kdir * a.sAk + (kk - kdir * a.kdiv);
 #pragma unroll
     for (int j = 0; j < LA; ++j) {
-      const int i = tid + 256 * j, r = i / CG_BK, kq = i % CG_BK;
-      const int gr = m0 + r, kk = k0 + kq;
-      T v = T(0);
-      if (gr < a.M && kk < a.K) {
-        const int k = kk / a.kdiv, c = kk - k * a.kdiv;
-        v = Ae[k * a.sAk + (size_t)gr * a.lda + c];
-      }
-      ra[j] = v;
+      const int gr = m0 + tid / CG_BK + (256 / CG_BK) * j;
+      ra[j] = (gr < a.M && kk < a.K) ? Ak[(size_t)gr * a.lda] : T(0);
     }
 #pragma unroll
     for (int j = 0; j < LB; ++j) {
@@ -342,7 +340,7 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
   size_t smem = sizeof(T) * (size_t)Nu * RC;
   if (smem > 220 * 1024) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: local matrices too large");
   CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(E, (Nt + RC - 1) / RC);
+  dim3 grid((Nt + RC - 1) / RC, E);
   phase_begin(ctx, PH_TRSM);
   k_lu_solve_multi<T, RC><<<grid, 256, smem, ctx->stream>>>(S, ctx->perm, C, X, Nu, Nt);
   CKL();
@@ -493,9 +491,13 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     if ((rc = batched_lu_t<float>(ctx, f32, ctx->fperm, nfb, ctx->F, ctx->dflag + 2))) return rc;
     const size_t smem = sizeof(float) * (size_t)nfb * 64;
     CK(cudaFuncSetAttribute(k_lu_solve_multi<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(ctx->F, (nfb + 63) / 64);
+    dim3 grid((nfb + 63) / 64, ctx->F);
     k_lu_solve_multi<float, 64><<<grid, 256, smem, st>>>(f32, ctx->fperm, nullptr, ctx->finv32, nfb, nfb);
     CKL();
+    if (ctx->finv16) {
+      k_to_bf16<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->finv32, ctx->finv16, tot);
+      CKL();
+    }
   } else {
     if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;
   }

@@ -98,6 +98,8 @@ struct mehdg_ctx {
   unsigned short* Ahat16 = nullptr;   // BF16 copy of A^T_i for the inner GMRES (precond_bf16)
   bool lowp_apply = false;            // set while the inner GMRES runs: apply the BF16 copy
   int apply_grid = 0, apply_grid16 = 0;   // persistent grids of the explicit apply kernels
+  int bj_grid = 0, bj_grid16 = 0;         // ... and of the block-Jacobi product
+  unsigned short* finv16 = nullptr;       // BF16 copy of the face-block inverses (precond_bf16)
   // mixed precision: S before its factorisation, for the FP64 refinement of local solves
   float* S32 = nullptr;
 

@@ -157,29 +157,46 @@ __global__ void __launch_bounds__(128) k_block_jacobi(const double* __restrict__
   for (int i = threadIdx.x; i < nfb; i += blockDim.x) z[(size_t)f * nfb + i] = sy[i];
 }
 
-// z_f = Minv_f r_f with an explicit FP32 inverse per face block (mixed precision)
-__global__ void __launch_bounds__(256) k_block_gemv(const float* __restrict__ Minv, const double* __restrict__ r,
-                                                    double* __restrict__ z, int nfb) {
+// z_f = Minv_f r_f with an explicit inverse per face block (mixed precision), stored in
+// FP32 or, for the inner GMRES with precond_bf16, in BF16 (raw 16-bit words).  Persistent
+// grid: each CTA takes a contiguous range of the F * nfb rows, stages r_f in shared
+// memory per face block and gives each warp one row at a time.
+__device__ __forceinline__ float gemv_elem(const float* p, int c) { return __ldg(p + c); }
+__device__ __forceinline__ float gemv_elem(const unsigned short* p, int c) {
+  return __uint_as_float((unsigned int)__ldg(p + c) << 16);
+}
+template <class T>
+__global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ Minv, const double* __restrict__ r,
+                                                    double* __restrict__ z, int nfb, int F, long long rows_per_cta) {
   __shared__ float xs[512];
-  const int f = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < nfb; i += blockDim.x) xs[i] = (float)r[(size_t)f * nfb + i];
-  __syncthreads();
-  const float* Mf = Minv + (size_t)f * nfb * nfb;
-  for (int row = w; row < nfb; row += nw) {
-    const float* mr = Mf + (size_t)row * nfb;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int c = lane;
-    for (; c + 96 < nfb; c += 128) {
-      s0 += mr[c] * xs[c];
-      s1 += mr[c + 32] * xs[c + 32];
-      s2 += mr[c + 64] * xs[c + 64];
-      s3 += mr[c + 96] * xs[c + 96];
+  const long long total = (long long)F * nfb, g0 = (long long)blockIdx.x * rows_per_cta;
+  const long long g1 = min(g0 + rows_per_cta, total);
+  for (long long gs = g0; gs < g1;) {
+    const int f = (int)(gs / nfb);
+    const long long ge = min(g1, (long long)(f + 1) * nfb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nfb; i += blockDim.x) xs[i] = (float)r[(size_t)f * nfb + i];
+    __syncthreads();
+    for (long long gr = gs + w; gr < ge; gr += nw) {
+      const T* mr = Minv + (size_t)gr * nfb;
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = lane + 32 * u;
+        v[u] = (c < nfb) ? gemv_elem(mr, c) : 0.f;
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = lane + 32 * u;
+        if (c < nfb) s += v[u] * xs[c];
+      }
+      for (int c = lane + 128; c < nfb; c += 32) s += gemv_elem(mr, c) * xs[c];
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) z[gr] = (double)s;
     }
-    for (; c < nfb; c += 32) s0 += mr[c] * xs[c];
-    float s = (s0 + s1) + (s2 + s3);
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) z[(size_t)f * nfb + row] = (double)s;
+    gs = ge;
   }
 }
 
@@ -293,8 +310,20 @@ int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b
 static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
   size_t smem = sizeof(double) * ctx->nfb;
   if (ctx->finv32) {
+    const bool lowp = ctx->lowp_apply && ctx->finv16;
+    int& grid = lowp ? ctx->bj_grid16 : ctx->bj_grid;
+    if (grid <= 0) {
+      int dev = 0, sms = 0, per = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      if (lowp) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv<unsigned short>, 256, 0));
+      else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv<float>, 256, 0));
+      grid = std::max(1, sms * std::max(1, per));
+    }
+    const long long total = (long long)ctx->F * ctx->nfb, rows = (total + grid - 1) / grid;
     phase_begin(ctx, PH_PRECOND);
-    k_block_gemv<<<ctx->F, 256, 0, ctx->stream>>>(ctx->finv32, r, z, ctx->nfb);
+    if (lowp) k_block_gemv<unsigned short><<<grid, 256, 0, ctx->stream>>>(ctx->finv16, r, z, ctx->nfb, ctx->F, rows);
+    else k_block_gemv<float><<<grid, 256, 0, ctx->stream>>>(ctx->finv32, r, z, ctx->nfb, ctx->F, rows);
     CKL();
     phase_end(ctx, PH_PRECOND);
     return MEHDG_OK;
@@ -323,11 +352,11 @@ static int inner_gmres_dev(mehdg_ctx* ctx, const double* r, double* z) {
   k_normalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dot, ctx->iw, IV, beta);
   CKL();
   for (int j = 0; j < nu; ++j) {
-    ctx->lowp_apply = true;   // the BF16 operator copy, when the context keeps one
+    ctx->lowp_apply = true;   // the BF16 operator and face-inverse copies, when the context keeps them
     rc = apply_trace_impl(ctx, IV + (size_t)j * n, ctx->tv);
+    if (rc == MEHDG_OK) rc = block_jacobi(ctx, ctx->tv, ctx->iw);
     ctx->lowp_apply = false;
     if (rc) return rc;
-    if ((rc = block_jacobi(ctx, ctx->tv, ctx->iw))) return rc;
     if ((rc = arnoldi_dev(ctx, IV, j, ctx->iw, n, h))) return rc;
   }
   k_lsq<<<1, 1, 0, ctx->stream>>>(h, nu, beta, y);

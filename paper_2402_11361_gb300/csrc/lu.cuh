@@ -268,7 +268,7 @@ __device__ inline void lu_solve_f32_refined(const float* __restrict__ LU, const 
 }
 
 // X = S^-1 B for a block of RC right-hand-side columns of one macro-element
-// (grid: macro x column block), from the LU factors and row permutation of S.
+// (grid: column block x macro), from the LU factors and row permutation of S.
 // B and X are row-major [n][nrhs]; the RC columns of P B live in shared memory.
 // Right-looking blocked substitution: for each 32-row block, the diagonal block of
 // L (or U) is staged in shared memory and the block's rows are solved in registers
@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
   T* x = reinterpret_cast<T*>(lum_raw);   // [n][RC]
   __shared__ T lt[32][33];                // diagonal block
   __shared__ T ls[CH][33];                // update chunk of L or U
-  const int e = blockIdx.x, c0 = blockIdx.y * RC;
+  // grid (column block, matrix): the column-block CTAs of one matrix are adjacent in
+  // launch order, so they run together and share its factors through L2
+  const int e = blockIdx.y, c0 = blockIdx.x * RC;
   const int rc = min(RC, nrhs - c0);
   const T* LU = LUall + (size_t)e * n * n;
   const int* perm = permall + (size_t)e * n;

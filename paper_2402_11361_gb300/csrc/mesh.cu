@@ -656,6 +656,8 @@ static int setup(mehdg_ctx* ctx) {
     size_t esz = ctx->opt.precision == MEHDG_PREC_MIXED ? sizeof(float) : sizeof(double);
     ALLOC(ctx->Xbuf, (size_t)E * Nu * Nt * esz / sizeof(double) + 1);
     if (ctx->opt.precond_bf16) ALLOC(ctx->Ahat16, (size_t)E * Nt * Nt);
+    if (ctx->opt.precond_bf16 && ctx->opt.precision == MEHDG_PREC_MIXED)
+      ALLOC(ctx->finv16, (size_t)F * ctx->nfb * ctx->nfb);
   }
   ctx->restart = std::min(120, std::max(2, ctx->opt.restart));
   const long long n = ctx->ntr;
@@ -849,7 +851,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
-                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16};
+                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
