@@ -336,7 +336,8 @@ template <class T>
 int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
   const int E = ctx->E, Nu = ctx->Nu, Nt = ctx->Nt;
   T* X = reinterpret_cast<T*>(ctx->Xbuf);
-  constexpr int RC = sizeof(T) == 4 ? 64 : 32;
+  // 32 right-hand sides per CTA: the 625 x 32 FP32 block (80 KB) lets two CTAs share an SM
+  constexpr int RC = 32;
   size_t smem = sizeof(T) * (size_t)Nu * RC;
   if (smem > 220 * 1024) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: local matrices too large");
   CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -272,24 +272,26 @@ __device__ inline void lu_solve_f32_refined(const float* __restrict__ LU, const 
 // B and X are row-major [n][nrhs]; the RC columns of P B live in shared memory.
 // Right-looking blocked substitution: for each 32-row block, the diagonal block of
 // L (or U) is staged in shared memory and the block's rows are solved in registers
-// (one thread per right-hand side); then every row below (forward) or above
+// (256 / RC threads per right-hand side); then every row below (forward) or above
 // (backward) is updated, x_r -= L[r, blk] x_blk, in chunks of 128 rows: the chunk of
-// L is staged in shared memory (prefetched into registers while the previous chunk
-// computes) and each thread keeps an 8-row x CPT-column tile of the update in
+// L is staged in shared memory transposed (prefetched into registers while the previous
+// chunk computes) and each thread keeps an 8-row x CPT-column tile of the update in
 // registers.  B == nullptr solves for the identity (columns of S^-1).
 template <class T, int RC>
-__global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
+__global__ void __launch_bounds__(256, (RC * sizeof(T) <= 128) ? 2 : 1)
+    k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
                                                        const T* __restrict__ Ball, T* __restrict__ Xall, int n,
                                                        int nrhs) {
   constexpr int CH = 128;                 // rows per update chunk
   constexpr int CPT = RC / 16;            // columns per thread in the update
   constexpr int PF = CH * 32 / 256;       // chunk elements per thread
-  static_assert(RC % 16 == 0 && CPT * sizeof(T) == 16, "RC");
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  static_assert(RC % 16 == 0 && (CPT * sizeof(T) == 16 || CPT * sizeof(T) == 8), "RC");
+  using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  using V = typename std::conditional<CPT * sizeof(T) == 16, V16, float2>::type;
   extern __shared__ __align__(16) unsigned char lum_raw[];
   T* x = reinterpret_cast<T*>(lum_raw);   // [n][RC]
   __shared__ T lt[32][33];                // diagonal block
-  __shared__ T ls[CH][33];                // update chunk of L or U
+  __shared__ __align__(16) T ls[32][CH + 4];   // update chunk of L or U, stored transposed [k][row]
   // grid (column block, matrix): the column-block CTAs of one matrix are adjacent in
   // launch order, so they run together and share its factors through L2
   const int e = blockIdx.y, c0 = blockIdx.x * RC;
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
       const int i = tid + 256 * j;
-      ls[i / 32][i % 32] = pf[j];
+      ls[i % 32][i / 32] = pf[j];
     }
   };
   // x[r0 + rr] -= ls[rr] . x[i0 .. i0 + ib) for the rows of the chunk
@@ -332,12 +334,21 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     for (int q = 0; q < ib; ++q) {
       const V xv = *reinterpret_cast<const V*>(x + (size_t)(i0 + q) * RC + tcol);
       const T* xs = reinterpret_cast<const T*>(&xv);
+      // the thread's 8 rows of column q of the chunk: contiguous, 16-byte aligned
+      T lv[8];
+      if constexpr (sizeof(T) == 4) {
+        const float4 l0 = *reinterpret_cast<const float4*>(&ls[q][tr * 8]);
+        const float4 l1 = *reinterpret_cast<const float4*>(&ls[q][tr * 8 + 4]);
+        lv[0] = l0.x; lv[1] = l0.y; lv[2] = l0.z; lv[3] = l0.w;
+        lv[4] = l1.x; lv[5] = l1.y; lv[6] = l1.z; lv[7] = l1.w;
+      } else {
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const T l = ls[tr * 8 + a][q];
-#pragma unroll
-        for (int o = 0; o < CPT; ++o) acc[a][o] += l * xs[o];
+        for (int a = 0; a < 8; ++a) lv[a] = ls[q][tr * 8 + a];
       }
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int o = 0; o < CPT; ++o) acc[a][o] += lv[a] * xs[o];
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -355,6 +366,65 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
       lt[a][b] = (a < ib && b < ib) ? LU[(size_t)(i0 + a) * n + i0 + b] : T(0);
     }
   };
+  // 32 x 32 diagonal-block solves: TPC threads per right-hand side, each holding the
+  // block rows q = dsub + TPC u in registers; per row the partial dot products are summed
+  // across the TPC lanes by shuffles and the owner of the row updates it
+  constexpr int TPC = 256 / RC, QPT = 32 / TPC;
+  static_assert(TPC * RC == 256 && TPC <= 32, "threads per right-hand side");
+  const int dcol = tid / TPC, dsub = tid % TPC;
+  auto diag_fwd = [&](int i0, int ib) {
+    T v[QPT];
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int q = dsub + TPC * u;
+      v[u] = (q < ib) ? x[(size_t)(i0 + q) * RC + dcol] : T(0);
+    }
+#pragma unroll
+    for (int r = 1; r < 32; ++r) {
+      if (r >= ib) break;
+      T part = T(0);
+#pragma unroll
+      for (int u = 0; u < QPT; ++u) {
+        const int q = dsub + TPC * u;
+        if (q < r) part += lt[r][q] * v[u];
+      }
+#pragma unroll
+      for (int o = TPC / 2; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (dsub == r % TPC) v[r / TPC] -= part;
+    }
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int q = dsub + TPC * u;
+      if (q < ib) x[(size_t)(i0 + q) * RC + dcol] = v[u];
+    }
+  };
+  auto diag_bwd = [&](int i0, int ib) {
+    T v[QPT];
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int q = dsub + TPC * u;
+      v[u] = (q < ib) ? x[(size_t)(i0 + q) * RC + dcol] : T(0);
+    }
+#pragma unroll
+    for (int r = 31; r >= 0; --r) {
+      if (r < ib) {
+        T part = T(0);
+#pragma unroll
+        for (int u = 0; u < QPT; ++u) {
+          const int q = dsub + TPC * u;
+          if (q > r && q < ib) part += lt[r][q] * v[u];
+        }
+#pragma unroll
+        for (int o = TPC / 2; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (dsub == r % TPC) v[r / TPC] = (v[r / TPC] - part) / lt[r][r];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int q = dsub + TPC * u;
+      if (q < ib) x[(size_t)(i0 + q) * RC + dcol] = v[u];
+    }
+  };
   __syncthreads();
   // ---- forward: L y = P b (unit diagonal)
   for (int i0 = 0; i0 < n; i0 += 32) {
@@ -363,21 +433,7 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     int r0 = i0 + ib;
     if (r0 < n) fetch(r0, n, i0, ib);
     __syncthreads();
-    for (int cc = tid; cc < RC; cc += blockDim.x) {
-      T v[32];
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = (r < ib) ? x[(i0 + r) * RC + cc] : T(0);
-#pragma unroll
-      for (int r = 1; r < 32; ++r) {
-        T s = T(0);
-#pragma unroll
-        for (int q = 0; q < r; ++q) s += lt[r][q] * v[q];
-        v[r] -= s;
-      }
-#pragma unroll
-      for (int r = 0; r < 32; ++r)
-        if (r < ib) x[(i0 + r) * RC + cc] = v[r];
-    }
+    diag_fwd(i0, ib);
     for (; r0 < n; r0 += CH) {
       stash();
       __syncthreads();
@@ -393,23 +449,7 @@ __global__ void __launch_bounds__(256) k_lu_solve_multi(const T* __restrict__ LU
     load_diag(i0, ib);
     if (i0 > 0) fetch(0, i0, i0, ib);
     __syncthreads();
-    for (int cc = tid; cc < RC; cc += blockDim.x) {
-      T v[32];
-#pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = (r < ib) ? x[(i0 + r) * RC + cc] : T(0);
-#pragma unroll
-      for (int r = 31; r >= 0; --r) {
-        if (r < ib) {
-          T s = T(0);
-#pragma unroll
-          for (int q = r + 1; q < 32; ++q) s += lt[r][q] * v[q];
-          v[r] = (v[r] - s) / lt[r][r];
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < 32; ++r)
-        if (r < ib) x[(i0 + r) * RC + cc] = v[r];
-    }
+    diag_bwd(i0, ib);
     for (int r0 = 0; r0 < i0; r0 += CH) {
       stash();
       __syncthreads();
