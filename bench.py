@@ -560,6 +560,144 @@ def run_tgv(args, ws, rank, lrank):
     return line
 
 
+def run_batched(args, ws, rank, lrank):
+    """Batched uneven steady solves: independent manufactured-solution problems of the
+    config-2 form with seeded sizes (m_c^3 macro-elements, m_c in 2..6) and degrees
+    (p in 1..3), each solved to a 1e-8 residual by the steady Newton-SER loop
+    (mehdg_dirk_stage stage 0).  The problems go through a work queue (largest first)
+    served by worker threads, each with its own CUDA stream and context, so several
+    problems of different shapes run on the GPU at once; a device-memory budget admits a
+    problem only when its blocks fit.  Reports the wall time of the batch."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+
+    dev = torch.device("cuda:%d" % lrank)
+    torch.cuda.set_device(dev)
+    probs = W.batched_problems(count=args.batch_count, seed0=1000)
+    if ws > 1:   # replicas: each rank takes every ws-th problem
+        probs = probs[rank::ws]
+    szs = [sizes(pr) for pr in probs]
+
+    def mem_bytes(z, amode):
+        Nu, Nt, E = z["Nu"], z["Nt"], z["E"]
+        w = 8.0 if amode == 0 else 4.0                 # FP64 blocks for p = 3
+        blocks = w * (4 * Nu * Nu + 2 * Nu * Nt + 3 * Nt * Nu + Nt * Nt + Nu * Nu)   # + S kept for refinement
+        extra = (4.0 * Nu * Nt + 2.0 * Nt * Nt) if amode == 1 else 0.0
+        p_ = round(z["Np"] ** (1.0 / 3.0)) // 2        # Np = (2p + 1)^3 for m = 2
+        kvol = 4.0 * 4 * z["ns"] * 8 * (p_ + 2) ** 3 * 80                             # pointwise Jacobians
+        ntr = z["F"] * z["ns"] * z["Nfn"]
+        return 1.25 * E * (blocks + extra + kvol) + 8.0 * ntr * (2 * args.restart + 40) + 256e6
+
+    def opts_for(pr, z):
+        # p <= 2: the mixed path with the stored local operators; p = 3 (Nu = 1715): FP64 blocks
+        # and the Algorithm-2 apply (the FP32 factors of these larger S made FGMRES stall)
+        if pr["p"] <= 2:
+            return 1, dict(precision=pkg.PREC_MIXED, precond=1, restart=args.restart, max_iters=3000,
+                           lin_rtol=args.lin_rtol, inner_iters=args.inner, newton_rtol=1e-8, max_newton=60,
+                           apply_mode=1, precond_bf16=1, refine_iters=args.refine)
+        return 0, dict(precision=pkg.PREC_FP64, precond=1, restart=args.restart, max_iters=3000,
+                       lin_rtol=args.lin_rtol, inner_iters=args.inner, newton_rtol=1e-8, max_newton=60,
+                       apply_mode=0)
+
+    order = sorted(range(len(probs)), key=lambda i: -szs[i]["E"] * szs[i]["Nu"] ** 2)
+    budget = args.batch_mem_gb * 1e9
+    cv = threading.Condition()
+    state = dict(next=0, used=0.0, err=None)
+    results = [None] * len(probs)
+
+    def worker():
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.Stream(device=dev)
+        while True:
+            with cv:
+                if state["next"] >= len(order) or state["err"]:
+                    return
+                i = order[state["next"]]
+                state["next"] += 1
+                amode, opts = opts_for(probs[i], szs[i])
+                need = mem_bytes(szs[i], amode)
+                while state["used"] + need > budget and state["used"] > 0:
+                    cv.wait()
+                state["used"] += need
+            try:
+                with torch.cuda.stream(stream):
+                    ctx = pkg.Context(probs[i], opts, device=dev)
+                    du, duh = W.perturbation(probs[i], 1000 + i)
+                    u, q, uh = ctx.init_state(torch.as_tensor(du, device=dev), torch.as_tensor(duh, device=dev),
+                                              lift=True)
+                    st = ctx.dirk_stage(0, 0.0, u, q, uh)
+                    stream.synchronize()
+                    results[i] = dict(E=szs[i]["E"], p=probs[i]["p"], newton=st["newton_steps"],
+                                      fgmres=st["fgmres_iters"], res=st["res"], res0=st["res0"], apply_mode=amode)
+                    ctx.close()
+            except Exception as exc:   # reported in the JSON line
+                with cv:
+                    state["err"] = "problem %d: %s" % (i, exc)
+            finally:
+                with cv:
+                    state["used"] -= need
+                    cv.notify_all()
+
+    torch.cuda.synchronize()
+    clk = ClockSampler(lrank)
+    clk.start()
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=worker) for _ in range(args.batch_workers)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    if ws > 1:
+        t = torch.tensor([wall], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        wall = float(t.item())
+    done = [r for r in results if r]
+    newton = sum(r["newton"] for r in done)
+    macro_steps = sum(r["newton"] * r["E"] for r in done)
+    by_p = {}
+    for r in done:
+        b = by_p.setdefault(r["p"], dict(problems=0, macros=0, newton_steps=0, fgmres_iters=0))
+        b["problems"] += 1
+        b["macros"] += r["E"]
+        b["newton_steps"] += r["newton"]
+        b["fgmres_iters"] += r["fgmres"]
+    return {
+        "metric": METRIC,
+        "value": wall,
+        "unit": "s per batch of %d problems" % len(probs),
+        "n_gpus": ws,
+        "steps": 1,
+        "warmup": 0,
+        "ms_per_step": wall * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 blocks + f64 residual/krylov",
+        "data": "synthetic (seeded manufactured-solution problems, seeds 1000 + k)",
+        "config": {"workload": "batched uneven steady MMS solves: %d problems, m_c in 2..6, p in 1..3, "
+                               "2^3 hexes per macro-element" % len(probs),
+                   "workers": args.batch_workers, "mem_budget_gb": args.batch_mem_gb,
+                   "schedule": "work queue, largest first, one stream and context per worker",
+                   "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "problems_solved": len(done),
+        # converged: |R_F| <= max(1e-8 |R_F^0|, 1e-14) (the library's stopping rule)
+        "all_converged_1e-8": all(r["res"] <= max(1e-8 * r["res0"], 1e-14) for r in done) and len(done) == len(probs),
+        "problems_per_s": len(done) / wall,
+        "newton_steps_total": newton,
+        "macro_newton_steps_per_s": macro_steps / wall,
+        "by_degree": by_p,
+        "not_converged": [dict(problem=i, p=r["p"], macros=r["E"], res=r["res"], res0=r["res0"])
+                          for i, r in enumerate(results) if r and r["res"] > max(1e-8 * r["res0"], 1e-14)],
+        "error": state["err"],
+        "clocks": clocks,
+    }
+
+
 def oracle_sample_time(pr, n_macro=2, fgmres_iters=None):
     """Oracle (numpy FP64) time of one Newton step on a bounded sample, scaled to the workload."""
     from oracle import solve as osolve
@@ -632,8 +770,12 @@ def main():
                     help="skip the plain FP64 (Algorithm 2) and learned-preconditioner solves")
     ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
-    ap.add_argument("--workload", default="mms", choices=["mms", "tgv"],
-                    help="mms: steady 3D manufactured solution (default); tgv: Taylor-Green DIRK steps")
+    ap.add_argument("--workload", default="mms", choices=["mms", "tgv", "batched"],
+                    help="mms: steady 3D manufactured solution (default); tgv: Taylor-Green DIRK steps; "
+                         "batched: independent uneven problems")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--batch-mem-gb", type=float, default=200.0)
     ap.add_argument("--nmac-tgv", type=int, default=16, help="TGV macro-elements per edge (16 = the config)")
     ap.add_argument("--nmac-tgv-fp64", type=int, default=8, help="reduced TGV mesh of the FP64 comparison")
     args = ap.parse_args()
@@ -648,9 +790,12 @@ def main():
     if ws > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload == "tgv":
+    if args.workload in ("tgv", "batched"):
+        if ws > 1:
+            import torch
+            torch.distributed.init_process_group("nccl")
         args.steps = args.steps or 2
-        line = run_tgv(args, ws, rank, lrank)
+        line = run_tgv(args, ws, rank, lrank) if args.workload == "tgv" else run_batched(args, ws, rank, lrank)
         if rank == 0:
             print(json.dumps(line))
         return

@@ -339,7 +339,16 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
   // 32 right-hand sides per CTA: the 625 x 32 FP32 block (80 KB) lets two CTAs share an SM
   constexpr int RC = 32;
   size_t smem = sizeof(T) * (size_t)Nu * RC;
-  if (smem > 220 * 1024) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: local matrices too large");
+  {
+    cudaFuncAttributes fa{};
+    int dev = 0, optin = 0;
+    CK(cudaFuncGetAttributes(&fa, k_lu_solve_multi<T, RC>));
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem + fa.sharedSizeBytes > (size_t)optin)
+      return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: S (Nu x 32 right-hand sides) exceeds shared memory; use "
+                                          "apply_mode 0 for this degree");
+  }
   CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((Nt + RC - 1) / RC, E);
   phase_begin(ctx, PH_TRSM);

@@ -654,6 +654,14 @@ static int setup(mehdg_ctx* ctx) {
   }
   if (ctx->opt.apply_mode == 1) {
     size_t esz = ctx->opt.precision == MEHDG_PREC_MIXED ? sizeof(float) : sizeof(double);
+    {
+      // forming A^T_i keeps a Nu x 32 block of right-hand sides in shared memory
+      int dev = 0, optin = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      if (esz * Nu * 32 + 48 * 1024 > (size_t)optin)
+        return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1 needs Nu x 32 entries in shared memory; use apply_mode 0");
+    }
     ALLOC(ctx->Xbuf, (size_t)E * Nu * Nt * esz / sizeof(double) + 1);
     if (ctx->opt.precond_bf16) ALLOC(ctx->Ahat16, (size_t)E * Nt * Nt);
     if (ctx->opt.precond_bf16 && ctx->opt.precision == MEHDG_PREC_MIXED)

@@ -137,6 +137,37 @@ def test_condensed_lu_3d_p2_matches_oracle(lib):
     ctx.close()
 
 
+def test_3d_p3_macro_matches_oracle(lib):
+    """One 3D macro-element with m = 2, p = 3 (Nu = 1715, Nt = 1470: the largest local
+    system of the batched configuration): FP64 blocks, condensed LU (the global-memory
+    LU kernel, the shared-memory panel does not fit) and the Algorithm-2 apply against
+    the oracle; the mixed path (FP32 blocks) within FP32 accuracy."""
+    pr = W.mms(dim=3, nmac=1, m=2, p=3)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 7)
+    blks, geos, onrm, _ = solve.global_assemble(P, u, q, uh)
+    cond = [solve.condense_second_layer(geos[0], blks[0], shift=0.3)]
+    x = W.random_vector(P.F * P.ns * P.Nfn, 9)
+    y_or = solve.apply_trace(P, cond, x)
+    Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+    assert (Nu, Nt) == (1715, 1470)
+    ctx = lib.Context(pr)
+    norms = ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    assert np.allclose(norms, [onrm["RQ"], onrm["RU"], onrm["RUh"], onrm["RF"]], rtol=1e-11)
+    assert rel(ctx.get_block(0, 0).reshape(Nu, Nu), blks[0]["Auu"]) < 1e-11
+    assert rel(ctx.get_block(9, 0).reshape(Nt, Nt), blks[0]["Ahh"]) < 1e-11
+    ctx.condense(shift=0.3)
+    assert np.array_equal(ctx.get_block(15, 0).astype(int), cond[0]["piv"])
+    assert rel(ctx.get_block(0, 0).reshape(Nu, Nu), cond[0]["LU"]) < 1e-10
+    assert rel(ctx.apply(to_dev(x)).cpu().numpy(), y_or) < 1e-11
+    ctx.close()
+    ctx = lib.Context(pr, dict(precision=1, apply_mode=0))
+    ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+    ctx.condense(shift=0.3)
+    assert rel(ctx.apply(to_dev(x)).cpu().numpy(), y_or) < 1e-3
+    ctx.close()
+
+
 def test_trace_apply_matches_algorithm2(condensed2d):
     P, ctx, blks, geos, cond, bhat = condensed2d
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
