@@ -93,10 +93,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
 #pragma unroll
     for (int kk = 0; kk < CG_BK; ++kk) {
       T av[8], bv[6];
+      if constexpr (sizeof(T) == 4) {
+        // explicit vector loads: 8 consecutive A entries (16-byte aligned), 6 B entries
+        // as three 8-byte pairs (the row of sB is 384 B, tn * 24 B is 8-byte aligned)
+        const float4 a0 = *reinterpret_cast<const float4*>(&sA[kk][tm * 8]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&sA[kk][tm * 8 + 4]);
+        av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+        av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+        const float2* b2 = reinterpret_cast<const float2*>(&sB[kk][tn * 6]);
+        const float2 b0 = b2[0], b1 = b2[1], bb = b2[2];
+        bv[0] = b0.x; bv[1] = b0.y; bv[2] = b1.x; bv[3] = b1.y; bv[4] = bb.x; bv[5] = bb.y;
+      } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) av[i] = sA[kk][tm * 8 + i];
+        for (int i = 0; i < 8; ++i) av[i] = sA[kk][tm * 8 + i];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) bv[j] = sB[kk][tn * 6 + j];
+        for (int j = 0; j < 6; ++j) bv[j] = sB[kk][tn * 6 + j];
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -337,6 +349,7 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
   const int E = ctx->E, Nu = ctx->Nu, Nt = ctx->Nt;
   T* X = reinterpret_cast<T*>(ctx->Xbuf);
   // 32 right-hand sides per CTA: the 625 x 32 FP32 block (80 KB) lets two CTAs share an SM
+  // (16 per CTA measured slower: more CTAs re-stream the factors)
   constexpr int RC = 32;
   size_t smem = sizeof(T) * (size_t)Nu * RC;
   {

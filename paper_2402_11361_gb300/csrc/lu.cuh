@@ -278,16 +278,18 @@ __device__ inline void lu_solve_f32_refined(const float* __restrict__ LU, const 
 // chunk computes) and each thread keeps an 8-row x CPT-column tile of the update in
 // registers.  B == nullptr solves for the identity (columns of S^-1).
 template <class T, int RC>
-__global__ void __launch_bounds__(256, (RC * sizeof(T) <= 128) ? 2 : 1)
+__global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeof(T) <= 128) ? 2 : 1))
     k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
                                                        const T* __restrict__ Ball, T* __restrict__ Xall, int n,
                                                        int nrhs) {
   constexpr int CH = 128;                 // rows per update chunk
   constexpr int CPT = RC / 16;            // columns per thread in the update
   constexpr int PF = CH * 32 / 256;       // chunk elements per thread
-  static_assert(RC % 16 == 0 && (CPT * sizeof(T) == 16 || CPT * sizeof(T) == 8), "RC");
+  static_assert(RC % 16 == 0 && (CPT * sizeof(T) == 16 || CPT * sizeof(T) == 8 || CPT * sizeof(T) == 4), "RC");
   using V16 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  using V = typename std::conditional<CPT * sizeof(T) == 16, V16, float2>::type;
+  using V8 = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+  using V = typename std::conditional<CPT * sizeof(T) == 16, V16,
+                                      typename std::conditional<CPT * sizeof(T) == 8, V8, float>::type>::type;
   extern __shared__ __align__(16) unsigned char lum_raw[];
   T* x = reinterpret_cast<T*>(lum_raw);   // [n][RC]
   __shared__ T lt[32][33];                // diagonal block
