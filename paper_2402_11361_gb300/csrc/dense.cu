@@ -51,14 +51,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
   const T* Be = a.Bc + e * a.sBe;
   constexpr int LA = CG_BM * CG_BK / 256, LB = CG_BK * CG_BN / 256;
   T ra[LA], rb[LB];
+  // A moves in 4-row x 8-column patches per warp (lane: row ll / 8, column ll % 8): 32-byte
+  // global segments, and one bank per lane in the transposed shared tile (row stride
+  // BM + 4 = 4 mod 32 banks); the thread's column is the same for all its rows
+  const int lw = tid >> 5, ll = tid & 31;
+  const int a_kq = (lw & 1) * 8 + (ll & 7), a_r = (lw >> 1) * 4 + (ll >> 3);
   auto fetch = [&](int k0) {
-    // this thread's A column kk = k0 + tid % CG_BK is the same for all its rows
-    const int kk = k0 + tid % CG_BK;
+    const int kk = k0 + a_kq;
     const int kdir = kk / a.kdiv;
     const T* Ak = Ae + kdir * a.sAk + (kk - kdir * a.kdiv);
 #pragma unroll
     for (int j = 0; j < LA; ++j) {
-      const int gr = m0 + tid / CG_BK + (256 / CG_BK) * j;
+      const int gr = m0 + a_r + 16 * j;
       ra[j] = (gr < a.M && kk < a.K) ? Ak[(size_t)gr * a.lda] : T(0);
     }
 #pragma unroll
@@ -70,10 +74,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_cond_gemm(CondA
   };
   auto stash = [&]() {
 #pragma unroll
-    for (int j = 0; j < LA; ++j) {
-      const int i = tid + 256 * j;
-      sA[i % CG_BK][i / CG_BK] = ra[j];
-    }
+    for (int j = 0; j < LA; ++j) sA[a_kq][a_r + 16 * j] = ra[j];
 #pragma unroll
     for (int j = 0; j < LB; ++j) {
       const int i = tid + 256 * j;

@@ -311,18 +311,22 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
   const int tr = tid / 16, tcol = (tid % 16) * CPT;   // update tile: rows tr*8.., columns tcol..
   T pf[PF];
   // chunk rows [r0, r1) x block columns [i0, i0 + ib) into registers (zero outside)
+  // a warp moves 4-row x 8-column patches of the chunk: 32-byte segments of 4 rows from
+  // global memory, and into the transposed shared layout (row stride CH + 4 = 4 mod 32
+  // banks) one bank per lane
+  const int lw = tid >> 5, ll = tid & 31;
   auto fetch = [&](int r0, int r1, int i0, int ib) {
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
-      const int i = tid + 256 * j, rr = i / 32, kk = i % 32;
+      const int t = lw + 8 * j, rr = (t >> 2) * 4 + (ll >> 3), kk = (t & 3) * 8 + (ll & 7);
       pf[j] = (r0 + rr < r1 && kk < ib) ? LU[(size_t)(r0 + rr) * n + i0 + kk] : T(0);
     }
   };
   auto stash = [&]() {
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
-      const int i = tid + 256 * j;
-      ls[i % 32][i / 32] = pf[j];
+      const int t = lw + 8 * j, rr = (t >> 2) * 4 + (ll >> 3), kk = (t & 3) * 8 + (ll & 7);
+      ls[kk][rr] = pf[j];
     }
   };
   // x[r0 + rr] -= ls[rr] . x[i0 .. i0 + ib) for the rows of the chunk
