@@ -366,12 +366,6 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
       }
     }
   };
-  auto load_diag = [&](int i0, int ib) {
-    for (int i = tid; i < 32 * 32; i += blockDim.x) {
-      int a = i / 32, b = i % 32;
-      lt[a][b] = (a < ib && b < ib) ? LU[(size_t)(i0 + a) * n + i0 + b] : T(0);
-    }
-  };
   // 32 x 32 diagonal-block solves: TPC threads per right-hand side, each holding the
   // block rows q = dsub + TPC u in registers; per row the partial dot products are summed
   // across the TPC lanes by shuffles and the owner of the row updates it
@@ -432,10 +426,29 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
     }
   };
   __syncthreads();
+  // the next 32 x 32 diagonal block is prefetched into registers while the current block
+  // is processed (4 entries per thread), so only the first one of each sweep waits
+  T dg[4];
+  auto fetch_diag = [&](int i0, int ib) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = tid + 256 * u, a = i / 32, b = i % 32;
+      dg[u] = (a < ib && b < ib) ? LU[(size_t)(i0 + a) * n + i0 + b] : T(0);
+    }
+  };
+  auto stash_diag = [&]() {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = tid + 256 * u;
+      lt[i / 32][i % 32] = dg[u];
+    }
+  };
   // ---- forward: L y = P b (unit diagonal)
+  fetch_diag(0, min(32, n));
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int ib = min(32, n - i0);
-    load_diag(i0, ib);
+    stash_diag();
+    if (i0 + 32 < n) fetch_diag(i0 + 32, min(32, n - i0 - 32));
     int r0 = i0 + ib;
     if (r0 < n) fetch(r0, n, i0, ib);
     __syncthreads();
@@ -450,9 +463,14 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
     __syncthreads();
   }
   // ---- backward: U x = y
+  {
+    const int il = ((n - 1) / 32) * 32;
+    fetch_diag(il, n - il);
+  }
   for (int i0 = ((n - 1) / 32) * 32; i0 >= 0; i0 -= 32) {
     const int ib = min(32, n - i0);
-    load_diag(i0, ib);
+    stash_diag();
+    if (i0 > 0) fetch_diag(i0 - 32, 32);
     if (i0 > 0) fetch(0, i0, i0, ib);
     __syncthreads();
     diag_bwd(i0, ib);
