@@ -205,13 +205,11 @@ __global__ void __launch_bounds__(256) k_recover(const T* __restrict__ S, const 
                                                  const double* __restrict__ Whk, const int* __restrict__ gather,
                                                  const double* __restrict__ duh, double* __restrict__ du,
                                                  double* __restrict__ dq, int Nu, int Nt, int Np, int Nth, int ns,
-                                                 int d, const T* __restrict__ S0, int iters) {
+                                                 int d) {
   extern __shared__ double sm[];
   double* xg = sm;        // Nt
   double* y1 = xg + Nt;   // Nu
   double* y2 = y1 + Nu;   // Nu
-  double* r = y2 + Nu;    // Nu, Nu: refinement scratch
-  double* t = r + Nu;
   const int e = blockIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = duh[gather[(size_t)e * Nt + i]];
@@ -228,7 +226,6 @@ __global__ void __launch_bounds__(256) k_recover(const T* __restrict__ S, const 
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) y2[i] = y1[pe[i]];
   __syncthreads();
   lu_solve_block<T, double>(S + (size_t)e * Nu * Nu, Nu, y2);
-  if (S0) lu_refine<T>(S + (size_t)e * Nu * Nu, pe, S0 + (size_t)e * Nu * Nu, Nu, y1, y2, r, t, iters);
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) du[(size_t)e * Nu + i] = y2[i];
   const int nq = d * ns * Np;
   for (int i = threadIdx.x; i < nq; i += blockDim.x) {
@@ -362,7 +359,7 @@ int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {
 
 int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "recover before mehdg_condense_factor");
-  size_t smem = sizeof(double) * (ctx->Nt + 4 * (size_t)ctx->Nu);
+  size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
   phase_begin(ctx, PH_RECOVER);
   if (ctx->opt.precision == MEHDG_PREC_MIXED) {
     const size_t Nu = ctx->Nu, Nt = ctx->Nt;
@@ -379,7 +376,7 @@ int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   CK(cudaFuncSetAttribute(k_recover<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_recover<double><<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Auh, ctx->gv, ctx->MinvRQ, ctx->Wk,
                                                 ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np,
-                                                ctx->Nth, ctx->ns, ctx->d, nullptr, 0);
+                                                ctx->Nth, ctx->ns, ctx->d);
   CKL();
   phase_end(ctx, PH_RECOVER);
   return MEHDG_OK;

@@ -199,8 +199,12 @@ template <int D, int P, class CT = double> struct VolCfg {
   static constexpr int NT0 = (ITEMS + 31) / 32 * 32;
   static constexpr int NT = NT0 > 512 ? 512 : NT0;
   static constexpr int OPT = (ITEMS + NT - 1) / NT;
+  // basis table T for all Gauss points of a sub-element when it fits (it is the same
+  // for every sub-element of every macro), else one chunk at a time
+  static constexpr bool TFULL = (size_t)NG * TG * sizeof(CT) <= 48 * 1024;
+  static constexpr int TROWS = TFULL ? NG : GC;
   static constexpr size_t SMEM =
-      sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + (size_t)GC * TG + 2 * (size_t)NG1 * P1 + 4);
+      sizeof(CT) * ((size_t)GC * KA + (size_t)GC * ZG + (size_t)TROWS * TG + 2 * (size_t)NG1 * P1 + 4);
 };
 
 // A_X[(t, A)][(s, B)] += sum_g sum_{alpha,beta} T[g][alpha][a] K[g][alpha][s][beta] T[g][beta][b]
@@ -219,8 +223,9 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
   constexpr int NLOCP = C::NLOCP;
   constexpr int ITEMS = C::ITEMS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT* sT = reinterpret_cast<CT*>(smem_raw);   // [GC][D+1][NLOCP]
-  CT* sK = sT + GC * TG;                      // [GC][KA]
+  constexpr bool TFULL = C::TFULL;
+  CT* sT = reinterpret_cast<CT*>(smem_raw);   // [TROWS][D+1][NLOCP]
+  CT* sK = sT + C::TROWS * TG;                // [GC][KA]
   CT* sZ = sK + GC * KA;                      // [GC][D+1][NCOL]
   CT* sb = sZ + GC * ZG;                      // 1D basis values [NG1][P1] in CT
   CT* sdb = sb + NG1 * P1;                    // 1D reference derivatives
@@ -233,6 +238,28 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
     sdb[i] = (CT)tab[NG1 * P1 + i];
   }
   __syncthreads();
+  // T[g][alpha][a] for points g0 .. g0 + ng - 1 into sT rows 0 .. ng - 1: value (alpha 0)
+  // or derivative along x_{alpha-1} of basis a at point g (rows padded with zeros)
+  auto tabulate_T = [&](int g0, int ng) {
+    for (int i = tid; i < ng * TG; i += NT) {
+      const int a = i % NLOCP, al = (i / NLOCP) % (D + 1), gg = i / TG;
+      CT v = CT(0);
+      if (a < NLOC) {
+        int t1 = g0 + gg, t2 = a;
+        v = CT(1);
+        for (int k = 0; k < D; ++k) {
+          const int gk = t1 % NG1, ak = t2 % P1;
+          t1 /= NG1; t2 /= P1;
+          v *= (al == 1 + k) ? sdb[gk * P1 + ak] * sc[k] : sb[gk * P1 + ak];
+        }
+      }
+      sT[i] = v;
+    }
+  };
+  if constexpr (TFULL) {
+    tabulate_T(0, NG);
+    __syncthreads();
+  }
   const size_t Nu = g.Nu, Np = g.Np;
   CT* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
   int icol[OPT], irow[OPT];
@@ -257,27 +284,14 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
     for (int g0 = 0; g0 < NG; g0 += GC) {
       const int gc = min(GC, NG - g0);
       for (int i = tid; i < gc * KA; i += NT) sK[i] = Kel[(size_t)g0 * KA + i];
-      // T[g][alpha][a]: value (alpha 0) or derivative along x_{alpha-1} of basis a at point g
-      for (int i = tid; i < gc * TG; i += NT) {
-        const int a = i % NLOCP, al = (i / NLOCP) % (D + 1), gg = i / TG;
-        CT v = CT(0);
-        if (a < NLOC) {
-          int t1 = g0 + gg, t2 = a;
-          v = CT(1);
-          for (int k = 0; k < D; ++k) {
-            const int gk = t1 % NG1, ak = t2 % P1;
-            t1 /= NG1; t2 /= P1;
-            v *= (al == 1 + k) ? sdb[gk * P1 + ak] * sc[k] : sb[gk * P1 + ak];
-          }
-        }
-        sT[i] = v;
-      }
+      if constexpr (!TFULL) tabulate_T(g0, gc);
+      const CT* sTc = TFULL ? sT + (size_t)g0 * TG : sT;   // T rows of this chunk
       __syncthreads();
       for (int i = tid; i < gc * ZG; i += NT) {
         const int col = i % NCOL, al = (i / NCOL) % (D + 1), gg = i / ZG;
         const int s = col / NLOC, b = col % NLOC;
         const CT* Kp = sK + gg * KA + (al * NS + s) * (D + 1);
-        const CT* Tp = sT + gg * TG + b;
+        const CT* Tp = sTc + gg * TG + b;
         CT z = CT(0);
 #pragma unroll
         for (int be = 0; be <= D; ++be) z += Kp[be] * Tp[be * NLOCP];
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
       for (int o = 0; o < OPT; ++o) {
         for (int k = 0; k < gc * (D + 1); ++k) {
           const CT z = sZ[k * NCOL + icol[o]];
-          const CT* Tk = sT + k * NLOCP + irow[o];
+          const CT* Tk = sTc + k * NLOCP + irow[o];
           if constexpr (sizeof(CT) == 4) {
 #pragma unroll
             for (int r = 0; r < RPT; r += 4) {

@@ -254,17 +254,14 @@ __global__ void k_face_blocks(const T* Ahh, const int* owner, double* fblk, int 
   fblk[i] = v;
 }
 
-// b_loc = h - B S^-1 g, one CTA per macro-element; with S0 (the FP32 copy of S before
-// its factorisation, mixed path) the local solve is refined `iters` times in FP64
+// b_loc = h - B S^-1 g, one CTA per macro-element (FP64 path)
 template <class T>
 __global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm, const T* B,
                                                      const double* gvec, const double* hvec, double* bloc, int Nu,
-                                                     int Nt, const T* S0, int iters) {
+                                                     int Nt) {
   extern __shared__ double sm[];
   double* y = sm;             // Nu: solution
   double* tmp = sm + Nu;      // Nu: right-hand side g
-  double* r = tmp + Nu;       // Nu, Nu: refinement scratch
-  double* t = r + Nu;
   const int e = blockIdx.x;
   const T* Se = S + (size_t)e * Nu * Nu;
   const int* pe = perm + (size_t)e * Nu;
@@ -273,7 +270,6 @@ __global__ void __launch_bounds__(256) k_bhat_local(const T* S, const int* perm,
   for (int i = threadIdx.x; i < Nu; i += blockDim.x) y[i] = tmp[pe[i]];
   __syncthreads();
   lu_solve_block<T, double>(Se, Nu, y);
-  if (S0) lu_refine<T>(Se, pe, S0 + (size_t)e * Nu * Nu, Nu, tmp, y, r, t, iters);
   const T* Be = B + (size_t)e * Nt * Nu;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int row = w; row < Nt; row += nw) {
@@ -536,10 +532,9 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
                                            (int)Nt, ctx->S32, ctx->opt.refine_iters);
     CKL();
   } else {
-    size_t smem = sizeof(double) * 4 * Nu;
+    size_t smem = sizeof(double) * 2 * Nu;
     CK(cudaFuncSetAttribute(k_bhat_local<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt,
-                                          nullptr, 0);
+    k_bhat_local<T><<<E, 256, smem, st>>>(Auu, ctx->perm, Ahu, ctx->gv, ctx->hv, ctx->bloc, (int)Nu, (int)Nt);
     CKL();
   }
   if (bhat) {

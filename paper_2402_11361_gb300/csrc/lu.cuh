@@ -211,31 +211,6 @@ __device__ void lu_solve_block(const T* __restrict__ LU, int n, Acc* y) {
   }
 }
 
-// Iterative refinement of x = S^-1 rhs computed from the LU factors of S: `iters`
-// steps of r = rhs - S0 x (S0 the matrix before factorisation, FP64 accumulation),
-// x += S^-1 r.  Called by all threads of the CTA; rhs (unpermuted), x, r and t are
-// shared-memory vectors of length n.
-template <class T>
-__device__ void lu_refine(const T* __restrict__ LU, const int* __restrict__ perm, const T* __restrict__ S0, int n,
-                          const double* rhs, double* x, double* r, double* t, int iters) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int it = 0; it < iters; ++it) {
-    for (int row = w; row < n; row += nw) {
-      const T* sr = S0 + (size_t)row * n;
-      double s = 0.0;
-      for (int c = lane; c < n; c += 32) s += (double)sr[c] * x[c];
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) r[row] = rhs[row] - s;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = r[perm[i]];
-    __syncthreads();
-    lu_solve_block<T, double>(LU, n, t);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += t[i];
-    __syncthreads();
-  }
-}
-
 // FP32-factor solve with FP64 refinement (mixed precision): x = S^-1 rhs by FP32
 // substitutions, then `iters` sweeps of r = rhs - S0 x accumulated in FP64 (S0 the FP32
 // matrix before factorisation, or none) and x += S^-1 r, the correction by substitutions

@@ -354,6 +354,26 @@ def test_mixed_newton_reaches_the_fp64_solution(lib):
     ctx.close()
 
 
+def test_mixed_dirk_step_reaches_the_fp64_solution(lib):
+    """The default mixed form (FP32 blocks and Jacobians, stored A^T_i, BF16 inner operator,
+    refined local solves) through one 3-stage DIRK step: the FP64 stage residuals reach
+    1e-11 and the end state matches the oracle's FP64 DIRK step to 1e-8."""
+    pr = W.periodic_uniform(dim=2, nmac=2, m=2, p=2, v=(0.1, 0.05, 0))
+    P = solve.Problem(pr)
+    du, duh = W.perturbation(pr, 4, amp=2e-3)
+    u0, q0, uh0 = _oracle_init(P, pr, du, duh)
+    ou, oq, ouh, stats = solve.dirk_step(P, u0, q0, uh0, dt=0.05, rtol=1e-13, precond="direct")
+    ctx = lib.Context(pr, dict(precision=1, apply_mode=1, precond=1, precond_bf16=1, refine_iters=1,
+                               newton_rtol=1e-11, newton_atol=1e-15, lin_rtol=1e-5, max_iters=4000))
+    u, q, uh = ctx.init_state(to_dev(du), to_dev(duh))
+    for stage in (1, 2, 3):
+        st = ctx.dirk_stage(stage, 0.05, u, q, uh)
+        assert st["res"] <= 1e-11 * st["res0"]
+    assert rel(u.cpu().numpy(), ou) < 1e-8
+    assert rel(uh.cpu().numpy(), ouh) < 1e-8
+    ctx.close()
+
+
 @pytest.mark.parametrize("iters", [0, 2])
 def test_mixed_local_solves_refined_in_fp64(lib, iters):
     """Mixed path: the recovery's local solve du = S^-1 (g + C duh) uses the FP32 LU of S;
