@@ -41,8 +41,7 @@ NMAC = 8
 # captures of the 6^3 case (216 macros; profiles/k_apply_explicit_mms3d_6cubed.md and
 # profiles/k_apply_explicit_bf16_mms3d_6cubed.md), scaled by the macro count; keyed by
 # (phase, precision, apply_mode)
-TRAFFIC_PER_MACRO = {("apply", "mixed", 1): (489.032960e6 + 4.069632e6) / 216,
-                     ("apply_bf16", "mixed", 1): (246.530048e6 + 4.774400e6) / 216}
+TRAFFIC_PER_MACRO = {("apply", "mixed", 1): (489.032960e6 + 4.069632e6) / 216}
 
 
 def workload():

@@ -94,52 +94,51 @@ __device__ __forceinline__ float warp_dot_f2(const float* __restrict__ row, cons
 }
 
 // The same product on the BF16 copy of A^T_i (inner GMRES of the multi-level
-// preconditioner): BF16 entries widened to FP32 by shifts, FP32 accumulation; the same
-// persistent row-range schedule as the FP32 kernel.
-__global__ void __launch_bounds__(256, 5) k_apply_explicit_bf16(const unsigned short* __restrict__ Ahat,
+// preconditioner), rows padded to ld entries (a multiple of 4, zeros beyond Nt): 8-byte
+// loads of four BF16 entries, consecutive across lanes, each matched by one float4 of x
+// from shared memory (no bank conflict); entries widened to FP32 by shifts, FP32
+// accumulation; the same persistent row-range schedule as the FP32 kernel.
+__global__ void __launch_bounds__(256, 5) k_apply_explicit_bf16(const unsigned short* __restrict__ Ahat, int ld,
                                                                 const int* __restrict__ gather,
                                                                 const double* __restrict__ x,
                                                                 double* __restrict__ slot, int Nt, int E,
                                                                 long long rows_per_cta) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  float* xg = reinterpret_cast<float*>(sm_raw);
+  float* xg = reinterpret_cast<float*>(sm_raw);   // ld floats, zero beyond Nt
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const float2* x2 = reinterpret_cast<const float2*>(xg);
+  const float4* x4 = reinterpret_cast<const float4*>(xg);
   const long long total = (long long)E * Nt, g0 = (long long)blockIdx.x * rows_per_cta;
   const long long g1 = min(g0 + rows_per_cta, total);
+  const int n4 = ld / 4;
   for (long long gs = g0; gs < g1;) {
    const int e = (int)(gs / Nt);
    const long long ge = min(g1, (long long)(e + 1) * Nt);
    __syncthreads();
-   for (int i = threadIdx.x; i < Nt; i += blockDim.x) xg[i] = (float)x[gather[(size_t)e * Nt + i]];
+   for (int i = threadIdx.x; i < ld; i += blockDim.x) xg[i] = i < Nt ? (float)x[gather[(size_t)e * Nt + i]] : 0.f;
    __syncthreads();
    for (long long gr = gs + w; gr < ge; gr += nw) {
-    const unsigned short* row = Ahat + (size_t)gr * Nt;
-    // 4-byte loads of BF16 pairs (rows start 4-byte aligned: Nt even), consecutive
-    // across lanes so the matching x pairs come from shared memory without conflicts;
-    // the whole row is requested at once (up to 12 loads per lane)
-    const unsigned int* w2 = reinterpret_cast<const unsigned int*>(row);
-    const int n2 = Nt / 2;
-    constexpr int RB = 12;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    for (int base = 0; base < n2; base += 32 * RB) {
-      unsigned int v[RB];
+    const uint2* w4 = reinterpret_cast<const uint2*>(Ahat + (size_t)gr * ld);
+    // the whole row is requested at once (up to 6 loads per lane)
+    constexpr int RB = 6;
+    float s0 = 0.f, s1 = 0.f;
+    for (int base = 0; base < n4; base += 32 * RB) {
+      uint2 v[RB];
 #pragma unroll
       for (int u = 0; u < RB; ++u) {
         const int j = base + lane + 32 * u;
-        v[u] = (j < n2) ? __ldg(w2 + j) : 0u;
+        v[u] = (j < n4) ? __ldg(w4 + j) : make_uint2(0u, 0u);
       }
 #pragma unroll
       for (int u = 0; u < RB; ++u) {
         const int j = base + lane + 32 * u;
-        const float2 xv = (j < n2) ? x2[j] : make_float2(0.f, 0.f);
-        const float a = __uint_as_float(v[u] << 16), b = __uint_as_float(v[u] & 0xFFFF0000u);
-        if (u & 1) s1 += a * xv.x + b * xv.y;
-        else s0 += a * xv.x + b * xv.y;
+        const float4 xv = (j < n4) ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float t = __uint_as_float(v[u].x << 16) * xv.x + __uint_as_float(v[u].x & 0xFFFF0000u) * xv.y +
+                        __uint_as_float(v[u].y << 16) * xv.z + __uint_as_float(v[u].y & 0xFFFF0000u) * xv.w;
+        if (u & 1) s1 += t;
+        else s0 += t;
       }
     }
-    if ((Nt & 1) && lane == 0) s3 += __uint_as_float((unsigned int)row[Nt - 1] << 16) * xg[Nt - 1];
-    float s = (s0 + s1) + (s2 + s3);
+    float s = s0 + s1;
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) slot[gr] = (double)s;
    }
@@ -310,14 +309,14 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
   if (ctx->opt.apply_mode == 1) {
     // persistent grid: (resident CTAs per SM) x (SM count), each CTA a contiguous
     // share of the rows, so no partial last wave
-    const bool lowp = ctx->lowp_apply && ctx->Ahat16 && (ctx->Nt % 2) == 0;
+    const bool lowp = ctx->lowp_apply && ctx->Ahat16;
     int& grid = lowp ? ctx->apply_grid16 : ctx->apply_grid;
     if (grid <= 0) {
       int dev = 0, sms = 0, per = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       if (lowp)
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_explicit_bf16, 256, sizeof(float) * ctx->Nt));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_explicit_bf16, 256, sizeof(float) * ctx->ld16));
       else
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_explicit<T, A>, 256, sizeof(A) * ctx->Nt));
       grid = std::max(1, sms * std::max(1, per));
@@ -326,8 +325,8 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
     const long long rows = (total + grid - 1) / grid;
     if (lowp) {
       phase_begin(ctx, PH_APPLY_BF16);
-      k_apply_explicit_bf16<<<grid, 256, sizeof(float) * ctx->Nt, ctx->stream>>>(ctx->Ahat16, ctx->gather, x,
-                                                                               ctx->slot, ctx->Nt, ctx->E, rows);
+      k_apply_explicit_bf16<<<grid, 256, sizeof(float) * ctx->ld16, ctx->stream>>>(
+          ctx->Ahat16, ctx->ld16, ctx->gather, x, ctx->slot, ctx->Nt, ctx->E, rows);
       CKL();
       phase_end(ctx, PH_APPLY_BF16);
       return face_reduce(ctx, ctx->slot, y);

@@ -188,11 +188,15 @@ __global__ void __launch_bounds__(256) k_cond_rhs(const T* __restrict__ A, int M
   if (lane == 0) y[(size_t)e * M + r] = s - R[(size_t)e * M + r];
 }
 
-// BF16 copy (round to nearest even) of the local operators for the inner GMRES
+// BF16 copy (round to nearest even) of row-major [rows x n] blocks for the inner GMRES,
+// rows padded to ld entries with zeros
 template <class T>
-__global__ void k_to_bf16(const T* __restrict__ x, unsigned short* __restrict__ y, long long n) {
+__global__ void k_to_bf16(const T* __restrict__ x, unsigned short* __restrict__ y, long long rows, int n, int ld) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = __bfloat16_as_ushort(__float2bfloat16_rn((float)x[i]));
+  if (i >= rows * ld) return;
+  const long long r = i / ld;
+  const int c = (int)(i - r * ld);
+  y[i] = c < n ? __bfloat16_as_ushort(__float2bfloat16_rn((float)x[r * n + c])) : (unsigned short)0;
 }
 
 __global__ void k_to_float(const double* x, float* y, long long n) {
@@ -515,7 +519,9 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     k_lu_solve_multi<float, 64><<<grid, 256, smem, st>>>(f32, ctx->fperm, nullptr, ctx->finv32, nfb, nfb);
     CKL();
     if (ctx->finv16) {
-      k_to_bf16<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->finv32, ctx->finv16, tot);
+      const long long rows = (long long)ctx->F * nfb, tot16 = rows * ctx->ldf16;
+      k_to_bf16<float><<<(unsigned)((tot16 + 255) / 256), 256, 0, st>>>(ctx->finv32, ctx->finv16, rows, nfb,
+                                                                        ctx->ldf16);
       CKL();
     }
   } else {
@@ -545,8 +551,8 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     phase_begin(ctx, PH_FORM);
     if ((rc = form_local_operator<T>(ctx, Auu, Ahu, Auh, Ahh))) return rc;
     if (ctx->Ahat16) {
-      const long long tot = (long long)E * Nt * Nt;
-      k_to_bf16<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Ahh, ctx->Ahat16, tot);
+      const long long rows = (long long)E * Nt, tot = rows * ctx->ld16;
+      k_to_bf16<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Ahh, ctx->Ahat16, rows, Nt, ctx->ld16);
       CKL();
     }
     phase_end(ctx, PH_FORM);

@@ -96,10 +96,12 @@ struct mehdg_ctx {
   float *uD32 = nullptr, *uh32 = nullptr;
   double* Xbuf = nullptr;     // S^-1 C of every macro (apply_mode 1), storage type of the blocks
   unsigned short* Ahat16 = nullptr;   // BF16 copy of A^T_i for the inner GMRES (precond_bf16)
+  int ld16 = 0;                       // its row stride: Nt rounded up to 4 (8-byte rows), zero-padded
   bool lowp_apply = false;            // set while the inner GMRES runs: apply the BF16 copy
   int apply_grid = 0, apply_grid16 = 0;   // persistent grids of the explicit apply kernels
   int bj_grid = 0, bj_grid16 = 0;         // ... and of the block-Jacobi product
   unsigned short* finv16 = nullptr;       // BF16 copy of the face-block inverses (precond_bf16)
+  int ldf16 = 0;                          // its row stride: nfb rounded up to 32, zero-padded
   // mixed precision: S before its factorisation, for the FP64 refinement of local solves
   float* S32 = nullptr;
 

@@ -21,34 +21,70 @@ namespace {
 
 constexpr int RB = 512;   // reduction blocks
 constexpr size_t RED_OUT = (size_t)RB * 128;   // dred layout: partials [128][RB], results, coefficients
+// block tickets of the one-launch reductions: 129 unsigned counters (one per vector of a
+// multi-dot, one for the norm of k_maxpy_norm), zero between launches; the context
+// clears the whole reduction buffer when it is made
+constexpr size_t RED_CNT = RED_OUT + 1024;
+constexpr int CNT_NORM = 128;
 
-__global__ void k_mdot_part(const double* __restrict__ V, long long ldv, int nv, const double* __restrict__ w,
-                            long long n, double* __restrict__ part) {
-  __shared__ double red[256 / 32];
+// Dot products out[i] = V_i . w (i < nv) in one launch: block (x, i) of the (RB, nv)
+// grid sums its grid-strided share of vector i and stores the partial; the block that
+// finishes vector i last (a ticket from an atomic counter, no waiting) adds the RB
+// partials in a fixed tree order, so the result does not depend on which block came
+// last.  With H, also H[i][col] (= or +=).  The last block resets its counter.
+__device__ __forceinline__ double block_sum_256(double s, double* red8) {
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 8; ++k) t += red8[k];
+  return t;   // valid in thread 0
+}
+// the last of the blocks that stored a partial in part[0..RB) (counter *cnt) returns
+// the fixed-order sum of those partials in thread 0 and true in every thread
+__device__ __forceinline__ bool last_block_sum(const double* part, unsigned int* cnt, unsigned int nblk, double* red,
+                                               double& total) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == nblk - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  // RB = 2 x 256 partials: the pairwise tree of a 512-wide reduction
+  red[threadIdx.x] = __ldcg(part + threadIdx.x) + __ldcg(part + threadIdx.x + 256);
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    total = red[0];
+    *cnt = 0u;
+  }
+  return true;
+}
+__global__ void __launch_bounds__(256) k_mdot(const double* __restrict__ V, long long ldv, const double* __restrict__ w,
+                                              long long n, double* __restrict__ part, unsigned int* __restrict__ cnt,
+                                              double* __restrict__ out, double* __restrict__ H, int ldh, int col,
+                                              int accumulate) {
+  __shared__ double red8[8];
+  __shared__ double red[256];
   const int i = blockIdx.y;
   const double* v = V + (size_t)i * ldv;
   double s = 0.0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
     s += v[k] * w[k];
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
+  s = block_sum_256(s, red8);
+  if (threadIdx.x == 0) part[(size_t)i * RB + blockIdx.x] = s;
+  double t;
+  if (!last_block_sum(part + (size_t)i * RB, cnt + i, gridDim.x, red, t)) return;
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[k];
-    part[(size_t)i * RB + blockIdx.x] = t;
+    out[i] = t;
+    if (H) H[(size_t)i * ldh + col] = accumulate ? H[(size_t)i * ldh + col] + t : t;
   }
-}
-__global__ void k_mdot_final(const double* __restrict__ part, double* __restrict__ out) {
-  __shared__ double red[RB];
-  const int i = blockIdx.x;
-  red[threadIdx.x] = part[(size_t)i * RB + threadIdx.x];
-  __syncthreads();
-  for (int s = RB / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[i] = red[0];
 }
 // y += sum_i c_i V_i  (c on the device)
 __global__ void k_maxpy(const double* __restrict__ V, long long ldv, int nv, const double* __restrict__ c,
@@ -58,6 +94,28 @@ __global__ void k_maxpy(const double* __restrict__ V, long long ldv, int nv, con
   double s = 0.0;
   for (int i = 0; i < nv; ++i) s += c[i] * V[(size_t)i * ldv + k];
   y[k] += sign * s;
+}
+// w -= sum_i c_i V_i over an (RB)-block grid-strided range, and *dot = |w|^2 of the
+// updated w by the same fixed-order reduction as k_mdot
+__global__ void __launch_bounds__(256) k_maxpy_norm(const double* __restrict__ V, long long ldv, int nv,
+                                                    const double* __restrict__ c, double* __restrict__ w, long long n,
+                                                    double* __restrict__ part, unsigned int* __restrict__ cnt,
+                                                    double* __restrict__ dot) {
+  __shared__ double red8[8];
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a += c[i] * V[(size_t)i * ldv + k];
+    const double y = w[k] - a;
+    w[k] = y;
+    s += y * y;
+  }
+  s = block_sum_256(s, red8);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  double t;
+  if (!last_block_sum(part, cnt, gridDim.x, red, t)) return;
+  if (threadIdx.x == 0) *dot = t;
 }
 __global__ void k_axpy(long long n, double a, const double* x, double* y) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -78,22 +136,6 @@ __global__ void k_lincomb(long long n, double a, const double* x, double b, cons
 // reads back one residual estimate per iteration, and the inner GMRES of the
 // multi-level preconditioner (a fixed number of steps) runs as one CUDA graph.
 
-// sum of the partials of vector i -> out[i]; with H, also H[i][col] (= or +=)
-__global__ void k_mdot_final_h(const double* __restrict__ part, double* __restrict__ out, double* __restrict__ H,
-                               int ldh, int col, int accumulate) {
-  __shared__ double red[RB];
-  const int i = blockIdx.x;
-  red[threadIdx.x] = part[(size_t)i * RB + threadIdx.x];
-  __syncthreads();
-  for (int s = RB / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    out[i] = red[0];
-    if (H) H[(size_t)i * ldh + col] = accumulate ? H[(size_t)i * ldh + col] + red[0] : red[0];
-  }
-}
 // v = w / sqrt(*dot) (v = 0 if the norm is 0); thread 0 stores the norm in *nrm
 __global__ void k_normalize(long long n, const double* __restrict__ dot, const double* __restrict__ w,
                             double* __restrict__ v, double* __restrict__ nrm) {
@@ -157,18 +199,13 @@ __global__ void __launch_bounds__(128) k_block_jacobi(const double* __restrict__
   for (int i = threadIdx.x; i < nfb; i += blockDim.x) z[(size_t)f * nfb + i] = sy[i];
 }
 
-// z_f = Minv_f r_f with an explicit inverse per face block (mixed precision), stored in
-// FP32 or, for the inner GMRES with precond_bf16, in BF16 (raw 16-bit words).  Persistent
-// grid: each CTA takes a contiguous range of the F * nfb rows, stages r_f in shared
-// memory per face block and gives each warp one row at a time.
-__device__ __forceinline__ float gemv_elem(const float* p, int c) { return __ldg(p + c); }
-__device__ __forceinline__ float gemv_elem(const unsigned short* p, int c) {
-  return __uint_as_float((unsigned int)__ldg(p + c) << 16);
-}
-template <class T>
-__global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ Minv, const double* __restrict__ r,
+// z_f = Minv_f r_f with an explicit inverse per face block (mixed precision).  Persistent
+// grid: each CTA takes a contiguous range of the F * nfb rows and stages r_f (FP32, in
+// dynamic shared memory of nfb floats) per face block.
+// FP32 inverses [F nfb][nfb]: one warp per row.
+__global__ void __launch_bounds__(256) k_block_gemv(const float* __restrict__ Minv, const double* __restrict__ r,
                                                     double* __restrict__ z, int nfb, int F, long long rows_per_cta) {
-  __shared__ float xs[512];
+  extern __shared__ __align__(16) float xs[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long total = (long long)F * nfb, g0 = (long long)blockIdx.x * rows_per_cta;
   const long long g1 = min(g0 + rows_per_cta, total);
@@ -179,12 +216,12 @@ __global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ Minv, 
     for (int i = threadIdx.x; i < nfb; i += blockDim.x) xs[i] = (float)r[(size_t)f * nfb + i];
     __syncthreads();
     for (long long gr = gs + w; gr < ge; gr += nw) {
-      const T* mr = Minv + (size_t)gr * nfb;
+      const float* mr = Minv + (size_t)gr * nfb;
       float v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int c = lane + 32 * u;
-        v[u] = (c < nfb) ? gemv_elem(mr, c) : 0.f;
+        v[u] = (c < nfb) ? __ldg(mr + c) : 0.f;
       }
       float s = 0.f;
 #pragma unroll
@@ -192,18 +229,66 @@ __global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ Minv, 
         const int c = lane + 32 * u;
         if (c < nfb) s += v[u] * xs[c];
       }
-      for (int c = lane + 128; c < nfb; c += 32) s += gemv_elem(mr, c) * xs[c];
+      for (int c = lane + 128; c < nfb; c += 32) s += __ldg(mr + c) * xs[c];
       for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) z[gr] = (double)s;
     }
     gs = ge;
   }
 }
+// BF16 inverses (raw 16-bit words) with rows padded to ld (a multiple of 32, zeros beyond
+// nfb): eight lanes per row, four rows per warp.  Lane l of a row reads the 4-entry
+// chunks at 32t + 4l (one 8-byte load each, 64 contiguous bytes per row and t) and the
+// matching x chunk as one float4 (128 contiguous bytes per 8 lanes: no bank conflict);
+// FP32 accumulation, a 3-step reduction within the 8 lanes.
+__global__ void __launch_bounds__(256) k_block_gemv_bf16(const unsigned short* __restrict__ Minv, int ld,
+                                                         const double* __restrict__ r, double* __restrict__ z,
+                                                         int nfb, int F, long long rows_per_cta) {
+  extern __shared__ __align__(16) float xs[];   // ld floats, zero beyond nfb
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int q = lane >> 3, l8 = lane & 7, nch = ld >> 5;
+  const long long total = (long long)F * nfb, g0 = (long long)blockIdx.x * rows_per_cta;
+  const long long g1 = min(g0 + rows_per_cta, total);
+  for (long long gs = g0; gs < g1;) {
+    const int f = (int)(gs / nfb);
+    const long long ge = min(g1, (long long)(f + 1) * nfb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) xs[i] = i < nfb ? (float)r[(size_t)f * nfb + i] : 0.f;
+    __syncthreads();
+    for (long long g4 = gs + 4 * w; g4 < ge; g4 += 4 * nw) {
+      const long long gr = g4 + q;
+      const bool act = gr < ge;
+      float s = 0.f;
+      if (act) {
+        const uint2* mr = reinterpret_cast<const uint2*>(Minv + (size_t)gr * ld);
+        for (int t0 = 0; t0 < nch; t0 += 4) {
+          uint2 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = (t0 + u < nch) ? __ldg(mr + 8 * (t0 + u) + l8) : make_uint2(0u, 0u);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (t0 + u < nch) {
+              const float4 xv = *reinterpret_cast<const float4*>(xs + 32 * (t0 + u) + 4 * l8);
+              s += __uint_as_float(v[u].x << 16) * xv.x + __uint_as_float(v[u].x & 0xFFFF0000u) * xv.y +
+                   __uint_as_float(v[u].y << 16) * xv.z + __uint_as_float(v[u].y & 0xFFFF0000u) * xv.w;
+            }
+          }
+        }
+      }
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (act && l8 == 0) z[gr] = (double)s;
+    }
+    gs = ge;
+  }
+}
+
+unsigned int* red_cnt(mehdg_ctx* ctx) { return reinterpret_cast<unsigned int*>(ctx->dred + RED_CNT); }
 
 int mdot(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* w, long long n, double* host) {
   dim3 grid(RB, nv);
-  k_mdot_part<<<grid, 256, 0, ctx->stream>>>(V, ldv, nv, w, n, ctx->dred);
-  k_mdot_final<<<nv, RB, 0, ctx->stream>>>(ctx->dred, ctx->dred + RED_OUT);
+  k_mdot<<<grid, 256, 0, ctx->stream>>>(V, ldv, w, n, ctx->dred, red_cnt(ctx), ctx->dred + RED_OUT, nullptr, 0, 0, 0);
   CKL();
   CK(cudaMemcpyAsync(ctx->hred, ctx->dred + RED_OUT, sizeof(double) * nv, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -229,9 +314,7 @@ constexpr size_t RED_SCAL = RED_OUT + 256;   // device scalars (norms, residual 
 int mdot_dev(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const double* w, long long n, double* out,
              double* H = nullptr, int ldh = 0, int col = 0, int accumulate = 0) {
   dim3 grid(RB, nv);
-  k_mdot_part<<<grid, 256, 0, ctx->stream>>>(V, ldv, nv, w, n, ctx->dred);
-  CKL();
-  k_mdot_final_h<<<nv, RB, 0, ctx->stream>>>(ctx->dred, out, H, ldh, col, accumulate);
+  k_mdot<<<grid, 256, 0, ctx->stream>>>(V, ldv, w, n, ctx->dred, red_cnt(ctx), out, H, ldh, col, accumulate);
   CKL();
   return MEHDG_OK;
 }
@@ -241,13 +324,17 @@ int mdot_dev(mehdg_ctx* ctx, const double* V, long long ldv, int nv, const doubl
 int arnoldi_dev(mehdg_ctx* ctx, double* V, int j, double* w, long long n, DevHess h) {
   double* coef = ctx->dred + RED_OUT;
   int rc;
+  double* dot = ctx->dred + RED_SCAL;
   for (int pass = 0; pass < 2; ++pass) {
     if ((rc = mdot_dev(ctx, V, n, j + 1, w, n, coef, h.H, h.m, j, pass))) return rc;
-    k_maxpy<<<(n + 255) / 256, 256, 0, ctx->stream>>>(V, n, j + 1, coef, w, n, -1.0);
+    if (pass == 0) {
+      k_maxpy<<<(n + 255) / 256, 256, 0, ctx->stream>>>(V, n, j + 1, coef, w, n, -1.0);
+    } else {
+      // second update fused with |w|^2
+      k_maxpy_norm<<<RB, 256, 0, ctx->stream>>>(V, n, j + 1, coef, w, n, ctx->dred, red_cnt(ctx) + CNT_NORM, dot);
+    }
     CKL();
   }
-  double* dot = ctx->dred + RED_SCAL;
-  if ((rc = mdot_dev(ctx, w, n, 1, w, n, dot))) return rc;
   k_normalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dot, w, V + (size_t)(j + 1) * n,
                                                          h.H + (size_t)(j + 1) * h.m + j);
   CKL();
@@ -312,18 +399,21 @@ static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
   if (ctx->finv32) {
     const bool lowp = ctx->lowp_apply && ctx->finv16;
     int& grid = lowp ? ctx->bj_grid16 : ctx->bj_grid;
+    const size_t xsm = sizeof(float) * (size_t)(lowp ? ctx->ldf16 : ctx->nfb);
     if (grid <= 0) {
       int dev = 0, sms = 0, per = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      if (lowp) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv<unsigned short>, 256, 0));
-      else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv<float>, 256, 0));
+      if (lowp) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv_bf16, 256, xsm));
+      else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv, 256, xsm));
       grid = std::max(1, sms * std::max(1, per));
     }
     const long long total = (long long)ctx->F * ctx->nfb, rows = (total + grid - 1) / grid;
     phase_begin(ctx, PH_PRECOND);
-    if (lowp) k_block_gemv<unsigned short><<<grid, 256, 0, ctx->stream>>>(ctx->finv16, r, z, ctx->nfb, ctx->F, rows);
-    else k_block_gemv<float><<<grid, 256, 0, ctx->stream>>>(ctx->finv32, r, z, ctx->nfb, ctx->F, rows);
+    if (lowp)
+      k_block_gemv_bf16<<<grid, 256, xsm, ctx->stream>>>(ctx->finv16, ctx->ldf16, r, z, ctx->nfb, ctx->F, rows);
+    else
+      k_block_gemv<<<grid, 256, xsm, ctx->stream>>>(ctx->finv32, r, z, ctx->nfb, ctx->F, rows);
     CKL();
     phase_end(ctx, PH_PRECOND);
     return MEHDG_OK;

@@ -634,6 +634,7 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
   ALLOC(ctx->dflag, 16);
   ALLOC(ctx->dred, 1 << 17);
+  CK(cudaMemsetAsync(ctx->dred, 0, sizeof(double) << 17, st));   // reduction tickets start at zero
   CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * 256));
   ALLOC(ctx->dtcerr, 4);
   CK(cudaMemsetAsync(ctx->dtcerr, 0, sizeof(int) * 4, st));
@@ -663,9 +664,14 @@ static int setup(mehdg_ctx* ctx) {
         return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1 needs Nu x 32 entries in shared memory; use apply_mode 0");
     }
     ALLOC(ctx->Xbuf, (size_t)E * Nu * Nt * esz / sizeof(double) + 1);
-    if (ctx->opt.precond_bf16) ALLOC(ctx->Ahat16, (size_t)E * Nt * Nt);
-    if (ctx->opt.precond_bf16 && ctx->opt.precision == MEHDG_PREC_MIXED)
-      ALLOC(ctx->finv16, (size_t)F * ctx->nfb * ctx->nfb);
+    if (ctx->opt.precond_bf16) {
+      ctx->ld16 = (Nt + 3) & ~3;
+      ALLOC(ctx->Ahat16, (size_t)E * Nt * ctx->ld16);
+    }
+    if (ctx->opt.precond_bf16 && ctx->opt.precision == MEHDG_PREC_MIXED) {
+      ctx->ldf16 = (ctx->nfb + 31) & ~31;
+      ALLOC(ctx->finv16, (size_t)F * ctx->nfb * ctx->ldf16);
+    }
   }
   ctx->restart = std::min(120, std::max(2, ctx->opt.restart));
   const long long n = ctx->ntr;
