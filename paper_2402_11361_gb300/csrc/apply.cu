@@ -97,7 +97,14 @@ __device__ __forceinline__ float warp_dot_f2(const float* __restrict__ row, cons
 // preconditioner), rows padded to ld entries (a multiple of 4, zeros beyond Nt): 8-byte
 // loads of four BF16 entries, consecutive across lanes, each matched by one float4 of x
 // from shared memory (no bank conflict); entries widened to FP32 by shifts, FP32
-// accumulation; the same persistent row-range schedule as the FP32 kernel.
+// accumulation; the same persistent row-range schedule as the FP32 kernel.  For rows of
+// up to 32 x RB loads a warp takes two adjacent rows at a time (3 KB in flight per warp,
+// as for one FP32 row; each x chunk serves both rows); the next pair's loads are issued
+// as soon as the current pair has been multiplied.
+__device__ __forceinline__ float bf16x4_dot(uint2 v, float4 x) {
+  return __uint_as_float(v.x << 16) * x.x + __uint_as_float(v.x & 0xFFFF0000u) * x.y +
+         __uint_as_float(v.y << 16) * x.z + __uint_as_float(v.y & 0xFFFF0000u) * x.w;
+}
 __global__ void __launch_bounds__(256, 5) k_apply_explicit_bf16(const unsigned short* __restrict__ Ahat, int ld,
                                                                 const int* __restrict__ gather,
                                                                 const double* __restrict__ x,
@@ -110,39 +117,72 @@ __global__ void __launch_bounds__(256, 5) k_apply_explicit_bf16(const unsigned s
   const long long total = (long long)E * Nt, g0 = (long long)blockIdx.x * rows_per_cta;
   const long long g1 = min(g0 + rows_per_cta, total);
   const int n4 = ld / 4;
+  constexpr int RB = 6;
+  const bool pair = n4 <= 32 * RB;
   for (long long gs = g0; gs < g1;) {
-   const int e = (int)(gs / Nt);
-   const long long ge = min(g1, (long long)(e + 1) * Nt);
-   __syncthreads();
-   for (int i = threadIdx.x; i < ld; i += blockDim.x) xg[i] = i < Nt ? (float)x[gather[(size_t)e * Nt + i]] : 0.f;
-   __syncthreads();
-   for (long long gr = gs + w; gr < ge; gr += nw) {
-    const uint2* w4 = reinterpret_cast<const uint2*>(Ahat + (size_t)gr * ld);
-    // the whole row is requested at once (up to 6 loads per lane)
-    constexpr int RB = 6;
-    float s0 = 0.f, s1 = 0.f;
-    for (int base = 0; base < n4; base += 32 * RB) {
-      uint2 v[RB];
+    const int e = (int)(gs / Nt);
+    const long long ge = min(g1, (long long)(e + 1) * Nt);
+    uint2 va[RB], vb[RB];
+    auto load_pair = [&](long long gr) {
+      const uint2* pa = reinterpret_cast<const uint2*>(Ahat) + (size_t)gr * n4 + lane;
+      const int na = gr < ge ? n4 - lane : 0, nb = gr + 1 < ge ? n4 - lane : 0;   // live entries from lane
 #pragma unroll
       for (int u = 0; u < RB; ++u) {
-        const int j = base + lane + 32 * u;
-        v[u] = (j < n4) ? __ldg(w4 + j) : make_uint2(0u, 0u);
+        va[u] = (32 * u < na) ? __ldg(pa + 32 * u) : make_uint2(0u, 0u);
+        vb[u] = (32 * u < nb) ? __ldg(pa + n4 + 32 * u) : make_uint2(0u, 0u);
       }
+    };
+    __syncthreads();
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) xg[i] = i < Nt ? (float)x[gather[(size_t)e * Nt + i]] : 0.f;
+    __syncthreads();
+    if (pair) {
+      load_pair(gs + 2 * w);
+      for (long long gr = gs + 2 * w; gr < ge; gr += 2 * nw) {
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
 #pragma unroll
-      for (int u = 0; u < RB; ++u) {
-        const int j = base + lane + 32 * u;
-        const float4 xv = (j < n4) ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float t = __uint_as_float(v[u].x << 16) * xv.x + __uint_as_float(v[u].x & 0xFFFF0000u) * xv.y +
-                        __uint_as_float(v[u].y << 16) * xv.z + __uint_as_float(v[u].y & 0xFFFF0000u) * xv.w;
-        if (u & 1) s1 += t;
-        else s0 += t;
+        for (int u = 0; u < RB; ++u) {
+          const int j = lane + 32 * u;
+          const float4 xv = (j < n4) ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float ta = bf16x4_dot(va[u], xv), tb = bf16x4_dot(vb[u], xv);
+          if (u & 1) { a1 += ta; b1 += tb; }
+          else { a0 += ta; b0 += tb; }
+        }
+        float sa = a0 + a1, sb = b0 + b1;
+        for (int o = 16; o; o >>= 1) {
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        }
+        if (lane == 0) {
+          slot[gr] = (double)sa;
+          if (gr + 1 < ge) slot[gr + 1] = (double)sb;
+        }
+        load_pair(gr + 2 * nw);
+      }
+    } else {
+      for (long long gr = gs + w; gr < ge; gr += nw) {
+        const uint2* w4 = reinterpret_cast<const uint2*>(Ahat + (size_t)gr * ld);
+        float s0 = 0.f, s1 = 0.f;
+        for (int base = 0; base < n4; base += 32 * RB) {
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int j = base + lane + 32 * u;
+            va[u] = (j < n4) ? __ldg(w4 + j) : make_uint2(0u, 0u);
+          }
+#pragma unroll
+          for (int u = 0; u < RB; ++u) {
+            const int j = base + lane + 32 * u;
+            const float4 xv = (j < n4) ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float t = bf16x4_dot(va[u], xv);
+            if (u & 1) s1 += t;
+            else s0 += t;
+          }
+        }
+        float s = s0 + s1;
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) slot[gr] = (double)s;
       }
     }
-    float s = s0 + s1;
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) slot[gr] = (double)s;
-   }
-   gs = ge;
+    gs = ge;
   }
 }
 
@@ -329,7 +369,7 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
           ctx->Ahat16, ctx->ld16, ctx->gather, x, ctx->slot, ctx->Nt, ctx->E, rows);
       CKL();
       phase_end(ctx, PH_APPLY_BF16);
-      return face_reduce(ctx, ctx->slot, y);
+      return y ? face_reduce(ctx, ctx->slot, y) : MEHDG_OK;
     }
     phase_begin(ctx, PH_APPLY);
     k_apply_explicit<T, A><<<grid, 256, sizeof(A) * ctx->Nt, ctx->stream>>>(
@@ -348,6 +388,20 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
   CKL();
   phase_end(ctx, PH_APPLY);
   return face_reduce(ctx, ctx->slot, y);
+}
+
+// The BF16 apply of the inner GMRES into the per-macro slots only (the face reduction is
+// left to the consumer); true when the context has that path.
+bool apply_bf16_slots_available(const mehdg_ctx* ctx) {
+  return ctx->opt.precision == MEHDG_PREC_MIXED && ctx->opt.apply_mode == 1 && ctx->Ahat16 && ctx->finv16;
+}
+int apply_bf16_slots(mehdg_ctx* ctx, const double* x) {
+  if (!apply_bf16_slots_available(ctx)) return ctx_fail(ctx, MEHDG_ERR_ARG, "no BF16 operator copy");
+  const bool keep = ctx->lowp_apply;
+  ctx->lowp_apply = true;
+  const int rc = apply_t<float, float>(ctx, x, nullptr);
+  ctx->lowp_apply = keep;
+  return rc;
 }
 
 int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {

@@ -151,6 +151,8 @@ int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double*
                  const mehdg_time_term* tt, double* norms);
 int condense_all(mehdg_ctx* ctx, double shift, double* bhat);
 int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y);
+bool apply_bf16_slots_available(const mehdg_ctx* ctx);
+int apply_bf16_slots(mehdg_ctx* ctx, const double* x);
 int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq);
 int precond_impl(mehdg_ctx* ctx, int kind, const double* r, double* z);
 int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_stats* st);

@@ -240,10 +240,24 @@ __global__ void __launch_bounds__(256) k_block_gemv(const float* __restrict__ Mi
 // nfb): eight lanes per row, four rows per warp.  Lane l of a row reads the 4-entry
 // chunks at 32t + 4l (one 8-byte load each, 64 contiguous bytes per row and t) and the
 // matching x chunk as one float4 (128 contiguous bytes per 8 lanes: no bank conflict);
-// FP32 accumulation, a 3-step reduction within the 8 lanes.
+// FP32 accumulation, a 3-step reduction within the 8 lanes.  For rows of up to 128
+// entries the next four rows are requested before the current ones are multiplied, and
+// a face block's first four rows before its x is gathered.
+// FROM_SLOT: r is not a trace vector but the per-macro slots of an apply, and r_f is
+// summed from the face's (up to two) owners on the fly (the face reduction fused in).
+struct SlotMap {
+  const int* owner;
+  int Nt, Nth, Nfn, twod;
+};
+__device__ __forceinline__ float bf16x4_dot(uint2 v, float4 x) {
+  return __uint_as_float(v.x << 16) * x.x + __uint_as_float(v.x & 0xFFFF0000u) * x.y +
+         __uint_as_float(v.y << 16) * x.z + __uint_as_float(v.y & 0xFFFF0000u) * x.w;
+}
+template <bool FROM_SLOT>
 __global__ void __launch_bounds__(256) k_block_gemv_bf16(const unsigned short* __restrict__ Minv, int ld,
-                                                         const double* __restrict__ r, double* __restrict__ z,
-                                                         int nfb, int F, long long rows_per_cta) {
+                                                         const double* __restrict__ r, SlotMap sm,
+                                                         double* __restrict__ z, int nfb, int F,
+                                                         long long rows_per_cta) {
   extern __shared__ __align__(16) float xs[];   // ld floats, zero beyond nfb
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int q = lane >> 3, l8 = lane & 7, nch = ld >> 5;
@@ -252,33 +266,77 @@ __global__ void __launch_bounds__(256) k_block_gemv_bf16(const unsigned short* _
   for (long long gs = g0; gs < g1;) {
     const int f = (int)(gs / nfb);
     const long long ge = min(g1, (long long)(f + 1) * nfb);
-    __syncthreads();
-    for (int i = threadIdx.x; i < ld; i += blockDim.x) xs[i] = i < nfb ? (float)r[(size_t)f * nfb + i] : 0.f;
-    __syncthreads();
-    for (long long g4 = gs + 4 * w; g4 < ge; g4 += 4 * nw) {
-      const long long gr = g4 + q;
-      const bool act = gr < ge;
-      float s = 0.f;
-      if (act) {
-        const uint2* mr = reinterpret_cast<const uint2*>(Minv + (size_t)gr * ld);
-        for (int t0 = 0; t0 < nch; t0 += 4) {
-          uint2 v[4];
+    // the first four rows' loads go out before x is gathered
+    const bool pipe = nch <= 4;
+    uint2 cur[4];
+    if (pipe) {
+      const long long gr = gs + 4 * w + q;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = (t0 + u < nch) ? __ldg(mr + 8 * (t0 + u) + l8) : make_uint2(0u, 0u);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (t0 + u < nch) {
-              const float4 xv = *reinterpret_cast<const float4*>(xs + 32 * (t0 + u) + 4 * l8);
-              s += __uint_as_float(v[u].x << 16) * xv.x + __uint_as_float(v[u].x & 0xFFFF0000u) * xv.y +
-                   __uint_as_float(v[u].y << 16) * xv.z + __uint_as_float(v[u].y & 0xFFFF0000u) * xv.w;
-            }
+      for (int u = 0; u < 4; ++u)
+        cur[u] = (gr < ge && u < nch) ? __ldg(reinterpret_cast<const uint2*>(Minv + (size_t)gr * ld) + 8 * u + l8)
+                                      : make_uint2(0u, 0u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+      float v = 0.f;
+      if (i < nfb) {
+        if (FROM_SLOT) {
+          const int s = i / sm.Nfn, j = i - s * sm.Nfn;
+          double a = 0.0;
+          for (int o = 0; o < 2; ++o) {
+            const int ow = sm.owner[2 * f + o];
+            if (ow < 0) continue;
+            const int e = ow / sm.twod, fl = ow % sm.twod;
+            a += r[(size_t)e * sm.Nt + (size_t)s * sm.Nth + fl * sm.Nfn + j];
           }
+          v = (float)a;
+        } else {
+          v = (float)r[(size_t)f * nfb + i];
         }
       }
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      if (act && l8 == 0) z[gr] = (double)s;
+      xs[i] = v;
+    }
+    __syncthreads();
+    if (pipe) {
+      for (long long g4 = gs + 4 * w; g4 < ge; g4 += 4 * nw) {
+        const long long gr = g4 + q, gn = gr + 4 * nw;
+        uint2 nxt[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          nxt[u] = (gn < ge && u < nch) ? __ldg(reinterpret_cast<const uint2*>(Minv + (size_t)gn * ld) + 8 * u + l8)
+                                        : make_uint2(0u, 0u);
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < nch) s += bf16x4_dot(cur[u], *reinterpret_cast<const float4*>(xs + 32 * u + 4 * l8));
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (gr < ge && l8 == 0) z[gr] = (double)s;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = nxt[u];
+      }
+    } else {
+      for (long long g4 = gs + 4 * w; g4 < ge; g4 += 4 * nw) {
+        const long long gr = g4 + q;
+        const bool act = gr < ge;
+        float s = 0.f;
+        if (act) {
+          const uint2* mr = reinterpret_cast<const uint2*>(Minv + (size_t)gr * ld);
+          for (int t0 = 0; t0 < nch; t0 += 4) {
+            uint2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = (t0 + u < nch) ? __ldg(mr + 8 * (t0 + u) + l8) : make_uint2(0u, 0u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (t0 + u < nch) s += bf16x4_dot(v[u], *reinterpret_cast<const float4*>(xs + 32 * (t0 + u) + 4 * l8));
+          }
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (act && l8 == 0) z[gr] = (double)s;
+      }
     }
     gs = ge;
   }
@@ -394,24 +452,31 @@ int vec_lincomb(mehdg_ctx* ctx, long long n, double a, const double* x, double b
   return MEHDG_OK;
 }
 
-static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z) {
+// from_slot: r holds the per-macro slots of an apply (BF16 face inverses only)
+static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z, bool from_slot = false) {
   size_t smem = sizeof(double) * ctx->nfb;
   if (ctx->finv32) {
     const bool lowp = ctx->lowp_apply && ctx->finv16;
+    if (from_slot && !lowp) return ctx_fail(ctx, MEHDG_ERR_ARG, "slot input needs the BF16 face inverses");
     int& grid = lowp ? ctx->bj_grid16 : ctx->bj_grid;
     const size_t xsm = sizeof(float) * (size_t)(lowp ? ctx->ldf16 : ctx->nfb);
     if (grid <= 0) {
       int dev = 0, sms = 0, per = 0;
       CK(cudaGetDevice(&dev));
       CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      if (lowp) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv_bf16, 256, xsm));
+      if (lowp) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv_bf16<true>, 256, xsm));
       else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_block_gemv, 256, xsm));
       grid = std::max(1, sms * std::max(1, per));
     }
     const long long total = (long long)ctx->F * ctx->nfb, rows = (total + grid - 1) / grid;
     phase_begin(ctx, PH_PRECOND);
-    if (lowp)
-      k_block_gemv_bf16<<<grid, 256, xsm, ctx->stream>>>(ctx->finv16, ctx->ldf16, r, z, ctx->nfb, ctx->F, rows);
+    const SlotMap sm{ctx->owner, ctx->Nt, ctx->Nth, ctx->Nfn, 2 * ctx->d};
+    if (lowp && from_slot)
+      k_block_gemv_bf16<true><<<grid, 256, xsm, ctx->stream>>>(ctx->finv16, ctx->ldf16, r, sm, z, ctx->nfb, ctx->F,
+                                                               rows);
+    else if (lowp)
+      k_block_gemv_bf16<false><<<grid, 256, xsm, ctx->stream>>>(ctx->finv16, ctx->ldf16, r, sm, z, ctx->nfb, ctx->F,
+                                                                rows);
     else
       k_block_gemv<<<grid, 256, xsm, ctx->stream>>>(ctx->finv32, r, z, ctx->nfb, ctx->F, rows);
     CKL();
@@ -441,10 +506,17 @@ static int inner_gmres_dev(mehdg_ctx* ctx, const double* r, double* z) {
   if ((rc = mdot_dev(ctx, ctx->iw, n, 1, ctx->iw, n, dot))) return rc;
   k_normalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, dot, ctx->iw, IV, beta);
   CKL();
+  const bool slots = apply_bf16_slots_available(ctx);
   for (int j = 0; j < nu; ++j) {
     ctx->lowp_apply = true;   // the BF16 operator and face-inverse copies, when the context keeps them
-    rc = apply_trace_impl(ctx, IV + (size_t)j * n, ctx->tv);
-    if (rc == MEHDG_OK) rc = block_jacobi(ctx, ctx->tv, ctx->iw);
+    if (slots) {
+      // BF16 apply into the per-macro slots; the block-Jacobi product sums the owners
+      rc = apply_bf16_slots(ctx, IV + (size_t)j * n);
+      if (rc == MEHDG_OK) rc = block_jacobi(ctx, ctx->slot, ctx->iw, true);
+    } else {
+      rc = apply_trace_impl(ctx, IV + (size_t)j * n, ctx->tv);
+      if (rc == MEHDG_OK) rc = block_jacobi(ctx, ctx->tv, ctx->iw);
+    }
     ctx->lowp_apply = false;
     if (rc) return rc;
     if ((rc = arnoldi_dev(ctx, IV, j, ctx->iw, n, h))) return rc;
