@@ -150,11 +150,26 @@ __global__ void __launch_bounds__(LU_NT) k_lu_batched(T* __restrict__ Aall, int*
 
 // y <- U^-1 L^-1 y for factors LU (row-major, unit L), y already permuted (P y).
 // Called by all threads of the CTA; y in shared memory; arithmetic in Acc.
+// Blocked by 32 rows: the warps first subtract the already-solved part from the block's
+// rows (one warp per row, dot products over the solved prefix or suffix) while the
+// 32 x 32 diagonal block is staged in shared memory (transposed, row stride 33: lane r
+// reads its row without bank conflicts); then warp 0 solves the block column by column:
+// lane l holds y_l, and once y_l is final it is broadcast by one shuffle and every lane
+// r below (above) it subtracts L[r][l] y_l (U[r][l] y_l).  The block's dependent chain
+// is one shuffle and one FMA per column, with no global-memory load inside it.
 template <class T, class Acc = double>
 __device__ void lu_solve_block(const T* __restrict__ LU, int n, Acc* y) {
+  __shared__ Acc dblk[32][33];   // dblk[l][r] = factor entry (row i0 + r, column i0 + l)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto stage = [&](int i0, int ib) {
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+      const int r = idx >> 5, l = idx & 31;
+      dblk[l][r] = (r < ib && l < ib) ? (Acc)LU[(size_t)(i0 + r) * n + i0 + l] : Acc(0);
+    }
+  };
   for (int i0 = 0; i0 < n; i0 += 32) {
     const int ib = min(32, n - i0);
+    stage(i0, ib);
     for (int r = warp; r < ib; r += nw) {
       const T* row = LU + (size_t)(i0 + r) * n;
       Acc s0 = Acc(0), s1 = Acc(0), s2 = Acc(0), s3 = Acc(0);
@@ -172,17 +187,18 @@ __device__ void lu_solve_block(const T* __restrict__ LU, int n, Acc* y) {
     }
     __syncthreads();
     if (warp == 0) {
-      for (int r = 1; r < ib; ++r) {
-        Acc v = (lane < r) ? (Acc)LU[(size_t)(i0 + r) * n + i0 + lane] * y[i0 + lane] : Acc(0);
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[i0 + r] -= v;
-        __syncwarp();
+      Acc yl = (lane < ib) ? y[i0 + lane] : Acc(0);
+      for (int l = 0; l < ib - 1; ++l) {
+        const Acc yb = __shfl_sync(0xffffffffu, yl, l);
+        if (lane > l) yl -= dblk[l][lane] * yb;
       }
+      if (lane < ib) y[i0 + lane] = yl;
     }
     __syncthreads();
   }
   for (int i0 = ((n - 1) / 32) * 32; i0 >= 0; i0 -= 32) {
     const int ib = min(32, n - i0);
+    stage(i0, ib);
     for (int r = warp; r < ib; r += nw) {
       const T* row = LU + (size_t)(i0 + r) * n;
       Acc s0 = Acc(0), s1 = Acc(0), s2 = Acc(0), s3 = Acc(0);
@@ -200,12 +216,13 @@ __device__ void lu_solve_block(const T* __restrict__ LU, int n, Acc* y) {
     }
     __syncthreads();
     if (warp == 0) {
-      for (int r = ib - 1; r >= 0; --r) {
-        Acc v = (lane > r && lane < ib) ? (Acc)LU[(size_t)(i0 + r) * n + i0 + lane] * y[i0 + lane] : Acc(0);
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[i0 + r] = (y[i0 + r] - v) / (Acc)LU[(size_t)(i0 + r) * n + i0 + r];
-        __syncwarp();
+      Acc yl = (lane < ib) ? y[i0 + lane] : Acc(0);
+      for (int l = ib - 1; l >= 0; --l) {
+        if (lane == l) yl = yl / dblk[l][l];
+        const Acc yb = __shfl_sync(0xffffffffu, yl, l);
+        if (lane < l) yl -= dblk[l][lane] * yb;
       }
+      if (lane < ib) y[i0 + lane] = yl;
     }
     __syncthreads();
   }
