@@ -358,12 +358,14 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
       }
     }
   };
-  // 32 x 32 diagonal-block solves: TPC threads per right-hand side, each holding the
-  // block rows q = dsub + TPC u in registers; per row the partial dot products are summed
-  // across the TPC lanes by shuffles and the owner of the row updates it
+  // 32 x 32 diagonal-block solves: TPC threads per right-hand side (adjacent lanes), each
+  // holding the block rows q = dsub + TPC u in registers; column by column, the owner of
+  // the finished row l broadcasts it within its lane group by one shuffle and every thread
+  // subtracts L[q][l] (U[q][l]) times it from its rows below (above) l, so the dependent
+  // chain is one shuffle and one FMA per column
   constexpr int TPC = 256 / RC, QPT = 32 / TPC;
-  static_assert(TPC * RC == 256 && TPC <= 32, "threads per right-hand side");
-  const int dcol = tid / TPC, dsub = tid % TPC;
+  static_assert(TPC * RC == 256 && TPC <= 32 && 32 % TPC == 0, "threads per right-hand side");
+  const int dcol = tid / TPC, dsub = tid % TPC, gbase = (tid & 31) & ~(TPC - 1);
   auto diag_fwd = [&](int i0, int ib) {
     T v[QPT];
 #pragma unroll
@@ -372,17 +374,14 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
       v[u] = (q < ib) ? x[(size_t)(i0 + q) * RC + dcol] : T(0);
     }
 #pragma unroll
-    for (int r = 1; r < 32; ++r) {
-      if (r >= ib) break;
-      T part = T(0);
+    for (int l = 0; l < 31; ++l) {
+      if (l >= ib - 1) break;
+      const T vb = __shfl_sync(0xffffffffu, v[l / TPC], gbase + l % TPC);
 #pragma unroll
       for (int u = 0; u < QPT; ++u) {
         const int q = dsub + TPC * u;
-        if (q < r) part += lt[r][q] * v[u];
+        if (q > l) v[u] -= lt[q][l] * vb;
       }
-#pragma unroll
-      for (int o = TPC / 2; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (dsub == r % TPC) v[r / TPC] -= part;
     }
 #pragma unroll
     for (int u = 0; u < QPT; ++u) {
@@ -398,17 +397,15 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
       v[u] = (q < ib) ? x[(size_t)(i0 + q) * RC + dcol] : T(0);
     }
 #pragma unroll
-    for (int r = 31; r >= 0; --r) {
-      if (r < ib) {
-        T part = T(0);
+    for (int l = 31; l >= 0; --l) {
+      if (l < ib) {
+        if (dsub == l % TPC) v[l / TPC] = v[l / TPC] / lt[l][l];
+        const T vb = __shfl_sync(0xffffffffu, v[l / TPC], gbase + l % TPC);
 #pragma unroll
         for (int u = 0; u < QPT; ++u) {
           const int q = dsub + TPC * u;
-          if (q > r && q < ib) part += lt[r][q] * v[u];
+          if (q < l) v[u] -= lt[q][l] * vb;
         }
-#pragma unroll
-        for (int o = TPC / 2; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (dsub == r % TPC) v[r / TPC] = (v[r / TPC] - part) / lt[r][r];
       }
     }
 #pragma unroll
