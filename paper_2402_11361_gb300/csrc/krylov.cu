@@ -4,9 +4,11 @@
 // preconditioned directions Z live on the device in FP64; the Arnoldi step uses
 // classical Gram-Schmidt applied twice (the paper's iterated CGS); dot products
 // are block-reduced in a fixed order, so results are reproducible run to run.
-// The (restart+1) x restart Hessenberg matrix and its Givens rotations stay on
-// the host.  Preconditioners: kind 0 applies (A_uhuh)^-1 face block by face block
-// with the LU factors made in mehdg_condense_factor; kind 1 runs inner_iters
+// The (restart+1) x restart Hessenberg matrix and its Givens rotations live on the
+// device; the host reads one residual estimate per outer iteration and copies the
+// rotated Hessenberg back at the end of a cycle for the back-substitution.
+// Preconditioners: kind 0 applies (A_uhuh)^-1 face block by face block (FP64 LU
+// factors, or explicit FP32/BF16 inverses in the mixed path); kind 1 runs inner_iters
 // steps of GMRES on A^, left-preconditioned by kind 0 (the paper's multi-level
 // preconditioner, a variable operator that FGMRES tolerates); kind 2 adds the
 // learned correction to kind 0.
