@@ -38,9 +38,9 @@ UNIT = "s/Newton step"
 NMAC = 8
 
 # DRAM bytes (read + write) per macro-element and launch of the apply kernels, from ncu
-# captures of the 6^3 case (216 macros; profiles/k_apply_explicit_mms3d_6cubed.md and
-# profiles/k_apply_explicit_bf16_mms3d_6cubed.md), scaled by the macro count; keyed by
-# (phase, precision, apply_mode)
+# captures of the 6^3 case (216 macros; profiles/k_apply_explicit_mms3d_6cubed.md),
+# scaled by the macro count; keyed by (phase, precision, apply_mode).  A kernel without
+# a capture of its current version has no entry (its traffic is reported as null).
 TRAFFIC_PER_MACRO = {("apply", "mixed", 1): (489.032960e6 + 4.069632e6) / 216}
 
 
@@ -60,6 +60,41 @@ def dist_env():
     rk = int(os.environ.get("RANK", "0"))
     lrk = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rk, lrk
+
+
+def rank_barrier(ws):
+    """All ranks meet here (no-op on one rank)."""
+    if ws > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x, ws, device=None):
+    """The largest x over the ranks (x itself on one rank): a timed region of the
+    replicas ends when the slowest rank ends.  device: where the collective's tensor
+    lives (the rank's GPU for NCCL, None = CPU for gloo)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws, device=None):
+    """The sum of x over the ranks (x itself on one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_value(seconds_per_step_max, ws):
+    """Whole-job time per step of N independent replicas (weak scaling): N steps, one
+    per rank, complete in the slowest rank's time per step."""
+    return seconds_per_step_max / max(1, ws)
 
 
 class ClockSampler:
@@ -279,11 +314,8 @@ def run_ours(args, ws, rank, lrank):
     t_dev = ev0.elapsed_time(ev1) / 1e3
     launches = ctx.launch_count() - l0
     clocks = clk.stop()
-    if ws > 1:
-        t = torch.tensor([t_dev], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(t.item())
-        torch.distributed.barrier()
+    t_dev = max_over_ranks(t_dev, ws, dev)
+    rank_barrier(ws)
 
     # ---- e2e: host (pinned) buffers in, state out, per step
     host = [(r[0].cpu().pin_memory(), r[1].cpu().pin_memory(), r[2].cpu().pin_memory()) for r in records]
@@ -291,6 +323,7 @@ def run_ours(args, ws, rank, lrank):
     out_q = torch.empty(q.shape, dtype=torch.float64).pin_memory()
     out_uh = torch.empty(uh.shape, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
+    rank_barrier(ws)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for k in range(args.steps):
@@ -300,7 +333,7 @@ def run_ours(args, ws, rank, lrank):
         out_uh.copy_(uh, non_blocking=True)
     e1.record(st)
     torch.cuda.synchronize()
-    t_e2e = e0.elapsed_time(e1) / 1e3
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws, dev)
     bytes_io = 8 * (u.numel() + q.numel() + uh.numel())
 
     # ---- comparison forms on the same workload (same initial state, same tolerance)
@@ -384,7 +417,7 @@ def run_ours(args, ws, rank, lrank):
     per_step = t_dev / args.steps
     line = {
         "metric": METRIC,
-        "value": per_step / ws,
+        "value": replica_value(per_step, ws),
         "unit": UNIT,
         "n_gpus": ws,
         "steps": args.steps,
@@ -462,6 +495,7 @@ def run_tgv(args, ws, rank, lrank):
     for _ in range(args.warmup):
         dirk_step(ctx, u, q, uh)
     torch.cuda.synchronize()
+    rank_barrier(ws)
     K = max(1, args.steps)
     clk = ClockSampler(lrank)
     clk.start()
@@ -475,7 +509,7 @@ def run_tgv(args, ws, rank, lrank):
         its += r["fgmres_iters"]
     ev1.record(st)
     torch.cuda.synchronize()
-    t = ev0.elapsed_time(ev1) / 1e3
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
     clocks = clk.stop()
     launches = ctx.launch_count() - l0
     # kinetic energy of the resolved field (nodal mean of rho |v|^2 / 2) as a sanity value
@@ -533,7 +567,7 @@ def run_tgv(args, ws, rank, lrank):
     per = t / K
     line = {
         "metric": METRIC,
-        "value": per / ws,
+        "value": replica_value(per, ws),
         "unit": "s/DIRK step",
         "n_gpus": ws,
         "steps": K,
@@ -550,7 +584,7 @@ def run_tgv(args, ws, rank, lrank):
                    "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
                    "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
                    "refine_iters": args.refine, "precond_bf16": args.precond_bf16,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": "1 GPU"},
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "newton_steps_per_dirk_step": newton / K,
         "fgmres_iters_per_dirk_step": its / K,
         "kinetic_energy_mean": ke,
@@ -642,6 +676,7 @@ def run_batched(args, ws, rank, lrank):
                     cv.notify_all()
 
     torch.cuda.synchronize()
+    rank_barrier(ws)
     clk = ClockSampler(lrank)
     clk.start()
     t0 = time.perf_counter()
@@ -653,13 +688,15 @@ def run_batched(args, ws, rank, lrank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = clk.stop()
-    if ws > 1:
-        t = torch.tensor([wall], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        wall = float(t.item())
+    wall = max_over_ranks(wall, ws, dev)
     done = [r for r in results if r]
-    newton = sum(r["newton"] for r in done)
-    macro_steps = sum(r["newton"] * r["E"] for r in done)
+    # whole-job counts (each rank solved its share of the batch)
+    n_done = int(sum_over_ranks(len(done), ws, dev))
+    n_probs = int(sum_over_ranks(len(probs), ws, dev))
+    newton = int(sum_over_ranks(sum(r["newton"] for r in done), ws, dev))
+    macro_steps = sum_over_ranks(sum(r["newton"] * r["E"] for r in done), ws, dev)
+    converged = all(r["res"] <= max(1e-8 * r["res0"], 1e-14) for r in done) and len(done) == len(probs)
+    converged = sum_over_ranks(0.0 if converged else 1.0, ws, dev) == 0.0
     by_p = {}
     for r in done:
         b = by_p.setdefault(r["p"], dict(problems=0, macros=0, newton_steps=0, fgmres_iters=0))
@@ -670,28 +707,29 @@ def run_batched(args, ws, rank, lrank):
     return {
         "metric": METRIC,
         "value": wall,
-        "unit": "s per batch of %d problems" % len(probs),
+        "unit": "s per batch of %d problems" % n_probs,
         "n_gpus": ws,
         "steps": 1,
         "warmup": 0,
         "ms_per_step": wall * 1e3,
         "higher_is_better": False,
-        "scaling": "weak",
+        "scaling": "strong",   # one fixed batch, split across the ranks
         "vs_baseline": None,
         "dtype": "f32 blocks + f64 residual/krylov",
         "data": "synthetic (seeded manufactured-solution problems, seeds 1000 + k)",
         "config": {"workload": "batched uneven steady MMS solves: %d problems, m_c in 2..6, p in 1..3, "
-                               "2^3 hexes per macro-element" % len(probs),
+                               "2^3 hexes per macro-element" % n_probs,
                    "workers": args.batch_workers, "mem_budget_gb": args.batch_mem_gb,
                    "schedule": "work queue, largest first, one stream and context per worker",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
-        "problems_solved": len(done),
+        "problems_solved": n_done,
         # converged: |R_F| <= max(1e-8 |R_F^0|, 1e-14) (the library's stopping rule)
-        "all_converged_1e-8": all(r["res"] <= max(1e-8 * r["res0"], 1e-14) for r in done) and len(done) == len(probs),
-        "problems_per_s": len(done) / wall,
+        "all_converged_1e-8": converged,
+        "problems_per_s": n_done / wall,
         "newton_steps_total": newton,
         "macro_newton_steps_per_s": macro_steps / wall,
         "by_degree": by_p,
+        "by_degree_scope": "rank 0's share of the batch" if ws > 1 else "whole batch",
         "not_converged": [dict(problem=i, p=r["p"], macros=r["E"], res=r["res"], res0=r["res0"])
                           for i, r in enumerate(results) if r and r["res"] > max(1e-8 * r["res0"], 1e-14)],
         "error": state["err"],
@@ -792,13 +830,13 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     if args.workload in ("tgv", "batched"):
-        if ws > 1:
-            import torch
-            torch.distributed.init_process_group("nccl")
         args.steps = args.steps or 2
         line = run_tgv(args, ws, rank, lrank) if args.workload == "tgv" else run_batched(args, ws, rank, lrank)
         if rank == 0:
             print(json.dumps(line))
+        if ws > 1:
+            import torch
+            torch.distributed.destroy_process_group()
         return
     if args.steps == 0:
         args.steps = -1       # one replay of every recorded Newton step
