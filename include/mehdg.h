@@ -98,7 +98,10 @@ typedef struct mehdg_options {
   int precond_bf16;   /* apply_mode 1 with precond 1: the inner GMRES of the multi-level
                          preconditioner applies a BF16 copy of A^T_i (half the bytes of
                          the FP32 operator; FGMRES allows the inexact preconditioner),
-                         the outer FGMRES keeps the FP32/FP64 operator */
+                         the outer FGMRES keeps the FP32/FP64 operator.  In the mixed
+                         path the face-block inverses get a BF16 copy too, and the
+                         inner block-Jacobi product reads the apply's per-macro results
+                         directly (the face sum is done inside it) */
 } mehdg_options;
 
 typedef struct mehdg_info {
