@@ -166,6 +166,34 @@ def test_viscous_flux_closed_forms():
     assert np.isclose(G[4, 1], -(tau_xy * v[0]))
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_supg_tau_limits(d):
+    """The SUPG coefficient (a reading: Sec. 2.3 defines it by reference) blends the two
+    textbook element time scales: h / (2 p (|v| + c)) when advection dominates and
+    Re rho h^2 / (4 p^2) when diffusion does, with c the ideal-gas sound speed
+    sqrt(gamma P / rho) of the conserved state.  It decreases with p, grows with h and
+    is never above either time scale."""
+    rng = np.random.default_rng(3 + d)
+    gamma = 1.4
+    rho = 0.8 + 0.4 * rng.random()
+    v = rng.standard_normal(d) * 0.3
+    P = 0.5 + rng.random()
+    rhoE = P / (gamma - 1.0) + 0.5 * rho * float(v @ v)
+    u = [rho] + list(rho * v) + [rhoE]
+    c = np.sqrt(gamma * P / rho)
+    h, p = 0.37, 2
+    t_adv = h / (2.0 * p * (np.linalg.norm(v) + c))
+    big = dict(gamma=gamma, Re=1e14)
+    assert np.isclose(ph.supg_tau(u, h, p, big), t_adv, rtol=1e-9)
+    small = dict(gamma=gamma, Re=1e-14)
+    t_dif = small["Re"] * rho * h * h / (4.0 * p * p)
+    assert np.isclose(ph.supg_tau(u, h, p, small), t_dif, rtol=1e-9)
+    mid = dict(gamma=gamma, Re=50.0)
+    tau = ph.supg_tau(u, h, p, mid)
+    assert tau <= t_adv and tau <= mid["Re"] * rho * h * h / (4.0 * p * p)
+    assert ph.supg_tau(u, h, p + 1, mid) < tau < ph.supg_tau(u, 2.0 * h, p, mid)
+
+
 # ---------------------------------------------------------------- residual and Jacobian
 
 def _uniform_state(P, u0):
