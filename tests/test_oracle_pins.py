@@ -194,6 +194,61 @@ def test_supg_tau_limits(d):
     assert ph.supg_tau(u, h, p + 1, mid) < tau < ph.supg_tau(u, 2.0 * h, p, mid)
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_numerical_flux_consistency_and_dissipation(d):
+    """Numerical flux of Sec. 2.3, (F + G)(u^) n + S (u - u^): at u = u^ it is the physical
+    flux; for a jump it adds S (u - u^) with the dissipative sign, whose inviscid part is
+    the largest |eigenvalue| of dF_n/du at u^ (found numerically, by complex-step columns)
+    and whose viscous part is the viscous flux's own coefficients: 0 for density, the
+    shear coefficient 1/Re for momentum, the heat-conduction coefficient for energy."""
+    rng = np.random.default_rng(11 + d)
+    g, Re, Pr = 1.4, 40.0, 0.72
+    phys = dict(gamma=g, Re=Re, Pr=Pr)
+    rho, T = rng.uniform(0.6, 1.5), rng.uniform(0.6, 1.5)
+    uh = fields.uniform_u(d, rho, rng.uniform(-0.4, 0.4, d), T, g)
+    q = rng.normal(size=(d + 2, d)) * 0.1
+    n = rng.normal(size=d)
+    n /= np.linalg.norm(n)
+    nl, ql = list(n), ph.to_list(q, 2)
+    F = np.array(ph.inviscid_flux(list(uh), g))
+    G = np.array(ph.viscous_flux(list(uh), ql, phys))
+    phys_flux = (F + G) @ n
+    assert np.allclose(ph.trace_flux(list(uh), ql, list(uh), nl, phys), phys_flux, atol=1e-14)
+    An = np.zeros((d + 2, d + 2))
+    for c in range(d + 2):
+        up = uh.astype(complex)
+        up[c] += 1j * ph.CS_H
+        Fc = ph.inviscid_flux(list(up), g)
+        An[:, c] = [np.imag(sum(Fc[t][k] * n[k] for k in range(d))) / ph.CS_H for t in range(d + 2)]
+    lam = np.abs(np.linalg.eigvals(An)).max()
+    visc = np.array([0.0] + [1.0 / Re] * d + [1.0 / (Re * Pr * (g - 1.0))])
+    for s in range(d + 2):
+        du = np.zeros(d + 2)
+        du[s] = 1e-3 * (1 + s)
+        jump = np.array(ph.trace_flux(list(uh), ql, list(uh + du), nl, phys)) - phys_flux
+        expect = np.zeros(d + 2)
+        expect[s] = (lam + visc[s]) * du[s]
+        assert np.allclose(jump, expect, rtol=1e-10, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_wall_operator_vanishes_on_the_wall_state(d):
+    """B^ of an isothermal moving wall is zero exactly when the trace state has the
+    interior density, the wall velocity and the wall temperature (ideal gas with
+    gamma P = rho T), and not otherwise."""
+    rng = np.random.default_rng(5 + d)
+    g = 1.4
+    u = fields.uniform_u(d, 1.1, rng.uniform(-0.3, 0.3, d), 0.9, g)
+    wall_v = list(rng.uniform(-0.2, 0.2, d)) + [0.0] * (3 - d)
+    wall_T = 1.3
+    uh = fields.uniform_u(d, u[0], np.array(wall_v[:d]), wall_T, g)
+    assert np.allclose(ph.wall_operator(list(uh), list(u), wall_T, wall_v, g), 0.0, atol=1e-14)
+    for s in range(d + 2):
+        up = uh.copy()
+        up[s] += 1e-3
+        assert np.abs(ph.wall_operator(list(up), list(u), wall_T, wall_v, g)).max() > 1e-5
+
+
 # ---------------------------------------------------------------- residual and Jacobian
 
 def _uniform_state(P, u0):
