@@ -855,7 +855,7 @@ def main():
         args.steps = -1       # one replay of every recorded Newton step
     line = run_ours(args, ws, rank, lrank)
     if rank == 0:
-        if args.cpu:
+        if args.cpu and ws == 1:   # the oracle baseline is taken at N = 1 only
             t, info = oracle_sample_time(workload(), n_macro=1,
                                          fgmres_iters=max(1, int(round(line["fgmres_iters_per_step"]))),
                                          applies_per_iter=1 + (args.inner if args.precond == 1 else 0))
