@@ -32,6 +32,8 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "time per Newton/DIRK step & FGMRES iters at 1e-8 residual; batched local LU TFLOP/s"
+MIXED_DETAIL = ("f32 blocks, Jacobians and local products; bf16 operator copies in the inner GMRES; "
+                "f64 residuals, Krylov vectors and refinement residuals")
 UNIT = "s/Newton step"
 
 
@@ -426,7 +428,8 @@ def run_ours(args, ws, rank, lrank):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32 blocks + f64 residual/krylov",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "dtype_detail": "f64 throughout" if args.precision == "fp64" else MIXED_DETAIL,
         "data": "synthetic (manufactured solution, seeded 1e-3 perturbation, seed 0)",
         "config": {"workload": "3D steady MMS cube, %d^3 macro-elements x 2^3 hexes, p=2 (%d macros, Nu=%d, Nt=%d, "
                                "%d trace DOFs)" % (NMAC, z["E"], z["Nu"], z["Nt"], z["F"] * z["ns"] * z["Nfn"]),
@@ -576,7 +579,8 @@ def run_tgv(args, ws, rank, lrank):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32 blocks + f64 residual/krylov",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
+        "dtype_detail": "f64 throughout" if args.precision == "fp64" else MIXED_DETAIL,
         "data": "synthetic (Taylor-Green initial condition, closed form)",
         "config": {"workload": "3D Taylor-Green vortex, periodic [0,2pi]^3, Re 1600, M0 0.1, %d^3 macro-elements "
                                "x 2^3 hexes, p=2 (%d macros, %d trace DOFs), DIRK3 dt = 0.05 t_c"
@@ -715,7 +719,8 @@ def run_batched(args, ws, rank, lrank):
         "higher_is_better": False,
         "scaling": "strong",   # one fixed batch, split across the ranks
         "vs_baseline": None,
-        "dtype": "f32 blocks + f64 residual/krylov",
+        "dtype": "f32",
+        "dtype_detail": MIXED_DETAIL + " (p = 3 problems in f64)",
         "data": "synthetic (seeded manufactured-solution problems, seeds 1000 + k)",
         "config": {"workload": "batched uneven steady MMS solves: %d problems, m_c in 2..6, p in 1..3, "
                                "2^3 hexes per macro-element" % n_probs,
