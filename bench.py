@@ -444,7 +444,7 @@ def run_ours(args, ws, rank, lrank):
         "trace_apply_gbs": apply_gbs,
         "phases_ms": ph_mean,
         "compare": compare,
-        "e2e": {"value": t_e2e / args.steps / ws, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+        "e2e": {"value": replica_value(t_e2e / args.steps, ws), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                 "d2h_bytes_per_step": bytes_io},
         "gpu_launches": launches,
         "roofline": roof,
