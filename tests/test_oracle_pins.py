@@ -394,6 +394,34 @@ def test_condense_solve_recover_equals_monolithic(small2d):
         assert np.allclose(dU[e].reshape(-1), x[o + P.d * P.ns * P.Np:o + nloc], atol=1e-10)
 
 
+@pytest.mark.parametrize("case", ["mms2d", "mms3d", "tgv3d_periodic"])
+def test_face_blocks_are_the_diagonal_of_the_assembled_trace_block(case):
+    """Block-Jacobi preconditioner (Sec. 4.2): the face blocks equal the diagonal blocks
+    of the global A_uhuh assembled independently through the gather maps (which carry
+    each owner's face-node order), the global A_uhuh has no coupling between different
+    faces (HDG traces interact only through the element unknowns), and the
+    preconditioner applies the exact inverse of each block."""
+    pr = {"mms2d": lambda: W.mms(dim=2, nmac=3, m=2, p=2), "mms3d": lambda: W.mms(dim=3, nmac=2, m=1, p=1),
+          "tgv3d_periodic": lambda: W.tgv(nmac=2, m=1, p=1)}[case]()
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 3)
+    blks, _, _, _ = solve.global_assemble(P, u, q, uh)
+    n, nb = P.F * P.ns * P.Nfn, P.ns * P.Nfn
+    G = np.zeros((n, n))
+    for e in range(P.E):
+        m = P.maps[e].reshape(-1)
+        G[np.ix_(m, m)] += blks[e]["Ahh"]
+    fb = solve.face_blocks(P, blks)
+    off = G.copy()
+    for f in range(P.F):
+        assert np.array_equal(fb[f], G[f * nb:(f + 1) * nb, f * nb:(f + 1) * nb])
+        off[f * nb:(f + 1) * nb, f * nb:(f + 1) * nb] = 0.0
+    assert not off.any()
+    r = W.random_vector(n, 4)
+    z = solve.block_jacobi(P, [solve.lu_factor(fb[f]) for f in range(P.F)], r)
+    assert np.allclose(G @ z, r, rtol=0, atol=1e-10 * np.abs(r).max())
+
+
 def test_fgmres_equals_dense_solve(small2d):
     P, blks, geos, cond = small2d
     A = solve.explicit_trace_matrix(P, cond)
