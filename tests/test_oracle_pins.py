@@ -422,6 +422,33 @@ def test_face_blocks_are_the_diagonal_of_the_assembled_trace_block(case):
     assert np.allclose(G @ z, r, rtol=0, atol=1e-10 * np.abs(r).max())
 
 
+def test_inner_gmres_minimises_the_residual_over_the_krylov_space():
+    """The fixed-step inner GMRES of the multi-level preconditioner (Sec. 4.2): after nu
+    steps its iterate minimises |M^-1 (b - A z)| over the Krylov space K_nu(M^-1 A,
+    M^-1 b) (checked against a brute-force least-squares fit on an explicit, orthonormalised
+    Krylov basis), the minimum never grows with nu, and at nu = n it is the exact solution."""
+    rng = np.random.default_rng(8)
+    n = 12
+    A = np.eye(n) * 3 + rng.standard_normal((n, n))
+    Md = np.diag(2 + rng.random(n))
+    Minv = lambda v: np.linalg.solve(Md, v)
+    b = rng.standard_normal(n)
+    B = np.linalg.solve(Md, A)
+    c = Minv(b)
+    prev = np.inf
+    for nu in range(1, n + 1):
+        z = solve.gmres_fixed(lambda v: A @ v, Minv, b, nu)
+        K = np.stack([np.linalg.matrix_power(B, k) @ c for k in range(nu)], 1)
+        Q, _ = np.linalg.qr(K)
+        coef = np.linalg.lstsq(B @ Q, c, rcond=None)[0]
+        best = np.linalg.norm(c - B @ (Q @ coef))
+        res = np.linalg.norm(c - B @ z)
+        assert abs(res - best) <= 1e-9 * np.linalg.norm(c)
+        assert res <= prev + 1e-12
+        prev = res
+    assert np.allclose(z, np.linalg.solve(A, b), rtol=0, atol=1e-9 * np.abs(np.linalg.solve(A, b)).max())
+
+
 def test_fgmres_equals_dense_solve(small2d):
     P, blks, geos, cond = small2d
     A = solve.explicit_trace_matrix(P, cond)
