@@ -511,6 +511,82 @@ def test_dirk_step_conserves_mass_momentum_energy():
     assert all(s["RF"] <= 1e-11 for s in stats)
 
 
+def test_dirk_step_self_convergence_rate_three():
+    """Sec. 2.4, eq. C242 with Alexander's DIRK(3,3): on a smooth periodic 2D flow the
+    time-discretisation error of the whole HDG step (stage history term, stage
+    solves, u^{n+1} = u^{n,3}) falls at rate 3.  Successive differences of the state at
+    t = 0.04 from 1, 2, 4, 8 steps on one fixed mesh cancel the spatial error.  A wrong
+    sign or index in the history term makes the scheme inconsistent or first order,
+    which this rate exposes (conservation alone does not: any time term conserves).
+    SUPG is off: its |v| is not smooth at the stagnation points of this flow."""
+    pr = W.periodic_uniform(dim=2, nmac=2, m=2, p=1, v=(0.0, 0.0, 0), supg=0)
+    P = solve.Problem(pr)
+    V = 0.1
+
+    def ufun(x):
+        v1 = V * np.sin(2 * np.pi * x[0]) * np.cos(2 * np.pi * x[1])
+        v2 = -V * np.cos(2 * np.pi * x[0]) * np.sin(2 * np.pi * x[1])
+        return fields.conserved(1.0 + 0 * x[0], [v1, v2], 1 / 1.4 + 0 * x[0], 1.4)
+
+    u0, q0, uh0 = _init_from_field(P, ufun, None)
+    T = 0.04
+    ends = []
+    for n in (1, 2, 4, 8):
+        u, q, uh = u0.copy(), q0.copy(), uh0.copy()
+        for _ in range(n):
+            u, q, uh, _ = solve.dirk_step(P, u, q, uh, dt=T / n, rtol=1e-12, precond="direct")
+        ends.append(u)
+    diff = [np.linalg.norm(a - b) for a, b in zip(ends[:-1], ends[1:])]
+    rates = [np.log2(diff[i] / diff[i + 1]) for i in range(2)]
+    assert all(2.7 < r < 3.3 for r in rates), (diff, rates)
+
+
+def test_tgv_initial_state_closed_form():
+    """Sec. 5.3, eq. TGV0: the initial velocity is divergence-free, the printed pressure
+    is the incompressible pressure of that velocity (Laplacian of P equals minus
+    sum_ij d_i v_j d_j v_i with rho_0 = 1), the state is isothermal (P / rho = P_0 /
+    rho_0, i.e. rho = gamma P with P_0 = 1/gamma) and 2 pi periodic.  Derivatives by the
+    complex step (first) and central differences (second), not from the formula."""
+    g, V0 = 1.4, 0.1
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 2 * np.pi, size=(3, 40))
+
+    def prim(xx):
+        u = fields.tgv_u(xx, V0, g)
+        rho = u[0]
+        v = u[1:4] / rho
+        P = (g - 1) * (u[4] - 0.5 * rho * (v * v).sum(0))
+        return rho, v, P
+
+    rho, v, P = prim(x)
+    h = 1e-30
+    dv = np.zeros((3, 3, x.shape[1]))          # dv[i][j] = d v_j / d x_i
+    for i in range(3):
+        xc = x.astype(complex)
+        xc[i] += 1j * h
+        dv[i] = np.imag(prim(xc)[1]) / h
+    assert np.abs(np.trace(dv)).max() < 1e-15
+    lapP = 0.0
+    hf = 1e-3
+    for i in range(3):
+        e = np.zeros((3, 1))
+        e[i] = hf
+        lapP = lapP + (prim(x + e)[2] - 2 * P + prim(x - e)[2]) / hf ** 2
+    rhs = -np.einsum("ijn,jin->n", dv, dv)
+    assert np.allclose(lapP, rhs, rtol=0, atol=1e-6 * V0 ** 2)
+    assert np.allclose(rho, g * P, rtol=1e-14)
+    assert np.isclose(prim(np.zeros((3, 1)) + np.array([[np.pi / 2], [0.0], [0.0]]))[1][0, 0], V0)
+    for k in range(3):
+        s = np.zeros((3, 1))
+        s[k] = 2 * np.pi
+        assert np.allclose(fields.tgv_u(x + s, V0, g), fields.tgv_u(x, V0, g), atol=1e-14)
+    # mean density rho_0 = 1: the pressure fluctuation has zero mean over the period
+    n = 24
+    t = np.arange(n) * 2 * np.pi / n
+    X = np.array(np.meshgrid(t, t, t, indexing="ij")).reshape(3, -1)
+    assert abs(prim(X)[0].mean() - 1.0) < 1e-14
+
+
 # ---------------------------------------------------------------- convergence rates
 
 def _init_from_field(P, ufun, qfun):
