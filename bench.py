@@ -1,20 +1,23 @@
-"""Benchmark: time per Newton step of the steady manufactured-solution solve (3D cube,
-8^3 macro-elements of 2^3 hexes, p = 2) to a 1e-8 nonlinear residual, FGMRES
-iterations, batched local LU TFLOP/s, on one GB300.
+"""Benchmark of the macro-element HDG hot path on one GB300: time per Newton step of the
+DIRK3 integration of the 3D Taylor-Green vortex (periodic [0, 2 pi]^3, 16^3 macro-elements
+of 2^3 hexes, p = 2, Re 1600, M0 0.1, dt = 0.05 t_c), FGMRES iterations per step and
+batched local LU TFLOP/s.
 
-A "step" is one Newton step of that solve: assembly of residuals and Newton
-blocks, second-layer condensation and batched LU, FGMRES on the trace system,
-local recovery and the state update.  The warm-up runs the whole solve once and
-records the state and pseudo-time step entering every Newton step; the timed
-region replays K Newton steps of that sequence (step k uses recorded state
-k mod N), so the per-step mean over N steps is the mean over the real solve.
-Inputs (about 18 GB of blocks per step) exceed the 129 MB L2, so no flush is needed.
+A "step" is one Newton step of a DIRK stage (Sec. 3.1, eq. C242): assembly of the
+residuals and Newton blocks, second-layer condensation and batched LU, FGMRES on the
+trace system, local recovery, the state update and the assembly at the new state
+(plus, when a step opens a stage, the assembly of the stage's first residual).  Each
+step is one mehdg_newton_step call of the library (mehdg_stage_begin / mehdg_stage_end
+open and close the stages; three stages make a DIRK step).  The value is the plain FP64
+form; the same line reports the mixed-precision form and the learned preconditioner
+correction on the same integration, each at the same 1e-8 relative Newton residual.
+Inputs (about 150 GB of blocks per step) exceed the 129 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
-                  [--impl ours|reference]
+                  [--workload tgv|mms|batched] [--impl ours|reference]
 
---impl reference times the FP64 numpy oracle on the host cores on a bounded
-sample of the same workload (a few macro-elements), scaled to the full problem.
+--impl reference times the FP64 numpy oracle on the host cores for the same metric on a
+bounded sample of the same workload (it prints what it ran and how it was scaled).
 """
 import argparse
 import json
@@ -35,6 +38,9 @@ METRIC = "time per Newton/DIRK step & FGMRES iters at 1e-8 residual; batched loc
 MIXED_DETAIL = ("f32 blocks, Jacobians and local products; bf16 operator copies in the inner GMRES; "
                 "f64 residuals, Krylov vectors and refinement residuals")
 UNIT = "s/Newton step"
+UNIT_TGV = "s/Newton step"
+WORKLOAD_TGV = ("3D Taylor-Green vortex, periodic [0,2pi]^3, Re 1600, M0 0.1, %d^3 macro-elements x 2^3 hexes, "
+                "p=2 (%d^3 = %d macros, Nu=625, Nt=750, %d trace DOFs), DIRK3 dt = 0.05 t_c, Newton steps")
 
 
 NMAC = 8
@@ -454,15 +460,190 @@ def run_ours(args, ws, rank, lrank):
     return line
 
 
-def run_tgv(args, ws, rank, lrank):
-    """Unsteady Taylor-Green vortex (periodic [0, 2 pi]^3, Re 1600, M0 0.1, p = 2): time per
-    DIRK3 step (three stages, each a Newton solve to a 1e-8 relative residual).
+class StepDriver:
+    """Newton steps of the DIRK3 integration through the library's step calls: each step()
+    is one mehdg_newton_step, with mehdg_stage_begin / mehdg_stage_end opening and closing
+    the stages (stage 1, 2, 3, then the next time step)."""
 
-    Warm-up: W DIRK steps from the initial condition (FGMRES pairs recorded for the
-    learned correction).  Timed: K DIRK steps.  Compare: the learned correction
-    (trained on the recorded pairs) against the multi-level preconditioner over the
-    same K steps from the same state, and the plain FP64 method (Algorithm 2 apply,
-    FP64 LU) against the mixed path on one DIRK step of a reduced mesh."""
+    def __init__(self, ctx, dt, max_newton=60):
+        self.ctx, self.dt, self.max_newton = ctx, dt, max_newton
+        self.stage, self.open, self.in_stage = 1, False, 0
+        self.newton = self.fgmres = self.dirk_steps = self.status = 0
+
+    def step(self, u, q, uh):
+        while True:
+            if not self.open:
+                st = self.ctx.stage_begin(self.stage, self.dt, u, q, uh)
+                self.open, self.in_stage = True, 0
+                if st["converged"]:
+                    self._close(u)
+                    continue
+            st = self.ctx.newton_step(u, q, uh)
+            self.newton += 1
+            self.in_stage += 1
+            self.fgmres += st["fgmres_iters"]
+            self.status |= st["status"]
+            if st["converged"]:
+                self._close(u)
+            elif self.in_stage >= self.max_newton:
+                raise RuntimeError("Newton cap reached in DIRK stage %d" % self.stage)
+            return st
+
+    def _close(self, u):
+        self.ctx.stage_end(u)
+        self.open = False
+        if self.stage == 3:
+            self.dirk_steps += 1
+        self.stage = self.stage % 3 + 1
+
+    def finish_dirk_step(self, u, q, uh):
+        while self.open or self.stage != 1:
+            self.step(u, q, uh)
+
+
+def dirk_steps_timed(ctx, n, dt, u, q, uh, st):
+    """n DIRK steps by mehdg_dirk_stage (three calls per step), timed with CUDA events."""
+    import torch
+    tot = dict(newton_steps=0, fgmres_iters=0, status=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n):
+        for stage in (1, 2, 3):
+            r = ctx.dirk_stage(stage, dt, u, q, uh)
+            tot["newton_steps"] += r["newton_steps"]
+            tot["fgmres_iters"] += r["fgmres_iters"]
+            tot["status"] |= r["status"]
+    e1.record(st)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    tot.update(time_s=t, s_per_dirk_step=t / max(n, 1), s_per_newton_step=t / max(tot["newton_steps"], 1),
+               fgmres_iters_per_newton_step=tot["fgmres_iters"] / max(tot["newton_steps"], 1),
+               fallback=bool(tot["status"] & 1), dirk_steps=n)
+    return tot
+
+
+def gemm_peaks(torch):
+    """Measured dense rates of this GPU for the roofline denominators the driver's file does
+    not hold: cuBLAS DGEMM 4096^3 (FP64 pipe), SGEMM 8192^3 without and with TF32, best of 5
+    (CUDA events).  Returns TFLOP/s."""
+    out = {}
+    saved = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, n, tf32 in (("fp64", torch.float64, 4096, False), ("fp32", torch.float32, 8192, False),
+                              ("tf32", torch.float32, 8192, True)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        c = torch.matmul(a, b)
+        best = 1e9
+        for _ in range(5):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            torch.matmul(a, b, out=c)
+            e.record()
+            e.synchronize()
+            best = min(best, s.elapsed_time(e) / 1e3)
+        out[name] = 2.0 * n ** 3 / best / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = saved
+    torch.cuda.empty_cache()
+    return out
+
+
+def sf_contract_macs(d, p):
+    """Multiply-adds of the sum-factorised volume contraction per (input, test species, trial
+    species, sub-element): an x pass over the (alpha, beta) pairs grouped by the classes of
+    their remaining factors, then a pass per further axis over the merged classes."""
+    p1, g1 = p + 1, p + 2
+
+    def cls(a, done):
+        return 0 if (a == 0 or a <= done) else a - done
+    pairs = [(a, b) for a in range(d + 1) for b in range(d + 1) if not (a == 0 and b != 0)]
+    macs = len(pairs) * g1 ** (d - 1) * p1 * p1 * g1                       # x pass
+    if d == 3:
+        n1c = {}
+        for a in range(d + 1):
+            n1c.setdefault(cls(a, 2), set()).add(cls(a, 1))
+        macs += sum(len(n1c[za]) * len(n1c[zb]) for za in n1c for zb in n1c) * g1 * p1 ** 4 * g1   # y pass
+    macs += 4 * g1 * p1 ** (2 * d)                                           # last pass
+    return macs
+
+
+def kernel_work(z, precision, apply_mode):
+    """Algorithmic work of one execution of each phase over all E macro-elements:
+    (kind, amount, kernel name).  kind "flop" or "byte"."""
+    E, Nu, Nt, Np, Nth, d, ns = z["E"], z["Nu"], z["Nt"], z["Np"], z["Nth"], z["d"], z["ns"]
+    n1 = round(Np ** (1.0 / d))
+    p_, m_ = (n1 - 1) // 2, 2
+    w = 8 if precision == "fp64" else 4
+    nloc, ngp = (p_ + 1) ** d, (p_ + 2) ** d
+    if precision == "fp64":
+        vc = 2.0 * sf_contract_macs(d, p_) * (d + 1) * ns * ns * m_ ** d * E
+    else:
+        # volume contraction: per (macro, input X, test species, sub-element) the product
+        # [nloc x (d+1) ng] [(d+1) ng x ns nloc] plus forming its right factor [(d+1) ng x ns nloc]
+        # from the pointwise Jacobian ((d+1) terms per entry)
+        vc = (2.0 * nloc * ns * nloc * ngp * (d + 1) + 2.0 * ngp * (d + 1) * ns * nloc * (d + 1)) \
+            * (d + 1) * ns * m_ ** d * E
+    # Kronecker condensation: n1 terms per direction for each S/B entry, n1 for each C/D entry,
+    # plus the rhs product over the row of A_.q
+    kron = 2.0 * (Nu + Nt) * (Nu * d * n1 + Nt * n1 + d * Nu) * E
+    if apply_mode == 1:
+        apply = ("byte", (w * Nt * Nt + (8 + 8 + 4) * Nt) * E, "k_apply_explicit")
+    else:
+        apply = ("byte" if precision != "fp64" else "flop",
+                 (w * (2 * Nu * Nt + Nt * Nt + Nu * Nu) + 20 * Nt + 4 * Nu) * E if precision != "fp64"
+                 else 2.0 * (2 * Nu * Nt + Nt * Nt + Nu * Nu) * E, "k_apply (Algorithm 2)")
+    return {"vol_contract": ("flop", vc, "k_vol_contract"),
+            "cond_gemm": ("flop", kron, "k_cond_kron"),
+            "lu": ("flop", (2.0 / 3.0) * Nu ** 3 * E, "k_lu_panel_smem / k_lu_batched"),
+            "trsm": ("flop", 2.0 * Nu * Nu * Nt * E, "k_lu_solve_multi"),
+            "apply": apply,
+            "apply_bf16": ("byte", (2 * Nt * Nt + 20 * Nt) * E, "k_apply_explicit_bf16 (inner GMRES)")}
+
+
+def roofline_of(stats, steps, z, precision, apply_mode, peaks, gp):
+    """Roofline of the kernel with the largest summed device time over the timed steps."""
+    work = kernel_work(z, precision, apply_mode)
+    per_step = {k: v[0] / steps for k, v in stats.items() if v[1] > 0}
+    cand = {k: v for k, v in per_step.items() if k in work}
+    if not cand:
+        return None, per_step
+    dom = max(cand, key=cand.get)
+    ms_sum, cnt = stats[dom]
+    kind, amount, name = work[dom]
+    ms_launch = ms_sum / cnt
+    if kind == "byte":
+        ach = amount / (ms_launch / 1e3) / 1e9
+        pk = peaks.get("hbm_gbs")
+        roof = dict(bound="hbm", achieved=ach, peak=pk, unit="GB/s", frac=ach / pk if pk else None,
+                    peak_source="MEASURED_PEAKS.json hbm_gbs (measured copy)")
+    else:
+        ach = amount / (ms_launch / 1e3) / 1e12
+        if precision == "fp64":
+            pk, src = gp["fp64"], "measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)"
+        else:
+            pk, src = gp["fp32"], "measured cuBLAS SGEMM 8192^3 without TF32 in this run (FP32 pipe)"
+        roof = dict(bound="alu", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk, peak_source=src)
+    roof.update(kernel=name + " (one launch = all %d macro-elements)" % z["E"], phase=dom,
+                algorithmic=amount / (1e9 if kind == "byte" else 1e12),
+                algorithmic_unit="GB/launch" if kind == "byte" else "TFLOP/launch",
+                ms_per_launch=ms_launch, launches_per_step=cnt / steps, ms_per_step_all_launches=ms_sum / steps,
+                traffic=None, traffic_note="ncu DRAM bytes of this kernel are in profiles/ (captured on a "
+                                           "reduced mesh); not re-measured in this run")
+    return roof, per_step
+
+
+def run_tgv(args, ws, rank, lrank):
+    """The headline: Newton steps of the DIRK3 integration of the 16^3 Taylor-Green vortex.
+
+    Primary (value): the plain FP64 form.  Warm-up: W Newton steps from the lifted initial
+    condition; timed: the next K Newton steps (device-resident state).  e2e: further steps
+    with the state copied in from and out to pinned host memory inside the timed region.
+    Compare (same integration, same 1e-8 Newton tolerance): the FP64 run is finished to a
+    whole number of DIRK steps; the mixed form runs those DIRK steps from the same initial
+    state by mehdg_dirk_stage (end-state difference from FP64 reported), recording
+    (residual, error) pairs; the learned correction is trained on them and compared with
+    the multi-level preconditioner over the next DIRK steps from the same state."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -474,104 +655,113 @@ def run_tgv(args, ws, rank, lrank):
     pr = W.tgv(nmac=nmac)
     z = sizes(pr)
     dt = 0.05 / 0.1          # 0.05 t_c, t_c = L / V0 = 10 acoustic units (L = 1, V0 = M0 = 0.1)
-    base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, max_newton=60,
-                inner_iters=args.inner, tc_mode=args.tc_mode, refine_iters=args.refine)
-    prec = pkg.PREC_MIXED if args.precision == "mixed" else pkg.PREC_FP64
-    ctx = pkg.Context(pr, dict(base, precision=prec, precond=args.precond, apply_mode=args.apply_mode,
-                               precond_bf16=args.precond_bf16 if prec == pkg.PREC_MIXED else 0), device=dev)
-    u, q, uh = ctx.init_state(None, None, lift=True)
+    base = dict(restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, newton_atol=1e-14,
+                max_newton=60, inner_iters=args.inner, refine_iters=args.refine, tc_mode=args.tc_mode)
+    opt64 = dict(base, precision=pkg.PREC_FP64, precond=1, apply_mode=args.fp64_apply_mode)
+    optmx = dict(base, precision=pkg.PREC_MIXED, precond=1, apply_mode=1, precond_bf16=args.precond_bf16)
+    primary = opt64 if args.precision == "fp64" else optmx
     st = torch.cuda.current_stream(dev)
-    learn = args.compare and args.precision == "mixed"
-    if learn:
-        ctx.mlp_setup(hidden=256, seed=0, max_pairs=64)
-        ctx.mlp_set_recording(True)
+    peaks = measured_peaks()
+    gp = gemm_peaks(torch) if rank == 0 else {}
 
-    def dirk_step(c, u, q, uh):
-        tot = dict(newton_steps=0, fgmres_iters=0, status=0)
-        for stage in (1, 2, 3):
-            r = c.dirk_stage(stage, dt, u, q, uh)
-            tot["newton_steps"] += r["newton_steps"]
-            tot["fgmres_iters"] += r["fgmres_iters"]
-            tot["status"] |= r["status"]
-        return tot
-
+    ctx = pkg.Context(pr, primary, device=dev)
+    u, q, uh = ctx.init_state(None, None, lift=True)
+    drv = StepDriver(ctx, dt)
     for _ in range(args.warmup):
-        dirk_step(ctx, u, q, uh)
+        drv.step(u, q, uh)
     torch.cuda.synchronize()
     rank_barrier(ws)
     K = max(1, args.steps)
+    ctx.phase_stats(reset=True)
+    n0, f0 = drv.newton, drv.fgmres
     clk = ClockSampler(lrank)
     clk.start()
     l0 = ctx.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    newton, its = 0, 0
     ev0.record(st)
     for _ in range(K):
-        r = dirk_step(ctx, u, q, uh)
-        newton += r["newton_steps"]
-        its += r["fgmres_iters"]
+        drv.step(u, q, uh)
     ev1.record(st)
     torch.cuda.synchronize()
-    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    t_dev = ev0.elapsed_time(ev1) / 1e3
     clocks = clk.stop()
     launches = ctx.launch_count() - l0
-    # kinetic energy of the resolved field (nodal mean of rho |v|^2 / 2) as a sanity value
-    ke = float((0.5 * (u[:, 1:4] ** 2).sum(1) / u[:, 0]).mean())
+    stats = ctx.phase_stats()
+    its_timed = drv.fgmres - f0
+    t_dev = max_over_ranks(t_dev, ws, dev)
+    rank_barrier(ws)
+
+    # ---- e2e: the state in from pinned host memory and out again around every step
+    n_e2e = max(1, min(K, args.e2e_steps))
+    hu, hq, huh = (x.cpu().pin_memory() for x in (u, q, uh))
+    torch.cuda.synchronize()
+    rank_barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n_e2e):
+        u.copy_(hu, non_blocking=True)
+        q.copy_(hq, non_blocking=True)
+        uh.copy_(huh, non_blocking=True)
+        drv.step(u, q, uh)
+        hu.copy_(u, non_blocking=True)
+        hq.copy_(q, non_blocking=True)
+        huh.copy_(uh, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws, dev)
+    bytes_io = 8 * (u.numel() + q.numel() + uh.numel())
+
+    # ---- the primary run to a whole number of DIRK steps (end state for the comparisons)
+    drv.finish_dirk_step(u, q, uh)
+    n_dirk = drv.dirk_steps
+    primary_end = u.clone()
+    primary_summary = dict(dirk_steps=n_dirk, newton_steps=drv.newton, fgmres_iters=drv.fgmres,
+                           newton_steps_per_dirk_step=drv.newton / max(n_dirk, 1))
+    ctx.close()
+    del ctx
+
     compare = {}
     if args.compare:
-        state = (u.clone(), q.clone(), uh.clone())
+        other = optmx if args.precision == "fp64" else opt64
+        oname = "mixed" if args.precision == "fp64" else "plain_fp64"
+        c2 = pkg.Context(pr, other, device=dev)
+        uu, qq, hh = c2.init_state(None, None, lift=True)
+        learn = oname == "mixed" and args.learn_compare_steps > 0
         if learn:
-            n_samples = ctx.mlp_set_recording(False)
-            first, last = ctx.mlp_train(epochs=args.mlp_epochs, batch=8192, lr=1e-3)
+            c2.mlp_setup(hidden=256, seed=0, max_pairs=args.mlp_pairs)
+            c2.mlp_set_recording(True)
+        r = dirk_steps_timed(c2, n_dirk, dt, uu, qq, hh, st)
+        r["rel_l2_u_vs_primary_end_state"] = float((uu - primary_end).norm() / primary_end.norm())
+        compare[oname] = r
+        if learn:
+            n_samples = c2.mlp_set_recording(False)
+            first, last = c2.mlp_train(epochs=args.mlp_epochs, batch=8192, lr=1e-3)
+            state = (uu.clone(), qq.clone(), hh.clone())
             res = {}
-            for kind, name in ((1, "multilevel"), (2, "learned")):
-                ctx.set_precond(kind)
-                uu, qq, hh = (x.clone() for x in state)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                tot = dict(newton_steps=0, fgmres_iters=0, status=0)
-                for _ in range(K):
-                    r = dirk_step(ctx, uu, qq, hh)
-                    for k2 in tot:
-                        tot[k2] = tot[k2] | r[k2] if k2 == "status" else tot[k2] + r[k2]
-                e1.record(st)
-                torch.cuda.synchronize()
-                res[name] = dict(s_per_dirk_step=e0.elapsed_time(e1) / 1e3 / K, newton_steps=tot["newton_steps"],
-                                 fgmres_iters=tot["fgmres_iters"], fallback=bool(tot["status"] & 1), state=uu)
-            du = res["learned"].pop("state") - res["multilevel"]["state"]
-            res["learned"]["rel_diff_u_vs_multilevel"] = float(du.norm() / res["multilevel"].pop("state").norm())
-            res["train"] = dict(samples=n_samples, loss_first=first, loss_last=last)
-            compare["learned_vs_multilevel"] = res
-        ctx.close()
-        # plain FP64 (Algorithm 2) vs mixed on one DIRK step of a reduced mesh
-        nsmall = args.nmac_tgv_fp64
-        prs = W.tgv(nmac=nsmall)
-        out = {}
-        for name, opt in (("mixed", dict(base, precision=pkg.PREC_MIXED, precond=1, apply_mode=1,
-                                         precond_bf16=args.precond_bf16)),
-                          ("plain_fp64_algorithm2", dict(base, precision=pkg.PREC_FP64, precond=1, apply_mode=0))):
-            c = pkg.Context(prs, opt, device=dev)
-            uu, qq, hh = c.init_state(None, None, lift=True)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            r = dirk_step(c, uu, qq, hh)
-            e1.record(st)
-            torch.cuda.synchronize()
-            out[name] = dict(s_per_dirk_step=e0.elapsed_time(e1) / 1e3, newton_steps=r["newton_steps"],
-                             fgmres_iters=r["fgmres_iters"], state=uu)
-            c.close()
-        du = out["mixed"]["state"] - out["plain_fp64_algorithm2"]["state"]
-        out["mixed"]["rel_diff_u_vs_fp64"] = float(du.norm() / out["plain_fp64_algorithm2"]["state"].norm())
-        for v in out.values():
-            v.pop("state", None)
-        compare["reduced_mesh_%d^3" % nsmall] = out
-    else:
-        ctx.close()
-    per = t / K
+            for kind, name in ((1, "multilevel"), (2, "learned"), (0, "block_jacobi")):
+                c2.set_precond(kind)
+                a, b_, c_ = (x.clone() for x in state)
+                res[name] = dirk_steps_timed(c2, args.learn_compare_steps, dt, a, b_, c_, st)
+                res[name]["state"] = a
+            ref_state = res["multilevel"]["state"]
+            for name in ("learned", "block_jacobi"):
+                res[name]["rel_l2_u_vs_multilevel"] = float((res[name].pop("state") - ref_state).norm()
+                                                            / ref_state.norm())
+            res["multilevel"].pop("state")
+            res["train"] = dict(pairs_from_dirk_steps=n_dirk, face_samples=n_samples, epochs=args.mlp_epochs,
+                                loss_first_epoch=first, loss_last_epoch=last)
+            compare["learned_vs_multilevel_mixed"] = res
+        c2.close()
+
+    roof, per_step = roofline_of(stats, K, z, args.precision, primary["apply_mode"], peaks, gp)
+    lu_tf = None
+    if stats.get("lu", (0, 0))[1]:
+        lu_tf = kernel_work(z, args.precision, 0)["lu"][1] / (stats["lu"][0] / stats["lu"][1] / 1e3) / 1e12
+    per = t_dev / K
     line = {
         "metric": METRIC,
         "value": replica_value(per, ws),
-        "unit": "s/DIRK step",
+        "unit": UNIT_TGV,
         "n_gpus": ws,
         "steps": K,
         "warmup": args.warmup,
@@ -581,19 +771,23 @@ def run_tgv(args, ws, rank, lrank):
         "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32",
         "dtype_detail": "f64 throughout" if args.precision == "fp64" else MIXED_DETAIL,
-        "data": "synthetic (Taylor-Green initial condition, closed form)",
-        "config": {"workload": "3D Taylor-Green vortex, periodic [0,2pi]^3, Re 1600, M0 0.1, %d^3 macro-elements "
-                               "x 2^3 hexes, p=2 (%d macros, %d trace DOFs), DIRK3 dt = 0.05 t_c"
-                               % (nmac, z["E"], z["F"] * z["ns"] * z["Nfn"]),
-                   "precision": args.precision, "precond": args.precond, "lin_rtol": args.lin_rtol,
-                   "restart": args.restart, "inner_iters": args.inner, "apply_mode": args.apply_mode,
-                   "refine_iters": args.refine, "precond_bf16": args.precond_bf16,
+        "data": "synthetic (Taylor-Green initial condition of the paper's Sec. 5.3, closed form; no perturbation)",
+        "config": {"workload": WORKLOAD_TGV % (nmac, nmac, z["E"], z["F"] * z["ns"] * z["Nfn"]),
+                   "precision": args.precision, "newton_rtol": 1e-8, "precond": 1, "lin_rtol": args.lin_rtol,
+                   "restart": args.restart, "inner_iters": args.inner, "apply_mode": primary["apply_mode"],
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU"},
-        "newton_steps_per_dirk_step": newton / K,
-        "fgmres_iters_per_dirk_step": its / K,
-        "kinetic_energy_mean": ke,
+        "fgmres_iters_per_step": its_timed / K,
+        "batched_lu_tflops": lu_tf,
+        "batched_lu_note": "sum of (2/3) Nu^3 over the macro-elements / device time of the LU launch",
+        "primary_run": primary_summary,
+        "phase_ms_per_step": {k: v for k, v in per_step.items()},
+        "phase_launches_per_step": {k: stats[k][1] / K for k in stats if stats[k][1]},
+        "gemm_peaks_tflops": gp,
         "compare": compare,
+        "e2e": {"value": replica_value(t_e2e / n_e2e, ws), "unit": UNIT_TGV, "steps": n_e2e,
+                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
         "gpu_launches": launches,
+        "roofline": roof,
         "clocks": clocks,
     }
     return line
@@ -779,63 +973,139 @@ def oracle_sample_time(pr, n_macro=2, fgmres_iters=None, applies_per_iter=1):
                                  % (n_macro, P.E, its, applies_per_iter), cores=os.cpu_count())
 
 
+# FGMRES iterations per Newton step of the 16^3 TGV integration (multi-level preconditioner, 10
+# inner iterations, rtol 1e-3), measured on GB300; the reference arm runs without a GPU and
+# scales its sampled costs by this count
+REF_FGMRES_ITERS_TGV = 4
+_ORACLE_CACHE = {}
+
+
+def oracle_tgv_newton_sample(pr, fgmres_iters, applies_per_iter, n_macro=1):
+    """Oracle (numpy FP64) cost of one Newton step of the TGV DIRK integration on a bounded
+    sample: assembly with a DIRK stage time term, second-layer condensation with LU, one
+    recovery and three Algorithm-2 applies of n_macro macro-elements, scaled to every
+    macro-element and to fgmres_iters x applies_per_iter applies (outer FGMRES apply plus
+    the inner GMRES steps of the multi-level preconditioner).  Returns (seconds, info)."""
+    from oracle import solve as osolve
+    from oracle import assemble as oasm
+    key = (pr["name"], tuple(pr["nmac"]))
+    if _ORACLE_CACHE.get("key") != key:     # mesh tables and the sampled state, built once
+        P = osolve.Problem(pr)
+        _ORACLE_CACHE.update(key=key, P=P, state=W.random_state(pr, 0))
+    P = _ORACLE_CACHE["P"]
+    u, q, uh = _ORACLE_CACHE["state"]
+    t_all = time.perf_counter()
+    hist = -2.0 * u[:n_macro]
+    t0 = time.perf_counter()
+    for e in range(n_macro):
+        geo = P.geometry(e)
+        tt = dict(coef=2.0, hist=hist[e], supg_time=True)
+        blk = oasm.assemble_macro(geo, P.phys, u[e], q[e], P.local_trace(e, uh), tt, P.source(geo),
+                                  P.bfaces(e, geo))
+        c = osolve.condense_second_layer(geo, blk, 0.0)
+    t_local = (time.perf_counter() - t0) / n_macro
+    x = np.random.default_rng(1).normal(size=c["C"].shape[1])
+    t1 = time.perf_counter()
+    for _ in range(3):
+        osolve.apply_local(c, x)
+    t_apply = (time.perf_counter() - t1) / 3
+    t2 = time.perf_counter()
+    osolve.recover(geo, blk, c, x)
+    t_recover = time.perf_counter() - t2
+    per_step = P.E * (t_local + t_recover) + fgmres_iters * applies_per_iter * P.E * t_apply
+    info = dict(sample="assembly (DIRK time term) + second-layer condensation + LU and one recovery of %d "
+                       "macro-element(s) and 3 Algorithm-2 applies of one macro-element, scaled by %d "
+                       "macro-elements, %s FGMRES iterations per Newton step and %d applies per iteration"
+                       % (n_macro, P.E, fgmres_iters, applies_per_iter),
+                cores=os.cpu_count(), sample_wall_s=time.perf_counter() - t_all)
+    return per_step, info
+
+
+def cpu_baseline_tgv(line):
+    """cpu_baseline of the headline line: the oracle on the host cores, bounded sample, scaled."""
+    import torch
+    its = line.get("fgmres_iters_per_step") or REF_FGMRES_ITERS_TGV
+    t, info = oracle_tgv_newton_sample(W.tgv(nmac=16), round(its, 2), 1 + 10)
+    return {"value": t, "unit": UNIT_TGV, "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
+            "extrapolated": True, "sample_wall_s": info["sample_wall_s"],
+            "threads_numpy": torch.get_num_threads()}
+
+
 def run_reference(args):
-    pr = workload()
-    times = []
-    info = None
+    """The reference arm: the oracle (this project's FP64 numpy restatement of the paper)
+    timed on the host cores for the headline's metric and workload.  Each of the W + K
+    steps is one bounded sample scaled to a whole Newton step (extrapolated: true)."""
+    pr = W.tgv(nmac=args.nmac_tgv)
+    z = sizes(pr)
     applies = 1 + (args.inner if args.precond == 1 else 0)
+    times, walls = [], []
+    info = None
+    t_run = time.perf_counter()
     for k in range(args.warmup + args.steps):
-        t, info = oracle_sample_time(pr, n_macro=1, applies_per_iter=applies)
+        t, info = oracle_tgv_newton_sample(pr, REF_FGMRES_ITERS_TGV, applies)
         if k >= args.warmup:
             times.append(t)
+            walls.append(info["sample_wall_s"])
     val = float(np.mean(times))
     import torch
     threads = torch.get_num_threads() if hasattr(torch, "get_num_threads") else os.cpu_count()
-    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3D steady MMS cube, 8^3 macro-elements x 2^3 hexes, p=2"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"], "threads_numpy": threads},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    nmac = args.nmac_tgv
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT_TGV, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TGV % (nmac, nmac, z["E"], z["F"] * z["ns"] * z["Nfn"])},
+            "extrapolated": True,
+            "timed": "%d bounded samples (%.1f s of host time in all), each scaled to one Newton step"
+                     % (len(times), float(np.sum(walls))),
+            "run_wall_s": time.perf_counter() - t_run,
+            "cpu_baseline": {"value": val, "unit": UNIT_TGV, "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"], "threads_numpy": threads, "extrapolated": True},
+            "e2e": {"value": val, "unit": UNIT_TGV, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=0, help="timed Newton steps (default: one full solve)")
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (default: 10 Newton steps for tgv)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched"],
+                    help="tgv: Newton steps of the 16^3 Taylor-Green DIRK integration (default, the headline); "
+                         "mms: steady 3D manufactured solution (8^3); batched: independent uneven problems")
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="form timed for the value (default: fp64 for tgv, mixed for mms)")
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--lin-rtol", type=float, default=1e-3)
     ap.add_argument("--restart", type=int, default=60)
     ap.add_argument("--inner", type=int, default=10, help="inner GMRES iterations of the multi-level preconditioner")
-    ap.add_argument("--apply-mode", type=int, default=1, help="0: Algorithm 2 four-step apply; 1: stored A^T_i")
+    ap.add_argument("--apply-mode", type=int, default=1, help="mms workload: 0 Algorithm 2 apply; 1 stored A^T_i")
+    ap.add_argument("--fp64-apply-mode", type=int, default=0,
+                    help="apply of the plain FP64 form: 0 Algorithm 2 (default), 1 stored A^T_i")
     ap.add_argument("--tc-mode", type=int, default=0,
-                    help="mixed path: 0 FP32 SIMT; 1 tcgen05 split-TF32 LU updates; 2 also condensation and A^T_i"
-                         " products; 3 plain TF32 products")
+                    help="mixed path: 0 FP32 SIMT; 1 tcgen05 split-TF32 LU updates; 2 also the A^T_i products; "
+                         "3 plain TF32 products")
     ap.add_argument("--refine", type=int, default=1,
                     help="FP64 refinement sweeps of each local S solve (b^ and recovery) on the mixed path")
     ap.add_argument("--precond-bf16", type=int, default=1,
                     help="mixed path: BF16 copy of A^T_i for the inner GMRES of the multi-level preconditioner")
     ap.add_argument("--no-phases", dest="phases", action="store_false")
-    ap.add_argument("--nmac", type=int, default=8, help="macro-elements per cube edge (8 = the config)")
-
+    ap.add_argument("--nmac", type=int, default=8, help="mms workload: macro-elements per cube edge (8 = the config)")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
-                    help="skip the plain FP64 (Algorithm 2) and learned-preconditioner solves")
-    ap.add_argument("--mlp-epochs", type=int, default=300)
-    ap.add_argument("--solve-steps", type=int, default=60, help="cap on the recorded Newton steps")
-    ap.add_argument("--workload", default="mms", choices=["mms", "tgv", "batched"],
-                    help="mms: steady 3D manufactured solution (default); tgv: Taylor-Green DIRK steps; "
-                         "batched: independent uneven problems")
+                    help="skip the comparison forms (mixed / learned / FP64)")
+    ap.add_argument("--mlp-epochs", type=int, default=200)
+    ap.add_argument("--mlp-pairs", type=int, default=64, help="recorded (residual, error) pairs per training run")
+    ap.add_argument("--learn-compare-steps", type=int, default=1,
+                    help="tgv: DIRK steps on which the learned correction is compared (0 = skip)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="tgv: Newton steps of the host-buffer (e2e) timing")
+    ap.add_argument("--solve-steps", type=int, default=60, help="mms: cap on the recorded Newton steps")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--batch-mem-gb", type=float, default=200.0)
     ap.add_argument("--nmac-tgv", type=int, default=16, help="TGV macro-elements per edge (16 = the config)")
-    ap.add_argument("--nmac-tgv-fp64", type=int, default=8, help="reduced TGV mesh of the FP64 comparison")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "tgv" else "mixed"
     global NMAC
     NMAC = args.nmac
     ws, rank, lrank = dist_env()
@@ -848,9 +1118,11 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     if args.workload in ("tgv", "batched"):
-        args.steps = args.steps or 2
+        args.steps = args.steps or 10
         line = run_tgv(args, ws, rank, lrank) if args.workload == "tgv" else run_batched(args, ws, rank, lrank)
         if rank == 0:
+            if args.workload == "tgv" and args.cpu and ws == 1:   # the oracle baseline, N = 1 only
+                line["cpu_baseline"] = cpu_baseline_tgv(line)
             print(json.dumps(line))
         if ws > 1:
             import torch

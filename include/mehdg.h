@@ -102,6 +102,10 @@ typedef struct mehdg_options {
                          path the face-block inverses get a BF16 copy too, and the
                          inner block-Jacobi product reads the apply's per-macro results
                          directly (the face sum is done inside it) */
+  int solver;         /* 0: FGMRES right-preconditioned by the option precond (flexible,
+                         Sec. 4.2); 1: GMRES left-preconditioned by the macro-face
+                         block-Jacobi (A_uhuh)^-1, the paper's baseline of Sec. 4.2 (Table 2);
+                         its tolerance applies to the preconditioned residual |M^-1 r| */
 } mehdg_options;
 
 typedef struct mehdg_info {
@@ -190,6 +194,26 @@ int mehdg_recover(mehdg_ctx* ctx, const double* duhat, double* du, double* dq);
  * updated in place (device).  stats: host or NULL. */
 int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q,
                      double* uhat, mehdg_solve_stats* stats);
+
+/* a11/a12 one Newton step at a time: the three calls mehdg_dirk_stage is made of, for
+ * callers that drive, interleave or time the nonlinear iteration step by step (Sec. 3.1:
+ * each Newton step is the linear solve of eq. C312 by Algorithm 1 plus the state update).
+ * mehdg_stage_begin: start the system of stage i = 1..3 of the DIRK step (eq. C242; stage 1
+ *   records u as u^n, later stages use the stage values stored by mehdg_stage_end) or, for
+ *   stage 0, the steady pseudo-transient system (dtau = tau_init); assembles at (u, q, uhat).
+ *   stats->res0 = stats->res = |R_F| there.
+ * mehdg_newton_step: one Newton step of the begun stage: condensation and LU, FGMRES,
+ *   recovery, the update of u, q, uhat in place and the assembly at the new state (and, for
+ *   stage 0, the SER update of dtau).  stats: fgmres_iters of this step, res = the new |R_F|.
+ * For both, stats->status bit 1 (value 2) is set when |R_F| <= max(newton_rtol |R_F^0|,
+ * newton_atol) with R_F^0 the residual at mehdg_stage_begin: the stage has converged.
+ * mehdg_stage_end: store u as the stage value u^{n,i} (stage >= 1) and close the stage.
+ * All three synchronise the stream.  Errors: ARG (bad arguments, a step or end without a
+ * begun stage), NAN (non-finite residual), and those of the phases they run. */
+int mehdg_stage_begin(mehdg_ctx* ctx, int stage, double dt, double* u, double* q, double* uhat,
+                      mehdg_solve_stats* stats);
+int mehdg_newton_step(mehdg_ctx* ctx, double* u, double* q, double* uhat, mehdg_solve_stats* stats);
+int mehdg_stage_end(mehdg_ctx* ctx, const double* u);
 
 /* Copy one internal per-macro array to host memory (test access).  which:
  * 0 A_uu/S (after condensation: LU factors), 1..3 A_uq_k, 4 A_uuh/C, 5 A_uhu/B,
@@ -282,6 +306,16 @@ int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long lda, long 
                        long long sC, float alpha, float beta, int batch, int split, int* err,
                        void* stream);
 
+/* Batched dense LU with partial pivoting (Remark, Sec. 3.3: the factorisation of the local
+ * Schur complements S), the kernel mehdg_condense_factor runs, for caller-owned matrices:
+ * P A_b = L_b U_b for b < batch.  A: device, batch row-major n x n matrices, contiguous,
+ * FP64 (fp32 = 0) or FP32 (fp32 != 0), overwritten by the factors (unit lower L below the
+ * diagonal, U on and above it); perm: device int [batch][n], row i of P A is row perm[i] of
+ * A (first row of largest magnitude wins ties); dflag: device int[2] of scratch owned by the
+ * caller.  Synchronises stream.  Errors: ARG, SINGULAR when a pivot is exactly zero (the
+ * message on stderr names the first such matrix; the other matrices are factored), CUDA. */
+int mehdg_lu_batched(int n, int batch, void* A, int* perm, int fp32, int* dflag, void* stream);
+
 /* Device time in milliseconds of the most recent execution of each internal phase
  * (CUDA events on the context stream; -1 for phases not run since mehdg_mesh):
  * 0 volume pointwise Jacobians, 1 volume contraction, 2 faces + R_Q, 3 condensation
@@ -293,6 +327,14 @@ int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long lda, long 
  * ms: host double[n], n <= 16.
  * Synchronises the stream. */
 int mehdg_phase_times(mehdg_ctx* ctx, double* ms, int n);
+
+/* Cumulative device time of the internal phases (numbered as in mehdg_phase_times): for
+ * each phase p < n, sum_ms[p] (host double[n], or NULL) receives the milliseconds summed over
+ * every execution since mehdg_mesh or the last reset, and count[p] (host long long[n], or
+ * NULL) the number of executions.  Executions inside the inner-GMRES CUDA graph (phase 11)
+ * are counted per replay at the duration of the latest one.  reset != 0 zeroes both after
+ * reading.  Synchronises the stream. */
+int mehdg_phase_stats(mehdg_ctx* ctx, double* sum_ms, long long* count, int n, int reset);
 
 /* Number of CUDA kernels this context has launched since mehdg_mesh (host counter;
  * count is host memory). */

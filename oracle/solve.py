@@ -323,6 +323,48 @@ def fgmres(A, M, b, rtol=1e-10, atol=0.0, restart=30, maxit=1000):
     return x, its, beta
 
 
+def gmres_left(A, Minv, b, rtol=1e-10, atol=0.0, restart=30, maxit=1000):
+    """Restarted GMRES(restart) on Minv A x = Minv b (left preconditioning, CGS2): the
+    baseline solver of Sec. 4.2 with the fixed block-Jacobi preconditioner (A_uhuh)^-1.
+    The stopping test is on the preconditioned residual |Minv (b - A x)|.
+
+    Each cycle minimises |Minv (b - A x)| over x_start + the Krylov space of Minv A,
+    here by a least-squares solve with the Arnoldi Hessenberg matrix.
+    Returns x, iterations, final preconditioned residual norm.
+    """
+    n = len(b)
+    x = np.zeros(n)
+    r = Minv(b)
+    beta = np.linalg.norm(r)
+    tol = max(rtol * beta, atol)
+    its = 0
+    while beta > tol and its < maxit:
+        V = np.zeros((restart + 1, n))
+        H = np.zeros((restart + 1, restart))
+        V[0] = r / beta
+        k = 0
+        for j in range(restart):
+            w = Minv(A(V[j]))
+            for _ in range(2):
+                h = V[:j + 1] @ w
+                w = w - V[:j + 1].T @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            its += 1
+            k = j + 1
+            e1 = np.zeros(k + 1)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
+            res = np.linalg.norm(e1 - H[:k + 1, :k] @ y)
+            if res <= tol or its >= maxit or H[j + 1, j] == 0.0:
+                break
+            V[j + 1] = w / H[j + 1, j]
+        x = x + V[:k].T @ y
+        r = Minv(b - A(x))
+        beta = np.linalg.norm(r)
+    return x, its, beta
+
+
 # ---------------------------------------------------------------- global drivers
 
 def global_assemble(P, u, q, uh, tt=None, want_jac=True):

@@ -19,9 +19,9 @@ PREC_FP64, PREC_MIXED = 0, 1
 
 EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_local", "mehdg_condense_factor",
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
-           "mehdg_get_block", "mehdg_phase_times", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
+           "mehdg_get_block", "mehdg_phase_times", "mehdg_phase_stats", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
-           "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_apply_trace_noalloc", "mehdg_destroy",
+           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_destroy",
            "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("lin_rtol", c_double), ("lin_atol", c_double), ("inner_iters", c_int),
                 ("newton_rtol", c_double), ("newton_atol", c_double), ("max_newton", c_int),
                 ("tau_init", c_double), ("tau_max", c_double), ("refine_iters", c_int), ("apply_mode", c_int),
-                ("tc_mode", c_int), ("precond_bf16", c_int)]
+                ("tc_mode", c_int), ("precond_bf16", c_int), ("solver", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -64,7 +64,7 @@ class SolveStats(ctypes.Structure):
 DEFAULT_OPTIONS = dict(precision=PREC_FP64, precond=0, restart=30, max_iters=2000, lin_rtol=1e-6, lin_atol=0.0,
                        inner_iters=5, newton_rtol=1e-8, newton_atol=1e-14, max_newton=100, tau_init=1.0,
                        tau_max=1e8, refine_iters=2, apply_mode=0, tc_mode=0,
-                       precond_bf16=0)
+                       precond_bf16=0, solver=0)
 
 _lib = None
 
@@ -88,8 +88,12 @@ def load_library(path=LIB_PATH):
     lib.mehdg_linear_solve.argtypes = [c_void_p, c_void_p, c_void_p, P(SolveStats)]
     lib.mehdg_recover.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     lib.mehdg_dirk_stage.argtypes = [c_void_p, I, c_double, c_void_p, c_void_p, c_void_p, P(SolveStats)]
+    lib.mehdg_stage_begin.argtypes = [c_void_p, I, c_double, c_void_p, c_void_p, c_void_p, P(SolveStats)]
+    lib.mehdg_newton_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, P(SolveStats)]
+    lib.mehdg_stage_end.argtypes = [c_void_p, c_void_p]
     lib.mehdg_get_block.argtypes = [c_void_p, I, I, c_void_p, P(c_longlong)]
     lib.mehdg_phase_times.argtypes = [c_void_p, P(c_double), I]
+    lib.mehdg_phase_stats.argtypes = [c_void_p, P(c_double), P(c_longlong), I, I]
     lib.mehdg_launch_count.argtypes = [c_void_p, P(c_longlong)]
     lib.mehdg_mlp_setup.argtypes = [c_void_p, I, ctypes.c_ulonglong, I]
     lib.mehdg_mlp_params.argtypes = [c_void_p, I, c_void_p, P(c_longlong)]
@@ -98,6 +102,7 @@ def load_library(path=LIB_PATH):
     lib.mehdg_mlp_gradient.argtypes = [c_void_p, c_void_p, c_void_p, I, c_void_p, P(c_double)]
     lib.mehdg_mlp_train.argtypes = [c_void_p, I, I, c_double, P(c_double)]
     lib.mehdg_set_precond.argtypes = [c_void_p, I]
+    lib.mehdg_lu_batched.argtypes = [I, I, c_void_p, c_void_p, I, c_void_p, c_void_p]
     lib.mehdg_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.restype = None
     lib.mehdg_last_error.argtypes = [c_void_p]
@@ -142,6 +147,26 @@ def options_struct(opts=None):
 
 class MehdgError(RuntimeError):
     pass
+
+
+def lu_batched(A, perm=None):
+    """P A_b = L_b U_b in place for a contiguous CUDA tensor A [batch, n, n] (float64 or
+    float32) through mehdg_lu_batched; returns perm [batch, n] (int32).  Raises MehdgError
+    (SINGULAR) on an exactly zero pivot."""
+    import torch
+    lib = load_library()
+    assert A.is_cuda and A.is_contiguous() and A.dim() == 3 and A.shape[1] == A.shape[2]
+    assert A.dtype in (torch.float64, torch.float32)
+    batch, n = A.shape[0], A.shape[1]
+    if perm is None:
+        perm = torch.empty(batch, n, dtype=torch.int32, device=A.device)
+    flag = torch.zeros(2, dtype=torch.int32, device=A.device)
+    rc = lib.mehdg_lu_batched(n, batch, c_void_p(A.data_ptr()), c_void_p(perm.data_ptr()),
+                              int(A.dtype == torch.float32), c_void_p(flag.data_ptr()),
+                              c_void_p(torch.cuda.current_stream(A.device).cuda_stream))
+    if rc != 0:
+        raise MehdgError("mehdg_lu_batched failed (%s)" % ERRORS.get(rc, rc))
+    return perm
 
 
 class Context:
@@ -249,6 +274,25 @@ class Context:
                                               self._ptr(uh), ctypes.byref(st)), "dirk_stage", allow)
         return st.as_dict()
 
+    def stage_begin(self, stage, dt, u, q, uh):
+        st = SolveStats()
+        self._check(self.lib.mehdg_stage_begin(self.h, int(stage), float(dt), self._ptr(u), self._ptr(q),
+                                               self._ptr(uh), ctypes.byref(st)), "stage_begin")
+        d = st.as_dict()
+        d["converged"] = bool(st.status & 2)
+        return d
+
+    def newton_step(self, u, q, uh):
+        st = SolveStats()
+        self._check(self.lib.mehdg_newton_step(self.h, self._ptr(u), self._ptr(q), self._ptr(uh),
+                                               ctypes.byref(st)), "newton_step")
+        d = st.as_dict()
+        d["converged"] = bool(st.status & 2)
+        return d
+
+    def stage_end(self, u):
+        self._check(self.lib.mehdg_stage_end(self.h, self._ptr(u)), "stage_end")
+
     def get_block(self, which, macro):
         n = c_longlong()
         self._check(self.lib.mehdg_get_block(self.h, int(which), int(macro), None, ctypes.byref(n)), "get_block")
@@ -267,6 +311,13 @@ class Context:
         return {k: out[i] for i, k in enumerate(self.PHASES)}
 
     # -- learned preconditioner correction (kind 2)
+    def phase_stats(self, reset=False):
+        """Cumulative device milliseconds and execution counts of each internal phase since
+        the context was made or the last reset: {name: (ms, count)}."""
+        ms, cnt = (c_double * 16)(), (c_longlong * 16)()
+        self._check(self.lib.mehdg_phase_stats(self.h, ms, cnt, 16, int(reset)), "phase_stats")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.PHASES)}
+
     def set_precond(self, kind):
         self._check(self.lib.mehdg_set_precond(self.h, int(kind)), "set_precond")
         self.options["precond"] = int(kind)

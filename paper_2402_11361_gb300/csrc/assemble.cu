@@ -345,6 +345,149 @@ __global__ void __launch_bounds__(VolCfg<D, P, CT>::NT) k_vol_contract(Geo g, co
   }
 }
 
+// The same blocks by sum factorisation (used on the FP64 path, where the FP64 pipe is the
+// bound).  On a sub-element both the basis T[g][alpha][a] and the Gauss points are tensor
+// products: T is a product over the axes of 1D values v(g_k, a_k) or, on axis alpha-1, of
+// the scaled 1D derivative d(g_k, a_k).  The bilinear sum
+//   A[a][b] = sum_{alpha,beta} sum_g T[g][alpha][a] K[g][alpha,s,beta] T[g][beta][b]
+// is contracted one axis at a time.  After the x axis the pairs (alpha, beta) whose
+// remaining factors agree are added (alpha = 0 and alpha = 1 both carry values on y and
+// z), and likewise after y, so the three passes run on 3 x 3, 2 x 2 and 2 x 2 classes
+// instead of 13 pairs (3D).  Per (sub-element, trial species) that is
+// 16 ((p+1)^2 (p+2)^2 + ...) multiply-adds instead of (p+1)^6 (p+2)^3 (d+1).
+// One CTA per (macro, input X, test species t) runs every sub-element and trial species.
+template <int D, int P, class CT>
+struct SfCfg {
+  static constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  static constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  static constexpr int KA = (D + 1) * NS * (D + 1);
+  static constexpr int NC1 = D;                                        // classes after the x pass
+  static constexpr int W1N = NC1 * NC1 * IPow<NG1, D - 1>::v * P1 * P1;
+  static constexpr int W2N = D == 3 ? 2 * 2 * NG1 * P1 * P1 * P1 * P1 : 1;
+  static constexpr int NT = 256;
+  static constexpr size_t SMEM = sizeof(CT) * ((size_t)NG * KA + W1N + W2N + 4 * NG1 * P1);
+};
+
+// class of a test/trial index alpha (0 value, 1 + k derivative along k) once the first
+// `done` axes are contracted: 0 when its remaining factors are all values, else alpha - done
+__device__ __forceinline__ int sf_class(int alpha, int done) { return (alpha == 0 || alpha <= done) ? 0 : alpha - done; }
+
+template <int D, int P, class CT>
+__global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __restrict__ tab,
+                                                         const CT* __restrict__ Kvol, CT* __restrict__ Auu,
+                                                         CT* __restrict__ Auq) {
+  typedef SfCfg<D, P, CT> C;
+  constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, NT = C::NT;
+  extern __shared__ __align__(16) unsigned char sf_raw[];
+  CT* sK = reinterpret_cast<CT*>(sf_raw);   // [NG][KA] pointwise kernels of one sub-element
+  CT* W1 = sK + NG * KA;                    // after the x pass
+  CT* W2 = W1 + C::W1N;                     // after the y pass (3D)
+  CT* fv = W2 + C::W2N;                     // [NG1][P1] 1D values, then derivatives along x, y, z
+  CT* fd = fv + NG1 * P1;
+  const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z, tid = threadIdx.x;
+  for (int i = tid; i < NG1 * P1; i += NT) {
+    fv[i] = (CT)tab[i];
+    for (int k = 0; k < D; ++k) fd[k * NG1 * P1 + i] = (CT)(tab[NG1 * P1 + i] * 2.0 / g.he[k]);
+  }
+  const size_t Nu = g.Nu, Np = g.Np;
+  CT* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
+  for (int el = 0; el < g.nel; ++el) {
+    int li[D];
+    {
+      int ll = el;
+      for (int k = 0; k < D; ++k) { li[k] = ll % g.m; ll /= g.m; }
+    }
+    __syncthreads();   // previous sub-element's readers of sK are done
+    const CT* Kel = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * g.nel + el) * (size_t)NG * KA;
+    for (int i = tid; i < NG * KA; i += NT) sK[i] = Kel[i];
+    __syncthreads();
+    for (int s = 0; s < NS; ++s) {
+      // x pass: W1[ca][cb][g_rest][ax][bx], classes after one axis
+      constexpr int GR = IPow<NG1, D - 1>::v;
+      for (int i = tid; i < C::W1N; i += NT) {
+        const int bx = i % P1, ax = (i / P1) % P1, gr = (i / (P1 * P1)) % GR;
+        const int cb = (i / (P1 * P1 * GR)) % D, ca = i / (P1 * P1 * GR * D);
+        CT acc = CT(0);
+        for (int al = 0; al <= D; ++al) {
+          if (sf_class(al, 1) != ca) continue;
+          for (int be = 0; be <= D; ++be) {
+            if (sf_class(be, 1) != cb || (al == 0 && be != 0)) continue;
+            const CT* fa = al == 1 ? fd : fv;
+            const CT* fb = be == 1 ? fd : fv;
+            const int ko = (al * NS + s) * (D + 1) + be;
+#pragma unroll
+            for (int gx = 0; gx < NG1; ++gx)
+              acc += fa[gx * P1 + ax] * fb[gx * P1 + bx] * sK[(gr * NG1 + gx) * KA + ko];
+          }
+        }
+        W1[i] = acc;
+      }
+      __syncthreads();
+      const CT* last;   // the pass before the final one: [classes z][classes z][NG1 gz][rest...]
+      if constexpr (D == 3) {
+        // y pass: W2[za][zb][gz][ay][ax][by][bx]
+        for (int i = tid; i < C::W2N; i += NT) {
+          const int bx = i % P1, by = (i / P1) % P1, ax = (i / (P1 * P1)) % P1, ay = (i / (P1 * P1 * P1)) % P1;
+          const int gz = (i / (P1 * P1 * P1 * P1)) % NG1, zb = (i / (P1 * P1 * P1 * P1 * NG1)) % 2;
+          const int za = i / (P1 * P1 * P1 * P1 * NG1 * 2);
+          CT acc = CT(0);
+          for (int ca = 0; ca < 3; ++ca) {
+            if ((ca == 2) != (za == 1)) continue;
+            const CT* fa = ca == 1 ? fd + NG1 * P1 : fv;
+            for (int cb = 0; cb < 3; ++cb) {
+              if ((cb == 2) != (zb == 1)) continue;
+              const CT* fb = cb == 1 ? fd + NG1 * P1 : fv;
+#pragma unroll
+              for (int gy = 0; gy < NG1; ++gy)
+                acc += fa[gy * P1 + ay] * fb[gy * P1 + by] *
+                       W1[((((ca * 3 + cb) * NG1 + gz) * NG1 + gy) * P1 + ax) * P1 + bx];
+            }
+          }
+          W2[i] = acc;
+        }
+        __syncthreads();
+        last = W2;
+      } else {
+        last = W1;
+      }
+      // final pass (z in 3D, y in 2D) and the scatter into the macro block
+      const CT* fdl = fd + (D - 1) * NG1 * P1;
+      for (int i = tid; i < NLOC * NLOC; i += NT) {
+        const int a = i / NLOC, b = i % NLOC;
+        int av[D], bv[D];
+        {
+          int aa = a, bb = b;
+          for (int k = 0; k < D; ++k) { av[k] = aa % P1; aa /= P1; bv[k] = bb % P1; bb /= P1; }
+        }
+        CT acc = CT(0);
+        for (int za = 0; za < 2; ++za) {
+          const CT* fa = za == 1 ? fdl : fv;
+          for (int zb = 0; zb < 2; ++zb) {
+            const CT* fb = zb == 1 ? fdl : fv;
+#pragma unroll
+            for (int gl = 0; gl < NG1; ++gl) {
+              CT w;
+              if constexpr (D == 3)
+                w = last[((((za * 2 + zb) * NG1 + gl) * P1 + av[1]) * P1 + av[0]) * P1 * P1 + bv[1] * P1 + bv[0]];
+              else
+                w = last[(((za * 2 + zb) * NG1 + gl) * P1 + av[0]) * P1 + bv[0]];
+              acc += fa[gl * P1 + av[D - 1]] * fb[gl * P1 + bv[D - 1]] * w;
+            }
+          }
+        }
+        int A = 0, B = 0, sa = 1;
+        for (int k = 0; k < D; ++k) {
+          A += (li[k] * P + av[k]) * sa;
+          B += (li[k] * P + bv[k]) * sa;
+          sa *= g.n1;
+        }
+        out[((size_t)t * Np + A) * Nu + (size_t)s * Np + B] += acc;
+      }
+      __syncthreads();   // W1/W2 are rewritten for the next trial species
+    }
+  }
+}
+
 // R_U[t][A] += sum_g sum_alpha T[g][alpha][a] r[g][t][alpha]
 template <int D, int P>
 __global__ void k_vol_res(Geo g, const double* __restrict__ tab, const double* __restrict__ rvol,
@@ -679,13 +822,24 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
     phase_end(ctx, PH_VOL_POINT);
   }
   {
-    typedef VolCfg<D, P, BT> C;
-    CK(cudaFuncSetAttribute(k_vol_contract<D, P, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     dim3 grid(E, D + 1, NS);
-    phase_begin(ctx, PH_VOL_CONTRACT);
-    k_vol_contract<D, P, BT><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, Kvol, Auu, Auq);
-    CKL();
-    phase_end(ctx, PH_VOL_CONTRACT);
+    if (sizeof(BT) == 8) {
+      // FP64 path: sum factorisation (FP64 pipe bound)
+      typedef SfCfg<D, P, BT> C;
+      CK(cudaFuncSetAttribute(k_vol_contract_sf<D, P, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)C::SMEM));
+      phase_begin(ctx, PH_VOL_CONTRACT);
+      k_vol_contract_sf<D, P, BT><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, Kvol, Auu, Auq);
+      CKL();
+      phase_end(ctx, PH_VOL_CONTRACT);
+    } else {
+      typedef VolCfg<D, P, BT> C;
+      CK(cudaFuncSetAttribute(k_vol_contract<D, P, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+      phase_begin(ctx, PH_VOL_CONTRACT);
+      k_vol_contract<D, P, BT><<<grid, C::NT, C::SMEM, st>>>(g, ctx->tab, Kvol, Auu, Auq);
+      CKL();
+      phase_end(ctx, PH_VOL_CONTRACT);
+    }
     phase_begin(ctx, PH_FACES);
     k_vol_res<D, P><<<E, 128, 0, st>>>(g, ctx->tab, ctx->rvol, ctx->RU);
     CKL();

@@ -10,6 +10,7 @@
 //   P S = L U,  b^_i = h - B S^-1 g
 // S, C, B, D overwrite A_uu, A_uuh, A_uhu, A_uhuh in place.
 #include <algorithm>
+#include <cstdio>
 
 #include "internal.cuh"
 #include <cuda_bf16.h>
@@ -144,6 +145,163 @@ int cond_gemm(mehdg_ctx* ctx, const CondArgs<T>& a, int E) {
   return MEHDG_OK;
 }
 
+
+// Second-layer condensation on affine box macros (eqs. AP12, ASC2).  There M and G_k are
+// Kronecker products of 1D mass and derivative matrices, so the liftings W_k = M^-1 G_k and
+// Wh_k = M^-1 Gh_k are sparse: column l of W_k holds n1 = m p + 1 entries, on the axis-k line
+// through node l, and column (f, i) of Wh_k holds n1 entries, on the line normal to face f
+// through face node i (only the two faces normal to k).  Each output entry of
+// A_.q_k (I (x) W_k) is therefore an n1-term sum: 15 multiply-adds per S or B entry and 5 per
+// C or D entry for p = 2 (3D), against K = d Np = 375 for the dense product.  The work is then
+// bound by streaming the blocks: one CTA takes one row of the stacked [A_uq; A_uhq] at a time
+// (all directions, all species, staged in shared memory), writes the matching row of S and C
+// (or B and D) in place, and adds the row's term of the right-hand side pieces g and h.  The
+// pseudo-time shift (I (x) M) on A_uu and the sign of C = -A_uuh + ... are folded in.
+__host__ __device__ constexpr int ipow_k(int b, int e) { return e <= 0 ? 1 : b * ipow_k(b, e - 1); }
+
+template <class T>
+struct CondK {
+  const T* Auq; const T* Ahq;   // [E][d][Nu][Nu], [E][d][Nt][Nu]
+  T* S; T* C; T* B; T* D;       // over A_uu [E][Nu][Nu], A_uuh [E][Nu][Nt], A_uhu [E][Nt][Nu], A_uhuh [E][Nt][Nt]
+  const double* klift;          // [d][n1][n1], then [2d][n1]
+  const int* fnode;             // [2d][Nfn] macro node of each face node
+  const double* M;              // [Np][Np]
+  double shift;
+  const T* xq;                  // [E][d][Nu] M^-1 R_Q in the block precision
+  const double* RU; const double* RUh;
+  double* g; double* h;
+  int E, d, n1, Np, Nfn, Nth, Nu, Nt;
+};
+constexpr int CK_NT = 128;
+// D, N1 > 0: compile-time dimension and nodes per macro edge (divisions by constants);
+// 0: taken from the arguments
+template <class T, int D, int N1>
+__global__ void __launch_bounds__(CK_NT) k_cond_kron(CondK<T> a) {
+  extern __shared__ __align__(16) unsigned char ck_raw[];
+  T* arow = reinterpret_cast<T*>(ck_raw);   // [d][Nu]: one row of A_uq_k (or A_uhq_k) for every k
+  __shared__ T w1[3 * 64];
+  __shared__ T wf[6 * 8];
+  __shared__ double red[CK_NT / 32];
+  const int tid = threadIdx.x;
+  const int d = D ? D : a.d, n1 = N1 ? N1 : a.n1;
+  const int Np = D && N1 ? ipow_k(N1, D) : a.Np;
+  const int Nfn = D && N1 ? ipow_k(N1, D - 1) : a.Nfn;
+  const int Nth = 2 * d * Nfn, Nu = (d + 2) * Np, Nt = (d + 2) * Nth;
+  for (int i = tid; i < d * n1 * n1; i += CK_NT) w1[i] = (T)a.klift[i];
+  for (int i = tid; i < 2 * d * n1; i += CK_NT) wf[i] = (T)a.klift[d * n1 * n1 + i];
+  const int strides[3] = {1, n1, n1 * n1};
+  const int rows = Nu + Nt;
+  const long long total = (long long)a.E * rows;
+  for (long long id = blockIdx.x; id < total; id += gridDim.x) {
+    const int e = (int)(id / rows), r = (int)(id - (long long)e * rows);
+    const bool top = r < Nu;
+    const int rr = top ? r : r - Nu;
+    const T* src = top ? a.Auq + (size_t)e * d * Nu * Nu + (size_t)rr * Nu
+                       : a.Ahq + (size_t)e * d * Nt * Nu + (size_t)rr * Nu;
+    const size_t sk = top ? (size_t)Nu * Nu : (size_t)Nt * Nu;
+    __syncthreads();   // the previous row's readers are done
+    for (int k = 0; k < d; ++k)
+      for (int c = tid; c < Nu; c += CK_NT) arow[k * Nu + c] = src[k * sk + c];
+    __syncthreads();
+    // right-hand side piece: g_r = -R_U,r + sum_k A_uq_k[r] . xq_k (h from A_uhq and R_Uh);
+    // per-thread partial sums in the block precision, reduced in FP64
+    {
+      const T* xq = a.xq + (size_t)e * d * Nu;
+      T part = T(0);
+      for (int c = tid; c < d * Nu; c += CK_NT) part += arow[c] * xq[c];
+      double pd = (double)part;
+      for (int o = 16; o; o >>= 1) pd += __shfl_xor_sync(0xffffffffu, pd, o);
+      if ((tid & 31) == 0) red[tid >> 5] = pd;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < CK_NT / 32; ++w) t += red[w];
+        if (top) a.g[(size_t)e * Nu + rr] = t - a.RU[(size_t)e * Nu + rr];
+        else a.h[(size_t)e * Nt + rr] = t - a.RUh[(size_t)e * Nt + rr];
+      }
+    }
+    // S row (A_uu + shift (I (x) M) - A_uq W) or B row (A_uhu - A_uhq W)
+    T* o1 = top ? a.S + (size_t)e * Nu * Nu + (size_t)rr * Nu : a.B + (size_t)e * Nt * Nu + (size_t)rr * Nu;
+    const int sr = top ? rr / Np : -1, lr = top ? rr - sr * Np : 0;
+    for (int c = tid; c < Nu; c += CK_NT) {
+      const int s = c / Np, l = c - s * Np;
+      T acc = T(0);
+      int rem = l;
+#pragma unroll
+      for (int k = 0; k < (D ? D : 3); ++k) {
+        if (!D && k >= d) break;
+        const int lk = rem % n1;
+        rem /= n1;
+        const T* ak = arow + k * Nu + c - lk * strides[k];
+        const T* wk = w1 + k * n1 * n1 + lk;
+#pragma unroll
+        for (int q = 0; q < (N1 ? N1 : 8); ++q) {
+          if (!N1 && q >= n1) break;
+          acc += ak[q * strides[k]] * wk[q * n1];
+        }
+      }
+      T v = o1[c] - acc;
+      if (s == sr && a.shift != 0.0) v += (T)(a.shift * a.M[(size_t)lr * Np + l]);
+      o1[c] = v;
+    }
+    // C row (-A_uuh + A_uq Wh) or D row (A_uhuh - A_uhq Wh): column (species, face, face node)
+    T* o2 = top ? a.C + (size_t)e * Nu * Nt + (size_t)rr * Nt : a.D + (size_t)e * Nt * Nt + (size_t)rr * Nt;
+    for (int c = tid; c < Nt; c += CK_NT) {
+      const int s = c / Nth, rem = c - s * Nth, fl = rem / Nfn, i = rem - fl * Nfn, k = fl >> 1;
+      const int l0 = a.fnode[fl * Nfn + i];
+      const int lk = (l0 / strides[k]) % n1;
+      const T* ak = arow + k * Nu + s * Np + l0 - lk * strides[k];
+      const T* wk = wf + fl * n1;
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < (N1 ? N1 : 8); ++q) {
+        if (!N1 && q >= n1) break;
+        acc += ak[q * strides[k]] * wk[q];
+      }
+      o2[c] = top ? acc - o2[c] : o2[c] - acc;
+    }
+  }
+}
+
+template <class T, int D, int N1>
+int cond_kron_launch(mehdg_ctx* ctx, const CondK<T>& a) {
+  const size_t smem = sizeof(T) * (size_t)ctx->d * ctx->Nu;
+  CK(cudaFuncSetAttribute(k_cond_kron<T, D, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, nsm = 0, per = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cond_kron<T, D, N1>, CK_NT, smem));
+  const long long total = (long long)ctx->E * (ctx->Nu + ctx->Nt);
+  const long long grid = std::min<long long>(total, (long long)nsm * std::max(per, 1));
+  k_cond_kron<T, D, N1><<<(unsigned)grid, CK_NT, smem, ctx->stream>>>(a);
+  CKL();
+  return MEHDG_OK;
+}
+
+template <class T>
+int cond_kron(mehdg_ctx* ctx, double shift, const T* xq) {
+  CondK<T> a{};
+  a.Auq = reinterpret_cast<const T*>(ctx->Auq);
+  a.Ahq = reinterpret_cast<const T*>(ctx->Ahq);
+  a.S = reinterpret_cast<T*>(ctx->Auu);
+  a.C = reinterpret_cast<T*>(ctx->Auh);
+  a.B = reinterpret_cast<T*>(ctx->Ahu);
+  a.D = reinterpret_cast<T*>(ctx->Ahh);
+  a.klift = ctx->klift; a.fnode = ctx->fnode; a.M = ctx->Mref; a.shift = shift; a.xq = xq;
+  a.RU = ctx->RU; a.RUh = ctx->RUh; a.g = ctx->gv; a.h = ctx->hv;
+  a.E = ctx->E; a.d = ctx->d; a.n1 = ctx->n1; a.Np = ctx->Np; a.Nfn = ctx->Nfn; a.Nth = ctx->Nth;
+  a.Nu = ctx->Nu; a.Nt = ctx->Nt;
+  const int key = ctx->d * 16 + ctx->n1;
+  switch (key) {
+    case 2 * 16 + 3: return cond_kron_launch<T, 2, 3>(ctx, a);
+    case 2 * 16 + 5: return cond_kron_launch<T, 2, 5>(ctx, a);
+    case 2 * 16 + 7: return cond_kron_launch<T, 2, 7>(ctx, a);
+    case 3 * 16 + 3: return cond_kron_launch<T, 3, 3>(ctx, a);
+    case 3 * 16 + 5: return cond_kron_launch<T, 3, 5>(ctx, a);
+    case 3 * 16 + 7: return cond_kron_launch<T, 3, 7>(ctx, a);
+    default: return cond_kron_launch<T, 0, 0>(ctx, a);
+  }
+}
 
 // The same product on the tcgen05 tensor cores (TF32 inputs, FP32 accumulation)
 int tc_gemm(mehdg_ctx* ctx, int M, int N, int K, const float* A, long long lda, long long sA1, long long sA2,
@@ -425,7 +583,18 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     CKL();
   }
   // g = -R_U + sum_k A_uq_k MinvRQ[k];  h = -R_Uh + sum_k A_uhq_k MinvRQ[k]  (eq. ASC2b pieces)
-  {
+  const bool kron = ctx->klift != nullptr && !(sizeof(T) == 4 && ctx->use_tc_condense);
+  if (kron) {
+    // Kronecker liftings: S, C, B, D, g and h in one streaming pass (k_cond_kron)
+    const T* xq = reinterpret_cast<const T*>(ctx->MinvRQ);
+    if constexpr (sizeof(T) == 4) {
+      if ((rc = to_float(ctx, ctx->MinvRQ, ctx->q32, (long long)E * d * Nu))) return rc;
+      xq = reinterpret_cast<const T*>(ctx->q32);
+    }
+    phase_begin(ctx, PH_COND_GEMM);
+    if ((rc = cond_kron<T>(ctx, shift, xq))) return rc;
+    phase_end(ctx, PH_COND_GEMM);
+  } else {
     // M^-1 R_Q in the block precision (FP32 path: into the FP32 q scratch of the assembly)
     const T* xq = reinterpret_cast<const T*>(ctx->MinvRQ);
     if constexpr (sizeof(T) == 4) {
@@ -442,14 +611,16 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     CKL();
   }
   // S, C, B, D
-  if (shift != 0.0) {
+  if (!kron && shift != 0.0) {
     long long tot = (long long)E * ns * Np * Np;
     k_mass_shift<T><<<(tot + 255) / 256, 256, 0, st>>>(Auu, ctx->Mref, Np, ns, shift, E);
     CKL();
   }
-  k_scale<T><<<(E * Nu * Nt + 255) / 256, 256, 0, st>>>(Auh, E * Nu * Nt, -1.0);
-  CKL();
-  if (!(sizeof(T) == 4 && ctx->use_tc_condense)) {
+  if (!kron) {
+    k_scale<T><<<(E * Nu * Nt + 255) / 256, 256, 0, st>>>(Auh, E * Nu * Nt, -1.0);
+    CKL();
+  }
+  if (!kron && !(sizeof(T) == 4 && ctx->use_tc_condense)) {
     // [S | C] -= A_uq [W | -Wh],  [B | -D] -= A_uhq [W | -Wh]  (all directions in one K)
     CondArgs<T> a{};
     a.Bc = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)ctx->Bcat32 : (const void*)ctx->Bcat);
@@ -571,6 +742,28 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
 int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
   if (ctx->opt.precision == MEHDG_PREC_MIXED) return condense_t<float>(ctx, shift, bhat);
   return condense_t<double>(ctx, shift, bhat);
+}
+
+extern "C" int mehdg_lu_batched(int n, int batch, void* A, int* perm, int fp32, int* dflag, void* stream) {
+  if (n < 1 || batch < 0 || !A || !perm || !dflag) return MEHDG_ERR_ARG;
+  mehdg_ctx tmp;
+  tmp.stream = static_cast<cudaStream_t>(stream);
+  mehdg_ctx* ctx = &tmp;
+  CK(cudaMemsetAsync(dflag, 0, sizeof(int) * 2, tmp.stream));
+  int rc = fp32 ? batched_lu_t<float>(ctx, static_cast<float*>(A), perm, n, batch, dflag)
+                : batched_lu_t<double>(ctx, static_cast<double*>(A), perm, n, batch, dflag);
+  if (rc) {
+    std::fprintf(stderr, "mehdg_lu_batched: %s\n", tmp.err.c_str());
+    return rc;
+  }
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, dflag, sizeof(h), cudaMemcpyDeviceToHost, tmp.stream));
+  CK(cudaStreamSynchronize(tmp.stream));
+  if (h[0]) {
+    std::fprintf(stderr, "mehdg_lu_batched: zero pivot in matrix %d\n", h[1] - 1);
+    return MEHDG_ERR_SINGULAR;
+  }
+  return MEHDG_OK;
 }
 
 extern "C" int mehdg_condense_factor(mehdg_ctx* ctx, double shift, double* bhat) {

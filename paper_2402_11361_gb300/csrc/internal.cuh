@@ -70,6 +70,11 @@ struct mehdg_ctx {
   double* Whk = nullptr;     // [d][Np][Nth]  M^-1 Gh_k
   double* Bcat = nullptr;    // [d*Np][Np+Nth] = [W_k | -Wh_k] stacked over k (fused condensation GEMM)
   float* Bcat32 = nullptr;   // FP32 copy (mixed precision)
+  // Kronecker factors of the liftings on affine box macros (null when the mesh is not of that
+  // kind): [d][n1][n1] with W_k[a][b] = klift[k][a_k][b_k] when a and b agree off axis k, then
+  // [2d][n1] with Wh_k[a][(f, i)] = klift[f][a_k] when face f is normal to k and a lies on the
+  // line through face node i
+  double* klift = nullptr;
   double* src = nullptr;     // [E][nel][Ng][ns] or null
   double* uD = nullptr;      // [E][2d][nsf][nfp][ns] or null
 
@@ -121,12 +126,28 @@ struct mehdg_ctx {
          *bhat = nullptr;
   int lu_status = 0;
   bool condensed = false;
+  // nonlinear iteration state of the current stage (mehdg_stage_begin / mehdg_newton_step)
+  int cur_stage = -1;         // -1: no stage begun
+  double stage_dt = 0.0, stage_R0 = 0.0, stage_dtau = 1.0;
+  double stage_norms[4] = {};
+  int stage_newton = 0;
+  mehdg_time_term stage_tt{};
   // MLP preconditioner correction (kind 2)
   void* mlp = nullptr;
-  // phase timers (CUDA events on the context stream)
+  // phase timers (CUDA events on the context stream).  Outside graph capture every execution
+  // of a phase records its own event pair from a per-phase pool; completed pairs are summed
+  // (ph_sum, ph_cnt) at the library's synchronisation points.  Phases captured into the inner
+  // GMRES graph keep one external pair, re-recorded by each replay (ev, ph_graph executions
+  // per replay).
   cudaEvent_t ev[2 * 16] = {};
   long long launches = 0;   // kernels launched by this context
   bool ev_rec[16] = {};
+  std::vector<cudaEvent_t> ring_b[16], ring_e[16];
+  int ring_n[16] = {};
+  double ph_sum[16] = {}, ph_last[16] = {};
+  long long ph_cnt[16] = {};
+  int ph_graph[16] = {};
+  long long ig_replays = 0;   // inner-GMRES graph replays not yet added to the sums
 };
 
 enum Phase {
@@ -136,6 +157,8 @@ enum Phase {
 };
 void phase_begin(mehdg_ctx* ctx, int p);
 void phase_end(mehdg_ctx* ctx, int p);
+// add every completed phase execution to the sums (call after a stream synchronisation)
+void phase_harvest(mehdg_ctx* ctx);
 
 int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg);
 

@@ -563,6 +563,7 @@ static int inner_gmres(mehdg_ctx* ctx, const double* r, double* z) {
   CK(cudaMemcpyAsync(ctx->gin, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaGraphLaunch(ctx->ig_exec, ctx->stream));
   ctx->launches += ctx->ig_nodes;
+  ++ctx->ig_replays;
   CK(cudaMemcpyAsync(z, ctx->gout, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   return MEHDG_OK;
 }
@@ -579,7 +580,71 @@ int precond_impl(mehdg_ctx* ctx, int kind, const double* r, double* z) {
   return ctx_fail(ctx, MEHDG_ERR_ARG, "unknown preconditioner kind");
 }
 
+// GMRES(k) left-preconditioned by the block-Jacobi (A_uhuh)^-1 of the macro-faces: the
+// baseline solver of Sec. 4.2 (the first option there, GMRES with a fixed preconditioner;
+// compared with FGMRES and the multi-level preconditioner in the paper's Table 2).  Arnoldi
+// (CGS2, FP64, on the device) runs on M^-1 A^; the iterate is x = x_start + V y; the
+// stopping test is on the preconditioned residual |M^-1 (b - A^ x)| <= max(rtol |M^-1 b|, atol).
+static int gmres_left_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_stats* st) {
+  const long long n = ctx->ntr;
+  const int m = ctx->restart;
+  int rc;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, ctx->stream));
+  if ((rc = block_jacobi(ctx, b, ctx->rv))) return rc;
+  double beta;
+  if ((rc = vec_dot(ctx, ctx->rv, ctx->rv, n, &beta))) return rc;
+  beta = std::sqrt(beta);
+  const double tol = std::max(ctx->opt.lin_rtol * beta, ctx->opt.lin_atol);
+  int its = 0;
+  bool conv = beta <= tol;
+  while (!conv && its < ctx->opt.max_iters) {
+    if ((rc = vec_lincomb(ctx, n, 1.0 / beta, ctx->rv, 0.0, ctx->rv, ctx->V))) return rc;
+    Hess hs(m);
+    hs.g[0] = beta;
+    DevHess dh = dev_hess(ctx->dHo, m);
+    CK(cudaMemsetAsync(dh.H, 0, sizeof(double) * ((size_t)(m + 1) * m + 3 * (size_t)m + 1), ctx->stream));
+    k_set<<<1, 1, 0, ctx->stream>>>(dh.g, beta);
+    CKL();
+    double* est = ctx->dred + RED_SCAL + 4;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      if ((rc = apply_trace_impl(ctx, ctx->V + (size_t)j * n, ctx->tv))) return rc;
+      if ((rc = block_jacobi(ctx, ctx->tv, ctx->wv))) return rc;
+      if ((rc = arnoldi_dev(ctx, ctx->V, j, ctx->wv, n, dh))) return rc;
+      k_givens_step<<<1, 1, 0, ctx->stream>>>(dh, j, est);
+      CKL();
+      CK(cudaMemcpyAsync(ctx->hred + 200, est, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      phase_harvest(ctx);
+      const double res = ctx->hred[200], hn = ctx->hred[201];
+      ++its;
+      k = j + 1;
+      if (!std::isfinite(res)) return ctx_fail(ctx, MEHDG_ERR_NAN, "non-finite GMRES residual");
+      if (res <= tol || its >= ctx->opt.max_iters || hn == 0.0) break;
+    }
+    CK(cudaMemcpyAsync(hs.H.data(), dh.H, sizeof(double) * hs.H.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hs.g.data(), dh.g, sizeof(double) * hs.g.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> y = hs.solve(k);
+    if ((rc = maxpy(ctx, ctx->V, n, k, y.data(), x, n, 1.0))) return rc;
+    // restart residual M^-1 (b - A^ x)
+    if ((rc = apply_trace_impl(ctx, x, ctx->wv))) return rc;
+    if ((rc = vec_lincomb(ctx, n, 1.0, b, -1.0, ctx->wv, ctx->tv))) return rc;
+    if ((rc = block_jacobi(ctx, ctx->tv, ctx->rv))) return rc;
+    if ((rc = vec_dot(ctx, ctx->rv, ctx->rv, n, &beta))) return rc;
+    beta = std::sqrt(beta);
+    conv = beta <= tol;
+  }
+  if (st) {
+    st->fgmres_iters += its;
+    st->res = beta;
+  }
+  if (!conv) return ctx_fail(ctx, MEHDG_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
+  return MEHDG_OK;
+}
+
 int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_stats* st) {
+  if (ctx->opt.solver == 1) return gmres_left_impl(ctx, b, x, st);
   const long long n = ctx->ntr;
   const int m = ctx->restart;
   int rc;
@@ -620,6 +685,7 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
       CKL();
       CK(cudaMemcpyAsync(ctx->hred + 200, est, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
+      phase_harvest(ctx);
       const double res = ctx->hred[200], hn = ctx->hred[201];
       ++its;
       k = j + 1;

@@ -22,17 +22,64 @@ int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg) {
 // (cudaEventRecordExternal), so phases inside the captured inner GMRES are timed at
 // each replay too.
 void phase_begin(mehdg_ctx* ctx, int p) {
-  if (!ctx->ev[2 * p]) {
-    cudaEventCreate(&ctx->ev[2 * p]);
-    cudaEventCreate(&ctx->ev[2 * p + 1]);
+  if (ctx->capturing) {
+    if (!ctx->ev[2 * p]) {
+      cudaEventCreate(&ctx->ev[2 * p]);
+      cudaEventCreate(&ctx->ev[2 * p + 1]);
+    }
+    cudaEventRecordWithFlags(ctx->ev[2 * p], ctx->stream, cudaEventRecordExternal);
+    ++ctx->ph_graph[p];
+    return;
   }
-  if (ctx->capturing) cudaEventRecordWithFlags(ctx->ev[2 * p], ctx->stream, cudaEventRecordExternal);
-  else cudaEventRecord(ctx->ev[2 * p], ctx->stream);
+  std::vector<cudaEvent_t>&b = ctx->ring_b[p], &e = ctx->ring_e[p];
+  if (ctx->ring_n[p] == (int)b.size()) {
+    if (b.size() < 1024) {
+      cudaEvent_t x = nullptr, y = nullptr;
+      cudaEventCreate(&x);
+      cudaEventCreate(&y);
+      b.push_back(x);
+      e.push_back(y);
+    } else {   // pool full: wait for its last pair and fold the pool into the sums
+      cudaEventSynchronize(e[ctx->ring_n[p] - 1]);
+      phase_harvest(ctx);
+    }
+  }
+  cudaEventRecord(b[ctx->ring_n[p]], ctx->stream);
 }
 void phase_end(mehdg_ctx* ctx, int p) {
-  if (ctx->capturing) cudaEventRecordWithFlags(ctx->ev[2 * p + 1], ctx->stream, cudaEventRecordExternal);
-  else cudaEventRecord(ctx->ev[2 * p + 1], ctx->stream);
-  ctx->ev_rec[p] = true;
+  if (ctx->capturing) {
+    cudaEventRecordWithFlags(ctx->ev[2 * p + 1], ctx->stream, cudaEventRecordExternal);
+    ctx->ev_rec[p] = true;
+    return;
+  }
+  cudaEventRecord(ctx->ring_e[p][ctx->ring_n[p]], ctx->stream);
+  ++ctx->ring_n[p];
+}
+void phase_harvest(mehdg_ctx* ctx) {
+  for (int p = 0; p < PH_COUNT; ++p) {
+    for (int i = 0; i < ctx->ring_n[p]; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ctx->ring_b[p][i], ctx->ring_e[p][i]) == cudaSuccess) {
+        ctx->ph_sum[p] += t;
+        ++ctx->ph_cnt[p];
+        ctx->ph_last[p] = t;
+      }
+    }
+    ctx->ring_n[p] = 0;
+    if (ctx->ph_graph[p] && ctx->ev_rec[p] && ctx->ig_replays > 0) {
+      // graph phases: the pair holds the last execution of the last replay; every execution
+      // of the replays since the last harvest is counted at that duration
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ctx->ev[2 * p], ctx->ev[2 * p + 1]) == cudaSuccess) {
+        const long long n = ctx->ig_replays * ctx->ph_graph[p];
+        ctx->ph_sum[p] += (double)t * n;
+        ctx->ph_cnt[p] += n;
+        ctx->ph_last[p] = t;
+      }
+    }
+  }
+  cudaGetLastError();
+  ctx->ig_replays = 0;
 }
 
 extern "C" int mehdg_launch_count(const mehdg_ctx* ctx, long long* count) {
@@ -44,13 +91,24 @@ extern "C" int mehdg_launch_count(const mehdg_ctx* ctx, long long* count) {
 extern "C" int mehdg_phase_times(mehdg_ctx* ctx, double* ms, int n) {
   if (!ctx || !ms || n < 0 || n > PH_COUNT) return MEHDG_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
+  phase_harvest(ctx);
+  for (int p = 0; p < n; ++p) ms[p] = ctx->ph_cnt[p] > 0 ? ctx->ph_last[p] : -1.0;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_phase_stats(mehdg_ctx* ctx, double* sum_ms, long long* count, int n, int reset) {
+  if (!ctx || n < 0 || n > PH_COUNT) return MEHDG_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  phase_harvest(ctx);
   for (int p = 0; p < n; ++p) {
-    ms[p] = -1.0;
-    if (!ctx->ev_rec[p]) continue;
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, ctx->ev[2 * p], ctx->ev[2 * p + 1]));
-    ms[p] = t;
+    if (sum_ms) sum_ms[p] = ctx->ph_sum[p];
+    if (count) count[p] = ctx->ph_cnt[p];
   }
+  if (reset)
+    for (int p = 0; p < PH_COUNT; ++p) {
+      ctx->ph_sum[p] = 0.0;
+      ctx->ph_cnt[p] = 0;
+    }
   return MEHDG_OK;
 }
 
@@ -365,6 +423,7 @@ static void default_options(mehdg_options* o) {
   o->apply_mode = 0;
   o->tc_mode = 0;
   o->precond_bf16 = 0;
+  o->solver = 0;
 }
 
 static int setup(mehdg_ctx* ctx) {
@@ -514,6 +573,49 @@ static int setup(mehdg_ctx* ctx) {
       }
     }
 
+  // Kronecker factors of W_k and Wh_k: on a box macro M and G_k are products of 1D mass and
+  // derivative matrices, so W_k = M^-1 G_k acts along axis k only and Wh_k lifts each face onto
+  // the line normal to it.  The factors are read off the dense products and the whole
+  // operators are checked against them; a mismatch keeps the dense condensation.
+  std::vector<double> klift;
+  if (n1 <= 8) {
+    const int strides[3] = {1, n1, n1 * n1};
+    klift.assign((size_t)d * n1 * n1 + 2 * d * n1, 0.0);
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a < n1; ++a) {
+        for (int b = 0; b < n1; ++b)
+          klift[(size_t)k * n1 * n1 + a * n1 + b] = Wk[(size_t)k * Np * Np + (size_t)a * strides[k] * Np + b * strides[k]];
+      }
+    for (int fl = 0; fl < 2 * d; ++fl) {
+      const int k = fl / 2;
+      for (int a = 0; a < n1; ++a)
+        klift[(size_t)d * n1 * n1 + fl * n1 + a] = Whk[(size_t)k * Np * Nth + (size_t)a * strides[k] * Nth + fl * Nfn];
+    }
+    double wmax = 0.0, hmax = 0.0, werr = 0.0, herr = 0.0;
+    for (size_t i = 0; i < Wk.size(); ++i) wmax = std::max(wmax, std::fabs(Wk[i]));
+    for (size_t i = 0; i < Whk.size(); ++i) hmax = std::max(hmax, std::fabs(Whk[i]));
+    auto digit = [&](int node, int k) { return (node / strides[k]) % n1; };
+    for (int k = 0; k < d; ++k)
+      for (int a = 0; a < Np; ++a) {
+        for (int b = 0; b < Np; ++b) {
+          bool line = true;
+          for (int kk = 0; kk < d; ++kk)
+            if (kk != k && digit(a, kk) != digit(b, kk)) line = false;
+          const double ref = line ? klift[(size_t)k * n1 * n1 + digit(a, k) * n1 + digit(b, k)] : 0.0;
+          werr = std::max(werr, std::fabs(Wk[(size_t)k * Np * Np + (size_t)a * Np + b] - ref));
+        }
+        for (int c = 0; c < Nth; ++c) {
+          const int fl = c / Nfn, fn = ctx->facenode[c];
+          bool line = fl / 2 == k;
+          for (int kk = 0; kk < d && line; ++kk)
+            if (kk != k && digit(a, kk) != digit(fn, kk)) line = false;
+          const double ref = line ? klift[(size_t)d * n1 * n1 + fl * n1 + digit(a, k)] : 0.0;
+          herr = std::max(herr, std::fabs(Whk[(size_t)k * Np * Nth + (size_t)a * Nth + c] - ref));
+        }
+      }
+    if (!(werr <= 1e-12 * wmax && herr <= 1e-12 * hmax)) klift.clear();
+  }
+
   // -- maps
   const int E = ctx->E, F = ctx->F, ns = ctx->ns, Nt = ctx->Nt;
   ctx->h_gather.assign((size_t)E * Nt, 0);
@@ -583,6 +685,10 @@ static int setup(mehdg_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->Ghk, Ghk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Wk, Wk.data(), sizeof(double) * d * Np * Np, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Whk, Whk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
+  if (!klift.empty()) {
+    ALLOC(ctx->klift, klift.size());
+    CK(cudaMemcpyAsync(ctx->klift, klift.data(), sizeof(double) * klift.size(), cudaMemcpyHostToDevice, st));
+  }
   {
     // right factor of the fused condensation GEMM: [W_1 | -Wh_1; ...; W_d | -Wh_d], [d*Np][Np+Nth]
     const int nc = Np + Nth;
@@ -738,6 +844,7 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
   for (int k = 0; k < pr.dim; ++k)
     if (pr.nmac[k] < 1 || !(pr.hi[k] > pr.lo[k])) return MEHDG_ERR_ARG;
   if (!(pr.gamma > 1.0) || !(pr.Re > 0.0) || !(pr.Pr > 0.0)) return MEHDG_ERR_ARG;
+  if (opt && (opt->solver < 0 || opt->solver > 1 || opt->precond < 0 || opt->precond > 2)) return MEHDG_ERR_ARG;
   mehdg_ctx* ctx = new mehdg_ctx();
   ctx->prob = pr;
   default_options(&ctx->opt);
@@ -865,7 +972,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
-                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16};
+                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
@@ -874,6 +981,10 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
   mlp_destroy(ctx);
   for (int i = 0; i < 2 * PH_COUNT; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int p = 0; p < PH_COUNT; ++p) {
+    for (cudaEvent_t x : ctx->ring_b[p]) cudaEventDestroy(x);
+    for (cudaEvent_t x : ctx->ring_e[p]) cudaEventDestroy(x);
+  }
   delete ctx;
 }
 

@@ -60,6 +60,7 @@ int newton_step(mehdg_ctx* ctx, double shift, double* u, double* q, double* uh, 
   if ((rc = vec_axpy(ctx, nu * ctx->d, 1.0, ctx->dq, q))) return rc;
   if ((rc = vec_axpy(ctx, ctx->ntr, 1.0, ctx->duh, uh))) return rc;
   CK(cudaStreamSynchronize(ctx->stream));
+  phase_harvest(ctx);
   double t3 = now();
   if (st) {
     st->t_condense += t1 - t0;
@@ -69,10 +70,14 @@ int newton_step(mehdg_ctx* ctx, double shift, double* u, double* q, double* uh, 
   return MEHDG_OK;
 }
 
+bool stage_converged(const mehdg_ctx* ctx) {
+  return ctx->stage_norms[3] <= std::max(ctx->opt.newton_rtol * ctx->stage_R0, ctx->opt.newton_atol);
+}
+
 }  // namespace
 
-extern "C" int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q, double* uh,
-                                mehdg_solve_stats* st) {
+extern "C" int mehdg_stage_begin(mehdg_ctx* ctx, int stage, double dt, double* u, double* q, double* uh,
+                                 mehdg_solve_stats* st) {
   if (!ctx || !u || !q || !uh || stage < 0 || stage > 3) return MEHDG_ERR_ARG;
   if (stage > 0 && !(dt > 0.0)) return MEHDG_ERR_ARG;
   mehdg_solve_stats local{};
@@ -80,9 +85,7 @@ extern "C" int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u,
   *st = mehdg_solve_stats{};
   const long long nu = (long long)ctx->E * ctx->Nu;
   int rc;
-  double norms[4];
-  mehdg_time_term tt{0.0, nullptr, 0};
-  const mehdg_time_term* ttp = nullptr;
+  ctx->stage_tt = mehdg_time_term{0.0, nullptr, 0};
   if (stage > 0) {
     static const Dirk3 dk;
     const int i = stage - 1;
@@ -96,38 +99,90 @@ extern "C" int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u,
     if ((rc = vec_lincomb(ctx, nu, cn, ctx->un, 0.0, ctx->un, ctx->hist))) return rc;
     for (int j = 0; j < i; ++j)
       if ((rc = vec_axpy(ctx, nu, dk.dinv[i][j] / dt, ctx->ustage + (size_t)j * nu, ctx->hist))) return rc;
-    tt.coef = coef;
-    tt.hist = ctx->hist;
-    tt.supg_time = 1;
-    ttp = &tt;
+    ctx->stage_tt = mehdg_time_term{coef, ctx->hist, 1};
   }
+  ctx->cur_stage = -1;
   double t0 = now();
-  if ((rc = assemble_all(ctx, u, q, uh, ttp, norms))) return rc;
+  if ((rc = assemble_all(ctx, u, q, uh, stage > 0 ? &ctx->stage_tt : nullptr, ctx->stage_norms))) return rc;
   st->t_assemble += now() - t0;
-  const double R0 = norms[3];
-  st->res0 = R0;
-  double dtau = ctx->opt.tau_init;
-  int steps = 0;
-  while (norms[3] > std::max(ctx->opt.newton_rtol * R0, ctx->opt.newton_atol) && steps < ctx->opt.max_newton) {
-    if (!std::isfinite(norms[3])) return ctx_fail(ctx, MEHDG_ERR_NAN, "non-finite residual");
-    double shift = (stage == 0) ? 1.0 / dtau : 0.0;
-    rc = newton_step(ctx, shift, u, q, uh, st);
-    if (rc) return rc;
-    double RU_old = norms[1];
-    t0 = now();
-    if ((rc = assemble_all(ctx, u, q, uh, ttp, norms))) return rc;
-    st->t_assemble += now() - t0;
-    ++steps;
-    if (stage == 0)
-      dtau = std::min(std::max(dtau * RU_old / std::max(norms[1], 1e-300), ctx->opt.tau_init), ctx->opt.tau_max);
-  }
-  st->newton_steps = steps;
-  st->res = norms[3];
+  if (!std::isfinite(ctx->stage_norms[3])) return ctx_fail(ctx, MEHDG_ERR_NAN, "non-finite residual");
+  ctx->cur_stage = stage;
+  ctx->stage_dt = dt;
+  ctx->stage_R0 = ctx->stage_norms[3];
+  ctx->stage_dtau = ctx->opt.tau_init;
+  ctx->stage_newton = 0;
+  st->res0 = st->res = ctx->stage_R0;
+  st->status = stage_converged(ctx) ? 2 : 0;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_newton_step(mehdg_ctx* ctx, double* u, double* q, double* uh, mehdg_solve_stats* st) {
+  if (!ctx || !u || !q || !uh) return MEHDG_ERR_ARG;
+  if (ctx->cur_stage < 0) return ctx_fail(ctx, MEHDG_ERR_ARG, "mehdg_newton_step before mehdg_stage_begin");
+  mehdg_solve_stats local{};
+  if (!st) st = &local;
+  *st = mehdg_solve_stats{};
+  const int stage = ctx->cur_stage;
+  st->res0 = ctx->stage_norms[3];
+  const double shift = (stage == 0) ? 1.0 / ctx->stage_dtau : 0.0;
+  int rc = newton_step(ctx, shift, u, q, uh, st);
+  if (rc) return rc;
+  const double RU_old = ctx->stage_norms[1];
+  double t0 = now();
+  if ((rc = assemble_all(ctx, u, q, uh, stage > 0 ? &ctx->stage_tt : nullptr, ctx->stage_norms))) return rc;
+  st->t_assemble += now() - t0;
+  ++ctx->stage_newton;
+  st->newton_steps = 1;
+  st->res = ctx->stage_norms[3];
+  if (!std::isfinite(st->res)) return ctx_fail(ctx, MEHDG_ERR_NAN, "non-finite residual");
+  if (stage == 0)
+    ctx->stage_dtau = std::min(std::max(ctx->stage_dtau * RU_old / std::max(ctx->stage_norms[1], 1e-300),
+                                        ctx->opt.tau_init), ctx->opt.tau_max);
+  st->status |= stage_converged(ctx) ? 2 : 0;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_stage_end(mehdg_ctx* ctx, const double* u) {
+  if (!ctx || !u) return MEHDG_ERR_ARG;
+  if (ctx->cur_stage < 0) return ctx_fail(ctx, MEHDG_ERR_ARG, "mehdg_stage_end before mehdg_stage_begin");
+  const int stage = ctx->cur_stage;
+  int rc;
   if (stage > 0) {
+    const long long nu = (long long)ctx->E * ctx->Nu;
     if ((rc = vec_copy(ctx, nu, u, ctx->ustage + (size_t)(stage - 1) * nu))) return rc;
   }
   CK(cudaStreamSynchronize(ctx->stream));
-  if (norms[3] > std::max(ctx->opt.newton_rtol * R0, ctx->opt.newton_atol))
-    return ctx_fail(ctx, MEHDG_ERR_NOT_CONVERGED, "Newton iteration cap reached");
+  ctx->cur_stage = -1;
+  return MEHDG_OK;
+}
+
+extern "C" int mehdg_dirk_stage(mehdg_ctx* ctx, int stage, double dt, double* u, double* q, double* uh,
+                                mehdg_solve_stats* st) {
+  if (!ctx || !u || !q || !uh || stage < 0 || stage > 3) return MEHDG_ERR_ARG;
+  if (stage > 0 && !(dt > 0.0)) return MEHDG_ERR_ARG;
+  mehdg_solve_stats local{}, one{};
+  if (!st) st = &local;
+  *st = mehdg_solve_stats{};
+  int rc = mehdg_stage_begin(ctx, stage, dt, u, q, uh, &one);
+  if (rc) return rc;
+  st->res0 = one.res0;
+  st->t_assemble += one.t_assemble;
+  int steps = 0;
+  while (!stage_converged(ctx) && steps < ctx->opt.max_newton) {
+    rc = mehdg_newton_step(ctx, u, q, uh, &one);
+    if (rc) return rc;
+    st->fgmres_iters += one.fgmres_iters;
+    st->t_assemble += one.t_assemble;
+    st->t_condense += one.t_condense;
+    st->t_krylov += one.t_krylov;
+    st->t_recover += one.t_recover;
+    st->status |= one.status & 1;
+    ++steps;
+  }
+  st->newton_steps = steps;
+  st->res = ctx->stage_norms[3];
+  const bool ok = stage_converged(ctx);
+  if ((rc = mehdg_stage_end(ctx, u))) return rc;
+  if (!ok) return ctx_fail(ctx, MEHDG_ERR_NOT_CONVERGED, "Newton iteration cap reached");
   return MEHDG_OK;
 }

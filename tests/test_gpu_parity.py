@@ -3,8 +3,10 @@
 Every test feeds the same seeded inputs to both sides and compares element by
 element.  Tolerances: blocks, residuals, condensed operators, the trace apply,
 local solves and recovery agree to 1e-11 relative to the largest entry (FP64 on
-both sides, different summation orders); Newton and DIRK end states agree to
-1e-9 relative in L2 (both solved to stagnation-level tolerances).
+both sides, different summation orders); the FP64 DIRK end state agrees to 1e-10
+relative in L2 (both solved to stagnation-level tolerances).  Mixed-path operators
+(FP32 blocks) are held to a small multiple of cond(S) u_32, and mixed end states,
+where the FP64 Newton residual decides, to 1e-8.
 """
 import numpy as np
 import pytest
@@ -34,6 +36,14 @@ def to_dev(x):
 
 def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def rel2(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+U32 = 2.0 ** -24   # FP32 unit roundoff
 
 
 CASES = {
@@ -247,6 +257,29 @@ def _oracle_init(P, pr, du, duh):
     return u, np.zeros((P.E, P.d, P.ns, P.Np)), uh + duh
 
 
+def test_gmres_left_baseline_matches_dense_solve(lib):
+    """The baseline solver of Sec. 4.2 (GMRES left-preconditioned by the macro-face
+    block-Jacobi, solver = 1) reaches the dense solution of the explicit trace system,
+    like FGMRES with the multi-level preconditioner; iteration counts are reported."""
+    pr = W.mms(dim=2, nmac=3, m=2, p=2)
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 5)
+    blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    xo = np.linalg.solve(solve.explicit_trace_matrix(P, cond), solve.assemble_bhat(P, cond))
+    its = {}
+    for solver, precond in ((1, 0), (0, 1)):
+        ctx = lib.Context(pr, dict(lin_rtol=1e-13, precond=precond, restart=40, solver=solver, max_iters=4000))
+        ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+        b = ctx.condense(shift=0.3)
+        x, st = ctx.linear_solve(b)
+        its[solver] = st["fgmres_iters"]
+        assert rel2(x.cpu().numpy(), xo) < 1e-9
+        ctx.close()
+    print("GMRES left (block-Jacobi) iterations %d, FGMRES (multi-level) iterations %d" % (its[1], its[0]))
+    assert its[1] > 0 and its[0] > 0
+
+
 def test_init_state_matches(lib):
     pr = W.couette2d(nmac=3)
     P = solve.Problem(pr)
@@ -295,13 +328,14 @@ def test_dirk_step_matches_oracle(lib):
     du, duh = W.perturbation(pr, 4, amp=2e-3)
     u0, q0, uh0 = _oracle_init(P, pr, du, duh)
     ou, oq, ouh, stats = solve.dirk_step(P, u0, q0, uh0, dt=0.05, rtol=1e-13, precond="direct")
-    ctx = lib.Context(pr, dict(newton_rtol=1e-11, newton_atol=1e-15, lin_rtol=1e-12, max_iters=4000, precond=1))
+    ctx = lib.Context(pr, dict(newton_rtol=1e-12, newton_atol=1e-15, lin_rtol=1e-13, max_iters=4000, precond=1))
     u, q, uh = ctx.init_state(to_dev(du), to_dev(duh))
     for stage in (1, 2, 3):
         st = ctx.dirk_stage(stage, 0.05, u, q, uh)
-        assert st["res"] <= 1e-11 * st["res0"]
-    assert rel(u.cpu().numpy(), ou) < 1e-9
-    assert rel(uh.cpu().numpy(), ouh) < 1e-9
+        assert st["res"] <= 1e-12 * st["res0"]
+    e = (rel2(u.cpu().numpy(), ou), rel2(uh.cpu().numpy(), ouh), rel2(u.cpu().numpy() - u0, ou - u0))
+    print("2D DIRK step rel L2: u %.2e uh %.2e increment %.2e" % e)
+    assert e[0] <= 1e-10 and e[1] <= 1e-10 and e[2] <= 1e-8
     ctx.close()
 
 
@@ -332,8 +366,14 @@ def test_mixed_blocks_and_apply_close_to_oracle(lib):
     cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
     y = ctx.apply(to_dev(x)).cpu().numpy()
-    # condensation products run as TF32 tensor-core tiles (10-bit mantissa)
-    assert rel(y, solve.apply_trace(P, cond, x)) < 5e-3
+    # FP32 blocks, FP32 condensation and FP32 LU of S (Algorithm-2 apply): the operator is the
+    # FP64 one perturbed at the FP32 level and amplified by the local solves, so the bound is
+    # a small multiple of cond(S) u_32
+    condS = max(np.linalg.cond(c["S"]) for c in cond)
+    err = rel2(y, solve.apply_trace(P, cond, x))
+    bound = min(16 * condS * U32, 1e-5)
+    print("mixed Algorithm-2 apply rel L2 %.2e, cond(S) %.1f, bound %.2e" % (err, condS, bound))
+    assert err <= bound
     ctx.close()
 
 
@@ -449,13 +489,20 @@ def test_explicit_local_operator_apply(lib, prec):
     ctx.condense(shift=0.3)
     blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
     Nt = P.ns * P.Nth
-    tol_blk, tol_apply = (1e-10, 1e-11) if prec == 0 else (5e-3, 5e-3)   # mixed: TF32 tensor-core products
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    condS = max(np.linalg.cond(c["S"]) for c in cond)
+    # FP64: summation order only; mixed: FP32 blocks, FP32 S^-1 C and B (S^-1 C) products, so a
+    # small multiple of cond(S) u_32 (the operator's own FP32 perturbation amplified by S^-1)
+    tol_blk, tol_apply = (1e-10, 1e-11) if prec == 0 else (min(16 * condS * U32, 1e-5),) * 2
     for e in (0, 4, 8):
         A1, _ = solve.condense_one_layer(geos[e], blks[e], shift=0.3)
-        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), A1) < tol_blk
-    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+        eb = rel2(ctx.get_block(9, e).reshape(Nt, Nt), A1)
+        print("explicit A^T_i precision %d macro %d rel L2 %.2e (bound %.2e)" % (prec, e, eb, tol_blk))
+        assert eb <= tol_blk
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
-    assert rel(ctx.apply(to_dev(x)).cpu().numpy(), solve.apply_trace(P, cond, x)) < tol_apply
+    ea = rel2(ctx.apply(to_dev(x)).cpu().numpy(), solve.apply_trace(P, cond, x))
+    print("explicit apply precision %d rel L2 %.2e (bound %.2e)" % (prec, ea, tol_apply))
+    assert ea <= tol_apply
     ctx.close()
 
 
@@ -488,6 +535,49 @@ def test_mlp_gradient_matches_oracle(lib):
     lo, go = omlp.loss_and_grad(po, X.astype(np.float64), T.astype(np.float64), nin, hid, nout)
     assert abs(loss - lo) <= 1e-5 * lo
     assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max()
+    ctx.close()
+
+
+def test_learned_correction_gains_out_of_sample(lib):
+    """North-star learned part, judged out of sample: the correction network is trained on
+    (residual, error) pairs recorded by the plain solver (block-Jacobi FGMRES, kind 0)
+    during the first DIRK step of a 3D Taylor-Green vortex (4^3 macro-elements, p = 2),
+    then the first Newton system of the next DIRK step -- a system it never saw -- is
+    solved with block-Jacobi alone (kind 0), with the learned correction (kind 2) and
+    with the multi-level preconditioner (kind 1).  The learned form must need fewer
+    FGMRES iterations than the method it corrects (kind 0) and reach the same solution
+    (FGMRES tolerates the variable preconditioner, Sec. 4.2); the multi-level numbers and
+    all three device times are reported."""
+    pr = W.tgv(nmac=4, m=2, p=2)
+    dt = 0.5
+    ctx = lib.Context(pr, dict(precision=0, precond=0, lin_rtol=1e-8, restart=60, max_iters=4000,
+                               newton_rtol=1e-8, inner_iters=10))
+    u, q, uh = ctx.init_state(None, None, lift=True)
+    ctx.mlp_setup(hidden=256, seed=0, max_pairs=96)
+    ctx.mlp_set_recording(True)
+    for stage in (1, 2, 3):
+        ctx.dirk_stage(stage, dt, u, q, uh)
+    nsamp = ctx.mlp_set_recording(False)
+    assert nsamp > 0
+    first, last = ctx.mlp_train(epochs=400, batch=4096, lr=1e-3)
+    assert last < first
+    ctx.stage_begin(1, dt, u, q, uh)
+    b = ctx.condense(shift=0.0)
+    out = {}
+    for kind in (0, 2, 1):
+        ctx.set_precond(kind)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, st = ctx.linear_solve(b)
+        e1.record()
+        torch.cuda.synchronize()
+        out[kind] = (x.cpu().numpy(), st["fgmres_iters"], st["status"] & 1, e0.elapsed_time(e1))
+    print("out-of-sample system: block-Jacobi %d its %.1f ms; learned %d its %.1f ms (fallback %d); "
+          "multi-level %d its %.1f ms; training samples %d, loss %.3f -> %.3f"
+          % (out[0][1], out[0][3], out[2][1], out[2][3], out[2][2], out[1][1], out[1][3], nsamp, first, last))
+    assert out[2][2] == 0                      # no fallback
+    assert out[2][1] < out[0][1]               # fewer iterations than the method it corrects
+    assert rel2(out[2][0], out[0][0]) < 1e-6   # same solution (both to rtol 1e-8)
     ctx.close()
 
 

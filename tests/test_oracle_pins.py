@@ -461,6 +461,33 @@ def test_fgmres_equals_dense_solve(small2d):
         assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
 
 
+def test_gmres_left_equals_dense_solve_and_minimises_the_preconditioned_residual(small2d):
+    """Sec. 4.2 baseline (GMRES left-preconditioned by the face blocks): converges to the
+    dense solve of the explicit trace matrix, and after k steps of one cycle its iterate
+    minimises |Minv (b - A x)| over span{Minv b, (Minv A) Minv b, ...} (brute-force
+    least squares on the explicit Krylov basis)."""
+    P, blks, geos, cond = small2d
+    A = solve.explicit_trace_matrix(P, cond)
+    b = solve.assemble_bhat(P, cond)
+    fb = solve.face_blocks(P, blks)
+    flu = [solve.lu_factor(fb[f]) for f in range(P.F)]
+    Minv = lambda r: solve.block_jacobi(P, flu, r)
+    x, its, res = solve.gmres_left(lambda v: A @ v, Minv, b, rtol=1e-13, restart=40, maxit=2000)
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd) and its > 0
+    k = 6
+    xk, _, _ = solve.gmres_left(lambda v: A @ v, Minv, b, rtol=0.0, restart=k, maxit=k)
+    Mb = Minv(b)
+    K = [Mb]
+    for _ in range(k - 1):
+        K.append(Minv(A @ K[-1]))
+    Kb = np.array(K).T
+    MA = np.array([Minv(A @ Kb[:, i]) for i in range(k)]).T
+    c = np.linalg.lstsq(MA, Mb, rcond=None)[0]
+    xb = Kb @ c
+    assert np.linalg.norm(xk - xb) <= 1e-7 * np.linalg.norm(xb)
+
+
 def test_lu_factor_against_definition_and_scipy():
     rng = np.random.default_rng(2)
     for n in (1, 7, 64, 130):
