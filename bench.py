@@ -1079,8 +1079,9 @@ def main():
     ap.add_argument("--restart", type=int, default=60)
     ap.add_argument("--inner", type=int, default=10, help="inner GMRES iterations of the multi-level preconditioner")
     ap.add_argument("--apply-mode", type=int, default=1, help="mms workload: 0 Algorithm 2 apply; 1 stored A^T_i")
-    ap.add_argument("--fp64-apply-mode", type=int, default=0,
-                    help="apply of the plain FP64 form: 0 Algorithm 2 (default), 1 stored A^T_i")
+    ap.add_argument("--fp64-apply-mode", type=int, default=2,
+                    help="apply of the plain FP64 form: 2 Algorithm 2 with row-compressed B, C, D (default), "
+                         "0 dense Algorithm 2, 1 stored A^T_i")
     ap.add_argument("--tc-mode", type=int, default=0,
                     help="mixed path: 0 FP32 SIMT; 1 tcgen05 split-TF32 LU updates; 2 also the A^T_i products; "
                          "3 plain TF32 products")

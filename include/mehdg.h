@@ -106,6 +106,11 @@ typedef struct mehdg_options {
                          Sec. 4.2); 1: GMRES left-preconditioned by the macro-face
                          block-Jacobi (A_uhuh)^-1, the paper's baseline of Sec. 4.2 (Table 2);
                          its tolerance applies to the preconditioned residual |M^-1 r| */
+  int condense_layers; /* 2 (or 0): second-layer static condensation, eqs. AP12 and ASC2 (the
+                         paper's method); 1: one-layer condensation of eqs. C46-C47, the whole
+                         local matrix [A_qq A_qu; A_uq A_uu] factored per macro-element, for
+                         comparison (paper's Table 4); needs precision FP64, apply_mode 1 and
+                         32 (d + 1) Nu doubles of shared memory (2D and 3D p = 1) */
 } mehdg_options;
 
 typedef struct mehdg_info {
@@ -253,7 +258,10 @@ int mehdg_get_block(mehdg_ctx* ctx, int which, int macro, double* host_out,
  * zero.  Calls that overlap on the GPU (other streams, other threads) race on the
  * array: order them on one stream.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress with that device current); make that
- * first call before any stream capture begins.  Errors: ARG for invalid sizes or
+ * first call before any stream capture begins.  The looked-up address is kept for the
+ * life of the process and does not survive cudaDeviceReset of that device.  Shared memory:
+ * Nt + 2 Nu doubles per block plus the kernel's static part must fit the device's
+ * per-block limit (ARG otherwise).  Errors: ARG for invalid sizes or
  * pointers, TOO_LARGE as above, CUDA for a failed lookup or launch. */
 int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
                               const double* S_lu, const int* perm, const double* B,

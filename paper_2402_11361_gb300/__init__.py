@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("lin_rtol", c_double), ("lin_atol", c_double), ("inner_iters", c_int),
                 ("newton_rtol", c_double), ("newton_atol", c_double), ("max_newton", c_int),
                 ("tau_init", c_double), ("tau_max", c_double), ("refine_iters", c_int), ("apply_mode", c_int),
-                ("tc_mode", c_int), ("precond_bf16", c_int), ("solver", c_int)]
+                ("tc_mode", c_int), ("precond_bf16", c_int), ("solver", c_int),
+                ("condense_layers", c_int)]
 
 
 class Info(ctypes.Structure):
@@ -64,7 +65,7 @@ class SolveStats(ctypes.Structure):
 DEFAULT_OPTIONS = dict(precision=PREC_FP64, precond=0, restart=30, max_iters=2000, lin_rtol=1e-6, lin_atol=0.0,
                        inner_iters=5, newton_rtol=1e-8, newton_atol=1e-14, max_newton=100, tau_init=1.0,
                        tau_max=1e8, refine_iters=2, apply_mode=0, tc_mode=0,
-                       precond_bf16=0, solver=0)
+                       precond_bf16=0, solver=0, condense_layers=2)
 
 _lib = None
 

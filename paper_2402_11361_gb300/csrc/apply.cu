@@ -407,11 +407,13 @@ int apply_bf16_slots(mehdg_ctx* ctx, const double* x) {
 int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y) {
   if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "apply before mehdg_condense_factor");
   if (ctx->opt.precision == MEHDG_PREC_MIXED) return apply_t<float, float>(ctx, x, y);
+  if (ctx->opt.apply_mode == 2) return apply_sparse(ctx, x, y);
   return apply_t<double, double>(ctx, x, y);
 }
 
 int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   if (!ctx->condensed) return ctx_fail(ctx, MEHDG_ERR_ARG, "recover before mehdg_condense_factor");
+  if (ctx->opt.condense_layers == 1) return recover_one(ctx, duh, du, dq);
   size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
   phase_begin(ctx, PH_RECOVER);
   if (ctx->opt.precision == MEHDG_PREC_MIXED) {
@@ -498,10 +500,24 @@ extern "C" int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int N
     return MEHDG_ERR_TOO_LARGE;
   }
   const size_t smem = sizeof(double) * (Nt + 2 * (size_t)Nu);
-  if (smem > 227 * 1024) return MEHDG_ERR_ARG;
   double* slot = nullptr;
   int rc = noalloc_slot(&slot);
   if (rc) return rc;
+  {
+    // the kernel's own static shared memory (the substitution's diagonal block) counts
+    // against the same per-block limit as the dynamic part
+    cudaFuncAttributes fa{};
+    int dev = 0, optin = 0;
+    if (cudaFuncGetAttributes(&fa, k_apply<double, double>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return MEHDG_ERR_CUDA;
+    if (smem + fa.sharedSizeBytes > (size_t)optin) {
+      fprintf(stderr, "mehdg_apply_trace_noalloc: Nt + 2 Nu = %lld doubles of shared memory exceed the %d bytes "
+              "a block may use next to the kernel's %zu static bytes\n", (long long)(Nt + 2 * (size_t)Nu), optin,
+              (size_t)fa.sharedSizeBytes);
+      return MEHDG_ERR_ARG;
+    }
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaFuncSetAttribute(k_apply<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)

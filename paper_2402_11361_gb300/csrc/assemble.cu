@@ -361,11 +361,13 @@ struct SfCfg {
   static constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   static constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
   static constexpr int KA = (D + 1) * NS * (D + 1);
+  static constexpr int KAP = KA | 1;                                   // odd row stride: no bank repeats
   static constexpr int NC1 = D;                                        // classes after the x pass
   static constexpr int W1N = NC1 * NC1 * IPow<NG1, D - 1>::v * P1 * P1;
   static constexpr int W2N = D == 3 ? 2 * 2 * NG1 * P1 * P1 * P1 * P1 : 1;
+  static constexpr int PT = 4 * NG1 * P1 * P1;                         // product table of one axis
   static constexpr int NT = 256;
-  static constexpr size_t SMEM = sizeof(CT) * ((size_t)NG * KA + W1N + W2N + 4 * NG1 * P1);
+  static constexpr size_t SMEM = sizeof(CT) * ((size_t)NG * KAP + W1N + W2N + D * PT);
 };
 
 // class of a test/trial index alpha (0 value, 1 + k derivative along k) once the first
@@ -377,17 +379,23 @@ __global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __
                                                          const CT* __restrict__ Kvol, CT* __restrict__ Auu,
                                                          CT* __restrict__ Auq) {
   typedef SfCfg<D, P, CT> C;
-  constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, NT = C::NT;
+  constexpr int NS = C::NS, P1 = C::P1, NG1 = C::NG1, NLOC = C::NLOC, NG = C::NG, KA = C::KA, KAP = C::KAP;
+  constexpr int NT = C::NT, PT = C::PT;
   extern __shared__ __align__(16) unsigned char sf_raw[];
-  CT* sK = reinterpret_cast<CT*>(sf_raw);   // [NG][KA] pointwise kernels of one sub-element
-  CT* W1 = sK + NG * KA;                    // after the x pass
+  CT* sK = reinterpret_cast<CT*>(sf_raw);   // [NG][KAP] pointwise kernels of one sub-element
+  CT* W1 = sK + NG * KAP;                   // after the x pass
   CT* W2 = W1 + C::W1N;                     // after the y pass (3D)
-  CT* fv = W2 + C::W2N;                     // [NG1][P1] 1D values, then derivatives along x, y, z
-  CT* fd = fv + NG1 * P1;
+  // per axis k: products pt[k][ta][tb][g][a][b] = f_ta(g, a) f_tb(g, b), f_0 = 1D value,
+  // f_1 = 1D derivative along k (scaled to the sub-element), so each term is one FMA
+  CT* pt = W2 + C::W2N;
   const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z, tid = threadIdx.x;
-  for (int i = tid; i < NG1 * P1; i += NT) {
-    fv[i] = (CT)tab[i];
-    for (int k = 0; k < D; ++k) fd[k * NG1 * P1 + i] = (CT)(tab[NG1 * P1 + i] * 2.0 / g.he[k]);
+  for (int i = tid; i < D * PT; i += NT) {
+    const int b = i % P1, a = (i / P1) % P1, gq = (i / (P1 * P1)) % NG1, tb = (i / (P1 * P1 * NG1)) % 2;
+    const int ta = (i / (P1 * P1 * NG1 * 2)) % 2, k = i / PT;
+    const double sc = 2.0 / g.he[k];
+    const double fa = ta ? tab[NG1 * P1 + gq * P1 + a] * sc : tab[gq * P1 + a];
+    const double fb = tb ? tab[NG1 * P1 + gq * P1 + b] * sc : tab[gq * P1 + b];
+    pt[i] = (CT)(fa * fb);
   }
   const size_t Nu = g.Nu, Np = g.Np;
   CT* out = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + X - 1) * Nu * Nu;
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __
     }
     __syncthreads();   // previous sub-element's readers of sK are done
     const CT* Kel = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * g.nel + el) * (size_t)NG * KA;
-    for (int i = tid; i < NG * KA; i += NT) sK[i] = Kel[i];
+    for (int i = tid; i < NG * KA; i += NT) sK[(i / KA) * KAP + i % KA] = Kel[i];
     __syncthreads();
     for (int s = 0; s < NS; ++s) {
       // x pass: W1[ca][cb][g_rest][ax][bx], classes after one axis
@@ -412,12 +420,10 @@ __global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __
           if (sf_class(al, 1) != ca) continue;
           for (int be = 0; be <= D; ++be) {
             if (sf_class(be, 1) != cb || (al == 0 && be != 0)) continue;
-            const CT* fa = al == 1 ? fd : fv;
-            const CT* fb = be == 1 ? fd : fv;
-            const int ko = (al * NS + s) * (D + 1) + be;
+            const CT* pp = pt + (((al == 1) * 2 + (be == 1)) * NG1) * P1 * P1 + ax * P1 + bx;
+            const CT* kk = sK + (size_t)gr * NG1 * KAP + (al * NS + s) * (D + 1) + be;
 #pragma unroll
-            for (int gx = 0; gx < NG1; ++gx)
-              acc += fa[gx * P1 + ax] * fb[gx * P1 + bx] * sK[(gr * NG1 + gx) * KA + ko];
+            for (int gx = 0; gx < NG1; ++gx) acc += pp[gx * P1 * P1] * kk[gx * KAP];
           }
         }
         W1[i] = acc;
@@ -433,14 +439,12 @@ __global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __
           CT acc = CT(0);
           for (int ca = 0; ca < 3; ++ca) {
             if ((ca == 2) != (za == 1)) continue;
-            const CT* fa = ca == 1 ? fd + NG1 * P1 : fv;
             for (int cb = 0; cb < 3; ++cb) {
               if ((cb == 2) != (zb == 1)) continue;
-              const CT* fb = cb == 1 ? fd + NG1 * P1 : fv;
+              const CT* pp = pt + PT + (((ca == 1) * 2 + (cb == 1)) * NG1) * P1 * P1 + ay * P1 + by;
+              const CT* ww = W1 + ((((ca * 3 + cb) * NG1 + gz) * NG1) * P1 + ax) * P1 + bx;
 #pragma unroll
-              for (int gy = 0; gy < NG1; ++gy)
-                acc += fa[gy * P1 + ay] * fb[gy * P1 + by] *
-                       W1[((((ca * 3 + cb) * NG1 + gz) * NG1 + gy) * P1 + ax) * P1 + bx];
+              for (int gy = 0; gy < NG1; ++gy) acc += pp[gy * P1 * P1] * ww[gy * P1 * P1];
             }
           }
           W2[i] = acc;
@@ -451,7 +455,7 @@ __global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __
         last = W1;
       }
       // final pass (z in 3D, y in 2D) and the scatter into the macro block
-      const CT* fdl = fd + (D - 1) * NG1 * P1;
+      const CT* ptl = pt + (D - 1) * PT;
       for (int i = tid; i < NLOC * NLOC; i += NT) {
         const int a = i / NLOC, b = i % NLOC;
         int av[D], bv[D];
@@ -460,21 +464,18 @@ __global__ void __launch_bounds__(256) k_vol_contract_sf(Geo g, const double* __
           for (int k = 0; k < D; ++k) { av[k] = aa % P1; aa /= P1; bv[k] = bb % P1; bb /= P1; }
         }
         CT acc = CT(0);
-        for (int za = 0; za < 2; ++za) {
-          const CT* fa = za == 1 ? fdl : fv;
+        for (int za = 0; za < 2; ++za)
           for (int zb = 0; zb < 2; ++zb) {
-            const CT* fb = zb == 1 ? fdl : fv;
+            const CT* pp = ptl + ((za * 2 + zb) * NG1) * P1 * P1 + av[D - 1] * P1 + bv[D - 1];
+            const CT* ww;
+            if constexpr (D == 3)
+              ww = last + ((((za * 2 + zb) * NG1) * P1 + av[1]) * P1 + av[0]) * P1 * P1 + bv[1] * P1 + bv[0];
+            else
+              ww = last + (((za * 2 + zb) * NG1) * P1 + av[0]) * P1 + bv[0];
+            constexpr int WS = D == 3 ? P1 * P1 * P1 * P1 : P1 * P1;   // stride of the last axis' point
 #pragma unroll
-            for (int gl = 0; gl < NG1; ++gl) {
-              CT w;
-              if constexpr (D == 3)
-                w = last[((((za * 2 + zb) * NG1 + gl) * P1 + av[1]) * P1 + av[0]) * P1 * P1 + bv[1] * P1 + bv[0]];
-              else
-                w = last[(((za * 2 + zb) * NG1 + gl) * P1 + av[0]) * P1 + bv[0]];
-              acc += fa[gl * P1 + av[D - 1]] * fb[gl * P1 + bv[D - 1]] * w;
-            }
+            for (int gl = 0; gl < NG1; ++gl) acc += pp[gl * P1 * P1] * ww[gl * WS];
           }
-        }
         int A = 0, B = 0, sa = 1;
         for (int k = 0; k < D; ++k) {
           A += (li[k] * P + av[k]) * sa;

@@ -718,6 +718,9 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     if ((rc = face_reduce(ctx, ctx->bloc, bhat))) return rc;
   }
   phase_end(ctx, PH_BHAT);
+  if constexpr (sizeof(T) == 8) {
+    if (ctx->opt.apply_mode == 2 && (rc = sparse_pack(ctx))) return rc;
+  }
   if (ctx->opt.apply_mode == 1) {
     phase_begin(ctx, PH_FORM);
     if ((rc = form_local_operator<T>(ctx, Auu, Ahu, Auh, Ahh))) return rc;
@@ -739,7 +742,190 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   return MEHDG_OK;
 }
 
+// ---------------------------------------------------------------- one-layer condensation
+// Eqs. C46-C47 (Sec. 3.2): the whole local matrix A_local = [A_qq A_qu; A_uq A_uu] of a
+// macro-element (size NL = Nq + Nu) is factored, and
+//   A^T_i = A_uhuh - [A_uhq A_uhu] A_local^-1 [A_quh; A_uuh],
+//   b^T_i = -R_Uh + [A_uhq A_uhu] A_local^-1 [R_Q; R_U],
+//   [dQ; dU] = -A_local^-1 ([R_Q; R_U] + [A_quh; A_uuh] dUh).
+// The paper's second layer (the default) factors only the Schur complement S (size Nu);
+// this form exists to measure that difference (the paper's Table 4).  FP64; A^T_i is stored
+// in place of A_uhuh and applied as in apply_mode 1.
+
+namespace {
+
+// A_local and the right-hand sides [A_quh; A_uuh | R] of every macro (eq. C312 blocks;
+// A_qq = I (x) M, A_qu = G_k, A_quh = Gh_k as in R_Q = M q + G_k u + Gh_k uh)
+__global__ void k_build_local(const double* __restrict__ M, const double* __restrict__ Gk,
+                              const double* __restrict__ Ghk, const double* __restrict__ Auq,
+                              const double* __restrict__ Auu, const double* __restrict__ Auh,
+                              const double* __restrict__ RQ, const double* __restrict__ RU, double shift, int E, int d,
+                              int ns, int Np, int Nth, double* __restrict__ Aloc, double* __restrict__ Rhs) {
+  const int Nu = ns * Np, Nq = d * Nu, NL = Nq + Nu, Nt = ns * Nth, NR = Nt + 1;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long na = (long long)E * NL * NL, nr = (long long)E * NL * NR;
+  if (i < na) {
+    const int c = (int)(i % NL), r = (int)((i / NL) % NL);
+    const long long e = i / ((long long)NL * NL);
+    double v = 0.0;
+    if (r < Nq) {
+      const int k = r / Nu, s = (r % Nu) / Np, a = r % Np;
+      if (c < Nq) {
+        if (c / Nu == k && (c % Nu) / Np == s) v = M[(size_t)a * Np + c % Np];
+      } else {
+        const int cu = c - Nq;
+        if (cu / Np == s) v = Gk[((size_t)k * Np + a) * Np + cu % Np];
+      }
+    } else {
+      const int ru = r - Nq;
+      if (c < Nq) {
+        v = Auq[(((size_t)e * d + c / Nu) * Nu + ru) * Nu + c % Nu];
+      } else {
+        const int cu = c - Nq;
+        v = Auu[((size_t)e * Nu + ru) * Nu + cu];
+        if (ru / Np == cu / Np) v += shift * M[(size_t)(ru % Np) * Np + cu % Np];
+      }
+    }
+    Aloc[i] = v;
+  }
+  if (i < nr) {
+    const int j = (int)(i % NR), r = (int)((i / NR) % NL);
+    const long long e = i / ((long long)NL * NR);
+    double v;
+    if (r < Nq) {
+      const int k = r / Nu, s = (r % Nu) / Np, a = r % Np;
+      if (j == Nt) v = RQ[(size_t)e * Nq + r];
+      else v = (j / Nth == s) ? Ghk[((size_t)k * Np + a) * Nth + j % Nth] : 0.0;
+    } else {
+      const int ru = r - Nq;
+      v = (j == Nt) ? RU[(size_t)e * Nu + ru] : Auh[((size_t)e * Nu + ru) * Nt + j];
+    }
+    Rhs[i] = v;
+  }
+}
+
+// b_loc[e][r] = -R_Uh[e][r] + [A_uhq A_uhu][r] . y[e], y = A_local^-1 [R_Q; R_U] (last column of X)
+__global__ void __launch_bounds__(256) k_onelayer_bhat(const double* __restrict__ Ahq, const double* __restrict__ Ahu,
+                                                       const double* __restrict__ X, const double* __restrict__ RUh,
+                                                       int d, int Nu, int Nt, double* __restrict__ bloc) {
+  const int e = blockIdx.y, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (r >= Nt) return;
+  const int Nq = d * Nu, NL = Nq + Nu, NR = Nt + 1;
+  const double* Xe = X + (size_t)e * NL * NR;
+  double s = 0.0;
+  for (int c = lane; c < Nq; c += 32) s += Ahq[(((size_t)e * d + c / Nu) * Nt + r) * Nu + c % Nu] * Xe[(size_t)c * NR + Nt];
+  for (int c = lane; c < Nu; c += 32) s += Ahu[((size_t)e * Nt + r) * Nu + c] * Xe[(size_t)(Nq + c) * NR + Nt];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) bloc[(size_t)e * Nt + r] = s - RUh[(size_t)e * Nt + r];
+}
+
+}  // namespace
+
+int condense_one(mehdg_ctx* ctx, double shift, double* bhat) {
+  cudaStream_t st = ctx->stream;
+  const int E = ctx->E, d = ctx->d, ns = ctx->ns, Np = ctx->Np, Nth = ctx->Nth;
+  const long long Nu = ctx->Nu, Nt = ctx->Nt, Nq = (long long)d * Nu, NL = Nq + Nu, NR = Nt + 1;
+  int rc;
+  {
+    long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
+    k_face_blocks<double><<<(tot + 255) / 256, 256, 0, st>>>(ctx->Ahh, ctx->owner, ctx->fblk, ns, ctx->Nfn, Nth,
+                                                            (int)Nt, d, ctx->F);
+    CKL();
+  }
+  phase_begin(ctx, PH_CONDENSE);
+  {
+    const long long tot = std::max((long long)E * NL * NL, (long long)E * NL * NR);
+    k_build_local<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ctx->Mref, ctx->Gk, ctx->Ghk, ctx->Auq, ctx->Auu,
+                                                                 ctx->Auh, ctx->RQ, ctx->RU, shift, E, d, ns, Np, Nth,
+                                                                 ctx->Aloc, ctx->Rloc);
+    CKL();
+  }
+  CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
+  phase_begin(ctx, PH_LU);
+  if ((rc = batched_lu_t<double>(ctx, ctx->Aloc, ctx->permL, (int)NL, E, ctx->dflag))) return rc;
+  phase_end(ctx, PH_LU);
+  {
+    // X = A_local^-1 [A_quh; A_uuh | R]: 32 right-hand sides per CTA (A_local^-1 applied once per column)
+    constexpr int RC = 32;
+    const size_t smem = sizeof(double) * (size_t)NL * RC;
+    CK(cudaFuncSetAttribute(k_lu_solve_multi<double, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((NR + RC - 1) / RC), E);
+    k_lu_solve_multi<double, RC><<<grid, 256, smem, st>>>(ctx->Aloc, ctx->permL, ctx->Rloc, ctx->Xloc, (int)NL,
+                                                           (int)NR);
+    CKL();
+  }
+  {
+    // A^T_i = A_uhuh - A_uhq X_q - A_uhu X_u (in place of A_uhuh)
+    CondArgs<double> a{};
+    a.A = ctx->Ahq; a.sAe = (long long)d * Nt * Nu; a.sAk = (long long)Nt * Nu; a.sAs = 0; a.lda = (int)Nu;
+    a.M = (int)Nt; a.kdiv = (int)Nu;
+    a.Bc = ctx->Xloc; a.sBe = NL * NR; a.ldb = (int)NR;
+    a.N = (int)Nt; a.K = (int)Nq; a.ns = 1;
+    a.O1 = ctx->Ahh; a.sO1e = Nt * Nt; a.sO1s = 0; a.ldo1 = (int)Nt; a.o1_add = 0; a.nsplit = (int)Nt;
+    a.O2 = ctx->Ahh; a.ldo2 = (int)Nt;
+    if ((rc = cond_gemm(ctx, a, E))) return rc;
+    a.A = ctx->Ahu; a.sAe = Nt * Nu; a.sAk = 0; a.K = (int)Nu;
+    a.Bc = ctx->Xloc + Nq * NR;
+    if ((rc = cond_gemm(ctx, a, E))) return rc;
+  }
+  phase_end(ctx, PH_CONDENSE);
+  phase_begin(ctx, PH_FACE_LU);
+  if ((rc = batched_lu(ctx, ctx->fblk, ctx->fperm, ctx->nfb, ctx->F, ctx->dflag + 2))) return rc;
+  phase_end(ctx, PH_FACE_LU);
+  phase_begin(ctx, PH_BHAT);
+  {
+    dim3 grid((unsigned)((Nt + 7) / 8), E);
+    k_onelayer_bhat<<<grid, 256, 0, st>>>(ctx->Ahq, ctx->Ahu, ctx->Xloc, ctx->RUh, d, (int)Nu, (int)Nt, ctx->bloc);
+    CKL();
+  }
+  if (bhat && (rc = face_reduce(ctx, ctx->bloc, bhat))) return rc;
+  phase_end(ctx, PH_BHAT);
+  int flags[4];
+  CK(cudaMemcpyAsync(flags, ctx->dflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->condensed = true;
+  if (flags[0]) return ctx_fail(ctx, MEHDG_ERR_SINGULAR, "zero pivot in A_local of macro-element " + std::to_string(flags[1] - 1));
+  if (flags[2]) return ctx_fail(ctx, MEHDG_ERR_SINGULAR, "zero pivot in the A_uhuh block of face " + std::to_string(flags[3] - 1));
+  return MEHDG_OK;
+}
+
+namespace {
+// [dQ; dU] = -(y + X dUh_loc) for the one-layer form (X, y from condense_one)
+__global__ void __launch_bounds__(256) k_recover_one(const double* __restrict__ X, const int* __restrict__ gather,
+                                                     const double* __restrict__ duh, int Nq, int Nu, int Nt,
+                                                     double* __restrict__ du, double* __restrict__ dq) {
+  extern __shared__ double xl[];
+  const int e = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int NL = Nq + Nu, NR = Nt + 1;
+  for (int i = threadIdx.x; i < Nt; i += blockDim.x) xl[i] = duh[gather[(size_t)e * Nt + i]];
+  __syncthreads();
+  const double* Xe = X + (size_t)e * NL * NR;
+  for (int r = w; r < NL; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < Nt; c += 32) s += Xe[(size_t)r * NR + c] * xl[c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const double v = -(s + Xe[(size_t)r * NR + Nt]);
+      if (r < Nq) dq[(size_t)e * Nq + r] = v;
+      else du[(size_t)e * Nu + r - Nq] = v;
+    }
+  }
+}
+}  // namespace
+
+int recover_one(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
+  const int Nq = ctx->d * ctx->Nu;
+  phase_begin(ctx, PH_RECOVER);
+  k_recover_one<<<ctx->E, 256, sizeof(double) * ctx->Nt, ctx->stream>>>(ctx->Xloc, ctx->gather, duh, Nq, ctx->Nu,
+                                                                        ctx->Nt, du, dq);
+  CKL();
+  phase_end(ctx, PH_RECOVER);
+  return MEHDG_OK;
+}
+
 int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
+  if (ctx->opt.condense_layers == 1) return condense_one(ctx, shift, bhat);
   if (ctx->opt.precision == MEHDG_PREC_MIXED) return condense_t<float>(ctx, shift, bhat);
   return condense_t<double>(ctx, shift, bhat);
 }

@@ -25,6 +25,15 @@
       return ctx_fail(ctx, MEHDG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
   } while (0)
 
+// a row-compressed operator of one macro-element type: row r of macro e holds val[e * nnz + k]
+// at column col[k] for off[r] <= k < off[r + 1] (pattern shared by all macro-elements)
+struct SpOp {
+  const int* off = nullptr;
+  const int* col = nullptr;
+  double* val = nullptr;
+  long long nnz = 0;
+};
+
 template <class T>
 struct DBuf {
   T* p = nullptr;
@@ -109,6 +118,14 @@ struct mehdg_ctx {
   int ldf16 = 0;                          // its row stride: nfb rounded up to 32, zero-padded
   // mixed precision: S before its factorisation, for the FP64 refinement of local solves
   float* S32 = nullptr;
+  // apply_mode 2: row-compressed B, C, D (FP64), their patterns and the row of each entry
+  SpOp spB, spC, spD;
+  int *spB_row = nullptr, *spC_row = nullptr, *spD_row = nullptr;
+  bool sp_pending = false;
+  // one-layer condensation (condense_layers 1): A_local [E][NL][NL] (factored in place), its
+  // pivots, the right-hand sides [A_quh; A_uuh | R] [E][NL][Nt + 1] and X = A_local^-1 of them
+  double *Aloc = nullptr, *Rloc = nullptr, *Xloc = nullptr;
+  int* permL = nullptr;
 
   // Krylov workspace
   int restart = 30;
@@ -180,6 +197,12 @@ int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq);
 int precond_impl(mehdg_ctx* ctx, int kind, const double* r, double* z);
 int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_stats* st);
 int face_reduce(mehdg_ctx* ctx, const double* slot, double* y);
+int condense_one(mehdg_ctx* ctx, double shift, double* bhat);
+int recover_one(mehdg_ctx* ctx, const double* duh, double* du, double* dq);
+int sparse_setup(mehdg_ctx* ctx);
+int sparse_pack(mehdg_ctx* ctx);
+int apply_sparse(mehdg_ctx* ctx, const double* x, double* y);
+void sparse_destroy(mehdg_ctx* ctx);
 int vec_dot(mehdg_ctx* ctx, const double* a, const double* b, long long n, double* out_host);
 int vec_axpy(mehdg_ctx* ctx, long long n, double a, const double* x, double* y);
 int vec_scal(mehdg_ctx* ctx, long long n, double a, double* x);

@@ -59,7 +59,6 @@ __device__ __forceinline__ bool lp_tc_update(float* A, int n, int j0, int c0, co
   unsigned char* sAl = sAh + LPTC_BM * 32 * 4;
   unsigned char* sBh = sAl + LPTC_BM * 32 * 4;
   unsigned char* sBl = sBh + LPTC_BN * 32 * 4;
-  bool ok = true;
   for (int ti = 0; ti < m2; ti += LPTC_BM) {
     // L21 tile [128 x 32] from the panel; lanes cover an 8-row x 4-column core-matrix patch
     for (int i = tid; i < LPTC_BM * 32; i += LP_NT) {
@@ -105,7 +104,14 @@ __device__ __forceinline__ bool lp_tc_update(float* A, int n, int j0, int c0, co
                          tc::smem_u32(bar))
                      : "memory");
       }
-      if (!tc::mbar_wait(bar, phase)) ok = false;
+      if (!__syncthreads_and(tc::mbar_wait(bar, phase))) {
+        // a wait ran out: issue nothing more, wait once more (bounded) for the MMAs of this
+        // commit to finish with TMEM and shared memory, and report the failure; the caller
+        // abandons the factorisation and releases TMEM
+        tc::mbar_wait(bar, phase);
+        phase ^= 1;
+        return false;
+      }
       phase ^= 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // warp w reads TMEM lanes 32 (w % 4).. (rows) and accumulator columns (w / 4) * 128 ..
@@ -135,7 +141,7 @@ __device__ __forceinline__ bool lp_tc_update(float* A, int n, int j0, int c0, co
       __syncthreads();
     }
   }
-  return ok;
+  return true;
 }
 
 template <class T, bool TC>
@@ -302,8 +308,10 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
     // ---- 4. trailing update A22 -= L21 U12
     if constexpr (TC) {
       if (!lp_tc_update(reinterpret_cast<float*>(A), n, j0, c0, reinterpret_cast<const float*>(sP), sX, tc_slot,
-                        &tc_bar, tc_phase))
-        tc_ok = false;
+                        &tc_bar, tc_phase)) {
+        tc_ok = false;   // uniform across the CTA: stop here, the factors are discarded by the host
+        break;
+      }
     } else {
       T* sU = reinterpret_cast<T*>(sX);   // [LP_NB][LP_TM + 1]
       const int m2 = n - c0;

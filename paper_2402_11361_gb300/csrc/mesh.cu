@@ -424,6 +424,7 @@ static void default_options(mehdg_options* o) {
   o->tc_mode = 0;
   o->precond_bf16 = 0;
   o->solver = 0;
+  o->condense_layers = 2;
 }
 
 static int setup(mehdg_ctx* ctx) {
@@ -831,6 +832,23 @@ static int setup(mehdg_ctx* ctx) {
     }
   }
   CK(cudaStreamSynchronize(st));
+  if (ctx->opt.apply_mode == 2) {
+    int r_ = sparse_setup(ctx);
+    if (r_) return r_;
+  }
+  if (ctx->opt.condense_layers == 1) {
+    // one-layer condensation (FP64, explicit A^T_i): A_local of size NL = (d + 1) Nu must fit the
+    // multi-right-hand-side solve (32 columns of NL doubles in shared memory)
+    const size_t NL = (size_t)(d + 1) * Nu;
+    if (ctx->opt.precision != MEHDG_PREC_FP64 || ctx->opt.apply_mode != 1)
+      return ctx_fail(ctx, MEHDG_ERR_ARG, "condense_layers 1 needs precision FP64 and apply_mode 1");
+    if (sizeof(double) * NL * 32 > 200 * 1024)
+      return ctx_fail(ctx, MEHDG_ERR_ARG, "condense_layers 1: A_local too large for this degree (use the second layer)");
+    ALLOC(ctx->Aloc, (size_t)E * NL * NL);
+    ALLOC(ctx->Rloc, (size_t)E * NL * (Nt + 1));
+    ALLOC(ctx->Xloc, (size_t)E * NL * (Nt + 1));
+    ALLOC(ctx->permL, (size_t)E * NL);
+  }
   return MEHDG_OK;
 }
 
@@ -844,7 +862,9 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
   for (int k = 0; k < pr.dim; ++k)
     if (pr.nmac[k] < 1 || !(pr.hi[k] > pr.lo[k])) return MEHDG_ERR_ARG;
   if (!(pr.gamma > 1.0) || !(pr.Re > 0.0) || !(pr.Pr > 0.0)) return MEHDG_ERR_ARG;
-  if (opt && (opt->solver < 0 || opt->solver > 1 || opt->precond < 0 || opt->precond > 2)) return MEHDG_ERR_ARG;
+  if (opt && (opt->solver < 0 || opt->solver > 1 || opt->precond < 0 || opt->precond > 2 || opt->apply_mode < 0 ||
+              opt->apply_mode > 2))
+    return MEHDG_ERR_ARG;
   mehdg_ctx* ctx = new mehdg_ctx();
   ctx->prob = pr;
   default_options(&ctx->opt);
@@ -972,13 +992,14 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
-                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16};
+                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->Aloc, ctx->Rloc, ctx->Xloc, ctx->permL, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
   if (ctx->ig_exec) cudaGraphExecDestroy(ctx->ig_exec);
   if (ctx->xstart) cudaFree(ctx->xstart);
   mlp_destroy(ctx);
+  sparse_destroy(ctx);
   for (int i = 0; i < 2 * PH_COUNT; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   for (int p = 0; p < PH_COUNT; ++p) {

@@ -11,8 +11,9 @@
 // K block into a TMEM accumulator and commits them to the stage's mbarrier; the
 // next K block is staged meanwhile (two stages).  The epilogue reads TMEM with
 // tcgen05.ld (warp w owns lanes 32w..32w+31 = rows) and writes alpha*acc + beta*C.
-// Every mbarrier wait is bounded; on timeout the kernel records an error word and
-// still releases its TMEM.
+// Every mbarrier wait is bounded; on timeout the CTA stops issuing MMAs, waits once more
+// (bounded) on a commit covering all MMAs it issued, records an error word, skips the
+// epilogue and releases its TMEM.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -155,7 +156,9 @@ __global__ void __launch_bounds__(128) k_tc_gemm_tf32(TcArgs a) {
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    // a timed-out wait stops the K loop for the whole CTA: no further MMAs are issued
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ahi = tc::smem_u32(sA), bhi = tc::smem_u32(sB);
@@ -182,6 +185,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_tf32(TcArgs a) {
                    : "memory");
     }
   }
+  // this commit tracks every MMA the CTA issued, also after an early stop: its bounded
+  // wait is the wait for the work still in flight before TMEM is released
   if (tid == 0) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      tc::smem_u32(&bar[2]))

@@ -53,6 +53,7 @@ def rel2(a, b):
 
 
 FP64 = dict(precision=0, precond=1, apply_mode=0)
+FP64SP = dict(precision=0, precond=1, apply_mode=2)      # row-compressed Algorithm 2 (the bench's FP64 form)
 MIXED = dict(precision=1, precond=1, apply_mode=1, precond_bf16=1, refine_iters=1)
 CASES3D = {"tgv": lambda: W.tgv(nmac=2, m=2, p=2), "mms": lambda: W.mms(dim=3, nmac=2, m=2, p=2)}
 SHIFT = 0.5
@@ -71,14 +72,14 @@ def _oracle_linear_step(case):
     return _oracle_cache[case]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64sp", "mixed"])
 @pytest.mark.parametrize("case", sorted(CASES3D))
 def test_newton_linear_step_3d(lib, case, prec):
     pr, P, (u, q, uh), (dU, dQ, dUh), condS = _oracle_linear_step(case)
     # FGMRES to 1e-13 on the FP64 operator; the mixed path's outer operator is the FP32-stored
     # A^T_i (FP64 accumulation), whose rounding puts the reachable residual near 1e-7
-    opts = dict(FP64 if prec == "fp64" else MIXED, lin_rtol=1e-13 if prec == "fp64" else 1e-6, lin_atol=0.0,
-                restart=60, max_iters=4000)
+    base = {"fp64": FP64, "fp64sp": FP64SP, "mixed": MIXED}[prec]
+    opts = dict(base, lin_rtol=1e-6 if prec == "mixed" else 1e-13, lin_atol=0.0, restart=60, max_iters=4000)
     ctx = lib.Context(pr, opts)
     ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
     b = ctx.condense(shift=SHIFT)
@@ -87,7 +88,7 @@ def test_newton_linear_step_3d(lib, case, prec):
     e = [rel2(duh.cpu().numpy(), dUh), rel2(du.cpu().numpy(), dU), rel2(dq.cpu().numpy(), dQ)]
     print("%s %s linear step rel L2 (dUh, dU, dQ) = %s, FGMRES its %d, cond(S) %.2e"
           % (case, prec, ["%.2e" % x for x in e], st["fgmres_iters"], condS))
-    if prec == "fp64":
+    if prec != "mixed":
         assert max(e) <= 1e-10
     else:
         # FP32 blocks: relative perturbation ~ 2^-24 per entry, amplified by the local
@@ -114,11 +115,12 @@ def test_init_state_tgv_lifted_matches_oracle(lib):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp64sp", "mixed"])
 def test_dirk_step_3d_tgv_matches_oracle(lib, prec):
     g = _gold()
     pr = W.tgv(nmac=2, m=2, p=2)
-    opts = dict(FP64 if prec == "fp64" else MIXED, newton_rtol=1e-12, newton_atol=0.0, lin_rtol=1e-12,
+    base = {"fp64": FP64, "fp64sp": FP64SP, "mixed": MIXED}[prec]
+    opts = dict(base, newton_rtol=1e-12, newton_atol=0.0, lin_rtol=1e-12,
                 restart=60, max_iters=4000, max_newton=40)
     ctx = lib.Context(pr, opts)
     u, q, uh = to_dev(g["u0"]), to_dev(g["q0"]), to_dev(g["uh0"])
@@ -129,7 +131,7 @@ def test_dirk_step_3d_tgv_matches_oracle(lib, prec):
     e_state = max(rel2(gu, g["u1"]), rel2(guh, g["uh1"]))
     e_inc = rel2(gu - g["u0"], g["u1"] - g["u0"])
     print("%s DIRK step rel L2: state %.2e, increment %.2e" % (prec, e_state, e_inc))
-    if prec == "fp64":
+    if prec != "mixed":
         assert e_state <= 1e-10 and e_inc <= 1e-8
     else:
         assert e_state <= 1e-8 and e_inc <= 1e-6
