@@ -793,6 +793,60 @@ def run_tgv(args, ws, rank, lrank):
     return line
 
 
+def run_layers(args, ws, rank, lrank):
+    """The paper's Table-4 comparison on this GPU: one-layer (eqs. C46-C47) against second-layer
+    (eqs. AP12, ASC2) static condensation, FP64, on a 3D manufactured-solution cube of p = 1
+    macro-elements (m = 2; the one-layer local matrix must fit the solver's shared memory).
+    Both forms store A^T_i explicitly and apply it the same way, so the FGMRES iterations are
+    equal and the local time (condensation, factorisation, b^) is what differs."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+    dev = torch.device("cuda:%d" % lrank)
+    torch.cuda.set_device(dev)
+    pr = W.mms(dim=3, nmac=args.nmac_layers, m=2, p=1)
+    z = sizes(pr)
+    du, duh = W.perturbation(pr, 0)
+    st = torch.cuda.current_stream(dev)
+    state = None
+    res = {}
+    for layers in (2, 1):
+        ctx = pkg.Context(pr, dict(precision=pkg.PREC_FP64, apply_mode=1, condense_layers=layers, precond=1,
+                                   lin_rtol=1e-3, restart=60, max_iters=2000,
+                                   inner_iters=10), device=dev)
+        if state is None:   # the first Newton system of the steady solve from the lifted initial state
+            state = ctx.init_state(torch.as_tensor(du, device=dev), torch.as_tensor(duh, device=dev), lift=True)
+        K = max(1, args.steps)
+        t_local = 0.0
+        for k in range(K + 1):      # the condensation works in place: assemble before each one
+            ctx.assemble(*state)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            b = ctx.condense(shift=0.5)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if k > 0:                # the first one is the warm-up
+                t_local += e0.elapsed_time(e1) / 1e3 / K
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(st)
+        x, stats = ctx.linear_solve(b, allow_not_converged=True)
+        g1.record(st)
+        torch.cuda.synchronize()
+        res["one_layer" if layers == 1 else "second_layer"] = dict(
+            local_s=t_local, local_ms_per_macro=t_local / z["E"] * 1e3, global_s=g0.elapsed_time(g1) / 1e3,
+            fgmres_iters=stats["fgmres_iters"], fgmres_res=stats["res"], local_matrix_size=(z["d"] + 1) * z["Nu"] if layers == 1 else z["Nu"])
+        ctx.close()
+    return {"metric": METRIC, "value": res["second_layer"]["local_s"], "unit": "s per condensation (second layer)",
+            "n_gpus": ws, "steps": max(1, args.steps), "warmup": 1, "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic (lifted manufactured solution + seeded 1e-3 perturbation)", "scaling": "weak",
+            "vs_baseline": None,
+            "config": {"workload": "3D MMS cube, %d^3 macro-elements x 2^3 hexes, p=1 (Nu=%d, Nt=%d): one-layer vs "
+                                   "second-layer condensation" % (args.nmac_layers, z["Nu"], z["Nt"])},
+            "layers": res, "speedup_second_over_one_layer": res["one_layer"]["local_s"] / res["second_layer"]["local_s"]}
+
+
 def run_batched(args, ws, rank, lrank):
     """Batched uneven steady solves: independent manufactured-solution problems of the
     config-2 form with seeded sizes (m_c^3 macro-elements, m_c in 2..6) and degrees
@@ -1069,7 +1123,7 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (default: 10 Newton steps for tgv)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched"],
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched", "layers"],
                     help="tgv: Newton steps of the 16^3 Taylor-Green DIRK integration (default, the headline); "
                          "mms: steady 3D manufactured solution (8^3); batched: independent uneven problems")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
@@ -1082,9 +1136,10 @@ def main():
     ap.add_argument("--fp64-apply-mode", type=int, default=2,
                     help="apply of the plain FP64 form: 2 Algorithm 2 with row-compressed B, C, D (default), "
                          "0 dense Algorithm 2, 1 stored A^T_i")
-    ap.add_argument("--tc-mode", type=int, default=0,
-                    help="mixed path: 0 FP32 SIMT; 1 tcgen05 split-TF32 LU updates; 2 also the A^T_i products; "
-                         "3 plain TF32 products")
+    ap.add_argument("--tc-mode", type=int, default=4,
+                    help="mixed path: 4 forming A^T_i with the swizzled K-major tcgen05 product (default); 0 FP32 "
+                         "SIMT; 1 tcgen05 split-TF32 LU updates; 2 also the condensation and A^T_i products (first "
+                         "tcgen05 kernel); 3 plain TF32; 5 dense volume contraction")
     ap.add_argument("--refine", type=int, default=1,
                     help="FP64 refinement sweeps of each local S solve (b^ and recovery) on the mixed path")
     ap.add_argument("--precond-bf16", type=int, default=1,
@@ -1104,6 +1159,7 @@ def main():
     ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--batch-mem-gb", type=float, default=200.0)
     ap.add_argument("--nmac-tgv", type=int, default=16, help="TGV macro-elements per edge (16 = the config)")
+    ap.add_argument("--nmac-layers", type=int, default=8, help="layers workload: macro-elements per cube edge")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "fp64" if args.workload == "tgv" else "mixed"
@@ -1118,9 +1174,10 @@ def main():
     if ws > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("tgv", "batched"):
+    if args.workload in ("tgv", "batched", "layers"):
         args.steps = args.steps or 10
-        line = run_tgv(args, ws, rank, lrank) if args.workload == "tgv" else run_batched(args, ws, rank, lrank)
+        run = {"tgv": run_tgv, "batched": run_batched, "layers": run_layers}[args.workload]
+        line = run(args, ws, rank, lrank)
         if rank == 0:
             if args.workload == "tgv" and args.cpu and ws == 1:   # the oracle baseline, N = 1 only
                 line["cpu_baseline"] = cpu_baseline_tgv(line)

@@ -94,7 +94,10 @@ typedef struct mehdg_options {
   int tc_mode;        /* mixed precision dense local work: 0 FP32 SIMT; 1 batched LU of S
                          with tcgen05 trailing updates in split TF32 (3 products, about
                          FP32 accuracy); 2 also the condensation products and forming
-                         A^T_i in split TF32; 3 as 2 with plain TF32 */
+                         A^T_i in split TF32; 3 as 2 with plain TF32; 4 forming A^T_i =
+                         D + B (S^-1 C) on tcgen05 with operands staged K-major in the
+                         128-byte-swizzled layout (split TF32), LU and substitutions SIMT;
+                         5 as 0 with the dense (not sum-factorised) volume contraction */
   int precond_bf16;   /* apply_mode 1 with precond 1: the inner GMRES of the multi-level
                          preconditioner applies a BF16 copy of A^T_i (half the bytes of
                          the FP32 operator; FGMRES allows the inexact preconditioner),
@@ -323,6 +326,17 @@ int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long lda, long 
  * caller.  Synchronises stream.  Errors: ARG, SINGULAR when a pivot is exactly zero (the
  * message on stderr names the first such matrix; the other matrices are factored), CUDA. */
 int mehdg_lu_batched(int n, int batch, void* A, int* perm, int fp32, int* dflag, void* stream);
+
+/* The product with a transposed right operand on the tcgen05 tensor cores (kind::tf32, each
+ * operand split into a TF32 part and a TF32 remainder, three products: close to FP32
+ * accuracy), the kernel of tc_mode 4:  C_b = alpha A_b Bt_b^T + beta C_b for b < batch, A_b =
+ * A + b sA [M x K], Bt_b = Bt + b sB [N x K], C_b = C + b sC [M x N], row-major FP32 device
+ * arrays with the given leading dimensions (4-byte alignment only).  err: device int set to 1
+ * if an internal wait timed out (the result is then invalid).  Asynchronous on stream.
+ * Errors: ARG, CUDA. */
+int mehdg_tc_gemm_nt(int M, int N, int K, const float* A, long long lda, long long sA, const float* Bt,
+                     long long ldb, long long sB, float* C, long long ldc, long long sC, float alpha,
+                     float beta, int batch, int* err, void* stream);
 
 /* Device time in milliseconds of the most recent execution of each internal phase
  * (CUDA events on the context stream; -1 for phases not run since mehdg_mesh):

@@ -21,7 +21,7 @@ EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_loca
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
            "mehdg_get_block", "mehdg_phase_times", "mehdg_phase_stats", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
-           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_destroy",
+           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_destroy",
            "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
@@ -104,6 +104,9 @@ def load_library(path=LIB_PATH):
     lib.mehdg_mlp_train.argtypes = [c_void_p, I, I, c_double, P(c_double)]
     lib.mehdg_set_precond.argtypes = [c_void_p, I]
     lib.mehdg_lu_batched.argtypes = [I, I, c_void_p, c_void_p, I, c_void_p, c_void_p]
+    L, F = c_longlong, ctypes.c_float
+    lib.mehdg_tc_gemm_nt.argtypes = [I, I, I, c_void_p, L, L, c_void_p, L, L, c_void_p, L, L, F, F, I, c_void_p,
+                                     c_void_p]
     lib.mehdg_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.restype = None
     lib.mehdg_last_error.argtypes = [c_void_p]
@@ -148,6 +151,27 @@ def options_struct(opts=None):
 
 class MehdgError(RuntimeError):
     pass
+
+
+def tc_gemm_nt(A, Bt, C, alpha=1.0, beta=0.0):
+    """C_b = alpha A_b Bt_b^T + beta C_b on tcgen05 (split TF32) for contiguous CUDA float32
+    tensors A [batch, M, K], Bt [batch, N, K], C [batch, M, N] (mehdg_tc_gemm_nt).  Returns the
+    error word (nonzero: a wait timed out and C is invalid)."""
+    import torch
+    lib = load_library()
+    batch, M, K = A.shape
+    N = Bt.shape[1]
+    assert Bt.shape == (batch, N, K) and C.shape == (batch, M, N)
+    for t in (A, Bt, C):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    P = c_void_p
+    rc = lib.mehdg_tc_gemm_nt(M, N, K, P(A.data_ptr()), K, M * K, P(Bt.data_ptr()), K, N * K, P(C.data_ptr()), N,
+                              M * N, ctypes.c_float(alpha), ctypes.c_float(beta), batch, P(err.data_ptr()),
+                              P(torch.cuda.current_stream(A.device).cuda_stream))
+    if rc != 0:
+        raise MehdgError("mehdg_tc_gemm_nt failed (%s)" % ERRORS.get(rc, rc))
+    return int(err.item())
 
 
 def lu_batched(A, perm=None):

@@ -824,8 +824,9 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   }
   {
     dim3 grid(E, D + 1, NS);
-    if (sizeof(BT) == 8) {
-      // FP64 path: sum factorisation (FP64 pipe bound)
+    if (ctx->opt.tc_mode != 5) {
+      // sum factorisation (both precisions; the dense k_vol_contract is kept as tc_mode 5 for
+      // comparison)
       typedef SfCfg<D, P, BT> C;
       CK(cudaFuncSetAttribute(k_vol_contract_sf<D, P, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)C::SMEM));

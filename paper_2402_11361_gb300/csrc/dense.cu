@@ -521,8 +521,31 @@ int form_local_operator(mehdg_ctx* ctx, T* S, T* B, T* C, T* D) {
       return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1: S (Nu x 32 right-hand sides) exceeds shared memory; use "
                                           "apply_mode 0 for this degree");
   }
-  CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((Nt + RC - 1) / RC, E);
+  if constexpr (sizeof(T) == 4) {
+    if (ctx->use_tc_nt) {
+      // tcgen05: X^T = (S^-1 C)^T written K-major, then D += B X^T^T on the tensor cores
+      CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+      phase_begin(ctx, PH_TRSM);
+      k_lu_solve_multi<T, RC, true><<<grid, 256, smem, ctx->stream>>>(S, ctx->perm, C, X, Nu, Nt);
+      CKL();
+      phase_end(ctx, PH_TRSM);
+      TcNT a{};
+      a.M = Nt; a.N = Nt; a.K = Nu;
+      a.A = B; a.lda = Nu; a.sA = (long long)Nt * Nu;
+      a.Bt = X; a.ldb = Nu; a.sB = (long long)Nt * Nu;
+      a.C = D; a.ldc = Nt; a.sC = (long long)Nt * Nt;
+      a.alpha = 1.f; a.beta = 1.f; a.err = ctx->dtcerr;
+      phase_begin(ctx, PH_COND_GEMM);
+      cudaError_t e = tc_gemm_nt_launch(a, E, ctx->stream);
+      ++ctx->launches;
+      phase_end(ctx, PH_COND_GEMM);
+      if (e != cudaSuccess) return ctx_fail(ctx, MEHDG_ERR_CUDA, std::string("tcgen05 NT GEMM: ") + cudaGetErrorString(e));
+      return MEHDG_OK;
+    }
+  }
+  CK(cudaFuncSetAttribute(k_lu_solve_multi<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   phase_begin(ctx, PH_TRSM);
   k_lu_solve_multi<T, RC><<<grid, 256, smem, ctx->stream>>>(S, ctx->perm, C, X, Nu, Nt);
   CKL();

@@ -102,7 +102,7 @@ struct mehdg_ctx {
 
   float *Wk32 = nullptr, *Whk32 = nullptr;   // FP32 copies of W_k, Wh_k (mixed precision)
   int* dtcerr = nullptr;                       // tensor-core kernel error word
-  bool use_tc_condense = false, use_tc_form = false, use_tc_lu = false, tc_split = true;
+  bool use_tc_condense = false, use_tc_form = false, use_tc_lu = false, tc_split = true, use_tc_nt = false;
   float* finv32 = nullptr;   // explicit FP32 inverses of the face blocks (mixed precision block-Jacobi)
   // mixed precision: FP32 copies of the state, history, 1D tables and source for the FP32
   // Jacobian pass of the assembly
@@ -216,3 +216,5 @@ int mlp_record_pair(mehdg_ctx* ctx, const double* r, const double* e);
 void mlp_destroy(mehdg_ctx* ctx);
 struct TcArgs;
 cudaError_t tc_gemm_launch(const TcArgs& a, int batch, cudaStream_t st, bool split);
+struct TcNT;
+cudaError_t tc_gemm_nt_launch(const TcNT& a, int batch, cudaStream_t st);

@@ -269,7 +269,8 @@ __device__ inline void lu_solve_f32_refined(const float* __restrict__ LU, const 
 // L is staged in shared memory transposed (prefetched into registers while the previous
 // chunk computes) and each thread keeps an 8-row x CPT-column tile of the update in
 // registers.  B == nullptr solves for the identity (columns of S^-1).
-template <class T, int RC>
+// XT: write X transposed, [nrhs][n] (the K-major right operand of a tcgen05 product)
+template <class T, int RC, bool XT = false>
 __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeof(T) <= 128) ? 2 : 1))
     k_lu_solve_multi(const T* __restrict__ LUall, const int* __restrict__ permall,
                                                        const T* __restrict__ Ball, T* __restrict__ Xall, int n,
@@ -472,8 +473,15 @@ __global__ void __launch_bounds__(256, (RC * sizeof(T) <= 64) ? 3 : ((RC * sizeo
     }
     __syncthreads();
   }
-  for (int i = tid; i < n * RC; i += blockDim.x) {
-    int r = i / RC, c = i % RC;
-    if (c < rc) X[(size_t)r * nrhs + c0 + c] = x[i];
+  if constexpr (XT) {
+    for (int i = tid; i < n * RC; i += blockDim.x) {
+      const int c = i / n, r = i % n;
+      if (c < rc) X[(size_t)(c0 + c) * n + r] = x[(size_t)r * RC + c];
+    }
+  } else {
+    for (int i = tid; i < n * RC; i += blockDim.x) {
+      int r = i / RC, c = i % RC;
+      if (c < rc) X[(size_t)r * nrhs + c0 + c] = x[i];
+    }
   }
 }

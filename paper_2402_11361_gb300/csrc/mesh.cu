@@ -842,7 +842,7 @@ static int setup(mehdg_ctx* ctx) {
     const size_t NL = (size_t)(d + 1) * Nu;
     if (ctx->opt.precision != MEHDG_PREC_FP64 || ctx->opt.apply_mode != 1)
       return ctx_fail(ctx, MEHDG_ERR_ARG, "condense_layers 1 needs precision FP64 and apply_mode 1");
-    if (sizeof(double) * NL * 32 > 200 * 1024)
+    if (sizeof(double) * NL * 32 > 176 * 1024)
       return ctx_fail(ctx, MEHDG_ERR_ARG, "condense_layers 1: A_local too large for this degree (use the second layer)");
     ALLOC(ctx->Aloc, (size_t)E * NL * NL);
     ALLOC(ctx->Rloc, (size_t)E * NL * (Nt + 1));
@@ -872,9 +872,11 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
   ctx->stream = (cudaStream_t)stream;
   // tc_mode: 0 SIMT; 1 tensor cores (split TF32) for the LU trailing updates only;
   // 2 split TF32 for LU, condensation and forming A^T_i; 3 plain TF32 everywhere
-  ctx->use_tc_lu = ctx->opt.tc_mode >= 1;
-  ctx->use_tc_condense = ctx->use_tc_form = ctx->opt.tc_mode >= 2;
+  ctx->use_tc_lu = ctx->opt.tc_mode >= 1 && ctx->opt.tc_mode <= 3;
+  ctx->use_tc_condense = ctx->use_tc_form = ctx->opt.tc_mode == 2 || ctx->opt.tc_mode == 3;
   ctx->tc_split = ctx->opt.tc_mode <= 2;
+  // 4: forming A^T_i on tcgen05 with the swizzled K-major product (D += B (S^-1 C)), the rest SIMT
+  ctx->use_tc_nt = ctx->opt.tc_mode == 4;
   int rc = setup(ctx);
   if (rc != MEHDG_OK) {
     std::string msg = ctx->err;

@@ -87,7 +87,8 @@ __device__ __forceinline__ double sp_row_dot(const double* __restrict__ v, const
 
 // Algorithm 2 for one macro-element per CTA with the row-compressed C, B, D: gather x on dT_i,
 // y1 = C x, y2 = S^-1 y1 (LU factors, dense), slot = B y2 + D x
-__global__ void __launch_bounds__(512) k_apply_sparse(const double* __restrict__ S, const int* __restrict__ perm,
+constexpr int SP_NT = 256;   // four CTAs (macro-elements) resident per SM hide the solves' latency
+__global__ void __launch_bounds__(SP_NT, 4) k_apply_sparse(const double* __restrict__ S, const int* __restrict__ perm,
                                                       SpOp B, SpOp C, SpOp D, const int* __restrict__ gather,
                                                       const double* __restrict__ x, double* __restrict__ slot, int Nu,
                                                       int Nt) {
@@ -214,7 +215,7 @@ int apply_sparse(mehdg_ctx* ctx, const double* x, double* y) {
   const size_t smem = sizeof(double) * (ctx->Nt + 2 * (size_t)ctx->Nu);
   CK(cudaFuncSetAttribute(k_apply_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   phase_begin(ctx, PH_APPLY);
-  k_apply_sparse<<<ctx->E, 512, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->spB, ctx->spC, ctx->spD, ctx->gather,
+  k_apply_sparse<<<ctx->E, SP_NT, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->spB, ctx->spC, ctx->spD, ctx->gather,
                                                      x, ctx->slot, ctx->Nu, ctx->Nt);
   CKL();
   int rc = face_reduce(ctx, ctx->slot, y);

@@ -40,3 +40,31 @@ extern "C" int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long
   return tc_gemm_launch(a, batch, static_cast<cudaStream_t>(stream), split != 0) == cudaSuccess ? MEHDG_OK
                                                                                                  : MEHDG_ERR_CUDA;
 }
+
+template <int BN>
+static cudaError_t launch_nt(const TcNT& a, int batch, cudaStream_t st) {
+  const size_t smem = tc_nt_smem<BN>();
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_nt<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.N + BN - 1) / BN, (a.M + 127) / 128, batch);
+  k_tc_gemm_nt<BN><<<grid, TCNT_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// N tile 128 for N <= 128, else 256 (A^T_i: N = Nt = 750 -> 3 tiles)
+cudaError_t tc_gemm_nt_launch(const TcNT& a, int batch, cudaStream_t st) {
+  return a.N <= 128 ? launch_nt<128>(a, batch, st) : launch_nt<256>(a, batch, st);
+}
+
+extern "C" int mehdg_tc_gemm_nt(int M, int N, int K, const float* A, long long lda, long long sA, const float* Bt,
+                                long long ldb, long long sB, float* C, long long ldc, long long sC, float alpha,
+                                float beta, int batch, int* err, void* stream) {
+  if (M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || !A || !Bt || !C || !err) return MEHDG_ERR_ARG;
+  TcNT a{};
+  a.M = M; a.N = N; a.K = K;
+  a.A = A; a.lda = lda; a.sA = sA;
+  a.Bt = Bt; a.ldb = ldb; a.sB = sB;
+  a.C = C; a.ldc = ldc; a.sC = sC;
+  a.alpha = alpha; a.beta = beta; a.err = err;
+  return tc_gemm_nt_launch(a, batch, static_cast<cudaStream_t>(stream)) == cudaSuccess ? MEHDG_OK : MEHDG_ERR_CUDA;
+}

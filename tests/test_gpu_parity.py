@@ -207,6 +207,39 @@ def test_row_compressed_apply_matches_algorithm2(lib, case):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["mms2d_p2", "couette2d_p2", "mms3d_p1"])
+def test_one_layer_condensation_matches_oracle(lib, case):
+    """condense_layers 1 (eqs. C46-C47, the paper's Table-4 alternative): the whole local
+    matrix factored per macro; A^T_i equals the oracle's one-layer operator, and b^, the
+    apply, the recovery and the solved Newton step equal the second-layer (default) ones."""
+    pr = CASES[case][0]()
+    P = solve.Problem(pr)
+    u, q, uh = W.random_state(pr, 8)
+    blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
+    cond = [solve.condense_second_layer(geos[e], blks[e], shift=0.3) for e in range(P.E)]
+    Nt = P.ns * P.Nth
+    out = {}
+    for layers in (1, 2):
+        ctx = lib.Context(pr, dict(precision=0, apply_mode=1, condense_layers=layers, lin_rtol=1e-13, precond=1,
+                                   restart=60, max_iters=4000))
+        ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+        b = ctx.condense(shift=0.3)
+        if layers == 1:
+            for e in (0, P.E - 1):
+                A1, _ = solve.condense_one_layer(geos[e], blks[e], shift=0.3)
+                assert rel(ctx.get_block(9, e).reshape(Nt, Nt), A1) < 1e-10
+        x = W.random_vector(P.F * P.ns * P.Nfn, 9)
+        y = ctx.apply(to_dev(x)).cpu().numpy()
+        assert rel(y, solve.apply_trace(P, cond, x)) < 1e-10
+        duh, st = ctx.linear_solve(b)
+        du, dq = ctx.recover(duh)
+        out[layers] = [t.cpu().numpy() for t in (b, duh, du, dq)]
+        ctx.close()
+    assert rel(out[1][0], solve.assemble_bhat(P, cond)) < 1e-10
+    for a, b2 in zip(out[1], out[2]):
+        assert rel2(a, b2) < 1e-10
+
+
 def test_recovery_matches_csc4(condensed2d):
     P, ctx, blks, geos, cond, bhat = condensed2d
     duh = W.random_vector(P.F * P.ns * P.Nfn, 10, 0.01)
@@ -497,14 +530,14 @@ def test_bf16_inner_operator_keeps_the_fgmres_solution(lib):
 
 # ---------------------------------------------------------------- explicit local operator (apply_mode 1)
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_explicit_local_operator_apply(lib, prec):
+@pytest.mark.parametrize("prec,tc", [(0, 0), (1, 0), (1, 4)])
+def test_explicit_local_operator_apply(lib, prec, tc):
     """apply_mode 1 forms A^T_i = B S^-1 C + D once (the one-layer form of eq. C47,
     equal to eq. ASC2a) and applies it; same operator as Algorithm 2."""
     pr = W.mms(dim=2, nmac=3, m=2, p=2)
     P = solve.Problem(pr)
     u, q, uh = W.random_state(pr, 5)
-    ctx = lib.Context(pr, dict(precision=prec, apply_mode=1))
+    ctx = lib.Context(pr, dict(precision=prec, apply_mode=1, tc_mode=tc))
     ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
     ctx.condense(shift=0.3)
     blks, geos, _, _ = solve.global_assemble(P, u, q, uh)
@@ -517,7 +550,7 @@ def test_explicit_local_operator_apply(lib, prec):
     for e in (0, 4, 8):
         A1, _ = solve.condense_one_layer(geos[e], blks[e], shift=0.3)
         eb = rel2(ctx.get_block(9, e).reshape(Nt, Nt), A1)
-        print("explicit A^T_i precision %d macro %d rel L2 %.2e (bound %.2e)" % (prec, e, eb, tol_blk))
+        print("explicit A^T_i precision %d tc %d macro %d rel L2 %.2e (bound %.2e)" % (prec, tc, e, eb, tol_blk))
         assert eb <= tol_blk
     x = W.random_vector(P.F * P.ns * P.Nfn, 9)
     ea = rel2(ctx.apply(to_dev(x)).cpu().numpy(), solve.apply_trace(P, cond, x))

@@ -54,7 +54,7 @@ def rel2(a, b):
 
 FP64 = dict(precision=0, precond=1, apply_mode=0)
 FP64SP = dict(precision=0, precond=1, apply_mode=2)      # row-compressed Algorithm 2 (the bench's FP64 form)
-MIXED = dict(precision=1, precond=1, apply_mode=1, precond_bf16=1, refine_iters=1)
+MIXED = dict(precision=1, precond=1, apply_mode=1, precond_bf16=1, refine_iters=1, tc_mode=4)   # the bench's mixed form
 CASES3D = {"tgv": lambda: W.tgv(nmac=2, m=2, p=2), "mms": lambda: W.mms(dim=3, nmac=2, m=2, p=2)}
 SHIFT = 0.5
 _oracle_cache = {}

@@ -49,3 +49,32 @@ def test_tc_gemm_tf32_matches_fp32_reference(M, N, K, batch, beta, split):
     # split (3xTF32) form drops the operand rounding to ~2^-21 (observed 3e-5 at K = 625, set by the
     # tensor-core FP32 accumulation)
     assert e < (1e-2 if split == 0 else 1e-4), e
+
+
+@pytest.mark.parametrize("M,N,K,batch,beta", [(128, 128, 32, 1, 0.0), (750, 750, 625, 2, 1.0),
+                                              (113, 77, 45, 3, 0.5), (300, 256, 200, 1, 0.0),
+                                              (64, 300, 17, 2, 1.0), (129, 257, 33, 2, 1.0)])
+def test_tc_gemm_nt_matches_fp64_reference(M, N, K, batch, beta):
+    """The swizzled K-major tcgen05 product (split TF32: three products of the hi and lo TF32
+    parts) against an FP64 product of the same FP32 inputs: the missing lo x lo term and the
+    TF32 rounding of the remainders leave about 2^-21 of the operands' scale per term, and the
+    FP32 accumulation over K adds rounding growing like sqrt(K): bound 8 sqrt(K) 2^-24 of the
+    scale sum_k |a_ik| |b_jk|.
+    Ragged M, N, K (not multiples of the 128 x BN x 32 tiles), batches and beta exercised."""
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N + K)
+    A = torch.randn(batch, M, K, generator=g).float().cuda()
+    Bt = torch.randn(batch, N, K, generator=g).float().cuda()
+    C0 = torch.randn(batch, M, N, generator=g).float().cuda()
+    C = C0.clone()
+    err = pkg.tc_gemm_nt(A, Bt, C, alpha=1.5, beta=beta)
+    torch.cuda.synchronize()
+    assert err == 0
+    ref = 1.5 * torch.bmm(A.double(), Bt.double().transpose(1, 2)) + beta * C0.double()
+    scale = (A.double().abs().bmm(Bt.double().abs().transpose(1, 2))).max().item()
+    e = (C.double() - ref).abs().max().item() / scale
+    bound = 8 * K ** 0.5 * 2.0 ** -24
+    print("tc_gemm_nt M %d N %d K %d: max error / scale %.2e (bound %.2e)" % (M, N, K, e, bound))
+    assert e < bound
