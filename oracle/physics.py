@@ -185,6 +185,49 @@ def wall_operator(uh, u, wall_T, wall_v, gamma):
     return B
 
 
+def flux_jacobian_apply(uh, du, n, gamma, delta=None):
+    """A_n(uh) du, or |A_n|_delta(uh) du when delta is given: the normal inviscid flux Jacobian
+    A_n = dF(uh).n / du applied through its eigen-decomposition (acoustic waves v_n -/+ c with
+    right eigenvectors (1, v -/+ c n, H -/+ c v_n), the remaining d waves at v_n).  A jump du
+    splits into acoustic strengths a1, a5 = (dp -/+ rho c dv_n) / (2 c^2), with dp and dv_n the
+    pressure and normal-velocity perturbations of du, and a remainder that moves at v_n.
+    |lambda|_delta = sqrt(lambda^2 + (delta c)^2): analytic, so the complex step differentiates
+    it, and nonzero where the flow is tangent to the boundary."""
+    d = len(uh) - 2
+    rho, v, E, P, T = primitives(uh, gamma)
+    c = sqrt(T)
+    H = E + P / rho
+    vn = sum(v[k] * n[k] for k in range(d))
+    ke = 0.5 * sum(v[k] * v[k] for k in range(d))
+    dp = (gamma - 1.0) * (du[d + 1] - sum(v[k] * du[1 + k] for k in range(d)) + ke * du[0])
+    dvn = (sum(du[1 + k] * n[k] for k in range(d)) - vn * du[0]) / rho
+    a1 = (dp - rho * c * dvn) / (2.0 * c * c)
+    a5 = (dp + rho * c * dvn) / (2.0 * c * c)
+    r1 = [1.0] + [v[k] - c * n[k] for k in range(d)] + [H - c * vn]
+    r5 = [1.0] + [v[k] + c * n[k] for k in range(d)] + [H + c * vn]
+    if delta is None:
+        l1, l2, l5 = vn - c, vn, vn + c
+    else:
+        dc2 = (delta * c) * (delta * c)
+        l1, l2, l5 = sqrt((vn - c) * (vn - c) + dc2), sqrt(vn * vn + dc2), sqrt((vn + c) * (vn + c) + dc2)
+    return [l2 * du[s] + (l1 - l2) * a1 * r1[s] + (l5 - l2) * a5 * r5[s] for s in range(d + 2)]
+
+
+FARFIELD_DELTA = 0.05
+
+
+def farfield_operator(uh, u, uinf, n, gamma, delta=FARFIELD_DELTA):
+    """Characteristic far-field trace operator (reading of B^ in Sec. 2.3, which gives no formula):
+    B^ = A_n^+(uh) (u - uh) - A_n^-(uh) (u_inf - uh), A_n^+- = (A_n +- |A_n|_delta) / 2: outgoing
+    characteristics of uh follow the interior state, incoming ones the free stream."""
+    d = len(uh) - 2
+    du_i = [u[s] - uh[s] for s in range(d + 2)]
+    du_o = [uinf[s] - uh[s] for s in range(d + 2)]
+    Ai, Ao = flux_jacobian_apply(uh, du_i, n, gamma), flux_jacobian_apply(uh, du_o, n, gamma)
+    Bi, Bo = flux_jacobian_apply(uh, du_i, n, gamma, delta), flux_jacobian_apply(uh, du_o, n, gamma, delta)
+    return [0.5 * (Ai[s] + Bi[s]) - 0.5 * (Ao[s] - Bo[s]) for s in range(d + 2)]
+
+
 def supg_tau(u, h, p, phys):
     """Scalar SUPG coefficient (reading of Sec. 2.3, which defines tau only by reference).
 

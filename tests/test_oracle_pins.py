@@ -232,6 +232,45 @@ def test_numerical_flux_consistency_and_dissipation(d):
 
 
 @pytest.mark.parametrize("d", [2, 3])
+def test_farfield_operator_against_eigendecomposition(d):
+    """The closed-form A_n and |A_n|_delta of the far-field operator against the flux Jacobian
+    taken by the complex step of F(u).n and decomposed by numpy.linalg.eig (independent of the
+    closed form), and the operator's defining properties: zero when u = uh = u_inf, and for a
+    constant coefficient state the trace it defines takes the outgoing characteristics of u and
+    the incoming ones of u_inf (the solution of B^ = 0 with A_n frozen is
+    |A|^-1 (A^+ u - A^- u_inf))."""
+    g = 1.4
+    rng = np.random.default_rng(d)
+    rho, v, T = 1.1, rng.uniform(-0.3, 0.3, d), 0.9
+    uh = fields.uniform_u(d, rho, v, T, g)
+    n = rng.normal(size=d)
+    n = n / np.linalg.norm(n)
+    A = np.zeros((d + 2, d + 2))
+    for j in range(d + 2):
+        x = [complex(a) for a in uh]
+        x[j] += 1j * ph.CS_H
+        F = ph.inviscid_flux(x, g)
+        A[:, j] = [np.imag(sum(F[s][k] * n[k] for k in range(d))) / ph.CS_H for s in range(d + 2)]
+    lam, V = np.linalg.eig(A)
+    lam, V = lam.real, V.real
+    c = np.sqrt(T)
+    absA = V @ np.diag(np.sqrt(lam ** 2 + (ph.FARFIELD_DELTA * c) ** 2)) @ np.linalg.inv(V)
+    du = rng.normal(size=d + 2)
+    assert np.allclose(ph.flux_jacobian_apply(list(uh), list(du), list(n), g), A @ du, rtol=1e-12, atol=1e-12)
+    assert np.allclose(ph.flux_jacobian_apply(list(uh), list(du), list(n), g, ph.FARFIELD_DELTA), absA @ du,
+                       rtol=1e-12, atol=1e-12)
+    assert np.allclose(ph.farfield_operator(list(uh), list(uh), list(uh), list(n), g), 0.0, atol=1e-15)
+    uin = uh + 0.01 * rng.normal(size=d + 2)
+    uinf = uh + 0.01 * rng.normal(size=d + 2)
+    Ap, Am = 0.5 * (A + absA), 0.5 * (A - absA)
+    ut = np.linalg.solve(absA, Ap @ uin - Am @ uinf)
+    B = lambda w: np.array([a + b for a, b in zip(Ap @ (uin - w), -(Am @ (uinf - w)))])
+    assert np.allclose(B(ut), 0.0, atol=1e-14)
+    assert np.allclose(ph.farfield_operator(list(uh), list(uin), list(uinf), list(n), g),
+                       Ap @ (uin - uh) - Am @ (uinf - uh), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
 def test_wall_operator_vanishes_on_the_wall_state(d):
     """B^ of an isothermal moving wall is zero exactly when the trace state has the
     interior density, the wall velocity and the wall temperature (ideal gas with
