@@ -64,6 +64,8 @@ def _face_eq(uh, q, u, n, bkind, bdata, phys):
         return [uh[s] - bdata["uD"][s] for s in range(len(uh))]
     if bkind == 2:   # isothermal wall
         return ph.wall_operator(uh, u, bdata["Tw"], bdata["vw"], phys["gamma"])
+    if bkind == 3:   # characteristic far field towards the free stream u_inf
+        return ph.farfield_operator(uh, u, list(bdata["uinf"]), n, phys["gamma"])
     raise ValueError(bkind)
 
 
@@ -79,7 +81,8 @@ def assemble_macro(geo, phys, u, q, uhl, tt=None, src=None, bfaces=None, want_ja
     tt     -- time term dict(coef, hist [ns, Np] or None, supg_time bool) or None
     src    -- source at volume points [ns, G] or None
     bfaces -- per local face: (kind, data); kind 0 interior/periodic,
-              1 Dirichlet (data["uD"] [ns, nfp]), 2 wall (data Tw, vw)
+              1 Dirichlet (data["uD"] [ns, nfp]), 2 wall (data Tw, vw),
+              3 far field (data["uinf"] [ns, nfp])
     Complex u, q, uhl are allowed when want_jac is False (residual only).
     """
     d = geo.d

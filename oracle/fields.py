@@ -127,3 +127,18 @@ def uniform_u(d, rho, v, T, gamma):
     """Constant conserved state from rho, v, T (gamma P = rho T)."""
     P = rho * T / gamma
     return conserved(rho, list(v[:d]), P, gamma)
+
+
+# ---- flow past a sphere: initial state (input recipe, not from the paper) ----------
+
+SHELL_BLEND = (0.6, 1.0)
+
+
+def shell_initial_u(x, rho, v, T, gamma):
+    """Free stream (rho, v, T) with the velocity scaled by a smooth step of r = |x|: zero
+    for r <= 0.6, one for r >= 1, 3 s^2 - 2 s^3 of s = (r - 0.6) / 0.4 between."""
+    r = np.sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2])
+    s = np.clip((r - SHELL_BLEND[0]) / (SHELL_BLEND[1] - SHELL_BLEND[0]), 0.0, 1.0)
+    beta = s * s * (3.0 - 2.0 * s)
+    P = rho * T / gamma
+    return conserved(rho + 0.0 * r, [v[k] * beta for k in range(3)], P + 0.0 * r, gamma)

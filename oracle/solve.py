@@ -10,7 +10,7 @@ import numpy as np
 
 from . import assemble as asm
 from . import fields
-from .space import BoxMesh, MacroGeometry
+from .space import BoxMesh, MacroGeometry, MappedMacroGeometry, ShellMesh
 
 
 # ---------------------------------------------------------------- dense LU (Remark, Sec. 3.3)
@@ -64,7 +64,8 @@ class Problem:
 
     def __init__(self, prob):
         self.prob = prob
-        self.mesh = BoxMesh(prob)
+        self.shell = int(prob.get("mesh_kind", 0)) == 1
+        self.mesh = ShellMesh(prob) if self.shell else BoxMesh(prob)
         self.d = prob["dim"]
         self.ns = self.d + 2
         self.phys = phys_of(prob)
@@ -76,6 +77,8 @@ class Problem:
         self.maps = [self.mesh.gather_map(e, self.ns) for e in range(self.E)]
 
     def geometry(self, e):
+        if self.shell:
+            return MappedMacroGeometry(self.mesh.nodes[e], self.m, self.p, self.mesh.h)
         lo, hi = self.mesh.macro_box(e)
         return MacroGeometry(lo, hi, self.m, self.p)
 
@@ -102,6 +105,9 @@ class Problem:
                 out.append((1, dict(uD=uD)))
             elif kind == 2:
                 out.append((2, dict(Tw=prob["wall_T"][bside], vw=list(prob["wall_v"][bside]))))
+            elif kind == 3:
+                uinf = np.repeat(uniform_from_par(prob)[:, None], len(fc["w"]), axis=1)
+                out.append((3, dict(uinf=uinf)))
             else:
                 raise ValueError("bad bc kind %d" % kind)
         return out
@@ -221,7 +227,8 @@ def face_blocks(P, blks):
     for e in range(P.E):
         for fl, (f, _) in enumerate(P.mesh.macro_faces(e)):
             idx = (np.arange(ns)[:, None] * Nth + fl * Nfn + np.arange(Nfn)[None, :]).ravel()
-            out[f] += blks[e]["Ahh"][np.ix_(idx, idx)]
+            loc = P.maps[e][:, fl * Nfn:(fl + 1) * Nfn].ravel() - f * ns * Nfn
+            out[f][np.ix_(loc, loc)] += blks[e]["Ahh"][np.ix_(idx, idx)]
     return out
 
 

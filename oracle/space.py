@@ -89,6 +89,12 @@ class Macro1D:
             self.xn[e * p:e * p + p + 1] = x0 + (xi + 1.0) * he / 2.0
         self.xn[0], self.xn[-1] = a, b
         self.end = [np.eye(self.n)[0:1], np.eye(self.n)[self.n - 1:self.n]]
+        # derivatives of the macro basis at the two ends of the interval
+        _, dl0 = lagrange(xi, [-1.0])
+        _, dl1 = lagrange(xi, [1.0])
+        self.end_d = [np.zeros((1, self.n)), np.zeros((1, self.n))]
+        self.end_d[0][0, 0:p + 1] = dl0[0] * (2.0 / he)
+        self.end_d[1][0, self.n - p - 1:] = dl1[0] * (2.0 / he)
 
 
 def kron_axes(mats):
@@ -230,3 +236,212 @@ class BoxMesh:
             for fl, (f, _) in enumerate(self.macro_faces(e)):
                 own[f].append((e, fl))
         return own
+
+
+class MappedMacroGeometry:
+    """Basis values, weights and faces of a macro-element mapped from [0, 1]^d.
+
+    The map is isoparametric (Sec. 2.2 spaces; the curved-macro reading): x(xi) =
+    sum_a x_a phi_a(xi) with the macro's own C0 basis, so the geometry is exactly the
+    interpolant of the node positions x_a.  At every quadrature point J[i][j] =
+    dx_i/dxi_j, the weight is the reference weight times det J, and physical
+    derivatives are d_k phi = sum_j (J^-1)[j][k] d phi / d xi_j.  On the face
+    xi_k = 0 (1) the area-weighted outward normal is -(+) det J (J^-T e_k): the
+    weight is its length and n its direction, one per face point.  The mass
+    matrix of these weights is the per-macro A_qq = I (x) M_J of a non-affine
+    macro (affine macros give back diag(J) M).  Same attributes as MacroGeometry,
+    except that each face's n is [d, points].
+    """
+
+    def __init__(self, xn, m, p, h):
+        xn = np.asarray(xn, dtype=float)
+        d = xn.shape[0]
+        self.d, self.m, self.p = d, m, p
+        ax = [Macro1D(0.0, 1.0, m, p) for _ in range(d)]
+        self.ax = ax
+        self.n1 = ax[0].n
+        self.Np = self.n1 ** d
+        self.h = h
+        Tr = [kron_axes([a.B for a in ax])]
+        for k in range(d):
+            Tr.append(kron_axes([ax[j].D if j == k else ax[j].B for j in range(d)]))
+        Tr = np.array(Tr)                                        # [d+1, G, Np], reference derivatives
+        J = np.einsum("ia,jga->gij", xn, Tr[1:])                 # J[g, i, j] = dx_i / dxi_j
+        det = np.linalg.det(J)
+        if np.any(det <= 0.0):
+            raise ValueError("mapped macro-element with non-positive Jacobian")
+        Ji = np.linalg.inv(J)                                    # Ji[g, j, i] = dxi_j / dx_i
+        T = [Tr[0]]
+        for k in range(d):
+            T.append(sum(Ji[:, j, k][:, None] * Tr[1 + j] for j in range(d)))
+        self.T = np.array(T)
+        self.detJ = det
+        self.w = kron_axes([a.w[:, None] for a in ax])[:, 0] * det
+        self.xq = xn @ Tr[0].T
+        self.xn = xn
+        self.Nfn = self.n1 ** (d - 1)
+        self.faces = []
+        for k in range(d):
+            tang = [j for j in range(d) if j != k]
+            for side in range(2):
+                phi = kron_axes([ax[j].end[side] if j == k else ax[j].B for j in range(d)])
+                psi = kron_axes([ax[j].B for j in tang]) if tang else np.ones((1, 1))
+                wref = kron_axes([ax[j].w[:, None] for j in tang])[:, 0] if tang else np.ones(1)
+                dphi = []
+                for jj in range(d):
+                    mats = []
+                    for j in range(d):
+                        if j == k:
+                            mats.append(ax[j].end_d[side] if jj == k else ax[j].end[side])
+                        else:
+                            mats.append(ax[j].D if jj == j else ax[j].B)
+                    dphi.append(kron_axes(mats))
+                Jf = np.einsum("ia,jfa->fij", xn, np.array(dphi))
+                detf = np.linalg.det(Jf)
+                Jif = np.linalg.inv(Jf)
+                nw = (1.0 if side == 1 else -1.0) * detf[:, None] * Jif[:, k, :]   # [fp, d]
+                area = np.sqrt(np.sum(nw * nw, axis=1))
+                self.faces.append(dict(k=k, side=side, phi=phi, psi=psi, w=wref * area,
+                                       n=(nw / area[:, None]).T.copy(), x=xn @ phi.T))
+        self.Nth = 2 * d * self.Nfn
+
+
+# cube-panel frames (e_n, e_1, e_2) of the cubed sphere, e_1 x e_2 = e_n, panels
+# (+x, -x, +y, -y, +z, -z)
+SHELL_FRAMES = (((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+                ((-1, 0, 0), (0, 0, 1), (0, 1, 0)),
+                ((0, 1, 0), (0, 0, 1), (1, 0, 0)),
+                ((0, -1, 0), (1, 0, 0), (0, 0, 1)),
+                ((0, 0, 1), (1, 0, 0), (0, 1, 0)),
+                ((0, 0, -1), (0, 1, 0), (1, 0, 0)))
+
+
+def shell_radius(s, r0, r1, nr, ratio):
+    """Radius at radial coordinate s in [0, nr]: layer k spans [R(k), R(k+1)], the layer
+    thicknesses grow by the factor ``ratio`` (uniform when ratio == 1)."""
+    if ratio == 1.0:
+        return r0 + (r1 - r0) * s / nr
+    return r0 + (r1 - r0) * (ratio ** s - 1.0) / (ratio ** nr - 1.0)
+
+
+class ShellMesh:
+    """Cubed-sphere O-grid of the spherical shell r0 <= |x| <= r1 (d = 3).
+
+    Macro e = ((panel nr + k) nq + j) nq + i, panel in SHELL_FRAMES order, (i, j) the
+    equiangular cell of the panel and k the radial layer.  Macro reference axes:
+    xi_0 along e_1, xi_1 along e_2, xi_2 outward.  A macro node with macro-lattice
+    coordinates (t0, t1, t2) in [0, 1]^3 sits at R(k + t2) dir / |dir| with dir = e_n +
+    tan(a) e_1 + tan(b) e_2, a = -pi/4 + (i + t0) pi / (2 nq), b likewise with (j, t1).
+    Faces are numbered in order of first appearance over (macro, local face); a face's
+    node order is that of its first owner (lexicographic in its tangential axes), the
+    second owner's nodes are matched by position.  Boundary sides: 0 the inner sphere
+    (xi_2 = 0 of layer 0), 1 the outer sphere.  SUPG length: the smaller of the first
+    layer's radial thickness and the inner cell's arc, divided by m.
+    """
+
+    def __init__(self, prob):
+        if prob["dim"] != 3:
+            raise ValueError("the shell mesh is three-dimensional")
+        self.d = 3
+        self.nq, self.nr = int(prob["shell_n"][0]), int(prob["shell_n"][1])
+        self.r0, self.r1, self.ratio = (float(x) for x in prob["shell_r"][:3])
+        self.m, self.p = prob["m"], prob["p"]
+        self.n1 = self.m * self.p + 1
+        self.Nfn = self.n1 ** 2
+        self.E = 6 * self.nq * self.nq * self.nr
+        self.h = min(shell_radius(1.0, self.r0, self.r1, self.nr, self.ratio) - self.r0,
+                     self.r0 * 0.5 * np.pi / self.nq) / self.m
+        t = Macro1D(0.0, 1.0, self.m, self.p).xn
+        self.t = t
+        n1 = self.n1
+        self.nodes = np.zeros((self.E, 3, n1 ** 3))
+        i2, i1, i0 = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+        i0, i1, i2 = i0.ravel(), i1.ravel(), i2.ravel()       # node a = i0 + n1 (i1 + n1 i2)
+        for e in range(self.E):
+            i, j, k, pan = self.macro_coords(e)
+            en, e1, e2 = (np.array(v, dtype=float) for v in SHELL_FRAMES[pan])
+            a = -0.25 * np.pi + (i + t[i0]) * 0.5 * np.pi / self.nq
+            b = -0.25 * np.pi + (j + t[i1]) * 0.5 * np.pi / self.nq
+            r = shell_radius(k + t[i2], self.r0, self.r1, self.nr, self.ratio)
+            dirs = en[:, None] + np.tan(a)[None, :] * e1[:, None] + np.tan(b)[None, :] * e2[:, None]
+            self.nodes[e] = r[None, :] * dirs / np.linalg.norm(dirs, axis=0)[None, :]
+        # local face nodes (lexicographic in the tangential axes, lower axis fastest)
+        idx = np.arange(n1 ** 3).reshape(n1, n1, n1)          # [i2, i1, i0]
+        self.fnodes = []
+        for k in range(3):
+            for side in range(2):
+                c = 0 if side == 0 else n1 - 1
+                sl = [slice(None)] * 3
+                sl[2 - k] = c
+                self.fnodes.append(idx[tuple(sl)].ravel())
+        # faces by matching node positions
+        tol = 1e-9 * self.r1
+        keys = []
+        for e in range(self.E):
+            for fl in range(6):
+                keys.append(self.nodes[e][:, self.fnodes[fl]].mean(axis=1))
+        keys = np.array(keys)
+        nloc = len(keys)
+        fid = -np.ones(nloc, dtype=np.int64)
+        self.F = 0
+        self.owners = []
+        for q_ in range(nloc):
+            if fid[q_] >= 0:
+                continue
+            dist = np.max(np.abs(keys - keys[q_][None, :]), axis=1)
+            same = np.nonzero(dist < tol)[0]
+            if len(same) > 2:
+                raise ValueError("face with more than two owners")
+            fid[same] = self.F
+            self.owners.append([(int(s) // 6, int(s) % 6) for s in same])
+            self.F += 1
+        self.fid = fid.reshape(self.E, 6)
+        # node permutation of each owner: global face node g <- local face node perm[g]
+        self.perm = np.zeros((self.E, 6, self.Nfn), dtype=np.int64)
+        for f, own in enumerate(self.owners):
+            e0, f0 = own[0]
+            x0 = self.nodes[e0][:, self.fnodes[f0]]
+            self.perm[e0, f0] = np.arange(self.Nfn)
+            for (e1_, f1_) in own[1:]:
+                x1 = self.nodes[e1_][:, self.fnodes[f1_]]
+                dd = np.max(np.abs(x0[:, :, None] - x1[:, None, :]), axis=0)   # [g0, l1]
+                match = np.argmin(dd, axis=1)
+                if np.any(dd[np.arange(self.Nfn), match] > tol) or len(set(match.tolist())) != self.Nfn:
+                    raise ValueError("face nodes of two owners do not match")
+                self.perm[e1_, f1_] = match
+
+    def macro_coords(self, e):
+        i = e % self.nq
+        r = e // self.nq
+        j = r % self.nq
+        r //= self.nq
+        k = r % self.nr
+        return i, j, k, r // self.nr
+
+    def macro_faces(self, e):
+        """Global face id and boundary side (0 inner, 1 outer, -1 interior) of local faces."""
+        i, j, k, _ = self.macro_coords(e)
+        out = []
+        for fl in range(6):
+            bside = -1
+            if fl == 4 and k == 0:
+                bside = 0
+            if fl == 5 and k == self.nr - 1:
+                bside = 1
+            out.append((int(self.fid[e, fl]), bside))
+        return out
+
+    def gather_map(self, e, ns):
+        """Indices into the flat global trace vector of the macro's local trace vector
+        (local order: species, local face, the macro's own face-node order)."""
+        g = np.zeros((ns, 6 * self.Nfn), dtype=np.int64)
+        for fl in range(6):
+            f = int(self.fid[e, fl])
+            inv = np.empty(self.Nfn, dtype=np.int64)
+            inv[self.perm[e, fl]] = np.arange(self.Nfn)       # local node -> global node
+            for s in range(ns):
+                g[s, fl * self.Nfn:(fl + 1) * self.Nfn] = (f * ns + s) * self.Nfn + inv
+        return g
+
+    def face_owners(self):
+        return [list(o) for o in self.owners]

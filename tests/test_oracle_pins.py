@@ -331,7 +331,7 @@ def _whole_residual_jacobian(P, geo, e, ue, qe, uhl, tt, src, bf, cols=None):
     return out
 
 
-@pytest.mark.parametrize("case", ["mms2d", "couette2d", "mms3d"])
+@pytest.mark.parametrize("case", ["mms2d", "couette2d", "mms3d", "sphere"])
 def test_jacobian_equals_complex_step_of_residual(case):
     """Every Newton block of eq. C312 equals the derivative of the residual (SUPG on,
     DIRK time term on), random state: catches any dropped or mis-signed term."""
@@ -339,8 +339,11 @@ def test_jacobian_equals_complex_step_of_residual(case):
         pr, e, cols = W.mms(dim=2, nmac=2, m=2, p=2), 3, None
     elif case == "couette2d":
         pr, e, cols = W.couette2d(nmac=2, m=2, p=2), 1, None
-    else:
+    elif case == "mms3d":
         pr, e = W.mms(dim=3, nmac=2, m=2, p=1), 5
+        cols = list(np.random.default_rng(0).choice(135 + 405 + 270, 36, replace=False))
+    else:   # curved macro touching the wall and the far field
+        pr, e = W.sphere(nq=2, nr=1, m=1, p=2), 5
         cols = list(np.random.default_rng(0).choice(135 + 405 + 270, 36, replace=False))
     P = solve.Problem(pr)
     u, q, uh = W.random_state(pr, 7)
@@ -433,7 +436,7 @@ def test_condense_solve_recover_equals_monolithic(small2d):
         assert np.allclose(dU[e].reshape(-1), x[o + P.d * P.ns * P.Np:o + nloc], atol=1e-10)
 
 
-@pytest.mark.parametrize("case", ["mms2d", "mms3d", "tgv3d_periodic"])
+@pytest.mark.parametrize("case", ["mms2d", "mms3d", "tgv3d_periodic", "sphere"])
 def test_face_blocks_are_the_diagonal_of_the_assembled_trace_block(case):
     """Block-Jacobi preconditioner (Sec. 4.2): the face blocks equal the diagonal blocks
     of the global A_uhuh assembled independently through the gather maps (which carry
@@ -441,7 +444,8 @@ def test_face_blocks_are_the_diagonal_of_the_assembled_trace_block(case):
     faces (HDG traces interact only through the element unknowns), and the
     preconditioner applies the exact inverse of each block."""
     pr = {"mms2d": lambda: W.mms(dim=2, nmac=3, m=2, p=2), "mms3d": lambda: W.mms(dim=3, nmac=2, m=1, p=1),
-          "tgv3d_periodic": lambda: W.tgv(nmac=2, m=1, p=1)}[case]()
+          "tgv3d_periodic": lambda: W.tgv(nmac=2, m=1, p=1),
+          "sphere": lambda: W.sphere(nq=2, nr=1, m=1, p=1)}[case]()
     P = solve.Problem(pr)
     u, q, uh = W.random_state(pr, 3)
     blks, _, _, _ = solve.global_assemble(P, u, q, uh)
@@ -765,3 +769,108 @@ def test_mlp_oracle_gradient_matches_finite_differences():
     # bf16 rounding: 8 significant bits, round to nearest even
     assert mlp.bf16_round(np.float32(1.0 + 2 ** -9))[()] == 1.0
     assert mlp.bf16_round(np.float32(1.0 + 3 * 2 ** -9))[()] == 1.0 + 2 ** -7
+
+
+# ---------------------------------------------------------------- curved macros on the cubed sphere
+
+def _uniform_trace(P, u0):
+    uh = np.zeros(P.F * P.ns * P.Nfn)
+    for f in range(P.F):
+        for s in range(P.ns):
+            uh[(f * P.ns + s) * P.Nfn:(f * P.ns + s + 1) * P.Nfn] = u0[s]
+    return uh
+
+
+def test_shell_mesh_counts_owners_and_node_matching():
+    """Cubed-sphere O-grid: E = 6 nq^2 nr macros, 6 nq^2 (nr + 1) radial plus 12 nq^2 nr
+    angular faces (brute-force count of distinct faces by position); inner and outer
+    spheres have one owner per face, every other face two, and the two owners' gather maps
+    send nodes at the same position to the same trace unknown (also across cube-panel
+    edges, where the two owners' face axes are permuted or reversed)."""
+    pr = W.sphere(nq=2, nr=2, m=1, p=2)
+    P = solve.Problem(pr)
+    assert P.E == 48 and P.F == 6 * 4 * 3 + 12 * 4 * 2 == W.sizes(pr)["F"]
+    own = P.mesh.face_owners()
+    nb = [0, 0]
+    for f, o in enumerate(own):
+        sides = [P.mesh.macro_faces(e)[fl][1] for e, fl in o]
+        if len(o) == 1:
+            assert sides[0] in (0, 1)
+            nb[sides[0]] += 1
+        else:
+            assert len(o) == 2 and sides == [-1, -1]
+    assert nb == [24, 24]
+    pos = {}
+    for e in range(P.E):
+        g = P.maps[e][0]
+        for fl in range(6):
+            for j in range(P.Nfn):
+                x = P.mesh.nodes[e][:, P.mesh.fnodes[fl][j]]
+                key = int(g[fl * P.Nfn + j])
+                if key in pos:
+                    assert np.abs(pos[key] - x).max() < 1e-12
+                else:
+                    pos[key] = x
+    assert len(pos) == P.F * P.Nfn
+    # the nodes of the inner and outer layers lie on the spheres
+    r = np.linalg.norm(P.mesh.nodes, axis=1)
+    assert np.abs(r.min() - 0.5) < 1e-14 and np.abs(r.max() - 10.0) < 1e-12
+
+
+def test_mapped_geometry_volume_and_area_converge():
+    """Isoparametric curved macros: the shell volume 4/3 pi (r1^3 - r0^3) and the inner
+    sphere's area 4 pi r0^2 from the quadrature weights converge under refinement of the
+    angular cells at least at rate 3 (degree-2 interpolation of the sphere), and the two
+    owners of every interior face see opposite area-weighted normals (watertight map)."""
+    r0, r1 = 0.5, 1.0
+    errs = []
+    for nq in (2, 4):
+        P = solve.Problem(W.sphere(nq=nq, nr=1, m=1, p=2, r0=r0, r1=r1, ratio=1.0))
+        geos = [P.geometry(e) for e in range(P.E)]
+        vol = sum(g.w.sum() for g in geos)
+        area = sum(geos[e].faces[4]["w"].sum() for e in range(P.E))
+        errs.append((abs(vol / (4.0 / 3.0 * np.pi * (r1 ** 3 - r0 ** 3)) - 1.0),
+                     abs(area / (4.0 * np.pi * r0 * r0) - 1.0)))
+        for o in P.mesh.face_owners():
+            if len(o) == 2:
+                nw = [(geos[e].faces[fl]["w"][None, :] * geos[e].faces[fl]["n"]).sum(axis=1) for e, fl in o]
+                assert np.abs(nw[0] + nw[1]).max() < 1e-13
+    for i in range(2):
+        assert errs[0][i] < 5e-3 and errs[1][i] < errs[0][i] / 8.0, errs
+
+
+@pytest.mark.parametrize("inner", [1, 3])
+def test_free_stream_preservation_on_the_sphere_mesh(inner):
+    """A uniform state (q = 0, u^ = u) on the curved shell mesh with Dirichlet or far-field
+    data equal to that state gives R_Q = R_U = R_Uh = 0 to rounding (SUPG on): the discrete
+    divergence theorem holds on the curved macros (the quadrature integrates the mapped
+    integrands of degree 3p exactly) and the far-field operator vanishes at u = u^ = u_inf."""
+    pr = W.sphere(nq=2, nr=1, m=1, p=2, inner=inner, outer=3)
+    pr["field_par"] = [1.2, 0.3, -0.1, 0.2, 1.1, 0.0, 0.0, 0.0]
+    P = solve.Problem(pr)
+    u0 = solve.uniform_from_par(pr)
+    u = np.repeat(np.repeat(u0[None, :, None], P.E, 0), P.Np, 2)
+    q = np.zeros((P.E, 3, P.ns, P.Np))
+    _, _, nrm, _ = solve.global_assemble(P, u, q, _uniform_trace(P, u0), want_jac=False)
+    assert nrm["RF"] < 1e-12, nrm
+
+
+def test_mapped_lifting_reproduces_gradients_of_linear_fields():
+    """R_Q = 0 on a curved macro (p = 1, where the quadrature is exact for the mapped
+    integrands): q_k = -M_J^-1 (G_k u + Gh_k u^) returns the exact constant gradient of
+    any linear field u = c + g.x given at the nodes and on the faces (x is in the
+    isoparametric space, so is u): pins J^-1 in the volume terms, the normals and weights of
+    the faces and the per-macro mass matrix."""
+    P = solve.Problem(W.sphere(nq=2, nr=2, m=2, p=1))
+    rng = np.random.default_rng(5)
+    for e in (0, 13, 47):
+        geo = P.geometry(e)
+        c, g = rng.uniform(-1, 1), rng.uniform(-1, 1, size=3)
+        u = c + g @ geo.xn
+        uh = np.concatenate([c + g @ geo.xn[:, P.mesh.fnodes[fl]] for fl in range(6)])
+        with np.errstate(invalid="ignore"):   # the residual of this non-physical state is unused
+            blk = asm.assemble_macro(geo, P.phys, np.repeat(u[None], P.ns, 0), np.zeros((3, P.ns, P.Np)),
+                                     np.repeat(uh[None], P.ns, 0), want_jac=False)
+        for k in range(3):
+            qk = -np.linalg.solve(blk["M"], blk["Gk"][k] @ u + blk["Ghk"][k] @ uh)
+            assert np.abs(qk - g[k]).max() < 1e-12

@@ -16,11 +16,19 @@ Workloads (all synthetic, generated from closed forms; no mesh or dataset files)
   tgv        -- periodic [0, 2pi]^3, Re = 1600 at Mach 0.1 (Re_c = 16000),
                 16^3 macros of 2^3 hexes, p = 2, DIRK3 dt = 0.05 t_c
   batched    -- 256 manufactured-solution problems with seeded m, p, amplitudes
+  sphere     -- flow past a sphere of diameter 1: cubed-sphere O-grid of the shell
+                0.5 <= r <= 10, 6 panels x 8 x 8 cells x 16 layers (layer thickness
+                ratio 1.15) of 2^3 curved hexes, p = 2; isothermal no-slip wall at
+                T = 1 on the sphere, characteristic far field at r = 10; free stream
+                rho = 1, v = (0.3, 0, 0), T = 1 (Mach 0.3), Re = 100 on the diameter
+                (Re_c = 100 / 0.3); initial state the free stream with the velocity
+                blended to zero inside r = 0.6 (smooth step over 0.6 <= r <= 1)
 """
 import numpy as np
 
-BC_NONE, BC_DIRICHLET, BC_WALL = 0, 1, 2
-FIELD_NONE, FIELD_MMS, FIELD_UNIFORM, FIELD_TGV = 0, 1, 2, 3
+BC_NONE, BC_DIRICHLET, BC_WALL, BC_FARFIELD = 0, 1, 2, 3
+FIELD_NONE, FIELD_MMS, FIELD_UNIFORM, FIELD_TGV, FIELD_SPHERE = 0, 1, 2, 3, 4
+MESH_BOX, MESH_SHELL = 0, 1
 
 
 def _base(dim, nmac, lo, hi, periodic, m, p, Re_c, Pr=0.72, gamma=1.4, supg=1):
@@ -74,11 +82,31 @@ def periodic_uniform(dim=3, nmac=2, m=2, p=2, rho=1.2, v=(0.2, -0.1, 0.05), T=0.
     return pr
 
 
+def sphere(nq=8, nr=16, m=2, p=2, r0=0.5, r1=10.0, ratio=1.15, Re=100.0, Mach=0.3, supg=1,
+           inner=BC_WALL, outer=BC_FARFIELD):
+    """Config 4: flow past a sphere on the cubed-sphere shell mesh (module docstring)."""
+    pr = _base(3, [1, 1, 1], [0.0] * 3, [1.0] * 3, [0, 0, 0], m, p, Re / Mach, supg=supg)
+    pr["mesh_kind"] = MESH_SHELL
+    pr["shell_n"] = [nq, nr]
+    pr["shell_r"] = [r0, r1, ratio]
+    pr["bc"] = [inner, outer, BC_NONE, BC_NONE, BC_NONE, BC_NONE]
+    pr["wall_T"] = [1.0] * 6
+    pr["field"] = FIELD_SPHERE
+    pr["field_par"] = [1.0, Mach, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
+    pr["name"] = "sphere"
+    return pr
+
+
 def sizes(prob):
     """Node and trace counts implied by the discrete spaces (used for array shapes)."""
     d, m, p = prob["dim"], prob["m"], prob["p"]
     n1 = m * p + 1
     Np, Nfn = n1 ** d, n1 ** (d - 1)
+    if prob.get("mesh_kind", MESH_BOX) == MESH_SHELL:
+        nq, nr = prob["shell_n"]
+        E = 6 * nq * nq * nr
+        F = 6 * nq * nq * (nr + 1) + 12 * nq * nq * nr
+        return dict(d=d, ns=d + 2, Np=Np, Nfn=Nfn, Nth=2 * d * Nfn, E=E, F=F)
     E = int(np.prod(prob["nmac"][:d]))
     F = 0
     for k in range(d):
