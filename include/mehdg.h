@@ -15,7 +15,8 @@
  *    return scalars to the host (norms, statistics) synchronise that stream.
  *
  * Data layout (one problem; E macro-elements, F macro-faces, d = dim, ns = d+2):
- *  - macro-elements are boxes; macro e = ix + nx (iy + ny iz);
+ *  - box meshes (mesh_kind MEHDG_MESH_BOX): macro-elements are boxes; macro
+ *    e = ix + nx (iy + ny iz); the shell mesh is described at MEHDG_MESH_SHELL;
  *  - Np = (m p + 1)^d C0 nodes per macro-element, lexicographic, x fastest;
  *  - Nfn = (m p + 1)^(d-1) nodes per macro-face, Nth = 2 d Nfn per macro-element;
  *  - u     [E][ns][Np]       conserved variables (rho, rho v, rho E)
@@ -50,12 +51,38 @@ extern "C" {
 #define MEHDG_BC_NONE 0      /* periodic direction (or unused) */
 #define MEHDG_BC_DIRICHLET 1 /* B^ = uhat - u_D, u_D from the problem's field */
 #define MEHDG_BC_WALL 2      /* isothermal no-slip wall at wall_T moving at wall_v */
+#define MEHDG_BC_FARFIELD 3  /* characteristic far field: B^ = A_n^+(uhat)(u - uhat) - A_n^-(uhat)
+                                (u_inf - uhat), A_n^+- = (A_n +- |A_n|_delta) / 2 with the
+                                eigenvalue magnitudes smoothed as sqrt(lambda^2 + (0.05 c)^2);
+                                u_inf is the uniform state of field_par (rho, v1, v2, v3, T).
+                                The paper's boundary operator of Sec. 2.3 leaves B^ open; this
+                                is the characteristic reading */
 
 /* closed-form fields (Dirichlet data, source term, initial state) */
 #define MEHDG_FIELD_NONE 0
 #define MEHDG_FIELD_MMS 1     /* par: rho amplitude, velocity amplitude, pressure amplitude */
 #define MEHDG_FIELD_UNIFORM 2 /* par: rho, v1, v2, v3, T */
 #define MEHDG_FIELD_TGV 3     /* par: V0 (Mach of the vortex) */
+#define MEHDG_FIELD_SPHERE 4  /* par as UNIFORM (the free stream, also the Dirichlet and far-field
+                                 state); initial state: the free stream with the velocity times
+                                 3 s^2 - 2 s^3, s = clamp((|x| - 0.6) / 0.4, 0, 1) */
+
+/* mesh kinds */
+#define MEHDG_MESH_BOX 0      /* nmac, lo, hi, periodic: a box of box macro-elements */
+#define MEHDG_MESH_SHELL 1    /* dim 3: cubed-sphere O-grid of the shell r0 <= |x| <= r1 (flow past a
+    sphere).  E = 6 nq^2 nr curved macro-elements; macro e = ((panel nr + k) nq + j) nq + i for the
+    cube panels (+x, -x, +y, -y, +z, -z) with frames (e_n, e_1, e_2) = (x, y, z), (-x, z, y),
+    (y, z, x), (-y, x, z), (z, x, y), (-z, y, x); macro reference axes xi_0 along e_1, xi_1 along
+    e_2, xi_2 outward.  The macro node with macro-lattice coordinates t in [0, 1]^3 sits at
+    R(k + t_2) dir / |dir|, dir = e_n + tan(a) e_1 + tan(b) e_2, a = -pi/4 + (i + t_0) pi / (2 nq),
+    b = -pi/4 + (j + t_1) pi / (2 nq), R(s) = r0 + (r1 - r0) (ratio^s - 1) / (ratio^nr - 1)
+    (linear when ratio == 1); the geometry inside each macro is the isoparametric interpolant of
+    its nodes (per-point Jacobians, per-macro mass matrix M_J).  Faces are numbered in order of
+    first appearance over (macro, local face); a face's node order is its first owner's
+    (lexicographic in that owner's tangential axes); the gather map of the second owner carries
+    the permutation found by matching node positions.  Boundary sides: bc[0], wall_T[0],
+    wall_v[0] for the inner sphere, bc[1] for the outer sphere.  SUPG length h = min(R(1) - r0,
+    r0 pi / (2 nq)) / m.  Supported with precision FP64, condense_layers 2 and m p <= 4. */
 
 #define MEHDG_PREC_FP64 0   /* every block and solve in FP64 */
 #define MEHDG_PREC_MIXED 1  /* FP32 blocks, TF32 tensor-core condensation and LU,
@@ -74,6 +101,9 @@ typedef struct mehdg_problem {
   int supg;           /* 1: SUPG term of eq. C38b on */
   int field;          /* MEHDG_FIELD_* */
   double field_par[8];
+  int mesh_kind;      /* MEHDG_MESH_* (0: box) */
+  int shell_n[2];     /* shell: nq cells per cube-panel edge, nr radial layers */
+  double shell_r[3];  /* shell: inner radius r0, outer radius r1, layer thickness ratio */
 } mehdg_problem;
 
 typedef struct mehdg_options {
@@ -251,7 +281,10 @@ int mehdg_get_block(mehdg_ctx* ctx, int which, int macro, double* host_out,
  * [n_macro][Nt][Nu], C [n_macro][Nu][Nt], D [n_macro][Nt][Nt]; gather [n_macro][Nt]
  * global trace index of each local trace entry; owner [n_face][2] the touching
  * (macro * 2 dim + local face) or -1; x, y global trace vectors (n_face ns Nfn),
- * x != y; stream a cudaStream_t or NULL.  All in the layouts of this header.
+ * x != y; stream a cudaStream_t or NULL.  All in the layouts of this header.  The
+ * face sum reads both owners' entries in the face's node order, so it serves meshes
+ * whose two owners of a face order its nodes alike (the box meshes); on the shell
+ * mesh use mehdg_apply_trace.
  *
  * Limits and sharing: n_macro * Nt must not exceed 4194304 (2^22) doubles, the size
  * of the fixed scratch array (32 MiB, held on every GPU that loads the library

@@ -121,6 +121,40 @@ class Problem:
                 np.zeros(self.F * self.ns * self.Nfn))
 
 
+def initial_state(P, lift=True):
+    """Initial state from the problem's closed-form field: u at the macro nodes, u^ on each face
+    from its first owner's u, q = 0 or (lift) the gradient that zeroes R_Q:
+    A_qq q = -(A_qu u + A_quh u^), i.e. M q_k = -(G_k u + Gh_k u^) per species."""
+    prob = P.prob
+    fp = prob["field_par"]
+    u = np.zeros((P.E, P.ns, P.Np))
+    for e in range(P.E):
+        x = P.geometry(e).xn
+        if prob["field"] == 1:
+            u[e] = fields.mms_u(x, fp, prob["gamma"])
+        elif prob["field"] == 3:
+            u[e] = fields.tgv_u(x, fp[0], prob["gamma"])
+        elif prob["field"] == 4:
+            u[e] = fields.shell_initial_u(x, fp[0], fp[1:4], fp[4], prob["gamma"])
+        else:
+            u[e] = uniform_from_par(prob)[:, None]
+    uh = np.zeros(P.F * P.ns * P.Nfn)
+    for f, own in enumerate(P.mesh.face_owners()):
+        e, fl = own[0]
+        g = P.maps[e][:, fl * P.Nfn:(fl + 1) * P.Nfn]          # [s, local face node] -> trace index
+        for s in range(P.ns):
+            uh[g[s]] = u[e, s, P.mesh.fnodes[fl]]
+    q = np.zeros((P.E, P.d, P.ns, P.Np))
+    if lift:
+        for e in range(P.E):
+            geo = P.geometry(e)
+            uhl = P.local_trace(e, uh)
+            b = asm.assemble_macro(geo, P.phys, u[e], q[e], uhl, want_jac=False)
+            for k in range(P.d):
+                q[e, k] = -np.linalg.solve(b["M"], b["Gk"][k] @ u[e].T + b["Ghk"][k] @ uhl.T).T
+    return u, q, uh
+
+
 # ---------------------------------------------------------------- condensation
 
 def condense_second_layer(geo, blk, shift=0.0):

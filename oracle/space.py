@@ -149,6 +149,19 @@ class MacroGeometry:
         self.Nth = 2 * d * self.Nfn
 
 
+def face_node_table(d, n1):
+    """Macro node of each local face node, per local face (-x, +x, -y, ...): the face nodes are
+    lexicographic in the face's tangential axes, the lower axis fastest."""
+    idx = np.arange(n1 ** d).reshape([n1] * d)          # [i_{d-1}, ..., i_0]
+    out = []
+    for k in range(d):
+        for side in range(2):
+            sl = [slice(None)] * d
+            sl[d - 1 - k] = 0 if side == 0 else n1 - 1
+            out.append(idx[tuple(sl)].ravel())
+    return out
+
+
 class BoxMesh:
     """Structured box mesh of macro-elements with global trace numbering."""
 
@@ -173,6 +186,7 @@ class BoxMesh:
             tot += self.npos[k] * ntan
         self.F = tot
         self.dx = (self.hi - self.lo) / np.array(self.nm)
+        self.fnodes = face_node_table(d, self.n1)
 
     def macro_index(self, idx):
         e = 0
@@ -365,15 +379,7 @@ class ShellMesh:
             r = shell_radius(k + t[i2], self.r0, self.r1, self.nr, self.ratio)
             dirs = en[:, None] + np.tan(a)[None, :] * e1[:, None] + np.tan(b)[None, :] * e2[:, None]
             self.nodes[e] = r[None, :] * dirs / np.linalg.norm(dirs, axis=0)[None, :]
-        # local face nodes (lexicographic in the tangential axes, lower axis fastest)
-        idx = np.arange(n1 ** 3).reshape(n1, n1, n1)          # [i2, i1, i0]
-        self.fnodes = []
-        for k in range(3):
-            for side in range(2):
-                c = 0 if side == 0 else n1 - 1
-                sl = [slice(None)] * 3
-                sl[2 - k] = c
-                self.fnodes.append(idx[tuple(sl)].ravel())
+        self.fnodes = face_node_table(3, n1)
         # faces by matching node positions
         tol = 1e-9 * self.r1
         keys = []

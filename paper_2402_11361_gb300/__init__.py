@@ -31,7 +31,8 @@ class Problem(ctypes.Structure):
     _fields_ = [("dim", c_int), ("m", c_int), ("p", c_int), ("nmac", c_int * 3), ("lo", c_double * 3),
                 ("hi", c_double * 3), ("periodic", c_int * 3), ("bc", c_int * 6), ("wall_T", c_double * 6),
                 ("wall_v", (c_double * 3) * 6), ("gamma", c_double), ("Re", c_double), ("Pr", c_double),
-                ("supg", c_int), ("field", c_int), ("field_par", c_double * 8)]
+                ("supg", c_int), ("field", c_int), ("field_par", c_double * 8), ("mesh_kind", c_int),
+                ("shell_n", c_int * 2), ("shell_r", c_double * 3)]
 
 
 class Options(ctypes.Structure):
@@ -137,6 +138,12 @@ def problem_struct(prob):
     s.supg, s.field = int(prob.get("supg", 0)), int(prob["field"])
     for i in range(8):
         s.field_par[i] = float(prob["field_par"][i])
+    s.mesh_kind = int(prob.get("mesh_kind", 0))
+    if s.mesh_kind == 1:
+        for i in range(2):
+            s.shell_n[i] = int(prob["shell_n"][i])
+        for i in range(3):
+            s.shell_r[i] = float(prob["shell_r"][i])
     return s
 
 

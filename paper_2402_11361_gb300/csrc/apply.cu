@@ -218,9 +218,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_apply_explicit(
   }
 }
 
-// y[f][s][j] = sum over the owners (e, fl) of slot[e][s][fl, j]
+// y[f][s][j] = sum over the owners (e, fl) of slot[e][s][fl, l], l = j or, when the owners order
+// the face nodes differently (curved meshes), l = ofn[f][o][j]
 __global__ void k_face_reduce(const double* __restrict__ slot, const int* __restrict__ owner,
-                              double* __restrict__ y, int ns, int Nfn, int Nth, int Nt, int d, long long ntr) {
+                              double* __restrict__ y, int ns, int Nfn, int Nth, int Nt, int d, long long ntr,
+                              const int* __restrict__ ofn = nullptr) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= ntr) return;
   int j = i % Nfn;
@@ -231,7 +233,8 @@ __global__ void k_face_reduce(const double* __restrict__ slot, const int* __rest
     int ow = owner[2 * f + o];
     if (ow < 0) continue;
     int e = ow / (2 * d), fl = ow % (2 * d);
-    v += slot[(size_t)e * Nt + (size_t)s * Nth + fl * Nfn + j];
+    const int l = ofn ? ofn[((size_t)2 * f + o) * Nfn + j] : j;
+    v += slot[(size_t)e * Nt + (size_t)s * Nth + fl * Nfn + l];
   }
   y[i] = v;
 }
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(256) k_recover(const T* __restrict__ S, const 
                                                  const double* __restrict__ Whk, const int* __restrict__ gather,
                                                  const double* __restrict__ duh, double* __restrict__ du,
                                                  double* __restrict__ dq, int Nu, int Nt, int Np, int Nth, int ns,
-                                                 int d) {
+                                                 int d, size_t sG, size_t sGh) {
   extern __shared__ double sm[];
   double* xg = sm;        // Nt
   double* y1 = xg + Nt;   // Nu
@@ -269,8 +272,8 @@ __global__ void __launch_bounds__(256) k_recover(const T* __restrict__ S, const 
   const int nq = d * ns * Np;
   for (int i = threadIdx.x; i < nq; i += blockDim.x) {
     int a = i % Np, s = (i / Np) % ns, k = i / (Np * ns);
-    const double* W = Wk + ((size_t)k * Np + a) * Np;
-    const double* Wh = Whk + ((size_t)k * Np + a) * Nth;
+    const double* W = Wk + e * sG + ((size_t)k * Np + a) * Np;
+    const double* Wh = Whk + e * sGh + ((size_t)k * Np + a) * Nth;
     double acc = MinvRQ[(size_t)e * nq + i];
     for (int b = 0; b < Np; ++b) acc += W[b] * y2[s * Np + b];
     for (int c = 0; c < Nth; ++c) acc += Wh[c] * xg[s * Nth + c];
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(256) k_recover_f32(const float* __restrict__ S
 
 int face_reduce(mehdg_ctx* ctx, const double* slot, double* y) {
   k_face_reduce<<<(ctx->ntr + 255) / 256, 256, 0, ctx->stream>>>(slot, ctx->owner, y, ctx->ns, ctx->Nfn, ctx->Nth,
-                                                                 ctx->Nt, ctx->d, ctx->ntr);
+                                                                 ctx->Nt, ctx->d, ctx->ntr, ctx->ofn);
   CKL();
   return MEHDG_OK;
 }
@@ -393,7 +396,10 @@ static int apply_t(mehdg_ctx* ctx, const double* x, double* y) {
 // The BF16 apply of the inner GMRES into the per-macro slots only (the face reduction is
 // left to the consumer); true when the context has that path.
 bool apply_bf16_slots_available(const mehdg_ctx* ctx) {
-  return ctx->opt.precision == MEHDG_PREC_MIXED && ctx->opt.apply_mode == 1 && ctx->Ahat16 && ctx->finv16;
+  // (the fused face sum inside the BF16 block-Jacobi product assumes both owners of a face
+  // order its nodes alike: box meshes)
+  return ctx->opt.precision == MEHDG_PREC_MIXED && ctx->opt.apply_mode == 1 && ctx->Ahat16 && ctx->finv16 &&
+         !ctx->ofn;
 }
 int apply_bf16_slots(mehdg_ctx* ctx, const double* x) {
   if (!apply_bf16_slots_available(ctx)) return ctx_fail(ctx, MEHDG_ERR_ARG, "no BF16 operator copy");
@@ -431,7 +437,7 @@ int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
   CK(cudaFuncSetAttribute(k_recover<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_recover<double><<<ctx->E, 256, smem, ctx->stream>>>(ctx->Auu, ctx->perm, ctx->Auh, ctx->gv, ctx->MinvRQ, ctx->Wk,
                                                 ctx->Whk, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np,
-                                                ctx->Nth, ctx->ns, ctx->d);
+                                                ctx->Nth, ctx->ns, ctx->d, ctx->sG, ctx->sGh);
   CKL();
   phase_end(ctx, PH_RECOVER);
   return MEHDG_OK;

@@ -45,12 +45,20 @@ __device__ __forceinline__ Tables<CT> tables(const CT* tab, int ng1, int p1) {
 // integrand (FP64 path); MODE 1 writes the Jacobian only (mixed path, CT = float:
 // the Jacobian only shapes an inexact Newton step); MODE 2 writes the residual
 // only, one thread per point, plain FP64 values (mixed path).
-template <int D, int P, class KT, class CT = double, int MODE = 0>
+//
+// MAPPED (curved macro-elements): vgeo holds per point (J^-1)[j][k] = dxi_j/dx_k, with xi the
+// macro reference coordinates in [0, 1]^d (the tables' derivatives, scaled by 2/he with he =
+// 1/m, are d/dxi), and the weight (reference weight times det J).  The interpolated gradients
+// are mapped to physical ones, and the outputs are mapped back to d/dxi test and trial
+// derivatives (K'[1+j] = sum_k J^-1[j][k] K[1+k] on both sides), so that the contraction
+// kernels stay those of the reference element.
+template <int D, int P, class KT, class CT = double, int MODE = 0, bool MAPPED = false>
 __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__ tab, Phys ph,
                                                     const CT* __restrict__ u, const CT* __restrict__ q,
                                                     const CT* __restrict__ hist, double coef, int supg_time,
                                                     const CT* __restrict__ src, KT* __restrict__ Kvol,
-                                                    double* __restrict__ rvol, int E) {
+                                                    double* __restrict__ rvol, int E,
+                                                    const double* __restrict__ vgeo = nullptr) {
   constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
   constexpr int NDIR = (MODE == 2) ? 1 : NS * (1 + D);
@@ -118,6 +126,28 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__
       }
     }
   }
+  CT Ji[D][D];
+  if constexpr (MAPPED) {
+    const double* vg = vgeo + (((size_t)e * nel + el) * NG + gq) * (D * D + 1);
+    for (int j = 0; j < D; ++j)
+      for (int k = 0; k < D; ++k) Ji[j][k] = (CT)vg[j * D + k];
+    wq = (CT)vg[D * D];
+    for (int s = 0; s < NS; ++s) {
+      CT t[D];
+      for (int k = 0; k < D; ++k) {
+        t[k] = CT(0);
+        for (int j = 0; j < D; ++j) t[k] += Ji[j][k] * GU[s][j];
+      }
+      for (int k = 0; k < D; ++k) GU[s][k] = t[k];
+      for (int jq = 0; jq < D; ++jq) {
+        for (int k = 0; k < D; ++k) {
+          t[k] = CT(0);
+          for (int j = 0; j < D; ++j) t[k] += Ji[j][k] * GQ[s][jq][j];
+        }
+        for (int k = 0; k < D; ++k) GQ[s][jq][k] = t[k];
+      }
+    }
+  }
   CT f[NS];
   for (int s = 0; s < NS; ++s) f[s] = src ? src[(((size_t)e * nel + el) * NG + gq) * NS + s] : CT(0);
 
@@ -129,7 +159,14 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__
     for (int t = 0; t < NS; ++t) {
       double* R = rvol + (((size_t)e * nel + el) * NG + gq) * NS * (D + 1) + t * (D + 1);
       R[0] = W[t] * wq;
-      for (int k = 0; k < D; ++k) R[1 + k] = V[t][k] * wq;
+      for (int k = 0; k < D; ++k) {
+        CT vk = V[t][k];
+        if constexpr (MAPPED) {
+          vk = CT(0);
+          for (int kk = 0; kk < D; ++kk) vk += Ji[k][kk] * V[t][kk];
+        }
+        R[1 + k] = vk * wq;
+      }
     }
   } else {
     typedef Dual<CT, 1> S;
@@ -147,6 +184,49 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__
     S W[NS], V[NS][D], FG[NS][D], A[D][NS][NS], tau;
     vol_integrand<D, S, CT>(Us, GUs, Qs, GQs, Ts, f, ph, supg_time, W, V, FG, A, tau);
 
+    if constexpr (MAPPED) {
+      for (int t = 0; t < NS; ++t) {
+        // physical block Kp[alpha][beta] (alpha: test value / d_k, beta: input value / d_l)
+        CT Kp[D + 1][D + 1];
+        Kp[0][0] = W[t].d[0];
+        for (int l = 0; l < D; ++l) Kp[0][1 + l] = CT(0);
+        for (int k = 0; k < D; ++k) {
+          Kp[1 + k][0] = V[t][k].d[0];
+          for (int l = 0; l < D; ++l) {
+            CT val = CT(0);
+            if (ph.supg) {
+              for (int rr = 0; rr < NS; ++rr) val += A[k][rr][t].v * FG[rr][l].d[0];
+              val *= tau.v;
+            }
+            Kp[1 + k][1 + l] = val;
+          }
+        }
+        KT* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
+        K[(0 * NS + s0) * (D + 1) + 0] = (KT)(Kp[0][0] * wq);
+        for (int j2 = 0; j2 < D; ++j2) K[(0 * NS + s0) * (D + 1) + 1 + j2] = (KT)0;
+        for (int j = 0; j < D; ++j) {
+          CT r0 = CT(0);
+          for (int k = 0; k < D; ++k) r0 += Ji[j][k] * Kp[1 + k][0];
+          K[((1 + j) * NS + s0) * (D + 1) + 0] = (KT)(r0 * wq);
+          for (int j2 = 0; j2 < D; ++j2) {
+            CT acc = CT(0);
+            for (int k = 0; k < D; ++k)
+              for (int l = 0; l < D; ++l) acc += Ji[j][k] * Kp[1 + k][1 + l] * Ji[j2][l];
+            K[((1 + j) * NS + s0) * (D + 1) + 1 + j2] = (KT)(acc * wq);
+          }
+        }
+        if (MODE == 0 && dir == 0) {
+          double* R = rvol + (((size_t)e * nel + el) * NG + gq) * NS * (D + 1) + t * (D + 1);
+          R[0] = W[t].v * wq;
+          for (int j = 0; j < D; ++j) {
+            CT acc = CT(0);
+            for (int k = 0; k < D; ++k) acc += Ji[j][k] * V[t][k].v;
+            R[1 + j] = acc * wq;
+          }
+        }
+      }
+      return;
+    }
     for (int t = 0; t < NS; ++t) {
       KT* K = Kvol + (((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG + gq) * KA;
       K[(0 * NS + s0) * (D + 1) + 0] = (KT)(W[t].d[0] * wq);
@@ -551,7 +631,8 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict_
                                                      const int* __restrict__ gather, const CT* __restrict__ uD,
                                                      const CT* __restrict__ u, const CT* __restrict__ q,
                                                      const CT* __restrict__ uh, CT* __restrict__ Kface,
-                                                     double* __restrict__ rface, int E) {
+                                                     double* __restrict__ rface, int E,
+                                                     const double* __restrict__ fgeo = nullptr) {
   constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
   constexpr int NFS = IPow<P1, D - 1>::v, NFP = IPow<NG1, D - 1>::v;
   constexpr int NDIR_K = NS * (D + 2);
@@ -601,8 +682,14 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict_
     }
   }
   double n[D];
-  for (int k = 0; k < D; ++k) n[k] = 0.0;
-  n[fl / 2] = (fl % 2) ? 1.0 : -1.0;
+  if (fgeo) {   // curved macro: unit outward normal and weight of this face point
+    const double* fg = fgeo + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * (D + 1);
+    for (int k = 0; k < D; ++k) n[k] = fg[k];
+    wf = (CT)fg[D];
+  } else {
+    for (int k = 0; k < D; ++k) n[k] = 0.0;
+    n[fl / 2] = (fl % 2) ? 1.0 : -1.0;
+  }
   const int bk = bkind[e * 2 * D + fl];
   const CT* ud = uD ? uD + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NS : nullptr;
   if constexpr (MODE == 2) {
@@ -613,6 +700,8 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict_
     } else if (bk == MEHDG_BC_WALL) {
       int bs = bside[e * 2 * D + fl];
       wall_operator<D, CT>(UHf, Uf, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+    } else if (bk == MEHDG_BC_FARFIELD) {
+      farfield_operator<D, CT, CT>(UHf, Uf, ud, n, pr.gamma, eq);
     } else {
       for (int s = 0; s < NS; ++s) eq[s] = fh[s];
     }
@@ -638,6 +727,8 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict_
     } else if (bk == MEHDG_BC_WALL) {
       int bs = bside[e * 2 * D + fl];
       wall_operator<D, S>(UHs, Us, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+    } else if (bk == MEHDG_BC_FARFIELD) {
+      farfield_operator<D, S, CT>(UHs, Us, ud, n, pr.gamma, eq);
     } else {
       for (int s = 0; s < NS; ++s) eq[s] = fh[s];
     }
@@ -747,9 +838,11 @@ __global__ void __launch_bounds__(256) k_face_contract(Geo g, const double* __re
 }
 
 // R_Q[k][s][a] = M q_k,s + G_k u_s + Gh_k uh_loc,s   (linear part of eq. C38a)
+// (M, G_k, Gh_k shared by all macro-elements, or per macro-element at strides sM, sG, sGh)
 __global__ void k_rq(Geo g, const double* __restrict__ M, const double* __restrict__ Gk,
                      const double* __restrict__ Ghk, const int* __restrict__ gather, const double* __restrict__ u,
-                     const double* __restrict__ q, const double* __restrict__ uh, double* __restrict__ RQ, int E) {
+                     const double* __restrict__ q, const double* __restrict__ uh, double* __restrict__ RQ, int E,
+                     size_t sM, size_t sG, size_t sGh) {
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long tot = (long long)E * g.d * g.ns * g.Np;
   if (tid >= tot) return;
@@ -758,9 +851,9 @@ __global__ void k_rq(Geo g, const double* __restrict__ M, const double* __restri
   int k = (tid / ((long long)g.Np * g.ns)) % g.d;
   int e = (int)(tid / ((long long)g.Np * g.ns * g.d));
   const size_t Np = g.Np;
-  const double* Mr = M + (size_t)a * Np;
-  const double* Gr = Gk + ((size_t)k * Np + a) * Np;
-  const double* Hr = Ghk + ((size_t)k * Np + a) * g.Nth;
+  const double* Mr = M + e * sM + (size_t)a * Np;
+  const double* Gr = Gk + e * sG + ((size_t)k * Np + a) * Np;
+  const double* Hr = Ghk + e * sGh + ((size_t)k * Np + a) * g.Nth;
   const double* qe = q + (((size_t)e * g.d + k) * g.ns + s) * Np;
   const double* ue = u + ((size_t)e * g.ns + s) * Np;
   const int* ge = gather + (size_t)e * g.Nt + (size_t)s * g.Nth;
@@ -814,6 +907,10 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
       const long long tot2 = (long long)E * ctx->nel * NG;
       k_vol_point<D, P, float, double, 2><<<(tot2 + 127) / 128, 128, 0, st>>>(
           g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, nullptr, ctx->rvol, E);
+      CKL();
+    } else if (ctx->mapped) {
+      k_vol_point<D, P, BT, double, 0, true><<<(tot + 127) / 128, 128, 0, st>>>(
+          g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, Kvol, ctx->rvol, E, ctx->vgeo);
       CKL();
     } else {
       k_vol_point<D, P, BT><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, hist, coef, supg_time,
@@ -869,7 +966,7 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
     } else {
       k_face_point<D, P><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, ctx->prob, ctx->bkind, ctx->bside,
                                                              ctx->fnode, ctx->gather, ctx->uD, u, q, uh,
-                                                             ctx->Kface, ctx->rface, E);
+                                                             ctx->Kface, ctx->rface, E, ctx->fgeo);
       CKL();
       k_face_contract<D, P, BT><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, ctx->Kface, ctx->rface, Auu, Auq,
                                                     Auh, Ahu, Ahq, Ahh, ctx->RU, ctx->RUh);
@@ -878,7 +975,8 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   }
   {
     long long tot = (long long)E * ctx->Nq;
-    k_rq<<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->Mref, ctx->Gk, ctx->Ghk, ctx->gather, u, q, uh, ctx->RQ, E);
+    k_rq<<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->Mref, ctx->Gk, ctx->Ghk, ctx->gather, u, q, uh, ctx->RQ, E,
+                                            ctx->sM, ctx->sG, ctx->sGh);
     CKL();
     phase_end(ctx, PH_FACES);
   }

@@ -370,7 +370,7 @@ __global__ void k_scale(T* x, long long n, double a) {
 
 // S[(s,a)][(s,b)] += shift M[a][b]
 template <class T>
-__global__ void k_mass_shift(T* S, const double* M, int Np, int ns, double shift, int E) {
+__global__ void k_mass_shift(T* S, const double* M, int Np, int ns, double shift, int E, size_t sM) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long tot = (long long)E * ns * Np * Np;
   if (i >= tot) return;
@@ -379,17 +379,20 @@ __global__ void k_mass_shift(T* S, const double* M, int Np, int ns, double shift
   int s = (i / ((long long)Np * Np)) % ns;
   int e = (int)(i / ((long long)Np * Np * ns));
   size_t Nu = (size_t)ns * Np;
-  S[(size_t)e * Nu * Nu + ((size_t)s * Np + a) * Nu + (size_t)s * Np + b] += (T)(shift * M[(size_t)a * Np + b]);
+  S[(size_t)e * Nu * Nu + ((size_t)s * Np + a) * Nu + (size_t)s * Np + b] +=
+      (T)(shift * M[e * sM + (size_t)a * Np + b]);
 }
 
-// MinvRQ[e][k][s] = M^-1 R_Q[e][k][s]
-__global__ void k_minv_rq(const double* Minv, const double* RQ, double* out, int Np, long long nvec) {
+// MinvRQ[e][k][s] = M^-1 R_Q[e][k][s]  (M^-1 shared, or per macro-element at stride sM; vpe
+// vectors per macro-element)
+__global__ void k_minv_rq(const double* Minv, const double* RQ, double* out, int Np, long long nvec, long long vpe,
+                          size_t sM) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= nvec * Np) return;
   int a = i % Np;
   long long v = i / Np;
   const double* r = RQ + v * Np;
-  const double* m = Minv + (size_t)a * Np;
+  const double* m = Minv + (size_t)(v / vpe) * sM + (size_t)a * Np;
   double s = 0.0;
   for (int b = 0; b < Np; ++b) s += m[b] * r[b];
   out[i] = s;
@@ -397,8 +400,9 @@ __global__ void k_minv_rq(const double* Minv, const double* RQ, double* out, int
 
 // face blocks of A_uhuh: sum of the owners' local blocks (before D overwrites A_uhuh)
 template <class T>
-__global__ void k_face_blocks(const T* Ahh, const int* owner, double* fblk, int ns, int Nfn, int Nth,
-                              int Nt, int d, int F) {
+// (ofn: each owner's local face node of every face node, or null when both owners share the order)
+__global__ void k_face_blocks(const T* Ahh, const int* owner, const int* ofn, double* fblk, int ns, int Nfn,
+                              int Nth, int Nt, int d, int F) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int nfb = ns * Nfn;
   if (i >= (long long)F * nfb * nfb) return;
@@ -411,7 +415,9 @@ __global__ void k_face_blocks(const T* Ahh, const int* owner, double* fblk, int 
     int ow = owner[2 * f + o];
     if (ow < 0) continue;
     int e = ow / (2 * d), fl = ow % (2 * d);
-    v += Ahh[(size_t)e * Nt * Nt + ((size_t)sr * Nth + fl * Nfn + jr) * Nt + (size_t)sc * Nth + fl * Nfn + jc];
+    const int lr = ofn ? ofn[((size_t)2 * f + o) * Nfn + jr] : jr;
+    const int lc = ofn ? ofn[((size_t)2 * f + o) * Nfn + jc] : jc;
+    v += Ahh[(size_t)e * Nt * Nt + ((size_t)sr * Nth + fl * Nfn + lr) * Nt + (size_t)sc * Nth + fl * Nfn + lc];
   }
   fblk[i] = v;
 }
@@ -594,7 +600,7 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // face blocks of A_uhuh for the preconditioner, then their LU
   {
     long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
-    k_face_blocks<T><<<(tot + 255) / 256, 256, 0, st>>>(Ahh, ctx->owner, ctx->fblk, ns, ctx->Nfn, Nth, (int)Nt, d,
+    k_face_blocks<T><<<(tot + 255) / 256, 256, 0, st>>>(Ahh, ctx->owner, ctx->ofn, ctx->fblk, ns, ctx->Nfn, Nth, (int)Nt, d,
                                                      ctx->F);
     CKL();
   }
@@ -602,7 +608,8 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // M^-1 R_Q
   {
     long long nvec = (long long)E * d * ns;
-    k_minv_rq<<<(nvec * Np + 255) / 256, 256, 0, st>>>(ctx->Minv, ctx->RQ, ctx->MinvRQ, Np, nvec);
+    k_minv_rq<<<(nvec * Np + 255) / 256, 256, 0, st>>>(ctx->Minv, ctx->RQ, ctx->MinvRQ, Np, nvec,
+                                                        (long long)d * ns, ctx->sM);
     CKL();
   }
   // g = -R_U + sum_k A_uq_k MinvRQ[k];  h = -R_Uh + sum_k A_uhq_k MinvRQ[k]  (eq. ASC2b pieces)
@@ -636,7 +643,7 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   // S, C, B, D
   if (!kron && shift != 0.0) {
     long long tot = (long long)E * ns * Np * Np;
-    k_mass_shift<T><<<(tot + 255) / 256, 256, 0, st>>>(Auu, ctx->Mref, Np, ns, shift, E);
+    k_mass_shift<T><<<(tot + 255) / 256, 256, 0, st>>>(Auu, ctx->Mref, Np, ns, shift, E, ctx->sM);
     CKL();
   }
   if (!kron) {
@@ -647,7 +654,7 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     // [S | C] -= A_uq [W | -Wh],  [B | -D] -= A_uhq [W | -Wh]  (all directions in one K)
     CondArgs<T> a{};
     a.Bc = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)ctx->Bcat32 : (const void*)ctx->Bcat);
-    a.sBe = 0; a.ldb = Np + Nth;
+    a.sBe = (long long)ctx->sB; a.ldb = Np + Nth;
     a.N = Np + Nth; a.K = d * Np; a.ns = ns; a.kdiv = Np; a.nsplit = Np;
     a.A = Auq; a.sAe = (long long)d * Nu * Nu; a.sAk = (long long)Nu * Nu; a.sAs = Np; a.lda = (int)Nu;
     a.M = (int)Nu;
@@ -852,7 +859,7 @@ int condense_one(mehdg_ctx* ctx, double shift, double* bhat) {
   int rc;
   {
     long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
-    k_face_blocks<double><<<(tot + 255) / 256, 256, 0, st>>>(ctx->Ahh, ctx->owner, ctx->fblk, ns, ctx->Nfn, Nth,
+    k_face_blocks<double><<<(tot + 255) / 256, 256, 0, st>>>(ctx->Ahh, ctx->owner, ctx->ofn, ctx->fblk, ns, ctx->Nfn, Nth,
                                                             (int)Nt, d, ctx->F);
     CKL();
   }

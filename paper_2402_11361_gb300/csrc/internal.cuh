@@ -84,6 +84,16 @@ struct mehdg_ctx {
   // [2d][n1] with Wh_k[a][(f, i)] = klift[f][a_k] when face f is normal to k and a lies on the
   // line through face node i
   double* klift = nullptr;
+  // curved (mapped) macro-elements of the shell mesh: per-point geometry, per-macro operators.
+  // Mref, Minv, Gk, Ghk, Wk, Whk and Bcat then hold one copy per macro-element at the strides
+  // below (0: one copy shared by all macro-elements, the box meshes)
+  bool mapped = false;
+  double* vgeo = nullptr;    // [E][nel][Ng][d*d + 1]: (J^-1)[j][k] = dxi_j/dx_k (xi in [0,1]^d), weight
+  double* fgeo = nullptr;    // [E][2d][nsf][nfp][d + 1]: unit outward normal, weight
+  double* xnode = nullptr;   // [E][d][Np] node positions
+  int* ofn = nullptr;        // [F][2][Nfn] owner's local face node of each face node (null: same order)
+  std::vector<int> h_ofn;
+  size_t sM = 0, sG = 0, sGh = 0, sB = 0;
   double* src = nullptr;     // [E][nel][Ng][ns] or null
   double* uD = nullptr;      // [E][2d][nsf][nfp][ns] or null
 
@@ -199,6 +209,11 @@ int linear_solve_impl(mehdg_ctx* ctx, const double* b, double* x, mehdg_solve_st
 int face_reduce(mehdg_ctx* ctx, const double* slot, double* y);
 int condense_one(mehdg_ctx* ctx, double shift, double* bhat);
 int recover_one(mehdg_ctx* ctx, const double* duh, double* du, double* dq);
+// shell mesh (curved macro-elements): host maps, device geometry, boundary data, initial state
+int shell_maps(mehdg_ctx* ctx, const std::vector<double>& t, std::vector<double>& xnode);
+int shell_geometry(mehdg_ctx* ctx, const double* dend);
+int shell_bdata(mehdg_ctx* ctx);
+int shell_init_state(mehdg_ctx* ctx, const double* du, double* u);
 int sparse_setup(mehdg_ctx* ctx);
 int sparse_pack(mehdg_ctx* ctx);
 int apply_sparse(mehdg_ctx* ctx, const double* x, double* y);

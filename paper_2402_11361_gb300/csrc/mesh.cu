@@ -305,6 +305,10 @@ __global__ void k_dirichlet(Geo g, const double* tab, mehdg_problem pr, const in
   int fl = (tid / ((long long)g.nfp * g.nsf)) % (2 * D);
   int e = (int)(tid / ((long long)g.nfp * g.nsf * 2 * D));
   double* out = uD + tid * NS;
+  if (bkind[e * 2 * D + fl] == MEHDG_BC_FARFIELD) {   // the free stream u_inf of field_par
+    field_uniform<D>(pr.field_par, pr.gamma, out);
+    return;
+  }
   if (bkind[e * 2 * D + fl] != MEHDG_BC_DIRICHLET) {
     for (int s = 0; s < NS; ++s) out[s] = 0.0;
     return;
@@ -372,7 +376,7 @@ __global__ void k_init_trace(Geo g, const int* owner, const int* fnode, const do
 
 // q = -M^-1 (G_k u + Gh_k uh_loc): the gradient that makes R_Q vanish
 __global__ void k_lift(Geo g, const double* Wk, const double* Whk, const int* gather,
-                       const double* u, const double* uh, double* q, int E) {
+                       const double* u, const double* uh, double* q, int E, size_t sG, size_t sGh) {
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long tot = (long long)E * g.d * g.ns * g.Np;
   if (tid >= tot) return;
@@ -380,8 +384,8 @@ __global__ void k_lift(Geo g, const double* Wk, const double* Whk, const int* ga
   int s = (tid / g.Np) % g.ns;
   int k = (tid / ((long long)g.Np * g.ns)) % g.d;
   int e = (int)(tid / ((long long)g.Np * g.ns * g.d));
-  const double* W = Wk + (size_t)k * g.Np * g.Np + (size_t)a * g.Np;
-  const double* Wh = Whk + (size_t)k * g.Np * g.Nth + (size_t)a * g.Nth;
+  const double* W = Wk + e * sG + (size_t)k * g.Np * g.Np + (size_t)a * g.Np;
+  const double* Wh = Whk + e * sGh + (size_t)k * g.Np * g.Nth + (size_t)a * g.Nth;
   const double* ue = u + ((size_t)e * g.ns + s) * g.Np;
   const int* ge = gather + (size_t)e * g.Nt + (size_t)s * g.Nth;
   double acc = 0.0;
@@ -453,32 +457,43 @@ static int setup(mehdg_ctx* ctx) {
   ctx->Nu = ctx->ns * ctx->Np;
   ctx->Nq = d * ctx->Nu;
   ctx->Nt = ctx->ns * ctx->Nth;
+  ctx->mapped = pr.mesh_kind == MEHDG_MESH_SHELL;
   ctx->E = 1;
   ctx->F = 0;
-  int npos[3];
-  for (int k = 0; k < d; ++k) {
-    ctx->E *= pr.nmac[k];
-    npos[k] = pr.periodic[k] ? pr.nmac[k] : pr.nmac[k] + 1;
+  int npos[3] = {1, 1, 1};
+  int goff[3] = {0, 0, 0};
+  if (ctx->mapped) {
+    // curved macros: sizes of the reference macro [0, 1]^3 (the tables then give d/dxi)
+    ctx->E = 6 * pr.shell_n[0] * pr.shell_n[0] * pr.shell_n[1];
+    const double r0 = pr.shell_r[0], r1 = pr.shell_r[1], q = pr.shell_r[2];
+    const int nr = pr.shell_n[1];
+    const double R1 = q == 1.0 ? r0 + (r1 - r0) / nr : r0 + (r1 - r0) * (q - 1.0) / (std::pow(q, (double)nr) - 1.0);
+    for (int k = 0; k < 3; ++k) { ctx->hm[k] = 1.0; ctx->he[k] = 1.0 / pr.m; }
+    ctx->h_supg = std::min(R1 - r0, r0 * M_PI / (2.0 * pr.shell_n[0])) / pr.m;
+  } else {
+    for (int k = 0; k < d; ++k) {
+      ctx->E *= pr.nmac[k];
+      npos[k] = pr.periodic[k] ? pr.nmac[k] : pr.nmac[k] + 1;
+    }
+    for (int k = 0; k < d; ++k) {
+      goff[k] = ctx->F;
+      int nt = 1;
+      for (int j = 0; j < d; ++j)
+        if (j != k) nt *= pr.nmac[j];
+      ctx->F += npos[k] * nt;
+    }
+    ctx->ntr = (long long)ctx->F * ctx->ns * ctx->Nfn;
+    double hmin = 1e300;
+    for (int k = 0; k < 3; ++k) { ctx->hm[k] = 1.0; ctx->he[k] = 1.0; }
+    for (int k = 0; k < d; ++k) {
+      ctx->hm[k] = (pr.hi[k] - pr.lo[k]) / pr.nmac[k];
+      ctx->he[k] = ctx->hm[k] / pr.m;
+      hmin = std::min(hmin, ctx->he[k]);
+    }
+    ctx->h_supg = hmin;
   }
-  int goff[3];
-  for (int k = 0; k < d; ++k) {
-    goff[k] = ctx->F;
-    int nt = 1;
-    for (int j = 0; j < d; ++j)
-      if (j != k) nt *= pr.nmac[j];
-    ctx->F += npos[k] * nt;
-  }
-  ctx->ntr = (long long)ctx->F * ctx->ns * ctx->Nfn;
   ctx->ndir_v = ctx->ns * (1 + d);
   ctx->ndir_f = ctx->ns * (d + 2);
-  double hmin = 1e300;
-  for (int k = 0; k < 3; ++k) { ctx->hm[k] = 1.0; ctx->he[k] = 1.0; }
-  for (int k = 0; k < d; ++k) {
-    ctx->hm[k] = (pr.hi[k] - pr.lo[k]) / pr.nmac[k];
-    ctx->he[k] = ctx->hm[k] / pr.m;
-    hmin = std::min(hmin, ctx->he[k]);
-  }
-  ctx->h_supg = hmin;
 
   // -- reference 1D data
   const int p = pr.p, n1 = ctx->n1, ng1 = ctx->ng1, m = pr.m;
@@ -489,6 +504,10 @@ static int setup(mehdg_ctx* ctx) {
   ctx->db1.assign(ng1 * (p + 1), 0.0);
   for (int gq = 0; gq < ng1; ++gq) lagrange_at(xl, xg[gq], &ctx->b1[gq * (p + 1)], &ctx->db1[gq * (p + 1)]);
   ctx->gw = wg;
+  // derivatives of the sub-element basis at xi = -1 and +1 (face Jacobians of curved macros)
+  std::vector<double> dend(2 * (p + 1)), lend(p + 1);
+  lagrange_at(xl, -1.0, lend.data(), dend.data());
+  lagrange_at(xl, 1.0, lend.data(), dend.data() + (p + 1));
 
   // -- 1D macro matrices per axis: mass M1, C1[i][j] = int dphi_i phi_j, node coordinates
   std::vector<std::vector<double>> M1(d), C1(d), iM1(d), xn1(d);
@@ -616,14 +635,22 @@ static int setup(mehdg_ctx* ctx) {
       }
     if (!(werr <= 1e-12 * wmax && herr <= 1e-12 * hmax)) klift.clear();
   }
+  if (ctx->mapped) klift.clear();   // per-macro (non-Kronecker) liftings on curved macros
 
   // -- maps
+  std::vector<double> xnode_h;
+  if (ctx->mapped) {
+    int r_ = shell_maps(ctx, xn1[0], xnode_h);
+    if (r_) return r_;
+  }
   const int E = ctx->E, F = ctx->F, ns = ctx->ns, Nt = ctx->Nt;
+  if (!ctx->mapped) {
   ctx->h_gather.assign((size_t)E * Nt, 0);
   ctx->h_owner.assign(2 * F, -1);
   ctx->h_bkind.assign(E * 2 * d, 0);
   ctx->h_bside.assign(E * 2 * d, -1);
-  for (int e = 0; e < E; ++e) {
+  }
+  for (int e = 0; e < E && !ctx->mapped; ++e) {
     int idx[3] = {0, 0, 0}, ee = e;
     for (int k = 0; k < d; ++k) { idx[k] = ee % pr.nmac[k]; ee /= pr.nmac[k]; }
     for (int k = 0; k < d; ++k)
@@ -660,13 +687,21 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->bkind, E * 2 * d);
   ALLOC(ctx->bside, E * 2 * d);
   ALLOC(ctx->fnode, 2 * d * Nfn);
-  ALLOC(ctx->tab, 2 * ng1 * (p + 1) + 2 * ng1 + d * n1);
-  ALLOC(ctx->Mref, (size_t)Np * Np);
-  ALLOC(ctx->Minv, (size_t)Np * Np);
-  ALLOC(ctx->Gk, (size_t)d * Np * Np);
-  ALLOC(ctx->Ghk, (size_t)d * Np * Nth);
-  ALLOC(ctx->Wk, (size_t)d * Np * Np);
-  ALLOC(ctx->Whk, (size_t)d * Np * Nth);
+  ALLOC(ctx->tab, 2 * ng1 * (p + 1) + 2 * ng1 + d * n1 + 2 * (p + 1));
+  // geometric operators: one copy, or one per curved macro-element
+  const size_t nge = ctx->mapped ? (size_t)E : 1;
+  if (ctx->mapped) {
+    ctx->sM = (size_t)Np * Np;
+    ctx->sG = (size_t)d * Np * Np;
+    ctx->sGh = (size_t)d * Np * Nth;
+    ctx->sB = (size_t)d * Np * (Np + Nth);
+  }
+  ALLOC(ctx->Mref, nge * Np * Np);
+  ALLOC(ctx->Minv, nge * Np * Np);
+  ALLOC(ctx->Gk, nge * d * Np * Np);
+  ALLOC(ctx->Ghk, nge * d * Np * Nth);
+  ALLOC(ctx->Wk, nge * d * Np * Np);
+  ALLOC(ctx->Whk, nge * d * Np * Nth);
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(ctx->gather, ctx->h_gather.data(), sizeof(int) * E * Nt, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->owner, ctx->h_owner.data(), sizeof(int) * 2 * F, cudaMemcpyHostToDevice, st));
@@ -679,18 +714,33 @@ static int setup(mehdg_ctx* ctx) {
   tab.insert(tab.end(), wg.begin(), wg.end());
   tab.insert(tab.end(), xg.begin(), xg.end());
   for (int k = 0; k < d; ++k) tab.insert(tab.end(), xn1[k].begin(), xn1[k].end());
+  const size_t dend_off = tab.size();
+  tab.insert(tab.end(), dend.begin(), dend.end());
   CK(cudaMemcpyAsync(ctx->tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+  if (ctx->mapped) {
+    ALLOC(ctx->ofn, ctx->h_ofn.size());
+    CK(cudaMemcpyAsync(ctx->ofn, ctx->h_ofn.data(), sizeof(int) * ctx->h_ofn.size(), cudaMemcpyHostToDevice, st));
+    ALLOC(ctx->xnode, xnode_h.size());
+    CK(cudaMemcpyAsync(ctx->xnode, xnode_h.data(), sizeof(double) * xnode_h.size(), cudaMemcpyHostToDevice, st));
+    ALLOC(ctx->vgeo, (size_t)E * ctx->nel * ctx->Ng * (d * d + 1));
+    ALLOC(ctx->fgeo, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * (d + 1));
+    ALLOC(ctx->dflag, 16);
+    ALLOC(ctx->Bcat, (size_t)E * ctx->sB);
+    int r_ = shell_geometry(ctx, ctx->tab + dend_off);
+    if (r_) return r_;
+  } else {
   CK(cudaMemcpyAsync(ctx->Mref, Mref.data(), sizeof(double) * Np * Np, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Minv, Minv.data(), sizeof(double) * Np * Np, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Gk, Gk.data(), sizeof(double) * d * Np * Np, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Ghk, Ghk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Wk, Wk.data(), sizeof(double) * d * Np * Np, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->Whk, Whk.data(), sizeof(double) * d * Np * Nth, cudaMemcpyHostToDevice, st));
+  }
   if (!klift.empty()) {
     ALLOC(ctx->klift, klift.size());
     CK(cudaMemcpyAsync(ctx->klift, klift.data(), sizeof(double) * klift.size(), cudaMemcpyHostToDevice, st));
   }
-  {
+  if (!ctx->mapped) {
     // right factor of the fused condensation GEMM: [W_1 | -Wh_1; ...; W_d | -Wh_d], [d*Np][Np+Nth]
     const int nc = Np + Nth;
     std::vector<double> bc((size_t)d * Np * nc);
@@ -739,7 +789,7 @@ static int setup(mehdg_ctx* ctx) {
   ctx->nfb = ns * Nfn;
   ALLOC(ctx->fblk, (size_t)F * ctx->nfb * ctx->nfb);
   ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
-  ALLOC(ctx->dflag, 16);
+  if (!ctx->dflag) ALLOC(ctx->dflag, 16);
   ALLOC(ctx->dred, 1 << 17);
   CK(cudaMemsetAsync(ctx->dred, 0, sizeof(double) << 17, st));   // reduction tickets start at zero
   CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * 256));
@@ -822,8 +872,14 @@ static int setup(mehdg_ctx* ctx) {
     long long tot = (long long)E * 2 * d * ctx->nsf * ctx->nfp;
     ALLOC(ctx->uD, tot * ns);
     int bs = 128;
-    if (d == 2) k_dirichlet<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
-    else k_dirichlet<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
+    if (ctx->mapped) {
+      int r_ = shell_bdata(ctx);
+      if (r_) return r_;
+    } else if (d == 2) {
+      k_dirichlet<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
+    } else {
+      k_dirichlet<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->tab, pr, ctx->bkind, ctx->uD);
+    }
     CKL();
     if (ctx->opt.precision == MEHDG_PREC_MIXED) {
       ALLOC(ctx->uD32, tot * ns);
@@ -859,8 +915,20 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
   if (nprob != 1) return MEHDG_ERR_ARG;
   const mehdg_problem& pr = prob[0];
   if (pr.dim < 2 || pr.dim > 3 || pr.m < 1 || pr.p < 1 || pr.p > 3 || pr.m * pr.p > 12) return MEHDG_ERR_ARG;
-  for (int k = 0; k < pr.dim; ++k)
-    if (pr.nmac[k] < 1 || !(pr.hi[k] > pr.lo[k])) return MEHDG_ERR_ARG;
+  if (pr.mesh_kind == MEHDG_MESH_SHELL) {
+    // curved macros: FP64, second-layer condensation, per-macro M_J^-1 in shared memory (m p <= 4)
+    if (pr.dim != 3 || pr.m * pr.p > 4 || pr.shell_n[0] < 1 || pr.shell_n[1] < 1 || !(pr.shell_r[0] > 0.0) ||
+        !(pr.shell_r[1] > pr.shell_r[0]) || !(pr.shell_r[2] > 0.0))
+      return MEHDG_ERR_ARG;
+    if (pr.field != MEHDG_FIELD_UNIFORM && pr.field != MEHDG_FIELD_SPHERE) return MEHDG_ERR_ARG;
+    for (int b = 0; b < 2; ++b)
+      if (pr.bc[b] < MEHDG_BC_DIRICHLET || pr.bc[b] > MEHDG_BC_FARFIELD) return MEHDG_ERR_ARG;
+    if (opt && (opt->precision != MEHDG_PREC_FP64 || opt->condense_layers == 1)) return MEHDG_ERR_ARG;
+  } else {
+    if (pr.mesh_kind != MEHDG_MESH_BOX) return MEHDG_ERR_ARG;
+    for (int k = 0; k < pr.dim; ++k)
+      if (pr.nmac[k] < 1 || !(pr.hi[k] > pr.lo[k])) return MEHDG_ERR_ARG;
+  }
   if (!(pr.gamma > 1.0) || !(pr.Re > 0.0) || !(pr.Pr > 0.0)) return MEHDG_ERR_ARG;
   if (opt && (opt->solver < 0 || opt->solver > 1 || opt->precond < 0 || opt->precond > 2 || opt->apply_mode < 0 ||
               opt->apply_mode > 2))
@@ -904,14 +972,20 @@ extern "C" int mehdg_init_state(mehdg_ctx* ctx, const double* du, const double* 
   const double* xnode1 = ctx->tab + 2 * ctx->ng1 * (ctx->p + 1) + 2 * ctx->ng1;
   long long tot = (long long)ctx->E * ctx->Np;
   int bs = 128;
-  if (ctx->d == 2) k_init_state<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
-  else k_init_state<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
-  CKL();
+  if (ctx->mapped) {
+    int r_ = shell_init_state(ctx, du, u);
+    if (r_) return r_;
+  } else {
+    if (ctx->d == 2) k_init_state<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
+    else k_init_state<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
+    CKL();
+  }
   k_init_trace<<<(ctx->ntr + bs - 1) / bs, bs, 0, st>>>(g, ctx->owner, ctx->fnode, u, duh, uh, ctx->F);
   CKL();
   long long nq = (long long)ctx->E * ctx->Nq;
   if (lift) {
-    k_lift<<<(nq + bs - 1) / bs, bs, 0, st>>>(g, ctx->Wk, ctx->Whk, ctx->gather, u, uh, q, ctx->E);
+    k_lift<<<(nq + bs - 1) / bs, bs, 0, st>>>(g, ctx->Wk, ctx->Whk, ctx->gather, u, uh, q, ctx->E, ctx->sG,
+                                              ctx->sGh);
     CKL();
   } else {
     CK(cudaMemsetAsync(q, 0, sizeof(double) * nq, st));
@@ -994,7 +1068,8 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->V, ctx->Zk, ctx->wv, ctx->tv, ctx->tv2, ctx->rv, ctx->iV, ctx->iw, ctx->un,
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
-                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->Aloc, ctx->Rloc, ctx->Xloc, ctx->permL, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16};
+                  ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->Aloc, ctx->Rloc, ctx->Xloc, ctx->permL, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16,
+                  ctx->vgeo, ctx->fgeo, ctx->xnode, ctx->ofn};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);

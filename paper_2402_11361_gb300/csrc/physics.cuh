@@ -120,6 +120,65 @@ HD void wall_operator(const T* uh, const T* u, double Tw, const double* vw, doub
   out[D + 1] = uh[D + 1] - uh[0] * (ew + 0.5 * kw);
 }
 
+// characteristic far field towards the uniform state uinf:
+//   B^ = A_n^+(uh) (u - uh) - A_n^-(uh) (uinf - uh),  A_n^+- = (A_n +- |A_n|_delta) / 2,
+// A_n = d(F(uh) n)/du.  A jump w splits into the two acoustic waves (speeds v_n -/+ c, right
+// eigenvectors (1, v -/+ c n, H -/+ c v_n), strengths (dp -/+ rho c dv_n) / (2 c^2) with dp and
+// dv_n the pressure and normal-velocity perturbations of w) and a remainder moving at v_n.
+// |lambda|_delta = sqrt(lambda^2 + (0.05 c)^2) keeps the operator smooth (and invertible where
+// the flow is tangent to the boundary).
+template <int D, class T, class U>
+HD void farfield_operator(const T* uh, const T* u, const U* uinf, const double* n, double g, T* out) {
+  const double delta = 0.05;
+  T rho, v[D], E, P, Tt;
+  primitives<D, T>(uh, g, rho, v, E, P, Tt);
+  T c = dsqrt(Tt);
+  T H = E + P / rho;
+  T vn = v[0] * n[0], ke = v[0] * v[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) {
+    vn = vn + v[k] * n[k];
+    ke = ke + v[k] * v[k];
+  }
+  ke = 0.5 * ke;
+  T dc2 = (delta * c) * (delta * c);
+  T lam[3] = {vn - c, vn, vn + c};
+  T lp[3], lm[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T a = dsqrt(lam[i] * lam[i] + dc2);
+    lp[i] = 0.5 * (lam[i] + a);
+    lm[i] = 0.5 * (lam[i] - a);
+  }
+#pragma unroll
+  for (int s = 0; s < D + 2; ++s) out[s] = zero<T>();
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    T w[D + 2];
+#pragma unroll
+    for (int s = 0; s < D + 2; ++s) w[s] = side == 0 ? u[s] - uh[s] : (double)uinf[s] - uh[s];
+    T mw = w[1] * v[0], nw = w[1] * n[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+      mw = mw + w[1 + k] * v[k];
+      nw = nw + w[1 + k] * n[k];
+    }
+    T dp = (g - 1.0) * (w[D + 1] - mw + ke * w[0]);
+    T dvn = (nw - vn * w[0]) / rho;
+    T i2c2 = 0.5 / Tt;
+    T s1 = (dp - rho * c * dvn) * i2c2, s5 = (dp + rho * c * dvn) * i2c2;
+    const T* L = side == 0 ? lp : lm;
+    T c1 = (L[0] - L[1]) * s1, c5 = (L[2] - L[1]) * s5;
+    T r[D + 2];
+    r[0] = L[1] * w[0] + c1 + c5;
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[1 + k] = L[1] * w[1 + k] + c1 * (v[k] - c * n[k]) + c5 * (v[k] + c * n[k]);
+    r[D + 1] = L[1] * w[D + 1] + c1 * (H - c * vn) + c5 * (H + c * vn);
+#pragma unroll
+    for (int s = 0; s < D + 2; ++s) out[s] = side == 0 ? out[s] + r[s] : out[s] - r[s];
+  }
+}
+
 // scalar tau_SUPG = ((2 (|v|+c) p/h)^2 + (4 p^2 /(Re rho h^2))^2)^(-1/2)
 template <int D, class T>
 HD T supg_tau(const T* u, const Phys& ph) {
