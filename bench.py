@@ -41,13 +41,17 @@ UNIT = "s/Newton step"
 UNIT_TGV = "s/Newton step"
 WORKLOAD_TGV = ("3D Taylor-Green vortex, periodic [0,2pi]^3, Re 1600, M0 0.1, %d^3 macro-elements x 2^3 hexes, "
                 "p=2 (%d^3 = %d macros, Nu=625, Nt=750, %d trace DOFs), DIRK3 dt = 0.05 t_c, Newton steps")
+WORKLOAD_SPHERE = ("flow past a sphere, Re 100, Mach 0.3: cubed-sphere shell 0.5 <= r <= 10, 6 x %d^2 x %d curved "
+                   "macro-elements (layer ratio 1.15) x 2^3 hexes, p=2 (%d macros, Nu=625, Nt=750, %d trace DOFs), "
+                   "isothermal wall + characteristic far field, DIRK3 dt = 0.1 (acoustic units) from the blended "
+                   "free stream, Newton steps")
 
 
 NMAC = 8
 
-# DRAM bytes (read + write) per macro-element and launch of the apply kernels, from ncu
-# captures of the 6^3 case (216 macros; profiles/k_apply_explicit_mms3d_6cubed.md),
-# scaled by the macro count; keyed by (phase, precision, apply_mode).  A kernel without
+# DRAM bytes (read + write) per macro-element and launch of the apply kernels, from an ncu
+# capture of the 6^3 manufactured-solution cube (216 macros), scaled by the macro count;
+# keyed by (phase, precision, apply_mode).  A kernel without
 # a capture of its current version has no entry (its traffic is reported as null).
 TRAFFIC_PER_MACRO = {("apply", "mixed", 1): (489.032960e6 + 4.069632e6) / 216}
 
@@ -568,9 +572,10 @@ def sf_contract_macs(d, p):
     return macs
 
 
-def kernel_work(z, precision, apply_mode):
+def kernel_work(z, precision, apply_mode, mapped=False):
     """Algorithmic work of one execution of each phase over all E macro-elements:
-    (kind, amount, kernel name).  kind "flop" or "byte"."""
+    (kind, amount, kernel name).  kind "flop" or "byte".  mapped: curved macro-elements, whose
+    per-macro liftings are dense (the condensation is the dense product k_cond_gemm)."""
     E, Nu, Nt, Np, Nth, d, ns = z["E"], z["Nu"], z["Nt"], z["Np"], z["Nth"], z["d"], z["ns"]
     n1 = round(Np ** (1.0 / d))
     p_, m_ = (n1 - 1) // 2, 2
@@ -587,6 +592,8 @@ def kernel_work(z, precision, apply_mode):
     # Kronecker condensation: n1 terms per direction for each S/B entry, n1 for each C/D entry,
     # plus the rhs product over the row of A_.q
     kron = 2.0 * (Nu + Nt) * (Nu * d * n1 + Nt * n1 + d * Nu) * E
+    # dense condensation: [S | C] and [B | D] updated by A_.q [W_k | -Wh_k], per species
+    dense = 2.0 * (Nu + Nt) * d * Np * (Np + Nth) * ns * E
     if apply_mode == 1:
         apply = ("byte", (w * Nt * Nt + (8 + 8 + 4) * Nt) * E, "k_apply_explicit")
     else:
@@ -594,16 +601,16 @@ def kernel_work(z, precision, apply_mode):
                  (w * (2 * Nu * Nt + Nt * Nt + Nu * Nu) + 20 * Nt + 4 * Nu) * E if precision != "fp64"
                  else 2.0 * (2 * Nu * Nt + Nt * Nt + Nu * Nu) * E, "k_apply (Algorithm 2)")
     return {"vol_contract": ("flop", vc, "k_vol_contract"),
-            "cond_gemm": ("flop", kron, "k_cond_kron"),
+            "cond_gemm": ("flop", dense, "k_cond_gemm") if mapped else ("flop", kron, "k_cond_kron"),
             "lu": ("flop", (2.0 / 3.0) * Nu ** 3 * E, "k_lu_panel_smem / k_lu_batched"),
             "trsm": ("flop", 2.0 * Nu * Nu * Nt * E, "k_lu_solve_multi"),
             "apply": apply,
             "apply_bf16": ("byte", (2 * Nt * Nt + 20 * Nt) * E, "k_apply_explicit_bf16 (inner GMRES)")}
 
 
-def roofline_of(stats, steps, z, precision, apply_mode, peaks, gp):
+def roofline_of(stats, steps, z, precision, apply_mode, peaks, gp, mapped=False):
     """Roofline of the kernel with the largest summed device time over the timed steps."""
-    work = kernel_work(z, precision, apply_mode)
+    work = kernel_work(z, precision, apply_mode, mapped)
     per_step = {k: v[0] / steps for k, v in stats.items() if v[1] > 0}
     cand = {k: v for k, v in per_step.items() if k in work}
     if not cand:
@@ -791,6 +798,108 @@ def run_tgv(args, ws, rank, lrank):
         "clocks": clocks,
     }
     return line
+
+
+def run_sphere(args, ws, rank, lrank):
+    """Flow past a sphere on curved macro-elements (the cubed-sphere shell): Newton steps of the
+    DIRK3 integration from the blended free stream.  Plain FP64 form (default, --precision fp64):
+    dense Algorithm-2 apply (the per-macro liftings fill B, C and D), 6 x 8^2 x 12 macros by
+    default, because the configuration's 6 x 8^2 x 16 = 6144 macros need about 285 GB of FP64
+    blocks and workspace, more than the device holds.  Mixed form (--precision mixed): FP32
+    blocks, stored A^T_i."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+
+    dev = torch.device("cuda:%d" % lrank)
+    torch.cuda.set_device(dev)
+    fp64 = args.precision == "fp64"
+    nr = args.sphere_nr or 12
+    pr = W.sphere(nq=args.sphere_nq, nr=nr)
+    z = sizes(pr)
+    dt = 0.1
+    opt = dict(precision=pkg.PREC_FP64, precond=1, apply_mode=args.sphere_apply_mode, restart=args.restart,
+               max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, newton_atol=1e-14, max_newton=60,
+               inner_iters=args.inner)
+    if not fp64:
+        opt.update(precision=pkg.PREC_MIXED, apply_mode=1, tc_mode=args.tc_mode, refine_iters=args.refine,
+                   precond_bf16=args.precond_bf16)
+    st = torch.cuda.current_stream(dev)
+    peaks = measured_peaks()
+    gp = gemm_peaks(torch) if rank == 0 else {}
+    ctx = pkg.Context(pr, opt, device=dev)
+    u, q, uh = ctx.init_state(None, None, lift=True)
+    drv = StepDriver(ctx, dt)
+    for _ in range(args.warmup):
+        drv.step(u, q, uh)
+    torch.cuda.synchronize()
+    rank_barrier(ws)
+    K = max(1, args.steps)
+    ctx.phase_stats(reset=True)
+    f0 = drv.fgmres
+    clk = ClockSampler(lrank)
+    clk.start()
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    for _ in range(K):
+        drv.step(u, q, uh)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    t_dev = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    clocks = clk.stop()
+    launches = ctx.launch_count() - l0
+    stats = ctx.phase_stats()
+    its = drv.fgmres - f0
+    rank_barrier(ws)
+    n_e2e = max(1, min(K, args.e2e_steps))
+    hu, hq, huh = (x.cpu().pin_memory() for x in (u, q, uh))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n_e2e):
+        u.copy_(hu, non_blocking=True)
+        q.copy_(hq, non_blocking=True)
+        uh.copy_(huh, non_blocking=True)
+        drv.step(u, q, uh)
+        hu.copy_(u, non_blocking=True)
+        hq.copy_(q, non_blocking=True)
+        huh.copy_(uh, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, ws, dev)
+    bytes_io = 8 * (u.numel() + q.numel() + uh.numel())
+    bytes_dev = ctx.info["bytes_device"]
+    ctx.close()
+    roof, per_step = roofline_of(stats, K, z, args.precision, opt["apply_mode"], peaks, gp, mapped=True)
+    lu_tf = None
+    if stats.get("lu", (0, 0))[1]:
+        lu_tf = kernel_work(z, args.precision, 0)["lu"][1] / (stats["lu"][0] / stats["lu"][1] / 1e3) / 1e12
+    per = t_dev / K
+    return {
+        "metric": METRIC, "value": replica_value(per, ws), "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
+        "dtype_detail": "f64 throughout" if fp64 else MIXED_DETAIL,
+        "data": "synthetic (free stream blended to rest near the sphere; closed form)",
+        "config": {"workload": WORKLOAD_SPHERE % (args.sphere_nq, nr, z["E"], z["F"] * z["ns"] * z["Nfn"]),
+                   "precision": args.precision, "newton_rtol": 1e-8, "precond": 1, "lin_rtol": args.lin_rtol,
+                   "restart": args.restart, "inner_iters": args.inner, "apply_mode": opt["apply_mode"],
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 GPU",
+                   "bytes_device": bytes_dev},
+        "fgmres_iters_per_step": its / K,
+        "batched_lu_tflops": lu_tf,
+        "primary_run": dict(dirk_steps=drv.dirk_steps, newton_steps=drv.newton, fgmres_iters=drv.fgmres),
+        "phase_ms_per_step": per_step,
+        "phase_launches_per_step": {k: stats[k][1] / K for k in stats if stats[k][1]},
+        "gemm_peaks_tflops": gp,
+        "e2e": {"value": replica_value(t_e2e / n_e2e, ws), "unit": UNIT, "steps": n_e2e,
+                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+    }
 
 
 def run_layers(args, ws, rank, lrank):
@@ -1123,7 +1232,7 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (default: 10 Newton steps for tgv)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched", "layers"],
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched", "layers", "sphere"],
                     help="tgv: Newton steps of the 16^3 Taylor-Green DIRK integration (default, the headline); "
                          "mms: steady 3D manufactured solution (8^3); batched: independent uneven problems")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
@@ -1160,9 +1269,13 @@ def main():
     ap.add_argument("--batch-mem-gb", type=float, default=200.0)
     ap.add_argument("--nmac-tgv", type=int, default=16, help="TGV macro-elements per edge (16 = the config)")
     ap.add_argument("--nmac-layers", type=int, default=8, help="layers workload: macro-elements per cube edge")
+    ap.add_argument("--sphere-nq", type=int, default=8, help="sphere workload: cells per cube-panel edge")
+    ap.add_argument("--sphere-nr", type=int, default=0, help="sphere workload: radial layers (default 12)")
+    ap.add_argument("--sphere-apply-mode", type=int, default=0,
+                    help="sphere workload, FP64 form: 0 dense Algorithm 2 (default)")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "fp64" if args.workload == "tgv" else "mixed"
+        args.precision = "fp64" if args.workload in ("tgv", "sphere") else "mixed"
     global NMAC
     NMAC = args.nmac
     ws, rank, lrank = dist_env()
@@ -1174,9 +1287,9 @@ def main():
     if ws > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("tgv", "batched", "layers"):
+    if args.workload in ("tgv", "batched", "layers", "sphere"):
         args.steps = args.steps or 10
-        run = {"tgv": run_tgv, "batched": run_batched, "layers": run_layers}[args.workload]
+        run = {"tgv": run_tgv, "batched": run_batched, "layers": run_layers, "sphere": run_sphere}[args.workload]
         line = run(args, ws, rank, lrank)
         if rank == 0:
             if args.workload == "tgv" and args.cpu and ws == 1:   # the oracle baseline, N = 1 only

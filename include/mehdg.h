@@ -82,7 +82,7 @@ extern "C" {
     (lexicographic in that owner's tangential axes); the gather map of the second owner carries
     the permutation found by matching node positions.  Boundary sides: bc[0], wall_T[0],
     wall_v[0] for the inner sphere, bc[1] for the outer sphere.  SUPG length h = min(R(1) - r0,
-    r0 pi / (2 nq)) / m.  Supported with precision FP64, condense_layers 2 and m p <= 4. */
+    r0 pi / (2 nq)) / m.  Supported with condense_layers 2, tc_mode 0, 1, 4 or 5 and m p <= 4. */
 
 #define MEHDG_PREC_FP64 0   /* every block and solve in FP64 */
 #define MEHDG_PREC_MIXED 1  /* FP32 blocks, TF32 tensor-core condensation and LU,

@@ -17,7 +17,8 @@ Conventions (Sec. 2.1, eqs. C4-C6):
 Every function works on Python lists of "scalars": numpy arrays (real or complex,
 any shape) or the forward-mode ``Dual`` below, so that the same expressions can
 be differentiated twice (Dual inside, complex step outside).  |x| is written so
-that its derivative is sign(x) with sign(0) = 0.
+that its derivative is sign(x) with sign(0) = 0; likewise the speed |v| = sqrt(v.v)
+has derivative v/|v| and 0 at v = 0 (sqrt0).
 """
 import numpy as np
 
@@ -71,6 +72,19 @@ def sqrt(x):
         s = np.sqrt(x.v)
         return Dual(s, x.d / (2.0 * s))
     return np.sqrt(x)
+
+
+def sqrt0(x):
+    """sqrt of a sum of squares x = v.v with derivative 0 where x vanishes: the magnitude |v|
+    at v = 0 (not differentiable there) takes the derivative 0, as |x| does at x = 0.  Under
+    the complex step at v = 0, x = -(h dv)^2 has a non-positive real part, and the result is 0."""
+    if isinstance(x, Dual):
+        s = sqrt0(x.v)
+        pos = np.real(x.v) > 0.0
+        return Dual(s, np.where(pos, x.d / (2.0 * np.where(pos, s, 1.0)), 0.0 * x.d))
+    x = np.asarray(x)
+    pos = np.real(x) > 0.0
+    return np.where(pos, np.sqrt(np.where(pos, x, 1.0)), 0.0 * x)
 
 
 def sign_of(x):
@@ -231,11 +245,12 @@ def farfield_operator(uh, u, uinf, n, gamma, delta=FARFIELD_DELTA):
 def supg_tau(u, h, p, phys):
     """Scalar SUPG coefficient (reading of Sec. 2.3, which defines tau only by reference).
 
-    tau = ((2 (|v| + c) p / h)^2 + (4 p^2 nu / h^2)^2)^(-1/2),  nu = 1 / (Re_c rho).
+    tau = ((2 (|v| + c) p / h)^2 + (4 p^2 nu / h^2)^2)^(-1/2),  nu = 1 / (Re_c rho);
+    |v| through sqrt0 (derivative 0 at v = 0, e.g. a gas at rest).
     """
     rho, v, E, P, T = primitives(u, phys["gamma"])
     d = len(v)
-    speed = sqrt(sum(v[i] * v[i] for i in range(d))) + sqrt(T)
+    speed = sqrt0(sum(v[i] * v[i] for i in range(d))) + sqrt(T)
     a = 2.0 * p / h * speed
     b = 4.0 * p * p / (phys["Re"] * h * h) / rho
     return 1.0 / sqrt(a * a + b * b)

@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(256) k_recover_f32(const float* __restrict__ S
                                                      const float* __restrict__ Whk, const int* __restrict__ gather,
                                                      const double* __restrict__ duh, double* __restrict__ du,
                                                      double* __restrict__ dq, int Nu, int Nt, int Np, int Nth, int ns,
-                                                     int d, const float* __restrict__ S0, int iters) {
+                                                     int d, const float* __restrict__ S0, int iters, size_t sG,
+                                                     size_t sGh) {
   extern __shared__ double sm[];
   double* y1 = sm;                                 // Nu: right-hand side
   double* y2 = y1 + Nu;                            // Nu: solution
@@ -329,8 +330,8 @@ __global__ void __launch_bounds__(256) k_recover_f32(const float* __restrict__ S
   const int nq = d * ns * Np;
   for (int i = threadIdx.x; i < nq; i += blockDim.x) {
     int a = i % Np, s = (i / Np) % ns, k = i / (Np * ns);
-    const float* W = Wk + ((size_t)k * Np + a) * Np;
-    const float* Wh = Whk + ((size_t)k * Np + a) * Nth;
+    const float* W = Wk + e * sG + ((size_t)k * Np + a) * Np;
+    const float* Wh = Whk + e * sGh + ((size_t)k * Np + a) * Nth;
     float acc = 0.f;
     for (int b = 0; b < Np; ++b) acc += W[b] * yf[s * Np + b];
     for (int c = 0; c < Nth; ++c) acc += Wh[c] * xf[s * Nth + c];
@@ -429,7 +430,7 @@ int recover_impl(mehdg_ctx* ctx, const double* duh, double* du, double* dq) {
     k_recover_f32<<<ctx->E, 256, smem32, ctx->stream>>>(
         reinterpret_cast<const float*>(ctx->Auu), ctx->perm, reinterpret_cast<const float*>(ctx->Auh), ctx->gv,
         ctx->MinvRQ, ctx->Wk32, ctx->Whk32, ctx->gather, duh, du, dq, ctx->Nu, ctx->Nt, ctx->Np, ctx->Nth, ctx->ns,
-        ctx->d, ctx->S32, ctx->opt.refine_iters);
+        ctx->d, ctx->S32, ctx->opt.refine_iters, ctx->sG, ctx->sGh);
     CKL();
     phase_end(ctx, PH_RECOVER);
     return MEHDG_OK;

@@ -900,14 +900,24 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
       if ((rc = to_float(ctx, u, ctx->u32, nu))) return rc;
       if ((rc = to_float(ctx, q, ctx->q32, nu * D))) return rc;
       if (hist && (rc = to_float(ctx, hist, ctx->h32, nu))) return rc;
-      k_vol_point<D, P, float, float, 1><<<(tot + 127) / 128, 128, 0, st>>>(
-          g, ctx->tab32, ph, ctx->u32, ctx->q32, hist ? ctx->h32 : nullptr, coef, supg_time, ctx->src32, Kvol,
-          nullptr, E);
-      CKL();
       const long long tot2 = (long long)E * ctx->nel * NG;
-      k_vol_point<D, P, float, double, 2><<<(tot2 + 127) / 128, 128, 0, st>>>(
-          g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, nullptr, ctx->rvol, E);
-      CKL();
+      if (ctx->mapped) {
+        k_vol_point<D, P, float, float, 1, true><<<(tot + 127) / 128, 128, 0, st>>>(
+            g, ctx->tab32, ph, ctx->u32, ctx->q32, hist ? ctx->h32 : nullptr, coef, supg_time, ctx->src32, Kvol,
+            nullptr, E, ctx->vgeo);
+        CKL();
+        k_vol_point<D, P, float, double, 2, true><<<(tot2 + 127) / 128, 128, 0, st>>>(
+            g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, nullptr, ctx->rvol, E, ctx->vgeo);
+        CKL();
+      } else {
+        k_vol_point<D, P, float, float, 1><<<(tot + 127) / 128, 128, 0, st>>>(
+            g, ctx->tab32, ph, ctx->u32, ctx->q32, hist ? ctx->h32 : nullptr, coef, supg_time, ctx->src32, Kvol,
+            nullptr, E);
+        CKL();
+        k_vol_point<D, P, float, double, 2><<<(tot2 + 127) / 128, 128, 0, st>>>(
+            g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, nullptr, ctx->rvol, E);
+        CKL();
+      }
     } else if (ctx->mapped) {
       k_vol_point<D, P, BT, double, 0, true><<<(tot + 127) / 128, 128, 0, st>>>(
           g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, Kvol, ctx->rvol, E, ctx->vgeo);
@@ -953,12 +963,12 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
       float* Kf = reinterpret_cast<float*>(ctx->Kface);
       k_face_point<D, P, float, 1><<<(tot + 127) / 128, 128, 0, st>>>(
           g, ctx->tab32, ph, ctx->prob, ctx->bkind, ctx->bside, ctx->fnode, ctx->gather, ctx->uD32, ctx->u32,
-          ctx->q32, ctx->uh32, Kf, nullptr, E);
+          ctx->q32, ctx->uh32, Kf, nullptr, E, ctx->fgeo);
       CKL();
       const long long tot2 = (long long)E * 2 * D * ctx->nsf * NFP;
       k_face_point<D, P, double, 2><<<(tot2 + 127) / 128, 128, 0, st>>>(
           g, ctx->tab, ph, ctx->prob, ctx->bkind, ctx->bside, ctx->fnode, ctx->gather, ctx->uD, u, q, uh, nullptr,
-          ctx->rface, E);
+          ctx->rface, E, ctx->fgeo);
       CKL();
       k_face_contract<D, P, BT, float><<<E, 256, 0, st>>>(g, ctx->tab, ctx->fnode, Kf, ctx->rface, Auu, Auq, Auh,
                                                           Ahu, Ahq, Ahh, ctx->RU, ctx->RUh);

@@ -153,6 +153,25 @@ HD Dual<T, N> dsqrt(const Dual<T, N>& a) {
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
   return r;
 }
+// sqrt of a sum of squares x = v.v: the magnitude |v| is not differentiable at v = 0, and its
+// derivative there is taken as 0 (as sign(0) = 0 for |x|), so a gas at rest gives finite
+// Jacobians
+HD double dsqrt0(double x) { return sqrt(x); }
+HD float dsqrt0(float x) { return sqrtf(x); }
+template <class T, int N>
+HD Dual<T, N> dsqrt0(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = dsqrt0(a.v);
+  if (!(val0(a) > 0.0)) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = zero<T>();
+    return r;
+  }
+  T f = cst<T>(0.5) / r.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+  return r;
+}
 HD double dsin(double x) { return sin(x); }
 HD double dcos(double x) { return cos(x); }
 HD float dsin(float x) { return sinf(x); }

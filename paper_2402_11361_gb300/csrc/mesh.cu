@@ -797,11 +797,23 @@ static int setup(mehdg_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->dtcerr, 0, sizeof(int) * 4, st));
   if (ctx->opt.precision == MEHDG_PREC_MIXED) {
     ALLOC(ctx->finv32, (size_t)F * ctx->nfb * ctx->nfb);
-    std::vector<float> w32(Wk.begin(), Wk.end()), wh32(Whk.begin(), Whk.end());
-    ALLOC(ctx->Wk32, w32.size());
-    ALLOC(ctx->Whk32, wh32.size());
-    CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
+    if (ctx->mapped) {
+      // FP32 copies of the per-macro liftings and condensation factor
+      const long long nw = (long long)E * ctx->sG, nwh = (long long)E * ctx->sGh, nb = (long long)E * ctx->sB;
+      ALLOC(ctx->Wk32, nw);
+      ALLOC(ctx->Whk32, nwh);
+      ALLOC(ctx->Bcat32, nb);
+      int r_;
+      if ((r_ = to_float(ctx, ctx->Wk, ctx->Wk32, nw))) return r_;
+      if ((r_ = to_float(ctx, ctx->Whk, ctx->Whk32, nwh))) return r_;
+      if ((r_ = to_float(ctx, ctx->Bcat, ctx->Bcat32, nb))) return r_;
+    } else {
+      std::vector<float> w32(Wk.begin(), Wk.end()), wh32(Whk.begin(), Whk.end());
+      ALLOC(ctx->Wk32, w32.size());
+      ALLOC(ctx->Whk32, wh32.size());
+      CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
+    }
     if (ctx->opt.refine_iters > 0) ALLOC(ctx->S32, (size_t)E * Nu * Nu);
     ALLOC(ctx->u32, (size_t)E * ns * Np);
     ALLOC(ctx->h32, (size_t)E * ns * Np);
@@ -923,7 +935,8 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
     if (pr.field != MEHDG_FIELD_UNIFORM && pr.field != MEHDG_FIELD_SPHERE) return MEHDG_ERR_ARG;
     for (int b = 0; b < 2; ++b)
       if (pr.bc[b] < MEHDG_BC_DIRICHLET || pr.bc[b] > MEHDG_BC_FARFIELD) return MEHDG_ERR_ARG;
-    if (opt && (opt->precision != MEHDG_PREC_FP64 || opt->condense_layers == 1)) return MEHDG_ERR_ARG;
+    // (tc_mode 2 and 3 run the condensation with one lifting shared by all macro-elements)
+    if (opt && (opt->condense_layers == 1 || opt->tc_mode == 2 || opt->tc_mode == 3)) return MEHDG_ERR_ARG;
   } else {
     if (pr.mesh_kind != MEHDG_MESH_BOX) return MEHDG_ERR_ARG;
     for (int k = 0; k < pr.dim; ++k)

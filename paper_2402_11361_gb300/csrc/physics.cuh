@@ -179,7 +179,8 @@ HD void farfield_operator(const T* uh, const T* u, const U* uinf, const double* 
   }
 }
 
-// scalar tau_SUPG = ((2 (|v|+c) p/h)^2 + (4 p^2 /(Re rho h^2))^2)^(-1/2)
+// scalar tau_SUPG = ((2 (|v|+c) p/h)^2 + (4 p^2 /(Re rho h^2))^2)^(-1/2), |v| with derivative 0
+// at v = 0
 template <int D, class T>
 HD T supg_tau(const T* u, const Phys& ph) {
   T rho, v[D], E, P, Tt;
@@ -187,7 +188,7 @@ HD T supg_tau(const T* u, const Phys& ph) {
   T vv = v[0] * v[0];
 #pragma unroll
   for (int i = 1; i < D; ++i) vv = vv + v[i] * v[i];
-  T a = (2.0 * ph.p / ph.h) * (dsqrt(vv) + dsqrt(Tt));
+  T a = (2.0 * ph.p / ph.h) * (dsqrt0(vv) + dsqrt(Tt));
   T b = (4.0 * ph.p * ph.p / (ph.Re * ph.h * ph.h)) / rho;
   return 1.0 / dsqrt(a * a + b * b);
 }

@@ -167,6 +167,35 @@ def test_viscous_flux_closed_forms():
 
 
 @pytest.mark.parametrize("d", [2, 3])
+def test_supg_tau_at_rest_has_zero_momentum_derivative(d):
+    """A gas at rest (v = 0) sits on the kink of |v| in tau: the derivative of tau along every
+    momentum direction is taken as 0 there (the sign(0) = 0 convention of |x|).  It equals the
+    central difference (|eps| - |-eps|) / (2 eps) = 0, the complex step of the oracle returns
+    it, the value is the closed form with |v| = 0, and away from rest the complex step still
+    matches the central difference."""
+    gamma, h, p = 1.4, 0.3, 2
+    phys = dict(gamma=gamma, Re=80.0)
+    rho, P = 1.1, 0.9
+    for v in (np.zeros(d), 0.2 * np.ones(d)):
+        u = np.array([rho] + list(rho * v) + [P / (gamma - 1.0) + 0.5 * rho * float(v @ v)])
+        for k in range(d):
+            uc = u.astype(complex)
+            uc[1 + k] += 1j * ph.CS_H
+            dcs = np.imag(ph.supg_tau(list(uc), h, p, phys)) / ph.CS_H
+            eps = 1e-7
+            up, um = u.copy(), u.copy()
+            up[1 + k] += eps
+            um[1 + k] -= eps
+            dfd = (ph.supg_tau(list(up), h, p, phys) - ph.supg_tau(list(um), h, p, phys)) / (2.0 * eps)
+            assert abs(dcs - dfd) <= 1e-6 * max(abs(dfd), 1e-3)
+            if not v.any():
+                assert dcs == 0.0
+    c = np.sqrt(gamma * P / rho)
+    tau0 = ph.supg_tau([rho] + [0.0] * d + [P / (gamma - 1.0)], h, p, phys)
+    assert np.isclose(tau0, 1.0 / np.hypot(2.0 * p / h * c, 4.0 * p * p / (phys["Re"] * h * h * rho)), rtol=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
 def test_supg_tau_limits(d):
     """The SUPG coefficient (a reading: Sec. 2.3 defines it by reference) blends the two
     textbook element time scales: h / (2 p (|v| + c)) when advection dominates and
