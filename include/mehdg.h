@@ -360,6 +360,64 @@ int mehdg_tc_gemm_tf32(int M, int N, int K, const float* A, long long lda, long 
  * message on stderr names the first such matrix; the other matrices are factored), CUDA. */
 int mehdg_lu_batched(int n, int batch, void* A, int* perm, int fp32, int* dflag, void* stream);
 
+/* The same factorisation for matrices of UNEVEN size in one persistent launch (the batching
+ * of independent problems): matrix i is n[i] x n[i] at the device address A[i] with pivot
+ * vector perm[i] (device int[n[i]]); n, A, perm are host arrays of nmat entries.  The CTAs of
+ * one grid sized to the GPU take the matrices from a device counter, largest first; nb is the
+ * panel width (8, 16 or 32), whose panel of n[i] x (nb + 1) entries must fit in shared memory
+ * (TOO_LARGE otherwise).  fp32 selects FP32 matrices.  dflag: device int[2] scratch.
+ * Synchronises stream.  Errors: ARG, TOO_LARGE, SINGULAR (first matrix named on stderr), CUDA. */
+int mehdg_lu_queue(int nmat, const int* n, void* const* A, int* const* perm, int fp32, int nb,
+                   int* dflag, void* stream);
+
+/* a13 -- a batch of independent problems of uneven size on one GPU (the benchmark spec's batching
+ * form; the paper solves one problem at a time).  mehdg_batch_create builds one context per
+ * problem (probs[i] with options opts[i], or defaults when opts is NULL), all on stream, and
+ * autotunes the panel width of the batched LU for every (precision, local size Nu) class of the
+ * batch: each width whose panel fits in shared memory is timed on sample matrices of that size.
+ * Each problem's context is reachable by mehdg_batch_context (for mehdg_init_state and every
+ * per-problem call) and is owned by the batch.  condense_layers must be 2 (default).  With
+ * stream NULL (the legacy default stream, on which CUDA graphs cannot be captured) the batch
+ * creates a blocking stream of its own, ordered with the default stream.
+ * Errors: ARG, OOM, CUDA. */
+typedef struct mehdg_batch mehdg_batch;
+int mehdg_batch_create(mehdg_batch** batch, const mehdg_problem* probs, int nprob,
+                       const mehdg_options* opts, void* stream);
+int mehdg_batch_size(const mehdg_batch* batch);
+mehdg_ctx* mehdg_batch_context(mehdg_batch* batch, int i);
+
+/* Steady solve of every problem of the batch (pseudo-transient Newton of Sec. 3.1 with the
+ * SER update, as mehdg_dirk_stage with stage 0, to each problem's newton_rtol), in lockstep
+ * rounds: per round one CUDA-graph replay assembles every unconverged problem and reduces its
+ * residual norms on the device; one replay condenses every such problem, factors all their
+ * local matrices S in ONE persistent work-queue launch (the autotuned panel widths) and forms
+ * their b^ (and explicit local operators); then each problem's FGMRES, recovery and update
+ * run.  The graphs are captured for the current set of unconverged problems and captured
+ * again when it changes; when capture is not possible the same work is launched directly.
+ * u, q, uh: host arrays of nprob device pointers to each problem's state (in/out, layouts as
+ * for one problem); st: host array of nprob statistics (newton_steps, fgmres_iters, res0,
+ * res; status bit 1 = converged, bit 2 (value 4) = a step was retried); rounds (host, or
+ * NULL): lockstep rounds run.  A step that leaves the physical states (non-finite residual at
+ * the new state: negative pressure or density somewhere) is undone and retried with a ten
+ * times smaller pseudo-time step (not in the paper, whose SER update has no such safeguard);
+ * a problem gives up after 20 retries or max_newton steps.  Errors: ARG, NAN (at the initial
+ * state), SINGULAR, NOT_CONVERGED (some problem did not converge; the others are solved),
+ * CUDA; the message names the problem (mehdg_batch_last_error). */
+int mehdg_batch_steady_solve(mehdg_batch* batch, double* const* u, double* const* q,
+                             double* const* uh, mehdg_solve_stats* st, int* rounds);
+
+/* The autotuner's record, one entry per (local size, precision) class, up to cap entries:
+ * n[i], fp64[i], the chosen panel width nb[i] and ms[3 i + j] the sample time of widths 8,
+ * 16, 32 (-1 where the panel does not fit).  Host arrays (or NULL).  Returns the number of
+ * classes, or a negative MEHDG_ERR_*. */
+int mehdg_batch_tiles(const mehdg_batch* batch, int cap, int* n, int* fp64, int* nb, double* ms);
+
+/* CUDA-graph replays of the last solves (-1 if capture was not possible and the work was
+ * launched directly). */
+long long mehdg_batch_graph_replays(const mehdg_batch* batch);
+const char* mehdg_batch_last_error(const mehdg_batch* batch);
+void mehdg_batch_destroy(mehdg_batch* batch);
+
 /* The product with a transposed right operand on the tcgen05 tensor cores (kind::tf32, each
  * operand split into a TF32 part and a TF32 remainder, three products: close to FP32
  * accuracy), the kernel of tc_mode 4:  C_b = alpha A_b Bt_b^T + beta C_b for b < batch, A_b =

@@ -21,7 +21,9 @@ EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_loca
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
            "mehdg_get_block", "mehdg_phase_times", "mehdg_phase_stats", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
-           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_destroy",
+           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_lu_queue", "mehdg_batch_create",
+           "mehdg_batch_size", "mehdg_batch_context", "mehdg_batch_steady_solve", "mehdg_batch_tiles",
+           "mehdg_batch_graph_replays", "mehdg_batch_last_error", "mehdg_batch_destroy", "mehdg_destroy",
            "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
@@ -108,6 +110,16 @@ def load_library(path=LIB_PATH):
     L, F = c_longlong, ctypes.c_float
     lib.mehdg_tc_gemm_nt.argtypes = [I, I, I, c_void_p, L, L, c_void_p, L, L, c_void_p, L, L, F, F, I, c_void_p,
                                      c_void_p]
+    lib.mehdg_lu_queue.argtypes = [I, P(c_int), P(c_void_p), P(c_void_p), I, I, c_void_p, c_void_p]
+    lib.mehdg_batch_create.argtypes = [P(c_void_p), P(Problem), I, P(Options), c_void_p]
+    lib.mehdg_batch_size.argtypes = [c_void_p]
+    lib.mehdg_batch_context.argtypes = [c_void_p, I]
+    lib.mehdg_batch_steady_solve.argtypes = [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p), P(SolveStats),
+                                             P(c_int)]
+    lib.mehdg_batch_tiles.argtypes = [c_void_p, I, P(c_int), P(c_int), P(c_int), P(c_double)]
+    lib.mehdg_batch_graph_replays.argtypes = [c_void_p]
+    lib.mehdg_batch_last_error.argtypes = [c_void_p]
+    lib.mehdg_batch_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.argtypes = [c_void_p]
     lib.mehdg_destroy.restype = None
     lib.mehdg_last_error.argtypes = [c_void_p]
@@ -117,6 +129,10 @@ def load_library(path=LIB_PATH):
             raise RuntimeError("libmehdg.so lacks %s" % name)
         if name not in ("mehdg_destroy", "mehdg_last_error"):
             getattr(lib, name).restype = c_int
+    lib.mehdg_batch_context.restype = c_void_p
+    lib.mehdg_batch_graph_replays.restype = c_longlong
+    lib.mehdg_batch_last_error.restype = ctypes.c_char_p
+    lib.mehdg_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -199,6 +215,30 @@ def lu_batched(A, perm=None):
     if rc != 0:
         raise MehdgError("mehdg_lu_batched failed (%s)" % ERRORS.get(rc, rc))
     return perm
+
+
+def lu_queue(mats, nb=16, perms=None):
+    """P A_i = L_i U_i in place for a list of square contiguous CUDA tensors of uneven size (all
+    float64 or all float32) in ONE persistent work-queue launch (mehdg_lu_queue) with panel
+    width nb (8, 16 or 32); returns the pivot vectors (int32)."""
+    import torch
+    lib = load_library()
+    n = len(mats)
+    fp32 = int(mats[0].dtype == torch.float32)
+    if perms is None:
+        perms = [torch.empty(a.shape[0], dtype=torch.int32, device=a.device) for a in mats]
+    for a in mats:
+        assert a.is_cuda and a.is_contiguous() and a.dim() == 2 and a.shape[0] == a.shape[1]
+        assert a.dtype == (torch.float32 if fp32 else torch.float64)
+    ns = (c_int * n)(*[a.shape[0] for a in mats])
+    As = (c_void_p * n)(*[a.data_ptr() for a in mats])
+    Ps = (c_void_p * n)(*[p.data_ptr() for p in perms])
+    flag = torch.zeros(2, dtype=torch.int32, device=mats[0].device)
+    rc = lib.mehdg_lu_queue(n, ns, As, Ps, fp32, int(nb), c_void_p(flag.data_ptr()),
+                            c_void_p(torch.cuda.current_stream(mats[0].device).cuda_stream))
+    if rc != 0:
+        raise MehdgError("mehdg_lu_queue failed (%s)" % ERRORS.get(rc, rc))
+    return perms
 
 
 class Context:
@@ -400,9 +440,29 @@ class Context:
         self._check(self.lib.mehdg_launch_count(self.h, ctypes.byref(n)), "launch_count")
         return n.value
 
+    @classmethod
+    def _borrow(cls, handle, prob, options, device):
+        """A Context view of a context owned by a Batch (not destroyed by close())."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda:0")
+        self.stream = torch.cuda.current_stream(self.device)
+        self.prob = dict(prob)
+        self.options = dict(DEFAULT_OPTIONS)
+        self.options.update(options or {})
+        self.h = c_void_p(handle)
+        self.owned = False
+        inf = Info()
+        self._check(self.lib.mehdg_query(self.h, ctypes.byref(inf)), "query")
+        self.info = {k: getattr(inf, k) for k, _ in Info._fields_}
+        return self
+
     def close(self):
         if getattr(self, "h", None):
-            self.lib.mehdg_destroy(self.h)
+            if getattr(self, "owned", True):
+                self.lib.mehdg_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -416,3 +476,76 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Independent problems of uneven size solved together on one GPU (mehdg_batch_*): one
+    context per problem (reachable as .contexts[i]), lockstep steady Newton rounds whose
+    assembly and condensation run as CUDA-graph replays, the local LU of all problems in one
+    persistent work-queue launch with autotuned panel widths."""
+
+    def __init__(self, probs, options=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise MehdgError("mehdg needs a CUDA device (no CPU fallback)")
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda:0")
+        torch.cuda.set_device(self.device)
+        self.stream = torch.cuda.current_stream(self.device)
+        n = len(probs)
+        opts = options if isinstance(options, (list, tuple)) else [options] * n
+        self._opts = [dict(DEFAULT_OPTIONS, **(o or {})) for o in opts]
+        self._p = (Problem * n)(*[problem_struct(p) for p in probs])
+        self._o = (Options * n)(*[options_struct(o) for o in self._opts])
+        h = c_void_p()
+        rc = self.lib.mehdg_batch_create(ctypes.byref(h), self._p, n, self._o, c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise MehdgError("mehdg_batch_create failed (%s)" % ERRORS.get(rc, rc))
+        self.h = h
+        self.contexts = [Context._borrow(self.lib.mehdg_batch_context(self.h, i), probs[i], self._opts[i],
+                                         self.device) for i in range(n)]
+
+    def steady_solve(self, states):
+        """states: list of (u, q, uh) CUDA float64 tensors, updated in place.  Returns (per-problem
+        statistics, lockstep rounds)."""
+        n = len(self.contexts)
+        U = (c_void_p * n)(*[s[0].data_ptr() for s in states])
+        Q = (c_void_p * n)(*[s[1].data_ptr() for s in states])
+        H = (c_void_p * n)(*[s[2].data_ptr() for s in states])
+        st = (SolveStats * n)()
+        rounds = c_int(0)
+        rc = self.lib.mehdg_batch_steady_solve(self.h, U, Q, H, st, ctypes.byref(rounds))
+        if rc != 0:
+            raise MehdgError("mehdg_batch_steady_solve failed (%s): %s"
+                             % (ERRORS.get(rc, rc), self.lib.mehdg_batch_last_error(self.h).decode()))
+        out = []
+        for s in st:
+            d = s.as_dict()
+            d["converged"] = bool(s.status & 2)
+            out.append(d)
+        return out, rounds.value
+
+    def tiles(self):
+        """The autotuner's record: [(n, fp64, chosen panel width, {width: sample ms})]."""
+        k = self.lib.mehdg_batch_tiles(self.h, 0, None, None, None, None)
+        n_, f_, nb_ = (c_int * k)(), (c_int * k)(), (c_int * k)()
+        ms = (c_double * (3 * k))()
+        self.lib.mehdg_batch_tiles(self.h, k, n_, f_, nb_, ms)
+        return [(n_[i], bool(f_[i]), nb_[i], {w: ms[3 * i + j] for j, w in enumerate((8, 16, 32)) if ms[3 * i + j] >= 0})
+                for i in range(k)]
+
+    def graph_replays(self):
+        return int(self.lib.mehdg_batch_graph_replays(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for c in self.contexts:
+                c.h = None
+            self.lib.mehdg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

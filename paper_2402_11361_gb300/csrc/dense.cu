@@ -167,6 +167,7 @@ struct CondK {
   const int* fnode;             // [2d][Nfn] macro node of each face node
   const double* M;              // [Np][Np]
   double shift;
+  const double* dshift;         // device copy of the shift (read instead of shift when set)
   const T* xq;                  // [E][d][Nu] M^-1 R_Q in the block precision
   const double* RU; const double* RUh;
   double* g; double* h;
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(CK_NT) k_cond_kron(CondK<T> a) {
   __shared__ T w1[3 * 64];
   __shared__ T wf[6 * 8];
   __shared__ double red[CK_NT / 32];
+  const double shift = a.dshift ? *a.dshift : a.shift;
   const int tid = threadIdx.x;
   const int d = D ? D : a.d, n1 = N1 ? N1 : a.n1;
   const int Np = D && N1 ? ipow_k(N1, D) : a.Np;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(CK_NT) k_cond_kron(CondK<T> a) {
         }
       }
       T v = o1[c] - acc;
-      if (s == sr && a.shift != 0.0) v += (T)(a.shift * a.M[(size_t)lr * Np + l]);
+      if (s == sr && shift != 0.0) v += (T)(shift * a.M[(size_t)lr * Np + l]);
       o1[c] = v;
     }
     // C row (-A_uuh + A_uq Wh) or D row (A_uhuh - A_uhq Wh): column (species, face, face node)
@@ -287,7 +289,7 @@ int cond_kron(mehdg_ctx* ctx, double shift, const T* xq) {
   a.C = reinterpret_cast<T*>(ctx->Auh);
   a.B = reinterpret_cast<T*>(ctx->Ahu);
   a.D = reinterpret_cast<T*>(ctx->Ahh);
-  a.klift = ctx->klift; a.fnode = ctx->fnode; a.M = ctx->Mref; a.shift = shift; a.xq = xq;
+  a.klift = ctx->klift; a.fnode = ctx->fnode; a.M = ctx->Mref; a.shift = shift; a.dshift = ctx->dshift; a.xq = xq;
   a.RU = ctx->RU; a.RUh = ctx->RUh; a.g = ctx->gv; a.h = ctx->hv;
   a.E = ctx->E; a.d = ctx->d; a.n1 = ctx->n1; a.Np = ctx->Np; a.Nfn = ctx->Nfn; a.Nth = ctx->Nth;
   a.Nu = ctx->Nu; a.Nt = ctx->Nt;
@@ -370,8 +372,10 @@ __global__ void k_scale(T* x, long long n, double a) {
 
 // S[(s,a)][(s,b)] += shift M[a][b]
 template <class T>
-__global__ void k_mass_shift(T* S, const double* M, int Np, int ns, double shift, int E, size_t sM) {
+__global__ void k_mass_shift(T* S, const double* M, int Np, int ns, double shift, int E, size_t sM,
+                             const double* dshift) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (dshift) shift = *dshift;
   long long tot = (long long)E * ns * Np * Np;
   if (i >= tot) return;
   int b = i % Np;
@@ -585,8 +589,11 @@ int batched_lu(mehdg_ctx* ctx, double* A, int* perm, int n, int batch, int* flag
   return batched_lu_t<double>(ctx, A, perm, n, batch, flag);
 }
 
+// part 0: the whole condensation and factorisation; part 1: up to the LU of S (which a batch
+// of problems then runs in one work-queue launch); part 2: from the face blocks' LU on, without
+// the final status read (condense_status)
 template <class T>
-int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
+int condense_t(mehdg_ctx* ctx, double shift, double* bhat, int part = 0) {
   cudaStream_t st = ctx->stream;
   const int E = ctx->E, d = ctx->d, ns = ctx->ns, Np = ctx->Np, Nth = ctx->Nth;
   const long long Nu = ctx->Nu, Nt = ctx->Nt;
@@ -597,6 +604,7 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   T* Ahu = reinterpret_cast<T*>(ctx->Ahu);
   T* Ahq = reinterpret_cast<T*>(ctx->Ahq);
   T* Ahh = reinterpret_cast<T*>(ctx->Ahh);
+  if (part != 2) {   // ---- condensation up to the LU of S
   // face blocks of A_uhuh for the preconditioner, then their LU
   {
     long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
@@ -641,9 +649,9 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     CKL();
   }
   // S, C, B, D
-  if (!kron && shift != 0.0) {
+  if (!kron && (shift != 0.0 || ctx->dshift)) {
     long long tot = (long long)E * ns * Np * Np;
-    k_mass_shift<T><<<(tot + 255) / 256, 256, 0, st>>>(Auu, ctx->Mref, Np, ns, shift, E, ctx->sM);
+    k_mass_shift<T><<<(tot + 255) / 256, 256, 0, st>>>(Auu, ctx->Mref, Np, ns, shift, E, ctx->sM, ctx->dshift);
     CKL();
   }
   if (!kron) {
@@ -697,12 +705,14 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
   phase_end(ctx, PH_CONDENSE);
   // LU of S and of the face blocks
   CK(cudaMemsetAsync(ctx->dflag, 0, sizeof(int) * 16, st));
-  phase_begin(ctx, PH_LU);
   if (sizeof(T) == 4 && ctx->S32)   // unfactored S for the FP64 refinement of the local solves
     CK(cudaMemcpyAsync(ctx->S32, Auu, sizeof(float) * E * Nu * Nu, cudaMemcpyDeviceToDevice, st));
+  if (part == 1) return MEHDG_OK;
+  phase_begin(ctx, PH_LU);
   if ((rc = batched_lu_t<T>(ctx, Auu, ctx->perm, (int)Nu, E, ctx->dflag, sizeof(T) == 4 && ctx->use_tc_lu)))
     return rc;
   phase_end(ctx, PH_LU);
+  }   // ---- from the face blocks' LU on
   phase_begin(ctx, PH_FACE_LU);
   if (ctx->finv32) {
     // mixed path: the block-Jacobi preconditioner only needs A_uhuh,f^-1 to FP32 accuracy, so
@@ -761,6 +771,13 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat) {
     }
     phase_end(ctx, PH_FORM);
   }
+  if (part == 2) return MEHDG_OK;
+  return condense_status(ctx);
+}
+
+// the statuses of the last condensation (synchronises the stream)
+int condense_status(mehdg_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
   int flags[4], tcerr = 0;
   CK(cudaMemcpyAsync(flags, ctx->dflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&tcerr, ctx->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -958,6 +975,12 @@ int condense_all(mehdg_ctx* ctx, double shift, double* bhat) {
   if (ctx->opt.condense_layers == 1) return condense_one(ctx, shift, bhat);
   if (ctx->opt.precision == MEHDG_PREC_MIXED) return condense_t<float>(ctx, shift, bhat);
   return condense_t<double>(ctx, shift, bhat);
+}
+
+int condense_part(mehdg_ctx* ctx, double shift, double* bhat, int part) {
+  if (ctx->opt.condense_layers == 1) return ctx_fail(ctx, MEHDG_ERR_ARG, "split condensation needs the second layer");
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) return condense_t<float>(ctx, shift, bhat, part);
+  return condense_t<double>(ctx, shift, bhat, part);
 }
 
 extern "C" int mehdg_lu_batched(int n, int batch, void* A, int* perm, int fp32, int* dflag, void* stream) {

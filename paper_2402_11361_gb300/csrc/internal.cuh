@@ -87,6 +87,10 @@ struct mehdg_ctx {
   // curved (mapped) macro-elements of the shell mesh: per-point geometry, per-macro operators.
   // Mref, Minv, Gk, Ghk, Wk, Whk and Bcat then hold one copy per macro-element at the strides
   // below (0: one copy shared by all macro-elements, the box meshes)
+  // batches of problems: the pseudo-time shift read from device memory (so that a captured
+  // condensation can be replayed with new shifts), phase timers off inside batch graphs
+  const double* dshift = nullptr;
+  bool no_phase = false;
   bool mapped = false;
   double* vgeo = nullptr;    // [E][nel][Ng][d*d + 1]: (J^-1)[j][k] = dxi_j/dx_k (xi in [0,1]^d), weight
   double* fgeo = nullptr;    // [E][2d][nsf][nfp][d + 1]: unit outward normal, weight
@@ -200,6 +204,10 @@ Geo make_geo(const mehdg_ctx* c);
 int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double* uh,
                  const mehdg_time_term* tt, double* norms);
 int condense_all(mehdg_ctx* ctx, double shift, double* bhat);
+// the condensation in parts (1: up to the LU of S, 2: from the face blocks' LU on, no status
+// read) and the status read that ends it
+int condense_part(mehdg_ctx* ctx, double shift, double* bhat, int part);
+int condense_status(mehdg_ctx* ctx);
 int apply_trace_impl(mehdg_ctx* ctx, const double* x, double* y);
 bool apply_bf16_slots_available(const mehdg_ctx* ctx);
 int apply_bf16_slots(mehdg_ctx* ctx, const double* x);

@@ -32,11 +32,11 @@ constexpr int LP_LDP = LP_NB + 1;     // panel row stride in shared memory
 constexpr int LP_TM = 64;             // SIMT update tile
 constexpr int LPTC_BM = 128, LPTC_BN = 256;
 
-template <class T, bool TC>
+template <class T, bool TC, int NB = LP_NB>
 inline size_t lu_panel_smem(int n) {
-  size_t p = (sizeof(T) * (size_t)n * LP_LDP + 127) / 128 * 128;
+  size_t p = (sizeof(T) * (size_t)n * (NB + 1) + 127) / 128 * 128;
   if (TC) return p + (size_t)2 * (LPTC_BM + LPTC_BN) * 32 * 4;
-  return p + sizeof(T) * (size_t)LP_NB * (LP_TM + 1);
+  return p + sizeof(T) * (size_t)NB * (LP_TM + 1);
 }
 
 template <class T>
@@ -144,21 +144,24 @@ __device__ __forceinline__ bool lp_tc_update(float* A, int n, int j0, int c0, co
   return true;
 }
 
-template <class T, bool TC>
-__global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_panel_smem(T* __restrict__ Aall, int* __restrict__ permall, int n,
-                                                         int* __restrict__ flag, int* __restrict__ tcerr) {
-  extern __shared__ __align__(128) unsigned char lp_raw[];
-  T* sP = reinterpret_cast<T*>(lp_raw);   // [n][LP_LDP], rows j0.. of the current panel
+// One CTA factors the n x n matrix A in place with panel width NB (8, 16 or 32; the
+// tcgen05 update needs 32).  A zero pivot sets flag[0] and flag[1] = tag.  The panel is
+// staged in the dynamic shared memory lp_raw (lu_panel_smem<T, TC, NB>(n) bytes).
+template <class T, bool TC, int NB>
+__device__ __forceinline__ void lp_factor(T* __restrict__ A, int* __restrict__ perm, int n, int* __restrict__ flag,
+                                          int* __restrict__ tcerr, int tag, unsigned char* lp_raw) {
+  static_assert(NB == 8 || NB == 16 || NB == 32, "panel width");
+  static_assert(!TC || NB == 32, "the tcgen05 update takes 32-wide panels");
+  constexpr int LP_LDP = NB + 1;
+  T* sP = reinterpret_cast<T*>(lp_raw);   // [n][NB + 1], rows j0.. of the current panel
   unsigned char* sX = lp_raw + (sizeof(T) * (size_t)n * LP_LDP + 127) / 128 * 128;
   __shared__ T rv[LP_NT / 32];   // pivot candidates, compared in the matrix's own precision
   __shared__ int ri[LP_NT / 32];
-  __shared__ int spiv[LP_NB];
-  __shared__ int topsrc[LP_NB], xsrc[LP_NB], xdst[LP_NB];
+  __shared__ int spiv[NB];
+  __shared__ int topsrc[NB], xsrc[NB], xdst[NB];
   __shared__ int nxs;
   __shared__ __align__(8) uint64_t tc_bar;
   __shared__ uint32_t tc_slot;
-  T* A = Aall + (size_t)blockIdx.x * n * n;
-  int* perm = permall + (size_t)blockIdx.x * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t tc_phase = 0;
   bool tc_ok = true;
@@ -179,11 +182,11 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
   __syncthreads();
   if constexpr (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  for (int j0 = 0; j0 < n; j0 += LP_NB) {
-    const int jb = min(LP_NB, n - j0), m = n - j0, c0 = j0 + jb;
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int jb = min(NB, n - j0), m = n - j0, c0 = j0 + jb;
     // ---- 1. panel to shared memory, factor it there
-    for (int idx = tid; idx < m * LP_NB; idx += LP_NT) {
-      const int r = idx / LP_NB, c = idx % LP_NB;
+    for (int idx = tid; idx < m * NB; idx += LP_NT) {
+      const int r = idx / NB, c = idx % NB;
       sP[r * LP_LDP + c] = (c < jb) ? A[(size_t)(j0 + r) * n + j0 + c] : T(0);
     }
     __syncthreads();
@@ -207,9 +210,9 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
       if (r >= m) r = j;   // no finite candidate (NaN column): keep the row
       if (tid == 0) {
         spiv[j] = r;
-        if (b == T(0) && atomicCAS(flag, 0, 1) == 0) flag[1] = blockIdx.x + 1;
+        if (b == T(0) && atomicCAS(flag, 0, 1) == 0) flag[1] = tag;
       }
-      if (r != j && tid < LP_NB) {
+      if (r != j && tid < NB) {
         const T t = sP[j * LP_LDP + tid];
         sP[j * LP_LDP + tid] = sP[r * LP_LDP + tid];
         sP[r * LP_LDP + tid] = t;
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
         if (r == j) continue;
         const int cj = __shfl_sync(0xffffffffu, content, j);
         int cr;
-        if (r < LP_NB) {
+        if (r < NB) {
           cr = __shfl_sync(0xffffffffu, content, r);
           if (lane == r) content = cj;
         } else {
@@ -273,23 +276,23 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
       if (lane < nx) perm[j0 + xdst[lane]] = px;
     }
     // panel back to global memory
-    for (int idx = tid; idx < m * LP_NB; idx += LP_NT) {
-      const int r = idx / LP_NB, c = idx % LP_NB;
+    for (int idx = tid; idx < m * NB; idx += LP_NT) {
+      const int r = idx / NB, c = idx % NB;
       if (c < jb) A[(size_t)(j0 + r) * n + j0 + c] = sP[r * LP_LDP + c];
     }
     // ---- 3. swaps outside the panel, and U12 = L11^-1 (P A12) for trailing columns
     for (int cidx = tid; cidx < n - jb; cidx += LP_NT) {
       const int col = (cidx < j0) ? cidx : cidx + jb;
       T* Ac = A + col;
-      T u[LP_NB], x[LP_NB];
+      T u[NB], x[NB];
 #pragma unroll
-      for (int k = 0; k < LP_NB; ++k) u[k] = (k < jb) ? Ac[(size_t)(j0 + topsrc[k]) * n] : T(0);
+      for (int k = 0; k < NB; ++k) u[k] = (k < jb) ? Ac[(size_t)(j0 + topsrc[k]) * n] : T(0);
 #pragma unroll
-      for (int k = 0; k < LP_NB; ++k) x[k] = (k < nx) ? Ac[(size_t)(j0 + xsrc[k]) * n] : T(0);
+      for (int k = 0; k < NB; ++k) x[k] = (k < nx) ? Ac[(size_t)(j0 + xsrc[k]) * n] : T(0);
       const bool trailing = col >= c0;
-      if (trailing) {   // here jb == LP_NB
+      if (trailing) {   // here jb == NB
 #pragma unroll
-        for (int r = 1; r < LP_NB; ++r) {
+        for (int r = 1; r < NB; ++r) {
           T s = u[r];
 #pragma unroll
           for (int q = 0; q < r; ++q) s -= sP[r * LP_LDP + q] * u[q];
@@ -297,10 +300,10 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
         }
       }
 #pragma unroll
-      for (int k = 0; k < LP_NB; ++k)
+      for (int k = 0; k < NB; ++k)
         if (k < jb && (trailing || topsrc[k] != k)) Ac[(size_t)(j0 + k) * n] = u[k];
 #pragma unroll
-      for (int k = 0; k < LP_NB; ++k)
+      for (int k = 0; k < NB; ++k)
         if (k < nx) Ac[(size_t)(j0 + xdst[k]) * n] = x[k];
     }
     __syncthreads();
@@ -313,11 +316,11 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
         break;
       }
     } else {
-      T* sU = reinterpret_cast<T*>(sX);   // [LP_NB][LP_TM + 1]
+      T* sU = reinterpret_cast<T*>(sX);   // [NB][LP_TM + 1]
       const int m2 = n - c0;
       const int tx = tid % 16, ty = tid / 16;
       const int nt = (m2 + LP_TM - 1) / LP_TM, ntiles = nt * nt;
-      constexpr int RU = LP_NB * LP_TM / LP_NT;
+      constexpr int RU = NB * LP_TM / LP_NT;
       T ru[RU];
       // U12 tile (32 x 64) of column block tj into registers
       auto fetch_u = [&](int tj) {
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
 #pragma unroll
         for (int a = 0; a < 4; ++a) prow[a] = min(jb + ti + ty + 16 * a, m - 1) * LP_LDP;
 #pragma unroll 8
-        for (int kk = 0; kk < LP_NB; ++kk) {
+        for (int kk = 0; kk < NB; ++kk) {
           T lv[4], uv[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) lv[a] = sP[prow[a] + kk];
@@ -385,5 +388,47 @@ __global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1) k_lu_p
     if (warp == 0)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc_slot), "r"((uint32_t)LPTC_BN)
                    : "memory");
+  }
+}
+
+template <class T, bool TC>
+__global__ void __launch_bounds__(LP_NT, (sizeof(T) == 4 && !TC) ? 2 : 1)
+    k_lu_panel_smem(T* __restrict__ Aall, int* __restrict__ permall, int n, int* __restrict__ flag,
+                    int* __restrict__ tcerr) {
+  extern __shared__ __align__(128) unsigned char lp_raw[];
+  lp_factor<T, TC, LP_NB>(Aall + (size_t)blockIdx.x * n * n, permall + (size_t)blockIdx.x * n, n, flag, tcerr,
+                          blockIdx.x + 1, lp_raw);
+}
+
+// Work queue of matrices of uneven size (the batching of independent problems): item i is
+// the n_i x n_i matrix A_i with pivot vector perm_i, factored with panel width nb_i (chosen
+// per size by the batch's autotuner); a zero pivot sets flag_i[0] and flag_i[1] = tag_i.
+struct LuItem {
+  void* A;
+  int* perm;
+  int* flag;
+  int n, nb, tag, pad;
+};
+
+// Persistent: the grid is sized to the GPU (SMs x resident CTAs), each CTA takes the next item
+// from the counter (items sorted largest first) until the queue is empty.  No waiting: the
+// counter only grows, so every CTA leaves after at most nitems + 1 fetches.
+template <class T>
+__global__ void __launch_bounds__(LP_NT, 1) k_lu_queue(const LuItem* __restrict__ items, int nitems,
+                                                       int* __restrict__ counter) {
+  extern __shared__ __align__(128) unsigned char lq_raw[];
+  __shared__ int it;
+  for (;;) {
+    if (threadIdx.x == 0) it = atomicAdd(counter, 1);
+    __syncthreads();
+    const int i = it;
+    __syncthreads();
+    if (i >= nitems) break;
+    const LuItem w = items[i];
+    T* A = static_cast<T*>(w.A);
+    if (w.nb == 8) lp_factor<T, false, 8>(A, w.perm, w.n, w.flag, nullptr, w.tag, lq_raw);
+    else if (w.nb == 16) lp_factor<T, false, 16>(A, w.perm, w.n, w.flag, nullptr, w.tag, lq_raw);
+    else lp_factor<T, false, 32>(A, w.perm, w.n, w.flag, nullptr, w.tag, lq_raw);
+    __syncthreads();
   }
 }

@@ -22,6 +22,7 @@ int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg) {
 // (cudaEventRecordExternal), so phases inside the captured inner GMRES are timed at
 // each replay too.
 void phase_begin(mehdg_ctx* ctx, int p) {
+  if (ctx->no_phase) return;
   if (ctx->capturing) {
     if (!ctx->ev[2 * p]) {
       cudaEventCreate(&ctx->ev[2 * p]);
@@ -47,6 +48,7 @@ void phase_begin(mehdg_ctx* ctx, int p) {
   cudaEventRecord(b[ctx->ring_n[p]], ctx->stream);
 }
 void phase_end(mehdg_ctx* ctx, int p) {
+  if (ctx->no_phase) return;
   if (ctx->capturing) {
     cudaEventRecordWithFlags(ctx->ev[2 * p + 1], ctx->stream, cudaEventRecordExternal);
     ctx->ev_rec[p] = true;

@@ -14,7 +14,8 @@ def declared_functions():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:int|void|const char\*)\s+\**(mehdg_\w+)\s*\(", src, flags=re.M)
+            names += re.findall(r"^\s*(?:int|void|long long|const char\*|mehdg_ctx\*)\s+\**(mehdg_\w+)\s*\(", src,
+                                flags=re.M)
     return names
 
 
