@@ -959,11 +959,11 @@ def run_layers(args, ws, rank, lrank):
 def run_batched(args, ws, rank, lrank):
     """Batched uneven steady solves: independent manufactured-solution problems of the
     config-2 form with seeded sizes (m_c^3 macro-elements, m_c in 2..6) and degrees
-    (p in 1..3), each solved to a 1e-8 residual by the steady Newton-SER loop
-    (mehdg_dirk_stage stage 0).  The problems go through a work queue (largest first)
-    served by worker threads, each with its own CUDA stream and context, so several
-    problems of different shapes run on the GPU at once; a device-memory budget admits a
-    problem only when its blocks fit.  Reports the wall time of the batch."""
+    (p in 1..3), each solved to a 1e-8 residual by the steady Newton-SER iteration.  The
+    problems go, largest first, into waves that fit a device-memory budget; each wave is one
+    mehdg_batch: lockstep Newton rounds of all its problems, their assembly and condensation
+    replayed as CUDA graphs, the local LU of every problem in one persistent work-queue launch
+    with autotuned panel widths.  Reports the wall time of the whole set."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -984,87 +984,83 @@ def run_batched(args, ws, rank, lrank):
         p_ = round(z["Np"] ** (1.0 / 3.0)) // 2        # Np = (2p + 1)^3 for m = 2
         kvol = 4.0 * 4 * z["ns"] * 8 * (p_ + 2) ** 3 * 80                             # pointwise Jacobians
         ntr = z["F"] * z["ns"] * z["Nfn"]
-        return 1.25 * E * (blocks + extra + kvol) + 8.0 * ntr * (2 * args.restart + 40) + 256e6
+        return 1.25 * E * (blocks + extra + kvol) + 8.0 * ntr * (2 * args.restart + 45) + 256e6
 
-    def opts_for(pr, z):
+    def opts_for(pr):
         # p <= 2: the mixed path with the stored local operators; p = 3 (Nu = 1715): FP64 blocks
         # and the Algorithm-2 apply (the FP32 factors of these larger S made FGMRES stall)
+        base = dict(precond=1, restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, inner_iters=args.inner,
+                    newton_rtol=1e-8, max_newton=60)
         if pr["p"] <= 2:
-            return 1, dict(precision=pkg.PREC_MIXED, precond=1, restart=args.restart, max_iters=3000,
-                           lin_rtol=args.lin_rtol, inner_iters=args.inner, newton_rtol=1e-8, max_newton=60,
-                           apply_mode=1, precond_bf16=1, refine_iters=args.refine)
-        return 0, dict(precision=pkg.PREC_FP64, precond=1, restart=args.restart, max_iters=3000,
-                       lin_rtol=args.lin_rtol, inner_iters=args.inner, newton_rtol=1e-8, max_newton=60,
-                       apply_mode=0)
+            return 1, dict(base, precision=pkg.PREC_MIXED, apply_mode=1, precond_bf16=1, refine_iters=args.refine,
+                           tc_mode=args.tc_mode)
+        return 0, dict(base, precision=pkg.PREC_FP64, apply_mode=0)
 
     order = sorted(range(len(probs)), key=lambda i: -szs[i]["E"] * szs[i]["Nu"] ** 2)
     budget = args.batch_mem_gb * 1e9
-    cv = threading.Condition()
-    state = dict(next=0, used=0.0, err=None)
+    waves, cur, used = [], [], 0.0
+    for i in order:
+        need = mem_bytes(szs[i], opts_for(probs[i])[0])
+        if cur and used + need > budget:
+            waves.append(cur)
+            cur, used = [], 0.0
+        cur.append(i)
+        used += need
+    if cur:
+        waves.append(cur)
+
     results = [None] * len(probs)
-
-    def worker():
-        torch.cuda.set_device(dev)
-        stream = torch.cuda.Stream(device=dev)
-        while True:
-            with cv:
-                if state["next"] >= len(order) or state["err"]:
-                    return
-                i = order[state["next"]]
-                state["next"] += 1
-                amode, opts = opts_for(probs[i], szs[i])
-                need = mem_bytes(szs[i], amode)
-                while state["used"] + need > budget and state["used"] > 0:
-                    cv.wait()
-                state["used"] += need
-            try:
-                with torch.cuda.stream(stream):
-                    ctx = pkg.Context(probs[i], opts, device=dev)
-                    du, duh = W.perturbation(probs[i], 1000 + i)
-                    u, q, uh = ctx.init_state(torch.as_tensor(du, device=dev), torch.as_tensor(duh, device=dev),
-                                              lift=True)
-                    st = ctx.dirk_stage(0, 0.0, u, q, uh)
-                    stream.synchronize()
-                    results[i] = dict(E=szs[i]["E"], p=probs[i]["p"], newton=st["newton_steps"],
-                                      fgmres=st["fgmres_iters"], res=st["res"], res0=st["res0"], apply_mode=amode)
-                    ctx.close()
-            except Exception as exc:   # reported in the JSON line
-                with cv:
-                    state["err"] = "problem %d: %s" % (i, exc)
-            finally:
-                with cv:
-                    state["used"] -= need
-                    cv.notify_all()
-
+    wave_info = []
+    err = None
     torch.cuda.synchronize()
     rank_barrier(ws)
     clk = ClockSampler(lrank)
     clk.start()
     t0 = time.perf_counter()
-    threads = [threading.Thread(target=worker) for _ in range(args.batch_workers)]
-    for th in threads:
-        th.start()
-    for th in threads:
-        th.join()
+    for wv in waves:
+        tw = time.perf_counter()
+        try:
+            batch = pkg.Batch([probs[i] for i in wv], [opts_for(probs[i])[1] for i in wv], device=dev)
+            states = []
+            for k, i in enumerate(wv):
+                du, duh = W.perturbation(probs[i], 1000 + i)
+                states.append(batch.contexts[k].init_state(torch.as_tensor(du, device=dev),
+                                                           torch.as_tensor(duh, device=dev), lift=True))
+            stats, rounds = batch.steady_solve(states, allow_not_converged=True)
+            tiles = batch.tiles()
+            replays = batch.graph_replays()
+            if True:
+                for k, i in enumerate(wv):
+                    results[i] = dict(E=szs[i]["E"], p=probs[i]["p"], newton=stats[k]["newton_steps"],
+                                      fgmres=stats[k]["fgmres_iters"], res=stats[k]["res"], res0=stats[k]["res0"],
+                                      retried=bool(stats[k]["status"] & 4), converged=stats[k]["converged"])
+            batch.close()
+            torch.cuda.synchronize()
+            wave_info.append(dict(problems=len(wv), macros=sum(szs[i]["E"] for i in wv), rounds=rounds,
+                                  graph_replays=replays, seconds=time.perf_counter() - tw,
+                                  tiles=[dict(n=t[0], fp64=t[1], panel_width=t[2], sample_ms=t[3]) for t in tiles]))
+        except Exception as exc:   # reported in the JSON line
+            err = "wave of %d problems: %s" % (len(wv), exc)
+            break
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clocks = clk.stop()
     wall = max_over_ranks(wall, ws, dev)
     done = [r for r in results if r]
-    # whole-job counts (each rank solved its share of the batch)
     n_done = int(sum_over_ranks(len(done), ws, dev))
     n_probs = int(sum_over_ranks(len(probs), ws, dev))
     newton = int(sum_over_ranks(sum(r["newton"] for r in done), ws, dev))
     macro_steps = sum_over_ranks(sum(r["newton"] * r["E"] for r in done), ws, dev)
-    converged = all(r["res"] <= max(1e-8 * r["res0"], 1e-14) for r in done) and len(done) == len(probs)
+    converged = all(r["converged"] for r in done) and len(done) == len(probs)
     converged = sum_over_ranks(0.0 if converged else 1.0, ws, dev) == 0.0
     by_p = {}
     for r in done:
-        b = by_p.setdefault(r["p"], dict(problems=0, macros=0, newton_steps=0, fgmres_iters=0))
-        b["problems"] += 1
-        b["macros"] += r["E"]
-        b["newton_steps"] += r["newton"]
-        b["fgmres_iters"] += r["fgmres"]
+        b_ = by_p.setdefault(r["p"], dict(problems=0, macros=0, newton_steps=0, fgmres_iters=0, retried=0))
+        b_["problems"] += 1
+        b_["macros"] += r["E"]
+        b_["newton_steps"] += r["newton"]
+        b_["fgmres_iters"] += r["fgmres"]
+        b_["retried"] += int(r["retried"])
     return {
         "metric": METRIC,
         "value": wall,
@@ -1081,20 +1077,22 @@ def run_batched(args, ws, rank, lrank):
         "data": "synthetic (seeded manufactured-solution problems, seeds 1000 + k)",
         "config": {"workload": "batched uneven steady MMS solves: %d problems, m_c in 2..6, p in 1..3, "
                                "2^3 hexes per macro-element" % n_probs,
-                   "workers": args.batch_workers, "mem_budget_gb": args.batch_mem_gb,
-                   "schedule": "work queue, largest first, one stream and context per worker",
+                   "mem_budget_gb": args.batch_mem_gb,
+                   "schedule": "waves under the memory budget, largest first; one mehdg_batch per wave (lockstep "
+                               "Newton rounds, graph-replayed assembly and condensation, one work-queue LU launch "
+                               "per precision and round, autotuned panel widths)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "problems_solved": n_done,
-        # converged: |R_F| <= max(1e-8 |R_F^0|, 1e-14) (the library's stopping rule)
         "all_converged_1e-8": converged,
         "problems_per_s": n_done / wall,
         "newton_steps_total": newton,
         "macro_newton_steps_per_s": macro_steps / wall,
         "by_degree": by_p,
         "by_degree_scope": "rank 0's share of the batch" if ws > 1 else "whole batch",
-        "not_converged": [dict(problem=i, p=r["p"], macros=r["E"], res=r["res"], res0=r["res0"])
-                          for i, r in enumerate(results) if r and r["res"] > max(1e-8 * r["res0"], 1e-14)],
-        "error": state["err"],
+        "waves": wave_info,
+        "not_converged": [dict(problem=i, p=r["p"], macros=r["E"], newton=r["newton"], res=r["res"], res0=r["res0"],
+                               retried=r["retried"]) for i, r in enumerate(results) if r and not r["converged"]],
+        "error": err,
         "clocks": clocks,
     }
 
@@ -1265,7 +1263,6 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3, help="tgv: Newton steps of the host-buffer (e2e) timing")
     ap.add_argument("--solve-steps", type=int, default=60, help="mms: cap on the recorded Newton steps")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--batch-mem-gb", type=float, default=200.0)
     ap.add_argument("--nmac-tgv", type=int, default=16, help="TGV macro-elements per edge (16 = the config)")
     ap.add_argument("--nmac-layers", type=int, default=8, help="layers workload: macro-elements per cube edge")

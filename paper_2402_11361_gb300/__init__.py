@@ -505,9 +505,10 @@ class Batch:
         self.contexts = [Context._borrow(self.lib.mehdg_batch_context(self.h, i), probs[i], self._opts[i],
                                          self.device) for i in range(n)]
 
-    def steady_solve(self, states):
+    def steady_solve(self, states, allow_not_converged=False):
         """states: list of (u, q, uh) CUDA float64 tensors, updated in place.  Returns (per-problem
-        statistics, lockstep rounds)."""
+        statistics, lockstep rounds).  allow_not_converged: return the statistics (each with its
+        'converged' flag) instead of raising when some problem did not converge."""
         n = len(self.contexts)
         U = (c_void_p * n)(*[s[0].data_ptr() for s in states])
         Q = (c_void_p * n)(*[s[1].data_ptr() for s in states])
@@ -515,7 +516,7 @@ class Batch:
         st = (SolveStats * n)()
         rounds = c_int(0)
         rc = self.lib.mehdg_batch_steady_solve(self.h, U, Q, H, st, ctypes.byref(rounds))
-        if rc != 0:
+        if rc != 0 and not (allow_not_converged and rc == -5):
             raise MehdgError("mehdg_batch_steady_solve failed (%s): %s"
                              % (ERRORS.get(rc, rc), self.lib.mehdg_batch_last_error(self.h).decode()))
         out = []
