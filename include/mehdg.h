@@ -63,6 +63,10 @@ extern "C" {
 #define MEHDG_FIELD_MMS 1     /* par: rho amplitude, velocity amplitude, pressure amplitude */
 #define MEHDG_FIELD_UNIFORM 2 /* par: rho, v1, v2, v3, T */
 #define MEHDG_FIELD_TGV 3     /* par: V0 (Mach of the vortex) */
+#define MEHDG_FIELD_COUETTE3D 5 /* compressible Couette flow with a source term (Sec. 5.1, eq. CF0), in acoustic
+                                 units: v_1 = M x_2 log(1 + x_2), v_2 = v_3 = 0, T = a + x_2 (b - a)
+                                 + K x_2 (1 - x_2), P = 1/gamma (rho = 1/T); par: M, a, b, K; the
+                                 source term is the divergence of the fluxes of this state */
 #define MEHDG_FIELD_SPHERE 4  /* par as UNIFORM (the free stream, also the Dirichlet and far-field
                                  state); initial state: the free stream with the velocity times
                                  3 s^2 - 2 s^3, s = clamp((|x| - 0.6) / 0.4, 0, 1) */
@@ -398,8 +402,9 @@ mehdg_ctx* mehdg_batch_context(mehdg_batch* batch, int i);
  * for one problem); st: host array of nprob statistics (newton_steps, fgmres_iters, res0,
  * res; status bit 1 = converged, bit 2 (value 4) = a step was retried); rounds (host, or
  * NULL): lockstep rounds run.  A step that leaves the physical states (non-finite residual at
- * the new state: negative pressure or density somewhere) is undone and retried with a ten
- * times smaller pseudo-time step (not in the paper, whose SER update has no such safeguard);
+ * the new state: negative pressure or density somewhere) or more than doubles |R_F| is undone
+ * and retried with a ten times smaller pseudo-time step (not in the paper, whose SER update
+ * has no such safeguard);
  * a problem gives up after 20 retries or max_newton steps.  Errors: ARG, NAN (at the initial
  * state), SINGULAR, NOT_CONVERGED (some problem did not converge; the others are solved),
  * CUDA; the message names the problem (mehdg_batch_last_error). */

@@ -76,23 +76,65 @@ def mms_q(x, par, gamma):
     return conserved_grad(rho, grho, v, gv, P, gP, gamma)
 
 
-def mms_source(x, par, phys):
-    """f = div(F + G)(u_ex, grad u_ex): the source that makes u_ex a steady solution.
-
-    The divergence is taken by the complex step in each coordinate direction.
-    """
+def flux_source(x, ufun, qfun, phys):
+    """f = div(F + G)(u_ex, grad u_ex): the source that makes the closed-form u_ex a steady
+    solution.  The divergence is taken by the complex step in each coordinate direction."""
     d = x.shape[0]
     gamma = phys["gamma"]
     f = 0.0
     for k in range(d):
         xp = x.astype(complex)
         xp[k] = xp[k] + 1j * physics.CS_H
-        u = mms_u(xp, par, gamma)
-        q = mms_q(xp, par, gamma)
+        u = ufun(xp)
+        q = qfun(xp)
         Fi = physics.inviscid_flux(u, gamma)
         Gv = physics.viscous_flux(u, q, phys)
         f = f + np.imag(np.array([Fi[s][k] + Gv[s][k] for s in range(len(Fi))])) / physics.CS_H
     return f
+
+
+def mms_source(x, par, phys):
+    """The manufactured solution's source (flux_source of mms_u)."""
+    g = phys["gamma"]
+    return flux_source(x, lambda y: mms_u(y, par, g), lambda y: mms_q(y, par, g), phys)
+
+
+# ---- compressible Couette flow with a source term (Sec. 5.1, eq. CF0) -------------
+# Reading in acoustic units (c = 1 at T = 1): v_1 = M x_2 log(1 + x_2), v_2 = v_3 = 0,
+# T = a + x_2 (b - a) + K x_2 (1 - x_2), P = 1/gamma (so rho = 1/T); par = (M, a, b, K).
+# The paper's printed source term is garbled; the source here is the divergence of the
+# fluxes of this state (flux_source), which is what the paper says it is.
+
+def couette3d_primitives(x, par, gamma):
+    M, a, b, K = par[0], par[1], par[2], par[3]
+    d = x.shape[0]
+    y = x[1]
+    T = a + y * (b - a) + K * y * (1.0 - y)
+    dT = (b - a) + K * (1.0 - 2.0 * y)
+    rho = 1.0 / T
+    grho = [0.0 * y for _ in range(d)]
+    grho[1] = -dT / (T * T)
+    v = [M * y * np.log(1.0 + y)] + [0.0 * y for _ in range(d - 1)]
+    gv = [[0.0 * y for _ in range(d)] for _ in range(d)]
+    gv[0][1] = M * (np.log(1.0 + y) + y / (1.0 + y))
+    P = 1.0 / gamma + 0.0 * y
+    gP = [0.0 * y for _ in range(d)]
+    return rho, grho, v, gv, P, gP
+
+
+def couette3d_u(x, par, gamma):
+    rho, grho, v, gv, P, gP = couette3d_primitives(x, par, gamma)
+    return conserved(rho, v, P, gamma)
+
+
+def couette3d_q(x, par, gamma):
+    rho, grho, v, gv, P, gP = couette3d_primitives(x, par, gamma)
+    return conserved_grad(rho, grho, v, gv, P, gP, gamma)
+
+
+def couette3d_source(x, par, phys):
+    g = phys["gamma"]
+    return flux_source(x, lambda y: couette3d_u(y, par, g), lambda y: couette3d_q(y, par, g), phys)
 
 
 # ---- Couette flow between isothermal walls (config "2D Couette") ------------------

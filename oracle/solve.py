@@ -85,6 +85,8 @@ class Problem:
     def source(self, geo):
         if self.prob["field"] == 1:
             return fields.mms_source(geo.xq, self.prob["field_par"], self.phys)
+        if self.prob["field"] == 5:
+            return fields.couette3d_source(geo.xq, self.prob["field_par"], self.phys)
         return None
 
     def bfaces(self, e, geo):
@@ -100,6 +102,8 @@ class Problem:
             if kind == 1:
                 if prob["field"] == 1:
                     uD = fields.mms_u(fc["x"], prob["field_par"], prob["gamma"])
+                elif prob["field"] == 5:
+                    uD = fields.couette3d_u(fc["x"], prob["field_par"], prob["gamma"])
                 else:
                     uD = np.repeat(uniform_from_par(prob)[:, None], len(fc["w"]), axis=1)
                 out.append((1, dict(uD=uD)))
@@ -134,6 +138,8 @@ def initial_state(P, lift=True):
             u[e] = fields.mms_u(x, fp, prob["gamma"])
         elif prob["field"] == 3:
             u[e] = fields.tgv_u(x, fp[0], prob["gamma"])
+        elif prob["field"] == 5:
+            u[e] = fields.couette3d_u(x, fp, prob["gamma"])
         elif prob["field"] == 4:
             u[e] = fields.shell_initial_u(x, fp[0], fp[1:4], fp[4], prob["gamma"])
         else:

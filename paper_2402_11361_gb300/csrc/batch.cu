@@ -412,7 +412,7 @@ extern "C" int mehdg_batch_steady_solve(mehdg_batch* b, double* const* u, double
   for (int i = 0; i < N; ++i)
     if (!u[i] || !q[i] || !uh[i]) return MEHDG_ERR_ARG;
   std::vector<char> active(N, 1);
-  std::vector<double> R0(N), RU(N), dtau(N);
+  std::vector<double> R0(N), RU(N), dtau(N), RF(N);
   std::vector<int> retries(N, 0);
   for (int i = 0; i < N; ++i) {
     st[i] = mehdg_solve_stats{};
@@ -441,6 +441,7 @@ extern "C" int mehdg_batch_steady_solve(mehdg_batch* b, double* const* u, double
     R0[i] = b->hnorm[4 * i + 3];
     if (!std::isfinite(R0[i])) return bfail(b, MEHDG_ERR_NAN, "problem " + std::to_string(i) + ": non-finite residual");
     RU[i] = std::sqrt(b->hnorm[4 * i + 1]);
+    RF[i] = R0[i];
     st[i].res0 = st[i].res = R0[i];
     if (conv(i)) {
       active[i] = 0;
@@ -495,9 +496,10 @@ extern "C" int mehdg_batch_steady_solve(mehdg_batch* b, double* const* u, double
     for (int i = 0; i < N; ++i) {
       if (!active[i]) continue;
       mehdg_ctx* c = b->ctx[i];
-      if (!std::isfinite(b->hnorm[4 * i + 3])) {
-        // the step left the physical states (a non-finite residual): back to the previous state
-        // with a ten times smaller pseudo-time step
+      const double rf = b->hnorm[4 * i + 3];
+      if (!std::isfinite(rf) || rf > 2.0 * RF[i]) {
+        // the step left the physical states (a non-finite residual) or more than doubled the
+        // residual: back to the previous state with a ten times smaller pseudo-time step
         const long long nu = (long long)c->E * c->Nu;
         const double* pv = b->prev[i];
         int rc;
@@ -513,7 +515,8 @@ extern "C" int mehdg_batch_steady_solve(mehdg_batch* b, double* const* u, double
       const double ru = std::sqrt(b->hnorm[4 * i + 1]);
       dtau[i] = std::min(std::max(dtau[i] * RU[i] / std::max(ru, 1e-300), c->opt.tau_init), c->opt.tau_max);
       RU[i] = ru;
-      st[i].res = b->hnorm[4 * i + 3];
+      RF[i] = rf;
+      st[i].res = rf;
       if (conv(i)) {
         active[i] = 0;
         st[i].status |= 2;

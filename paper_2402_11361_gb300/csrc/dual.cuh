@@ -195,6 +195,17 @@ HD Dual<T, N> dcos(const Dual<T, N>& a) {
   return r;
 }
 // |x| with derivative sign(x), sign(0) = 0
+HD double dlog(double x) { return log(x); }
+HD float dlog(float x) { return logf(x); }
+template <class T, int N>
+HD Dual<T, N> dlog(const Dual<T, N>& a) {
+  Dual<T, N> r;
+  r.v = dlog(a.v);
+  T f = cst<T>(1.0) / a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * f;
+  return r;
+}
 HD double dabs(double x) { return x > 0 ? x : (x < 0 ? -x : 0.0); }
 HD float dabs(float x) { return x > 0 ? x : (x < 0 ? -x : 0.f); }
 template <class T, int N>

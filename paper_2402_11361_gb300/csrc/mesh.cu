@@ -267,7 +267,8 @@ __global__ void k_source(Geo g, const double* tab, mehdg_problem pr, double* src
     xs[k].d[k].v = 1.0;
   }
   X2 u2[NS];
-  field_mms<D, X2>(xs, pr.field_par, pr.gamma, u2);
+  if (pr.field == MEHDG_FIELD_COUETTE3D) field_couette3d<D, X2>(xs, pr.field_par, pr.gamma, u2);
+  else field_mms<D, X2>(xs, pr.field_par, pr.gamma, u2);
   T1 uu[NS], qq[NS][D], F[NS][D], G[NS][D];
   for (int s = 0; s < NS; ++s) {
     uu[s].v = u2[s].v.v;
@@ -291,6 +292,7 @@ __global__ void k_source(Geo g, const double* tab, mehdg_problem pr, double* src
 template <int D>
 __device__ void field_at(const mehdg_problem& pr, const double* x, double* u) {
   if (pr.field == MEHDG_FIELD_MMS) field_mms<D, double>(x, pr.field_par, pr.gamma, u);
+  else if (pr.field == MEHDG_FIELD_COUETTE3D) field_couette3d<D, double>(x, pr.field_par, pr.gamma, u);
   else if (pr.field == MEHDG_FIELD_TGV) field_tgv<D, double>(x, pr.field_par, pr.gamma, u);
   else field_uniform<D>(pr.field_par, pr.gamma, u);
 }
@@ -870,7 +872,7 @@ static int setup(mehdg_ctx* ctx) {
 
   // closed-form data
   Geo g = make_geo(ctx);
-  if (pr.field == MEHDG_FIELD_MMS) {
+  if (pr.field == MEHDG_FIELD_MMS || pr.field == MEHDG_FIELD_COUETTE3D) {
     long long tot = (long long)E * ctx->nel * ctx->Ng;
     ALLOC(ctx->src, tot * ns);
     int bs = 128;

@@ -333,6 +333,21 @@ HD void field_tgv(const X* x, const double* par, double g, X* u) {
   conserved_from<D, X>(rho, v, P, g, u);
 }
 
+// compressible Couette flow with a source term (Sec. 5.1, eq. CF0; the reading in acoustic units):
+// v_1 = M x_2 log(1 + x_2), v_2 = v_3 = 0, T = alpha + x_2 (beta - alpha) + K x_2 (1 - x_2),
+// P = 1/gamma, rho = gamma P / T; par: M, alpha, beta, K
+template <int D, class X>
+HD void field_couette3d(const X* x, const double* par, double g, X* u) {
+  const X y = x[1];
+  X v[D];
+  v[0] = par[0] * (y * dlog(1.0 + y));
+  for (int k = 1; k < D; ++k) v[k] = zero<X>();
+  X T = par[1] + y * (par[2] - par[1]) + par[3] * (y * (1.0 - y));
+  X P = cst<X>(1.0 / g);
+  X rho = 1.0 / T;
+  conserved_from<D, X>(rho, v, P, g, u);
+}
+
 template <int D>
 HD void field_uniform(const double* par, double g, double* u) {
   double rho = par[0], v[D];

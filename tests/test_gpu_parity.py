@@ -470,8 +470,12 @@ def test_mixed_dirk_step_reaches_the_fp64_solution(lib):
 @pytest.mark.parametrize("iters", [0, 2])
 def test_mixed_local_solves_refined_in_fp64(lib, iters):
     """Mixed path: the recovery's local solve du = S^-1 (g + C duh) uses the FP32 LU of S;
-    with refinement sweeps (residual of the stored unfactored S accumulated in FP64) the
-    solve residual drops from the FP32 level to the FP64 level."""
+    with refinement sweeps (residual of the stored unfactored FP32 S accumulated in FP64) the
+    solve residual against that FP32-assembled S drops from the FP32 level to the FP64 level.
+    The refinement converges to the solution of the FP32-assembled system, not of the FP64 one
+    (the mixed path never forms an FP64 S): against the FP64 oracle's local solve the error
+    stays at the level of the FP32 blocks, about cond(S) u_32, and is reported and bounded here;
+    the FP64 Newton residual removes it over the nonlinear iteration."""
     pr = W.mms(dim=3, nmac=2, m=2, p=2)
     P = solve.Problem(pr)
     u, q, uh = W.random_state(pr, 5)
@@ -482,18 +486,28 @@ def test_mixed_local_solves_refined_in_fp64(lib, iters):
     du, _ = ctx.recover(to_dev(duh))
     du = du.cpu().numpy()
     Nu, Nt = P.ns * P.Np, P.ns * P.Nth
-    worst = 0.0
+    worst = worst64 = 0.0
+    bound64 = 0.0
     for e in (0, 3, 7):
+        geo = P.geometry(e)
+        c = solve.condense_second_layer(geo, asm.assemble_macro(geo, P.phys, u[e], q[e], P.local_trace(e, uh), None,
+                                                                P.source(geo), P.bfaces(e, geo)), shift=0.3)
+        duh_loc = duh[P.maps[e].reshape(-1)]
+        du64 = np.linalg.solve(c["S"], c["g"] + c["C"] @ duh_loc)
+        worst64 = max(worst64, rel2(du[e].reshape(-1), du64))
+        bound64 = max(bound64, min(64 * np.linalg.cond(c["S"]) * U32, 1e-3))
         if iters == 0:
             with pytest.raises(RuntimeError):
                 ctx.get_block(17, e)
-            break
+            continue
         S0 = ctx.get_block(17, e).reshape(Nu, Nu)
         C = ctx.get_block(4, e).reshape(Nu, Nt)
-        rhs = ctx.get_block(13, e) + C @ duh[P.maps[e].reshape(-1)]
+        rhs = ctx.get_block(13, e) + C @ duh_loc
         res = np.linalg.norm(rhs - S0 @ du[e].reshape(-1)) / np.linalg.norm(rhs)
         worst = max(worst, res)
-    print("refine_iters", iters, "worst relative local residual", worst)
+    print("refine_iters", iters, "worst relative local residual (FP32-assembled S)", worst,
+          "worst relative error vs the FP64 oracle's local solve %.2e (bound %.2e)" % (worst64, bound64))
+    assert worst64 <= bound64
     if iters:
         assert worst < 1e-12
     ctx.close()

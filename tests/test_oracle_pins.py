@@ -903,3 +903,27 @@ def test_mapped_lifting_reproduces_gradients_of_linear_fields():
         for k in range(3):
             qk = -np.linalg.solve(blk["M"], blk["Gk"][k] @ u + blk["Ghk"][k] @ uh)
             assert np.abs(qk - g[k]).max() < 1e-12
+
+
+def test_couette3d_closed_form_gradient_and_walls():
+    """Compressible Couette flow with a source (Sec. 5.1): the closed-form gradient used for the
+    source equals the complex-step derivative of the closed-form state; the state is a shear
+    flow (only v_1, depending on x_2 only, zero at x_2 = 0), at constant pressure 1/gamma, with
+    T(0) = alpha and T(1) = beta."""
+    pr = W.couette3d()
+    par, g = pr["field_par"], pr["gamma"]
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0.0, 1.0, size=(3, 7))
+    q = np.array(fields.couette3d_q(x, par, g))        # [s][k]
+    for k in range(3):
+        xc = x.astype(complex)
+        xc[k] += 1j * ph.CS_H
+        dk = np.imag(np.array(fields.couette3d_u(xc, par, g))) / ph.CS_H
+        assert np.abs(dk - q[:, k]).max() < 1e-13
+    u = np.array(fields.couette3d_u(x, par, g))
+    rho, v, E, P, T = ph.primitives(list(u), g)
+    assert np.allclose(P, 1.0 / g, rtol=1e-14) and np.abs(v[1]).max() == 0.0 and np.abs(v[2]).max() == 0.0
+    ends = np.array([[0.3, 0.3], [0.0, 1.0], [0.6, 0.6]])
+    ue = np.array(fields.couette3d_u(ends, par, g))
+    _, ve, _, _, Te = ph.primitives(list(ue), g)
+    assert abs(ve[0][0]) < 1e-16 and np.allclose(Te, [par[1], par[2]], rtol=1e-14)

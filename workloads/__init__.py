@@ -27,7 +27,7 @@ Workloads (all synthetic, generated from closed forms; no mesh or dataset files)
 import numpy as np
 
 BC_NONE, BC_DIRICHLET, BC_WALL, BC_FARFIELD = 0, 1, 2, 3
-FIELD_NONE, FIELD_MMS, FIELD_UNIFORM, FIELD_TGV, FIELD_SPHERE = 0, 1, 2, 3, 4
+FIELD_NONE, FIELD_MMS, FIELD_UNIFORM, FIELD_TGV, FIELD_SPHERE, FIELD_COUETTE3D = 0, 1, 2, 3, 4, 5
 MESH_BOX, MESH_SHELL = 0, 1
 
 
@@ -94,6 +94,19 @@ def sphere(nq=8, nr=16, m=2, p=2, r0=0.5, r1=10.0, ratio=1.15, Re=100.0, Mach=0.
     pr["field"] = FIELD_SPHERE
     pr["field_par"] = [1.0, Mach, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0]
     pr["name"] = "sphere"
+    return pr
+
+
+def couette3d(nmac=2, m=2, p=2, Mach=0.15, Re=1.0, Pr=0.71, alpha=0.8, beta=0.85, supg=1):
+    """Compressible Couette flow with a source term on the unit cube (the paper's Sec. 5.1
+    case), Dirichlet data from the closed form on every side; Re on the unit length, so
+    Re_c = Re / Mach; viscous-heating coefficient K = (gamma - 1) Pr Mach^2 / 2."""
+    gamma = 1.4
+    pr = _base(3, [nmac] * 3, [0.0] * 3, [1.0] * 3, [0, 0, 0], m, p, Re / Mach, Pr=Pr, gamma=gamma, supg=supg)
+    pr["bc"] = [BC_DIRICHLET] * 6
+    pr["field"] = FIELD_COUETTE3D
+    pr["field_par"] = [Mach, alpha, beta, 0.5 * (gamma - 1.0) * Pr * Mach * Mach, 0.0, 0.0, 0.0, 0.0]
+    pr["name"] = "couette3d"
     return pr
 
 
