@@ -658,6 +658,9 @@ def run_tgv(args, ws, rank, lrank):
 
     dev = torch.device("cuda:%d" % lrank)
     torch.cuda.set_device(dev)
+    # a stream of its own for everything that follows (torch work and library calls alike): the
+    # legacy default stream cannot capture the inner-GMRES CUDA graph
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
     nmac = args.nmac_tgv
     pr = W.tgv(nmac=nmac)
     z = sizes(pr)
@@ -693,6 +696,7 @@ def run_tgv(args, ws, rank, lrank):
     t_dev = ev0.elapsed_time(ev1) / 1e3
     clocks = clk.stop()
     launches = ctx.launch_count() - l0
+    graph_replays = ctx.graph_replays()
     stats = ctx.phase_stats()
     its_timed = drv.fgmres - f0
     t_dev = max_over_ranks(t_dev, ws, dev)
@@ -794,6 +798,7 @@ def run_tgv(args, ws, rank, lrank):
         "e2e": {"value": replica_value(t_e2e / n_e2e, ws), "unit": UNIT_TGV, "steps": n_e2e,
                 "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
         "gpu_launches": launches,
+        "inner_gmres_graph_replays": graph_replays,
         "roofline": roof,
         "clocks": clocks,
     }
@@ -814,6 +819,9 @@ def run_sphere(args, ws, rank, lrank):
 
     dev = torch.device("cuda:%d" % lrank)
     torch.cuda.set_device(dev)
+    # a stream of its own for everything that follows (torch work and library calls alike): the
+    # legacy default stream cannot capture the inner-GMRES CUDA graph
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
     fp64 = args.precision == "fp64"
     nr = args.sphere_nr or 12
     pr = W.sphere(nq=args.sphere_nq, nr=nr)

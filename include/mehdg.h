@@ -458,6 +458,12 @@ int mehdg_phase_stats(mehdg_ctx* ctx, double* sum_ms, long long* count, int n, i
  * count is host memory). */
 int mehdg_launch_count(const mehdg_ctx* ctx, long long* count);
 
+/* Replays of the inner-GMRES CUDA graph (multi-level preconditioner) since mehdg_mesh (host).
+ * The graph is captured at the first preconditioner call when the context's stream is not the
+ * legacy default stream, on which CUDA graphs cannot be captured; there (count 0) the same
+ * kernels are launched directly. */
+int mehdg_graph_replays(const mehdg_ctx* ctx, long long* count);
+
 void mehdg_destroy(mehdg_ctx* ctx);
 const char* mehdg_last_error(const mehdg_ctx* ctx);
 

@@ -21,7 +21,7 @@ EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_loca
            "mehdg_apply_trace", "mehdg_precondition", "mehdg_linear_solve", "mehdg_recover", "mehdg_dirk_stage",
            "mehdg_get_block", "mehdg_phase_times", "mehdg_phase_stats", "mehdg_launch_count", "mehdg_mlp_setup", "mehdg_mlp_params",
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
-           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_lu_queue", "mehdg_batch_create",
+           "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_lu_queue", "mehdg_graph_replays", "mehdg_batch_create",
            "mehdg_batch_size", "mehdg_batch_context", "mehdg_batch_steady_solve", "mehdg_batch_tiles",
            "mehdg_batch_graph_replays", "mehdg_batch_last_error", "mehdg_batch_destroy", "mehdg_destroy",
            "mehdg_last_error"]
@@ -99,6 +99,7 @@ def load_library(path=LIB_PATH):
     lib.mehdg_phase_times.argtypes = [c_void_p, P(c_double), I]
     lib.mehdg_phase_stats.argtypes = [c_void_p, P(c_double), P(c_longlong), I, I]
     lib.mehdg_launch_count.argtypes = [c_void_p, P(c_longlong)]
+    lib.mehdg_graph_replays.argtypes = [c_void_p, P(c_longlong)]
     lib.mehdg_mlp_setup.argtypes = [c_void_p, I, ctypes.c_ulonglong, I]
     lib.mehdg_mlp_params.argtypes = [c_void_p, I, c_void_p, P(c_longlong)]
     lib.mehdg_mlp_record.argtypes = [c_void_p, c_void_p, c_void_p]
@@ -434,6 +435,12 @@ class Context:
         out = (c_double * 2)()
         self._check(self.lib.mehdg_mlp_train(self.h, int(epochs), int(batch), float(lr), out), "mlp_train")
         return out[0], out[1]
+
+    def graph_replays(self):
+        """Replays of the inner-GMRES CUDA graph (0 on the legacy default stream: no capture)."""
+        n = c_longlong(0)
+        self._check(self.lib.mehdg_graph_replays(self.h, ctypes.byref(n)), "graph_replays")
+        return n.value
 
     def launch_count(self):
         n = c_longlong()

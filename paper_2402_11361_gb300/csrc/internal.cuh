@@ -179,6 +179,7 @@ struct mehdg_ctx {
   long long ph_cnt[16] = {};
   int ph_graph[16] = {};
   long long ig_replays = 0;   // inner-GMRES graph replays not yet added to the sums
+  long long ig_total = 0;     // inner-GMRES graph replays since mehdg_mesh
 };
 
 enum Phase {

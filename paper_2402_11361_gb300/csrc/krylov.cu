@@ -564,6 +564,7 @@ static int inner_gmres(mehdg_ctx* ctx, const double* r, double* z) {
   CK(cudaGraphLaunch(ctx->ig_exec, ctx->stream));
   ctx->launches += ctx->ig_nodes;
   ++ctx->ig_replays;
+  ++ctx->ig_total;
   CK(cudaMemcpyAsync(z, ctx->gout, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   return MEHDG_OK;
 }

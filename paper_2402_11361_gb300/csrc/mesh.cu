@@ -84,6 +84,12 @@ void phase_harvest(mehdg_ctx* ctx) {
   ctx->ig_replays = 0;
 }
 
+extern "C" int mehdg_graph_replays(const mehdg_ctx* ctx, long long* count) {
+  if (!ctx || !count) return MEHDG_ERR_ARG;
+  *count = ctx->ig_total;
+  return MEHDG_OK;
+}
+
 extern "C" int mehdg_launch_count(const mehdg_ctx* ctx, long long* count) {
   if (!ctx || !count) return MEHDG_ERR_ARG;
   *count = ctx->launches;

@@ -684,3 +684,27 @@ def test_mlp_training_and_kind2_solve(lib):
           (st0["fgmres_iters"], st2["fgmres_iters"], st2["status"] & 1))
     ctx.close()
     ctx2.close()
+
+
+def test_inner_gmres_graph_equals_direct_launches(lib):
+    """The multi-level preconditioner's inner GMRES runs as one CUDA graph per call when the
+    context's stream can capture (not the legacy default stream) and as direct launches
+    otherwise: the same FGMRES solve both ways gives the same iterate to rounding."""
+    pr = W.mms(dim=3, nmac=2, m=2, p=1)
+    u, q, uh = W.random_state(pr, 13)
+    opts = dict(precision=0, precond=1, inner_iters=8, lin_rtol=1e-10, restart=40, max_iters=400)
+    out = {}
+    for mode in ("direct", "graph"):
+        s = torch.cuda.Stream() if mode == "graph" else torch.cuda.default_stream()
+        with torch.cuda.stream(s):
+            ctx = lib.Context(pr, opts)
+            ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+            b = ctx.condense(shift=0.4)
+            x, st = ctx.linear_solve(b)
+            torch.cuda.synchronize()
+            out[mode] = (x.cpu().numpy(), st["fgmres_iters"], ctx.graph_replays())
+            ctx.close()
+    (xd, itd, gd), (xg, itg, gg) = out["direct"], out["graph"]
+    print("inner GMRES graph replays: direct %d, graph %d; FGMRES its %d / %d" % (gd, gg, itd, itg))
+    assert gd == 0 and gg > 0 and itd == itg
+    assert rel2(xg, xd) < 1e-12
