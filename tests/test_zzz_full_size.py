@@ -126,3 +126,74 @@ def test_full_size_mixed_path_sampled_against_oracle(lib):
             assert res < 1e-7
     finally:
         ctx.close()
+
+
+def _sampled_blocks(ctx, P, u, q, uh, sampled, tol_blk, tol_res):
+    Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+    out = {}
+    for e in sampled:
+        geo = P.geometry(e)
+        b = asm.assemble_macro(geo, P.phys, u[e], q[e], P.local_trace(e, uh), None, P.source(geo), P.bfaces(e, geo))
+        out[e] = (geo, b)
+        assert rel(ctx.get_block(0, e).reshape(Nu, Nu), b["Auu"]) < tol_blk
+        assert rel(ctx.get_block(1, e).reshape(Nu, Nu), b["Auq"][0]) < tol_blk
+        assert rel(ctx.get_block(9, e).reshape(Nt, Nt), b["Ahh"]) < tol_blk
+        assert rel(ctx.get_block(10, e), b["RQ"].reshape(-1)) < tol_res
+        assert rel(ctx.get_block(11, e), b["RU"].reshape(-1)) < tol_res
+        assert rel(ctx.get_block(12, e), b["RUh"].reshape(-1)) < tol_res
+    return out
+
+
+def test_full_size_tgv_fp64_sampled_against_oracle(lib):
+    """The headline configuration (16^3 TGV, 4096 macros, the bench's plain FP64 options with
+    the row-compressed Algorithm-2 apply): blocks, residuals and the condensed operators S, B,
+    C, D, g, h, b^ of sampled macros (a corner, an interior macro, the opposite corner; the
+    mesh is periodic, so every macro is interior) against the oracle at 1e-11 / 1e-10."""
+    pr = W.tgv(nmac=16)
+    P = solve.Problem(pr)
+    assert P.E == 4096
+    Nu, Nt = P.ns * P.Np, P.ns * P.Nth
+    opts = dict(precision=0, apply_mode=2, precond=1, inner_iters=10, restart=60, lin_rtol=LIN_RTOL, max_iters=3000)
+    u, q, uh = W.random_state(pr, 17)
+    ctx = lib.Context(pr, opts)
+    try:
+        ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+        sampled = (0, 2184, 4095)
+        ob = _sampled_blocks(ctx, P, u, q, uh, sampled, 1e-11, 1e-11)
+        ctx.condense(shift=SHIFT)
+        for e in sampled:
+            c = solve.condense_second_layer(ob[e][0], ob[e][1], shift=SHIFT)
+            assert rel(ctx.get_block(4, e).reshape(Nu, Nt), c["C"]) < 1e-11
+            assert rel(ctx.get_block(5, e).reshape(Nt, Nu), c["B"]) < 1e-11
+            assert rel(ctx.get_block(9, e).reshape(Nt, Nt), c["D"]) < 1e-11
+            assert rel(ctx.get_block(13, e), c["g"]) < 1e-11
+            assert rel(ctx.get_block(14, e), c["h"]) < 1e-11
+            assert np.array_equal(ctx.get_block(15, e).astype(int), c["piv"])
+            assert rel(ctx.get_block(0, e).reshape(Nu, Nu), c["LU"]) < 1e-10
+            assert rel(ctx.get_block(16, e), c["bhat"]) < 1e-10
+    finally:
+        ctx.close()
+
+
+def test_full_size_sphere_mixed_sampled_against_oracle(lib):
+    """The sphere configuration at full size (6 x 8^2 x 16 = 6144 curved macros, the mixed form
+    that fits it): FP32 blocks of sampled macros (at the wall on a cube-panel corner, in the
+    middle of the shell, at the far field) within the FP32 level, their FP64 residuals to 1e-10,
+    and the local condensed right-hand side through the FP32 local factors within 1e-3."""
+    pr = W.sphere()
+    P = solve.Problem(pr)
+    assert P.E == 6144
+    opts = dict(precision=1, apply_mode=1, precond=1, precond_bf16=1, refine_iters=1, tc_mode=4, inner_iters=10,
+                restart=60, lin_rtol=LIN_RTOL, max_iters=3000)
+    u, q, uh = W.random_state(pr, 19)
+    ctx = lib.Context(pr, opts)
+    try:
+        ctx.assemble(to_dev(u), to_dev(q), to_dev(uh))
+        sampled = (0, 2524, 6143)
+        ob = _sampled_blocks(ctx, P, u, q, uh, sampled, 3e-6, 1e-10)
+        ctx.condense(shift=SHIFT)
+        for e in sampled:
+            c = solve.condense_second_layer(ob[e][0], ob[e][1], shift=SHIFT)
+            assert rel(ctx.get_block(16, e), c["bhat"]) < 1e-3
+    finally:
+        ctx.close()
