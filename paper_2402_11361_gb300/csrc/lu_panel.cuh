@@ -413,9 +413,10 @@ struct LuItem {
 // Persistent: the grid is sized to the GPU (SMs x resident CTAs), each CTA takes the next item
 // from the counter (items sorted largest first) until the queue is empty.  No waiting: the
 // counter only grows, so every CTA leaves after at most nitems + 1 fetches.
+// (FP32: two CTAs per SM, as k_lu_panel_smem<float>, when the largest panel leaves room)
 template <class T>
-__global__ void __launch_bounds__(LP_NT, 1) k_lu_queue(const LuItem* __restrict__ items, int nitems,
-                                                       int* __restrict__ counter) {
+__global__ void __launch_bounds__(LP_NT, sizeof(T) == 4 ? 2 : 1)
+    k_lu_queue(const LuItem* __restrict__ items, int nitems, int* __restrict__ counter) {
   extern __shared__ __align__(128) unsigned char lq_raw[];
   __shared__ int it;
   for (;;) {
