@@ -739,7 +739,7 @@ def run_tgv(args, ws, rank, lrank):
         uu, qq, hh = c2.init_state(None, None, lift=True)
         learn = oname == "mixed" and args.learn_compare_steps > 0
         if learn:
-            c2.mlp_setup(hidden=256, seed=0, max_pairs=args.mlp_pairs)
+            c2.mlp_setup(hidden=256, seed=0, max_pairs=args.mlp_pairs, neighbors=args.mlp_neighbors)
             c2.mlp_set_recording(True)
         r = dirk_steps_timed(c2, n_dirk, dt, uu, qq, hh, st)
         r["rel_l2_u_vs_primary_end_state"] = float((uu - primary_end).norm() / primary_end.norm())
@@ -1315,6 +1315,8 @@ def main():
                     help="skip the comparison forms (mixed / learned / FP64)")
     ap.add_argument("--mlp-epochs", type=int, default=200)
     ap.add_argument("--mlp-pairs", type=int, default=64, help="recorded (residual, error) pairs per training run")
+    ap.add_argument("--mlp-neighbors", type=int, default=0,
+                    help="learned correction: 1 adds the neighbouring faces' block-Jacobi outputs to the input")
     ap.add_argument("--learn-compare-steps", type=int, default=1,
                     help="tgv: DIRK steps on which the learned correction is compared (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="tgv: Newton steps of the host-buffer (e2e) timing")

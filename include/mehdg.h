@@ -311,9 +311,11 @@ int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
 /* Learned preconditioner correction (preconditioner kind 2).  No counterpart in the
  * paper (spec addition): FGMRES tolerates a variable preconditioner (Sec. 4.2),
  * so the block-Jacobi output z0 is corrected face by face,
- *   z_f = z0_f + |z0_f| MLP(r_f/|r_f|, z0_f/|z0_f|),
+ *   z_f = z0_f + |z0_f| MLP(r_f/|r_f|, z0_f/|z0_f| [, z0_g/|z0_f| for the other faces g of
+ *                                                   the face's owner macro-elements]),
  * by a network n_in -> hidden (ReLU) -> hidden (ReLU) -> n_out (n_out = ns Nfn rounded up
- * to 32, n_in = 2 n_out) with BF16 weights, FP32 biases and FP32 accumulation.
+ * to 32, n_in = 2 n_out, or (2 + 2 (2d - 1)) n_out with neighbors != 0; absent neighbours
+ * of boundary faces are zeros) with BF16 weights, FP32 biases and FP32 accumulation.
  * mehdg_mlp_setup: allocate with seeded weights and room for max_pairs pairs.
  * mehdg_mlp_params: copy the FP32 master parameters to (set = 0) or from (set = 1)
  *   host memory, packed [W1 (h x n_in), b1, W2 (h x h), b2, W3 (n_out x h), b3];
@@ -332,7 +334,7 @@ int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int Nu, int Nfn,
  * learned correction with the multi-level preconditioner on one resident problem.
  * Kind 2 needs mehdg_mlp_setup first.  Returns MEHDG_ERR_ARG otherwise. */
 int mehdg_set_precond(mehdg_ctx* ctx, int kind);
-int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long seed, int max_pairs);
+int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long seed, int max_pairs, int neighbors);
 int mehdg_mlp_params(mehdg_ctx* ctx, int set, float* host, long long* count);
 int mehdg_mlp_record(mehdg_ctx* ctx, const double* r, const double* e);
 int mehdg_mlp_set_recording(mehdg_ctx* ctx, int on, int* n_samples);

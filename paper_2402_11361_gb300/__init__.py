@@ -100,7 +100,7 @@ def load_library(path=LIB_PATH):
     lib.mehdg_phase_stats.argtypes = [c_void_p, P(c_double), P(c_longlong), I, I]
     lib.mehdg_launch_count.argtypes = [c_void_p, P(c_longlong)]
     lib.mehdg_graph_replays.argtypes = [c_void_p, P(c_longlong)]
-    lib.mehdg_mlp_setup.argtypes = [c_void_p, I, ctypes.c_ulonglong, I]
+    lib.mehdg_mlp_setup.argtypes = [c_void_p, I, ctypes.c_ulonglong, I, I]
     lib.mehdg_mlp_params.argtypes = [c_void_p, I, c_void_p, P(c_longlong)]
     lib.mehdg_mlp_record.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.mehdg_mlp_set_recording.argtypes = [c_void_p, I, P(c_int)]
@@ -395,13 +395,14 @@ class Context:
         self._check(self.lib.mehdg_set_precond(self.h, int(kind)), "set_precond")
         self.options["precond"] = int(kind)
 
-    def mlp_setup(self, hidden=256, seed=0, max_pairs=400):
-        self._check(self.lib.mehdg_mlp_setup(self.h, int(hidden), int(seed), int(max_pairs)), "mlp_setup")
+    def mlp_setup(self, hidden=256, seed=0, max_pairs=400, neighbors=0):
+        self._check(self.lib.mehdg_mlp_setup(self.h, int(hidden), int(seed), int(max_pairs), int(neighbors)),
+                    "mlp_setup")
         n = c_longlong()
         self._check(self.lib.mehdg_mlp_params(self.h, 0, None, ctypes.byref(n)), "mlp_params")
         self.mlp_nparams = n.value
         self.mlp_nout = ((self.info["ns"] * self.info["Nfn"] + 31) // 32) * 32
-        self.mlp_nin = 2 * self.mlp_nout
+        self.mlp_nin = (2 + (2 * (2 * self.info["dim"] - 1) if neighbors else 0)) * self.mlp_nout
         self.mlp_hidden = int(hidden)
 
     def mlp_params(self, values=None):

@@ -1,9 +1,12 @@
 // Learned preconditioner correction (preconditioner kind 2).  Not part of the
 // paper: FGMRES accepts a variable preconditioner (Sec. 4.2), so the block-Jacobi
 // output z0 = (A_uhuh)^-1 r is corrected face by face by a small network,
-//   z_f = z0_f + |z0_f| MLP(r_f / |r_f|, z0_f / |z0_f|),
+//   z_f = z0_f + |z0_f| MLP(r_f / |r_f|, z0_f / |z0_f| [, z0_g / |z0_f| for the faces g
+//                                                         of the face's owners]),
 // MLP: n_in -> hid (ReLU) -> hid (ReLU) -> n_out with n_out = ns Nfn rounded up to a
-// multiple of 32 and n_in = 2 n_out (the two normalised face vectors).  Weights are
+// multiple of 32 and n_in = 2 n_out (the two normalised face vectors), or (2 + 2 (2d - 1))
+// n_out with the neighbouring faces' block-Jacobi outputs (the error that block-Jacobi
+// leaves is carried by the coupling through the two owner macro-elements).  Weights are
 // stored in BF16 for the products, with FP32 master copies, FP32 biases and FP32
 // accumulation everywhere.  Training pairs (residual r, error e) come from the plain
 // FGMRES solves; the target of face f is (e_f - z0_f) / |z0_f|, what block-Jacobi
@@ -21,6 +24,8 @@ namespace {
 
 struct Mlp {
   int nin, nh, nout, nfb, F;
+  int nnb = 0;                   // neighbouring faces per face in the input (0: the face alone)
+  int* nbr = nullptr;            // [F][nnb] their face ids, -1 where absent
   long long np;                  // parameter count
   long long oW1, ob1, oW2, ob2, oW3, ob3;
   float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr;   // master params, grads, Adam moments
@@ -143,7 +148,8 @@ __global__ void k_to_bf16(const float* P, __nv_bfloat16* Ph, long long n) {
 // the target (e_f - z0_f)/|z0_f|
 __global__ void k_face_samples(const double* __restrict__ r, const double* __restrict__ e,
                                const double* __restrict__ z0, float* __restrict__ X, float* __restrict__ T,
-                               double* __restrict__ nrm, int nfb, int nin, int nout) {
+                               double* __restrict__ nrm, int nfb, int nin, int nout, const int* __restrict__ nbr,
+                               int nnb) {
   __shared__ double red[2][8];
   const int f = blockIdx.x;
   const double* rf = r + (size_t)f * nfb;
@@ -171,11 +177,17 @@ __global__ void k_face_samples(const double* __restrict__ r, const double* __res
   const double nz = sqrt(sz);
   const double iz = nz > 0.0 ? 1.0 / nz : 0.0;
   if (threadIdx.x == 0 && nrm) nrm[f] = nz;
-  const int half = nin / 2;
   for (int i = threadIdx.x; i < nin; i += blockDim.x) {
     float v = 0.f;
-    if (i < half) v = i < nfb ? (float)(rf[i] * ir) : 0.f;
-    else if (i - half < nfb) v = (float)(zf[i - half] * iz);
+    const int part = i / nout, j = i % nout;
+    if (j < nfb) {
+      if (part == 0) v = (float)(rf[j] * ir);
+      else if (part == 1) v = (float)(zf[j] * iz);
+      else {
+        const int g = nbr[(size_t)f * nnb + part - 2];
+        if (g >= 0) v = (float)(z0[(size_t)g * nfb + j] * iz);
+      }
+    }
     X[(size_t)f * nin + i] = v;
   }
   if (T)
@@ -281,7 +293,8 @@ void init_params(std::vector<float>& p, const Mlp& m, unsigned long long seed) {
 int mlp_apply(mehdg_ctx* ctx, const double* r, double* z) {
   Mlp* m = M_(ctx);
   if (!m) return ctx_fail(ctx, MEHDG_ERR_ARG, "preconditioner kind 2 needs mehdg_mlp_setup");
-  k_face_samples<<<m->F, 256, 0, ctx->stream>>>(r, nullptr, z, m->Xin, nullptr, m->nrm, m->nfb, m->nin, m->nout);
+  k_face_samples<<<m->F, 256, 0, ctx->stream>>>(r, nullptr, z, m->Xin, nullptr, m->nrm, m->nfb, m->nin, m->nout,
+                                                m->nbr, m->nnb);
   CKL();
   int rc;
   if ((rc = forward(ctx, m->Xin, m->F))) return rc;
@@ -305,20 +318,41 @@ int mlp_record_pair(mehdg_ctx* ctx, const double* r, const double* e) {
   double* z0 = ctx->iw;   // block-Jacobi output of r (scratch of the inner GMRES, idle here)
   if ((rc = precond_impl(ctx, 0, r, z0))) return rc;
   k_face_samples<<<m->F, 256, 0, ctx->stream>>>(r, e, z0, m->X + (size_t)m->count * m->nin,
-                                                m->T + (size_t)m->count * m->nout, nullptr, m->nfb, m->nin, m->nout);
+                                                m->T + (size_t)m->count * m->nout, nullptr, m->nfb, m->nin, m->nout,
+                                                m->nbr, m->nnb);
   CKL();
   m->count += m->F;
   return MEHDG_OK;
 }
 
-extern "C" int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long seed, int max_pairs) {
+extern "C" int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long seed, int max_pairs, int neighbors) {
   if (!ctx || hidden < 32 || hidden > 4096 || max_pairs < 1) return MEHDG_ERR_ARG;
   if (ctx->mlp) return ctx_fail(ctx, MEHDG_ERR_ARG, "MLP already set up");
   Mlp* m = new Mlp();
   m->nfb = ctx->nfb;
   m->F = ctx->F;
   m->nout = ((ctx->nfb + 31) / 32) * 32;
-  m->nin = 2 * m->nout;
+  // the other faces of the face's (one or two) owner macro-elements, from the owner and
+  // gather maps: owner o of face f is (e, fl), face fl' of e is gather[e][fl' Nfn] / (ns Nfn)
+  std::vector<int> nbr;
+  if (neighbors) {
+    const int nf = 2 * ctx->d;
+    m->nnb = 2 * (nf - 1);
+    nbr.assign((size_t)ctx->F * m->nnb, -1);
+    for (int f = 0; f < ctx->F; ++f) {
+      int k = 0;
+      for (int o = 0; o < 2; ++o) {
+        const int ow = ctx->h_owner[2 * f + o];
+        if (ow < 0) { k += nf - 1; continue; }
+        const int e = ow / nf, fl = ow % nf;
+        for (int g = 0; g < nf; ++g) {
+          if (g == fl) continue;
+          nbr[(size_t)f * m->nnb + k++] = ctx->h_gather[(size_t)e * ctx->Nt + (size_t)g * ctx->Nfn] / (ctx->ns * ctx->Nfn);
+        }
+      }
+    }
+  }
+  m->nin = (2 + m->nnb) * m->nout;
   m->nh = hidden;
   m->oW1 = 0;
   m->ob1 = m->oW1 + (long long)m->nh * m->nin;
@@ -353,7 +387,9 @@ extern "C" int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long se
   rc |= al((void**)&m->Xin, sizeof(float) * (size_t)m->F * m->nin);
   rc |= al((void**)&m->nrm, sizeof(double) * m->F);
   rc |= al((void**)&m->dloss, sizeof(double));
+  if (m->nnb) rc |= al((void**)&m->nbr, sizeof(int) * nbr.size());
   if (rc) return rc;
+  if (m->nnb) CK(cudaMemcpy(m->nbr, nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice));
   std::vector<float> p(m->np);
   init_params(p, *m, seed);
   CK(cudaMemcpy(m->P, p.data(), sizeof(float) * m->np, cudaMemcpyHostToDevice));
@@ -448,7 +484,7 @@ void mlp_destroy(mehdg_ctx* ctx) {
   Mlp* m = M_(ctx);
   if (!m) return;
   void* ptrs[] = {m->P, m->G, m->Mm, m->Vv, m->Ph, m->X, m->T, m->H1, m->H2, m->dH1, m->dH2, m->Y, m->dY, m->Xin,
-                  m->nrm, m->dloss};
+                  m->nrm, m->dloss, m->nbr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete m;

@@ -581,7 +581,7 @@ def test_mlp_gradient_matches_oracle(lib):
     from oracle import mlp as omlp
     pr = W.mms(dim=2, nmac=2, m=2, p=2)
     ctx = lib.Context(pr)
-    ctx.mlp_setup(hidden=64, seed=3)
+    ctx.mlp_setup(hidden=64, seed=3, neighbors=1)
     nin, hid, nout = ctx.mlp_nin, ctx.mlp_hidden, ctx.mlp_nout
     rng = np.random.default_rng(8)
     p = (rng.normal(size=ctx.mlp_nparams) * 0.2).astype(np.float32)
