@@ -437,6 +437,36 @@ def global_assemble(P, u, q, uh, tt=None, want_jac=True):
     return blks, geos, norms, RUh_g
 
 
+def flow_integrals(P, u, q):
+    """Volume integrals behind the Taylor-Green diagnostics of Sec. 5.3, by the method's own
+    volume quadrature (geo.T[0] values, geo.w physical weights) on every macro-element:
+
+        K = int rho |v|^2 / 2,   Z = int rho (omega . omega) / 2,   V = int 1,
+
+    with v = m / rho and omega = curl v (the scalar d_1 v_2 - d_2 v_1 in 2D).  The velocity
+    gradient is taken from the HDG gradient q = grad u (eq. C5a): d_j v_i = (q[j, 1+i] -
+    v_i q[j, 0]) / rho.  Eq. C5321 gives the dissipation rate eps = 2 mu Z / V; the kinetic
+    energy per unit volume is K / V."""
+    d = P.d
+    K = Z = V = 0.0
+    for e in range(P.E):
+        geo = P.geometry(e)
+        U = u[e] @ geo.T[0].T                                   # [ns, G]
+        Q = np.einsum("jsa,ga->jsg", q[e], geo.T[0])            # [d, ns, G]
+        rho = U[0]
+        v = U[1:1 + d] / rho
+        gv = np.array([[(Q[j, 1 + i] - v[i] * Q[j, 0]) / rho for j in range(d)]
+                       for i in range(d)])                      # gv[i, j] = d_j v_i
+        if d == 3:
+            om = np.array([gv[2, 1] - gv[1, 2], gv[0, 2] - gv[2, 0], gv[1, 0] - gv[0, 1]])
+        else:
+            om = np.array([gv[1, 0] - gv[0, 1]])
+        K += np.sum(geo.w * 0.5 * rho * np.sum(v * v, axis=0))
+        Z += np.sum(geo.w * 0.5 * rho * np.sum(om * om, axis=0))
+        V += np.sum(geo.w)
+    return K, Z, V
+
+
 def linear_step(P, blks, geos, shift=0.0, precond=0, rtol=1e-10, atol=0.0, restart=30,
                 maxit=2000, inner=5):
     """One Newton linear solve by condensation + FGMRES + recovery (Algorithm 1)."""

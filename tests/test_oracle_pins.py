@@ -686,6 +686,134 @@ def test_tgv_initial_state_closed_form():
     assert abs(prim(X)[0].mean() - 1.0) < 1e-14
 
 
+# ---------------------------------------------------------------- Taylor-Green diagnostics (eq. C5321)
+
+def _box_moment(lo, hi, powers):
+    """int over the box of prod_k x_k^a_k, in closed form."""
+    out = 1.0
+    for a, b, n in zip(lo, hi, powers):
+        out *= (b ** (n + 1) - a ** (n + 1)) / (n + 1)
+    return out
+
+
+def _linear_flow_state(P, rho_c, rho_g, A, b):
+    """u at the nodes and the exact q = grad u for rho = rho_c + rho_g . x, v = A x + b
+    (energy component and its gradient zero: the diagnostics do not read them)."""
+    d = P.d
+    u = np.zeros((P.E, P.ns, P.Np))
+    q = np.zeros((P.E, d, P.ns, P.Np))
+    for e in range(P.E):
+        x = P.geometry(e).xn
+        rho = rho_c + rho_g @ x
+        v = A @ x + b[:, None]
+        u[e, 0] = rho
+        u[e, 1:1 + d] = rho * v
+        for j in range(d):
+            q[e, j, 0] = rho_g[j]
+            q[e, j, 1:1 + d] = rho_g[j] * v + rho * A[:, j][:, None]   # d_j (rho v_i)
+    return u, q
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_flow_integrals_of_linear_velocity_fields(d):
+    """Polynomial states the p = 2 space holds exactly, integrals in closed form.
+    (a) rho constant, v = A x + b: K = rho/2 int |A x + b|^2 (box moments), Z = rho/2 |curl A|^2
+    |Omega|.  (b) rho linear (m = rho v quadratic): the velocity gradient d_j v_i = A_ij is
+    recovered exactly from q = grad u only with the - v_i d_j rho term, so Z = |curl A|^2 / 2
+    int rho = |curl A|^2 / 2 rho(centre) |Omega|.  A is not symmetric (curl A != 0)."""
+    pr = W.mms(dim=d, nmac=2, m=2, p=2)
+    P = solve.Problem(pr)
+    lo, hi = pr["lo"][:d], pr["hi"][:d]
+    vol = _box_moment(lo, hi, [0] * d)
+    rng = np.random.default_rng(17 + d)
+    A = rng.uniform(-1, 1, size=(d, d))
+    b = rng.uniform(-1, 1, size=d)
+    if d == 3:
+        curl = np.array([A[2, 1] - A[1, 2], A[0, 2] - A[2, 0], A[1, 0] - A[0, 1]])
+    else:
+        curl = np.array([A[1, 0] - A[0, 1]])
+    # (a)
+    rho0 = 1.3
+    u, q = _linear_flow_state(P, rho0, np.zeros(d), A, b)
+    K, Z, V = solve.flow_integrals(P, u, q)
+    Kx = 0.0
+    for i in range(d):
+        for j in range(d):
+            for k in range(d):
+                pw = [0] * d
+                pw[j] += 1
+                pw[k] += 1
+                Kx += A[i, j] * A[i, k] * _box_moment(lo, hi, pw)
+            pw = [0] * d
+            pw[j] = 1
+            Kx += 2.0 * b[i] * A[i, j] * _box_moment(lo, hi, pw)
+        Kx += b[i] * b[i] * vol
+    Kx *= 0.5 * rho0
+    assert abs(V - vol) < 1e-14 * vol
+    assert abs(K - Kx) < 1e-13 * abs(Kx), (K, Kx)
+    assert abs(Z - 0.5 * rho0 * curl @ curl * vol) < 1e-13 * Z
+    # (b)
+    rg = np.array([0.1, -0.07, 0.05][:d])
+    u, q = _linear_flow_state(P, 1.0, rg, A, b)
+    K, Z, V = solve.flow_integrals(P, u, q)
+    centre = 0.5 * (np.array(lo) + np.array(hi))
+    assert abs(Z - 0.5 * curl @ curl * (1.0 + rg @ centre) * vol) < 1e-13 * Z
+    # without the density-gradient term the recovered gradient (hence Z) is wrong
+    q_bad = q.copy()
+    q_bad[:, :, 0] = 0.0
+    assert abs(solve.flow_integrals(P, u, q_bad)[1] - Z) > 1e-4 * Z
+
+
+def test_flow_integrals_rigid_rotation_on_the_curved_shell():
+    """On the isoparametric shell a rigid rotation v = W x (W skew, angular velocity w) lies in
+    the mapped space, so curl v = 2 w at every point: Z / V = 2 rho |w|^2 to rounding; and
+    K = rho |w|^2 / 3 int r^2 converges to its closed form 4 pi rho |w|^2 (r1^5 - r0^5) / 15."""
+    r0, r1, rho0 = 0.5, 1.0, 1.1
+    w = np.array([0.3, -0.2, 0.5])
+    W_ = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    Kx = 4.0 * np.pi * rho0 * (w @ w) * (r1 ** 5 - r0 ** 5) / 15.0
+    errs = []
+    for nq in (2, 4):
+        P = solve.Problem(W.sphere(nq=nq, nr=1, m=1, p=2, r0=r0, r1=r1, ratio=1.0))
+        u, q = _linear_flow_state(P, rho0, np.zeros(3), W_, np.zeros(3))
+        K, Z, V = solve.flow_integrals(P, u, q)
+        assert abs(Z / V - 2.0 * rho0 * (w @ w)) < 1e-13
+        errs.append(abs(K / Kx - 1.0))
+    assert errs[0] < 1e-2 and errs[1] < errs[0] / 8.0, errs
+
+
+def test_flow_integrals_of_the_tgv_initial_state_converge():
+    """Sec. 5.3 (eq. C5321 at t = 0): the integrals of the lifted initial state (nodal
+    interpolation, q from R_Q = 0) converge to those of the closed-form field, K / V -> mean
+    of rho |v|^2 / 2 and Z / V -> mean of rho |omega|^2 / 2 with the hand-derived vorticity
+    omega = V0 (-cos x sin y sin z, -sin x cos y sin z, 2 sin x sin y cos z).  The exact means
+    come from the trapezoidal rule on a 24^3 periodic grid (exact for these trigonometric
+    polynomials); their incompressible limits are 1/8 and 3/8 of V0^2.  Observed rate about 4."""
+    g, V0 = 1.4, 0.1
+    n = 24
+    t = np.arange(n) * 2 * np.pi / n
+    X = np.array(np.meshgrid(t, t, t, indexing="ij")).reshape(3, -1)
+    ue = fields.tgv_u(X, V0, g)
+    rho = ue[0]
+    v = ue[1:4] / rho
+    x, y, z = X
+    om = V0 * np.array([-np.cos(x) * np.sin(y) * np.sin(z), -np.sin(x) * np.cos(y) * np.sin(z),
+                        2 * np.sin(x) * np.sin(y) * np.cos(z)])
+    Kx = (0.5 * rho * (v * v).sum(0)).mean()
+    Zx = (0.5 * rho * (om * om).sum(0)).mean()
+    assert abs(Kx / V0 ** 2 - 0.125) < 1e-3 and abs(Zx / V0 ** 2 - 0.375) < 1e-3
+    errs = []
+    for nm in (2, 4):
+        P = solve.Problem(W.tgv(nmac=nm, Re=100.0))
+        u, q, _ = solve.initial_state(P, lift=True)
+        K, Z, V = solve.flow_integrals(P, u, q)
+        assert abs(V / (2 * np.pi) ** 3 - 1.0) < 1e-13
+        errs.append((abs(K / V / Kx - 1.0), abs(Z / V / Zx - 1.0)))
+    assert errs[1][0] < 3e-3 and errs[1][1] < 3e-3, errs
+    for i in range(2):
+        assert errs[0][i] / errs[1][i] > 8.0, errs
+
+
 # ---------------------------------------------------------------- convergence rates
 
 def _init_from_field(P, ufun, qfun):
