@@ -959,6 +959,84 @@ def run_mpsweep(args, ws, rank, lrank):
             "sweep": rows}
 
 
+def run_dissipation(args, ws, rank, lrank):
+    """The paper's accuracy study of Sec. 5.3 on this GPU: the Taylor-Green vortex at Re = 100
+    (M0 = 0.1, (m, p) = (2, 2)) integrated by DIRK3 on two macro meshes, with the kinetic energy
+    E_k and the dissipation rate eps of eq. C5321 (mehdg_flow_integrals) after every DIRK step,
+    in the scaling rho_0 = L = V0 = 1 over t / t_c.  The ExaDG reference curves are not
+    available: reported are the self-convergence between the meshes (largest difference of eps
+    over the run, with the value at the coarse mesh's peak) and, per mesh, the gap between eps
+    and -dE_k/dt (central differences), which is the compressible and numerical dissipation
+    that eq. C5321 leaves out.  Mixed form (FP64 residuals, Newton to 1e-8)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2402_11361_gb300 as pkg
+    dev = torch.device("cuda:%d" % lrank)
+    torch.cuda.set_device(dev)
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
+    st_ = torch.cuda.current_stream(dev)
+    V0 = 0.1
+    dt_c = args.diss_dt
+    n_steps = int(round(args.diss_tend / dt_c))
+    opt = dict(precision=pkg.PREC_MIXED, precond=1, apply_mode=1, precond_bf16=args.precond_bf16,
+               restart=args.restart, max_iters=3000, lin_rtol=args.lin_rtol, newton_rtol=1e-8, newton_atol=1e-14,
+               max_newton=60, inner_iters=args.inner, refine_iters=args.refine, tc_mode=args.tc_mode)
+    runs = {}
+    t_total = 0.0
+    newton_total = 0
+    for nm in [int(x) for x in args.diss_nmac.split(",")]:
+        pr = W.tgv(nmac=nm, m=2, p=2, Re=args.diss_re, M0=V0)
+        ctx = pkg.Context(pr, opt, device=dev)
+        u, q, uh = ctx.init_state(None, None, lift=True)
+        ek, eps = ctx.tgv_diagnostics(u, q, V0)
+        series = [[0.0, ek, eps]]
+        newton = fg = status = 0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(st_)
+        for n in range(n_steps):
+            for stage in (1, 2, 3):
+                r = ctx.dirk_stage(stage, dt_c / V0, u, q, uh)
+                newton += r["newton_steps"]
+                fg += r["fgmres_iters"]
+                status |= r["status"]
+            ek, eps = ctx.tgv_diagnostics(u, q, V0)
+            series.append([(n + 1) * dt_c, ek, eps])
+        ev1.record(st_)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        t_total += t
+        newton_total += newton
+        ctx.close()
+        ser = np.array(series)
+        dek = np.full(len(ser), np.nan)
+        dek[1:-1] = -(ser[2:, 1] - ser[:-2, 1]) / (2 * dt_c)
+        ipk = int(np.argmax(ser[:, 2]))
+        gap = np.nanmax(np.abs(dek - ser[:, 2]))
+        runs[nm] = dict(macros=nm ** 3, n_eff=nm * 2 * 2, dirk_steps=n_steps, newton_steps=newton,
+                        fgmres_iters=fg, fallback=bool(status & 1), time_s=t,
+                        eps_peak=float(ser[ipk, 2]), t_peak=float(ser[ipk, 0]),
+                        max_abs_eps_minus_dEk=float(gap),
+                        series=[[round(a, 6), float(b), float(c), None if np.isnan(d) else float(d)]
+                                for (a, b, c), d in zip(series, dek)])
+    keys = sorted(runs)
+    conv = None
+    if len(keys) >= 2:
+        a, b = np.array(runs[keys[0]]["series"], dtype=float), np.array(runs[keys[-1]]["series"], dtype=float)
+        conv = dict(max_abs_eps_difference=float(np.max(np.abs(a[:, 2] - b[:, 2]))),
+                    max_abs_Ek_difference=float(np.max(np.abs(a[:, 1] - b[:, 1]))),
+                    eps_peak_fine=runs[keys[-1]]["eps_peak"])
+    return {"metric": "TGV kinetic-energy dissipation rate eps(t) (eq. C5321)", "value": t_total / max(newton_total, 1),
+            "unit": "s per Newton step", "n_gpus": ws, "steps": n_steps, "warmup": 0, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 residuals, f32 blocks",
+            "data": "synthetic (closed-form TGV initial condition)",
+            "config": {"workload": "Taylor-Green vortex Re %g, M0 0.1, (m, p) = (2, 2), macro meshes %s, dt %g t_c, "
+                                   "t_end %g t_c" % (args.diss_re, args.diss_nmac, dt_c, args.diss_tend),
+                       "precision": "mixed", "newton_rtol": 1e-8},
+            "series_columns": ["t/t_c", "E_k/V0^2", "eps L/V0^3", "-dE_k/dt L/V0^3"],
+            "runs": {str(k): v for k, v in runs.items()}, "self_convergence": conv}
+
+
 def run_layers(args, ws, rank, lrank):
     """The paper's Table-4 comparison on this GPU: one-layer (eqs. C46-C47) against second-layer
     (eqs. AP12, ASC2) static condensation, FP64, on a 3D manufactured-solution cube of p = 1
@@ -1287,7 +1365,8 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed steps (default: 10 Newton steps for tgv)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched", "layers", "sphere", "mpsweep"],
+    ap.add_argument("--workload", default="tgv", choices=["tgv", "mms", "batched", "layers", "sphere", "mpsweep",
+                                                  "dissipation"],
                     help="tgv: Newton steps of the 16^3 Taylor-Green DIRK integration (default, the headline); "
                          "mms: steady 3D manufactured solution (8^3); batched: independent uneven problems")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
@@ -1328,6 +1407,10 @@ def main():
     ap.add_argument("--nmac-sweep", type=int, default=3, help="mpsweep workload: macro-elements per cube edge")
     ap.add_argument("--sphere-nq", type=int, default=8, help="sphere workload: cells per cube-panel edge")
     ap.add_argument("--sphere-nr", type=int, default=0, help="sphere workload: radial layers (default 12)")
+    ap.add_argument("--diss-nmac", default="4,8", help="dissipation workload: macro-elements per edge, per mesh")
+    ap.add_argument("--diss-re", type=float, default=100.0, help="dissipation workload: Reynolds number V0 L / nu")
+    ap.add_argument("--diss-dt", type=float, default=0.1, help="dissipation workload: DIRK step in t_c = L / V0")
+    ap.add_argument("--diss-tend", type=float, default=10.0, help="dissipation workload: end time in t_c")
     ap.add_argument("--sphere-apply-mode", type=int, default=0,
                     help="sphere workload, FP64 form: 0 dense Algorithm 2 (default)")
     args = ap.parse_args()
@@ -1344,10 +1427,10 @@ def main():
     if ws > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("tgv", "batched", "layers", "sphere", "mpsweep"):
+    if args.workload in ("tgv", "batched", "layers", "sphere", "mpsweep", "dissipation"):
         args.steps = args.steps or 10
         run = {"tgv": run_tgv, "batched": run_batched, "layers": run_layers, "sphere": run_sphere,
-               "mpsweep": run_mpsweep}[args.workload]
+               "mpsweep": run_mpsweep, "dissipation": run_dissipation}[args.workload]
         line = run(args, ws, rank, lrank)
         if rank == 0:
             if args.workload == "tgv" and args.cpu and ws == 1:   # the oracle baseline, N = 1 only

@@ -192,6 +192,18 @@ int mehdg_query(const mehdg_ctx* ctx, mehdg_info* info);
 int mehdg_init_state(mehdg_ctx* ctx, const double* du_pert, const double* duh_pert,
                      int lift, double* u, double* q, double* uhat);
 
+/* Taylor-Green diagnostics (Sec. 5.3, eq. C5321) of a state, by the volume quadrature of the
+ * method (the Gauss points of every sub-element; the curved weights on shell meshes):
+ * out[0] = int rho |v|^2 / 2, out[1] = int rho (omega . omega) / 2, out[2] = int 1, with
+ * v = m / rho and omega = curl v (2D: the scalar d_1 v_2 - d_2 v_1) taken from the HDG
+ * gradient, d_j v_i = (q_{j,1+i} - v_i q_{j,0}) / rho.  The dissipation rate of eq. C5321 is
+ * eps = 2 mu out[1] / out[2] (mu = 1 / Re in the problem's units), the kinetic energy per
+ * unit volume out[0] / out[2].  u [E][ns][Np] and q [E][d][ns][Np]: device state (FP64 in
+ * both precisions), read only; out: host double[3].  The sums run in a fixed order (the
+ * same state gives the same bits).  Synchronises the context's stream.  Errors: ARG (null
+ * pointer), CUDA. */
+int mehdg_flow_integrals(mehdg_ctx* ctx, const double* u, const double* q, double* out);
+
 /* a1-a2 -- residuals R_Q, R_U, R_Uhat (eq. C31221 from C38 / C242) and the Newton
  * blocks of eq. C312 of every macro-element at (u, q, uhat).  tt may be NULL
  * (steady).  res_norms: host double[4] = |R_Q|, |R_U|, |R_Uhat|, |R_F| (global

@@ -23,7 +23,7 @@ EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_loca
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
            "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_lu_queue", "mehdg_graph_replays", "mehdg_batch_create",
            "mehdg_batch_size", "mehdg_batch_context", "mehdg_batch_steady_solve", "mehdg_batch_tiles",
-           "mehdg_batch_graph_replays", "mehdg_batch_last_error", "mehdg_batch_destroy", "mehdg_destroy",
+           "mehdg_batch_graph_replays", "mehdg_batch_last_error", "mehdg_batch_destroy", "mehdg_flow_integrals", "mehdg_destroy",
            "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
@@ -302,6 +302,19 @@ class Context:
         self._check(self.lib.mehdg_init_state(self.h, self._ptr(du), self._ptr(duh), int(lift), self._ptr(u),
                                               self._ptr(q), self._ptr(uh)), "init_state")
         return u, q, uh
+
+    def flow_integrals(self, u, q):
+        """(int rho |v|^2 / 2, int rho |curl v|^2 / 2, int 1) of the state (mehdg_flow_integrals)."""
+        out = (c_double * 3)()
+        self._check(self.lib.mehdg_flow_integrals(self.h, self._ptr(u), self._ptr(q), out), "flow_integrals")
+        return tuple(out)
+
+    def tgv_diagnostics(self, u, q, V0):
+        """Kinetic energy per unit volume and the dissipation rate of eq. C5321 in the Taylor-Green
+        scaling (rho_0 = L = 1): E_k / V0^2 and eps / (V0^3 / L), with mu = 1 / Re of the problem."""
+        K, Z, V = self.flow_integrals(u, q)
+        mu = 1.0 / self.prob["Re"]
+        return K / V / V0 ** 2, 2.0 * mu * Z / V / V0 ** 3
 
     def assemble(self, u, q, uh, coef=0.0, hist=None, supg_time=0):
         norms = (c_double * 4)()

@@ -1005,6 +1005,120 @@ int assemble_bt(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
 }
 
+// ---------------------------------------------------------------- flow diagnostics (Sec. 5.3)
+// Per macro-element (one CTA): the integrals of rho |v|^2 / 2, rho (omega . omega) / 2 and 1 by the
+// volume quadrature, threads striding over the (sub-element, Gauss point) pairs.  v = m / rho and
+// omega = curl v, with the velocity gradient from the HDG gradient q = grad u: d_j v_i = (q_{j,1+i}
+// - v_i q_{j,0}) / rho.  Only rho and the momentum are interpolated.  The CTA's sums are reduced by a
+// fixed tree into part[e][3] (blockDim.x == FD_NT).
+constexpr int FD_NT = 128;
+
+template <int D, int P>
+__global__ void __launch_bounds__(FD_NT) k_flow_diag(Geo g, const double* __restrict__ tab,
+                                                     const double* __restrict__ u, const double* __restrict__ q,
+                                                     const double* __restrict__ vgeo, double* __restrict__ part) {
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  __shared__ double sb[NG1 * P1], sw[NG1];
+  __shared__ double red[3][FD_NT];
+  const int e = blockIdx.x;
+  for (int i = threadIdx.x; i < NG1 * P1; i += blockDim.x) sb[i] = tab[i];
+  for (int i = threadIdx.x; i < NG1; i += blockDim.x) sw[i] = tab[2 * NG1 * P1 + i];
+  __syncthreads();
+  const size_t Np = g.Np;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int pt = threadIdx.x; pt < g.nel * NG; pt += blockDim.x) {
+    const int el = pt / NG, gq = pt % NG;
+    int gi[D], li[D];
+    double wq = 1.0;
+    {
+      int gg = gq, ll = el;
+      for (int k = 0; k < D; ++k) {
+        gi[k] = gg % NG1; gg /= NG1;
+        li[k] = ll % g.m; ll /= g.m;
+        wq *= sw[gi[k]] * 0.5 * g.he[k];
+      }
+    }
+    if (vgeo) wq = vgeo[(((size_t)e * g.nel + el) * NG + gq) * (D * D + 1) + D * D];
+    double U[D + 1], Q[D][D + 1];
+    for (int s = 0; s <= D; ++s) {
+      U[s] = 0.0;
+      for (int j = 0; j < D; ++j) Q[j][s] = 0.0;
+    }
+    for (int al = 0; al < NLOC; ++al) {
+      int a = 0, aa = al, stride = 1;
+      double phi = 1.0;
+      for (int k = 0; k < D; ++k) {
+        const int ak = aa % P1;
+        aa /= P1;
+        a += (li[k] * P + ak) * stride;
+        stride *= g.n1;
+        phi *= sb[gi[k] * P1 + ak];
+      }
+      for (int s = 0; s <= D; ++s) {
+        U[s] += phi * u[((size_t)e * NS + s) * Np + a];
+        for (int j = 0; j < D; ++j) Q[j][s] += phi * q[(((size_t)e * D + j) * NS + s) * Np + a];
+      }
+    }
+    const double rho = U[0];
+    double v[D], gv[D][D], v2 = 0.0;
+    for (int i = 0; i < D; ++i) {
+      v[i] = U[1 + i] / rho;
+      v2 += v[i] * v[i];
+    }
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) gv[i][j] = (Q[j][1 + i] - v[i] * Q[j][0]) / rho;
+    double w2;
+    if constexpr (D == 3) {
+      const double o0 = gv[2][1] - gv[1][2], o1 = gv[0][2] - gv[2][0], o2 = gv[1][0] - gv[0][1];
+      w2 = o0 * o0 + o1 * o1 + o2 * o2;
+    } else {
+      const double o = gv[1][0] - gv[0][1];
+      w2 = o * o;
+    }
+    acc[0] += wq * 0.5 * rho * v2;
+    acc[1] += wq * 0.5 * rho * w2;
+    acc[2] += wq;
+  }
+  for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int h = FD_NT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) part[(size_t)e * 3 + k] = red[k][0];
+}
+
+// out[k] = sum_e part[e][k], one CTA of FD_NT threads, fixed order
+__global__ void __launch_bounds__(FD_NT) k_flow_diag_sum(const double* __restrict__ part, int E,
+                                                         double* __restrict__ out) {
+  __shared__ double red[3][FD_NT];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int e = threadIdx.x; e < E; e += blockDim.x)
+    for (int k = 0; k < 3; ++k) acc[k] += part[(size_t)e * 3 + k];
+  for (int k = 0; k < 3; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int h = FD_NT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+template <int D, int P>
+int flow_diag_dp(mehdg_ctx* ctx, const double* u, const double* q) {
+  Geo g = make_geo(ctx);
+  k_flow_diag<D, P><<<ctx->E, FD_NT, 0, ctx->stream>>>(g, ctx->tab, u, q, ctx->mapped ? ctx->vgeo : nullptr,
+                                                        ctx->ddiag);
+  CKL();
+  k_flow_diag_sum<<<1, FD_NT, 0, ctx->stream>>>(ctx->ddiag, ctx->E, ctx->ddiag + (size_t)ctx->E * 3);
+  CKL();
+  return MEHDG_OK;
+}
+
 }  // namespace
 
 int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt,
@@ -1036,4 +1150,23 @@ extern "C" int mehdg_assemble_local(mehdg_ctx* ctx, const double* u, const doubl
                                     const mehdg_time_term* tt, double* res_norms) {
   if (!ctx || !u || !q || !uhat) return MEHDG_ERR_ARG;
   return assemble_all(ctx, u, q, uhat, tt, res_norms);
+}
+
+extern "C" int mehdg_flow_integrals(mehdg_ctx* ctx, const double* u, const double* q, double* out) {
+  if (!ctx || !u || !q || !out) return MEHDG_ERR_ARG;
+  const int d = ctx->d, p = ctx->p;
+  int rc;
+  if (d == 2 && p == 1) rc = flow_diag_dp<2, 1>(ctx, u, q);
+  else if (d == 2 && p == 2) rc = flow_diag_dp<2, 2>(ctx, u, q);
+  else if (d == 2 && p == 3) rc = flow_diag_dp<2, 3>(ctx, u, q);
+  else if (d == 3 && p == 1) rc = flow_diag_dp<3, 1>(ctx, u, q);
+  else if (d == 3 && p == 2) rc = flow_diag_dp<3, 2>(ctx, u, q);
+  else if (d == 3 && p == 3) rc = flow_diag_dp<3, 3>(ctx, u, q);
+  else return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
+  if (rc) return rc;
+  double* h = ctx->hred;
+  CK(cudaMemcpyAsync(h, ctx->ddiag + (size_t)ctx->E * 3, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < 3; ++k) out[k] = h[k];
+  return MEHDG_OK;
 }

@@ -112,6 +112,7 @@ struct mehdg_ctx {
   int nfb = 0;
   int* dflag = nullptr;      // device status words
   double* dred = nullptr;    // reduction scratch
+  double* ddiag = nullptr;   // per-macro partial sums of mehdg_flow_integrals, [E][3] + 4
   double* hred = nullptr;    // pinned host mirror
 
   float *Wk32 = nullptr, *Whk32 = nullptr;   // FP32 copies of W_k, Wh_k (mixed precision)

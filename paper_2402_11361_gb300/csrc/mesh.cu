@@ -801,6 +801,7 @@ static int setup(mehdg_ctx* ctx) {
   ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
   if (!ctx->dflag) ALLOC(ctx->dflag, 16);
   ALLOC(ctx->dred, 1 << 17);
+  ALLOC(ctx->ddiag, (size_t)E * 3 + 4);
   CK(cudaMemsetAsync(ctx->dred, 0, sizeof(double) << 17, st));   // reduction tickets start at zero
   CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * 256));
   ALLOC(ctx->dtcerr, 4);
@@ -1092,7 +1093,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
                   ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->Aloc, ctx->Rloc, ctx->Xloc, ctx->permL, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16,
-                  ctx->vgeo, ctx->fgeo, ctx->xnode, ctx->ofn};
+                  ctx->vgeo, ctx->fgeo, ctx->xnode, ctx->ofn, ctx->ddiag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);
