@@ -52,80 +52,19 @@ __device__ __forceinline__ Tables<CT> tables(const CT* tab, int ng1, int p1) {
 // are mapped to physical ones, and the outputs are mapped back to d/dxi test and trial
 // derivatives (K'[1+j] = sum_k J^-1[j][k] K[1+k] on both sides), so that the contraction
 // kernels stay those of the reference element.
-template <int D, int P, class KT, class CT = double, int MODE = 0, bool MAPPED = false>
-__global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__ tab, Phys ph,
-                                                    const CT* __restrict__ u, const CT* __restrict__ q,
-                                                    const CT* __restrict__ hist, double coef, int supg_time,
-                                                    const CT* __restrict__ src, KT* __restrict__ Kvol,
-                                                    double* __restrict__ rvol, int E,
-                                                    const double* __restrict__ vgeo = nullptr) {
-  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
-  constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
-  constexpr int NDIR = (MODE == 2) ? 1 : NS * (1 + D);
+// Everything after the interpolation at one point for one input direction: the mapping of the
+// interpolated gradients (curved macros), the pointwise integrand on dual numbers and the
+// writes of the Jacobian columns and (MODE 0, direction 0; MODE 2) of the residual integrand.
+template <int D, int P, class KT, class CT, int MODE, bool MAPPED>
+__device__ __forceinline__ void vol_point_eval(const Geo& g, const Phys& ph, int e, int el, int gq, int dir, CT wq,
+                                               CT (&U)[D + 2], CT (&GU)[D + 2][D], CT (&Q)[D + 2][D],
+                                               CT (&GQ)[D + 2][D][D], const CT (&Hh)[D + 2], double coef,
+                                               int supg_time, const CT* __restrict__ src, KT* __restrict__ Kvol,
+                                               double* __restrict__ rvol, const double* __restrict__ vgeo) {
+  constexpr int NS = D + 2, NG1 = P + 2;
+  constexpr int NG = IPow<NG1, D>::v;
   constexpr int KA = (D + 1) * NS * (D + 1);
-  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int nel = g.nel;
-  if (tid >= (long long)E * nel * NG * NDIR) return;
-  const int dir = tid % NDIR;
-  long long r = tid / NDIR;
-  const int gq = r % NG;
-  r /= NG;
-  const int el = r % nel;
-  const int e = (int)(r / nel);
-  Tables<CT> tb = tables(tab, NG1, P1);
-
-  int gi[D], li[D];
-  CT wq = CT(1), he[D];
-  {
-    int gg = gq, ll = el;
-    for (int k = 0; k < D; ++k) {
-      gi[k] = gg % NG1; gg /= NG1;
-      li[k] = ll % g.m; ll /= g.m;
-      he[k] = (CT)g.he[k];
-      wq *= tb.gw[gi[k]] * CT(0.5) * he[k];
-    }
-  }
-  CT U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
-  for (int s = 0; s < NS; ++s) {
-    U[s] = CT(0); Hh[s] = CT(0);
-    for (int l = 0; l < D; ++l) {
-      GU[s][l] = CT(0);
-      for (int j = 0; j < D; ++j) { GQ[s][j][l] = CT(0); }
-      Q[s][l] = CT(0);
-    }
-  }
-  const size_t Np = g.Np;
-  for (int al = 0; al < NLOC; ++al) {
-    int ai[D], a = 0, aa = al, stride = 1;
-    for (int k = 0; k < D; ++k) {
-      ai[k] = aa % P1; aa /= P1;
-      a += (li[k] * P + ai[k]) * stride;
-      stride *= g.n1;
-    }
-    CT bv[D], dv[D];
-    for (int k = 0; k < D; ++k) {
-      bv[k] = tb.b1[gi[k] * P1 + ai[k]];
-      dv[k] = tb.db1[gi[k] * P1 + ai[k]] * CT(2) / he[k];
-    }
-    CT phi = CT(1), dphi[D];
-    for (int k = 0; k < D; ++k) phi *= bv[k];
-    for (int l = 0; l < D; ++l) {
-      dphi[l] = dv[l];
-      for (int k = 0; k < D; ++k)
-        if (k != l) dphi[l] *= bv[k];
-    }
-    for (int s = 0; s < NS; ++s) {
-      CT ua = u[((size_t)e * NS + s) * Np + a];
-      U[s] += phi * ua;
-      for (int l = 0; l < D; ++l) GU[s][l] += dphi[l] * ua;
-      if (hist) Hh[s] += phi * hist[((size_t)e * NS + s) * Np + a];
-      for (int j = 0; j < D; ++j) {
-        CT qa = q[(((size_t)e * D + j) * NS + s) * Np + a];
-        Q[s][j] += phi * qa;
-        for (int l = 0; l < D; ++l) GQ[s][j][l] += dphi[l] * qa;
-      }
-    }
-  }
   CT Ji[D][D];
   if constexpr (MAPPED) {
     const double* vg = vgeo + (((size_t)e * nel + el) * NG + gq) * (D * D + 1);
@@ -249,6 +188,225 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__
       }
     }
   }
+}
+
+template <int D, int P, class KT, class CT = double, int MODE = 0, bool MAPPED = false>
+__global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__ tab, Phys ph,
+                                                    const CT* __restrict__ u, const CT* __restrict__ q,
+                                                    const CT* __restrict__ hist, double coef, int supg_time,
+                                                    const CT* __restrict__ src, KT* __restrict__ Kvol,
+                                                    double* __restrict__ rvol, int E,
+                                                    const double* __restrict__ vgeo = nullptr) {
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  constexpr int NDIR = (MODE == 2) ? 1 : NS * (1 + D);
+  constexpr int KA = (D + 1) * NS * (D + 1);
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nel = g.nel;
+  if (tid >= (long long)E * nel * NG * NDIR) return;
+  const int dir = tid % NDIR;
+  long long r = tid / NDIR;
+  const int gq = r % NG;
+  r /= NG;
+  const int el = r % nel;
+  const int e = (int)(r / nel);
+  Tables<CT> tb = tables(tab, NG1, P1);
+
+  int gi[D], li[D];
+  CT wq = CT(1), he[D];
+  {
+    int gg = gq, ll = el;
+    for (int k = 0; k < D; ++k) {
+      gi[k] = gg % NG1; gg /= NG1;
+      li[k] = ll % g.m; ll /= g.m;
+      he[k] = (CT)g.he[k];
+      wq *= tb.gw[gi[k]] * CT(0.5) * he[k];
+    }
+  }
+  CT U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
+  for (int s = 0; s < NS; ++s) {
+    U[s] = CT(0); Hh[s] = CT(0);
+    for (int l = 0; l < D; ++l) {
+      GU[s][l] = CT(0);
+      for (int j = 0; j < D; ++j) { GQ[s][j][l] = CT(0); }
+      Q[s][l] = CT(0);
+    }
+  }
+  const size_t Np = g.Np;
+  for (int al = 0; al < NLOC; ++al) {
+    int ai[D], a = 0, aa = al, stride = 1;
+    for (int k = 0; k < D; ++k) {
+      ai[k] = aa % P1; aa /= P1;
+      a += (li[k] * P + ai[k]) * stride;
+      stride *= g.n1;
+    }
+    CT bv[D], dv[D];
+    for (int k = 0; k < D; ++k) {
+      bv[k] = tb.b1[gi[k] * P1 + ai[k]];
+      dv[k] = tb.db1[gi[k] * P1 + ai[k]] * CT(2) / he[k];
+    }
+    CT phi = CT(1), dphi[D];
+    for (int k = 0; k < D; ++k) phi *= bv[k];
+    for (int l = 0; l < D; ++l) {
+      dphi[l] = dv[l];
+      for (int k = 0; k < D; ++k)
+        if (k != l) dphi[l] *= bv[k];
+    }
+    for (int s = 0; s < NS; ++s) {
+      CT ua = u[((size_t)e * NS + s) * Np + a];
+      U[s] += phi * ua;
+      for (int l = 0; l < D; ++l) GU[s][l] += dphi[l] * ua;
+      if (hist) Hh[s] += phi * hist[((size_t)e * NS + s) * Np + a];
+      for (int j = 0; j < D; ++j) {
+        CT qa = q[(((size_t)e * D + j) * NS + s) * Np + a];
+        Q[s][j] += phi * qa;
+        for (int l = 0; l < D; ++l) GQ[s][j][l] += dphi[l] * qa;
+      }
+    }
+  }
+  vol_point_eval<D, P, KT, CT, MODE, MAPPED>(g, ph, e, el, gq, dir, wq, U, GU, Q, GQ, Hh, coef, supg_time, src,
+                                             Kvol, rvol, vgeo);
+}
+
+// The FP64 Jacobian pass with the interpolation shared by the input directions of a point: one
+// CTA takes VpCfg::PPB points with all NDIR directions of each.  The basis values and physical
+// derivatives of the points' sub-element nodes (phase 0), then u, grad u, q, grad q and the
+// history at each point (phase 1), are formed once in shared memory, with the operations of
+// k_vol_point in the same order (the same bits); each thread then runs the pointwise physics
+// of one direction (phase 2).  k_vol_point repeats the interpolation in all NDIR threads of a
+// point.
+template <int D> struct VpCfg {
+  static constexpr int NS = D + 2;
+  static constexpr int NDIR = NS * (1 + D);
+  static constexpr int PPB = 240 / NDIR;                 // D = 3: 12 points, D = 2: 20 points
+  static constexpr int NT = PPB * NDIR;                  // 240 threads
+  static constexpr int NV = NS * (2 + 2 * D + D * D);    // U, GU, Q, GQ, Hh of a point
+  // offsets in a point's row of values
+  static constexpr int OGU = NS, OQ = NS * (1 + D), OGQ = NS * (1 + 2 * D), OH = NS * (1 + 2 * D + D * D);
+};
+
+template <int D, int P, class KT, bool MAPPED>
+__global__ void __launch_bounds__(VpCfg<D>::NT) k_vol_point_sh(Geo g, const double* __restrict__ tab, Phys ph,
+                                                             const double* __restrict__ u,
+                                                             const double* __restrict__ q,
+                                                             const double* __restrict__ hist, double coef,
+                                                             int supg_time, const double* __restrict__ src,
+                                                             KT* __restrict__ Kvol, double* __restrict__ rvol,
+                                                             int E, const double* __restrict__ vgeo) {
+  typedef VpCfg<D> C;
+  constexpr int NS = D + 2, P1 = P + 1, NG1 = P + 2;
+  constexpr int NLOC = IPow<P1, D>::v, NG = IPow<NG1, D>::v;
+  constexpr int NDIR = C::NDIR, PPB = C::PPB, NGRP = D + 2;
+  __shared__ double sphi[PPB][NLOC][D + 1];   // phi and d phi / d x_l of each node of the point's sub-element
+  __shared__ int snode[PPB][NLOC];            // its macro node
+  __shared__ double sv[PPB][C::NV];
+  const int nel = g.nel;
+  const size_t Np = g.Np;
+  const long long npts = (long long)E * nel * NG;
+  const long long p0 = (long long)blockIdx.x * PPB;
+  Tables<double> tb = tables(tab, NG1, P1);
+  for (int i = threadIdx.x; i < PPB * NLOC; i += blockDim.x) {
+    const int pl = i / NLOC, al = i % NLOC;
+    const long long pt = p0 + pl;
+    if (pt >= npts) continue;
+    const int gq = (int)(pt % NG);
+    const int el = (int)((pt / NG) % nel);
+    int gi[D], li[D];
+    double he[D];
+    {
+      int gg = gq, ll = el;
+      for (int k = 0; k < D; ++k) {
+        gi[k] = gg % NG1; gg /= NG1;
+        li[k] = ll % g.m; ll /= g.m;
+        he[k] = g.he[k];
+      }
+    }
+    int a = 0, aa = al, stride = 1;
+    double bv[D], dv[D];
+    for (int k = 0; k < D; ++k) {
+      const int ak = aa % P1;
+      aa /= P1;
+      a += (li[k] * P + ak) * stride;
+      stride *= g.n1;
+      bv[k] = tb.b1[gi[k] * P1 + ak];
+      dv[k] = tb.db1[gi[k] * P1 + ak] * 2.0 / he[k];
+    }
+    double phi = 1.0, dphi[D];
+    for (int k = 0; k < D; ++k) phi *= bv[k];
+    for (int l = 0; l < D; ++l) {
+      dphi[l] = dv[l];
+      for (int k = 0; k < D; ++k)
+        if (k != l) dphi[l] *= bv[k];
+    }
+    sphi[pl][al][0] = phi;
+    for (int l = 0; l < D; ++l) sphi[pl][al][1 + l] = dphi[l];
+    snode[pl][al] = a;
+  }
+  __syncthreads();
+  // one task per (point, species, group): group 0 u (U, GU), 1 + j q_j (Q_j, GQ_j), D + 1 history
+  for (int i = threadIdx.x; i < PPB * NS * NGRP; i += blockDim.x) {
+    const int pl = i / (NS * NGRP), rr = i % (NS * NGRP);
+    const int sp = rr / NGRP, grp = rr % NGRP;
+    const long long pt = p0 + pl;
+    if (pt >= npts) continue;
+    const int e = (int)(pt / ((long long)nel * NG));
+    double* out = sv[pl];
+    if (grp == D + 1) {
+      double h = 0.0;
+      if (hist) {
+        const double* hs = hist + ((size_t)e * NS + sp) * Np;
+        for (int al = 0; al < NLOC; ++al) h += sphi[pl][al][0] * hs[snode[pl][al]];
+      }
+      out[C::OH + sp] = h;
+    } else {
+      const double* xs = grp == 0 ? u + ((size_t)e * NS + sp) * Np
+                                  : q + (((size_t)e * D + (grp - 1)) * NS + sp) * Np;
+      double v = 0.0, gv[D];
+      for (int l = 0; l < D; ++l) gv[l] = 0.0;
+      for (int al = 0; al < NLOC; ++al) {
+        const double x = xs[snode[pl][al]];
+        v += sphi[pl][al][0] * x;
+        for (int l = 0; l < D; ++l) gv[l] += sphi[pl][al][1 + l] * x;
+      }
+      if (grp == 0) {
+        out[sp] = v;
+        for (int l = 0; l < D; ++l) out[C::OGU + sp * D + l] = gv[l];
+      } else {
+        const int j = grp - 1;
+        out[C::OQ + sp * D + j] = v;
+        for (int l = 0; l < D; ++l) out[C::OGQ + (sp * D + j) * D + l] = gv[l];
+      }
+    }
+  }
+  __syncthreads();
+  const int pl = threadIdx.x / NDIR, dir = threadIdx.x % NDIR;
+  const long long pt = p0 + pl;
+  if (pl >= PPB || pt >= npts) return;
+  const int gq = (int)(pt % NG);
+  const int el = (int)((pt / NG) % nel);
+  const int e = (int)(pt / ((long long)nel * NG));
+  double wq = 1.0;
+  {
+    int gg = gq;
+    for (int k = 0; k < D; ++k) {
+      const int gk = gg % NG1;
+      gg /= NG1;
+      wq *= tb.gw[gk] * 0.5 * g.he[k];
+    }
+  }
+  double U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
+  const double* in = sv[pl];
+  for (int s2 = 0; s2 < NS; ++s2) {
+    U[s2] = in[s2];
+    Hh[s2] = in[C::OH + s2];
+    for (int j = 0; j < D; ++j) {
+      GU[s2][j] = in[C::OGU + s2 * D + j];
+      Q[s2][j] = in[C::OQ + s2 * D + j];
+      for (int l = 0; l < D; ++l) GQ[s2][j][l] = in[C::OGQ + (s2 * D + j) * D + l];
+    }
+  }
+  vol_point_eval<D, P, KT, double, 0, MAPPED>(g, ph, e, el, gq, dir, wq, U, GU, Q, GQ, Hh, coef, supg_time, src,
+                                              Kvol, rvol, vgeo);
 }
 
 // basis value T[g][alpha][a] of a sub-element from 1D tables (alpha 0: value, 1+k: d/dx_k)
@@ -918,13 +1076,17 @@ int assemble_dp(mehdg_ctx* ctx, const double* u, const double* q, const double* 
             g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, nullptr, ctx->rvol, E);
         CKL();
       }
-    } else if (ctx->mapped) {
-      k_vol_point<D, P, BT, double, 0, true><<<(tot + 127) / 128, 128, 0, st>>>(
-          g, ctx->tab, ph, u, q, hist, coef, supg_time, ctx->src, Kvol, ctx->rvol, E, ctx->vgeo);
-      CKL();
     } else {
-      k_vol_point<D, P, BT><<<(tot + 127) / 128, 128, 0, st>>>(g, ctx->tab, ph, u, q, hist, coef, supg_time,
-                                                                ctx->src, Kvol, ctx->rvol, E);
+      // FP64: the interpolation once per point, shared by its input directions
+      typedef VpCfg<D> VC;
+      const long long npts = (long long)E * ctx->nel * NG;
+      const unsigned blocks = (unsigned)((npts + VC::PPB - 1) / VC::PPB);
+      if (ctx->mapped)
+        k_vol_point_sh<D, P, BT, true><<<blocks, VC::NT, 0, st>>>(g, ctx->tab, ph, u, q, hist, coef, supg_time,
+                                                                  ctx->src, Kvol, ctx->rvol, E, ctx->vgeo);
+      else
+        k_vol_point_sh<D, P, BT, false><<<blocks, VC::NT, 0, st>>>(g, ctx->tab, ph, u, q, hist, coef, supg_time,
+                                                                   ctx->src, Kvol, ctx->rvol, E, nullptr);
       CKL();
     }
     phase_end(ctx, PH_VOL_POINT);
