@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__
 // CTA takes VpCfg::PPB points with all NDIR directions of each.  The basis values and physical
 // derivatives of the points' sub-element nodes (phase 0), then u, grad u, q, grad q and the
 // history at each point (phase 1), are formed once in shared memory, with the operations of
-// k_vol_point in the same order (the same bits); each thread then runs the pointwise physics
+// k_vol_point in the same order; each thread then runs the pointwise physics
 // of one direction (phase 2).  k_vol_point repeats the interpolation in all NDIR threads of a
 // point.
 template <int D> struct VpCfg {
