@@ -42,7 +42,8 @@ __device__ __forceinline__ Tables<CT> tables(const CT* tab, int ng1, int p1) {
 // (with the SUPG term) on Dual numbers seeded along one input (u_s or q_js), and
 // writes the Jacobian column K[X][t][s0][.] of the integrand, pre-weighted by the
 // quadrature weight.  CT is the arithmetic type.  MODE 0 also writes the residual
-// integrand (FP64 path); MODE 1 writes the Jacobian only (mixed path, CT = float:
+// integrand (the FP64 path launches this mode as k_vol_point_sh, below, which shares the
+// interpolation among the directions of a point); MODE 1 writes the Jacobian only (mixed path, CT = float:
 // the Jacobian only shapes an inexact Newton step); MODE 2 writes the residual
 // only, one thread per point, plain FP64 values (mixed path).
 //
