@@ -10,6 +10,7 @@ import numpy as np
 
 from . import assemble as asm
 from . import fields
+from .simplex import SimplexBoxMesh
 from .space import BoxMesh, MacroGeometry, MappedMacroGeometry, ShellMesh
 
 
@@ -65,7 +66,13 @@ class Problem:
     def __init__(self, prob):
         self.prob = prob
         self.shell = int(prob.get("mesh_kind", 0)) == 1
-        self.mesh = ShellMesh(prob) if self.shell else BoxMesh(prob)
+        self.simplex = int(prob.get("mesh_kind", 0)) == 2
+        if self.shell:
+            self.mesh = ShellMesh(prob)
+        elif self.simplex:
+            self.mesh = SimplexBoxMesh(prob)
+        else:
+            self.mesh = BoxMesh(prob)
         self.d = prob["dim"]
         self.ns = self.d + 2
         self.phys = phys_of(prob)
@@ -79,6 +86,8 @@ class Problem:
     def geometry(self, e):
         if self.shell:
             return MappedMacroGeometry(self.mesh.nodes[e], self.m, self.p, self.mesh.h)
+        if self.simplex:
+            return self.mesh.geometry(e)
         lo, hi = self.mesh.macro_box(e)
         return MacroGeometry(lo, hi, self.m, self.p)
 

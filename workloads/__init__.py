@@ -28,7 +28,7 @@ import numpy as np
 
 BC_NONE, BC_DIRICHLET, BC_WALL, BC_FARFIELD = 0, 1, 2, 3
 FIELD_NONE, FIELD_MMS, FIELD_UNIFORM, FIELD_TGV, FIELD_SPHERE, FIELD_COUETTE3D = 0, 1, 2, 3, 4, 5
-MESH_BOX, MESH_SHELL = 0, 1
+MESH_BOX, MESH_SHELL, MESH_SIMPLEX = 0, 1, 2
 
 
 def _base(dim, nmac, lo, hi, periodic, m, p, Re_c, Pr=0.72, gamma=1.4, supg=1):
@@ -115,6 +115,19 @@ def sizes(prob):
     d, m, p = prob["dim"], prob["m"], prob["p"]
     n1 = m * p + 1
     Np, Nfn = n1 ** d, n1 ** (d - 1)
+    if prob.get("mesh_kind", MESH_BOX) == MESH_SIMPLEX:
+        # d! simplicial macros per box cell; d + 1 faces each, shared by two except on the
+        # non-periodic boundary planes ((d-1)! simplicial faces per boundary cell face)
+        from math import comb, factorial
+        n = m * p
+        ncell = int(np.prod(prob["nmac"][:d]))
+        E = ncell * factorial(d)
+        B = 0
+        for k in range(d):
+            if not prob["periodic"][k]:
+                B += 2 * factorial(d - 1) * int(np.prod([prob["nmac"][j] for j in range(d) if j != k]))
+        Nfn = comb(n + d - 1, d - 1)
+        return dict(d=d, ns=d + 2, Np=comb(n + d, d), Nfn=Nfn, Nth=(d + 1) * Nfn, E=E, F=((d + 1) * E + B) // 2)
     if prob.get("mesh_kind", MESH_BOX) == MESH_SHELL:
         nq, nr = prob["shell_n"]
         E = 6 * nq * nq * nr
