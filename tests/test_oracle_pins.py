@@ -951,8 +951,8 @@ def test_simplex_macro_subdivision_and_nodes_brute_force(d):
 def test_simplex_spaces_reproduce_the_papers_dof_tables():
     """The paper's tetrahedral DOF tables, now from the constructed spaces (not a formula):
     (d + 1)(d + 2) = 20 unknowns per node of KuhnMacro(3, m, p), 5 per node of a face, and
-    n_macro m^3 = 768 elements in Table 1; Table 3's m p = 8 gives the same local count for
-    (m, p) = (8, 1), (4, 2), (2, 4)."""
+    n_macro m^3 = 768 elements in Table 1; the m p = 8 counts of Tables 3, 8 and 10 come out
+    the same for (m, p) = (8, 1), (4, 2), (2, 4); the sphere's Table 6 for m = 1, 2."""
     gold = json.load(open(os.path.join(GOLD, "dof_tables.json")))
     t1 = gold["table1_couette_768_elements_p3"]
     for r in t1["rows"]:
@@ -968,6 +968,15 @@ def test_simplex_spaces_reproduce_the_papers_dof_tables():
             assert 20 * K.Np == r["local"]
             faces = (4 * r["n_macro"] + r["boundary_triangles"]) // 2
             assert 5 * faces * K.Nfn == r["global"]
+        t8 = gold["table8_tgv_mp8_periodic"]
+        for r in t8["rows"]:      # periodic: every face has two owners, F = 2 E
+            assert 20 * K.Np * r["n_macro"] == r["total_local"]
+            assert 5 * 2 * r["n_macro"] * K.Nfn == r["global"]
+    t6 = gold["table6_sphere_p3"]
+    for r in t6["rows"]:
+        K = sx.KuhnMacro(3, r["m"], t6["p"], tables=False)
+        assert 20 * K.Np * r["n_macro"] == r["total_local"]
+        assert r["global"] % (5 * K.Nfn) == 0
 
 
 @pytest.mark.parametrize("d", [2, 3])
