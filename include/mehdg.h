@@ -29,6 +29,16 @@
  *    the tangential axes, lower axis fastest;
  *  - local faces of a macro-element are ordered (-x, +x, -y, +y, -z, +z); a
  *    macro's local trace vector is species-major [ns][(local face, face node)].
+ *  - simplicial meshes (MEHDG_MESH_SIMPLEX, the paper's element type, Sec. 2.2): every box
+ *    cell is split into d! macro-elements x = C + H P_sigma xi over the Kuhn simplex
+ *    K = {1 >= xi_1 >= ... >= xi_d >= 0}, macro e = cell d! + (rank of the axis order sigma in
+ *    lexicographic order), cell index x fastest; each macro is refined m times into m^d
+ *    sub-simplices carrying P_p; Np = C(m p + d, d) nodes a / (m p), m p >= a_1 >= ... >= a_d
+ *    >= 0 (lexicographic, a_d fastest); d + 1 local faces xi_1 = 1, xi_k = xi_{k+1},
+ *    xi_d = 0, Nfn = C(m p + d - 1, d - 1) nodes each (the face's lattice points), Nth =
+ *    (d + 1) Nfn; faces numbered in order of first appearance over (macro, local face), a
+ *    face's nodes in its first owner's order.  Supported with precision FP64, apply_mode 0,
+ *    tc_mode 0, condense_layers 2 and m p <= 6.
  */
 #ifndef MEHDG_H
 #define MEHDG_H
@@ -73,6 +83,7 @@ extern "C" {
 
 /* mesh kinds */
 #define MEHDG_MESH_BOX 0      /* nmac, lo, hi, periodic: a box of box macro-elements */
+#define MEHDG_MESH_SIMPLEX 2  /* nmac, lo, hi, periodic: each box cell split into d! simplicial macros */
 #define MEHDG_MESH_SHELL 1    /* dim 3: cubed-sphere O-grid of the shell r0 <= |x| <= r1 (flow past a
     sphere).  E = 6 nq^2 nr curved macro-elements; macro e = ((panel nr + k) nq + j) nq + i for the
     cube panels (+x, -x, +y, -y, +z, -z) with frames (e_n, e_1, e_2) = (x, y, z), (-x, z, y),
@@ -191,6 +202,29 @@ int mehdg_query(const mehdg_ctx* ctx, mehdg_info* info);
  * [F][ns][Nfn] are device pointers or NULL. */
 int mehdg_init_state(mehdg_ctx* ctx, const double* du_pert, const double* duh_pert,
                      int lift, double* u, double* q, double* uhat);
+
+/* Inspection of the simplicial reference macro-element (Sec. 2.2), host only (no device
+ * needed): the tables of the m-refined Kuhn simplex with P_p sub-elements that simplicial
+ * meshes use.  counts (host int[8], required): Np, Nfn, nel (sub-simplices), ng (points per
+ * sub-simplex), nloc (nodes per sub-simplex), nsf (sub-faces per face), nfp (points per
+ * sub-face), nfs (nodes per sub-face).  The other host arrays may be NULL: lattice [Np][d]
+ * integer node coordinates (spacing 1 / (m p)); vxi [nel ng][d] volume points in K and vw
+ * [nel ng] their weights; vtab [nel ng][nloc][d + 1] values and d/dxi of the point's
+ * sub-simplex basis; vnode [nel][nloc] their macro nodes; fnodes [d + 1][Nfn] macro node of
+ * each face node; fxi [d + 1][nsf nfp][d] face points in K and fwt [d + 1][nsf nfp] their
+ * weights in face coordinates.  Errors: ARG (d not 2 or 3, p not 1..3, m p > 12). */
+int mehdg_simplex_reference(int d, int m, int p, int* counts, int* lattice, double* vxi, double* vw,
+                            double* vtab, int* vnode, int* fnodes, double* fxi, double* fwt);
+
+/* Inspection of a simplicial mesh, host only (no device needed): prob a MEHDG_MESH_SIMPLEX
+ * description.  counts (host int[5], required): E, F, Np, Nfn, Nth.  The other host arrays may
+ * be NULL: gather [E][Nt] (the map eps of Algorithm 2), owner [F][2] (e (d + 1) + local face,
+ * -1 for none; the first owner orders the face's nodes), bside [E][d + 1] (boundary side or
+ * -1), the per-macro mass and lifting matrices M [E][Np][Np], Gk [E][d][Np][Np], Ghk
+ * [E][d][Np][Nth] (A_qq, A_qu, A_quh per species, Sec. 3.3) and xnode [E][d][Np] node
+ * positions.  Errors: ARG (invalid description, m p > 6). */
+int mehdg_simplex_mesh(const mehdg_problem* prob, int* counts, int* gather, int* owner, int* bside, double* M,
+                       double* Gk, double* Ghk, double* xnode);
 
 /* Taylor-Green diagnostics (Sec. 5.3, eq. C5321) of a state, by the volume quadrature of the
  * method (the Gauss points of every sub-element; the curved weights on shell meshes):

@@ -23,7 +23,8 @@ EXPORTS = ["mehdg_mesh", "mehdg_query", "mehdg_init_state", "mehdg_assemble_loca
            "mehdg_mlp_record", "mehdg_mlp_set_recording", "mehdg_mlp_gradient", "mehdg_mlp_train",
            "mehdg_stage_begin", "mehdg_newton_step", "mehdg_stage_end", "mehdg_set_precond", "mehdg_tc_gemm_tf32", "mehdg_tc_gemm_nt", "mehdg_lu_batched", "mehdg_apply_trace_noalloc", "mehdg_lu_queue", "mehdg_graph_replays", "mehdg_batch_create",
            "mehdg_batch_size", "mehdg_batch_context", "mehdg_batch_steady_solve", "mehdg_batch_tiles",
-           "mehdg_batch_graph_replays", "mehdg_batch_last_error", "mehdg_batch_destroy", "mehdg_flow_integrals", "mehdg_destroy",
+           "mehdg_batch_graph_replays", "mehdg_batch_last_error", "mehdg_batch_destroy", "mehdg_flow_integrals",
+           "mehdg_simplex_reference", "mehdg_simplex_mesh", "mehdg_destroy",
            "mehdg_last_error"]
 
 ERRORS = {0: "OK", -1: "ARG", -2: "CUDA", -3: "OOM", -4: "SINGULAR", -5: "NOT_CONVERGED", -6: "TIMEOUT", -7: "NAN"}
@@ -240,6 +241,56 @@ def lu_queue(mats, nb=16, perms=None):
     if rc != 0:
         raise MehdgError("mehdg_lu_queue failed (%s)" % ERRORS.get(rc, rc))
     return perms
+
+
+def simplex_reference(d, m, p):
+    """The simplicial reference macro-element's tables (mehdg_simplex_reference; host only)."""
+    import ctypes as C
+    lib = load_library()
+    cnt = (C.c_int * 8)()
+    rc = lib.mehdg_simplex_reference(d, m, p, cnt, None, None, None, None, None, None, None, None)
+    if rc != 0:
+        raise MehdgError("mehdg_simplex_reference failed (%s)" % ERRORS.get(rc, rc))
+    Np, Nfn, nel, ng, nloc, nsf, nfp, nfs = list(cnt)
+    lat = np.zeros((Np, d), dtype=np.int32)
+    vxi = np.zeros((nel * ng, d))
+    vw = np.zeros(nel * ng)
+    vtab = np.zeros((nel * ng, nloc, d + 1))
+    vnode = np.zeros((nel, nloc), dtype=np.int32)
+    fnodes = np.zeros((d + 1, Nfn), dtype=np.int32)
+    fxi = np.zeros((d + 1, nsf * nfp, d))
+    fwt = np.zeros((d + 1, nsf * nfp))
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    rc = lib.mehdg_simplex_reference(d, m, p, cnt, ptr(lat), ptr(vxi), ptr(vw), ptr(vtab), ptr(vnode), ptr(fnodes),
+                                     ptr(fxi), ptr(fwt))
+    if rc != 0:
+        raise MehdgError("mehdg_simplex_reference failed (%s)" % ERRORS.get(rc, rc))
+    return dict(counts=dict(Np=Np, Nfn=Nfn, nel=nel, ng=ng, nloc=nloc, nsf=nsf, nfp=nfp, nfs=nfs), lattice=lat,
+                vxi=vxi, vw=vw, vtab=vtab, vnode=vnode, fnodes=fnodes, fxi=fxi, fwt=fwt)
+
+
+def simplex_mesh(prob):
+    """Maps and per-macro operators of a simplicial mesh (mehdg_simplex_mesh; host only)."""
+    import ctypes as C
+    lib = load_library()
+    ps = problem_struct(prob)
+    cnt = (C.c_int * 5)()
+    z = [None] * 7
+    rc = lib.mehdg_simplex_mesh(C.byref(ps), cnt, *z)
+    if rc != 0:
+        raise MehdgError("mehdg_simplex_mesh failed (%s)" % ERRORS.get(rc, rc))
+    E, F, Np, Nfn, Nth = list(cnt)
+    d, ns = prob["dim"], prob["dim"] + 2
+    out = dict(E=E, F=F, Np=Np, Nfn=Nfn, Nth=Nth, gather=np.zeros((E, ns * Nth), dtype=np.int32),
+               owner=np.zeros((F, 2), dtype=np.int32), bside=np.zeros((E, d + 1), dtype=np.int32),
+               M=np.zeros((E, Np, Np)), Gk=np.zeros((E, d, Np, Np)), Ghk=np.zeros((E, d, Np, Nth)),
+               xnode=np.zeros((E, d, Np)))
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    rc = lib.mehdg_simplex_mesh(C.byref(ps), cnt, ptr(out["gather"]), ptr(out["owner"]), ptr(out["bside"]),
+                                ptr(out["M"]), ptr(out["Gk"]), ptr(out["Ghk"]), ptr(out["xnode"]))
+    if rc != 0:
+        raise MehdgError("mehdg_simplex_mesh failed (%s)" % ERRORS.get(rc, rc))
+    return out
 
 
 class Context:

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_apply_explicit(
 // y[f][s][j] = sum over the owners (e, fl) of slot[e][s][fl, l], l = j or, when the owners order
 // the face nodes differently (curved meshes), l = ofn[f][o][j]
 __global__ void k_face_reduce(const double* __restrict__ slot, const int* __restrict__ owner,
-                              double* __restrict__ y, int ns, int Nfn, int Nth, int Nt, int d, long long ntr,
+                              double* __restrict__ y, int ns, int Nfn, int Nth, int Nt, int nf, long long ntr,
                               const int* __restrict__ ofn = nullptr) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= ntr) return;
@@ -232,7 +232,7 @@ __global__ void k_face_reduce(const double* __restrict__ slot, const int* __rest
   for (int o = 0; o < 2; ++o) {
     int ow = owner[2 * f + o];
     if (ow < 0) continue;
-    int e = ow / (2 * d), fl = ow % (2 * d);
+    int e = ow / nf, fl = ow % nf;
     const int l = ofn ? ofn[((size_t)2 * f + o) * Nfn + j] : j;
     v += slot[(size_t)e * Nt + (size_t)s * Nth + fl * Nfn + l];
   }
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256) k_recover_f32(const float* __restrict__ S
 
 int face_reduce(mehdg_ctx* ctx, const double* slot, double* y) {
   k_face_reduce<<<(ctx->ntr + 255) / 256, 256, 0, ctx->stream>>>(slot, ctx->owner, y, ctx->ns, ctx->Nfn, ctx->Nth,
-                                                                 ctx->Nt, ctx->d, ctx->ntr, ctx->ofn);
+                                                                 ctx->Nt, ctx->nf, ctx->ntr, ctx->ofn);
   CKL();
   return MEHDG_OK;
 }
@@ -531,7 +531,7 @@ extern "C" int mehdg_apply_trace_noalloc(int dim, int n_macro, int n_face, int N
     return MEHDG_ERR_CUDA;
   k_apply<double, double><<<n_macro, 512, smem, st>>>(S_lu, perm, B, C, D, gather, x, slot, Nu, Nt);
   const long long ntr = (long long)n_face * ns * Nfn;
-  k_face_reduce<<<(ntr + 255) / 256, 256, 0, st>>>(slot, owner, y, ns, Nfn, Nth, Nt, dim, ntr);
+  k_face_reduce<<<(ntr + 255) / 256, 256, 0, st>>>(slot, owner, y, ns, Nfn, Nth, Nt, 2 * dim, ntr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     fprintf(stderr, "mehdg_apply_trace_noalloc: launch failed (%s)\n", cudaGetErrorString(e));

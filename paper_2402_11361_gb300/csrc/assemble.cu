@@ -61,9 +61,9 @@ __device__ __forceinline__ void vol_point_eval(const Geo& g, const Phys& ph, int
                                                CT (&U)[D + 2], CT (&GU)[D + 2][D], CT (&Q)[D + 2][D],
                                                CT (&GQ)[D + 2][D][D], const CT (&Hh)[D + 2], double coef,
                                                int supg_time, const CT* __restrict__ src, KT* __restrict__ Kvol,
-                                               double* __restrict__ rvol, const double* __restrict__ vgeo) {
-  constexpr int NS = D + 2, NG1 = P + 2;
-  constexpr int NG = IPow<NG1, D>::v;
+                                               double* __restrict__ rvol, const double* __restrict__ vgeo,
+                                               const int NG) {
+  constexpr int NS = D + 2;
   constexpr int KA = (D + 1) * NS * (D + 1);
   const int nel = g.nel;
   CT Ji[D][D];
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(128) k_vol_point(Geo g, const CT* __restrict__
     }
   }
   vol_point_eval<D, P, KT, CT, MODE, MAPPED>(g, ph, e, el, gq, dir, wq, U, GU, Q, GQ, Hh, coef, supg_time, src,
-                                             Kvol, rvol, vgeo);
+                                             Kvol, rvol, vgeo, NG);
 }
 
 // The FP64 Jacobian pass with the interpolation shared by the input directions of a point: one
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(VpCfg<D>::NT) k_vol_point_sh(Geo g, const doub
     }
   }
   vol_point_eval<D, P, KT, double, 0, MAPPED>(g, ph, e, el, gq, dir, wq, U, GU, Q, GQ, Hh, coef, supg_time, src,
-                                              Kvol, rvol, vgeo);
+                                              Kvol, rvol, vgeo, NG);
 }
 
 // basis value T[g][alpha][a] of a sub-element from 1D tables (alpha 0: value, 1+k: d/dx_k)
@@ -783,6 +783,71 @@ __device__ __forceinline__ void face_axes(int fl, int* tang) {
 // against the volume space, differentiated along one input (u^_s, q_js or u_s).
 // MODE 0: Jacobian and residual (FP64 path); MODE 1: Jacobian only, CT = float, from
 // FP32 copies of the state (mixed path); MODE 2: residual only, one thread per point.
+// The numerical flux and the trace equation (interior flux, or B^ of the face's boundary kind
+// bk with side bs and data ud) at one face point with unit normal n and weight wf, for one input
+// direction (uhat_s, q_sj, u_s): writes the Jacobian column (and, MODE 0 direction 0 or MODE 2,
+// the residual integrands) of face point pidx.
+template <int D, class CT, int MODE>
+__device__ __forceinline__ void face_point_eval(const Phys& ph, const mehdg_problem& pr, int bk, int bs,
+                                                const CT* __restrict__ ud, const double* n, CT wf,
+                                                const CT (&Uf)[D + 2], const CT (&Qf)[D + 2][D],
+                                                const CT (&UHf)[D + 2], int dir, size_t pidx,
+                                                CT* __restrict__ Kface, double* __restrict__ rface) {
+  constexpr int NS = D + 2;
+  constexpr int NDIR_K = NS * (D + 2);
+  if constexpr (MODE == 2) {
+    CT fh[NS], eq[NS];
+    trace_flux<D, CT>(UHf, Qf, Uf, n, ph, fh);
+    if (bk == MEHDG_BC_DIRICHLET) {
+      for (int s = 0; s < NS; ++s) eq[s] = UHf[s] - ud[s];
+    } else if (bk == MEHDG_BC_WALL) {
+      wall_operator<D, CT>(UHf, Uf, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+    } else if (bk == MEHDG_BC_FARFIELD) {
+      farfield_operator<D, CT, CT>(UHf, Uf, ud, n, pr.gamma, eq);
+    } else {
+      for (int s = 0; s < NS; ++s) eq[s] = fh[s];
+    }
+    double* R = rface + pidx * 2 * NS;
+    for (int t = 0; t < NS; ++t) {
+      R[t] = fh[t] * wf;
+      R[NS + t] = eq[t] * wf;
+    }
+  } else {
+    typedef Dual<CT, 1> S;
+    S Us[NS], Qs[NS][D], UHs[NS], fh[NS], eq[NS];
+    for (int s = 0; s < NS; ++s) {
+      UHs[s].v = UHf[s]; UHs[s].d[0] = (dir == s) ? CT(1) : CT(0);
+      for (int j = 0; j < D; ++j) {
+        Qs[s][j].v = Qf[s][j];
+        Qs[s][j].d[0] = (dir == NS + j * NS + s) ? CT(1) : CT(0);
+      }
+      Us[s].v = Uf[s]; Us[s].d[0] = (dir == NS + NS * D + s) ? CT(1) : CT(0);
+    }
+    trace_flux<D, S>(UHs, Qs, Us, n, ph, fh);
+    if (bk == MEHDG_BC_DIRICHLET) {
+      for (int s = 0; s < NS; ++s) eq[s] = UHs[s] - (double)ud[s];
+    } else if (bk == MEHDG_BC_WALL) {
+      wall_operator<D, S>(UHs, Us, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
+    } else if (bk == MEHDG_BC_FARFIELD) {
+      farfield_operator<D, S, CT>(UHs, Us, ud, n, pr.gamma, eq);
+    } else {
+      for (int s = 0; s < NS; ++s) eq[s] = fh[s];
+    }
+    CT* K = Kface + (pidx * NDIR_K + dir) * 2 * NS;
+    for (int t = 0; t < NS; ++t) {
+      K[t] = fh[t].d[0] * wf;
+      K[NS + t] = eq[t].d[0] * wf;
+    }
+    if (MODE == 0 && dir == 0) {
+      double* R = rface + pidx * 2 * NS;
+      for (int t = 0; t < NS; ++t) {
+        R[t] = fh[t].v * wf;
+        R[NS + t] = eq[t].v * wf;
+      }
+    }
+  }
+}
+
 template <int D, int P, class CT = double, int MODE = 0>
 __global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict__ tab, Phys ph,
                                                      mehdg_problem pr, const int* __restrict__ bkind,
@@ -850,60 +915,10 @@ __global__ void __launch_bounds__(128) k_face_point(Geo g, const CT* __restrict_
     n[fl / 2] = (fl % 2) ? 1.0 : -1.0;
   }
   const int bk = bkind[e * 2 * D + fl];
+  const int bs = bside[e * 2 * D + fl];
   const CT* ud = uD ? uD + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NS : nullptr;
-  if constexpr (MODE == 2) {
-    CT fh[NS], eq[NS];
-    trace_flux<D, CT>(UHf, Qf, Uf, n, ph, fh);
-    if (bk == MEHDG_BC_DIRICHLET) {
-      for (int s = 0; s < NS; ++s) eq[s] = UHf[s] - ud[s];
-    } else if (bk == MEHDG_BC_WALL) {
-      int bs = bside[e * 2 * D + fl];
-      wall_operator<D, CT>(UHf, Uf, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
-    } else if (bk == MEHDG_BC_FARFIELD) {
-      farfield_operator<D, CT, CT>(UHf, Uf, ud, n, pr.gamma, eq);
-    } else {
-      for (int s = 0; s < NS; ++s) eq[s] = fh[s];
-    }
-    double* R = rface + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * 2 * NS;
-    for (int t = 0; t < NS; ++t) {
-      R[t] = fh[t] * wf;
-      R[NS + t] = eq[t] * wf;
-    }
-  } else {
-    typedef Dual<CT, 1> S;
-    S Us[NS], Qs[NS][D], UHs[NS], fh[NS], eq[NS];
-    for (int s = 0; s < NS; ++s) {
-      UHs[s].v = UHf[s]; UHs[s].d[0] = (dir == s) ? CT(1) : CT(0);
-      for (int j = 0; j < D; ++j) {
-        Qs[s][j].v = Qf[s][j];
-        Qs[s][j].d[0] = (dir == NS + j * NS + s) ? CT(1) : CT(0);
-      }
-      Us[s].v = Uf[s]; Us[s].d[0] = (dir == NS + NS * D + s) ? CT(1) : CT(0);
-    }
-    trace_flux<D, S>(UHs, Qs, Us, n, ph, fh);
-    if (bk == MEHDG_BC_DIRICHLET) {
-      for (int s = 0; s < NS; ++s) eq[s] = UHs[s] - (double)ud[s];
-    } else if (bk == MEHDG_BC_WALL) {
-      int bs = bside[e * 2 * D + fl];
-      wall_operator<D, S>(UHs, Us, pr.wall_T[bs], pr.wall_v[bs], pr.gamma, eq);
-    } else if (bk == MEHDG_BC_FARFIELD) {
-      farfield_operator<D, S, CT>(UHs, Us, ud, n, pr.gamma, eq);
-    } else {
-      for (int s = 0; s < NS; ++s) eq[s] = fh[s];
-    }
-    CT* K = Kface + (((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * NDIR_K + dir) * 2 * NS;
-    for (int t = 0; t < NS; ++t) {
-      K[t] = fh[t].d[0] * wf;
-      K[NS + t] = eq[t].d[0] * wf;
-    }
-    if (MODE == 0 && dir == 0) {
-      double* R = rface + ((((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp) * 2 * NS;
-      for (int t = 0; t < NS; ++t) {
-        R[t] = fh[t].v * wf;
-        R[NS + t] = eq[t].v * wf;
-      }
-    }
-  }
+  const size_t pidx = (((size_t)e * 2 * D + fl) * nsf + sf) * NFP + fp;
+  face_point_eval<D, CT, MODE>(ph, pr, bk, bs, ud, n, wf, Uf, Qf, UHf, dir, pidx, Kface, rface);
 }
 
 template <int D, int P, class BT, class KT = double>
@@ -1168,6 +1183,323 @@ int assemble_bt(mehdg_ctx* ctx, const double* u, const double* q, const double* 
   return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
 }
 
+// ---------------------------------------------------------------- simplicial macro-elements
+// P_p on m-refined simplices (csrc/simplex.cu holds the reference tables and the mesh).  The same
+// pointwise physics as the tensor kernels (vol_point_eval in its curved form, face_point_eval),
+// with the interpolation read from per-point tables: each Gauss point of sub-simplex el touches
+// its NLOC nodes (values and d/dxi), each face point the NFS nodes of its sub-face (the volume
+// basis restricted to a face is the trace basis).  The contractions run over sub-elements in
+// turn, one CTA per (macro, input block, test species) or per macro, so that no two threads add
+// to one block entry at a time.  FP64 only.
+template <int D, int P> struct SxN {
+  static constexpr int NLOC = (D == 2) ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int NFS = (D == 2) ? P + 1 : (P + 1) * (P + 2) / 2;
+  static constexpr int NG = IPow<P + 3, D>::v, NFP = IPow<P + 3, D - 1>::v;
+};
+
+template <int D, int P>
+__global__ void __launch_bounds__(128) k_vol_point_sx(Geo g, const double* __restrict__ vtab,
+                                                      const int* __restrict__ vnode, Phys ph,
+                                                      const double* __restrict__ u, const double* __restrict__ q,
+                                                      const double* __restrict__ hist, double coef, int supg_time,
+                                                      const double* __restrict__ src, double* __restrict__ Kvol,
+                                                      double* __restrict__ rvol, int E,
+                                                      const double* __restrict__ vgeo) {
+  constexpr int NS = D + 2, NLOC = SxN<D, P>::NLOC, NG = SxN<D, P>::NG;
+  constexpr int NDIR = NS * (1 + D);
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nel = g.nel;
+  if (tid >= (long long)E * nel * NG * NDIR) return;
+  const int dir = (int)(tid % NDIR);
+  long long r = tid / NDIR;
+  const int gq = (int)(r % NG);
+  r /= NG;
+  const int el = (int)(r % nel);
+  const int e = (int)(r / nel);
+  double U[NS], GU[NS][D], Q[NS][D], GQ[NS][D][D], Hh[NS];
+  for (int s = 0; s < NS; ++s) {
+    U[s] = 0.0;
+    Hh[s] = 0.0;
+    for (int l = 0; l < D; ++l) {
+      GU[s][l] = 0.0;
+      Q[s][l] = 0.0;
+      for (int j = 0; j < D; ++j) GQ[s][j][l] = 0.0;
+    }
+  }
+  const double* T = vtab + ((size_t)el * NG + gq) * NLOC * (D + 1);
+  const int* nd = vnode + (size_t)el * NLOC;
+  const size_t Np = g.Np;
+  for (int al = 0; al < NLOC; ++al) {
+    const int a = nd[al];
+    const double phi = T[al * (D + 1)];
+    double dphi[D];
+    for (int l = 0; l < D; ++l) dphi[l] = T[al * (D + 1) + 1 + l];
+    for (int s = 0; s < NS; ++s) {
+      const double ua = u[((size_t)e * NS + s) * Np + a];
+      U[s] += phi * ua;
+      for (int l = 0; l < D; ++l) GU[s][l] += dphi[l] * ua;
+      if (hist) Hh[s] += phi * hist[((size_t)e * NS + s) * Np + a];
+      for (int j = 0; j < D; ++j) {
+        const double qa = q[(((size_t)e * D + j) * NS + s) * Np + a];
+        Q[s][j] += phi * qa;
+        for (int l = 0; l < D; ++l) GQ[s][j][l] += dphi[l] * qa;
+      }
+    }
+  }
+  vol_point_eval<D, P, double, double, 0, true>(g, ph, e, el, gq, dir, 1.0, U, GU, Q, GQ, Hh, coef, supg_time,
+                                                src, Kvol, rvol, vgeo, NG);
+}
+
+// A_X[(t, a), (s, b)] += sum_g sum_{alpha, beta} T_alpha[g][a] K_X[t][g][(alpha, s), beta] T_beta[g][b]:
+// X = 0 A_uu, X = 1 + j A_uq_j; one CTA per (macro, X, t), the sub-simplex's tables in shared memory
+template <int D, int P>
+__global__ void __launch_bounds__(256) k_vol_contract_sx(Geo g, const double* __restrict__ vtab,
+                                                         const int* __restrict__ vnode,
+                                                         const double* __restrict__ Kvol, double* Auu, double* Auq) {
+  constexpr int NS = D + 2, NLOC = SxN<D, P>::NLOC, NG = SxN<D, P>::NG;
+  constexpr int KA = (D + 1) * NS * (D + 1);
+  extern __shared__ double sT[];   // [NG][NLOC][D + 1]
+  const int e = blockIdx.x, X = blockIdx.y, t = blockIdx.z;
+  const int nel = g.nel;
+  const size_t Np = g.Np, Nu = g.Nu;
+  double* A = (X == 0) ? Auu + (size_t)e * Nu * Nu : Auq + ((size_t)e * D + (X - 1)) * Nu * Nu;
+  for (int el = 0; el < nel; ++el) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < NG * NLOC * (D + 1); i += blockDim.x)
+      sT[i] = vtab[(size_t)el * NG * NLOC * (D + 1) + i];
+    __syncthreads();
+    const double* K = Kvol + ((((size_t)e * (D + 1) + X) * NS + t) * nel + el) * NG * KA;
+    const int* nd = vnode + (size_t)el * NLOC;
+    for (int o = threadIdx.x; o < NS * NLOC * NLOC; o += blockDim.x) {
+      const int s = o / (NLOC * NLOC), i = (o / NLOC) % NLOC, j = o % NLOC;
+      double sum = 0.0;
+      for (int gq = 0; gq < NG; ++gq) {
+        const double* Kg = K + (size_t)gq * KA;
+        const double* Ti = sT + ((size_t)gq * NLOC + i) * (D + 1);
+        const double* Tj = sT + ((size_t)gq * NLOC + j) * (D + 1);
+        for (int al = 0; al <= D; ++al) {
+          double inner = 0.0;
+          for (int be = 0; be <= D; ++be) inner += Kg[(al * NS + s) * (D + 1) + be] * Tj[be];
+          sum += Ti[al] * inner;
+        }
+      }
+      A[((size_t)t * Np + nd[i]) * Nu + (size_t)s * Np + nd[j]] += sum;
+    }
+  }
+}
+
+// R_U[t][a] += sum_g sum_alpha T_alpha[g][a] r[g][t][alpha], one CTA per macro
+template <int D, int P>
+__global__ void __launch_bounds__(128) k_vol_res_sx(Geo g, const double* __restrict__ vtab,
+                                                    const int* __restrict__ vnode, const double* __restrict__ rvol,
+                                                    double* __restrict__ RU) {
+  constexpr int NS = D + 2, NLOC = SxN<D, P>::NLOC, NG = SxN<D, P>::NG;
+  const int e = blockIdx.x, nel = g.nel;
+  const size_t Np = g.Np;
+  for (int el = 0; el < nel; ++el) {
+    __syncthreads();
+    const int* nd = vnode + (size_t)el * NLOC;
+    for (int o = threadIdx.x; o < NS * NLOC; o += blockDim.x) {
+      const int t = o / NLOC, i = o % NLOC;
+      double sum = 0.0;
+      for (int gq = 0; gq < NG; ++gq) {
+        const double* T = vtab + (((size_t)el * NG + gq) * NLOC + i) * (D + 1);
+        const double* R = rvol + (((size_t)e * nel + el) * NG + gq) * NS * (D + 1) + t * (D + 1);
+        for (int al = 0; al <= D; ++al) sum += T[al] * R[al];
+      }
+      RU[((size_t)e * NS + t) * Np + nd[i]] += sum;
+    }
+  }
+}
+
+// one thread per (macro, face, sub-face, face point, input direction)
+template <int D, int P>
+__global__ void __launch_bounds__(128) k_face_point_sx(Geo g, const double* __restrict__ ftab,
+                                                       const int* __restrict__ fsub, Phys ph, mehdg_problem pr,
+                                                       const int* __restrict__ bkind, const int* __restrict__ bside,
+                                                       const int* __restrict__ fnode, const int* __restrict__ gather,
+                                                       const double* __restrict__ uD, const double* __restrict__ u,
+                                                       const double* __restrict__ q, const double* __restrict__ uh,
+                                                       double* __restrict__ Kface, double* __restrict__ rface, int E,
+                                                       const double* __restrict__ fgeo) {
+  constexpr int NS = D + 2, NFS = SxN<D, P>::NFS, NFP = SxN<D, P>::NFP;
+  constexpr int NDIR = NS * (D + 2), NF = D + 1;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nsf = g.nsf;
+  if (tid >= (long long)E * NF * nsf * NFP * NDIR) return;
+  const int dir = (int)(tid % NDIR);
+  long long r = tid / NDIR;
+  const int fp = (int)(r % NFP);
+  r /= NFP;
+  const int sf = (int)(r % nsf);
+  r /= nsf;
+  const int fl = (int)(r % NF);
+  const int e = (int)(r / NF);
+  const double* T = ftab + (((size_t)fl * nsf + sf) * NFP + fp) * NFS;
+  const int* js = fsub + ((size_t)fl * nsf + sf) * NFS;
+  double Uf[NS], Qf[NS][D], UHf[NS];
+  for (int s = 0; s < NS; ++s) {
+    Uf[s] = 0.0;
+    UHf[s] = 0.0;
+    for (int j = 0; j < D; ++j) Qf[s][j] = 0.0;
+  }
+  const size_t Np = g.Np;
+  for (int il = 0; il < NFS; ++il) {
+    const int jf = js[il];
+    const double psi = T[il];
+    const int a = fnode[fl * g.Nfn + jf];
+    for (int s = 0; s < NS; ++s) {
+      Uf[s] += psi * u[((size_t)e * NS + s) * Np + a];
+      UHf[s] += psi * uh[gather[(size_t)e * g.Nt + s * g.Nth + fl * g.Nfn + jf]];
+      for (int j = 0; j < D; ++j) Qf[s][j] += psi * q[(((size_t)e * D + j) * NS + s) * Np + a];
+    }
+  }
+  const size_t pidx = (((size_t)e * NF + fl) * nsf + sf) * NFP + fp;
+  const double* fg = fgeo + pidx * (D + 1);
+  double n[D];
+  for (int k = 0; k < D; ++k) n[k] = fg[k];
+  const int bk = bkind[e * NF + fl], bs = bside[e * NF + fl];
+  face_point_eval<D, double, 0>(ph, pr, bk, bs, uD + pidx * NS, n, fg[D], Uf, Qf, UHf, dir, pidx, Kface, rface);
+}
+
+// the face blocks and residuals from the face-point columns, one CTA per macro (as k_face_contract)
+template <int D, int P>
+__global__ void __launch_bounds__(256) k_face_contract_sx(Geo g, const double* __restrict__ ftab,
+                                                          const int* __restrict__ fsub, const int* __restrict__ fnode,
+                                                          const double* __restrict__ Kface,
+                                                          const double* __restrict__ rface, double* Auu, double* Auq,
+                                                          double* Auh, double* Ahu, double* Ahq, double* Ahh,
+                                                          double* RU, double* RUh) {
+  constexpr int NS = D + 2, NFS = SxN<D, P>::NFS, NFP = SxN<D, P>::NFP;
+  constexpr int NDIR = NS * (D + 2), NF = D + 1;
+  __shared__ double spsi[NFS * NFP];
+  const int e = blockIdx.x;
+  const size_t Nu = g.Nu, Nt = g.Nt, Np = g.Np;
+  const int Nth = g.Nth, Nfn = g.Nfn, nsf = g.nsf;
+  const int tid = threadIdx.x;
+  for (int fl = 0; fl < NF; ++fl) {
+    for (int sf = 0; sf < nsf; ++sf) {
+      __syncthreads();
+      for (int i = tid; i < NFS * NFP; i += blockDim.x) {
+        const int il = i / NFP, fp = i % NFP;
+        spsi[i] = ftab[(((size_t)fl * nsf + sf) * NFP + fp) * NFS + il];
+      }
+      __syncthreads();
+      const double* K = Kface + (((size_t)e * NF + fl) * nsf + sf) * NFP * NDIR * 2 * NS;
+      const double* R = rface + (((size_t)e * NF + fl) * nsf + sf) * NFP * 2 * NS;
+      const int* js = fsub + ((size_t)fl * nsf + sf) * NFS;
+      const int NOUT = NDIR * 2 * NS * NFS * NFS;
+      for (int oi = tid; oi < NOUT; oi += blockDim.x) {
+        const int jn = oi % NFS;
+        const int in = (oi / NFS) % NFS;
+        const int t = (oi / (NFS * NFS)) % NS;
+        const int et = (oi / (NFS * NFS * NS)) % 2;
+        const int dir = oi / (NFS * NFS * NS * 2);
+        double sum = 0.0;
+        for (int fp = 0; fp < NFP; ++fp)
+          sum += spsi[in * NFP + fp] * K[((size_t)fp * NDIR + dir) * 2 * NS + et * NS + t] * spsi[jn * NFP + fp];
+        const int ji = js[in], jj = js[jn];
+        const int ai = fnode[fl * Nfn + ji], aj = fnode[fl * Nfn + jj];
+        int s, kind, jd = 0;
+        if (dir < NS) { kind = 0; s = dir; }
+        else if (dir < NS + NS * D) { kind = 1; jd = (dir - NS) / NS; s = (dir - NS) % NS; }
+        else { kind = 2; s = dir - NS - NS * D; }
+        if (et == 0) {   // numerical flux tested with phi (u rows)
+          const size_t row = (size_t)t * Np + ai;
+          if (kind == 0) Auh[(size_t)e * Nu * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += sum;
+          else if (kind == 1) Auq[((size_t)e * D + jd) * Nu * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+          else Auu[(size_t)e * Nu * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+        } else {         // trace equation tested with psi (uhat rows)
+          const size_t row = (size_t)t * Nth + fl * Nfn + ji;
+          if (kind == 0) Ahh[(size_t)e * Nt * Nt + row * Nt + (size_t)s * Nth + fl * Nfn + jj] += sum;
+          else if (kind == 1) Ahq[((size_t)e * D + jd) * Nt * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+          else Ahu[(size_t)e * Nt * Nu + row * Nu + (size_t)s * Np + aj] += sum;
+        }
+      }
+      for (int oi = tid; oi < 2 * NS * NFS; oi += blockDim.x) {
+        const int in = oi % NFS;
+        const int t = (oi / NFS) % NS;
+        const int et = oi / (NFS * NS);
+        double sum = 0.0;
+        for (int fp = 0; fp < NFP; ++fp) sum += spsi[in * NFP + fp] * R[(size_t)fp * 2 * NS + et * NS + t];
+        const int ji = js[in];
+        if (et == 0) RU[((size_t)e * NS + t) * Np + fnode[fl * Nfn + ji]] += sum;
+        else RUh[(size_t)e * Nt + (size_t)t * Nth + fl * Nfn + ji] += sum;
+      }
+    }
+  }
+}
+
+template <int D, int P>
+int assemble_sx(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt) {
+  typedef SxN<D, P> C;
+  constexpr int NS = D + 2;
+  Geo g = make_geo(ctx);
+  cudaStream_t st = ctx->stream;
+  const int E = ctx->E;
+  const size_t Nu = ctx->Nu, Nt = ctx->Nt;
+  Phys ph{ctx->prob.gamma, ctx->prob.Re, ctx->prob.Pr, ctx->prob.supg, ctx->h_supg, ctx->p};
+  CK(cudaMemsetAsync(ctx->Auu, 0, sizeof(double) * E * Nu * Nu, st));
+  CK(cudaMemsetAsync(ctx->Auq, 0, sizeof(double) * E * D * Nu * Nu, st));
+  CK(cudaMemsetAsync(ctx->Auh, 0, sizeof(double) * E * Nu * Nt, st));
+  CK(cudaMemsetAsync(ctx->Ahu, 0, sizeof(double) * E * Nt * Nu, st));
+  CK(cudaMemsetAsync(ctx->Ahq, 0, sizeof(double) * E * D * Nt * Nu, st));
+  CK(cudaMemsetAsync(ctx->Ahh, 0, sizeof(double) * E * Nt * Nt, st));
+  CK(cudaMemsetAsync(ctx->RU, 0, sizeof(double) * E * Nu, st));
+  CK(cudaMemsetAsync(ctx->RUh, 0, sizeof(double) * E * Nt, st));
+  const double* hist = tt ? tt->hist : nullptr;
+  const double coef = tt ? tt->coef : 0.0;
+  const int supg_time = tt ? tt->supg_time : 0;
+  {
+    const long long tot = (long long)E * ctx->nel * C::NG * NS * (1 + D);
+    phase_begin(ctx, PH_VOL_POINT);
+    k_vol_point_sx<D, P><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(
+        g, ctx->sx_vtab, ctx->sx_vnode, ph, u, q, hist, coef, supg_time, ctx->src, ctx->Kvol, ctx->rvol, E, ctx->vgeo);
+    CKL();
+    phase_end(ctx, PH_VOL_POINT);
+    const size_t smem = sizeof(double) * C::NG * C::NLOC * (D + 1);
+    CK(cudaFuncSetAttribute(k_vol_contract_sx<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    phase_begin(ctx, PH_VOL_CONTRACT);
+    k_vol_contract_sx<D, P><<<dim3(E, D + 1, NS), 256, smem, st>>>(g, ctx->sx_vtab, ctx->sx_vnode, ctx->Kvol, ctx->Auu,
+                                                                  ctx->Auq);
+    CKL();
+    phase_end(ctx, PH_VOL_CONTRACT);
+  }
+  phase_begin(ctx, PH_FACES);
+  k_vol_res_sx<D, P><<<E, 128, 0, st>>>(g, ctx->sx_vtab, ctx->sx_vnode, ctx->rvol, ctx->RU);
+  CKL();
+  {
+    const long long tot = (long long)E * (D + 1) * ctx->nsf * C::NFP * NS * (D + 2);
+    k_face_point_sx<D, P><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(
+        g, ctx->sx_ftab, ctx->sx_fsub, ph, ctx->prob, ctx->bkind, ctx->bside, ctx->fnode, ctx->gather, ctx->uD, u, q,
+        uh, ctx->Kface, ctx->rface, E, ctx->fgeo);
+    CKL();
+    k_face_contract_sx<D, P><<<E, 256, 0, st>>>(g, ctx->sx_ftab, ctx->sx_fsub, ctx->fnode, ctx->Kface, ctx->rface,
+                                               ctx->Auu, ctx->Auq, ctx->Auh, ctx->Ahu, ctx->Ahq, ctx->Ahh, ctx->RU,
+                                               ctx->RUh);
+    CKL();
+  }
+  {
+    const long long tot = (long long)E * ctx->Nq;
+    k_rq<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(g, ctx->Mref, ctx->Gk, ctx->Ghk, ctx->gather, u, q, uh, ctx->RQ,
+                                                        E, ctx->sM, ctx->sG, ctx->sGh);
+    CKL();
+  }
+  phase_end(ctx, PH_FACES);
+  return MEHDG_OK;
+}
+
+int assemble_simplex(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt) {
+  const int d = ctx->d, p = ctx->p;
+  if (d == 2 && p == 1) return assemble_sx<2, 1>(ctx, u, q, uh, tt);
+  if (d == 2 && p == 2) return assemble_sx<2, 2>(ctx, u, q, uh, tt);
+  if (d == 2 && p == 3) return assemble_sx<2, 3>(ctx, u, q, uh, tt);
+  if (d == 3 && p == 1) return assemble_sx<3, 1>(ctx, u, q, uh, tt);
+  if (d == 3 && p == 2) return assemble_sx<3, 2>(ctx, u, q, uh, tt);
+  if (d == 3 && p == 3) return assemble_sx<3, 3>(ctx, u, q, uh, tt);
+  return ctx_fail(ctx, MEHDG_ERR_ARG, "unsupported (dim, p)");
+}
+
 // ---------------------------------------------------------------- flow diagnostics (Sec. 5.3)
 // Per macro-element (one CTA): the integrals of rho |v|^2 / 2, rho (omega . omega) / 2 and 1 by the
 // volume quadrature, threads striding over the (sub-element, Gauss point) pairs.  v = m / rho and
@@ -1287,7 +1619,8 @@ int flow_diag_dp(mehdg_ctx* ctx, const double* u, const double* q) {
 int assemble_all(mehdg_ctx* ctx, const double* u, const double* q, const double* uh, const mehdg_time_term* tt,
                  double* norms) {
   int rc;
-  if (ctx->opt.precision == MEHDG_PREC_MIXED) rc = assemble_bt<float>(ctx, u, q, uh, tt);
+  if (ctx->simplex) rc = assemble_simplex(ctx, u, q, uh, tt);
+  else if (ctx->opt.precision == MEHDG_PREC_MIXED) rc = assemble_bt<float>(ctx, u, q, uh, tt);
   else rc = assemble_bt<double>(ctx, u, q, uh, tt);
   if (rc) return rc;
   ctx->condensed = false;
@@ -1317,6 +1650,7 @@ extern "C" int mehdg_assemble_local(mehdg_ctx* ctx, const double* u, const doubl
 
 extern "C" int mehdg_flow_integrals(mehdg_ctx* ctx, const double* u, const double* q, double* out) {
   if (!ctx || !u || !q || !out) return MEHDG_ERR_ARG;
+  if (ctx->simplex) return ctx_fail(ctx, MEHDG_ERR_ARG, "flow integrals: box and shell meshes only");
   const int d = ctx->d, p = ctx->p;
   int rc;
   if (d == 2 && p == 1) rc = flow_diag_dp<2, 1>(ctx, u, q);

@@ -406,7 +406,7 @@ __global__ void k_minv_rq(const double* Minv, const double* RQ, double* out, int
 template <class T>
 // (ofn: each owner's local face node of every face node, or null when both owners share the order)
 __global__ void k_face_blocks(const T* Ahh, const int* owner, const int* ofn, double* fblk, int ns, int Nfn,
-                              int Nth, int Nt, int d, int F) {
+                              int Nth, int Nt, int nf, int F) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int nfb = ns * Nfn;
   if (i >= (long long)F * nfb * nfb) return;
@@ -418,7 +418,7 @@ __global__ void k_face_blocks(const T* Ahh, const int* owner, const int* ofn, do
   for (int o = 0; o < 2; ++o) {
     int ow = owner[2 * f + o];
     if (ow < 0) continue;
-    int e = ow / (2 * d), fl = ow % (2 * d);
+    int e = ow / nf, fl = ow % nf;
     const int lr = ofn ? ofn[((size_t)2 * f + o) * Nfn + jr] : jr;
     const int lc = ofn ? ofn[((size_t)2 * f + o) * Nfn + jc] : jc;
     v += Ahh[(size_t)e * Nt * Nt + ((size_t)sr * Nth + fl * Nfn + lr) * Nt + (size_t)sc * Nth + fl * Nfn + lc];
@@ -608,8 +608,8 @@ int condense_t(mehdg_ctx* ctx, double shift, double* bhat, int part = 0) {
   // face blocks of A_uhuh for the preconditioner, then their LU
   {
     long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
-    k_face_blocks<T><<<(tot + 255) / 256, 256, 0, st>>>(Ahh, ctx->owner, ctx->ofn, ctx->fblk, ns, ctx->Nfn, Nth, (int)Nt, d,
-                                                     ctx->F);
+    k_face_blocks<T><<<(tot + 255) / 256, 256, 0, st>>>(Ahh, ctx->owner, ctx->ofn, ctx->fblk, ns, ctx->Nfn, Nth, (int)Nt,
+                                                     ctx->nf, ctx->F);
     CKL();
   }
   phase_begin(ctx, PH_CONDENSE);
@@ -877,7 +877,7 @@ int condense_one(mehdg_ctx* ctx, double shift, double* bhat) {
   {
     long long tot = (long long)ctx->F * ctx->nfb * ctx->nfb;
     k_face_blocks<double><<<(tot + 255) / 256, 256, 0, st>>>(ctx->Ahh, ctx->owner, ctx->ofn, ctx->fblk, ns, ctx->Nfn, Nth,
-                                                            (int)Nt, d, ctx->F);
+                                                            (int)Nt, ctx->nf, ctx->F);
     CKL();
   }
   phase_begin(ctx, PH_CONDENSE);

@@ -113,6 +113,13 @@ struct mehdg_ctx {
   int* dflag = nullptr;      // device status words
   double* dred = nullptr;    // reduction scratch
   double* ddiag = nullptr;   // per-macro partial sums of mehdg_flow_integrals, [E][3] + 4
+  // simplicial macro-elements (mesh_kind MEHDG_MESH_SIMPLEX): reference tables on the device
+  int simplex = 0;
+  int nf = 0;                  // faces per macro-element: 2 d (boxes, shell), d + 1 (simplices)
+  double* sx_vtab = nullptr;   // [nel][Ng][nloc][d + 1]: phi, d phi / d xi_j of the sub-simplex's nodes
+  int* sx_vnode = nullptr;     // [nel][nloc] macro node of each sub-simplex node
+  double* sx_ftab = nullptr;   // [nf][nsf][nfp][nfs]: trace basis of the sub-face's nodes at its points
+  int* sx_fsub = nullptr;      // [nf][nsf][nfs] face node of each sub-face node
   double* hred = nullptr;    // pinned host mirror
 
   float *Wk32 = nullptr, *Whk32 = nullptr;   // FP32 copies of W_k, Wh_k (mixed precision)
@@ -198,8 +205,37 @@ int ctx_fail(mehdg_ctx* ctx, int code, const std::string& msg);
 // geometry helpers usable on the device
 struct Geo {
   int d, ns, m, p, n1, Np, Nfn, Nth, Nu, Nt, nel, nloc, ng1, Ng, nsf, nfs, nfp;
+  int nf;   // faces per macro-element
   double he[3];
 };
+
+// reference tables of the m-refined Kuhn simplex (csrc/simplex.cu)
+struct SxRef {
+  int d = 0, m = 0, p = 0, Np = 0, Nfn = 0, nel = 0, ng = 0, nloc = 0, nsf = 0, nfp = 0, nfs = 0;
+  std::vector<int> lat;        // [Np][d] integer node coordinates (spacing 1 / (m p))
+  std::vector<double> vxi;     // [nel ng][d] volume points in K
+  std::vector<double> vw;      // [nel ng] their weights
+  std::vector<double> vtab;    // [nel ng][nloc][d + 1]
+  std::vector<int> vnode;      // [nel][nloc]
+  std::vector<int> fnodes;     // [d + 1][Nfn] macro node of each face node
+  std::vector<double> nref;    // [d + 1][d] unit outward normals in K
+  std::vector<double> fM;      // [d + 1][d][d - 1] face vertex differences (xi = W0 + M t)
+  std::vector<double> fxi;     // [d + 1][nsf nfp][d] face points in K
+  std::vector<double> fwt;     // [d + 1][nsf nfp] their weights in face coordinates t
+  std::vector<double> ftab;    // [d + 1][nsf nfp][nfs]
+  std::vector<int> fsub;       // [d + 1][nsf][nfs]
+};
+// host geometry of a simplicial mesh, uploaded by setup()
+struct SxHost {
+  std::vector<double> vgeo, fgeo, xnode, xq, xf, M, Minv, Gk, Ghk, Wk, Whk, Bcat;
+};
+int sx_reference(int d, int m, int p, SxRef& R);
+int sx_maps(mehdg_ctx* ctx, SxRef& R, SxHost& H);
+int sx_source(mehdg_ctx* ctx, const double* xq, long long n, double* src);
+int sx_bdata(mehdg_ctx* ctx, const double* xf, long long n, int per_f, double* uD);
+int sx_init_state(mehdg_ctx* ctx, const double* du, double* u);
+void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w);
+void invert(std::vector<double>& A, int n);
 Geo make_geo(const mehdg_ctx* c);
 
 // launch helpers implemented in the .cu files

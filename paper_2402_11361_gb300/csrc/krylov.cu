@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_block_gemv(const float* __restrict__ Mi
 // summed from the face's (up to two) owners on the fly (the face reduction fused in).
 struct SlotMap {
   const int* owner;
-  int Nt, Nth, Nfn, twod;
+  int Nt, Nth, Nfn, nf;   // nf: faces per macro-element
 };
 __device__ __forceinline__ float bf16x4_dot(uint2 v, float4 x) {
   return __uint_as_float(v.x << 16) * x.x + __uint_as_float(v.x & 0xFFFF0000u) * x.y +
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_block_gemv_bf16(const unsigned short* _
           for (int o = 0; o < 2; ++o) {
             const int ow = sm.owner[2 * f + o];
             if (ow < 0) continue;
-            const int e = ow / sm.twod, fl = ow % sm.twod;
+            const int e = ow / sm.nf, fl = ow % sm.nf;
             a += r[(size_t)e * sm.Nt + (size_t)s * sm.Nth + fl * sm.Nfn + j];
           }
           v = (float)a;
@@ -472,7 +472,7 @@ static int block_jacobi(mehdg_ctx* ctx, const double* r, double* z, bool from_sl
     }
     const long long total = (long long)ctx->F * ctx->nfb, rows = (total + grid - 1) / grid;
     phase_begin(ctx, PH_PRECOND);
-    const SlotMap sm{ctx->owner, ctx->Nt, ctx->Nth, ctx->Nfn, 2 * ctx->d};
+    const SlotMap sm{ctx->owner, ctx->Nt, ctx->Nth, ctx->Nfn, ctx->nf};
     if (lowp && from_slot)
       k_block_gemv_bf16<true><<<grid, 256, xsm, ctx->stream>>>(ctx->finv16, ctx->ldf16, r, sm, z, ctx->nfb, ctx->F,
                                                                rows);

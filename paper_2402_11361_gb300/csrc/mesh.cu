@@ -125,6 +125,7 @@ Geo make_geo(const mehdg_ctx* c) {
   g.d = c->d; g.ns = c->ns; g.m = c->m; g.p = c->p; g.n1 = c->n1; g.Np = c->Np; g.Nfn = c->Nfn;
   g.Nth = c->Nth; g.Nu = c->Nu; g.Nt = c->Nt; g.nel = c->nel; g.nloc = c->nloc; g.ng1 = c->ng1;
   g.Ng = c->Ng; g.nsf = c->nsf; g.nfs = c->nfs; g.nfp = c->nfp;
+  g.nf = c->nf;
   for (int k = 0; k < 3; ++k) g.he[k] = c->he[k];
   return g;
 }
@@ -142,7 +143,7 @@ static void legendre(int n, double x, double& P, double& dP) {
   dP = n * (x * p1 - p0) / (x * x - 1.0);
 }
 
-static void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
   for (int i = 0; i < n; ++i) {
@@ -200,7 +201,7 @@ static void lagrange_at(const std::vector<double>& xn, double x, double* L, doub
 }
 
 // small dense inverse (Gauss-Jordan with partial pivoting)
-static void invert(std::vector<double>& A, int n) {
+void invert(std::vector<double>& A, int n) {
   std::vector<double> I(n * n, 0.0);
   for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
   for (int c = 0; c < n; ++c) {
@@ -263,35 +264,7 @@ __global__ void k_source(Geo g, const double* tab, mehdg_problem pr, double* src
     double hm = (pr.hi[k] - pr.lo[k]) / pr.nmac[k];
     x[k] = pr.lo[k] + ek * hm + (lk + 0.5 * (gx[gk] + 1.0)) * g.he[k];
   }
-  typedef Dual<Dual<double, D>, D> X2;
-  typedef Dual<double, D> T1;
-  X2 xs[D];
-  for (int k = 0; k < D; ++k) {
-    xs[k] = zero<X2>();
-    xs[k].v.v = x[k];
-    xs[k].v.d[k] = 1.0;
-    xs[k].d[k].v = 1.0;
-  }
-  X2 u2[NS];
-  if (pr.field == MEHDG_FIELD_COUETTE3D) field_couette3d<D, X2>(xs, pr.field_par, pr.gamma, u2);
-  else field_mms<D, X2>(xs, pr.field_par, pr.gamma, u2);
-  T1 uu[NS], qq[NS][D], F[NS][D], G[NS][D];
-  for (int s = 0; s < NS; ++s) {
-    uu[s].v = u2[s].v.v;
-    for (int l = 0; l < D; ++l) uu[s].d[l] = u2[s].v.d[l];
-    for (int j = 0; j < D; ++j) {
-      qq[s][j].v = u2[s].d[j].v;
-      for (int l = 0; l < D; ++l) qq[s][j].d[l] = u2[s].d[j].d[l];
-    }
-  }
-  Phys ph{pr.gamma, pr.Re, pr.Pr, 0, 1.0, 1};
-  inviscid_flux<D, T1>(uu, pr.gamma, F);
-  viscous_flux<D, T1>(uu, qq, ph, G);
-  for (int s = 0; s < NS; ++s) {
-    double f = 0.0;
-    for (int l = 0; l < D; ++l) f += F[s][l].d[l] + G[s][l].d[l];
-    src[tid * NS + s] = f;
-  }
+  closed_form_source<D>(pr.field == MEHDG_FIELD_COUETTE3D, pr.field_par, pr.gamma, pr.Re, pr.Pr, x, src + tid * NS);
 }
 
 // closed-form state at a physical point
@@ -379,7 +352,7 @@ __global__ void k_init_trace(Geo g, const int* owner, const int* fnode, const do
   int s = (tid / g.Nfn) % g.ns;
   int o = owner[2 * f];
   if (o < 0) o = owner[2 * f + 1];
-  int e = o / (2 * g.d), fl = o % (2 * g.d);
+  int e = o / g.nf, fl = o % g.nf;
   int a = fnode[fl * g.Nfn + j];
   uh[tid] = u[((long long)e * g.ns + s) * g.Np + a] + (duh ? duh[tid] : 0.0);
 }
@@ -441,8 +414,217 @@ static void default_options(mehdg_options* o) {
   o->condense_layers = 2;
 }
 
+// allocations common to every mesh kind: blocks, pointwise scratch, face blocks, reduction
+// scratch, Krylov and state vectors (tab, Wk, Whk: host tables for the FP32 copies of box meshes)
+static int setup_common(mehdg_ctx* ctx, const std::vector<double>& tab, const std::vector<double>& Wk,
+                        const std::vector<double>& Whk) {
+  const int d = ctx->d, E = ctx->E, F = ctx->F, ns = ctx->ns, Np = ctx->Np, Nfn = ctx->Nfn;
+  const size_t Nu = ctx->Nu, Nt = ctx->Nt;
+  cudaStream_t st = ctx->stream;
+
+  // blocks are FP32 in the mixed-precision path: allocate half the doubles
+  const size_t bsz = ctx->opt.precision == MEHDG_PREC_MIXED ? 2 : 1;
+  ALLOC(ctx->Auu, (size_t)E * Nu * Nu / bsz + 1);
+  ALLOC(ctx->Auq, (size_t)E * d * Nu * Nu / bsz + 1);
+  ALLOC(ctx->Auh, (size_t)E * Nu * Nt / bsz + 1);
+  ALLOC(ctx->Ahu, (size_t)E * Nt * Nu / bsz + 1);
+  ALLOC(ctx->Ahq, (size_t)E * d * Nt * Nu / bsz + 1);
+  ALLOC(ctx->Ahh, (size_t)E * Nt * Nt / bsz + 1);
+  ALLOC(ctx->perm, (size_t)E * Nu);
+  ALLOC(ctx->RQ, (size_t)E * d * Nu);
+  ALLOC(ctx->RU, (size_t)E * Nu);
+  ALLOC(ctx->RUh, (size_t)E * Nt);
+  ALLOC(ctx->gv, (size_t)E * Nu);
+  ALLOC(ctx->hv, (size_t)E * Nt);
+  ALLOC(ctx->MinvRQ, (size_t)E * d * Nu);
+  ALLOC(ctx->bloc, (size_t)E * Nt);
+  ALLOC(ctx->slot, (size_t)E * Nt);
+  {
+    size_t nk = (size_t)E * (d + 1) * ns * ctx->nel * ctx->Ng * (d + 1) * ns * (d + 1) / bsz + 1;
+    // the same scratch holds the face-block inverses of the mixed block-Jacobi (FP64, F nfb^2)
+    nk = std::max(nk, (size_t)ctx->F * ns * Nfn * ns * Nfn);
+    ALLOC(ctx->Kvol, nk);
+  }
+  ALLOC(ctx->rvol, (size_t)E * ctx->nel * ctx->Ng * ns * (d + 1));
+  ALLOC(ctx->Kface, (size_t)E * ctx->nf * ctx->nsf * ctx->nfp * ctx->ndir_f * 2 * ns);
+  ALLOC(ctx->rface, (size_t)E * ctx->nf * ctx->nsf * ctx->nfp * 2 * ns);
+  ctx->nfb = ns * Nfn;
+  ALLOC(ctx->fblk, (size_t)F * ctx->nfb * ctx->nfb);
+  ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
+  if (!ctx->dflag) ALLOC(ctx->dflag, 16);
+  ALLOC(ctx->dred, 1 << 17);
+  ALLOC(ctx->ddiag, (size_t)E * 3 + 4);
+  CK(cudaMemsetAsync(ctx->dred, 0, sizeof(double) << 17, st));   // reduction tickets start at zero
+  CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * 256));
+  ALLOC(ctx->dtcerr, 4);
+  CK(cudaMemsetAsync(ctx->dtcerr, 0, sizeof(int) * 4, st));
+  if (ctx->opt.precision == MEHDG_PREC_MIXED) {
+    ALLOC(ctx->finv32, (size_t)F * ctx->nfb * ctx->nfb);
+    if (ctx->mapped) {
+      // FP32 copies of the per-macro liftings and condensation factor
+      const long long nw = (long long)E * ctx->sG, nwh = (long long)E * ctx->sGh, nb = (long long)E * ctx->sB;
+      ALLOC(ctx->Wk32, nw);
+      ALLOC(ctx->Whk32, nwh);
+      ALLOC(ctx->Bcat32, nb);
+      int r_;
+      if ((r_ = to_float(ctx, ctx->Wk, ctx->Wk32, nw))) return r_;
+      if ((r_ = to_float(ctx, ctx->Whk, ctx->Whk32, nwh))) return r_;
+      if ((r_ = to_float(ctx, ctx->Bcat, ctx->Bcat32, nb))) return r_;
+    } else {
+      std::vector<float> w32(Wk.begin(), Wk.end()), wh32(Whk.begin(), Whk.end());
+      ALLOC(ctx->Wk32, w32.size());
+      ALLOC(ctx->Whk32, wh32.size());
+      CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
+    }
+    if (ctx->opt.refine_iters > 0) ALLOC(ctx->S32, (size_t)E * Nu * Nu);
+    ALLOC(ctx->u32, (size_t)E * ns * Np);
+    ALLOC(ctx->h32, (size_t)E * ns * Np);
+    ALLOC(ctx->q32, (size_t)E * d * ns * Np);
+    std::vector<float> t32(tab.begin(), tab.end());
+    ALLOC(ctx->tab32, t32.size());
+    CK(cudaMemcpy(ctx->tab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+  }
+  if (ctx->opt.apply_mode == 1) {
+    size_t esz = ctx->opt.precision == MEHDG_PREC_MIXED ? sizeof(float) : sizeof(double);
+    {
+      // forming A^T_i keeps a Nu x 32 block of right-hand sides in shared memory
+      int dev = 0, optin = 0;
+      CK(cudaGetDevice(&dev));
+      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      if (esz * Nu * 32 + 48 * 1024 > (size_t)optin)
+        return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1 needs Nu x 32 entries in shared memory; use apply_mode 0");
+    }
+    ALLOC(ctx->Xbuf, (size_t)E * Nu * Nt * esz / sizeof(double) + 1);
+    if (ctx->opt.precond_bf16) {
+      ctx->ld16 = (Nt + 3) & ~3;
+      ALLOC(ctx->Ahat16, (size_t)E * Nt * ctx->ld16);
+    }
+    if (ctx->opt.precond_bf16 && ctx->opt.precision == MEHDG_PREC_MIXED) {
+      ctx->ldf16 = (ctx->nfb + 31) & ~31;
+      ALLOC(ctx->finv16, (size_t)F * ctx->nfb * ctx->ldf16);
+    }
+  }
+  ctx->restart = std::min(120, std::max(2, ctx->opt.restart));
+  const long long n = ctx->ntr;
+  ALLOC(ctx->V, (size_t)(ctx->restart + 1) * n);
+  ALLOC(ctx->Zk, (size_t)ctx->restart * n);
+  ALLOC(ctx->wv, n);
+  ALLOC(ctx->tv, n);
+  ALLOC(ctx->tv2, n);
+  ALLOC(ctx->rv, n);
+  int nin = std::min(120, std::max(1, ctx->opt.inner_iters));
+  ALLOC(ctx->iV, (size_t)(nin + 1) * n);
+  ALLOC(ctx->iw, n);
+  ALLOC(ctx->xstart, n);
+  ALLOC(ctx->dHo, (size_t)(ctx->restart + 1) * ctx->restart + 3 * (size_t)ctx->restart + 1);
+  ALLOC(ctx->dHi, (size_t)(nin + 1) * nin + 3 * (size_t)nin + 1);
+  ALLOC(ctx->gin, n);
+  ALLOC(ctx->gout, n);
+  ALLOC(ctx->un, (size_t)E * Nu);
+  ALLOC(ctx->ustage, (size_t)3 * E * Nu);
+  ALLOC(ctx->hist, (size_t)E * Nu);
+  ALLOC(ctx->du, (size_t)E * Nu);
+  ALLOC(ctx->dq, (size_t)E * d * Nu);
+  ALLOC(ctx->duh, n);
+  ALLOC(ctx->bhat, n);
+
+  return MEHDG_OK;
+}
+
+// simplicial macro-elements: sizes, maps and per-macro geometry from csrc/simplex.cu, uploaded
+// as for curved macros (per-macro M, G_k, Gh_k, liftings and condensation factor), then the
+// common allocations and the closed-form data at the volume and face points.  FP64 only.
+static int setup_simplex(mehdg_ctx* ctx) {
+  const mehdg_problem& pr = ctx->prob;
+  const int d = pr.dim;
+  ctx->d = d;
+  ctx->ns = d + 2;
+  ctx->m = pr.m;
+  ctx->p = pr.p;
+  ctx->n1 = pr.m * pr.p + 1;
+  ctx->ng1 = pr.p + 3;
+  ctx->mapped = false;
+  ctx->simplex = 1;
+  ctx->ndir_v = ctx->ns * (1 + d);
+  ctx->ndir_f = ctx->ns * (d + 2);
+  SxRef R;
+  SxHost H;
+  if (int r_ = sx_maps(ctx, R, H)) return r_;
+  const int E = ctx->E, F = ctx->F, Np = ctx->Np, Nfn = ctx->Nfn, Nth = ctx->Nth, Nt = ctx->Nt, nf = ctx->nf;
+  const int ns = ctx->ns;
+  ctx->sM = (size_t)Np * Np;
+  ctx->sG = (size_t)d * Np * Np;
+  ctx->sGh = (size_t)d * Np * Nth;
+  ctx->sB = (size_t)d * Np * (Np + Nth);
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  ALLOC(ctx->gather, (size_t)E * Nt);
+  ALLOC(ctx->owner, 2 * (size_t)F);
+  ALLOC(ctx->bkind, (size_t)E * nf);
+  ALLOC(ctx->bside, (size_t)E * nf);
+  ALLOC(ctx->fnode, (size_t)nf * Nfn);
+  ALLOC(ctx->ofn, ctx->h_ofn.size());
+  ALLOC(ctx->Mref, (size_t)E * ctx->sM);
+  ALLOC(ctx->Minv, (size_t)E * ctx->sM);
+  ALLOC(ctx->Gk, (size_t)E * ctx->sG);
+  ALLOC(ctx->Wk, (size_t)E * ctx->sG);
+  ALLOC(ctx->Ghk, (size_t)E * ctx->sGh);
+  ALLOC(ctx->Whk, (size_t)E * ctx->sGh);
+  ALLOC(ctx->Bcat, (size_t)E * ctx->sB);
+  ALLOC(ctx->vgeo, H.vgeo.size());
+  ALLOC(ctx->fgeo, H.fgeo.size());
+  ALLOC(ctx->xnode, H.xnode.size());
+  ALLOC(ctx->sx_vtab, R.vtab.size());
+  ALLOC(ctx->sx_vnode, R.vnode.size());
+  ALLOC(ctx->sx_ftab, R.ftab.size());
+  ALLOC(ctx->sx_fsub, R.fsub.size());
+  CK(up(ctx->gather, ctx->h_gather.data(), sizeof(int) * ctx->h_gather.size()));
+  CK(up(ctx->owner, ctx->h_owner.data(), sizeof(int) * ctx->h_owner.size()));
+  CK(up(ctx->bkind, ctx->h_bkind.data(), sizeof(int) * ctx->h_bkind.size()));
+  CK(up(ctx->bside, ctx->h_bside.data(), sizeof(int) * ctx->h_bside.size()));
+  CK(up(ctx->fnode, ctx->facenode.data(), sizeof(int) * ctx->facenode.size()));
+  CK(up(ctx->ofn, ctx->h_ofn.data(), sizeof(int) * ctx->h_ofn.size()));
+  CK(up(ctx->Mref, H.M.data(), sizeof(double) * H.M.size()));
+  CK(up(ctx->Minv, H.Minv.data(), sizeof(double) * H.Minv.size()));
+  CK(up(ctx->Gk, H.Gk.data(), sizeof(double) * H.Gk.size()));
+  CK(up(ctx->Wk, H.Wk.data(), sizeof(double) * H.Wk.size()));
+  CK(up(ctx->Ghk, H.Ghk.data(), sizeof(double) * H.Ghk.size()));
+  CK(up(ctx->Whk, H.Whk.data(), sizeof(double) * H.Whk.size()));
+  CK(up(ctx->Bcat, H.Bcat.data(), sizeof(double) * H.Bcat.size()));
+  CK(up(ctx->vgeo, H.vgeo.data(), sizeof(double) * H.vgeo.size()));
+  CK(up(ctx->fgeo, H.fgeo.data(), sizeof(double) * H.fgeo.size()));
+  CK(up(ctx->xnode, H.xnode.data(), sizeof(double) * H.xnode.size()));
+  CK(up(ctx->sx_vtab, R.vtab.data(), sizeof(double) * R.vtab.size()));
+  CK(up(ctx->sx_vnode, R.vnode.data(), sizeof(int) * R.vnode.size()));
+  CK(up(ctx->sx_ftab, R.ftab.data(), sizeof(double) * R.ftab.size()));
+  CK(up(ctx->sx_fsub, R.fsub.data(), sizeof(int) * R.fsub.size()));
+  if (int r_ = setup_common(ctx, std::vector<double>(), std::vector<double>(), std::vector<double>())) return r_;
+  // closed-form data: the source at the volume points, the boundary data at the face points
+  const long long nvol = (long long)E * ctx->nel * ctx->Ng, nfac = (long long)E * nf * ctx->nsf * ctx->nfp;
+  double* xtmp = nullptr;
+  CK(cudaMalloc(&xtmp, sizeof(double) * std::max(H.xq.size(), H.xf.size())));
+  int rc = MEHDG_OK;
+  if (pr.field == MEHDG_FIELD_MMS || pr.field == MEHDG_FIELD_COUETTE3D) {
+    rc = alloc(ctx, (void**)&ctx->src, sizeof(double) * (size_t)nvol * ns);
+    if (!rc && up(xtmp, H.xq.data(), sizeof(double) * H.xq.size()) != cudaSuccess)
+      rc = ctx_fail(ctx, MEHDG_ERR_CUDA, "simplex: point upload");
+    if (!rc) rc = sx_source(ctx, xtmp, nvol, ctx->src);
+    if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = ctx_fail(ctx, MEHDG_ERR_CUDA, "simplex: source");
+  }
+  if (!rc) rc = alloc(ctx, (void**)&ctx->uD, sizeof(double) * (size_t)nfac * ns);
+  if (!rc && up(xtmp, H.xf.data(), sizeof(double) * H.xf.size()) != cudaSuccess)
+    rc = ctx_fail(ctx, MEHDG_ERR_CUDA, "simplex: point upload");
+  if (!rc) rc = sx_bdata(ctx, xtmp, nfac, ctx->nsf * ctx->nfp, ctx->uD);
+  if (!rc && cudaStreamSynchronize(ctx->stream) != cudaSuccess) rc = ctx_fail(ctx, MEHDG_ERR_CUDA, "simplex: boundary data");
+  cudaFree(xtmp);
+  return rc;
+}
+
 static int setup(mehdg_ctx* ctx) {
   const mehdg_problem& pr = ctx->prob;
+  if (pr.mesh_kind == MEHDG_MESH_SIMPLEX) return setup_simplex(ctx);
   const int d = pr.dim;
   ctx->d = d;
   ctx->ns = d + 2;
@@ -468,6 +650,7 @@ static int setup(mehdg_ctx* ctx) {
   ctx->Nq = d * ctx->Nu;
   ctx->Nt = ctx->ns * ctx->Nth;
   ctx->mapped = pr.mesh_kind == MEHDG_MESH_SHELL;
+  ctx->nf = 2 * d;
   ctx->E = 1;
   ctx->F = 0;
   int npos[3] = {1, 1, 1};
@@ -769,113 +952,7 @@ static int setup(mehdg_ctx* ctx) {
     }
   }
   CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
-
-  // blocks are FP32 in the mixed-precision path: allocate half the doubles
-  const size_t bsz = ctx->opt.precision == MEHDG_PREC_MIXED ? 2 : 1;
-  ALLOC(ctx->Auu, (size_t)E * Nu * Nu / bsz + 1);
-  ALLOC(ctx->Auq, (size_t)E * d * Nu * Nu / bsz + 1);
-  ALLOC(ctx->Auh, (size_t)E * Nu * Nt / bsz + 1);
-  ALLOC(ctx->Ahu, (size_t)E * Nt * Nu / bsz + 1);
-  ALLOC(ctx->Ahq, (size_t)E * d * Nt * Nu / bsz + 1);
-  ALLOC(ctx->Ahh, (size_t)E * Nt * Nt / bsz + 1);
-  ALLOC(ctx->perm, (size_t)E * Nu);
-  ALLOC(ctx->RQ, (size_t)E * d * Nu);
-  ALLOC(ctx->RU, (size_t)E * Nu);
-  ALLOC(ctx->RUh, (size_t)E * Nt);
-  ALLOC(ctx->gv, (size_t)E * Nu);
-  ALLOC(ctx->hv, (size_t)E * Nt);
-  ALLOC(ctx->MinvRQ, (size_t)E * d * Nu);
-  ALLOC(ctx->bloc, (size_t)E * Nt);
-  ALLOC(ctx->slot, (size_t)E * Nt);
-  {
-    size_t nk = (size_t)E * (d + 1) * ns * ctx->nel * ctx->Ng * (d + 1) * ns * (d + 1) / bsz + 1;
-    // the same scratch holds the face-block inverses of the mixed block-Jacobi (FP64, F nfb^2)
-    nk = std::max(nk, (size_t)ctx->F * ns * Nfn * ns * Nfn);
-    ALLOC(ctx->Kvol, nk);
-  }
-  ALLOC(ctx->rvol, (size_t)E * ctx->nel * ctx->Ng * ns * (d + 1));
-  ALLOC(ctx->Kface, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * ctx->ndir_f * 2 * ns);
-  ALLOC(ctx->rface, (size_t)E * 2 * d * ctx->nsf * ctx->nfp * 2 * ns);
-  ctx->nfb = ns * Nfn;
-  ALLOC(ctx->fblk, (size_t)F * ctx->nfb * ctx->nfb);
-  ALLOC(ctx->fperm, (size_t)F * ctx->nfb);
-  if (!ctx->dflag) ALLOC(ctx->dflag, 16);
-  ALLOC(ctx->dred, 1 << 17);
-  ALLOC(ctx->ddiag, (size_t)E * 3 + 4);
-  CK(cudaMemsetAsync(ctx->dred, 0, sizeof(double) << 17, st));   // reduction tickets start at zero
-  CK(cudaMallocHost((void**)&ctx->hred, sizeof(double) * 256));
-  ALLOC(ctx->dtcerr, 4);
-  CK(cudaMemsetAsync(ctx->dtcerr, 0, sizeof(int) * 4, st));
-  if (ctx->opt.precision == MEHDG_PREC_MIXED) {
-    ALLOC(ctx->finv32, (size_t)F * ctx->nfb * ctx->nfb);
-    if (ctx->mapped) {
-      // FP32 copies of the per-macro liftings and condensation factor
-      const long long nw = (long long)E * ctx->sG, nwh = (long long)E * ctx->sGh, nb = (long long)E * ctx->sB;
-      ALLOC(ctx->Wk32, nw);
-      ALLOC(ctx->Whk32, nwh);
-      ALLOC(ctx->Bcat32, nb);
-      int r_;
-      if ((r_ = to_float(ctx, ctx->Wk, ctx->Wk32, nw))) return r_;
-      if ((r_ = to_float(ctx, ctx->Whk, ctx->Whk32, nwh))) return r_;
-      if ((r_ = to_float(ctx, ctx->Bcat, ctx->Bcat32, nb))) return r_;
-    } else {
-      std::vector<float> w32(Wk.begin(), Wk.end()), wh32(Whk.begin(), Whk.end());
-      ALLOC(ctx->Wk32, w32.size());
-      ALLOC(ctx->Whk32, wh32.size());
-      CK(cudaMemcpy(ctx->Wk32, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(ctx->Whk32, wh32.data(), sizeof(float) * wh32.size(), cudaMemcpyHostToDevice));
-    }
-    if (ctx->opt.refine_iters > 0) ALLOC(ctx->S32, (size_t)E * Nu * Nu);
-    ALLOC(ctx->u32, (size_t)E * ns * Np);
-    ALLOC(ctx->h32, (size_t)E * ns * Np);
-    ALLOC(ctx->q32, (size_t)E * d * ns * Np);
-    std::vector<float> t32(tab.begin(), tab.end());
-    ALLOC(ctx->tab32, t32.size());
-    CK(cudaMemcpy(ctx->tab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
-  }
-  if (ctx->opt.apply_mode == 1) {
-    size_t esz = ctx->opt.precision == MEHDG_PREC_MIXED ? sizeof(float) : sizeof(double);
-    {
-      // forming A^T_i keeps a Nu x 32 block of right-hand sides in shared memory
-      int dev = 0, optin = 0;
-      CK(cudaGetDevice(&dev));
-      CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      if (esz * Nu * 32 + 48 * 1024 > (size_t)optin)
-        return ctx_fail(ctx, MEHDG_ERR_ARG, "apply_mode 1 needs Nu x 32 entries in shared memory; use apply_mode 0");
-    }
-    ALLOC(ctx->Xbuf, (size_t)E * Nu * Nt * esz / sizeof(double) + 1);
-    if (ctx->opt.precond_bf16) {
-      ctx->ld16 = (Nt + 3) & ~3;
-      ALLOC(ctx->Ahat16, (size_t)E * Nt * ctx->ld16);
-    }
-    if (ctx->opt.precond_bf16 && ctx->opt.precision == MEHDG_PREC_MIXED) {
-      ctx->ldf16 = (ctx->nfb + 31) & ~31;
-      ALLOC(ctx->finv16, (size_t)F * ctx->nfb * ctx->ldf16);
-    }
-  }
-  ctx->restart = std::min(120, std::max(2, ctx->opt.restart));
-  const long long n = ctx->ntr;
-  ALLOC(ctx->V, (size_t)(ctx->restart + 1) * n);
-  ALLOC(ctx->Zk, (size_t)ctx->restart * n);
-  ALLOC(ctx->wv, n);
-  ALLOC(ctx->tv, n);
-  ALLOC(ctx->tv2, n);
-  ALLOC(ctx->rv, n);
-  int nin = std::min(120, std::max(1, ctx->opt.inner_iters));
-  ALLOC(ctx->iV, (size_t)(nin + 1) * n);
-  ALLOC(ctx->iw, n);
-  ALLOC(ctx->xstart, n);
-  ALLOC(ctx->dHo, (size_t)(ctx->restart + 1) * ctx->restart + 3 * (size_t)ctx->restart + 1);
-  ALLOC(ctx->dHi, (size_t)(nin + 1) * nin + 3 * (size_t)nin + 1);
-  ALLOC(ctx->gin, n);
-  ALLOC(ctx->gout, n);
-  ALLOC(ctx->un, (size_t)E * Nu);
-  ALLOC(ctx->ustage, (size_t)3 * E * Nu);
-  ALLOC(ctx->hist, (size_t)E * Nu);
-  ALLOC(ctx->du, (size_t)E * Nu);
-  ALLOC(ctx->dq, (size_t)E * d * Nu);
-  ALLOC(ctx->duh, n);
-  ALLOC(ctx->bhat, n);
+  if (int r_ = setup_common(ctx, tab, Wk, Whk)) return r_;
 
   // closed-form data
   Geo g = make_geo(ctx);
@@ -948,6 +1025,15 @@ extern "C" int mehdg_mesh(mehdg_ctx** out, const mehdg_problem* prob, int nprob,
       if (pr.bc[b] < MEHDG_BC_DIRICHLET || pr.bc[b] > MEHDG_BC_FARFIELD) return MEHDG_ERR_ARG;
     // (tc_mode 2 and 3 run the condensation with one lifting shared by all macro-elements)
     if (opt && (opt->condense_layers == 1 || opt->tc_mode == 2 || opt->tc_mode == 3)) return MEHDG_ERR_ARG;
+  } else if (pr.mesh_kind == MEHDG_MESH_SIMPLEX) {
+    // simplicial macros: FP64, second-layer condensation, the dense Algorithm-2 apply, SIMT
+    // kernels, per-macro M^-1 and the sub-simplex tables in shared memory (m p <= 6)
+    if (pr.m * pr.p > 6) return MEHDG_ERR_ARG;
+    for (int k = 0; k < pr.dim; ++k)
+      if (pr.nmac[k] < 1 || !(pr.hi[k] > pr.lo[k])) return MEHDG_ERR_ARG;
+    if (opt && (opt->precision != MEHDG_PREC_FP64 || opt->apply_mode != 0 || opt->tc_mode != 0 ||
+                opt->condense_layers != 2))
+      return MEHDG_ERR_ARG;
   } else {
     if (pr.mesh_kind != MEHDG_MESH_BOX) return MEHDG_ERR_ARG;
     for (int k = 0; k < pr.dim; ++k)
@@ -993,13 +1079,16 @@ extern "C" int mehdg_init_state(mehdg_ctx* ctx, const double* du, const double* 
   if (!ctx || !u || !q || !uh) return MEHDG_ERR_ARG;
   Geo g = make_geo(ctx);
   cudaStream_t st = ctx->stream;
-  const double* xnode1 = ctx->tab + 2 * ctx->ng1 * (ctx->p + 1) + 2 * ctx->ng1;
   long long tot = (long long)ctx->E * ctx->Np;
   int bs = 128;
-  if (ctx->mapped) {
+  if (ctx->simplex) {
+    int r_ = sx_init_state(ctx, du, u);
+    if (r_) return r_;
+  } else if (ctx->mapped) {
     int r_ = shell_init_state(ctx, du, u);
     if (r_) return r_;
   } else {
+    const double* xnode1 = ctx->tab + 2 * ctx->ng1 * (ctx->p + 1) + 2 * ctx->ng1;
     if (ctx->d == 2) k_init_state<2><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
     else k_init_state<3><<<(tot + bs - 1) / bs, bs, 0, st>>>(g, ctx->prob, xnode1, du, u);
     CKL();
@@ -1093,7 +1182,7 @@ extern "C" void mehdg_destroy(mehdg_ctx* ctx) {
                   ctx->ustage, ctx->hist, ctx->du, ctx->dq, ctx->duh, ctx->bhat, ctx->Xbuf, ctx->Wk32,
                   ctx->Whk32, ctx->dtcerr, ctx->finv32, ctx->u32, ctx->q32, ctx->h32, ctx->tab32, ctx->src32,
                   ctx->uD32, ctx->uh32, ctx->Bcat, ctx->Bcat32, ctx->klift, ctx->Aloc, ctx->Rloc, ctx->Xloc, ctx->permL, ctx->dHo, ctx->dHi, ctx->gin, ctx->gout, ctx->Ahat16, ctx->finv16,
-                  ctx->vgeo, ctx->fgeo, ctx->xnode, ctx->ofn, ctx->ddiag};
+                  ctx->vgeo, ctx->fgeo, ctx->xnode, ctx->ofn, ctx->ddiag, ctx->sx_vtab, ctx->sx_vnode, ctx->sx_ftab, ctx->sx_fsub};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->hred) cudaFreeHost(ctx->hred);

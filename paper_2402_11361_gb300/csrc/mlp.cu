@@ -336,7 +336,7 @@ extern "C" int mehdg_mlp_setup(mehdg_ctx* ctx, int hidden, unsigned long long se
   // gather maps: owner o of face f is (e, fl), face fl' of e is gather[e][fl' Nfn] / (ns Nfn)
   std::vector<int> nbr;
   if (neighbors) {
-    const int nf = 2 * ctx->d;
+    const int nf = ctx->nf;
     m->nnb = 2 * (nf - 1);
     nbr.assign((size_t)ctx->F * m->nnb, -1);
     for (int f = 0; f < ctx->F; ++f) {

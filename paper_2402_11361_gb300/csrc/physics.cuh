@@ -348,6 +348,44 @@ HD void field_couette3d(const X* x, const double* par, double g, X* u) {
   conserved_from<D, X>(rho, v, P, g, u);
 }
 
+// the source f = div (F + G) of a closed-form field (the manufactured solution, or the 3D Couette
+// flow when couette3d) at the point x: the field on second-order duals gives u, grad u and the
+// derivatives of grad u, first-order duals carry the fluxes' divergence
+template <int D>
+HD void closed_form_source(bool couette3d, const double* par, double g, double Re, double Pr, const double* x,
+                           double* f) {
+  constexpr int NS = D + 2;
+  typedef Dual<Dual<double, D>, D> X2;
+  typedef Dual<double, D> T1;
+  X2 xs[D];
+  for (int k = 0; k < D; ++k) {
+    xs[k] = zero<X2>();
+    xs[k].v.v = x[k];
+    xs[k].v.d[k] = 1.0;
+    xs[k].d[k].v = 1.0;
+  }
+  X2 u2[NS];
+  if (couette3d) field_couette3d<D, X2>(xs, par, g, u2);
+  else field_mms<D, X2>(xs, par, g, u2);
+  T1 uu[NS], qq[NS][D], F[NS][D], G[NS][D];
+  for (int s = 0; s < NS; ++s) {
+    uu[s].v = u2[s].v.v;
+    for (int l = 0; l < D; ++l) uu[s].d[l] = u2[s].v.d[l];
+    for (int j = 0; j < D; ++j) {
+      qq[s][j].v = u2[s].d[j].v;
+      for (int l = 0; l < D; ++l) qq[s][j].d[l] = u2[s].d[j].d[l];
+    }
+  }
+  Phys ph{g, Re, Pr, 0, 1.0, 1};
+  inviscid_flux<D, T1>(uu, g, F);
+  viscous_flux<D, T1>(uu, qq, ph, G);
+  for (int s = 0; s < NS; ++s) {
+    double v = 0.0;
+    for (int l = 0; l < D; ++l) v += F[s][l].d[l] + G[s][l].d[l];
+    f[s] = v;
+  }
+}
+
 template <int D>
 HD void field_uniform(const double* par, double g, double* u) {
   double rho = par[0], v[D];
