@@ -83,7 +83,12 @@ extern "C" {
 
 /* mesh kinds */
 #define MEHDG_MESH_BOX 0      /* nmac, lo, hi, periodic: a box of box macro-elements */
-#define MEHDG_MESH_SIMPLEX 2  /* nmac, lo, hi, periodic: each box cell split into d! simplicial macros */
+#define MEHDG_MESH_SIMPLEX 2  /* nmac, lo, hi, periodic: each box cell split into d! simplicial
+    macro-elements (the Kuhn triangulation), each refined m times into m^d sub-simplices with P_p
+    (the data-layout notes above give the numbering).  Boundary sides as on box meshes (the planes
+    x_k = lo_k, hi_k).  SUPG length h = min_k (hi_k - lo_k) / nmac_k / m.  Supported with precision
+    FP64, apply_mode 0, tc_mode 0, condense_layers 2 and m p <= 6; mehdg_flow_integrals refuses
+    these meshes. */
 #define MEHDG_MESH_SHELL 1    /* dim 3: cubed-sphere O-grid of the shell r0 <= |x| <= r1 (flow past a
     sphere).  E = 6 nq^2 nr curved macro-elements; macro e = ((panel nr + k) nq + j) nq + i for the
     cube panels (+x, -x, +y, -y, +z, -z) with frames (e_n, e_1, e_2) = (x, y, z), (-x, z, y),
