@@ -58,18 +58,18 @@ struct mehdg_ctx {
 
   // host tables
   std::vector<double> b1, db1, gw;   // [ng1][p+1] reference basis at Gauss points, weights
-  std::vector<int> facenode;         // [2d][Nfn] macro node of each face node
+  std::vector<int> facenode;         // [nf][Nfn] macro node of each face node (nf faces per macro)
   std::vector<int> h_gather;         // [E][Nt]
   std::vector<int> h_owner;          // [F][2] (e * 2d + fl) or -1
-  std::vector<int> h_bkind;          // [E][2d]
-  std::vector<int> h_bside;          // [E][2d] domain side or -1
+  std::vector<int> h_bkind;          // [E][nf]
+  std::vector<int> h_bside;          // [E][nf] domain side or -1
 
   // device: maps and reference data
   int* gather = nullptr;     // [E][Nt]
   int* owner = nullptr;      // [F][2]
-  int* bkind = nullptr;      // [E][2d]
-  int* bside = nullptr;      // [E][2d]
-  int* fnode = nullptr;      // [2d][Nfn]
+  int* bkind = nullptr;      // [E][nf]
+  int* bside = nullptr;      // [E][nf]
+  int* fnode = nullptr;      // [nf][Nfn]
   double* tab = nullptr;     // b1, db1, gw packed
   double* Mref = nullptr;    // [Np][Np]
   double* Minv = nullptr;    // [Np][Np]
@@ -93,13 +93,13 @@ struct mehdg_ctx {
   bool no_phase = false;
   bool mapped = false;
   double* vgeo = nullptr;    // [E][nel][Ng][d*d + 1]: (J^-1)[j][k] = dxi_j/dx_k (xi in [0,1]^d), weight
-  double* fgeo = nullptr;    // [E][2d][nsf][nfp][d + 1]: unit outward normal, weight
+  double* fgeo = nullptr;    // [E][nf][nsf][nfp][d + 1]: unit outward normal, weight
   double* xnode = nullptr;   // [E][d][Np] node positions
   int* ofn = nullptr;        // [F][2][Nfn] owner's local face node of each face node (null: same order)
   std::vector<int> h_ofn;
   size_t sM = 0, sG = 0, sGh = 0, sB = 0;
   double* src = nullptr;     // [E][nel][Ng][ns] or null
-  double* uD = nullptr;      // [E][2d][nsf][nfp][ns] or null
+  double* uD = nullptr;      // [E][nf][nsf][nfp][ns] or null
 
   // device: blocks (FP64)
   double *Auu = nullptr, *Auq = nullptr, *Auh = nullptr, *Ahu = nullptr, *Ahq = nullptr, *Ahh = nullptr;
