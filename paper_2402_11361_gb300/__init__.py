@@ -466,7 +466,8 @@ class Context:
         self._check(self.lib.mehdg_mlp_params(self.h, 0, None, ctypes.byref(n)), "mlp_params")
         self.mlp_nparams = n.value
         self.mlp_nout = ((self.info["ns"] * self.info["Nfn"] + 31) // 32) * 32
-        self.mlp_nin = (2 + (2 * (2 * self.info["dim"] - 1) if neighbors else 0)) * self.mlp_nout
+        nf = self.info["Nth"] // self.info["Nfn"]          # faces per macro-element
+        self.mlp_nin = (2 + (2 * (nf - 1) if neighbors else 0)) * self.mlp_nout
         self.mlp_hidden = int(hidden)
 
     def mlp_params(self, values=None):

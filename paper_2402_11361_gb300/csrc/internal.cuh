@@ -92,7 +92,7 @@ struct mehdg_ctx {
   const double* dshift = nullptr;
   bool no_phase = false;
   bool mapped = false;
-  double* vgeo = nullptr;    // [E][nel][Ng][d*d + 1]: (J^-1)[j][k] = dxi_j/dx_k (xi in [0,1]^d), weight
+  double* vgeo = nullptr;    // [E][nel][Ng][d*d + 1]: (J^-1)[j][k] = dxi_j/dx_k (xi the macro reference coordinates), weight
   double* fgeo = nullptr;    // [E][nf][nsf][nfp][d + 1]: unit outward normal, weight
   double* xnode = nullptr;   // [E][d][Np] node positions
   int* ofn = nullptr;        // [F][2][Nfn] owner's local face node of each face node (null: same order)
