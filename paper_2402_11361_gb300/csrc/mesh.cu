@@ -270,10 +270,8 @@ __global__ void k_source(Geo g, const double* tab, mehdg_problem pr, double* src
 // closed-form state at a physical point
 template <int D>
 __device__ void field_at(const mehdg_problem& pr, const double* x, double* u) {
-  if (pr.field == MEHDG_FIELD_MMS) field_mms<D, double>(x, pr.field_par, pr.gamma, u);
-  else if (pr.field == MEHDG_FIELD_COUETTE3D) field_couette3d<D, double>(x, pr.field_par, pr.gamma, u);
-  else if (pr.field == MEHDG_FIELD_TGV) field_tgv<D, double>(x, pr.field_par, pr.gamma, u);
-  else field_uniform<D>(pr.field_par, pr.gamma, u);
+  static_assert(MEHDG_FIELD_MMS == 1 && MEHDG_FIELD_TGV == 3 && MEHDG_FIELD_COUETTE3D == 5, "field kinds");
+  closed_form_state<D>(pr.field, pr.field_par, pr.gamma, x, u);
 }
 
 template <int D>

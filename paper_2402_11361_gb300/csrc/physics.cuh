@@ -393,3 +393,14 @@ HD void field_uniform(const double* par, double g, double* u) {
   double P = rho * par[4] / g;
   conserved_from<D, double>(rho, v, P, g, u);
 }
+
+// the closed-form state of a problem's field at the point x: kind 1 the manufactured solution,
+// 3 the Taylor-Green vortex, 5 the 3D Couette flow, otherwise the uniform state of par (the
+// values of the library's field kinds)
+template <int D>
+HD void closed_form_state(int kind, const double* par, double g, const double* x, double* u) {
+  if (kind == 1) field_mms<D, double>(x, par, g, u);
+  else if (kind == 5) field_couette3d<D, double>(x, par, g, u);
+  else if (kind == 3) field_tgv<D, double>(x, par, g, u);
+  else field_uniform<D>(par, g, u);
+}

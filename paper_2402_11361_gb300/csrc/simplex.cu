@@ -668,13 +668,6 @@ int sx_maps(mehdg_ctx* ctx, SxRef& R, SxHost& H) {
 // ---------------------------------------------------------------- closed-form data at points
 namespace {
 
-template <int D>
-__device__ void sx_field(const mehdg_problem& pr, const double* x, double* u) {
-  if (pr.field == MEHDG_FIELD_MMS) field_mms<D, double>(x, pr.field_par, pr.gamma, u);
-  else if (pr.field == MEHDG_FIELD_COUETTE3D) field_couette3d<D, double>(x, pr.field_par, pr.gamma, u);
-  else if (pr.field == MEHDG_FIELD_TGV) field_tgv<D, double>(x, pr.field_par, pr.gamma, u);
-  else field_uniform<D>(pr.field_par, pr.gamma, u);
-}
 
 // source f = div (F + G) of the closed form at the volume points x [n][D]
 template <int D>
@@ -695,7 +688,7 @@ __global__ void k_sx_bdata(long long n, int per_f, mehdg_problem pr, const int* 
   if (i >= n) return;
   const int bk = bkind[i / per_f];
   double* out = uD + i * NS;
-  if (bk == MEHDG_BC_DIRICHLET) sx_field<D>(pr, x + i * D, out);
+  if (bk == MEHDG_BC_DIRICHLET) closed_form_state<D>(pr.field, pr.field_par, pr.gamma, x + i * D, out);
   else if (bk == MEHDG_BC_FARFIELD) field_uniform<D>(pr.field_par, pr.gamma, out);
   else
     for (int s = 0; s < NS; ++s) out[s] = 0.0;
@@ -712,7 +705,7 @@ __global__ void k_sx_init(long long n, int Np, mehdg_problem pr, const double* _
   const long long e = i / Np;
   double x[D], uu[NS];
   for (int k = 0; k < D; ++k) x[k] = xnode[(e * D + k) * Np + a];
-  sx_field<D>(pr, x, uu);
+  closed_form_state<D>(pr.field, pr.field_par, pr.gamma, x, uu);
   for (int s = 0; s < NS; ++s) {
     const size_t o = ((size_t)e * NS + s) * Np + a;
     u[o] = uu[s] + (du ? du[o] : 0.0);
