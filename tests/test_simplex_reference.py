@@ -68,7 +68,8 @@ def test_simplex_reference_rejects_bad_arguments(pkg):
         pkg.simplex_reference(3, 2, 4)
 
 
-@pytest.mark.parametrize("case", ["2d_dirichlet_p2", "2d_periodic_p1_m3", "3d_dirichlet_p1", "3d_periodic_p2_m1"])
+@pytest.mark.parametrize("case", ["2d_dirichlet_p2", "2d_periodic_p1_m3", "2d_wall_p2_m3", "3d_dirichlet_p1",
+                                  "3d_periodic_p2_m1", "3d_periodic_x_p3_m1"])
 def test_simplex_mesh_maps_and_operators_match_the_oracle(pkg, case):
     """The library's simplicial mesh (host code) against the oracle's: the same macro and face
     numbering, gather maps (node by node), owners, boundary sides and node positions, and the
@@ -81,8 +82,14 @@ def test_simplex_mesh_maps_and_operators_match_the_oracle(pkg, case):
         pr = W.mms(dim=2, nmac=2, m=2, p=2)
     elif case == "2d_periodic_p1_m3":
         pr = W.periodic_uniform(dim=2, nmac=2, m=3, p=1)
+    elif case == "2d_wall_p2_m3":
+        pr = W.couette2d(nmac=2, m=3, p=2)
     elif case == "3d_dirichlet_p1":
         pr = W.mms(dim=3, nmac=1, m=2, p=1)
+    elif case == "3d_periodic_x_p3_m1":
+        pr = W.mms(dim=3, nmac=2, m=1, p=3)
+        pr["periodic"] = [1, 0, 0]
+        pr["bc"][0] = pr["bc"][1] = W.BC_NONE
     else:
         pr = W.periodic_uniform(dim=3, nmac=2, m=1, p=2)
     pr["mesh_kind"] = W.MESH_SIMPLEX
